@@ -1,0 +1,201 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+* brute-force second quantisation (explicit determinants, e^{-T} H e^{T}) for M, b_p, c_q at
+  random amplitudes and several shapes: a dropped term, wrong sign, factor or index fails here;
+* closed forms: Koopmans poles when T = Lambda = 0 and v = 0; the exact resolvent of Eq. gfxn0 over
+  the whole N-1 sector when T = Lambda = 0 and o = 2;
+* linear algebra: dense LU and GMRES agree; the reduced model interpolates the full one at its
+  sampled frequencies, is exact when S spans the space, and is invariant under a unitary change of
+  basis of S; the refinement loop reaches its tolerance;
+* the generator: SplitMix64's published first output, Box-Muller moments, 8-fold symmetry.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import bc, fockspace, hbar, mor
+from oracle import sigma as sg
+from oracle import solve as sv
+
+
+def _random_case(o, v, seed):
+    return synth.random_amplitudes(synth.make_inputs(o, v, seed, scale_mode="literal"), seed + 1)
+
+
+@pytest.mark.parametrize("o,v,seed", [(2, 3, 5), (3, 3, 11), (3, 5, 12), (4, 4, 13), (5, 3, 14),
+                                      (2, 6, 15), (4, 6, 16)])
+def test_sigma_b_c_match_brute_force(o, v, seed):
+    inp = _random_case(o, v, seed)
+    bf = fockspace.build_from_inputs(inp)
+    hb = hbar.build(inp)
+    M = sg.dense_matrix(hb)
+    scale = np.abs(bf.M).max()
+    assert np.abs(M - bf.M).max() <= 1e-12 * scale
+    assert np.abs(bc.b_vectors(inp) - bf.b).max() <= 1e-12
+    assert np.abs(bc.c_vectors(inp) - bf.c).max() <= 1e-12
+
+
+@pytest.mark.parametrize("part", ["t1", "t2", "l1", "l2"])
+def test_each_amplitude_block_matters(part):
+    """Zeroing one amplitude block changes M (or c): the pins above are not vacuous."""
+    inp = _random_case(3, 4, 21)
+    bf = fockspace.build_from_inputs(inp)
+    getattr(inp, part)[:] = 0.0
+    hb = hbar.build(inp)
+    dM = np.abs(sg.dense_matrix(hb) - bf.M).max()
+    dc = np.abs(bc.c_vectors(inp) - bf.c).max()
+    db = np.abs(bc.b_vectors(inp) - bf.b).max()
+    assert max(dM, dc, db) > 1e-4
+
+
+def test_tiny_workload_brute_force():
+    """The o=4, v=8 workload with its MP2-like amplitudes (495-determinant N sector)."""
+    W = synth.WORKLOADS["tiny_o4_v8"]
+    inp = synth.make_inputs(W["o"], W["v"], W["seed"])
+    bf = fockspace.build_from_inputs(inp)
+    hb = hbar.build(inp)
+    assert np.abs(sg.dense_matrix(hb) - bf.M).max() <= 1e-12
+    assert np.abs(bc.b_vectors(inp) - bf.b).max() <= 1e-13
+    assert np.abs(bc.c_vectors(inp) - bf.c).max() <= 1e-13
+    # G from the brute-force objects equals the oracle's
+    ws = np.linspace(W["wmin"], W["wmax"], 7)
+    Xb = sv.dense_solve(bf.M, bf.b, ws, W["eta"])
+    Xo = sv.dense_solve(sg.dense_matrix(hb), bc.b_vectors(inp), ws, W["eta"])
+    Gb = sv.green(bf.c, Xb)
+    Go = sv.green(bc.c_vectors(inp), Xo)
+    assert np.abs(Gb - Go).max() <= 1e-10 * np.abs(Gb).max()
+
+
+def test_koopmans_limit():
+    """T = Lambda = 0, v = 0: G_ii(w) = 1/(w - eps_i - i eta), no other poles."""
+    inp = synth.make_inputs(5, 0, 3, with_t=False, with_lambda=False)
+    hb = hbar.build(inp)
+    M = sg.dense_matrix(hb)
+    ws = np.linspace(-2, 0, 11)
+    eta = 0.01
+    G = sv.green(bc.c_vectors(inp), sv.dense_solve(M, bc.b_vectors(inp), ws, eta))
+    ref = np.zeros_like(G)
+    for i in range(5):
+        ref[:, i, i] = 1.0 / (ws - inp.eps[i] - 1j * eta)
+    assert np.abs(G - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("v,seed", [(3, 7), (6, 8)])
+def test_exact_resolvent_when_space_is_complete(v, seed):
+    """T = Lambda = 0 and o = 2: 1h+2h1p is the whole N-1 sector, so Eq. gfxn0 (with Psi = Phi,
+    E_0 = E_HF) is reproduced exactly, for every (p, q)."""
+    inp = synth.make_inputs(2, v, seed, scale_mode="literal", with_t=False, with_lambda=False)
+    bf = fockspace.build_from_inputs(inp)
+    hb = hbar.build(inp)
+    ws = np.linspace(-1.5, 0.5, 9)
+    eta = 0.02
+    G = sv.green(bc.c_vectors(inp), sv.dense_solve(sg.dense_matrix(hb), bc.b_vectors(inp), ws, eta))
+    Gx = fockspace.exact_resolvent(bf, ws, eta)
+    assert np.abs(G - Gx).max() <= 1e-12 * np.abs(Gx).max()
+
+
+def test_gmres_matches_dense():
+    inp = synth.make_inputs(6, 12, 31)
+    hb = hbar.build(inp)
+    B = bc.b_vectors(inp, range(8))
+    ws = [-1.0, -0.55, -0.2]
+    Xd = sv.dense_solve(sg.dense_matrix(hb), B, ws, 0.01)
+    Xg, res = sv.gmres_solve(hb, B, ws, 0.01, tol=1e-11)
+    assert res.max() <= 1e-11
+    assert np.abs(Xd - Xg).max() <= 1e-9 * np.abs(Xd).max()
+
+
+def _mor_case():
+    inp = synth.make_inputs(5, 10, 41)
+    hb = hbar.build(inp)
+    p = list(range(5))
+    return inp, hb, bc.b_vectors(inp, p), bc.c_vectors(inp, p), sg.dense_matrix(hb)
+
+
+def test_mor_interpolates_at_sampled_frequencies():
+    inp, hb, B, C, M = _mor_case()
+    seeds = [-1.1, -0.8, -0.5]
+    X = sv.dense_solve(M, B, seeds, 0.01)
+    S, kept = mor.orthonormalise(None, X.reshape(-1, X.shape[-1]).T)
+    assert all(kept)
+    rm = mor.project(hb, S, B, C)
+    Gh = mor.reduced_green(rm, seeds, 0.01)
+    G = sv.green(C, X)
+    assert np.abs(Gh - G).max() <= 1e-11 * np.abs(G).max()
+    # and it is NOT exact away from the samples (the test is not vacuous)
+    Gm = sv.green(C, sv.dense_solve(M, B, [-0.65], 0.01))
+    assert np.abs(mor.reduced_green(rm, [-0.65], 0.01) - Gm).max() > 1e-6 * np.abs(Gm).max()
+
+
+def test_mor_exact_when_subspace_is_whole_space():
+    inp, hb, B, C, M = _mor_case()
+    D = M.shape[0]
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((D, D)) + 1j * rng.standard_normal((D, D)))
+    rm = mor.project(hb, Q, B, C)
+    ws = np.linspace(-1.2, -0.3, 13)
+    G = sv.green(C, sv.dense_solve(M, B, ws, 0.01))
+    assert np.abs(mor.reduced_green(rm, ws, 0.01) - G).max() <= 1e-10 * np.abs(G).max()
+
+
+def test_mor_invariant_under_unitary_change_of_basis():
+    inp, hb, B, C, M = _mor_case()
+    X = sv.dense_solve(M, B, [-1.0, -0.4], 0.01)
+    S, _ = mor.orthonormalise(None, X.reshape(-1, X.shape[-1]).T)
+    rng = np.random.default_rng(1)
+    U, _ = np.linalg.qr(rng.standard_normal((S.shape[1],) * 2) + 1j * rng.standard_normal((S.shape[1],) * 2))
+    ws = np.linspace(-1.2, -0.3, 9)
+    G1 = mor.reduced_green(mor.project(hb, S, B, C), ws, 0.01)
+    G2 = mor.reduced_green(mor.project(hb, S @ U, B, C), ws, 0.01)
+    assert np.abs(G1 - G2).max() <= 1e-11 * np.abs(G1).max()
+
+
+def test_orthonormalise_drops_dependent_columns():
+    rng = np.random.default_rng(2)
+    Y = rng.standard_normal((40, 5)) + 1j * rng.standard_normal((40, 5))
+    Y = np.concatenate([Y, Y[:, :2] @ np.array([[1.0, 2.0], [3.0, -1.0]])], axis=1)
+    S, kept = mor.orthonormalise(None, Y)
+    assert kept == [True] * 5 + [False, False]
+    assert np.abs(S.conj().T @ S - np.eye(5)).max() <= 1e-14
+
+
+def test_refinement_reaches_tolerance_and_matches_full():
+    inp, hb, B, C, M = _mor_case()
+    r = mor.build_and_refine(hb, B, C, [-1.2, -0.75, -0.3], -1.2, -0.3, 300, 0.01, 1e-6,
+                             10 ** 6, solver="dense", M=M)
+    assert r.converged and r.history[-1][1] <= 1e-6
+    grid = np.linspace(-1.2, -0.3, 300)
+    A = sv.spectral(sv.green(C, sv.dense_solve(M, B, grid, 0.01)))
+    Ah = sv.spectral(mor.reduced_green(r.model, grid, 0.01))
+    assert np.abs(A - Ah).max() <= 1e-6 * np.abs(A).max()
+    # the error estimate decreases from round to round
+    assert r.history[0][1] > r.history[-1][1]
+
+
+def test_refinement_respects_order_bound():
+    inp, hb, B, C, M = _mor_case()
+    r = mor.build_and_refine(hb, B, C, [-1.2, -0.3], -1.2, -0.3, 300, 0.01, 1e-12, 20,
+                             solver="dense", M=M)
+    assert r.model.m <= 20 and not r.converged
+
+
+def test_splitmix64_published_value_and_normals():
+    # SplitMix64 from state 0: first output 0xE220A8397B1DCDAF (Steele et al. reference code)
+    assert int(synth._mix(np.array([0x9E3779B97F4A7C15], dtype=np.uint64))[0]) == 0xE220A8397B1DCDAF
+    z = synth.normal(5, 9, np.arange(200000))
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1.0) < 0.01
+    g = synth.make_inputs(3, 4, 9).full_antisym()
+    assert np.abs(g + g.transpose(1, 0, 2, 3)).max() == 0.0
+    assert np.abs(g + g.transpose(0, 1, 3, 2)).max() == 0.0
+    assert np.abs(g - g.transpose(2, 3, 0, 1)).max() == 0.0
+
+
+def test_generator_blocks_are_slices_of_the_full_tensor():
+    inp = synth.make_inputs(3, 4, 9, scale_mode="literal")
+    g = inp.full_antisym()
+    o = 3
+    assert np.array_equal(inp.oooo, g[:o, :o, :o, :o])
+    assert np.array_equal(inp.ooov, g[:o, :o, :o, o:])
+    assert np.array_equal(inp.oovv, g[:o, :o, o:, o:])
+    assert np.array_equal(inp.ovov, g[:o, o:, :o, o:])
+    assert np.array_equal(inp.ovvv, g[:o, o:, o:, o:])
