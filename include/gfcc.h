@@ -1,0 +1,167 @@
+/*
+ * gfcc.h - C ABI of libgfcc: IP Green's-function coupled cluster (GFCCSD) linear systems and their
+ * model-order reduction on one GB300 GPU.
+ *
+ * Method (Peng, Van Beeumen, Williams-Young, Kowalski, Yang, "Approximate Green's function coupled
+ * cluster method employing effective dimension reduction", arXiv 1902.06016):
+ *   Eq. xp      X_p(w) = sum_i x^i a_i + sum_{i<j,a} x^{ij}_a a_a^+ a_j a_i   (1h + 2h1p space)
+ *   Eq. xplin   (w + Hbar_N - i eta) X_p(w)|Phi> = abar_p |Phi>
+ *   Eq. gfxn2   G_pq(w) = <Phi|(1 + Lambda) abar_q^+ X_p(w)|Phi> = c_q^T X_p(w)
+ *   Eq. gfcclineqn / model   MIMO system, Galerkin reduced model Hhat = S^H Hbar S, bhat = S^H b,
+ *                            chat^T = c^T S over an orthonormal subspace S of solved X_p(w_k)
+ *   MOR text after Eq. model: adaptive refinement by midpoints of adjacent sampled frequencies.
+ *   A(w) = -(1/pi) sum_p Im G_pp(w)   (spectral function, returned exactly as written).
+ *
+ * Conventions (all entry points):
+ *   - Status: 0 = success, negative = error (GFCC_ERR_*); gfcc_last_error() gives the message.
+ *   - Indices: o occupied and v virtual spin-orbitals, n = o + v, occupied first. P = o(o-1)/2.
+ *     Vector dimension D = o + P*v. Packed vector index: i for x^i; o + pair(i,j)*v + a for
+ *     x^{ij}_a with i < j and pair(i,j) = j(j-1)/2 + i.
+ *   - Complex numbers are interleaved (re, im) doubles. A block of nvec vectors is column-major:
+ *     vector c starts at element c*ld (complex units), ld >= D.
+ *   - Pointer arguments marked "host or device" may point to host memory or to device memory on
+ *     the context's GPU; the kind is detected with cudaPointerGetAttributes. Host buffers are
+ *     copied synchronously; device buffers are used in place on the context's stream.
+ *   - All inputs are copied (the caller keeps ownership); all outputs are caller-allocated.
+ *   - Calls on one context are not thread-safe; distinct contexts are independent.
+ */
+#ifndef GFCC_H
+#define GFCC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GFCC_OK 0
+#define GFCC_ERR_ARG (-1)            /* invalid argument (sizes, null pointers, ranges) */
+#define GFCC_ERR_NOT_CONVERGED (-2)  /* iteration cap reached before the tolerance */
+#define GFCC_ERR_RANK (-3)           /* subspace became rank deficient / empty */
+#define GFCC_ERR_NONFINITE (-4)      /* NaN or Inf in inputs or iterates */
+#define GFCC_ERR_OOM (-5)            /* device allocation failed */
+#define GFCC_ERR_CUDA (-6)           /* CUDA runtime error */
+#define GFCC_ERR_STATE (-7)          /* call out of order (e.g. mor_eval before mor_build) */
+
+/* arithmetic of the H-bar sigma contractions */
+#define GFCC_PREC_FP64 0        /* FP64 everywhere */
+#define GFCC_PREC_TF32 1        /* ring/oooo GEMMs on tcgen05 kind::tf32, FP32 accumulate (inner solves) */
+#define GFCC_PREC_BF16 2        /* ring/oooo GEMMs on tcgen05 kind::f16 (bf16), FP32 accumulate */
+#define GFCC_PREC_BF16X2 3      /* split bf16 (hi+lo of the operator), FP32 accumulate */
+
+typedef struct gfcc_ctx* gfcc_t;
+
+/* Antisymmetrised two-electron integral blocks <pq||rs>, real, row-major, occupied index range
+ * first: oooo[i][j][k][l], ooov[i][j][k][a], oovv[i][j][a][b], ovov[i][a][j][b], ovvv[i][a][b][c].
+ * Host pointers. (No vvvv block is needed by the IP space.) */
+typedef struct {
+  const double* oooo;
+  const double* ooov;
+  const double* oovv;
+  const double* ovov;
+  const double* ovvv;
+} gfcc_vblocks;
+
+typedef struct {
+  double tol;          /* relative residual ||b - A x|| / ||b|| at which a column is converged (1e-8) */
+  int restart;         /* Krylov dimension per restart cycle (GMRES(k)); default 30 */
+  int max_restarts;    /* cycle cap per column; default 200 */
+  int precision;       /* GFCC_PREC_* of the inner (Krylov) sigma; residuals are always FP64 */
+  int max_batch;       /* max columns (p, w) per batched solve; 0 = choose from memory */
+  double drop_tol;     /* subspace rank-truncation threshold (relative), default 1e-10 */
+  int verbose;         /* 0 silent, 1 per-call summary on stderr */
+} gfcc_opts;
+
+typedef struct {
+  long long sigma_calls;   /* batched sigma launches */
+  long long sigma_cols;    /* complex columns processed by sigma */
+  long long gmres_iters;   /* Arnoldi steps summed over batches */
+  long long restarts;      /* restart (iterative-refinement) cycles summed over batches */
+  double max_rel_res;      /* largest final relative residual over the columns of the call */
+  int not_converged;       /* columns that hit the cycle cap */
+} gfcc_stats;
+
+/* Fill *opts with the defaults listed above. */
+int gfcc_default_opts(gfcc_opts* opts);
+
+/* Create a context on the current CUDA device: copy the ground-state inputs and build the H-bar
+ * elements of the IP space on the GPU (Hbar_N = e^{-T} H e^{T} - E_0, text after Eq. gfxn1),
+ * the free terms b_p (Eq. xplin) and the left vectors c_q (Eq. gfxn2) for all n orbitals.
+ *   eps[n]      orbital energies (the reference Fock matrix is diag(eps)); host.
+ *   vb          integral blocks, host.
+ *   t1[o][v], t2[o][o][v][v] (t_ij^ab, antisymmetric), l1[o][v] (lambda^i_a), l2[o][o][v][v]
+ *               (lambda^ij_ab); host.
+ *   opts        may be NULL (defaults).  stream: cudaStream_t or NULL for the legacy stream.
+ * Errors: GFCC_ERR_ARG (o < 2, v < 1, null pointers), GFCC_ERR_NONFINITE, GFCC_ERR_OOM, GFCC_ERR_CUDA. */
+int gfcc_init(gfcc_t* ctx, int o, int v, const double* eps, const gfcc_vblocks* vb,
+              const double* t1, const double* t2, const double* l1, const double* l2,
+              const gfcc_opts* opts, void* stream);
+
+/* Dimension D of the 1h+2h1p space. */
+int gfcc_dim(gfcc_t ctx, int* D);
+
+/* Replace the options (tolerance, restart length, precision, ...) of an existing context. */
+int gfcc_set_opts(gfcc_t ctx, const gfcc_opts* opts);
+
+/* Y = M X (transpose = 0) or Y = M^T X (transpose = 1) for nvec complex vectors, where M is the
+ * matrix of Hbar_N on the 1h+2h1p space (Eq. xplin). X, Y: host or device, column-major with
+ * leading dimension ld (complex units). precision: GFCC_PREC_*. */
+int gfcc_sigma(gfcc_t ctx, const double* X, double* Y, int nvec, int ld, int precision,
+               int transpose);
+
+/* b_p (transpose = 0) or c_q (transpose = 1) rows for the given orbitals: out[k*ld + nu], real,
+ * host or device. Eqs. xplin and gfxn2. */
+int gfcc_vectors(gfcc_t ctx, const int* orbitals, int norb, int transpose, double* out, int ld);
+
+/* Full-dimension solves of Eq. xplin for every (w, p): (w - i eta + M) X_p(w) = b_p, by batched
+ * restarted GMRES with iterative refinement (FP64 residuals, inner sigma in opts.precision).
+ *   omegas[nw] (host), orbitals[np] (host, p set), qorb[nq] (host, q set; NULL = same as p set).
+ *   G  (optional, host or device): G[(w*np + p)*nq + q] complex = c_q^T X_p(w).
+ *   A  (optional, host or device): A[w] = -(1/pi) sum_{p in set, p also in q set} Im G_pp(w).
+ *   X  (optional, host or device): X[(w*np + p)*ldx ...] complex solutions, ldx >= D.
+ *   stats (optional, host).
+ * Returns GFCC_ERR_NOT_CONVERGED (outputs still written) if a column hit the cycle cap. */
+int gfcc_solve_full(gfcc_t ctx, const double* omegas, int nw, double eta, const int* orbitals,
+                    int np, const int* qorb, int nq, double* G, double* A, double* X, int ldx,
+                    gfcc_stats* stats);
+
+/* Start a reduced model (Eq. model): solve Eq. xplin at the seed frequencies for every p in
+ * orbitals (host), orthonormalise the solutions into S (columns whose norm after two
+ * Gram-Schmidt passes falls below opts.drop_tol of their norm before are dropped), and project:
+ * Hhat = S^H M S, bhat = S^H b, chat = c^T S. qorb/nq as in gfcc_solve_full. */
+int gfcc_mor_build(gfcc_t ctx, const double* seeds, int ns, double eta, const int* orbitals,
+                   int np, const int* qorb, int nq);
+
+/* Adaptive refinement (MOR text after Eq. model): on a uniform grid of ngrid points over
+ * [wmin, wmax], estimate for each interval between adjacent sampled frequencies the largest relative
+ * residual ||(w - i eta + M) S yhat_p - b_p|| / ||b_p|| (grid points strictly inside, all p); add
+ * the midpoints of intervals above tol (largest first, ties to the lower frequency) while the
+ * model order stays <= m_max; re-solve, re-project and repeat until every estimate is <= tol.
+ * m_out (host, optional) receives the final order; max_err (host, optional) the last estimate.
+ * Returns GFCC_ERR_NOT_CONVERGED if m_max stopped the refinement first. */
+int gfcc_mor_refine(gfcc_t ctx, double wmin, double wmax, int ngrid, double tol, int m_max,
+                    int* m_out, double* max_err);
+
+/* Evaluate the reduced model at nw frequencies (host array): Ghat (optional, host or device,
+ * layout as in gfcc_solve_full) and A (optional, host or device). maxres (optional, host or
+ * device): per-frequency max over p of the relative residual estimate. */
+int gfcc_mor_eval(gfcc_t ctx, const double* omegas, int nw, double* G, double* A, double* maxres);
+
+/* Sampled frequencies of the current model: writes up to cap values to w (host) and the count to
+ * *ns; *m receives the model order, *np and *nq the sizes of the p and q orbital sets. Any output
+ * pointer may be NULL. */
+int gfcc_mor_info(gfcc_t ctx, double* w, int cap, int* ns, int* m, int* np, int* nq);
+
+/* Save / load the reduced model (sampled frequencies, S, Z = M S and the projected matrices) so that
+ * refinement resumes without re-solving. The file is a flat binary written by this library. */
+int gfcc_mor_save(gfcc_t ctx, const char* path);
+int gfcc_mor_load(gfcc_t ctx, const char* path);
+
+/* Message of the last error on this context ("" if none). Valid until the next call. */
+const char* gfcc_last_error(gfcc_t ctx);
+
+/* Release all device memory of the context. NULL is allowed. */
+void gfcc_free(gfcc_t ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GFCC_H */

@@ -1,0 +1,628 @@
+// C ABI of libgfcc (declared in include/gfcc.h): argument checks, host/device marshalling, batching
+// and the host side of the adaptive MOR refinement loop. All arithmetic runs in the kernels of the
+// other translation units.
+#include "gfcc_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <fstream>
+#include <new>
+
+using gfcc::cplx;
+using gfcc::DBuf;
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// copy n bytes from a user buffer (host or device) to device memory
+void copy_in(void* dst_dev, const void* src, size_t n, cudaStream_t s) {
+  GFCC_CUDA(cudaMemcpyAsync(dst_dev, src, n, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+void copy_out(void* dst, const void* src_dev, size_t n, cudaStream_t s) {
+  GFCC_CUDA(cudaMemcpyAsync(dst, src_dev, n, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+}
+
+int choose_batch(gfcc_ctx* c, long long ncols) {
+  if (c->opts.max_batch > 0) return (int)std::min<long long>(ncols, c->opts.max_batch);
+  size_t freeb = 0, totalb = 0;
+  if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) { cudaGetLastError(); freeb = 8ull << 30; }
+  const long long D = c->D, ov = (long long)c->o * c->v;
+  const long long per_col = (long long)sizeof(cplx) * (D * (c->opts.restart + 10)) + 16LL * ov * c->o * 2 + 4096;
+  long long nb = (long long)(0.5 * (double)freeb) / per_col;
+  nb = std::max<long long>(1, std::min<long long>({nb, ncols, 1024}));
+  return (int)nb;
+}
+
+__global__ void spectral_kernel(const cplx* G, int nw, int np, int nq, const int* qidx, double* A) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nw) return;
+  double s = 0.0;
+  for (int p = 0; p < np; ++p)
+    if (qidx[p] >= 0) s += G[((long long)w * np + p) * nq + qidx[p]].y;
+  A[w] = -s / 3.14159265358979323846;
+}
+
+// MX = B - shift X - R   (all batch-minor [D][nb])
+__global__ void mx_kernel(const cplx* B, const cplx* X, const cplx* R, const cplx* shift, cplx* MX, long long D, int nb) {
+  long long total = D * nb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    int c = (int)(t % nb);
+    cplx sx = cuCmul(shift[c], X[t]);
+    MX[t] = make_cuDoubleComplex(B[t].x - sx.x - R[t].x, B[t].y - sx.y - R[t].y);
+  }
+}
+
+__global__ void rownorm2_kernel(const double* rows, long long D, const int* idx, int n, double* out) {
+  __shared__ double red[256];
+  int r = blockIdx.x;
+  const double* x = rows + (long long)idx[r] * D;
+  double s = 0.0;
+  for (long long t = threadIdx.x; t < D; t += blockDim.x) s += x[t] * x[t];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[r] = red[0];
+}
+
+int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  return (int)std::min<long long>(std::max<long long>(g, 1), 152LL * 32);
+}
+
+std::vector<int> q_positions(const std::vector<int>& porb, const std::vector<int>& qorb) {
+  std::vector<int> qi(porb.size(), -1);
+  for (size_t p = 0; p < porb.size(); ++p)
+    for (size_t q = 0; q < qorb.size(); ++q)
+      if (qorb[q] == porb[p]) { qi[p] = (int)q; break; }
+  return qi;
+}
+
+// Solve all (w, p) columns; writes X (batch-minor, [D][ncols]) and R into caller-provided device
+// buffers when non-null, and G [ncols][nq] when Gdev is non-null.
+void solve_columns(gfcc_ctx* c, const std::vector<double>& ws, double eta, const std::vector<int>& porb,
+                   const std::vector<int>& qorb, cplx* Gdev, cplx* Xall, cplx* Rall, gfcc_stats* st_out) {
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  const int np = (int)porb.size(), nq = (int)qorb.size();
+  const long long ncols = (long long)ws.size() * np;
+  const int nbmax = choose_batch(c, ncols);
+  c->stats = gfcc::Stats{};
+  DBuf<cplx> B, X, R, sh;
+  DBuf<int> rows;
+  B.alloc(D * nbmax); X.alloc(D * nbmax); R.alloc(D * nbmax); sh.alloc(nbmax); rows.alloc(nbmax);
+  double maxres = 0.0;
+  int notconv = 0;
+  for (long long c0 = 0; c0 < ncols; c0 += nbmax) {
+    const int nb = (int)std::min<long long>(nbmax, ncols - c0);
+    std::vector<int> hr(nb);
+    std::vector<cplx> hs(nb);
+    for (int k = 0; k < nb; ++k) {
+      long long col = c0 + k;
+      hr[k] = porb[col % np];
+      hs[k] = make_cuDoubleComplex(ws[col / np], -eta);
+    }
+    GFCC_CUDA(cudaMemcpyAsync(rows.p, hr.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s));
+    GFCC_CUDA(cudaMemcpyAsync(sh.p, hs.data(), sizeof(cplx) * nb, cudaMemcpyHostToDevice, s));
+    gfcc::gather_rows_real_to_cplx(c->bvec.p, (int)D, rows.p, nb, (int)D, B.p, nb, s);
+    gfcc::SolveStatus st;
+    gfcc::gmres_batched(c, B.p, X.p, R.p, sh.p, nb, st, false);
+    for (int k = 0; k < nb; ++k) {
+      maxres = std::max(maxres, st.relres[k]);
+      if (!st.converged[k]) ++notconv;
+    }
+    if (Gdev) gfcc::green_from_batch(c->cvec.p, (int)D, qorb.data(), nq, X.p, nb, nb, Gdev + c0 * nq, s);
+    if (Xall) {  // copy columns into the big batch-minor block [D][ncols]
+      GFCC_CUDA(cudaMemcpy2DAsync(Xall + c0, sizeof(cplx) * ncols, X.p, sizeof(cplx) * nb, sizeof(cplx) * nb, D,
+                                  cudaMemcpyDeviceToDevice, s));
+    }
+    if (Rall) {
+      GFCC_CUDA(cudaMemcpy2DAsync(Rall + c0, sizeof(cplx) * ncols, R.p, sizeof(cplx) * nb, sizeof(cplx) * nb, D,
+                                  cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  GFCC_CUDA(cudaStreamSynchronize(s));
+  c->stats.max_rel_res = maxres;
+  c->stats.not_converged = notconv;
+  if (st_out) {
+    st_out->sigma_calls = c->stats.sigma_calls;
+    st_out->sigma_cols = c->stats.sigma_cols;
+    st_out->gmres_iters = c->stats.gmres_iters;
+    st_out->restarts = c->stats.restarts;
+    st_out->max_rel_res = maxres;
+    st_out->not_converged = notconv;
+  }
+}
+
+// Solve at frequencies ws for the model's p set and append the solutions to the subspace.
+void mor_add_frequencies(gfcc_ctx* c, const std::vector<double>& ws) {
+  gfcc::MorState& ms = c->mor;
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  const int np = (int)ms.porb.size();
+  const long long ncols = (long long)ws.size() * np;
+  DBuf<cplx> X, R, MX, B, sh;
+  DBuf<int> rows;
+  X.alloc(D * ncols); R.alloc(D * ncols); MX.alloc(D * ncols); B.alloc(D * ncols); sh.alloc(ncols);
+  rows.alloc(ncols);
+  solve_columns(c, ws, ms.eta, ms.porb, ms.qorb, nullptr, X.p, R.p, nullptr);
+  std::vector<int> hr(ncols);
+  std::vector<cplx> hs(ncols);
+  for (long long k = 0; k < ncols; ++k) {
+    hr[k] = ms.porb[k % np];
+    hs[k] = make_cuDoubleComplex(ws[k / np], -ms.eta);
+  }
+  GFCC_CUDA(cudaMemcpyAsync(rows.p, hr.data(), sizeof(int) * ncols, cudaMemcpyHostToDevice, s));
+  GFCC_CUDA(cudaMemcpyAsync(sh.p, hs.data(), sizeof(cplx) * ncols, cudaMemcpyHostToDevice, s));
+  gfcc::gather_rows_real_to_cplx(c->bvec.p, (int)D, rows.p, (int)ncols, (int)D, B.p, (int)ncols, s);
+  mx_kernel<<<grid_for(D * ncols), 256, 0, s>>>(B.p, X.p, R.p, sh.p, MX.p, D, (int)ncols);
+  GFCC_LAUNCH_CHECK();
+  GFCC_CUDA(cudaStreamSynchronize(s));
+  gfcc::mor_append(c, X.p, MX.p, (int)ncols);
+  for (double w : ws) ms.sampled.push_back(w);
+  std::sort(ms.sampled.begin(), ms.sampled.end());
+}
+
+}  // namespace
+
+#define API_BEGIN \
+  try {
+#define API_END(ctx)                                                   \
+  }                                                                    \
+  catch (gfcc::Error & e) {                                            \
+    if (ctx) (ctx)->last_error = e.msg;                                \
+    return e.code;                                                     \
+  }                                                                    \
+  catch (std::bad_alloc&) {                                            \
+    if (ctx) (ctx)->last_error = "host allocation failed";             \
+    return GFCC_ERR_OOM;                                               \
+  }                                                                    \
+  catch (std::exception & e) {                                         \
+    if (ctx) (ctx)->last_error = e.what();                             \
+    return GFCC_ERR_ARG;                                               \
+  }                                                                    \
+  return GFCC_OK;
+
+extern "C" {
+
+int gfcc_default_opts(gfcc_opts* o) {
+  if (!o) return GFCC_ERR_ARG;
+  o->tol = 1e-8;
+  o->restart = 30;
+  o->max_restarts = 200;
+  o->precision = GFCC_PREC_FP64;
+  o->max_batch = 0;
+  o->drop_tol = 1e-10;
+  o->verbose = 0;
+  return GFCC_OK;
+}
+
+static int check_opts(const gfcc_opts* o, std::string& why) {
+  if (!(o->tol > 0.0 && o->tol < 1.0)) { why = "opts.tol must be in (0, 1)"; return GFCC_ERR_ARG; }
+  if (o->restart < 1 || o->restart > 256) { why = "opts.restart must be in [1, 256]"; return GFCC_ERR_ARG; }
+  if (o->max_restarts < 1) { why = "opts.max_restarts must be >= 1"; return GFCC_ERR_ARG; }
+  if (o->precision < GFCC_PREC_FP64 || o->precision > GFCC_PREC_BF16X2) { why = "opts.precision unknown"; return GFCC_ERR_ARG; }
+  if (o->max_batch < 0) { why = "opts.max_batch must be >= 0"; return GFCC_ERR_ARG; }
+  if (!(o->drop_tol > 0.0 && o->drop_tol < 1.0)) { why = "opts.drop_tol must be in (0, 1)"; return GFCC_ERR_ARG; }
+  return GFCC_OK;
+}
+
+int gfcc_init(gfcc_t* out, int o, int v, const double* eps, const gfcc_vblocks* vb, const double* t1,
+              const double* t2, const double* l1, const double* l2, const gfcc_opts* opts, void* stream) {
+  if (!out) return GFCC_ERR_ARG;
+  *out = nullptr;
+  if (o < 2 || v < 1 || !eps || !vb || !t1 || !t2 || !l1 || !l2 || !vb->oooo || !vb->ooov || !vb->oovv ||
+      !vb->ovov || !vb->ovvv)
+    return GFCC_ERR_ARG;
+  const long long P = (long long)o * (o - 1) / 2;
+  const long long D = o + P * v;
+  if (D >= (1LL << 31) || (long long)o * v * o * v >= (1LL << 40)) return GFCC_ERR_ARG;
+  gfcc_ctx* c = new (std::nothrow) gfcc_ctx();
+  if (!c) return GFCC_ERR_OOM;
+  c->o = o; c->v = v; c->n = o + v; c->P = (int)P; c->D = (int)D;
+  c->stream = (cudaStream_t)stream;
+  if (opts) c->opts = *opts; else gfcc_default_opts(&c->opts);
+  std::string why;
+  int rc = check_opts(&c->opts, why);
+  if (rc != GFCC_OK) { delete c; return rc; }
+  int status = GFCC_OK;
+  try {
+    GFCC_CUDA(cudaGetDevice(&c->device));
+    gfcc::HostInputs in{eps, vb->oooo, vb->ooov, vb->oovv, vb->ovov, vb->ovvv, t1, t2, l1, l2};
+    gfcc::build_operator(c, in);
+    if (c->opts.precision != GFCC_PREC_FP64) gfcc::build_low_precision(c, c->opts.precision);
+  } catch (gfcc::Error& e) {
+    status = e.code;
+    fprintf(stderr, "gfcc_init: %s\n", e.msg.c_str());
+  } catch (std::bad_alloc&) {
+    status = GFCC_ERR_OOM;
+  }
+  if (status != GFCC_OK) { delete c; return status; }
+  *out = c;
+  return GFCC_OK;
+}
+
+int gfcc_dim(gfcc_t c, int* D) {
+  if (!c || !D) return GFCC_ERR_ARG;
+  *D = c->D;
+  return GFCC_OK;
+}
+
+int gfcc_set_opts(gfcc_t c, const gfcc_opts* opts) {
+  if (!c || !opts) return GFCC_ERR_ARG;
+  std::string why;
+  int rc = check_opts(opts, why);
+  if (rc != GFCC_OK) { c->last_error = why; return rc; }
+  API_BEGIN
+  c->opts = *opts;
+  if (opts->precision != GFCC_PREC_FP64 && c->lp.kind != opts->precision) gfcc::build_low_precision(c, opts->precision);
+  API_END(c)
+}
+
+int gfcc_sigma(gfcc_t c, const double* X, double* Y, int nvec, int ld, int precision, int transpose) {
+  if (!c) return GFCC_ERR_ARG;
+  if (nvec < 0 || (nvec > 0 && (!X || !Y || ld < c->D)) || precision < 0 || precision > GFCC_PREC_BF16X2) {
+    c->last_error = "gfcc_sigma: bad arguments";
+    return GFCC_ERR_ARG;
+  }
+  API_BEGIN
+  if (nvec == 0) return GFCC_OK;
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  if (precision != GFCC_PREC_FP64 && c->lp.kind != precision) gfcc::build_low_precision(c, precision);
+  const int nbmax = std::max(1, std::min(nvec, c->opts.max_batch > 0 ? c->opts.max_batch : 256));
+  DBuf<cplx> stage, Xb, Yb;
+  stage.alloc((long long)nbmax * ld);
+  Xb.alloc(D * nbmax);
+  Yb.alloc(D * nbmax);
+  const cplx* Xc = reinterpret_cast<const cplx*>(X);
+  cplx* Yc = reinterpret_cast<cplx*>(Y);
+  const bool xdev = is_device_ptr(X), ydev = is_device_ptr(Y);
+  for (int c0 = 0; c0 < nvec; c0 += nbmax) {
+    const int nb = std::min(nbmax, nvec - c0);
+    const cplx* src = Xc + (long long)c0 * ld;
+    if (!xdev) {
+      GFCC_CUDA(cudaMemcpyAsync(stage.p, src, sizeof(cplx) * nb * ld, cudaMemcpyHostToDevice, s));
+      src = stage.p;
+    }
+    gfcc::pack_cols_to_batch(src, ld, nb, (int)D, Xb.p, nb, s);
+    gfcc::sigma_batch(c, Xb.p, Yb.p, nb, nb, nullptr, precision, transpose != 0, s);
+    if (ydev) {
+      gfcc::batch_to_cols(Yb.p, nb, nb, (int)D, Yc + (long long)c0 * ld, ld, s);
+    } else {
+      gfcc::batch_to_cols(Yb.p, nb, nb, (int)D, stage.p, ld, s);
+      GFCC_CUDA(cudaMemcpyAsync(Yc + (long long)c0 * ld, stage.p, sizeof(cplx) * nb * ld, cudaMemcpyDeviceToHost, s));
+    }
+    GFCC_CUDA(cudaStreamSynchronize(s));
+  }
+  API_END(c)
+}
+
+int gfcc_vectors(gfcc_t c, const int* orbitals, int norb, int transpose, double* out, int ld) {
+  if (!c) return GFCC_ERR_ARG;
+  if (norb < 0 || (norb > 0 && (!orbitals || !out || ld < c->D))) { c->last_error = "gfcc_vectors: bad arguments"; return GFCC_ERR_ARG; }
+  for (int k = 0; k < norb; ++k)
+    if (orbitals[k] < 0 || orbitals[k] >= c->n) { c->last_error = "gfcc_vectors: orbital out of range"; return GFCC_ERR_ARG; }
+  API_BEGIN
+  const double* src = transpose ? c->cvec.p : c->bvec.p;
+  for (int k = 0; k < norb; ++k)
+    copy_out(out + (long long)k * ld, src + (long long)orbitals[k] * c->D, sizeof(double) * c->D, c->stream);
+  GFCC_CUDA(cudaStreamSynchronize(c->stream));
+  API_END(c)
+}
+
+static int check_orbitals(gfcc_t c, const int* orb, int n, const char* what) {
+  if (n <= 0 || !orb) { c->last_error = std::string(what) + ": empty orbital set"; return GFCC_ERR_ARG; }
+  for (int k = 0; k < n; ++k)
+    if (orb[k] < 0 || orb[k] >= c->n) { c->last_error = std::string(what) + ": orbital out of range"; return GFCC_ERR_ARG; }
+  return GFCC_OK;
+}
+
+int gfcc_solve_full(gfcc_t c, const double* omegas, int nw, double eta, const int* orbitals, int np,
+                    const int* qorb, int nq, double* G, double* A, double* X, int ldx, gfcc_stats* stats) {
+  if (!c) return GFCC_ERR_ARG;
+  if (nw < 0 || (nw > 0 && !omegas) || !std::isfinite(eta) || eta < 0.0) { c->last_error = "gfcc_solve_full: bad frequencies or eta"; return GFCC_ERR_ARG; }
+  int rc = check_orbitals(c, orbitals, np, "gfcc_solve_full");
+  if (rc) return rc;
+  if (qorb) { rc = check_orbitals(c, qorb, nq, "gfcc_solve_full(q)"); if (rc) return rc; }
+  if (X && ldx < c->D) { c->last_error = "gfcc_solve_full: ldx < D"; return GFCC_ERR_ARG; }
+  for (int k = 0; k < nw; ++k)
+    if (!std::isfinite(omegas[k])) { c->last_error = "gfcc_solve_full: non-finite frequency"; return GFCC_ERR_NONFINITE; }
+  API_BEGIN
+  if (nw == 0) return GFCC_OK;
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  std::vector<int> porb(orbitals, orbitals + np);
+  std::vector<int> qv = qorb ? std::vector<int>(qorb, qorb + nq) : porb;
+  nq = (int)qv.size();
+  std::vector<double> ws(omegas, omegas + nw);
+  const long long ncols = (long long)nw * np;
+  DBuf<cplx> Gd, Xd;
+  DBuf<double> Ad;
+  DBuf<int> dq;
+  const bool needG = G || A;
+  if (needG) Gd.alloc(ncols * nq);
+  if (X) Xd.alloc(D * ncols);
+  gfcc_stats st{};
+  solve_columns(c, ws, eta, porb, qv, needG ? Gd.p : nullptr, X ? Xd.p : nullptr, nullptr, &st);
+  if (A) {
+    std::vector<int> qi = q_positions(porb, qv);
+    dq.alloc(np);
+    Ad.alloc(nw);
+    GFCC_CUDA(cudaMemcpyAsync(dq.p, qi.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+    spectral_kernel<<<(nw + 127) / 128, 128, 0, s>>>(Gd.p, nw, np, nq, dq.p, Ad.p);
+    GFCC_LAUNCH_CHECK();
+    copy_out(A, Ad.p, sizeof(double) * nw, s);
+  }
+  if (G) copy_out(G, Gd.p, sizeof(cplx) * ncols * nq, s);
+  if (X) {
+    if (is_device_ptr(X)) {
+      gfcc::batch_to_cols(Xd.p, (int)ncols, (int)ncols, (int)D, reinterpret_cast<cplx*>(X), ldx, s);
+    } else {
+      DBuf<cplx> stage;
+      stage.alloc(ncols * ldx);
+      gfcc::batch_to_cols(Xd.p, (int)ncols, (int)ncols, (int)D, stage.p, ldx, s);
+      GFCC_CUDA(cudaMemcpyAsync(X, stage.p, sizeof(cplx) * ncols * ldx, cudaMemcpyDeviceToHost, s));
+      GFCC_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+  GFCC_CUDA(cudaStreamSynchronize(s));
+  if (stats) *stats = st;
+  if (st.not_converged > 0) {
+    c->last_error = "gfcc_solve_full: " + std::to_string(st.not_converged) + " column(s) not converged";
+    return GFCC_ERR_NOT_CONVERGED;
+  }
+  API_END(c)
+}
+
+int gfcc_mor_build(gfcc_t c, const double* seeds, int ns, double eta, const int* orbitals, int np,
+                   const int* qorb, int nq) {
+  if (!c) return GFCC_ERR_ARG;
+  if (ns <= 0 || !seeds || !std::isfinite(eta) || eta <= 0.0) { c->last_error = "gfcc_mor_build: bad seeds or eta"; return GFCC_ERR_ARG; }
+  int rc = check_orbitals(c, orbitals, np, "gfcc_mor_build");
+  if (rc) return rc;
+  if (qorb) { rc = check_orbitals(c, qorb, nq, "gfcc_mor_build(q)"); if (rc) return rc; }
+  for (int k = 0; k < ns; ++k)
+    if (!std::isfinite(seeds[k])) { c->last_error = "gfcc_mor_build: non-finite seed"; return GFCC_ERR_NONFINITE; }
+  API_BEGIN
+  gfcc::MorState& ms = c->mor;
+  ms.reset();
+  ms.eta = eta;
+  ms.porb.assign(orbitals, orbitals + np);
+  ms.qorb = qorb ? std::vector<int>(qorb, qorb + nq) : ms.porb;
+  {  // ||b_p||^2
+    DBuf<int> idx;
+    DBuf<double> out;
+    idx.alloc(np); out.alloc(np);
+    GFCC_CUDA(cudaMemcpyAsync(idx.p, ms.porb.data(), sizeof(int) * np, cudaMemcpyHostToDevice, c->stream));
+    rownorm2_kernel<<<np, 256, 0, c->stream>>>(c->bvec.p, c->D, idx.p, np, out.p);
+    GFCC_LAUNCH_CHECK();
+    ms.bnorm.resize(np);
+    GFCC_CUDA(cudaMemcpyAsync(ms.bnorm.data(), out.p, sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
+    GFCC_CUDA(cudaStreamSynchronize(c->stream));
+    for (double& x : ms.bnorm) x = std::sqrt(x);
+    for (double x : ms.bnorm) GFCC_CHECK(x > 0.0, GFCC_ERR_ARG, "gfcc_mor_build: zero right-hand side");
+  }
+  gfcc::mor_init_basis(c);
+  std::vector<double> ws(seeds, seeds + ns);
+  std::sort(ws.begin(), ws.end());
+  ws.erase(std::unique(ws.begin(), ws.end()), ws.end());
+  mor_add_frequencies(c, ws);
+  GFCC_CHECK(ms.m > 0, GFCC_ERR_RANK, "gfcc_mor_build: every seed solution was dropped");
+  ms.built = true;
+  API_END(c)
+}
+
+int gfcc_mor_refine(gfcc_t c, double wmin, double wmax, int ngrid, double tol, int m_max, int* m_out,
+                    double* max_err) {
+  if (!c) return GFCC_ERR_ARG;
+  if (!c->mor.built) { c->last_error = "gfcc_mor_refine: call gfcc_mor_build first"; return GFCC_ERR_STATE; }
+  if (!(wmax > wmin) || ngrid < 2 || !(tol > 0.0) || m_max < 1 || !std::isfinite(wmin) || !std::isfinite(wmax)) {
+    c->last_error = "gfcc_mor_refine: bad arguments";
+    return GFCC_ERR_ARG;
+  }
+  API_BEGIN
+  gfcc::MorState& ms = c->mor;
+  const int np = (int)ms.porb.size();
+  std::vector<double> grid(ngrid);
+  for (int k = 0; k < ngrid; ++k) grid[k] = wmin + (wmax - wmin) * (double)k / (double)(ngrid - 1);
+  DBuf<double> dres;
+  dres.alloc(ngrid);
+  std::vector<double> res(ngrid);
+  bool converged = false;
+  double emax = 0.0;
+  for (int round = 0; round < 10000; ++round) {
+    gfcc::mor_eval(c, grid.data(), ngrid, nullptr, nullptr, dres.p);
+    GFCC_CUDA(cudaMemcpyAsync(res.data(), dres.p, sizeof(double) * ngrid, cudaMemcpyDeviceToHost, c->stream));
+    GFCC_CUDA(cudaStreamSynchronize(c->stream));
+    const std::vector<double>& smp = ms.sampled;
+    std::vector<double> e(smp.size() > 0 ? smp.size() - 1 : 0, 0.0);
+    for (size_t k = 0; k + 1 < smp.size(); ++k)
+      for (int g = 0; g < ngrid; ++g)
+        if (grid[g] > smp[k] && grid[g] < smp[k + 1]) e[k] = std::max(e[k], res[g]);
+    emax = 0.0;
+    for (double x : e) emax = std::max(emax, x);
+    ms.history.push_back({ms.m, emax});
+    ms.last_max_err = emax;
+    if (emax <= tol) { converged = true; break; }
+    int max_new = (m_max - ms.m) / np;
+    std::vector<std::pair<double, double>> cand;   // (-error, midpoint)
+    for (size_t k = 0; k < e.size(); ++k)
+      if (e[k] > tol) cand.push_back({-e[k], 0.5 * (smp[k] + smp[k + 1])});
+    std::sort(cand.begin(), cand.end());
+    std::vector<double> nw;
+    for (int k = 0; k < (int)cand.size() && k < max_new; ++k) nw.push_back(cand[k].second);
+    if (nw.empty()) break;
+    std::sort(nw.begin(), nw.end());
+    mor_add_frequencies(c, nw);
+  }
+  if (m_out) *m_out = ms.m;
+  if (max_err) *max_err = emax;
+  if (!converged) {
+    c->last_error = "gfcc_mor_refine: model order bound reached before the tolerance";
+    return GFCC_ERR_NOT_CONVERGED;
+  }
+  API_END(c)
+}
+
+int gfcc_mor_eval(gfcc_t c, const double* omegas, int nw, double* G, double* A, double* maxres) {
+  if (!c) return GFCC_ERR_ARG;
+  if (!c->mor.built) { c->last_error = "gfcc_mor_eval: no reduced model"; return GFCC_ERR_STATE; }
+  if (nw < 0 || (nw > 0 && !omegas)) { c->last_error = "gfcc_mor_eval: bad frequencies"; return GFCC_ERR_ARG; }
+  for (int k = 0; k < nw; ++k)
+    if (!std::isfinite(omegas[k])) { c->last_error = "gfcc_mor_eval: non-finite frequency"; return GFCC_ERR_NONFINITE; }
+  API_BEGIN
+  if (nw == 0) return GFCC_OK;
+  gfcc::MorState& ms = c->mor;
+  cudaStream_t s = c->stream;
+  const int np = (int)ms.porb.size(), nq = (int)ms.qorb.size();
+  DBuf<cplx> Gd;
+  DBuf<double> Ad, Rd;
+  if (G) Gd.alloc((long long)nw * np * nq);
+  if (A) Ad.alloc(nw);
+  if (maxres) Rd.alloc(nw);
+  gfcc::mor_eval(c, omegas, nw, G ? Gd.p : nullptr, A ? Ad.p : nullptr, maxres ? Rd.p : nullptr);
+  if (G) copy_out(G, Gd.p, sizeof(cplx) * nw * np * nq, s);
+  if (A) copy_out(A, Ad.p, sizeof(double) * nw, s);
+  if (maxres) copy_out(maxres, Rd.p, sizeof(double) * nw, s);
+  GFCC_CUDA(cudaStreamSynchronize(s));
+  API_END(c)
+}
+
+int gfcc_mor_info(gfcc_t c, double* w, int cap, int* ns, int* m, int* np, int* nq) {
+  if (!c) return GFCC_ERR_ARG;
+  const gfcc::MorState& ms = c->mor;
+  if (ns) *ns = (int)ms.sampled.size();
+  if (m) *m = ms.m;
+  if (np) *np = (int)ms.porb.size();
+  if (nq) *nq = (int)ms.qorb.size();
+  if (w)
+    for (int k = 0; k < cap && k < (int)ms.sampled.size(); ++k) w[k] = ms.sampled[k];
+  return GFCC_OK;
+}
+
+int gfcc_mor_save(gfcc_t c, const char* path) {
+  if (!c || !path) return GFCC_ERR_ARG;
+  if (!c->mor.built) { c->last_error = "gfcc_mor_save: no reduced model"; return GFCC_ERR_STATE; }
+  API_BEGIN
+  const gfcc::MorState& ms = c->mor;
+  const long long D = c->D;
+  const int m = ms.m, cap = ms.m_cap, np = (int)ms.porb.size(), nq = (int)ms.qorb.size();
+  const int qn = ms.qn, qcap = ms.q_cap;
+  std::ofstream f(path, std::ios::binary);
+  GFCC_CHECK(f.good(), GFCC_ERR_ARG, std::string("gfcc_mor_save: cannot open ") + path);
+  const char magic[8] = {'G', 'F', 'C', 'C', 'M', 'O', 'R', '2'};
+  f.write(magic, 8);
+  int hdr[7] = {c->o, c->v, (int)D, m, np, nq, qn};
+  f.write(reinterpret_cast<const char*>(hdr), sizeof(hdr));
+  f.write(reinterpret_cast<const char*>(&ms.eta), sizeof(double));
+  int ns = (int)ms.sampled.size();
+  f.write(reinterpret_cast<const char*>(&ns), sizeof(int));
+  f.write(reinterpret_cast<const char*>(ms.sampled.data()), sizeof(double) * ns);
+  f.write(reinterpret_cast<const char*>(ms.porb.data()), sizeof(int) * np);
+  f.write(reinterpret_cast<const char*>(ms.qorb.data()), sizeof(int) * nq);
+  f.write(reinterpret_cast<const char*>(ms.bnorm.data()), sizeof(double) * np);
+  std::vector<cplx> h;
+  auto dump2d = [&](const cplx* dev, long long rows, int width, int ld) {   // rows x width out of ld
+    h.resize((size_t)rows * width);
+    GFCC_CUDA(cudaMemcpy2D(h.data(), sizeof(cplx) * width, dev, sizeof(cplx) * ld, sizeof(cplx) * width, rows,
+                           cudaMemcpyDeviceToHost));
+    f.write(reinterpret_cast<const char*>(h.data()), sizeof(cplx) * h.size());
+  };
+  dump2d(ms.S.p, D, m, cap);
+  dump2d(ms.Z.p, D, m, cap);
+  dump2d(ms.Hh.p, m, m, cap);      // col-major: m columns of m entries
+  dump2d(ms.bh.p, np, m, cap);
+  dump2d(ms.ch.p, m, nq, nq);
+  dump2d(ms.Q.p, D, qn, qcap);
+  dump2d(ms.RS.p, m, qn, qcap);
+  dump2d(ms.RZ.p, m, qn, qcap);
+  dump2d(ms.RB.p, np, qn, qcap);
+  GFCC_CHECK(f.good(), GFCC_ERR_ARG, "gfcc_mor_save: write failed");
+  API_END(c)
+}
+
+int gfcc_mor_load(gfcc_t c, const char* path) {
+  if (!c || !path) return GFCC_ERR_ARG;
+  API_BEGIN
+  std::ifstream f(path, std::ios::binary);
+  GFCC_CHECK(f.good(), GFCC_ERR_ARG, std::string("gfcc_mor_load: cannot open ") + path);
+  char magic[8];
+  f.read(magic, 8);
+  GFCC_CHECK(f.good() && std::memcmp(magic, "GFCCMOR2", 8) == 0, GFCC_ERR_ARG, "gfcc_mor_load: not a model file");
+  int hdr[7];
+  f.read(reinterpret_cast<char*>(hdr), sizeof(hdr));
+  GFCC_CHECK(f.good() && hdr[0] == c->o && hdr[1] == c->v && hdr[2] == c->D, GFCC_ERR_ARG,
+             "gfcc_mor_load: size mismatch");
+  const int m = hdr[3], np = hdr[4], nq = hdr[5], qn = hdr[6];
+  GFCC_CHECK(m > 0 && np > 0 && nq > 0 && qn >= m && np <= c->n && nq <= c->n && m <= c->D, GFCC_ERR_ARG,
+             "gfcc_mor_load: corrupt header");
+  gfcc::MorState& ms = c->mor;
+  ms.reset();
+  f.read(reinterpret_cast<char*>(&ms.eta), sizeof(double));
+  int ns = 0;
+  f.read(reinterpret_cast<char*>(&ns), sizeof(int));
+  GFCC_CHECK(f.good() && ns > 0 && ns < (1 << 24), GFCC_ERR_ARG, "gfcc_mor_load: corrupt header");
+  ms.sampled.resize(ns);
+  ms.porb.resize(np);
+  ms.qorb.resize(nq);
+  ms.bnorm.resize(np);
+  f.read(reinterpret_cast<char*>(ms.sampled.data()), sizeof(double) * ns);
+  f.read(reinterpret_cast<char*>(ms.porb.data()), sizeof(int) * np);
+  f.read(reinterpret_cast<char*>(ms.qorb.data()), sizeof(int) * nq);
+  f.read(reinterpret_cast<char*>(ms.bnorm.data()), sizeof(double) * np);
+  GFCC_CHECK(f.good(), GFCC_ERR_ARG, "gfcc_mor_load: truncated file");
+  const long long D = c->D;
+  const int cap = std::max(m, 64), qcap = std::max(qn, 128);
+  ms.m_cap = cap;
+  ms.q_cap = qcap;
+  ms.S.alloc(D * cap); ms.Z.alloc(D * cap);
+  ms.Hh.alloc((long long)cap * cap);
+  ms.bh.alloc((long long)cap * np);
+  ms.ch.alloc((long long)nq * cap);
+  ms.Q.alloc(D * qcap);
+  ms.RS.alloc((long long)qcap * cap); ms.RZ.alloc((long long)qcap * cap);
+  ms.RB.alloc((long long)qcap * np);
+  for (DBuf<cplx>* b : {&ms.S, &ms.Z, &ms.Hh, &ms.bh, &ms.ch, &ms.Q, &ms.RS, &ms.RZ, &ms.RB}) b->zero(c->stream);
+  GFCC_CUDA(cudaStreamSynchronize(c->stream));
+  std::vector<cplx> h;
+  auto load2d = [&](cplx* dev, long long rows, int width, int ld) {
+    h.resize((size_t)rows * width);
+    f.read(reinterpret_cast<char*>(h.data()), sizeof(cplx) * h.size());
+    GFCC_CHECK(f.good(), GFCC_ERR_ARG, "gfcc_mor_load: truncated file");
+    GFCC_CUDA(cudaMemcpy2D(dev, sizeof(cplx) * ld, h.data(), sizeof(cplx) * width, sizeof(cplx) * width, rows,
+                           cudaMemcpyHostToDevice));
+  };
+  load2d(ms.S.p, D, m, cap);
+  load2d(ms.Z.p, D, m, cap);
+  load2d(ms.Hh.p, m, m, cap);
+  load2d(ms.bh.p, np, m, cap);
+  load2d(ms.ch.p, m, nq, nq);
+  load2d(ms.Q.p, D, qn, qcap);
+  load2d(ms.RS.p, m, qn, qcap);
+  load2d(ms.RZ.p, m, qn, qcap);
+  load2d(ms.RB.p, np, qn, qcap);
+  ms.m = m;
+  ms.qn = qn;
+  ms.built = true;
+  API_END(c)
+}
+
+const char* gfcc_last_error(gfcc_t c) { return c ? c->last_error.c_str() : "null context"; }
+
+void gfcc_free(gfcc_t c) { delete c; }
+
+}  // extern "C"

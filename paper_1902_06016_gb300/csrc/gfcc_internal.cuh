@@ -1,0 +1,245 @@
+// Internal declarations shared by the translation units of libgfcc (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuComplex.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/gfcc.h"
+
+namespace gfcc {
+
+// ---------------------------------------------------------------------------------------------
+// error handling: every internal failure becomes a status code plus a message on the context
+// ---------------------------------------------------------------------------------------------
+struct Error {
+  int code;
+  std::string msg;
+};
+
+#define GFCC_CUDA(call)                                                                    \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      throw ::gfcc::Error{GFCC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+#define GFCC_CHECK(cond, code, msg)                                                        \
+  do {                                                                                     \
+    if (!(cond)) throw ::gfcc::Error{(code), (msg)};                                       \
+  } while (0)
+
+#define GFCC_LAUNCH_CHECK() GFCC_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------------------------------------
+// device buffers owned by the context
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    if (count <= n && p) return;
+    release();
+    if (count == 0) return;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      throw Error{GFCC_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed"};
+    }
+    n = count;
+  }
+  void zero(cudaStream_t s) {
+    if (p && n) GFCC_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+  }
+};
+
+using cplx = cuDoubleComplex;
+
+// ---------------------------------------------------------------------------------------------
+// The similarity-transformed Hamiltonian on the 1h+2h1p space, laid out for the sigma GEMMs.
+// Index conventions: o occupied, v virtual, P = o(o-1)/2 pairs i<j, pair(i,j) = j(j-1)/2 + i,
+// packed vector index: 1h i -> i, 2h1p (i<j,a) -> o + pair(i,j)*v + a.
+// ---------------------------------------------------------------------------------------------
+struct Operator {
+  DBuf<double> Wr;     // [(a,i)][(m,e)]  ov x ov : W_maei - d_ae F_mi(off) + 1/2 d_mi F_ae(off)
+  DBuf<double> Woo;    // [pair(ij)][pair(mn)]  P x P : W_mnij
+  DBuf<double> A11;    // [i][m]  o x o : -F_mi (off-diagonal)
+  DBuf<double> A12;    // [i][(pair(mn),e)]  o x Pv : 1h <- 2h1p block
+  DBuf<double> A21;    // [(pair(ij),a)][m]  Pv x o : 2h1p <- 1h block (-W_maij)
+  DBuf<double> Vt;     // [e][(pair(mn),f)]  v x Pv : <mn||ef>   (three-body, first half)
+  DBuf<double> T2p;    // [(pair(ij),a)][e]  Pv x v : t_ij^ae     (three-body, second half)
+  DBuf<double> diag;   // [D] Fock-diagonal part: -F_ii (1h), F_aa - F_ii - F_jj (2h1p)
+  DBuf<double> mdiag;  // [D] full diagonal of M (Jacobi preconditioner)
+  // transposed-action copies are built lazily (adjoint systems)
+  bool have_T = false;
+  DBuf<double> WrT, WooT, A12T, A21T, VtT, T2pT;
+};
+
+// low-precision copies of the dominant operator (mixed-precision path)
+struct LowPrecision {
+  int kind = 0;          // GFCC_PREC_*
+  int K_pad = 0;         // padded K (elements) of the ring operand
+  DBuf<uint16_t> Wr_bf16;   // [(a,i)][K_pad]
+  DBuf<float> Wr_f32;       // [(a,i)][K_pad] (tf32 operand)
+  DBuf<uint16_t> Wr_lo_bf16;  // second bf16 term for split precision
+  DBuf<uint16_t> Woo_bf16;
+  DBuf<float> Woo_f32;
+};
+
+struct Workspace {
+  DBuf<double> ut;      // unpacked 2h1p  [(m,e)][(j,c)] complex -> 2*ov*o*nb doubles
+  DBuf<double> ct;      // ring product   [(a,i)][(j,c)] complex
+  DBuf<double> xe;      // three-body X_e [e][c] complex
+  DBuf<uint16_t> ut16;  // low-precision ring operand
+  DBuf<float> ct32;     // low-precision ring product
+  DBuf<float> ut32;
+  size_t nb_cap = 0;
+};
+
+struct MorState {
+  bool built = false;
+  double eta = 0.0;
+  std::vector<int> porb, qorb;     // orbital sets
+  std::vector<double> sampled;     // sampled frequencies (sorted)
+  int m = 0, m_cap = 0;            // model order and capacity
+  DBuf<cplx> S, Z;                 // [D][m_cap] batch-minor: column i of S at S[nu*m_cap + i]; Z = M S
+  DBuf<cplx> Hh;                   // [m_cap x m_cap] col-major  Hhat = S^H Z
+  DBuf<cplx> bh;                   // [m_cap x np]    col-major  S^H B
+  DBuf<cplx> ch;                   // [nq x m_cap]    col-major  C S  (ld nq)
+  // orthonormal basis Q of span[B, S, Z] and the coefficients of B, S, Z in it, for residual norms
+  // ||(w - i eta) S y + Z y - b_p|| = ||(w - i eta) RS y + RZ y - RB e_p|| without cancellation
+  int qn = 0, q_cap = 0;
+  DBuf<cplx> Q;                    // [D][q_cap] batch-minor
+  DBuf<cplx> RS, RZ;               // [q_cap x m_cap] col-major (ld q_cap)
+  DBuf<cplx> RB;                   // [q_cap x np]    col-major (ld q_cap)
+  std::vector<double> bnorm;       // ||b_p||
+  std::vector<std::pair<int, double>> history;
+  double last_max_err = -1.0;
+  void reset() {
+    built = false;
+    eta = 0.0;
+    porb.clear(); qorb.clear(); sampled.clear(); bnorm.clear(); history.clear();
+    m = 0; m_cap = 0; qn = 0; q_cap = 0;
+    for (DBuf<cplx>* b : {&S, &Z, &Hh, &bh, &ch, &Q, &RS, &RZ, &RB}) b->release();
+    last_max_err = -1.0;
+  }
+};
+
+struct Stats {
+  long long sigma_calls = 0, sigma_cols = 0, gmres_iters = 0, restarts = 0;
+  double max_rel_res = 0.0;
+  int not_converged = 0;
+};
+
+}  // namespace gfcc
+
+struct gfcc_ctx {
+  int o = 0, v = 0, n = 0, P = 0, D = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  gfcc_opts opts{};
+  std::string last_error;
+  gfcc::Operator op;
+  gfcc::LowPrecision lp;
+  gfcc::Workspace ws;
+  gfcc::MorState mor;
+  gfcc::Stats stats;
+  gfcc::DBuf<double> bvec;   // [n][D]  b_p rows
+  gfcc::DBuf<double> cvec;   // [n][D]  c_q rows
+  gfcc::DBuf<double> t1, t2; // kept for derivative work
+};
+
+namespace gfcc {
+
+// ---- gemm.cu -----------------------------------------------------------------------------------
+// C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n), with element strides and batch strides
+// (blockIdx.z). Real FP64 SIMT kernel; complex data whose re/im pairs lie along N is handled by
+// passing N' = 2N with unit n-stride.
+struct GemmDesc {
+  int M = 0, N = 0, K = 0, batch = 1;
+  const double* A = nullptr; long long sam = 0, sak = 0, bsa = 0;
+  const double* B = nullptr; long long sbk = 0, sbn = 0, bsb = 0;
+  double* C = nullptr; long long scm = 0, scn = 0, bsc = 0;
+  double alpha = 1.0, beta = 0.0;
+};
+void dgemm(const GemmDesc& g, cudaStream_t s);
+
+// complex FP64 GEMM, op(A) may be conjugated; strides in complex elements
+struct ZGemmDesc {
+  int M = 0, N = 0, K = 0, batch = 1;
+  const cplx* A = nullptr; long long sam = 0, sak = 0, bsa = 0; bool conjA = false;
+  const cplx* B = nullptr; long long sbk = 0, sbn = 0, bsb = 0; bool conjB = false;
+  cplx* C = nullptr; long long scm = 0, scn = 0, bsc = 0;
+  cplx alpha = {1.0, 0.0}, beta = {0.0, 0.0};
+};
+void zgemm(const ZGemmDesc& g, cudaStream_t s);
+
+// row-major contiguous helpers
+void dgemm_rm(int M, int N, int K, double alpha, const double* A, int lda, bool transA,
+              const double* B, int ldb, bool transB, double beta, double* C, int ldc, cudaStream_t s);
+
+// ---- tensor.cu ---------------------------------------------------------------------------------
+// dst = alpha * permute(src) + beta * dst for up to 6-D tensors (row-major);
+// dst index order is src axes perm[0], perm[1], ...
+void permute(const double* src, const int* dims, int nd, const int* perm, double* dst,
+             double alpha, double beta, cudaStream_t s);
+void axpby(long long n, double alpha, const double* x, double beta, double* y, cudaStream_t s);
+
+// ---- hbar.cu -----------------------------------------------------------------------------------
+struct HostInputs {
+  const double *eps, *oooo, *ooov, *oovv, *ovov, *ovvv, *t1, *t2, *l1, *l2;
+};
+void build_operator(gfcc_ctx* c, const HostInputs& in);
+
+// ---- sigma.cu ----------------------------------------------------------------------------------
+// Y = M X (+ shift*X per column) on a batch in batch-minor layout X[nu][c] (complex), c < nb,
+// leading dimension ldb (complex elements per row). shift may be null.
+void sigma_batch(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, int ldb, const cplx* shift,
+                 int precision, bool transpose, cudaStream_t s);
+void ensure_workspace(gfcc_ctx* c, int nb);
+void build_transpose_operator(gfcc_ctx* c);
+
+// ---- sigma_tc.cu (tcgen05 mixed-precision ring GEMM) -------------------------------------------
+void build_low_precision(gfcc_ctx* c, int kind);
+void ring_lowprec(gfcc_ctx* c, const double* ut_cplx, double* ct_cplx, int nb, cudaStream_t s);
+
+// ---- krylov.cu ---------------------------------------------------------------------------------
+struct SolveStatus {
+  std::vector<double> relres;   // per column
+  std::vector<int> iters;       // per column
+  std::vector<int> converged;   // per column
+};
+// Solve (shift_c + M) x_c = b_c for nb columns (batch-minor layout, ld = nb).
+void gmres_batched(gfcc_ctx* c, const cplx* B, cplx* X, cplx* R, const cplx* shifts, int nb,
+                   SolveStatus& st, bool transpose);
+
+// ---- kernels shared between units ------------------------------------------------------------
+void gather_rows_real_to_cplx(const double* src, int ld_src, const int* rows, int nrows, int D,
+                              cplx* dst, int ldb, cudaStream_t s);   // dst[nu][k] = src[rows[k]][nu]
+void pack_cols_to_batch(const cplx* src, int ld_src, int ncols, int D, cplx* dst, int ldb,
+                        cudaStream_t s);   // dst[nu][c] = src[c][nu]
+void batch_to_cols(const cplx* src, int ldb, int ncols, int D, cplx* dst, int ld_dst,
+                   cudaStream_t s);        // dst[c][nu] = src[nu][c]
+void green_from_batch(const double* cvec, int D, const int* qrows, int nq, const cplx* X, int ldb,
+                      int ncols, cplx* G, cudaStream_t s);   // G[c][q] = sum_nu c_q[nu] X[nu][c]
+
+// mor.cu
+void mor_init_basis(gfcc_ctx* c);   // Q <- orth(B), after porb/qorb/eta are set
+void mor_append(gfcc_ctx* c, const cplx* X, const cplx* MX, int ncols);
+void mor_eval(gfcc_ctx* c, const double* omegas, int nw, cplx* G_dev, double* A_dev,
+              double* maxres_dev);
+
+}  // namespace gfcc

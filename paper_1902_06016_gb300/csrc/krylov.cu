@@ -1,0 +1,562 @@
+// Batched restarted GMRES with iterative refinement for the shifted systems of Eq. xplin,
+// (w_c - i eta + M) x_c = b_c, one column per (p, w) pair, all columns in lock step.
+//
+// Each restart cycle is one refinement step: the residual r = b - (shift x + M x) is formed with
+// the FP64 sigma, then GMRES(k) on the correction runs with the sigma in the requested
+// precision (classical Gram-Schmidt with one re-orthogonalisation, FP64 basis, Givens least
+// squares), and x += P V y with the Jacobi right preconditioner P = (shift + diag M)^{-1}.
+// Columns whose FP64 residual meets the tolerance are written out and compacted away between
+// cycles. The paper used a complex DIIS solver (convergence study after Table 1); any convergent
+// solver reaches the same solution of Eq. xplin.
+#include "gfcc_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace gfcc {
+namespace {
+
+int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  return (int)std::min<long long>(std::max<long long>(g, 1), 152LL * 32);
+}
+
+__device__ __forceinline__ cplx cmul(cplx a, cplx b) { return cuCmul(a, b); }
+__device__ __forceinline__ cplx cconjmul(cplx a, cplx b) {  // conj(a) * b
+  return make_cuDoubleComplex(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+// partial[chunk][i][c] = sum_{nu in chunk} conj(V_i[nu][c]) W[nu][c], i < nv (V_i = V + i*stride)
+constexpr int MD_TX = 32, MD_TY = 8, MD_MAXV = 32;
+__global__ void multidot_kernel(const cplx* __restrict__ V, long long vstride, int nv,
+                                const cplx* __restrict__ W, long long D, int nb, long long rows_per_chunk,
+                                cplx* __restrict__ partial) {
+  __shared__ cplx red[MD_TY][MD_TX];
+  const int c = blockIdx.x * MD_TX + threadIdx.x;
+  const long long r0 = blockIdx.y * rows_per_chunk;
+  const long long r1 = min(D, r0 + rows_per_chunk);
+  cplx acc[MD_MAXV];
+#pragma unroll
+  for (int i = 0; i < MD_MAXV; ++i) acc[i] = make_cuDoubleComplex(0.0, 0.0);
+  if (c < nb) {
+    for (long long nu = r0 + threadIdx.y; nu < r1; nu += MD_TY) {
+      cplx w = W[nu * nb + c];
+#pragma unroll
+      for (int i = 0; i < MD_MAXV; ++i) {
+        if (i < nv) {
+          cplx vv = V[i * vstride + nu * nb + c];
+          acc[i].x += vv.x * w.x + vv.y * w.y;
+          acc[i].y += vv.x * w.y - vv.y * w.x;
+        }
+      }
+    }
+  }
+  for (int i = 0; i < nv; ++i) {
+    red[threadIdx.y][threadIdx.x] = acc[i];
+    __syncthreads();
+    if (threadIdx.y == 0 && c < nb) {
+      cplx s = red[0][threadIdx.x];
+      for (int k = 1; k < MD_TY; ++k) { s.x += red[k][threadIdx.x].x; s.y += red[k][threadIdx.x].y; }
+      partial[((long long)blockIdx.y * nv + i) * nb + c] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// h[c*hld + hoff + i] (+)= sum_chunk partial[chunk][i][c]
+__global__ void reduce_partial_kernel(const cplx* __restrict__ partial, int nchunk, int nv, int nb,
+                                      cplx* __restrict__ h, int hld, int hoff, int accumulate) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nv * nb) return;
+  int i = t / nb, c = t % nb;
+  cplx s = make_cuDoubleComplex(0.0, 0.0);
+  for (int k = 0; k < nchunk; ++k) {
+    cplx p = partial[((long long)k * nv + i) * nb + c];
+    s.x += p.x; s.y += p.y;
+  }
+  cplx* dst = h + (long long)c * hld + hoff + i;
+  if (accumulate) { dst->x += s.x; dst->y += s.y; } else { *dst = s; }
+}
+
+// W[nu][c] -= sum_{i<nv} V_i[nu][c] h[c*hld + hoff + i]   (or +=, sign)
+__global__ void update_kernel(const cplx* __restrict__ V, long long vstride, int nv, cplx* __restrict__ W,
+                              long long D, int nb, const cplx* __restrict__ h, int hld, int hoff, double sign) {
+  long long total = D * nb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int c = (int)(t % nb);
+    cplx s = make_cuDoubleComplex(0.0, 0.0);
+    const cplx* hc = h + (long long)c * hld + hoff;
+    for (int i = 0; i < nv; ++i) {
+      cplx vv = V[i * vstride + t];
+      cplx hh = hc[i];
+      s.x += vv.x * hh.x - vv.y * hh.y;
+      s.y += vv.x * hh.y + vv.y * hh.x;
+    }
+    W[t].x += sign * s.x;
+    W[t].y += sign * s.y;
+  }
+}
+
+// H[c*hld + i] (+)= hb[c*hbld + i], i < n
+__global__ void add_h_kernel(const cplx* __restrict__ hb, int hbld, cplx* __restrict__ H, int hld, int n, int nb,
+                             int accumulate) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nb) return;
+  int c = t / n, i = t % n;
+  cplx v = hb[(long long)c * hbld + i];
+  cplx* d = H + (long long)c * hld + i;
+  if (accumulate) { d->x += v.x; d->y += v.y; } else { *d = v; }
+}
+
+// column 2-norms: partial over chunks then reduce (reuses multidot with V = W)
+__global__ void finalize_norm_kernel(const cplx* __restrict__ dots, int nb, double* __restrict__ out) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nb) out[c] = sqrt(fmax(dots[c].x, 0.0));
+}
+
+// Z[nu][c] = V[nu][c] / (shift_c + mdiag[nu])
+__global__ void precond_kernel(const cplx* __restrict__ V, cplx* __restrict__ Z, const double* __restrict__ md,
+                               const cplx* __restrict__ shift, long long D, int nb) {
+  long long total = D * nb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int c = (int)(t % nb);
+    long long nu = t / nb;
+    cplx d = make_cuDoubleComplex(shift[c].x + md[nu], shift[c].y);
+    Z[t] = cuCdiv(V[t], d);
+  }
+}
+
+// V[nu][c] = W[nu][c] * scale[c]  (scale = 1/norm, 0 for broken-down columns)
+__global__ void scale_cols_kernel(const cplx* __restrict__ W, cplx* __restrict__ V, const double* __restrict__ nrm,
+                                  long long D, int nb) {
+  long long total = D * nb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int c = (int)(t % nb);
+    double n = nrm[c];
+    double s = (n > 0.0 && isfinite(n)) ? 1.0 / n : 0.0;
+    V[t] = make_cuDoubleComplex(W[t].x * s, W[t].y * s);
+  }
+}
+
+// R = B - Y
+__global__ void residual_kernel(const cplx* __restrict__ B, const cplx* __restrict__ Y, cplx* __restrict__ R,
+                                long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    R[t] = make_cuDoubleComplex(B[t].x - Y[t].x, B[t].y - Y[t].y);
+}
+
+// Per-column Givens step j on H[c] (column-major (k+1) x k), cs/sn/g; writes the residual
+// estimate |g_{j+1}| / bnorm and counts columns still above tol*0.5 that are active in this cycle.
+__global__ void givens_kernel(cplx* __restrict__ H, cplx* __restrict__ cs, cplx* __restrict__ sn,
+                              cplx* __restrict__ g, const double* __restrict__ hnext,
+                              const double* __restrict__ bnorm, int* __restrict__ kc, int* __restrict__ live,
+                              int nb, int k, int j, double tol, int* __restrict__ n_live) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nb) return;
+  if (!live[c]) return;
+  cplx* Hc = H + (long long)c * (k + 1) * k;
+  cplx* col = Hc + (long long)j * (k + 1);
+  col[j + 1] = make_cuDoubleComplex(hnext[c], 0.0);
+  cplx* csc = cs + (long long)c * k;
+  cplx* snc = sn + (long long)c * k;
+  cplx* gc = g + (long long)c * (k + 1);
+  for (int i = 0; i < j; ++i) {
+    cplx a = col[i], b = col[i + 1];
+    cplx t = cuCadd(cuCmul(csc[i], a), cuCmul(snc[i], b));
+    cplx u = cuCadd(cuCmul(make_cuDoubleComplex(-snc[i].x, snc[i].y), a), cuCmul(cuConj(csc[i]), b));
+    col[i] = t;
+    col[i + 1] = u;
+  }
+  cplx a = col[j], b = col[j + 1];
+  double den = sqrt(a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y);
+  cplx cj, sj;
+  if (den > 0.0) {
+    cj = make_cuDoubleComplex(a.x / den, -a.y / den);
+    sj = make_cuDoubleComplex(b.x / den, -b.y / den);
+  } else {
+    cj = make_cuDoubleComplex(1.0, 0.0);
+    sj = make_cuDoubleComplex(0.0, 0.0);
+  }
+  csc[j] = cj;
+  snc[j] = sj;
+  col[j] = make_cuDoubleComplex(den, 0.0);
+  col[j + 1] = make_cuDoubleComplex(0.0, 0.0);
+  cplx gj = gc[j];
+  gc[j + 1] = cuCmul(make_cuDoubleComplex(-sj.x, sj.y), gj);
+  gc[j] = cuCmul(cj, gj);
+  kc[c] = j + 1;
+  double est = cuCabs(gc[j + 1]) / bnorm[c];
+  if (!(est > 0.5 * tol) || den == 0.0 || !isfinite(est)) {
+    live[c] = 0;   // converged (or broken down) within this cycle: stop extending its basis use
+  } else {
+    atomicAdd(n_live, 1);
+  }
+}
+
+// y = H[:kc,:kc]^{-1} g (upper triangular), stored in g
+__global__ void backsolve_kernel(const cplx* __restrict__ H, cplx* __restrict__ g, const int* __restrict__ kc,
+                                 int nb, int k) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nb) return;
+  const cplx* Hc = H + (long long)c * (k + 1) * k;
+  cplx* gc = g + (long long)c * (k + 1);
+  int n = kc[c];
+  for (int i = n - 1; i >= 0; --i) {
+    cplx s = gc[i];
+    for (int jj = i + 1; jj < n; ++jj) s = cuCsub(s, cuCmul(Hc[(long long)jj * (k + 1) + i], gc[jj]));
+    cplx d = Hc[(long long)i * (k + 1) + i];
+    gc[i] = (d.x == 0.0 && d.y == 0.0) ? make_cuDoubleComplex(0.0, 0.0) : cuCdiv(s, d);
+  }
+  for (int i = n; i <= k; ++i) gc[i] = make_cuDoubleComplex(0.0, 0.0);
+}
+
+// X[nu][c] += P_c[nu] * sum_i V_i[nu][c] y_i[c]
+__global__ void correct_kernel(const cplx* __restrict__ V, long long vstride, int nv, const cplx* __restrict__ y,
+                               int yld, cplx* __restrict__ X, const double* __restrict__ md,
+                               const cplx* __restrict__ shift, long long D, int nb) {
+  long long total = D * nb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int c = (int)(t % nb);
+    long long nu = t / nb;
+    cplx s = make_cuDoubleComplex(0.0, 0.0);
+    const cplx* yc = y + (long long)c * yld;
+    for (int i = 0; i < nv; ++i) {
+      cplx yi = yc[i];
+      if (yi.x != 0.0 || yi.y != 0.0) s = cuCadd(s, cuCmul(V[i * vstride + t], yi));
+    }
+    cplx d = make_cuDoubleComplex(shift[c].x + md[nu], shift[c].y);
+    cplx z = cuCdiv(s, d);
+    X[t].x += z.x;
+    X[t].y += z.y;
+  }
+}
+
+// dst[nu][k] = src[nu][cols[k]]  (column gather between batch-minor blocks)
+__global__ void gather_cols_kernel(const cplx* __restrict__ src, int lds, const int* __restrict__ cols, int nk,
+                                   cplx* __restrict__ dst, int ldd, long long D) {
+  long long total = D * nk;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int k = (int)(t % nk);
+    long long nu = t / nk;
+    dst[nu * ldd + k] = src[nu * lds + cols[k]];
+  }
+}
+// dst[nu][cols[k]] = src[nu][k]
+__global__ void scatter_cols_kernel(const cplx* __restrict__ src, int lds, const int* __restrict__ cols, int nk,
+                                    cplx* __restrict__ dst, int ldd, long long D) {
+  long long total = D * nk;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int k = (int)(t % nk);
+    long long nu = t / nk;
+    dst[nu * ldd + cols[k]] = src[nu * lds + k];
+  }
+}
+
+__global__ void nonfinite_cplx_kernel(const cplx* x, long long n, int* flag) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(x[t].x) || !isfinite(x[t].y)) *flag = 1;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// column norms of a batch-minor block: out[c] = ||W_c||  (device array)
+static void col_norms(const cplx* W, long long D, int nb, double* out, DBuf<cplx>& partial,
+                      DBuf<cplx>& tmp, cudaStream_t s) {
+  const long long rows = std::max<long long>(256, (D + 511) / 512);
+  const int nchunk = (int)((D + rows - 1) / rows);
+  partial.alloc((long long)nchunk * nb);
+  tmp.alloc(nb);
+  dim3 grid((nb + MD_TX - 1) / MD_TX, nchunk);
+  multidot_kernel<<<grid, dim3(MD_TX, MD_TY), 0, s>>>(W, 0, 1, W, D, nb, rows, partial.p);
+  GFCC_LAUNCH_CHECK();
+  reduce_partial_kernel<<<(nb + 255) / 256, 256, 0, s>>>(partial.p, nchunk, 1, nb, tmp.p, 1, 0, 0);
+  GFCC_LAUNCH_CHECK();
+  finalize_norm_kernel<<<(nb + 255) / 256, 256, 0, s>>>(tmp.p, nb, out);
+  GFCC_LAUNCH_CHECK();
+}
+
+// h[c][hoff + i] (+)= V_i^H W_c for i < nv, with chunked partial sums
+static void multidot(const cplx* V, long long vstride, int nv, const cplx* W, long long D, int nb,
+                     cplx* h, int hld, int hoff, bool accumulate, DBuf<cplx>& partial, cudaStream_t s) {
+  for (int i0 = 0; i0 < nv; i0 += MD_MAXV) {
+    int n = std::min(MD_MAXV, nv - i0);
+    const long long rows = std::max<long long>(256, (D + 255) / 256);
+    const int nchunk = (int)((D + rows - 1) / rows);
+    partial.alloc((long long)nchunk * n * nb);
+    dim3 grid((nb + MD_TX - 1) / MD_TX, nchunk);
+    multidot_kernel<<<grid, dim3(MD_TX, MD_TY), 0, s>>>(V + i0 * vstride, vstride, n, W, D, nb, rows,
+                                                       partial.p);
+    GFCC_LAUNCH_CHECK();
+    reduce_partial_kernel<<<(n * nb + 255) / 256, 256, 0, s>>>(partial.p, nchunk, n, nb, h, hld, hoff + i0,
+                                                               accumulate ? 1 : 0);
+    GFCC_LAUNCH_CHECK();
+  }
+}
+
+void gmres_batched(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, const cplx* shifts_dev, int nb0,
+                   SolveStatus& st, bool transpose) {
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  const int k = std::max(1, std::min(c->opts.restart, 256));
+  const double tol = c->opts.tol;
+  const int inner_prec = c->opts.precision;
+  st.relres.assign(nb0, 0.0);
+  st.iters.assign(nb0, 0);
+  st.converged.assign(nb0, 0);
+  if (nb0 == 0) return;
+
+  // shifts on host (for compaction bookkeeping)
+  std::vector<cplx> hshift(nb0);
+  GFCC_CUDA(cudaMemcpyAsync(hshift.data(), shifts_dev, sizeof(cplx) * nb0, cudaMemcpyDeviceToHost, s));
+
+  // working copies
+  DBuf<cplx> Bw, Xw, Rw, Yw, V, Zw, H, cs, sn, g, partial, tmpc, shw, hb;
+  DBuf<double> nrm, bnorm;
+  DBuf<int> kc, live, nlive, cols, flag;
+  Bw.alloc(D * nb0); Xw.alloc(D * nb0); Rw.alloc(D * nb0); Yw.alloc(D * nb0); Zw.alloc(D * nb0);
+  V.alloc((long long)(k + 1) * D * nb0);
+  V.zero(s);
+  H.alloc((long long)nb0 * (k + 1) * k);
+  cs.alloc((long long)nb0 * k); sn.alloc((long long)nb0 * k); g.alloc((long long)nb0 * (k + 1));
+  hb.alloc((long long)nb0 * (k + 1));
+  nrm.alloc(nb0); bnorm.alloc(nb0); kc.alloc(nb0); live.alloc(nb0); nlive.alloc(1); cols.alloc(nb0);
+  shw.alloc(nb0);
+  flag.alloc(1);
+  GFCC_CUDA(cudaMemcpyAsync(Bw.p, Bin, sizeof(cplx) * D * nb0, cudaMemcpyDeviceToDevice, s));
+  GFCC_CUDA(cudaMemcpyAsync(shw.p, shifts_dev, sizeof(cplx) * nb0, cudaMemcpyDeviceToDevice, s));
+  Xw.zero(s);
+  {  // non-finite right-hand sides or shifts
+    flag.zero(s);
+    nonfinite_cplx_kernel<<<grid_for(D * nb0), 256, 0, s>>>(Bw.p, D * nb0, flag.p);
+    nonfinite_cplx_kernel<<<1, 256, 0, s>>>(shw.p, nb0, flag.p);
+    GFCC_LAUNCH_CHECK();
+    int hf = 0;
+    GFCC_CUDA(cudaMemcpyAsync(&hf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GFCC_CUDA(cudaStreamSynchronize(s));
+    GFCC_CHECK(hf == 0, GFCC_ERR_NONFINITE, "solve: non-finite right-hand side or frequency");
+  }
+  col_norms(Bw.p, D, nb0, bnorm.p, partial, tmpc, s);
+  std::vector<double> hbn(nb0);
+  GFCC_CUDA(cudaMemcpyAsync(hbn.data(), bnorm.p, sizeof(double) * nb0, cudaMemcpyDeviceToHost, s));
+  GFCC_CUDA(cudaStreamSynchronize(s));
+
+  std::vector<int> map(nb0);   // working column -> original column
+  for (int i = 0; i < nb0; ++i) map[i] = i;
+  int nb = nb0;
+  std::vector<double> hres(nb0);
+  const int max_cycles = std::max(1, c->opts.max_restarts);
+
+  for (int cycle = 0; cycle <= max_cycles && nb > 0; ++cycle) {
+    // FP64 residual R = B - (shift X + M X)
+    sigma_batch(c, Xw.p, Yw.p, nb, nb, shw.p, GFCC_PREC_FP64, transpose, s);
+    residual_kernel<<<grid_for(D * nb), 256, 0, s>>>(Bw.p, Yw.p, Rw.p, D * nb);
+    GFCC_LAUNCH_CHECK();
+    col_norms(Rw.p, D, nb, nrm.p, partial, tmpc, s);
+    GFCC_CUDA(cudaMemcpyAsync(hres.data(), nrm.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+    GFCC_CUDA(cudaStreamSynchronize(s));
+    c->stats.restarts++;
+
+    // classify columns
+    std::vector<int> done, keep;
+    for (int w = 0; w < nb; ++w) {
+      int orig = map[w];
+      double bn = hbn[orig];
+      double rel = bn > 0.0 ? hres[w] / bn : 0.0;
+      GFCC_CHECK(std::isfinite(rel), GFCC_ERR_NONFINITE, "solve: non-finite residual (singular shift?)");
+      st.relres[orig] = rel;
+      if (rel <= tol || cycle == max_cycles) {
+        done.push_back(w);
+        st.converged[orig] = rel <= tol ? 1 : 0;
+      } else {
+        keep.push_back(w);
+      }
+    }
+    if (!done.empty()) {  // write finished columns out
+      std::vector<int> hd(done.size()), ho(done.size());
+      for (size_t q = 0; q < done.size(); ++q) { hd[q] = done[q]; ho[q] = map[done[q]]; }
+      DBuf<int> dsrc, ddst;
+      dsrc.alloc(hd.size()); ddst.alloc(ho.size());
+      GFCC_CUDA(cudaMemcpyAsync(dsrc.p, hd.data(), sizeof(int) * hd.size(), cudaMemcpyHostToDevice, s));
+      GFCC_CUDA(cudaMemcpyAsync(ddst.p, ho.data(), sizeof(int) * ho.size(), cudaMemcpyHostToDevice, s));
+      // gather done columns into Zw (scratch) then scatter to the outputs
+      gather_cols_kernel<<<grid_for(D * hd.size()), 256, 0, s>>>(Xw.p, nb, dsrc.p, (int)hd.size(), Zw.p,
+                                                                  (int)hd.size(), D);
+      scatter_cols_kernel<<<grid_for(D * hd.size()), 256, 0, s>>>(Zw.p, (int)hd.size(), ddst.p, (int)hd.size(),
+                                                                   Xout, nb0, D);
+      if (Rout) {
+        gather_cols_kernel<<<grid_for(D * hd.size()), 256, 0, s>>>(Rw.p, nb, dsrc.p, (int)hd.size(), Zw.p,
+                                                                    (int)hd.size(), D);
+        scatter_cols_kernel<<<grid_for(D * hd.size()), 256, 0, s>>>(Zw.p, (int)hd.size(), ddst.p,
+                                                                     (int)hd.size(), Rout, nb0, D);
+      }
+      GFCC_LAUNCH_CHECK();
+      GFCC_CUDA(cudaStreamSynchronize(s));
+    }
+    if (keep.empty()) { nb = 0; break; }
+    if ((int)keep.size() < nb) {  // compact B, X, R, shifts
+      int nk = (int)keep.size();
+      GFCC_CUDA(cudaMemcpyAsync(cols.p, keep.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, s));
+      for (DBuf<cplx>* b : {&Bw, &Xw, &Rw}) {
+        gather_cols_kernel<<<grid_for(D * nk), 256, 0, s>>>(b->p, nb, cols.p, nk, Zw.p, nk, D);
+        GFCC_LAUNCH_CHECK();
+        GFCC_CUDA(cudaMemcpyAsync(b->p, Zw.p, sizeof(cplx) * D * nk, cudaMemcpyDeviceToDevice, s));
+      }
+      std::vector<cplx> nsh(nk);
+      std::vector<int> nmap(nk);
+      for (int q = 0; q < nk; ++q) { nsh[q] = hshift[map[keep[q]]]; nmap[q] = map[keep[q]]; }
+      GFCC_CUDA(cudaMemcpyAsync(shw.p, nsh.data(), sizeof(cplx) * nk, cudaMemcpyHostToDevice, s));
+      std::vector<double> nbn(nk), nres(nk);
+      for (int q = 0; q < nk; ++q) nres[q] = hres[keep[q]];
+      GFCC_CUDA(cudaMemcpyAsync(nrm.p, nres.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, s));
+      map = nmap;
+      nb = nk;
+      GFCC_CUDA(cudaStreamSynchronize(s));
+    }
+    // bnorm of the working set (for the in-cycle estimate, relative to ||b||)
+    {
+      std::vector<double> wb(nb);
+      for (int q = 0; q < nb; ++q) wb[q] = hbn[map[q]];
+      GFCC_CUDA(cudaMemcpyAsync(bnorm.p, wb.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+    }
+    // GMRES(k) on the correction: V0 = R / ||R||, g = (||R||, 0, ...)
+    scale_cols_kernel<<<grid_for(D * nb), 256, 0, s>>>(Rw.p, V.p, nrm.p, D, nb);
+    GFCC_LAUNCH_CHECK();
+    {
+      std::vector<cplx> g0((size_t)nb * (k + 1), make_cuDoubleComplex(0.0, 0.0));
+      std::vector<double> rn(nb);
+      GFCC_CUDA(cudaMemcpyAsync(rn.data(), nrm.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+      GFCC_CUDA(cudaStreamSynchronize(s));
+      for (int q = 0; q < nb; ++q) g0[(size_t)q * (k + 1)] = make_cuDoubleComplex(rn[q], 0.0);
+      GFCC_CUDA(cudaMemcpyAsync(g.p, g0.data(), sizeof(cplx) * g0.size(), cudaMemcpyHostToDevice, s));
+      std::vector<int> ones(nb, 1);
+      GFCC_CUDA(cudaMemcpyAsync(live.p, ones.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s));
+      GFCC_CUDA(cudaMemsetAsync(kc.p, 0, sizeof(int) * nb, s));
+      GFCC_CUDA(cudaMemsetAsync(H.p, 0, sizeof(cplx) * (size_t)nb * (k + 1) * k, s));
+    }
+    const long long vstride = D * nb;
+    for (int j = 0; j < k; ++j) {
+      cplx* Vj = V.p + j * vstride;
+      cplx* Vn = V.p + (j + 1) * vstride;
+      precond_kernel<<<grid_for(D * nb), 256, 0, s>>>(Vj, Zw.p, c->op.mdiag.p, shw.p, D, nb);
+      GFCC_LAUNCH_CHECK();
+      sigma_batch(c, Zw.p, Yw.p, nb, nb, shw.p, inner_prec, transpose, s);
+      // CGS with one re-orthogonalisation: h = V^H w, w -= V h, twice; H[:, j] = h1 + h2
+      for (int pass = 0; pass < 2; ++pass) {
+        multidot(V.p, vstride, j + 1, Yw.p, D, nb, hb.p, k + 1, 0, false, partial, s);
+        update_kernel<<<grid_for(D * nb), 256, 0, s>>>(V.p, vstride, j + 1, Yw.p, D, nb, hb.p, k + 1, 0, -1.0);
+        GFCC_LAUNCH_CHECK();
+        add_h_kernel<<<(nb * (j + 1) + 255) / 256, 256, 0, s>>>(hb.p, k + 1, H.p + (long long)j * (k + 1),
+                                                                (k + 1) * k, j + 1, nb, pass == 0 ? 0 : 1);
+        GFCC_LAUNCH_CHECK();
+      }
+      col_norms(Yw.p, D, nb, nrm.p, partial, tmpc, s);
+      scale_cols_kernel<<<grid_for(D * nb), 256, 0, s>>>(Yw.p, Vn, nrm.p, D, nb);
+      GFCC_LAUNCH_CHECK();
+      GFCC_CUDA(cudaMemsetAsync(nlive.p, 0, sizeof(int), s));
+      givens_kernel<<<(nb + 127) / 128, 128, 0, s>>>(H.p, cs.p, sn.p, g.p, nrm.p, bnorm.p, kc.p, live.p, nb, k, j,
+                                                     tol, nlive.p);
+      GFCC_LAUNCH_CHECK();
+      int hl = 0;
+      GFCC_CUDA(cudaMemcpyAsync(&hl, nlive.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+      GFCC_CUDA(cudaStreamSynchronize(s));
+      c->stats.gmres_iters++;
+      for (int q = 0; q < nb; ++q) st.iters[map[q]]++;
+      if (hl == 0) break;
+    }
+    backsolve_kernel<<<(nb + 127) / 128, 128, 0, s>>>(H.p, g.p, kc.p, nb, k);
+    GFCC_LAUNCH_CHECK();
+    // X += P V y (only the first kc basis vectors carry weight; later y entries are zero)
+    correct_kernel<<<grid_for(D * nb), 256, 0, s>>>(V.p, vstride, k, g.p, k + 1, Xw.p, c->op.mdiag.p, shw.p, D, nb);
+    GFCC_LAUNCH_CHECK();
+  }
+  GFCC_CUDA(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------------------------------------------
+namespace {
+__global__ void gather_rows_kernel(const double* __restrict__ src, int ld_src, const int* __restrict__ rows,
+                                   int nrows, long long D, cplx* __restrict__ dst, int ldb) {
+  long long total = D * nrows;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int kq = (int)(t % nrows);
+    long long nu = t / nrows;
+    dst[nu * ldb + kq] = make_cuDoubleComplex(src[(long long)rows[kq] * ld_src + nu], 0.0);
+  }
+}
+__global__ void cols_to_batch_kernel(const cplx* __restrict__ src, int lds, int ncols, long long D,
+                                     cplx* __restrict__ dst, int ldb) {
+  long long total = D * ncols;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int cc = (int)(t % ncols);
+    long long nu = t / ncols;
+    dst[nu * ldb + cc] = src[(long long)cc * lds + nu];
+  }
+}
+__global__ void batch_to_cols_kernel(const cplx* __restrict__ src, int ldb, int ncols, long long D,
+                                     cplx* __restrict__ dst, int ldd) {
+  long long total = D * ncols;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long nu = t % D;
+    int cc = (int)(t / D);
+    dst[(long long)cc * ldd + nu] = src[nu * ldb + cc];
+  }
+}
+}  // namespace
+
+void gather_rows_real_to_cplx(const double* src, int ld_src, const int* rows, int nrows, int D, cplx* dst,
+                              int ldb, cudaStream_t s) {
+  if (nrows == 0) return;
+  gather_rows_kernel<<<grid_for((long long)D * nrows), 256, 0, s>>>(src, ld_src, rows, nrows, D, dst, ldb);
+  GFCC_LAUNCH_CHECK();
+}
+void pack_cols_to_batch(const cplx* src, int ld_src, int ncols, int D, cplx* dst, int ldb, cudaStream_t s) {
+  if (ncols == 0) return;
+  cols_to_batch_kernel<<<grid_for((long long)D * ncols), 256, 0, s>>>(src, ld_src, ncols, D, dst, ldb);
+  GFCC_LAUNCH_CHECK();
+}
+void batch_to_cols(const cplx* src, int ldb, int ncols, int D, cplx* dst, int ld_dst, cudaStream_t s) {
+  if (ncols == 0) return;
+  batch_to_cols_kernel<<<grid_for((long long)D * ncols), 256, 0, s>>>(src, ldb, ncols, D, dst, ld_dst);
+  GFCC_LAUNCH_CHECK();
+}
+
+// G[c][q] = sum_nu c_q[nu] X[nu][c]  as a complex GEMM with a real-valued left operand: do it as a
+// real GEMM on the interleaved columns: G'[q][2c+r] = sum_nu cvec[q][nu] X'[nu][2c+r]
+void green_from_batch(const double* cvec, int D, const int* qrows_host, int nq, const cplx* X, int ldb,
+                      int ncols, cplx* G, cudaStream_t s) {
+  if (nq == 0 || ncols == 0) return;
+  DBuf<double> Cq;
+  DBuf<cplx> tmp;
+  Cq.alloc((long long)nq * D);
+  tmp.alloc((long long)nq * ncols);
+  for (int q = 0; q < nq; ++q)
+    GFCC_CUDA(cudaMemcpyAsync(Cq.p + (long long)q * D, cvec + (long long)qrows_host[q] * D, sizeof(double) * D,
+                              cudaMemcpyDeviceToDevice, s));
+  // tmp'[q][2c+r] = sum_nu Cq[q][nu] X'[nu][2c+r]
+  GemmDesc gd;
+  gd.M = nq; gd.N = 2 * ncols; gd.K = D;
+  gd.A = Cq.p; gd.sam = D; gd.sak = 1;
+  gd.B = reinterpret_cast<const double*>(X); gd.sbk = 2LL * ldb; gd.sbn = 1;
+  gd.C = reinterpret_cast<double*>(tmp.p); gd.scm = 2LL * ncols; gd.scn = 1;
+  gd.alpha = 1.0; gd.beta = 0.0;
+  dgemm(gd, s);
+  // G[c][q] = tmp[q][c]
+  int dims[3] = {nq, ncols, 2};
+  int pm[3] = {1, 0, 2};
+  permute(reinterpret_cast<const double*>(tmp.p), dims, 3, pm, reinterpret_cast<double*>(G), 1.0, 0.0, s);
+  GFCC_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace gfcc

@@ -1,0 +1,727 @@
+// Model-order reduction of the MIMO system (Eqs. gfcclineqn and model) on the GPU, FP64.
+//
+// * Subspace: S holds orthonormalised solutions X_p(w_k). New columns lose their components along
+//   the current S by block classical Gram-Schmidt (two passes), then along each other column by
+//   column (two passes); a column is kept when its norm after the passes is >= drop_tol times its
+//   norm before, else dropped. Orthonormality is in the complex inner product, so the projections
+//   written S^T in Eq. model are applied as S^H.
+// * Z = M S comes for free: every solved column satisfies M x = b - (w - i eta) x - r with the FP64
+//   residual r of the solver, and every linear combination applied to S is applied to Z as well.
+// * Reduced model: Hhat = S^H Z, bhat = S^H b, chat = c^T S, updated incrementally.
+// * Evaluation at many frequencies: Hhat is reduced once to upper Hessenberg form by Householder
+//   reflections (applied alongside to bhat, chat and the residual Gram data); each frequency is then
+//   an O(m^2) shifted Hessenberg solve (one CTA per frequency, partial pivoting between adjacent
+//   rows), followed by Ghat_pq = chat_q^T yhat_p and A = -(1/pi) sum_p Im Ghat_pp.
+// * Residual estimate for refinement: r = (w - i eta) S y + Z y - b is orthogonal to S (Galerkin),
+//   so ||r||^2 = y^H (Z^H Z - Hhat^H Hhat) y - 2 Re y^H (Z^H b - Hhat^H bhat) + ||b||^2 - ||bhat||^2.
+#include "gfcc_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace gfcc {
+namespace {
+
+int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  return (int)std::min<long long>(std::max<long long>(g, 1), 152LL * 32);
+}
+
+__device__ __forceinline__ cplx cz() { return make_cuDoubleComplex(0.0, 0.0); }
+
+// ---- column operations on a batch-minor block Y[nu][c] (ld = nc) -------------------------------
+// partial[chunk][i] = sum_{nu in chunk} conj(Y[nu][i]) Y[nu][j], i < j
+__global__ void rowdot_kernel(const cplx* __restrict__ Y, int nc, long long D, int j, long long rows,
+                              cplx* __restrict__ partial) {
+  const long long r0 = blockIdx.y * rows, r1 = min(D, r0 + rows);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= j) return;
+  cplx acc = cz();
+  for (long long nu = r0; nu < r1; ++nu) {
+    cplx a = Y[nu * nc + i], b = Y[nu * nc + j];
+    acc.x += a.x * b.x + a.y * b.y;
+    acc.y += a.x * b.y - a.y * b.x;
+  }
+  partial[(long long)blockIdx.y * j + i] = acc;
+}
+__global__ void rowdot_reduce_kernel(const cplx* __restrict__ partial, int nchunk, int j, cplx* __restrict__ h) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= j) return;
+  cplx s = cz();
+  for (int k = 0; k < nchunk; ++k) { s.x += partial[(long long)k * j + i].x; s.y += partial[(long long)k * j + i].y; }
+  h[i] = s;
+}
+// Y[nu][j] -= sum_{i<j} Y[nu][i] h[i] (and the same for MY): one warp per row
+__global__ void rowupdate_kernel(cplx* __restrict__ Y, cplx* __restrict__ MY, int nc, long long D, int j,
+                                 const cplx* __restrict__ h) {
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= D) return;
+  cplx s1 = cz(), s2 = cz();
+  for (int i = lane; i < j; i += 32) {
+    cplx hh = h[i];
+    cplx a = Y[warp * nc + i];
+    s1.x += a.x * hh.x - a.y * hh.y; s1.y += a.x * hh.y + a.y * hh.x;
+    if (MY) {
+      cplx b = MY[warp * nc + i];
+      s2.x += b.x * hh.x - b.y * hh.y; s2.y += b.x * hh.y + b.y * hh.x;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    s1.x += __shfl_down_sync(0xffffffffu, s1.x, off); s1.y += __shfl_down_sync(0xffffffffu, s1.y, off);
+    s2.x += __shfl_down_sync(0xffffffffu, s2.x, off); s2.y += __shfl_down_sync(0xffffffffu, s2.y, off);
+  }
+  if (lane == 0) {
+    Y[warp * nc + j].x -= s1.x; Y[warp * nc + j].y -= s1.y;
+    if (MY) { MY[warp * nc + j].x -= s2.x; MY[warp * nc + j].y -= s2.y; }
+  }
+}
+// partial sums of |Y[nu][j]|^2
+__global__ void colnorm_kernel(const cplx* __restrict__ Y, int nc, long long D, int j, double* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (long long nu = blockIdx.x * (long long)blockDim.x + threadIdx.x; nu < D; nu += (long long)gridDim.x * blockDim.x) {
+    cplx a = Y[nu * nc + j];
+    s += a.x * a.x + a.y * a.y;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+__global__ void colscale_kernel(cplx* __restrict__ Y, cplx* __restrict__ MY, int nc, long long D, int j, double s) {
+  for (long long nu = blockIdx.x * (long long)blockDim.x + threadIdx.x; nu < D; nu += (long long)gridDim.x * blockDim.x) {
+    Y[nu * nc + j].x *= s; Y[nu * nc + j].y *= s;
+    if (MY) { MY[nu * nc + j].x *= s; MY[nu * nc + j].y *= s; }
+  }
+}
+// dst[nu][off + k] = src[nu][cols[k]]
+__global__ void append_cols_kernel(const cplx* __restrict__ src, int lds, const int* __restrict__ cols, int nk,
+                                   cplx* __restrict__ dst, int ldd, int off, long long D) {
+  long long total = D * nk;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int k = (int)(t % nk);
+    long long nu = t / nk;
+    dst[nu * ldd + off + k] = src[nu * lds + cols[k]];
+  }
+}
+
+// ---- Householder reduction to Hessenberg form (column-major matrices) ---------------------------
+// v = x - alpha e1 with alpha = -e^{i arg x0} ||x||, tau = 2 / ||v||^2; stores v in vbuf[0..len), tau in *tau
+__global__ void house_kernel(const cplx* __restrict__ x, int len, cplx* __restrict__ v, double* __restrict__ tau) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) s += x[i].x * x[i].x + x[i].y * x[i].y;
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  double nx = sqrt(red[0]);
+  cplx x0 = x[0];
+  double a0 = cuCabs(x0);
+  cplx ph = a0 > 0.0 ? make_cuDoubleComplex(x0.x / a0, x0.y / a0) : make_cuDoubleComplex(1.0, 0.0);
+  cplx alpha = make_cuDoubleComplex(-ph.x * nx, -ph.y * nx);
+  for (int i = threadIdx.x; i < len; i += blockDim.x) v[i] = x[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    v[0] = cuCsub(x0, alpha);
+    double vn2 = red[0] - (x0.x * x0.x + x0.y * x0.y) + (v[0].x * v[0].x + v[0].y * v[0].y);
+    *tau = (nx > 0.0 && vn2 > 0.0) ? 2.0 / vn2 : 0.0;
+  }
+}
+// left: A[r0+i][col] -= tau v[i] (sum_k conj(v[k]) A[r0+k][col]) for col in [c0, c0+ncols); one block per column
+__global__ void house_left_kernel(cplx* __restrict__ A, long long lda, int r0, int len, int c0,
+                                  const cplx* __restrict__ v, const double* __restrict__ tau) {
+  __shared__ cplx red[256];
+  const int col = c0 + blockIdx.x;
+  cplx* a = A + (long long)col * lda + r0;
+  cplx s = cz();
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    cplx vv = v[i], aa = a[i];
+    s.x += vv.x * aa.x + vv.y * aa.y;
+    s.y += vv.x * aa.y - vv.y * aa.x;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) { red[threadIdx.x].x += red[threadIdx.x + w].x; red[threadIdx.x].y += red[threadIdx.x + w].y; }
+    __syncthreads();
+  }
+  cplx wsum = red[0];
+  double t = *tau;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    cplx vv = v[i];
+    cplx d = cuCmul(vv, wsum);
+    a[i].x -= t * d.x;
+    a[i].y -= t * d.y;
+  }
+}
+// right: w[row] = sum_k A[row][c0+k] v[k]; A[row][c0+k] -= tau w[row] conj(v[k]); rows [0, nrows)
+__global__ void house_right_w_kernel(const cplx* __restrict__ A, long long lda, int nrows, int c0, int len,
+                                     const cplx* __restrict__ v, cplx* __restrict__ w) {
+  int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nrows) return;
+  cplx s = cz();
+  for (int k = 0; k < len; ++k) s = cuCadd(s, cuCmul(A[(long long)(c0 + k) * lda + row], v[k]));
+  w[row] = s;
+}
+__global__ void house_right_update_kernel(cplx* __restrict__ A, long long lda, int nrows, int c0, int len,
+                                          const cplx* __restrict__ v, const cplx* __restrict__ w,
+                                          const double* __restrict__ tau) {
+  long long total = (long long)nrows * len;
+  double t = *tau;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    int row = (int)(q % nrows);
+    int k = (int)(q / nrows);
+    cplx d = cuCmul(w[row], cuConj(v[k]));
+    cplx* p = A + (long long)(c0 + k) * lda + row;
+    p->x -= t * d.x;
+    p->y -= t * d.y;
+  }
+}
+
+// ---- per-frequency shifted Hessenberg solve --------------------------------------------------------
+struct EvalArgs {
+  int m, np, nq, nw;
+  const cplx* H;      // m x m col-major (ld m), upper Hessenberg
+  const cplx* bw;     // m x np col-major (ld m)
+  const cplx* cw;     // nq x m col-major (ld nq)
+  const cplx* A1;     // qn x m col-major (ld qn): RS rotated into the Hessenberg basis, may be null
+  const cplx* A2;     // qn x m col-major: RZ rotated
+  const cplx* RB;     // qn x np col-major: coefficients of b_p
+  int qn;
+  const double* bn;   // np: ||b||
+  const int* qidx;    // np: position of p in the q set (-1: none)
+  const double* omegas;
+  double eta;
+  cplx* scratch;      // per CTA: U (m(m+1)/2) | R (m*np) | rows (2m) | T (max(qn*np, np*nq))
+  long long scratch_per_cta;
+  cplx* G;            // [nw][np][nq] or null
+  double* A;          // [nw] or null
+  double* maxres;     // [nw] or null
+  int* singular;
+};
+
+__device__ __forceinline__ double cabs2(cplx a) { return a.x * a.x + a.y * a.y; }
+
+__global__ void __launch_bounds__(256) eval_kernel(EvalArgs a) {
+  const int m = a.m, np = a.np, nq = a.nq;
+  cplx* U = a.scratch + blockIdx.x * a.scratch_per_cta;
+  cplx* R = U + (long long)m * (m + 1) / 2;
+  cplx* rowA = R + (long long)m * np;
+  cplx* rowB = rowA + m;
+  cplx* T = rowB + m;
+  __shared__ int s_swap;
+  __shared__ cplx s_l;
+  __shared__ double s_red[256];
+  for (int w = blockIdx.x; w < a.nw; w += gridDim.x) {
+    const cplx sig = make_cuDoubleComplex(a.omegas[w], -a.eta);
+    // RHS rows R[k*np + p] = bw[k + p*m]
+    for (long long t = threadIdx.x; t < (long long)m * np; t += blockDim.x) {
+      int k = (int)(t / np), p = (int)(t % np);
+      R[t] = a.bw[k + (long long)p * m];
+    }
+    for (int col = threadIdx.x; col < m; col += blockDim.x) {
+      cplx h = a.H[(long long)col * m + 0];
+      if (col == 0) h = cuCadd(h, sig);
+      rowA[col] = h;
+    }
+    __syncthreads();
+    cplx* cur = rowA;
+    cplx* nxt = rowB;
+    for (int j = 0; j < m; ++j) {
+      if (j + 1 < m) {
+        for (int col = j + threadIdx.x; col < m; col += blockDim.x) {
+          cplx h = a.H[(long long)col * m + (j + 1)];
+          if (col == j + 1) h = cuCadd(h, sig);
+          nxt[col] = h;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        s_swap = (j + 1 < m && cabs2(nxt[j]) > cabs2(cur[j])) ? 1 : 0;
+      }
+      __syncthreads();
+      if (s_swap) {
+        cplx* tmp = cur; cur = nxt; nxt = tmp;
+        for (int p = threadIdx.x; p < np; p += blockDim.x) {
+          cplx t0 = R[(long long)j * np + p];
+          R[(long long)j * np + p] = R[(long long)(j + 1) * np + p];
+          R[(long long)(j + 1) * np + p] = t0;
+        }
+      }
+      __syncthreads();
+      const long long off = (long long)j * m - (long long)j * (j - 1) / 2;   // packed row j starts here
+      for (int col = j + threadIdx.x; col < m; col += blockDim.x) U[off + (col - j)] = cur[col];
+      if (j + 1 < m) {
+        if (threadIdx.x == 0) {
+          cplx piv = cur[j];
+          if (piv.x == 0.0 && piv.y == 0.0) { atomicExch(a.singular, 1); s_l = cz(); }
+          else s_l = cuCdiv(nxt[j], piv);
+        }
+        __syncthreads();
+        const cplx l = s_l;
+        for (int col = j + 1 + threadIdx.x; col < m; col += blockDim.x) nxt[col] = cuCsub(nxt[col], cuCmul(l, cur[col]));
+        for (int p = threadIdx.x; p < np; p += blockDim.x)
+          R[(long long)(j + 1) * np + p] = cuCsub(R[(long long)(j + 1) * np + p], cuCmul(l, R[(long long)j * np + p]));
+        __syncthreads();
+        cplx* tmp = cur; cur = nxt; nxt = tmp;
+      }
+    }
+    __syncthreads();
+    // back substitution, column oriented: y_j = R_j / U_jj ; R_i -= U_ij y_j for i < j
+    for (int j = m - 1; j >= 0; --j) {
+      const long long offj = (long long)j * m - (long long)j * (j - 1) / 2;
+      cplx d = U[offj];
+      for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        cplx y = (d.x == 0.0 && d.y == 0.0) ? cz() : cuCdiv(R[(long long)j * np + p], d);
+        R[(long long)j * np + p] = y;
+      }
+      __syncthreads();
+      // R[i][p] -= U[i][j] y_j[p] for i < j
+      for (long long t = threadIdx.x; t < (long long)j * np; t += blockDim.x) {
+        int i = (int)(t / np), p = (int)(t % np);
+        const long long offi = (long long)i * m - (long long)i * (i - 1) / 2;
+        cplx u = U[offi + (j - i)];
+        R[t] = cuCsub(R[t], cuCmul(u, R[(long long)j * np + p]));
+      }
+      __syncthreads();
+    }
+    // Ghat[p][q] = sum_k cw[q][k] y[k][p]
+    if (a.G || a.A) {
+      for (int t = threadIdx.x; t < np * nq; t += blockDim.x) {
+        int p = t / nq, q = t % nq;
+        cplx s = cz();
+        for (int k = 0; k < m; ++k) s = cuCadd(s, cuCmul(a.cw[q + (long long)k * nq], R[(long long)k * np + p]));
+        if (a.G) a.G[((long long)w * np + p) * nq + q] = s;
+        T[t] = s;
+      }
+      __syncthreads();
+      if (a.A) {
+        double acc = 0.0;
+        for (int p = threadIdx.x; p < np; p += blockDim.x) {
+          int qi = a.qidx[p];
+          if (qi >= 0) acc += T[(long long)p * nq + qi].y;
+        }
+        s_red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s2 = 128; s2 > 0; s2 >>= 1) {
+          if (threadIdx.x < s2) s_red[threadIdx.x] += s_red[threadIdx.x + s2];
+          __syncthreads();
+        }
+        if (threadIdx.x == 0) a.A[w] = -s_red[0] / 3.14159265358979323846;
+      }
+      __syncthreads();
+    }
+    // residual norm: u_p = sigma A1 y_p + A2 y_p - RB e_p  (coefficients of r_p in an orthonormal basis)
+    if (a.maxres) {
+      for (long long t = threadIdx.x; t < (long long)a.qn * np; t += blockDim.x) {
+        int r = (int)(t / np), p = (int)(t % np);
+        cplx s = make_cuDoubleComplex(-a.RB[r + (long long)p * a.qn].x, -a.RB[r + (long long)p * a.qn].y);
+        for (int k = 0; k < m; ++k) {
+          cplx coef = cuCadd(cuCmul(sig, a.A1[r + (long long)k * a.qn]), a.A2[r + (long long)k * a.qn]);
+          s = cuCadd(s, cuCmul(coef, R[(long long)k * np + p]));
+        }
+        T[t] = s;
+      }
+      __syncthreads();
+      double mx = 0.0;
+      for (int p = 0; p < np; ++p) {
+        double part = 0.0;
+        for (int r = threadIdx.x; r < a.qn; r += blockDim.x) part += cabs2(T[(long long)r * np + p]);
+        s_red[threadIdx.x] = part;
+        __syncthreads();
+        for (int s2 = 128; s2 > 0; s2 >>= 1) {
+          if (threadIdx.x < s2) s_red[threadIdx.x] += s_red[threadIdx.x + s2];
+          __syncthreads();
+        }
+        mx = fmax(mx, sqrt(s_red[0]) / a.bn[p]);
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) a.maxres[w] = mx;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+__global__ void add_cols_kernel(cplx* __restrict__ T, int ldt, int col, const cplx* __restrict__ h, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) { T[i + (long long)col * ldt].x += h[i].x; T[i + (long long)col * ldt].y += h[i].y; }
+}
+__global__ void set_entry_kernel(cplx* __restrict__ T, long long idx, double v) { T[idx] = make_cuDoubleComplex(v, 0.0); }
+
+// reallocate a batch-minor [rows][old_cap] block as [rows][new_cap] keeping ncols columns
+void regrow_rows(DBuf<cplx>& b, long long rows, int old_cap, int new_cap, int ncols, cudaStream_t s) {
+  DBuf<cplx> nb2;
+  nb2.alloc(rows * new_cap);
+  nb2.zero(s);
+  if (ncols > 0)
+    GFCC_CUDA(cudaMemcpy2DAsync(nb2.p, sizeof(cplx) * new_cap, b.p, sizeof(cplx) * old_cap, sizeof(cplx) * ncols, rows,
+                                cudaMemcpyDeviceToDevice, s));
+  GFCC_CUDA(cudaStreamSynchronize(s));
+  std::swap(b.p, nb2.p);
+  std::swap(b.n, nb2.n);
+}
+// reallocate a col-major [old_ld x ...] matrix as [new_ld x alloc_cols] keeping nrows x ncols
+void regrow_cm(DBuf<cplx>& b, int old_ld, int new_ld, int alloc_cols, int nrows, int ncols, cudaStream_t s) {
+  DBuf<cplx> nb2;
+  nb2.alloc((long long)new_ld * std::max(alloc_cols, 1));
+  nb2.zero(s);
+  if (nrows > 0 && ncols > 0)
+    GFCC_CUDA(cudaMemcpy2DAsync(nb2.p, sizeof(cplx) * new_ld, b.p, sizeof(cplx) * old_ld, sizeof(cplx) * nrows, ncols,
+                                cudaMemcpyDeviceToDevice, s));
+  GFCC_CUDA(cudaStreamSynchronize(s));
+  std::swap(b.p, nb2.p);
+  std::swap(b.n, nb2.n);
+}
+
+// Orthonormalise the nc columns of Y ([D][nc] batch-minor) against the n_cur columns of the basis
+// Bs ([D][cap]) by two block CGS passes, then against each other column by column (two passes),
+// dropping a column whose norm falls below drop_tol of its norm before. The same linear operations
+// are applied to MY when it is non-null. On return the kept columns of Y are orthonormal (dropped ones
+// are zero); Cold (device, n_cur x nc col-major, ld n_cur) and T (device, nc x nc col-major) hold the
+// coefficients y_j = Bs Cold[:, j] + sum_i T[i, j] ynew_i when the pointers are non-null.
+std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cplx* Y, cplx* MY, const cplx* MBs,
+                             int nc, cplx* Cold, cplx* T) {
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  const int nblk = 304;
+  DBuf<double> nparts;
+  nparts.alloc(nblk);
+  auto colnorm = [&](int j) {
+    colnorm_kernel<<<nblk, 256, 0, s>>>(Y, nc, D, j, nparts.p);
+    GFCC_LAUNCH_CHECK();
+    std::vector<double> hp(nblk);
+    GFCC_CUDA(cudaMemcpyAsync(hp.data(), nparts.p, sizeof(double) * nblk, cudaMemcpyDeviceToHost, s));
+    GFCC_CUDA(cudaStreamSynchronize(s));
+    double t = 0.0;
+    for (double x : hp) t += x;
+    return std::sqrt(t);
+  };
+  std::vector<double> n0(nc);
+  for (int j = 0; j < nc; ++j) n0[j] = colnorm(j);
+  if (T) GFCC_CUDA(cudaMemsetAsync(T, 0, sizeof(cplx) * nc * nc, s));
+  if (n_cur > 0) {
+    DBuf<cplx> Cf;
+    Cf.alloc((long long)n_cur * nc);
+    if (Cold) GFCC_CUDA(cudaMemsetAsync(Cold, 0, sizeof(cplx) * n_cur * nc, s));
+    for (int pass = 0; pass < 2; ++pass) {
+      ZGemmDesc g;   // Cf(i, j) = sum_nu conj(Bs[nu][i]) Y[nu][j]   (row-major [n_cur][nc])
+      g.M = n_cur; g.N = nc; g.K = (int)D;
+      g.A = Bs; g.sam = 1; g.sak = cap; g.conjA = true;
+      g.B = Y; g.sbk = nc; g.sbn = 1;
+      g.C = Cf.p; g.scm = nc; g.scn = 1;
+      zgemm(g, s);
+      ZGemmDesc u;   // Y -= Bs Cf
+      u.M = (int)D; u.N = nc; u.K = n_cur;
+      u.A = Bs; u.sam = cap; u.sak = 1;
+      u.B = Cf.p; u.sbk = nc; u.sbn = 1;
+      u.C = Y; u.scm = nc; u.scn = 1;
+      u.alpha = make_cuDoubleComplex(-1.0, 0.0); u.beta = make_cuDoubleComplex(1.0, 0.0);
+      zgemm(u, s);
+      if (MY) { u.A = MBs; u.C = MY; zgemm(u, s); }
+      if (Cold) {   // Cold (col-major, ld n_cur) += Cf (row-major [n_cur][nc])
+        int dims[3] = {n_cur, nc, 2};
+        int pm[3] = {1, 0, 2};
+        permute(reinterpret_cast<const double*>(Cf.p), dims, 3, pm, reinterpret_cast<double*>(Cold), 1.0, 1.0, s);
+      }
+    }
+    GFCC_CUDA(cudaStreamSynchronize(s));
+  }
+  std::vector<int> kept;
+  DBuf<cplx> partial, h;
+  const long long rows = std::max<long long>(512, (D + 255) / 256);
+  const int nchunk = (int)((D + rows - 1) / rows);
+  partial.alloc((long long)nchunk * std::max(nc, 1));
+  h.alloc(std::max(nc, 1));
+  for (int j = 0; j < nc; ++j) {
+    if (j > 0) {
+      for (int pass = 0; pass < 2; ++pass) {
+        dim3 grid((j + 127) / 128, nchunk);
+        rowdot_kernel<<<grid, 128, 0, s>>>(Y, nc, D, j, rows, partial.p);
+        GFCC_LAUNCH_CHECK();
+        rowdot_reduce_kernel<<<(j + 127) / 128, 128, 0, s>>>(partial.p, nchunk, j, h.p);
+        GFCC_LAUNCH_CHECK();
+        rowupdate_kernel<<<(int)((D * 32 + 255) / 256), 256, 0, s>>>(Y, MY, nc, D, j, h.p);
+        GFCC_LAUNCH_CHECK();
+        if (T) {
+          add_cols_kernel<<<(j + 127) / 128, 128, 0, s>>>(T, nc, j, h.p, j);
+          GFCC_LAUNCH_CHECK();
+        }
+      }
+    }
+    double n1 = colnorm(j);
+    bool keep = n0[j] > 0.0 && n1 >= c->opts.drop_tol * n0[j];
+    colscale_kernel<<<grid_for(D), 256, 0, s>>>(Y, MY, nc, D, j, keep ? 1.0 / n1 : 0.0);
+    GFCC_LAUNCH_CHECK();
+    if (T && keep) set_entry_kernel<<<1, 1, 0, s>>>(T, (long long)j * nc + j, n1);
+    if (keep) kept.push_back(j);
+  }
+  GFCC_CUDA(cudaStreamSynchronize(s));
+  return kept;
+}
+
+}  // namespace
+
+static void grow_model(gfcc_ctx* c, int need) {
+  MorState& ms = c->mor;
+  if (need <= ms.m_cap) return;
+  const int np = (int)ms.porb.size(), nq = (int)ms.qorb.size();
+  const int cap = std::max(need, std::max(64, 2 * ms.m_cap));
+  cudaStream_t s = c->stream;
+  regrow_rows(ms.S, c->D, ms.m_cap, cap, ms.m, s);
+  regrow_rows(ms.Z, c->D, ms.m_cap, cap, ms.m, s);
+  regrow_cm(ms.Hh, ms.m_cap, cap, cap, ms.m, ms.m, s);
+  regrow_cm(ms.bh, ms.m_cap, cap, np, ms.m, np, s);
+  regrow_cm(ms.ch, nq, nq, cap, nq, ms.m, s);
+  regrow_cm(ms.RS, ms.q_cap, ms.q_cap, cap, ms.qn, ms.m, s);
+  regrow_cm(ms.RZ, ms.q_cap, ms.q_cap, cap, ms.qn, ms.m, s);
+  ms.m_cap = cap;
+}
+
+static void grow_basis(gfcc_ctx* c, int need) {
+  MorState& ms = c->mor;
+  if (need <= ms.q_cap) return;
+  const int np = (int)ms.porb.size();
+  const int cap = std::max(need, std::max(128, 2 * ms.q_cap));
+  cudaStream_t s = c->stream;
+  regrow_rows(ms.Q, c->D, ms.q_cap, cap, ms.qn, s);
+  regrow_cm(ms.RS, ms.q_cap, cap, std::max(ms.m_cap, 1), ms.qn, ms.m, s);
+  regrow_cm(ms.RZ, ms.q_cap, cap, std::max(ms.m_cap, 1), ms.qn, ms.m, s);
+  regrow_cm(ms.RB, ms.q_cap, cap, np, ms.qn, np, s);
+  ms.q_cap = cap;
+}
+
+// Append the kept columns of Ynew ([D][nc], destroyed) to Q and return, col-major [qn_new x nc], the
+// coefficients of the ORIGINAL columns of Ynew in the enlarged basis (host memory).
+static std::vector<cplx> basis_append(gfcc_ctx* c, cplx* Ynew, int nc) {
+  MorState& ms = c->mor;
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  const int qn0 = ms.qn;
+  DBuf<cplx> Cold, T;
+  Cold.alloc((long long)std::max(qn0, 1) * nc);
+  T.alloc((long long)nc * nc);
+  std::vector<int> kept = ortho_block(c, ms.Q.p, ms.q_cap, qn0, Ynew, nullptr, nullptr, nc,
+                                      qn0 > 0 ? Cold.p : nullptr, T.p);
+  const int acc = (int)kept.size();
+  grow_basis(c, qn0 + acc);
+  if (acc > 0) {
+    DBuf<int> dk;
+    dk.alloc(acc);
+    GFCC_CUDA(cudaMemcpyAsync(dk.p, kept.data(), sizeof(int) * acc, cudaMemcpyHostToDevice, s));
+    append_cols_kernel<<<grid_for(D * acc), 256, 0, s>>>(Ynew, nc, dk.p, acc, ms.Q.p, ms.q_cap, qn0, D);
+    GFCC_LAUNCH_CHECK();
+    GFCC_CUDA(cudaStreamSynchronize(s));
+  }
+  const int qn1 = qn0 + acc;
+  ms.qn = qn1;
+  std::vector<cplx> hC((size_t)std::max(qn0, 1) * nc), hT((size_t)nc * nc);
+  if (qn0 > 0) GFCC_CUDA(cudaMemcpyAsync(hC.data(), Cold.p, sizeof(cplx) * qn0 * nc, cudaMemcpyDeviceToHost, s));
+  GFCC_CUDA(cudaMemcpyAsync(hT.data(), T.p, sizeof(cplx) * nc * nc, cudaMemcpyDeviceToHost, s));
+  GFCC_CUDA(cudaStreamSynchronize(s));
+  std::vector<cplx> out((size_t)qn1 * nc, make_cuDoubleComplex(0.0, 0.0));
+  for (int j = 0; j < nc; ++j) {
+    for (int i = 0; i < qn0; ++i) out[(size_t)j * qn1 + i] = hC[(size_t)j * qn0 + i];
+    for (int r = 0; r < acc; ++r) out[(size_t)j * qn1 + qn0 + r] = hT[(size_t)j * nc + kept[r]];
+  }
+  return out;
+}
+
+// write coefficient columns (host, col-major [rows x ncols]) into a device col-major matrix
+static void put_cols(DBuf<cplx>& R, int ld, int col0, const std::vector<cplx>& h, int rows, int hcol0, int ncols,
+                     cudaStream_t s) {
+  if (ncols <= 0 || rows <= 0) return;
+  GFCC_CUDA(cudaMemcpy2DAsync(R.p + (long long)col0 * ld, sizeof(cplx) * ld, h.data() + (size_t)hcol0 * rows,
+                              sizeof(cplx) * rows, sizeof(cplx) * rows, ncols, cudaMemcpyHostToDevice, s));
+  GFCC_CUDA(cudaStreamSynchronize(s));
+}
+
+void mor_init_basis(gfcc_ctx* c) {
+  MorState& ms = c->mor;
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  const int np = (int)ms.porb.size();
+  DBuf<cplx> Bc;
+  DBuf<int> rows;
+  Bc.alloc(D * np);
+  rows.alloc(np);
+  GFCC_CUDA(cudaMemcpyAsync(rows.p, ms.porb.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+  gather_rows_real_to_cplx(c->bvec.p, (int)D, rows.p, np, (int)D, Bc.p, np, s);
+  GFCC_CUDA(cudaStreamSynchronize(s));
+  std::vector<cplx> coef = basis_append(c, Bc.p, np);
+  grow_basis(c, ms.qn);
+  put_cols(ms.RB, ms.q_cap, 0, coef, ms.qn, 0, np, s);
+}
+
+void mor_append(gfcc_ctx* c, const cplx* Xin, const cplx* MXin, int nc) {
+  MorState& ms = c->mor;
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  const int np = (int)ms.porb.size(), nq = (int)ms.qorb.size();
+  if (nc == 0) return;
+  DBuf<cplx> Y, MY;
+  Y.alloc(D * nc);
+  MY.alloc(D * nc);
+  GFCC_CUDA(cudaMemcpyAsync(Y.p, Xin, sizeof(cplx) * D * nc, cudaMemcpyDeviceToDevice, s));
+  GFCC_CUDA(cudaMemcpyAsync(MY.p, MXin, sizeof(cplx) * D * nc, cudaMemcpyDeviceToDevice, s));
+  std::vector<int> kept = ortho_block(c, ms.S.p, ms.m_cap, ms.m, Y.p, MY.p, ms.Z.p, nc, nullptr, nullptr);
+  const int acc = (int)kept.size();
+  if (acc == 0) return;
+  const int m0 = ms.m, m1 = ms.m + acc;
+  grow_model(c, m1);
+  const int cap = ms.m_cap;
+  DBuf<cplx> SZ;   // [S_new | Z_new] for the residual basis
+  SZ.alloc(D * 2 * acc);
+  {
+    DBuf<int> dk, di;
+    dk.alloc(acc);
+    di.alloc(acc);
+    std::vector<int> iota(acc);
+    for (int k = 0; k < acc; ++k) iota[k] = k;
+    GFCC_CUDA(cudaMemcpyAsync(dk.p, kept.data(), sizeof(int) * acc, cudaMemcpyHostToDevice, s));
+    append_cols_kernel<<<grid_for(D * acc), 256, 0, s>>>(Y.p, nc, dk.p, acc, ms.S.p, cap, m0, D);
+    append_cols_kernel<<<grid_for(D * acc), 256, 0, s>>>(MY.p, nc, dk.p, acc, ms.Z.p, cap, m0, D);
+    append_cols_kernel<<<grid_for(D * acc), 256, 0, s>>>(Y.p, nc, dk.p, acc, SZ.p, 2 * acc, 0, D);
+    append_cols_kernel<<<grid_for(D * acc), 256, 0, s>>>(MY.p, nc, dk.p, acc, SZ.p, 2 * acc, acc, D);
+    GFCC_LAUNCH_CHECK();
+    GFCC_CUDA(cudaStreamSynchronize(s));
+  }
+  auto proj = [&](const cplx* Lp, int l0, int nl, const cplx* Rp, int r0, int nr, long long ldr_rows,
+                  cplx* Cp, long long scm, long long scn) {
+    // C(i, j) = sum_nu conj(L[nu][l0+i]) R[nu][r0+j]
+    ZGemmDesc g;
+    g.M = nl; g.N = nr; g.K = (int)D;
+    g.A = Lp + l0; g.sam = 1; g.sak = cap; g.conjA = true;
+    g.B = Rp + r0; g.sbk = ldr_rows; g.sbn = 1;
+    g.C = Cp; g.scm = scm; g.scn = scn;
+    zgemm(g, s);
+  };
+  // Hhat[0:m1, m0:m1] = S^H Z_new ; Hhat[m0:m1, 0:m0] = S_new^H Z_old
+  proj(ms.S.p, 0, m1, ms.Z.p, m0, acc, cap, ms.Hh.p + (long long)m0 * cap, 1, cap);
+  if (m0 > 0) proj(ms.S.p, m0, acc, ms.Z.p, 0, m0, cap, ms.Hh.p + m0, 1, cap);
+  DBuf<cplx> Bc, Cc;
+  Bc.alloc(D * np);
+  Cc.alloc(D * nq);
+  {
+    DBuf<int> rows_p, rows_q;
+    rows_p.alloc(np); rows_q.alloc(nq);
+    GFCC_CUDA(cudaMemcpyAsync(rows_p.p, ms.porb.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+    GFCC_CUDA(cudaMemcpyAsync(rows_q.p, ms.qorb.data(), sizeof(int) * nq, cudaMemcpyHostToDevice, s));
+    gather_rows_real_to_cplx(c->bvec.p, (int)D, rows_p.p, np, (int)D, Bc.p, np, s);
+    gather_rows_real_to_cplx(c->cvec.p, (int)D, rows_q.p, nq, (int)D, Cc.p, nq, s);
+    GFCC_CUDA(cudaStreamSynchronize(s));
+  }
+  proj(ms.S.p, m0, acc, Bc.p, 0, np, np, ms.bh.p + m0, 1, cap);
+  {  // chat[q][m0+i] = sum_nu Cc[nu][q] S[nu][m0+i]
+    ZGemmDesc g;
+    g.M = nq; g.N = acc; g.K = (int)D;
+    g.A = Cc.p; g.sam = 1; g.sak = nq;
+    g.B = ms.S.p + m0; g.sbk = cap; g.sbn = 1;
+    g.C = ms.ch.p + (long long)m0 * nq; g.scm = 1; g.scn = nq;
+    zgemm(g, s);
+  }
+  GFCC_CUDA(cudaStreamSynchronize(s));
+  ms.m = m1;
+  // residual basis: coefficients of S_new and Z_new in Q
+  std::vector<cplx> coef = basis_append(c, SZ.p, 2 * acc);
+  grow_basis(c, ms.qn);
+  grow_model(c, m1);
+  put_cols(ms.RS, ms.q_cap, m0, coef, ms.qn, 0, acc, s);
+  put_cols(ms.RZ, ms.q_cap, m0, coef, ms.qn, acc, acc, s);
+}
+
+void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, double* A_dev, double* maxres_dev) {
+  MorState& ms = c->mor;
+  cudaStream_t s = c->stream;
+  const int m = ms.m, np = (int)ms.porb.size(), nq = (int)ms.qorb.size(), cap = ms.m_cap, qn = ms.qn;
+  GFCC_CHECK(m > 0, GFCC_ERR_STATE, "mor_eval: empty reduced model");
+  const bool want_res = maxres_dev != nullptr;
+  DBuf<cplx> Hw, bw, cw, A1, A2, RBw, v, wv;
+  DBuf<double> tau, dbn;
+  Hw.alloc((long long)m * m); bw.alloc((long long)m * np); cw.alloc((long long)nq * m);
+  GFCC_CUDA(cudaMemcpy2DAsync(Hw.p, sizeof(cplx) * m, ms.Hh.p, sizeof(cplx) * cap, sizeof(cplx) * m, m,
+                              cudaMemcpyDeviceToDevice, s));
+  GFCC_CUDA(cudaMemcpy2DAsync(bw.p, sizeof(cplx) * m, ms.bh.p, sizeof(cplx) * cap, sizeof(cplx) * m, np,
+                              cudaMemcpyDeviceToDevice, s));
+  GFCC_CUDA(cudaMemcpyAsync(cw.p, ms.ch.p, sizeof(cplx) * nq * m, cudaMemcpyDeviceToDevice, s));
+  if (want_res) {
+    A1.alloc((long long)qn * m); A2.alloc((long long)qn * m); RBw.alloc((long long)qn * np);
+    GFCC_CUDA(cudaMemcpy2DAsync(A1.p, sizeof(cplx) * qn, ms.RS.p, sizeof(cplx) * ms.q_cap, sizeof(cplx) * qn, m,
+                                cudaMemcpyDeviceToDevice, s));
+    GFCC_CUDA(cudaMemcpy2DAsync(A2.p, sizeof(cplx) * qn, ms.RZ.p, sizeof(cplx) * ms.q_cap, sizeof(cplx) * qn, m,
+                                cudaMemcpyDeviceToDevice, s));
+    GFCC_CUDA(cudaMemcpy2DAsync(RBw.p, sizeof(cplx) * qn, ms.RB.p, sizeof(cplx) * ms.q_cap, sizeof(cplx) * qn, np,
+                                cudaMemcpyDeviceToDevice, s));
+  }
+  // Householder reduction to upper Hessenberg form: H = P^H Hhat P, P = P_0 P_1 ...; the left
+  // reflections go to bhat, the right ones to chat and to the residual coefficient matrices.
+  v.alloc(m); wv.alloc(std::max({m, nq, qn, 1})); tau.alloc(1);
+  for (int j = 0; j + 2 < m; ++j) {
+    const int len = m - j - 1;
+    house_kernel<<<1, 256, 0, s>>>(Hw.p + (long long)j * m + j + 1, len, v.p, tau.p);
+    GFCC_LAUNCH_CHECK();
+    house_left_kernel<<<m - j, 256, 0, s>>>(Hw.p, m, j + 1, len, j, v.p, tau.p);
+    house_left_kernel<<<np, 256, 0, s>>>(bw.p, m, j + 1, len, 0, v.p, tau.p);
+    GFCC_LAUNCH_CHECK();
+    house_right_w_kernel<<<(m + 127) / 128, 128, 0, s>>>(Hw.p, m, m, j + 1, len, v.p, wv.p);
+    house_right_update_kernel<<<grid_for((long long)m * len), 256, 0, s>>>(Hw.p, m, m, j + 1, len, v.p, wv.p, tau.p);
+    house_right_w_kernel<<<(nq + 127) / 128, 128, 0, s>>>(cw.p, nq, nq, j + 1, len, v.p, wv.p);
+    house_right_update_kernel<<<grid_for((long long)nq * len), 256, 0, s>>>(cw.p, nq, nq, j + 1, len, v.p, wv.p, tau.p);
+    if (want_res) {
+      house_right_w_kernel<<<(qn + 127) / 128, 128, 0, s>>>(A1.p, qn, qn, j + 1, len, v.p, wv.p);
+      house_right_update_kernel<<<grid_for((long long)qn * len), 256, 0, s>>>(A1.p, qn, qn, j + 1, len, v.p, wv.p, tau.p);
+      house_right_w_kernel<<<(qn + 127) / 128, 128, 0, s>>>(A2.p, qn, qn, j + 1, len, v.p, wv.p);
+      house_right_update_kernel<<<grid_for((long long)qn * len), 256, 0, s>>>(A2.p, qn, qn, j + 1, len, v.p, wv.p, tau.p);
+    }
+    GFCC_LAUNCH_CHECK();
+  }
+  std::vector<int> qidx(np, -1);
+  for (int p = 0; p < np; ++p)
+    for (int q = 0; q < nq; ++q)
+      if (ms.qorb[q] == ms.porb[p]) { qidx[p] = q; break; }
+  DBuf<int> dq, dsing;
+  DBuf<double> dom;
+  dq.alloc(np); dsing.alloc(1); dom.alloc(nw); dbn.alloc(np);
+  dsing.zero(s);
+  GFCC_CUDA(cudaMemcpyAsync(dq.p, qidx.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+  GFCC_CUDA(cudaMemcpyAsync(dom.p, omegas_host, sizeof(double) * nw, cudaMemcpyHostToDevice, s));
+  GFCC_CUDA(cudaMemcpyAsync(dbn.p, ms.bnorm.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s));
+  // per-CTA scratch, grid bounded by memory
+  const long long tsz = std::max<long long>((long long)np * nq, want_res ? (long long)qn * np : 0);
+  const long long per = (long long)m * (m + 1) / 2 + (long long)m * np + 2LL * m + tsz + 64;
+  size_t freeb = 0, totalb = 0;
+  GFCC_CUDA(cudaMemGetInfo(&freeb, &totalb));
+  long long maxcta = std::max<long long>(1, (long long)(0.4 * (double)freeb) / (per * (long long)sizeof(cplx)));
+  int ncta = (int)std::min<long long>({(long long)nw, 2LL * 152, maxcta});
+  DBuf<cplx> scratch;
+  scratch.alloc(per * ncta);
+  EvalArgs ea;
+  ea.m = m; ea.np = np; ea.nq = nq; ea.nw = nw;
+  ea.H = Hw.p; ea.bw = bw.p; ea.cw = cw.p;
+  ea.A1 = want_res ? A1.p : nullptr; ea.A2 = want_res ? A2.p : nullptr; ea.RB = want_res ? RBw.p : nullptr;
+  ea.qn = qn;
+  ea.bn = dbn.p; ea.qidx = dq.p; ea.omegas = dom.p; ea.eta = ms.eta;
+  ea.scratch = scratch.p; ea.scratch_per_cta = per;
+  ea.G = G_dev; ea.A = A_dev; ea.maxres = maxres_dev; ea.singular = dsing.p;
+  eval_kernel<<<ncta, 256, 0, s>>>(ea);
+  GFCC_LAUNCH_CHECK();
+  int hs = 0;
+  GFCC_CUDA(cudaMemcpyAsync(&hs, dsing.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GFCC_CUDA(cudaStreamSynchronize(s));
+  GFCC_CHECK(hs == 0, GFCC_ERR_NONFINITE, "mor_eval: singular reduced system at a requested frequency");
+}
+
+}  // namespace gfcc

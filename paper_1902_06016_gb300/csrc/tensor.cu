@@ -1,0 +1,176 @@
+// Dense-tensor helpers for the one-time H-bar build: strided permutation and a two-operand
+// contraction (permute -> FP64 GEMM -> permute-accumulate) driven by index labels.
+#include "gfcc_internal.cuh"
+#include "tensor.h"
+
+#include <algorithm>
+#include <map>
+
+namespace gfcc {
+namespace {
+
+struct PermArgs {
+  int nd;
+  long long dst_dims[6];
+  long long src_stride[6];   // stride in src of the source axis placed at dst position k
+  long long total;
+  double alpha, beta;
+};
+
+__global__ void permute_kernel(const double* __restrict__ src, double* __restrict__ dst, PermArgs a) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < a.total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long rem = t, off = 0;
+#pragma unroll
+    for (int k = 5; k >= 0; --k) {
+      if (k >= a.nd) continue;
+      long long c = rem % a.dst_dims[k];
+      rem /= a.dst_dims[k];
+      off += c * a.src_stride[k];
+    }
+    double v = a.alpha * src[off];
+    dst[t] = (a.beta == 0.0) ? v : v + a.beta * dst[t];
+  }
+}
+
+__global__ void axpby_kernel(long long n, double alpha, const double* __restrict__ x, double beta,
+                             double* __restrict__ y) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] = alpha * x[t] + (beta == 0.0 ? 0.0 : beta * y[t]);
+}
+
+int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  return (int)std::min<long long>(std::max<long long>(g, 1), 152LL * 32);
+}
+
+}  // namespace
+
+void permute(const double* src, const int* dims, int nd, const int* perm, double* dst, double alpha,
+             double beta, cudaStream_t s) {
+  GFCC_CHECK(nd >= 1 && nd <= 6, GFCC_ERR_ARG, "permute: 1..6 dims");
+  long long stride[6];
+  stride[nd - 1] = 1;
+  for (int k = nd - 2; k >= 0; --k) stride[k] = stride[k + 1] * dims[k + 1];
+  PermArgs a{};
+  a.nd = nd;
+  a.total = 1;
+  for (int k = 0; k < nd; ++k) {
+    a.dst_dims[k] = dims[perm[k]];
+    a.src_stride[k] = stride[perm[k]];
+    a.total *= dims[perm[k]];
+  }
+  a.alpha = alpha;
+  a.beta = beta;
+  if (a.total == 0) return;
+  permute_kernel<<<grid_for(a.total), 256, 0, s>>>(src, dst, a);
+  GFCC_LAUNCH_CHECK();
+}
+
+void axpby(long long n, double alpha, const double* x, double beta, double* y, cudaStream_t s) {
+  if (n <= 0) return;
+  axpby_kernel<<<grid_for(n), 256, 0, s>>>(n, alpha, x, beta, y);
+  GFCC_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------------------------
+Tensor::Tensor(std::string l, std::vector<int> d) : labels(std::move(l)), dims(std::move(d)) {
+  GFCC_CHECK(labels.size() == dims.size(), GFCC_ERR_ARG, "tensor labels/dims mismatch");
+  buf.alloc(size());
+}
+long long Tensor::size() const {
+  long long n = 1;
+  for (int d : dims) n *= d;
+  return n;
+}
+TV Tensor::as(const std::string& l) const {
+  GFCC_CHECK(l.size() == dims.size(), GFCC_ERR_ARG, "tensor relabel: rank mismatch");
+  return TV{buf.p, l, dims};
+}
+
+void contract(double alpha, const TV& A, const TV& B, double beta, const TV& C, cudaStream_t s) {
+  const std::string &la = A.l, &lb = B.l, &lc = C.l;
+  std::map<char, int> size;
+  auto reg = [&](const std::string& l, const std::vector<int>& d) {
+    GFCC_CHECK(l.size() == d.size(), GFCC_ERR_ARG, "contract: labels/dims mismatch");
+    for (size_t k = 0; k < l.size(); ++k) {
+      auto it = size.find(l[k]);
+      GFCC_CHECK(it == size.end() || it->second == d[k], GFCC_ERR_ARG,
+                 std::string("contract: size clash on label ") + l[k]);
+      size[l[k]] = d[k];
+    }
+  };
+  reg(la, A.d); reg(lb, B.d); reg(lc, C.d);
+  std::string Ml, Nl, Kl;
+  for (char ch : la) {
+    bool inB = lb.find(ch) != std::string::npos, inC = lc.find(ch) != std::string::npos;
+    GFCC_CHECK(!(inB && inC), GFCC_ERR_ARG, "contract: batch labels unsupported");
+    GFCC_CHECK(inB || inC, GFCC_ERR_ARG, "contract: dangling label in A");
+    if (inC) Ml += ch; else Kl += ch;
+  }
+  for (char ch : lb) {
+    bool inA = la.find(ch) != std::string::npos, inC = lc.find(ch) != std::string::npos;
+    GFCC_CHECK(inA || inC, GFCC_ERR_ARG, "contract: dangling label in B");
+    if (!inA) Nl += ch;
+  }
+  GFCC_CHECK(Ml.size() + Nl.size() == lc.size(), GFCC_ERR_ARG, "contract: output labels");
+  long long M = 1, N = 1, K = 1;
+  for (char ch : Ml) M *= size[ch];
+  for (char ch : Nl) N *= size[ch];
+  for (char ch : Kl) K *= size[ch];
+
+  auto perm_of = [&](const std::string& from, const std::string& to) {
+    std::vector<int> p;
+    for (char ch : to) p.push_back((int)from.find(ch));
+    return p;
+  };
+  auto identity = [](const std::vector<int>& p) {
+    for (size_t k = 0; k < p.size(); ++k)
+      if (p[k] != (int)k) return false;
+    return true;
+  };
+  DBuf<double> Ap, Bp, Cp;
+  const double* Aop = A.p;
+  std::vector<int> pa = perm_of(la, Ml + Kl);
+  if (!identity(pa)) {
+    Ap.alloc(M * K);
+    permute(A.p, A.d.data(), (int)A.d.size(), pa.data(), Ap.p, 1.0, 0.0, s);
+    Aop = Ap.p;
+  }
+  const double* Bop = B.p;
+  std::vector<int> pb = perm_of(lb, Kl + Nl);
+  if (!identity(pb)) {
+    Bp.alloc(K * N);
+    permute(B.p, B.d.data(), (int)B.d.size(), pb.data(), Bp.p, 1.0, 0.0, s);
+    Bop = Bp.p;
+  }
+  std::string lt = Ml + Nl;
+  std::vector<int> pc = perm_of(lt, lc);
+  GFCC_CHECK(M < (1LL << 31) && N < (1LL << 31) && K < (1LL << 31), GFCC_ERR_ARG, "contract: too big");
+  if (identity(pc)) {
+    dgemm_rm((int)M, (int)N, (int)K, alpha, Aop, (int)K, false, Bop, (int)N, false, beta, C.p, (int)N, s);
+  } else {
+    Cp.alloc(M * N);
+    dgemm_rm((int)M, (int)N, (int)K, 1.0, Aop, (int)K, false, Bop, (int)N, false, 0.0, Cp.p, (int)N, s);
+    std::vector<int> dt;
+    for (char ch : lt) dt.push_back(size[ch]);
+    permute(Cp.p, dt.data(), (int)dt.size(), pc.data(), C.p, alpha, beta, s);
+  }
+  // temporaries are released when they leave scope: the stream must be done with them first
+  GFCC_CUDA(cudaStreamSynchronize(s));
+}
+
+void perm(const TV& src, double alpha, double beta, const TV& dst, cudaStream_t s) {
+  GFCC_CHECK(src.l.size() == dst.l.size(), GFCC_ERR_ARG, "perm: rank mismatch");
+  std::vector<int> p;
+  for (size_t k = 0; k < dst.l.size(); ++k) {
+    size_t j = src.l.find(dst.l[k]);
+    GFCC_CHECK(j != std::string::npos, GFCC_ERR_ARG, "perm: label missing");
+    GFCC_CHECK(src.d[j] == dst.d[k], GFCC_ERR_ARG, "perm: size clash");
+    p.push_back((int)j);
+  }
+  permute(src.p, src.d.data(), (int)src.d.size(), p.data(), dst.p, alpha, beta, s);
+}
+
+}  // namespace gfcc

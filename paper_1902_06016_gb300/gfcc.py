@@ -1,0 +1,262 @@
+"""Thin ctypes binding of libgfcc (include/gfcc.h). Argument marshalling only.
+
+Arrays may be NumPy arrays (host memory) or CUDA torch tensors (device memory); outputs are
+allocated here as NumPy arrays unless the caller passes its own buffers. Every computation runs in
+the CUDA library: if ``libgfcc.so`` is missing or cannot be loaded, importing this module's
+``load()`` raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgfcc.so")
+
+PREC_FP64, PREC_TF32, PREC_BF16, PREC_BF16X2 = 0, 1, 2, 3
+PRECISIONS = {"fp64": PREC_FP64, "tf32": PREC_TF32, "bf16": PREC_BF16, "bf16x2": PREC_BF16X2}
+
+ERRORS = {-1: "GFCC_ERR_ARG", -2: "GFCC_ERR_NOT_CONVERGED", -3: "GFCC_ERR_RANK", -4: "GFCC_ERR_NONFINITE",
+          -5: "GFCC_ERR_OOM", -6: "GFCC_ERR_CUDA", -7: "GFCC_ERR_STATE"}
+
+# exported symbols and their prototypes (kept in one place: the CPU tests check the library
+# exports exactly these)
+_dp, _ip, _vp = C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p
+
+
+class VBlocks(C.Structure):
+    _fields_ = [("oooo", _vp), ("ooov", _vp), ("oovv", _vp), ("ovov", _vp), ("ovvv", _vp)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_restarts", C.c_int),
+                ("precision", C.c_int), ("max_batch", C.c_int), ("drop_tol", C.c_double),
+                ("verbose", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("sigma_calls", C.c_longlong), ("sigma_cols", C.c_longlong),
+                ("gmres_iters", C.c_longlong), ("restarts", C.c_longlong),
+                ("max_rel_res", C.c_double), ("not_converged", C.c_int)]
+
+
+PROTOTYPES = {
+    "gfcc_default_opts": (C.c_int, [C.POINTER(Opts)]),
+    "gfcc_init": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, _vp, C.POINTER(VBlocks), _vp, _vp, _vp, _vp,
+                            C.POINTER(Opts), _vp]),
+    "gfcc_dim": (C.c_int, [_vp, _ip]),
+    "gfcc_set_opts": (C.c_int, [_vp, C.POINTER(Opts)]),
+    "gfcc_sigma": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "gfcc_vectors": (C.c_int, [_vp, _vp, C.c_int, C.c_int, _vp, C.c_int]),
+    "gfcc_solve_full": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, C.c_int, _vp, _vp, _vp,
+                                  C.c_int, C.POINTER(Stats)]),
+    "gfcc_mor_build": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, C.c_int]),
+    "gfcc_mor_refine": (C.c_int, [_vp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, _ip, _dp]),
+    "gfcc_mor_eval": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp]),
+    "gfcc_mor_info": (C.c_int, [_vp, _dp, C.c_int, _ip, _ip, _ip, _ip]),
+    "gfcc_mor_save": (C.c_int, [_vp, C.c_char_p]),
+    "gfcc_mor_load": (C.c_int, [_vp, C.c_char_p]),
+    "gfcc_last_error": (C.c_char_p, [_vp]),
+    "gfcc_free": (None, [_vp]),
+}
+
+_LIB = None
+
+
+def load(path: str | None = None):
+    """Load libgfcc.so (raises OSError/RuntimeError if it is missing: there is no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libgfcc.so not found at {p}: build it with paper_1902_06016_gb300.build.build()")
+    lib = C.CDLL(p)
+    for name, (res, args) in PROTOTYPES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class GfccError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(a):
+    """Data pointer of a NumPy array or a torch tensor (host or CUDA)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _c64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _ints(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+@dataclass
+class SolveStats:
+    sigma_calls: int
+    sigma_cols: int
+    gmres_iters: int
+    restarts: int
+    max_rel_res: float
+    not_converged: int
+
+
+class Context:
+    """One GFCC problem on the current CUDA device (wraps gfcc_t)."""
+
+    def __init__(self, inputs, tol=1e-8, restart=30, max_restarts=200, precision="fp64", max_batch=0,
+                 drop_tol=1e-10, stream=None):
+        lib = load()
+        self._lib = lib
+        o, v = inputs.o, inputs.v
+        self.o, self.v = o, v
+        opts = Opts()
+        lib.gfcc_default_opts(C.byref(opts))
+        opts.tol, opts.restart, opts.max_restarts = tol, restart, max_restarts
+        opts.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        opts.max_batch, opts.drop_tol = max_batch, drop_tol
+        self._keep = [_c64(x) for x in (inputs.eps, inputs.oooo, inputs.ooov, inputs.oovv, inputs.ovov,
+                                         inputs.ovvv, inputs.t1, inputs.t2, inputs.l1, inputs.l2)]
+        eps, oooo, ooov, oovv, ovov, ovvv, t1, t2, l1, l2 = self._keep
+        vb = VBlocks(_ptr(oooo), _ptr(ooov), _ptr(oovv), _ptr(ovov), _ptr(ovvv))
+        h = C.c_void_p()
+        rc = lib.gfcc_init(C.byref(h), o, v, _ptr(eps), C.byref(vb), _ptr(t1), _ptr(t2), _ptr(l1), _ptr(l2),
+                           C.byref(opts), stream)
+        if rc != 0:
+            raise GfccError(rc, "gfcc_init failed")
+        self._h = h
+        self._keep = None
+        d = C.c_int()
+        lib.gfcc_dim(h, C.byref(d))
+        self.D = d.value
+
+    # ---------------------------------------------------------------------------------------
+    def _check(self, rc, allow=()):
+        if rc != 0 and rc not in allow:
+            msg = self._lib.gfcc_last_error(self._h)
+            raise GfccError(rc, msg.decode() if msg else "")
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gfcc_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_opts(self, tol=1e-8, restart=30, max_restarts=200, precision="fp64", max_batch=0, drop_tol=1e-10):
+        opts = Opts()
+        self._lib.gfcc_default_opts(C.byref(opts))
+        opts.tol, opts.restart, opts.max_restarts = tol, restart, max_restarts
+        opts.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        opts.max_batch, opts.drop_tol = max_batch, drop_tol
+        self._check(self._lib.gfcc_set_opts(self._h, C.byref(opts)))
+
+    # ---------------------------------------------------------------------------------------
+    def sigma(self, X, precision="fp64", transpose=False, out=None):
+        """Y = M X (or M^T X) for X of shape [nvec, D] complex (NumPy or CUDA torch)."""
+        single = False
+        if isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X, dtype=np.complex128)
+            if X.ndim == 1:
+                X = X[None, :]
+                single = True
+        nvec, ld = X.shape
+        if out is None:
+            out = np.empty((nvec, ld), dtype=np.complex128) if isinstance(X, np.ndarray) else X.new_empty(X.shape)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self._check(self._lib.gfcc_sigma(self._h, _ptr(X), _ptr(out), nvec, ld, prec, int(bool(transpose))))
+        return out[0] if single else out
+
+    def vectors(self, orbitals, left=False):
+        orb = _ints(orbitals)
+        out = np.empty((len(orb), self.D))
+        self._check(self._lib.gfcc_vectors(self._h, _ptr(orb), len(orb), int(left), _ptr(out), self.D))
+        return out
+
+    def solve_full(self, omegas, eta, orbitals, qorb=None, want_G=True, want_A=True, want_X=False,
+                   G=None, A=None, X=None):
+        """Full-dimension solves; returns dict with G [nw, np, nq], A [nw], X [nw, np, D], stats."""
+        w = _c64(omegas)
+        porb = _ints(orbitals)
+        q = _ints(qorb) if qorb is not None else None
+        nq = len(q) if q is not None else len(porb)
+        nw, npp = len(w), len(porb)
+        if want_G and G is None:
+            G = np.empty((nw, npp, nq), dtype=np.complex128)
+        if want_A and A is None:
+            A = np.empty(nw)
+        if want_X and X is None:
+            X = np.empty((nw, npp, self.D), dtype=np.complex128)
+        st = Stats()
+        rc = self._lib.gfcc_solve_full(self._h, _ptr(w), nw, float(eta), _ptr(porb), npp, _ptr(q), nq,
+                                       _ptr(G), _ptr(A), _ptr(X), self.D, C.byref(st))
+        self._check(rc, allow=(-2,))
+        stats = SolveStats(st.sigma_calls, st.sigma_cols, st.gmres_iters, st.restarts, st.max_rel_res,
+                           st.not_converged)
+        return {"G": G, "A": A, "X": X, "stats": stats, "converged": rc == 0}
+
+    def mor_build(self, seeds, eta, orbitals, qorb=None):
+        s = _c64(seeds)
+        porb = _ints(orbitals)
+        q = _ints(qorb) if qorb is not None else None
+        self._check(self._lib.gfcc_mor_build(self._h, _ptr(s), len(s), float(eta), _ptr(porb), len(porb), _ptr(q),
+                                             len(q) if q is not None else 0))
+
+    def mor_refine(self, wmin, wmax, ngrid, tol, m_max):
+        m = C.c_int()
+        e = C.c_double()
+        rc = self._lib.gfcc_mor_refine(self._h, float(wmin), float(wmax), int(ngrid), float(tol), int(m_max),
+                                       C.byref(m), C.byref(e))
+        self._check(rc, allow=(-2,))
+        return {"m": m.value, "max_err": e.value, "converged": rc == 0}
+
+    def mor_eval(self, omegas, want_G=True, want_A=True, want_res=False, np_=None, nq=None, G=None, A=None,
+                 maxres=None):
+        w = _c64(omegas)
+        nw = len(w)
+        if want_G and G is None:
+            info = self.mor_info()
+            G = np.empty((nw, info["np"], info["nq"]), dtype=np.complex128)
+        if want_A and A is None:
+            A = np.empty(nw)
+        if want_res and maxres is None:
+            maxres = np.empty(nw)
+        self._check(self._lib.gfcc_mor_eval(self._h, _ptr(w), nw, _ptr(G), _ptr(A), _ptr(maxres)))
+        return {"G": G, "A": A, "maxres": maxres}
+
+    def mor_info(self):
+        ns, m, npp, nq = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        self._check(self._lib.gfcc_mor_info(self._h, None, 0, C.byref(ns), C.byref(m), None, None))
+        w = np.empty(max(ns.value, 1))
+        self._check(self._lib.gfcc_mor_info(self._h, w.ctypes.data_as(_dp), ns.value, C.byref(ns), C.byref(m),
+                                            C.byref(npp), C.byref(nq)))
+        return {"sampled": w[:ns.value].copy(), "m": m.value, "np": npp.value, "nq": nq.value}
+
+    def mor_save(self, path):
+        self._check(self._lib.gfcc_mor_save(self._h, os.fsencode(path)))
+
+    def mor_load(self, path):
+        self._check(self._lib.gfcc_mor_load(self._h, os.fsencode(path)))
