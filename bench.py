@@ -1,0 +1,301 @@
+"""Benchmark: G_pq(w) points per second of the MOR-accelerated, mixed-precision IP-GFCC pipeline.
+
+One step = the whole hot path on one synthetic molecule-sized problem, through the C ABI:
+  gfcc_init (H-bar build on the GPU) -> gfcc_mor_build (batched GMRES-IR solves at the seed
+  frequencies, orthonormalisation, projection) -> gfcc_mor_refine (adaptive midpoint refinement to
+  the reduced-residual tolerance) -> gfcc_mor_eval (G_pq and A on the dense output grid).
+value = N_w * N_p / step time (G points per second, p = q = occupied spin-orbitals).
+
+Default workload: benzene-sized, o = 42 occupied and v = 186 virtual spin-orbitals (D = 160,188),
+5000 output frequencies on [-1.0, -0.2] Ha, eta = 0.01, 8 seed frequencies, reduced-residual
+tolerance 1e-6, solver tolerance 1e-8, inner sigma in TF32 on the tensor cores.
+
+--impl reference times the FP64 CPU oracle (full-dimension GMRES solves for a bounded sample of
+(w, p) points at the same size) on the host cores and prints the same kind of line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "G_pq(w) points/s, MOR + mixed precision"
+UNIT = "points/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="benzene_o42_v186", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "bf16", "fp64"])
+    ap.add_argument("--nomega", type=int, default=0, help="output grid size (0: the workload's)")
+    ap.add_argument("--seeds", type=int, default=8)
+    ap.add_argument("--mor-tol", type=float, default=1e-6)
+    ap.add_argument("--ngrid", type=int, default=500, help="refinement check grid")
+    ap.add_argument("--m-max", type=int, default=1700)
+    ap.add_argument("--solve-tol", type=float, default=1e-8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=2, help="(w, p) columns in the oracle sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    from paper_1902_06016_gb300 import Context, load
+    from paper_1902_06016_gb300 import gfcc as G
+
+    dev = torch.device("cuda", rank % torch.cuda.device_count())
+    torch.cuda.set_device(dev)
+    load()
+    W = synth.WORKLOADS[args.workload]
+    o, v, eta = W["o"], W["v"], W["eta"]
+    nw = args.nomega or W["nw"]
+    inp = synth.make_inputs(o, v, W["seed"] + rank)       # weak scaling: one problem per rank
+    porb = list(range(o))
+    seeds = synth.omega_grid(W["wmin"], W["wmax"], args.seeds)
+    grid = np.linspace(W["wmin"], W["wmax"], nw)
+
+    # device-resident inputs (HBM) for the device-timed value
+    dev_inputs = synth.Inputs(**{k: (torch.from_numpy(np.ascontiguousarray(getattr(inp, k))).to(dev)
+                                     if isinstance(getattr(inp, k), np.ndarray) else getattr(inp, k))
+                                 for k in inp.__dataclass_fields__})
+    G_dev = torch.empty((nw, o, o), dtype=torch.complex128, device=dev)
+    A_dev = torch.empty((nw,), dtype=torch.float64, device=dev)
+    omega_host = np.ascontiguousarray(grid)
+
+    stream = torch.cuda.current_stream(dev)
+
+    def step(inputs, G_out, A_out):
+        ctx = Context(inputs, tol=args.solve_tol, precision=args.precision, stream=stream.cuda_stream)
+        ctx.mor_build(seeds, eta, porb)
+        ref = ctx.mor_refine(W["wmin"], W["wmax"], args.ngrid, args.mor_tol, args.m_max)
+        ctx.mor_eval(omega_host, G=G_out, A=A_out)
+        info = ctx.mor_info()
+        ctx.close()
+        return ref, info
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(dev_inputs, G_dev, A_dev)
+    torch.cuda.synchronize()
+
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    G.profile(True)
+    l0 = G.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ref, info = step(dev_inputs, G_dev, A_dev)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = G.launch_count() - l0
+    dev_ms = ev0.elapsed_time(ev1) / args.steps
+    classes = {k: G.profile_read(k) for k in (0, 1, 2)}   # (launches, ms, flops)
+    phase_names = {3: "sigma_lowprec", 4: "sigma_fp64_accurate", 5: "krylov_arnoldi", 6: "mor_orthonormalise",
+                   7: "mor_eval", 8: "hbar_build"}
+    phases = {phase_names[k]: round(G.profile_read(k)[1], 1) for k in phase_names}
+    G.profile(False)
+    clk = clocks.stop()
+
+    # end to end: host inputs, host outputs, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        G_host = np.empty((nw, o, o), dtype=np.complex128)
+        A_host = np.empty(nw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(inp, G_host, A_host)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        h2d = sum(getattr(inp, k).nbytes for k in ("eps", "oooo", "ooov", "oovv", "ovov", "ovvv", "t1", "t2", "l1", "l2"))
+        e2e = {"value": nw * o / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(G_host.nbytes + A_host.nbytes)}
+
+    # max over ranks
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dev_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms = float(t.item())
+    value = world * nw * o / (dev_ms / 1e3)
+
+    peaks, peak_kind = measured_peaks()
+    bf16 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    names = {0: f"tc_gemm_kernel<{args.precision}> (inner low-precision sigma GEMMs)",
+             1: "gemm_kernel<double> (FP64 SIMT GEMM)",
+             2: "tc_gemm_kernel<bf16> on exact slices (FP64-accurate residual / projection GEMMs)"}
+    ratio0 = 0.5 if args.precision == "tf32" else 1.0
+    kernels = {}
+    for k, (n, ms, fl) in classes.items():
+        if n == 0 or ms <= 0:
+            continue
+        ach = fl / (ms / 1e3) / 1e12
+        if k == 1:
+            kernels[names[k]] = {"bound": "alu", "launches": n, "ms": ms, "achieved": ach, "unit": "TFLOP/s"}
+        else:
+            pk = bf16 * (ratio0 if k == 0 else 1.0)
+            kernels[names[k]] = {"bound": "tensor", "launches": n, "ms": ms, "achieved": ach, "peak": pk,
+                                 "unit": "TFLOP/s", "frac": ach / pk}
+    roof = None
+    dom = max((k for k in classes if classes[k][0] > 0 and k != 1), key=lambda k: classes[k][1], default=None)
+    if dom is not None:
+        n, ms, fl = classes[dom]
+        ach = fl / (ms / 1e3) / 1e12
+        pk = bf16 * (ratio0 if dom == 0 else 1.0)
+        roof = {"kernel": names[dom], "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk, "traffic": None,
+                "peak_kind": f"{peak_kind} sustained bf16" + (f" x {ratio0} (tf32 rate)" if dom == 0 and ratio0 != 1 else ""),
+                "launches": n, "avg_launch_ms": ms / n}
+    return inp, {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dev_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"c128 (f64 residuals, {args.precision} tensor-core inner sigma)", "data": "synthetic",
+        "config": {"workload": args.workload, "o": o, "v": v, "D": inp.dim, "n_omega": nw, "n_p": o, "n_q": o,
+                   "eta": eta, "window_ha": [W["wmin"], W["wmax"]], "seeds": args.seeds, "mor_tol": args.mor_tol,
+                   "solve_tol": args.solve_tol, "model_order": info["m"], "sampled_freqs": len(info["sampled"]),
+                   "l2": "working set (operators >= 0.5 GB, Krylov bases) larger than L2; no flush",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "gemm_classes": kernels, "phases_ms": phases, "clocks": clk,
+    }
+
+
+# ---------------------------------------------------------------------------------------------
+def oracle_sample(args, ncols, inp=None):
+    """Time the FP64 CPU oracle on a bounded sample: full GMRES solves of ncols (w, p) points."""
+    from oracle import bc, hbar
+    from oracle import solve as sv
+    W = synth.WORKLOADS[args.workload]
+    if inp is None:
+        inp = synth.make_inputs(W["o"], W["v"], W["seed"])
+    hb = hbar.build(inp)
+    porb = list(range(ncols))
+    B = bc.b_vectors(inp, porb)
+    w = [0.5 * (W["wmin"] + W["wmax"])]
+    t0 = time.perf_counter()
+    X, res = sv.gmres_solve(hb, B, w, W["eta"], tol=args.solve_tol)
+    dt = time.perf_counter() - t0
+    return {"value": ncols / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{ncols} full-dimension FP64 GMRES solves (tol {args.solve_tol}) at w = {w[0]} Ha, "
+                      f"p = 0..{ncols - 1}, {args.workload}; H-bar build and input generation untimed",
+            "seconds": dt}
+
+
+def run_reference(args):
+    vals = []
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm-up effects worth a full sample; samples are bounded
+    for _ in range(max(1, args.steps)):
+        vals.append(oracle_sample(args, args.cpu_sample))
+    v = statistics.median(x["value"] for x in vals)
+    cb = dict(vals[0])
+    cb["value"] = v
+    W = synth.WORKLOADS[args.workload]
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": args.workload, "o": W["o"], "v": W["v"]}, "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    inp, out = run_ours(args, rank, world)
+    if rank == 0:
+        if args.cpu_sample > 0:
+            try:
+                out["cpu_baseline"] = oracle_sample(args, args.cpu_sample, inp)
+            except Exception as e:  # the baseline must not hide the GPU line
+                out["cpu_baseline"] = {"error": str(e)}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

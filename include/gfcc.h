@@ -43,15 +43,16 @@ extern "C" {
 
 /* arithmetic of the H-bar sigma contractions */
 #define GFCC_PREC_FP64 0        /* FP64 everywhere */
-#define GFCC_PREC_TF32 1        /* ring/oooo GEMMs on tcgen05 kind::tf32, FP32 accumulate (inner solves) */
-#define GFCC_PREC_BF16 2        /* ring/oooo GEMMs on tcgen05 kind::f16 (bf16), FP32 accumulate */
-#define GFCC_PREC_BF16X2 3      /* split bf16 (hi+lo of the operator), FP32 accumulate */
+#define GFCC_PREC_TF32 1        /* every sigma GEMM on tcgen05 kind::tf32, FP32 accumulate; FP64 diagonal */
+#define GFCC_PREC_BF16 2        /* every sigma GEMM on tcgen05 kind::f16 with bf16 operands, FP32 accumulate */
+#define GFCC_PREC_FP64_TC 3     /* FP64-accurate: exact integer bf16 slices of the FP64 operands on tcgen05,
+                                   exact FP32 partial sums recombined in FP64 (Ozaki scheme) */
 
 typedef struct gfcc_ctx* gfcc_t;
 
 /* Antisymmetrised two-electron integral blocks <pq||rs>, real, row-major, occupied index range
  * first: oooo[i][j][k][l], ooov[i][j][k][a], oovv[i][j][a][b], ovov[i][a][j][b], ovvv[i][a][b][c].
- * Host pointers. (No vvvv block is needed by the IP space.) */
+ * Host or device pointers. (No vvvv block is needed by the IP space.) */
 typedef struct {
   const double* oooo;
   const double* ooov;
@@ -68,6 +69,9 @@ typedef struct {
   int max_batch;       /* max columns (p, w) per batched solve; 0 = choose from memory */
   double drop_tol;     /* subspace rank-truncation threshold (relative), default 1e-10 */
   int verbose;         /* 0 silent, 1 per-call summary on stderr */
+  int residual_precision; /* sigma of the refinement residuals: GFCC_PREC_FP64 (FP64 CUDA cores) or
+                             GFCC_PREC_FP64_TC; -1 (default) = FP64_TC when precision is a tensor-core
+                             kind, FP64 otherwise */
 } gfcc_opts;
 
 typedef struct {
@@ -85,10 +89,11 @@ int gfcc_default_opts(gfcc_opts* opts);
 /* Create a context on the current CUDA device: copy the ground-state inputs and build the H-bar
  * elements of the IP space on the GPU (Hbar_N = e^{-T} H e^{T} - E_0, text after Eq. gfxn1),
  * the free terms b_p (Eq. xplin) and the left vectors c_q (Eq. gfxn2) for all n orbitals.
- *   eps[n]      orbital energies (the reference Fock matrix is diag(eps)); host.
- *   vb          integral blocks, host.
+ *   eps[n]      orbital energies (the reference Fock matrix is diag(eps)).
+ *   vb          integral blocks.
  *   t1[o][v], t2[o][o][v][v] (t_ij^ab, antisymmetric), l1[o][v] (lambda^i_a), l2[o][o][v][v]
- *               (lambda^ij_ab); host.
+ *               (lambda^ij_ab).
+ *   All arrays: host or device (copied with cudaMemcpyDefault).
  *   opts        may be NULL (defaults).  stream: cudaStream_t or NULL for the legacy stream.
  * Errors: GFCC_ERR_ARG (o < 2, v < 1, null pointers), GFCC_ERR_NONFINITE, GFCC_ERR_OOM, GFCC_ERR_CUDA. */
 int gfcc_init(gfcc_t* ctx, int o, int v, const double* eps, const gfcc_vblocks* vb,
@@ -154,6 +159,25 @@ int gfcc_mor_info(gfcc_t ctx, double* w, int cap, int* ns, int* m, int* np, int*
  * refinement resumes without re-solving. The file is a flat binary written by this library. */
 int gfcc_mor_save(gfcc_t ctx, const char* path);
 int gfcc_mor_load(gfcc_t ctx, const char* path);
+
+/* Diagnostic entry point of the tensor-core GEMM used by the low-precision sigma:
+ * C[M][N] = A[M][K] . B[N][K]^T with A, B rounded to bf16 (GFCC_PREC_BF16) or tf32 (GFCC_PREC_TF32)
+ * and FP32 accumulation. Host pointers, row-major; runs on the current device. The paper has no
+ * counterpart: it exists to test the kernel in isolation. */
+int gfcc_tc_gemm(int precision, const double* A, const double* B, int M, int N, int K, float* C);
+
+/* Number of CUDA kernels launched by this library since it was loaded (all contexts). */
+long long gfcc_launch_count(void);
+
+/* Turn per-launch CUDA-event timing of the GEMM kernel classes on (enable = 1) or off, clearing
+ * earlier records. Class 0: tcgen05 GEMM with tf32/bf16-rounded operands (inner solves);
+ * class 1: FP64 SIMT GEMM; class 2: tcgen05 GEMM on exact bf16 slices (FP64-accurate products).
+ * Events are recorded on the stream each kernel is launched on. */
+int gfcc_profile(int enable);
+
+/* Sum over the recorded launches of class cls: number of launches, device milliseconds (CUDA
+ * events, waits for completion) and algorithmic flops (2 M N K per launch, K padded). */
+int gfcc_profile_read(int cls, long long* launches, double* ms, double* flops);
 
 /* Message of the last error on this context ("" if none). Valid until the next call. */
 const char* gfcc_last_error(gfcc_t ctx);

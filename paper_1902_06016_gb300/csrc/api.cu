@@ -207,6 +207,7 @@ int gfcc_default_opts(gfcc_opts* o) {
   o->max_batch = 0;
   o->drop_tol = 1e-10;
   o->verbose = 0;
+  o->residual_precision = -1;
   return GFCC_OK;
 }
 
@@ -214,9 +215,13 @@ static int check_opts(const gfcc_opts* o, std::string& why) {
   if (!(o->tol > 0.0 && o->tol < 1.0)) { why = "opts.tol must be in (0, 1)"; return GFCC_ERR_ARG; }
   if (o->restart < 1 || o->restart > 256) { why = "opts.restart must be in [1, 256]"; return GFCC_ERR_ARG; }
   if (o->max_restarts < 1) { why = "opts.max_restarts must be >= 1"; return GFCC_ERR_ARG; }
-  if (o->precision < GFCC_PREC_FP64 || o->precision > GFCC_PREC_BF16X2) { why = "opts.precision unknown"; return GFCC_ERR_ARG; }
+  if (o->precision < GFCC_PREC_FP64 || o->precision > GFCC_PREC_BF16) { why = "opts.precision unknown"; return GFCC_ERR_ARG; }
   if (o->max_batch < 0) { why = "opts.max_batch must be >= 0"; return GFCC_ERR_ARG; }
   if (!(o->drop_tol > 0.0 && o->drop_tol < 1.0)) { why = "opts.drop_tol must be in (0, 1)"; return GFCC_ERR_ARG; }
+  if (o->residual_precision != -1 && o->residual_precision != GFCC_PREC_FP64 && o->residual_precision != GFCC_PREC_FP64_TC) {
+    why = "opts.residual_precision must be -1, GFCC_PREC_FP64 or GFCC_PREC_FP64_TC";
+    return GFCC_ERR_ARG;
+  }
   return GFCC_OK;
 }
 
@@ -274,7 +279,7 @@ int gfcc_set_opts(gfcc_t c, const gfcc_opts* opts) {
 
 int gfcc_sigma(gfcc_t c, const double* X, double* Y, int nvec, int ld, int precision, int transpose) {
   if (!c) return GFCC_ERR_ARG;
-  if (nvec < 0 || (nvec > 0 && (!X || !Y || ld < c->D)) || precision < 0 || precision > GFCC_PREC_BF16X2) {
+  if (nvec < 0 || (nvec > 0 && (!X || !Y || ld < c->D)) || precision < 0 || precision > GFCC_PREC_FP64_TC) {
     c->last_error = "gfcc_sigma: bad arguments";
     return GFCC_ERR_ARG;
   }
@@ -282,7 +287,8 @@ int gfcc_sigma(gfcc_t c, const double* X, double* Y, int nvec, int ld, int preci
   if (nvec == 0) return GFCC_OK;
   cudaStream_t s = c->stream;
   const long long D = c->D;
-  if (precision != GFCC_PREC_FP64 && c->lp.kind != precision) gfcc::build_low_precision(c, precision);
+  if ((precision == GFCC_PREC_TF32 || precision == GFCC_PREC_BF16) && c->lp.kind != precision)
+    gfcc::build_low_precision(c, precision);
   const int nbmax = std::max(1, std::min(nvec, c->opts.max_batch > 0 ? c->opts.max_batch : 256));
   DBuf<cplx> stage, Xb, Yb;
   stage.alloc((long long)nbmax * ld);
@@ -621,8 +627,36 @@ int gfcc_mor_load(gfcc_t c, const char* path) {
   API_END(c)
 }
 
+int gfcc_tc_gemm(int precision, const double* A, const double* B, int M, int N, int K, float* C) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || (precision != GFCC_PREC_BF16 && precision != GFCC_PREC_TF32))
+    return GFCC_ERR_ARG;
+  gfcc_ctx* ctx = nullptr;
+  try {
+    DBuf<double> a, b;
+    DBuf<float> cdev;
+    a.alloc((size_t)M * K);
+    b.alloc((size_t)N * K);
+    cdev.alloc((size_t)M * N);
+    GFCC_CUDA(cudaMemcpy(a.p, A, sizeof(double) * M * K, cudaMemcpyHostToDevice));
+    GFCC_CUDA(cudaMemcpy(b.p, B, sizeof(double) * N * K, cudaMemcpyHostToDevice));
+    gfcc::tc_selftest(precision, a.p, b.p, M, N, K, cdev.p, nullptr);
+    GFCC_CUDA(cudaMemcpy(C, cdev.p, sizeof(float) * M * N, cudaMemcpyDeviceToHost));
+  } catch (gfcc::Error& e) {
+    fprintf(stderr, "gfcc_tc_gemm: %s\n", e.msg.c_str());
+    return e.code;
+  }
+  (void)ctx;
+  return GFCC_OK;
+}
+
 const char* gfcc_last_error(gfcc_t c) { return c ? c->last_error.c_str() : "null context"; }
 
 void gfcc_free(gfcc_t c) { delete c; }
+
+}  // extern "C"
+
+gfcc_ctx::~gfcc_ctx() { gfcc::free_low_precision(this); }
+
+extern "C" {
 
 }  // extern "C"

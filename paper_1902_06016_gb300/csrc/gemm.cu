@@ -5,6 +5,9 @@
 // memory) keeps the DFMA pipe fed. They serve the one-time H-bar build, the FP64 residual sigma and
 // the FP64 projections of the reduced model.
 #include "gfcc_internal.cuh"
+#include "ozaki.cuh"
+
+#include <algorithm>
 
 namespace gfcc {
 namespace {
@@ -13,12 +16,14 @@ constexpr int BM = 64, BN = 64;
 
 template <typename T> struct Ops;
 template <> struct Ops<double> {
-  __device__ static double zero() { return 0.0; }
+  __host__ __device__ static double zero() { return 0.0; }
+  __host__ __device__ static double one() { return 1.0; }
   __device__ static double fma(double a, double b, double c) { return ::fma(a, b, c); }
   __device__ static double cj(double a, bool) { return a; }
 };
 template <> struct Ops<cplx> {
-  __device__ static cplx zero() { return make_cuDoubleComplex(0.0, 0.0); }
+  __host__ __device__ static cplx zero() { return make_cuDoubleComplex(0.0, 0.0); }
+  __host__ __device__ static cplx one() { return make_cuDoubleComplex(1.0, 0.0); }
   __device__ static cplx fma(cplx a, cplx b, cplx c) {
     return make_cuDoubleComplex(::fma(a.x, b.x, ::fma(-a.y, b.y, c.x)), ::fma(a.x, b.y, ::fma(a.y, b.x, c.y)));
   }
@@ -29,8 +34,8 @@ __device__ inline double scal_mul(double a, double b) { return a * b; }
 __device__ inline cplx scal_mul(cplx a, cplx b) { return cuCmul(a, b); }
 __device__ inline double scal_add(double a, double b) { return a + b; }
 __device__ inline cplx scal_add(cplx a, cplx b) { return cuCadd(a, b); }
-__device__ inline bool is_zero(double a) { return a == 0.0; }
-__device__ inline bool is_zero(cplx a) { return a.x == 0.0 && a.y == 0.0; }
+__host__ __device__ inline bool is_zero(double a) { return a == 0.0; }
+__host__ __device__ inline bool is_zero(cplx a) { return a.x == 0.0 && a.y == 0.0; }
 
 template <typename T>
 struct Args {
@@ -39,6 +44,7 @@ struct Args {
   const T* B; long long sbk, sbn, bsb; bool conjB;
   T* C; long long scm, scn, bsc;
   T alpha, beta;
+  int ksplit = 1, kchunk = 0;   // split-K: blockIdx.z = batch * ksplit + split, partials in C
 };
 
 // 256 threads: thread (tx, ty) in a 16x16 grid owns rows ty + 16*i and columns tx + 16*j.
@@ -50,10 +56,14 @@ __global__ void __launch_bounds__(256) gemm_kernel(Args<T> g) {
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const long long bz = blockIdx.z;
-  const T* A = g.A + bz * g.bsa;
-  const T* B = g.B + bz * g.bsb;
-  T* C = g.C + bz * g.bsc;
+  const long long bz = blockIdx.z / g.ksplit;
+  const int split = blockIdx.z % g.ksplit;
+  const int kbeg = split * g.kchunk;
+  const int kend = g.ksplit > 1 ? min(g.K, kbeg + g.kchunk) : g.K;
+  const T* A = g.A + bz * g.bsa + (long long)kbeg * g.sak;
+  const T* B = g.B + bz * g.bsb + (long long)kbeg * g.sbk;
+  T* C = g.C + bz * g.bsc + (g.ksplit > 1 ? (long long)split * g.M * g.N : 0LL);
+  const int Kloc = max(0, kend - kbeg);
   const bool a_k_fast = (g.sak == 1);
   const bool b_n_fast = (g.sbn == 1);
 
@@ -65,11 +75,11 @@ __global__ void __launch_bounds__(256) gemm_kernel(Args<T> g) {
       int mm, kk;
       if (a_k_fast) { kk = idx % BK; mm = idx / BK; } else { mm = idx % BM; kk = idx / BM; }
       int gm = m0 + mm, gk = k0 + kk;
-      ra[r] = (gm < g.M && gk < g.K) ? Ops<T>::cj(A[gm * g.sam + gk * g.sak], g.conjA) : Ops<T>::zero();
+      ra[r] = (gm < g.M && gk < Kloc) ? Ops<T>::cj(A[gm * g.sam + gk * g.sak], g.conjA) : Ops<T>::zero();
       int nn, kb;
       if (b_n_fast) { nn = idx % BN; kb = idx / BN; } else { kb = idx % BK; nn = idx / BK; }
       int gn = n0 + nn, gkb = k0 + kb;
-      rb[r] = (gn < g.N && gkb < g.K) ? Ops<T>::cj(B[gkb * g.sbk + gn * g.sbn], g.conjB) : Ops<T>::zero();
+      rb[r] = (gn < g.N && gkb < Kloc) ? Ops<T>::cj(B[gkb * g.sbk + gn * g.sbn], g.conjB) : Ops<T>::zero();
     }
   };
   auto store_tiles = [&](int buf) {
@@ -91,7 +101,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(Args<T> g) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = Ops<T>::zero();
 
-  const int nk = (g.K + BK - 1) / BK;
+  const int nk = (Kloc + BK - 1) / BK;
   if (nk > 0) {
     load_tiles(0);
     store_tiles(0);
@@ -132,15 +142,71 @@ __global__ void __launch_bounds__(256) gemm_kernel(Args<T> g) {
   }
 }
 
+// C = alpha * sum_split P[split] + beta * C  (P packed [batch][ksplit][M][N])
 template <typename T>
-void launch(const Args<T>& a, int batch, cudaStream_t s) {
+__global__ void splitk_reduce_kernel(const T* __restrict__ P, int ksplit, int M, int N, int batch, T* C, long long scm,
+                                     long long scn, long long bsc, T alpha, T beta) {
+  const long long per = (long long)M * N;
+  const long long total = per * batch;
+  const bool beta0 = is_zero(beta);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / per, r = t % per;
+    const int m = (int)(r / N), n = (int)(r % N);
+    T sum = Ops<T>::zero();
+    for (int k = 0; k < ksplit; ++k) sum = scal_add(sum, P[(b * ksplit + k) * per + r]);
+    T* cp = C + b * bsc + m * scm + n * scn;
+    T v = scal_mul(alpha, sum);
+    if (!beta0) v = scal_add(v, scal_mul(beta, *cp));
+    *cp = v;
+  }
+}
+
+template <typename T>
+void launch(Args<T> a, int batch, cudaStream_t s) {
   if (a.M <= 0 || a.N <= 0 || batch <= 0) return;
-  GFCC_CHECK(batch <= 65535, GFCC_ERR_ARG, "gemm batch too large");
   dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, batch);
   GFCC_CHECK(grid.y <= 65535, GFCC_ERR_ARG, "gemm M too large");
   constexpr int BK = sizeof(T) == 8 ? 16 : 8;   // 33 KB of static shared memory either way
-  gemm_kernel<T, BK><<<grid, 256, 0, s>>>(a);
+  ProfScope prof(PROF_F64_GEMM, (sizeof(T) == 8 ? 2.0 : 8.0) * (double)a.M * (double)a.N * (double)a.K * batch, s);
+  // too few tiles to fill 152 SMs and a long K: split K, then reduce the partial tiles
+  const long long tiles = (long long)grid.x * grid.y * batch;
+  int ksplit = 1;
+  if (tiles < 2 * 152 && a.K >= 1024) {
+    ksplit = (int)std::min<long long>((2 * 152 + tiles - 1) / tiles, a.K / 256);
+    ksplit = std::max(1, std::min(ksplit, 65535 / std::max(batch, 1)));
+  }
+  GFCC_CHECK((long long)batch * ksplit <= 65535, GFCC_ERR_ARG, "gemm batch too large");
+  if (ksplit == 1) {
+    gemm_kernel<T, BK><<<grid, 256, 0, s>>>(a);
+    GFCC_LAUNCH_CHECK();
+    return;
+  }
+  const int kchunk = ((a.K + ksplit - 1) / ksplit + BK - 1) / BK * BK;
+  ksplit = (a.K + kchunk - 1) / kchunk;
+  const long long per = (long long)a.M * a.N;
+  DBuf<T> part;
+  part.alloc(per * ksplit * batch);
+  Args<T> p = a;
+  p.C = part.p;
+  p.scm = a.N;
+  p.scn = 1;
+  p.bsc = per * ksplit;
+  p.alpha = Ops<T>::one();
+  p.beta = Ops<T>::zero();
+  p.ksplit = ksplit;
+  p.kchunk = kchunk;
+  // partial z = batch * ksplit + split lands at part + (batch * ksplit + split) * per
+  p.bsc = per * ksplit;
+  grid.z = batch * ksplit;
+  gemm_kernel<T, BK><<<grid, 256, 0, s>>>(p);
   GFCC_LAUNCH_CHECK();
+  const long long total = per * batch;
+  const int rgrid = (int)std::min<long long>((total + 255) / 256, 152LL * 32);
+  splitk_reduce_kernel<T><<<rgrid, 256, 0, s>>>(part.p, ksplit, a.M, a.N, batch, a.C, a.scm, a.scn, a.bsc, a.alpha,
+                                                a.beta);
+  GFCC_LAUNCH_CHECK();
+  GFCC_CUDA(cudaStreamSynchronize(s));   // the partial buffer is released on return
 }
 
 }  // namespace
@@ -152,6 +218,13 @@ void dgemm(const GemmDesc& d, cudaStream_t s) {
 }
 
 void zgemm(const ZGemmDesc& d, cudaStream_t s) {
+  // large complex products (the subspace projections of the reduced model) go to the exact-slice
+  // tensor-core GEMM with 7 slices (48 bits per row)
+  if (d.batch == 1 && (double)d.M * (double)d.N * (double)d.K >= oz_min_macs() && d.M >= 16 && d.N >= 1 &&
+      (double)d.K >= 256) {
+    zgemm_oz(d, 7, s);
+    return;
+  }
   Args<cplx> a{d.M, d.N, d.K, d.A, d.sam, d.sak, d.bsa, d.conjA, d.B, d.sbk, d.sbn, d.bsb, d.conjB,
                d.C, d.scm, d.scn, d.bsc, d.alpha, d.beta};
   launch(a, d.batch, s);

@@ -32,7 +32,35 @@ struct Error {
     if (!(cond)) throw ::gfcc::Error{(code), (msg)};                                       \
   } while (0)
 
-#define GFCC_LAUNCH_CHECK() GFCC_CUDA(cudaGetLastError())
+// every kernel launch is followed by this check; it also counts the launches of the library
+#define GFCC_LAUNCH_CHECK()                     \
+  do {                                          \
+    ::gfcc::count_launch();                     \
+    GFCC_CUDA(cudaGetLastError());              \
+  } while (0)
+
+// launch counting and optional per-kernel-class timing (profile.cu)
+void count_launch();
+enum ProfClass {
+  PROF_TC_GEMM = 0,      // tcgen05 GEMM, tf32/bf16-rounded operands
+  PROF_F64_GEMM = 1,     // FP64 SIMT GEMM
+  PROF_TC_SLICE = 2,     // tcgen05 GEMM on exact bf16 slices
+  PROF_SIGMA_LP = 3,     // whole low-precision sigma (operand prep, GEMMs, combine)
+  PROF_SIGMA_EX = 4,     // whole FP64-accurate sigma (exact slices or FP64 SIMT)
+  PROF_KRYLOV = 5,       // Arnoldi: preconditioner, Gram-Schmidt, norms, Givens, corrections
+  PROF_MOR_ORTHO = 6,    // subspace orthonormalisation and projections
+  PROF_MOR_EVAL = 7,     // Hessenberg reduction and per-frequency reduced solves
+  PROF_INIT = 8,         // H-bar build, b and c vectors
+  PROF_NCLASS = 9
+};
+struct ProfScope {   // records CUDA events around one launch on stream s when profiling is on
+  int cls;
+  double flops;
+  cudaStream_t s;
+  void* rec = nullptr;
+  ProfScope(int cls, double flops, cudaStream_t s);
+  ~ProfScope();
+};
 
 // ---------------------------------------------------------------------------------------------
 // device buffers owned by the context
@@ -88,24 +116,17 @@ struct Operator {
   DBuf<double> WrT, WooT, A12T, A21T, VtT, T2pT;
 };
 
-// low-precision copies of the dominant operator (mixed-precision path)
+// low-precision (tensor-core) copies of the sigma operands; the state lives in sigma_tc.cu
 struct LowPrecision {
-  int kind = 0;          // GFCC_PREC_*
-  int K_pad = 0;         // padded K (elements) of the ring operand
-  DBuf<uint16_t> Wr_bf16;   // [(a,i)][K_pad]
-  DBuf<float> Wr_f32;       // [(a,i)][K_pad] (tf32 operand)
-  DBuf<uint16_t> Wr_lo_bf16;  // second bf16 term for split precision
-  DBuf<uint16_t> Woo_bf16;
-  DBuf<float> Woo_f32;
+  int kind = 0;          // GFCC_PREC_* of the built operands (0: none)
+  void* impl = nullptr;
+  void* emu = nullptr;   // exact-slice (FP64-accurate) operands
 };
 
 struct Workspace {
   DBuf<double> ut;      // unpacked 2h1p  [(m,e)][(j,c)] complex -> 2*ov*o*nb doubles
   DBuf<double> ct;      // ring product   [(a,i)][(j,c)] complex
   DBuf<double> xe;      // three-body X_e [e][c] complex
-  DBuf<uint16_t> ut16;  // low-precision ring operand
-  DBuf<float> ct32;     // low-precision ring product
-  DBuf<float> ut32;
   size_t nb_cap = 0;
 };
 
@@ -160,6 +181,7 @@ struct gfcc_ctx {
   gfcc::DBuf<double> bvec;   // [n][D]  b_p rows
   gfcc::DBuf<double> cvec;   // [n][D]  c_q rows
   gfcc::DBuf<double> t1, t2; // kept for derivative work
+  ~gfcc_ctx();
 };
 
 namespace gfcc {
@@ -212,9 +234,18 @@ void sigma_batch(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, int ldb, const cpl
 void ensure_workspace(gfcc_ctx* c, int nb);
 void build_transpose_operator(gfcc_ctx* c);
 
-// ---- sigma_tc.cu (tcgen05 mixed-precision ring GEMM) -------------------------------------------
+// ---- sigma_tc.cu (tcgen05 low-precision sigma for the inner solves) ---------------------------
 void build_low_precision(gfcc_ctx* c, int kind);
-void ring_lowprec(gfcc_ctx* c, const double* ut_cplx, double* ct_cplx, int nb, cudaStream_t s);
+void free_low_precision(gfcc_ctx* c);
+void sigma_lowprec(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shift, cudaStream_t s);
+// the same with FP32 complex vectors (the FP32 Krylov basis of the mixed-precision solver)
+void sigma_lowprec_f32(gfcc_ctx* c, const cuFloatComplex* X, cuFloatComplex* Y, int nb, const cplx* shift,
+                       cudaStream_t s);
+int low_precision_error(gfcc_ctx* c);   // 1 if a tensor-core pipeline wait timed out
+int emulated_error(gfcc_ctx* c);
+void build_emulated(gfcc_ctx* c);
+void sigma_emulated(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shift, cudaStream_t s);
+void tc_selftest(int kind, const double* A, const double* B, int M, int N, int K, float* C, cudaStream_t s);
 
 // ---- krylov.cu ---------------------------------------------------------------------------------
 struct SolveStatus {

@@ -261,13 +261,14 @@ void build_operator(gfcc_ctx* c, const HostInputs& in) {
   const int o = c->o, v = c->v, P = c->P, n = c->n;
   const long long D = c->D;
   cudaStream_t s = c->stream;
+  ProfScope prof(PROF_INIT, 0.0, s);
 
   // ---- upload inputs -------------------------------------------------------------------------
   auto up = [&](std::vector<int> dims, const double* h) {
     std::string lab(dims.size(), 'x');
     for (size_t k = 0; k < dims.size(); ++k) lab[k] = (char)('A' + k);
     auto t = std::make_unique<Tensor>(lab, dims);
-    GFCC_CUDA(cudaMemcpyAsync(t->p(), h, t->size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    GFCC_CUDA(cudaMemcpyAsync(t->p(), h, t->size() * sizeof(double), cudaMemcpyDefault, s));   // host or device
     return t;
   };
   auto eps = up({n}, in.eps);

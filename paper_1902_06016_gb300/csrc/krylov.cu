@@ -26,40 +26,56 @@ __device__ __forceinline__ cplx cconjmul(cplx a, cplx b) {  // conj(a) * b
   return make_cuDoubleComplex(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 
-// partial[chunk][i][c] = sum_{nu in chunk} conj(V_i[nu][c]) W[nu][c], i < nv (V_i = V + i*stride)
+// real component type of a complex vector element
+template <typename VT> struct RealOf;
+template <> struct RealOf<cplx> { using type = double; };
+template <> struct RealOf<cuFloatComplex> { using type = float; };
+template <typename VT> __device__ __forceinline__ VT mk(double re, double im);
+template <> __device__ __forceinline__ cplx mk<cplx>(double re, double im) { return make_cuDoubleComplex(re, im); }
+template <> __device__ __forceinline__ cuFloatComplex mk<cuFloatComplex>(double re, double im) {
+  return make_cuFloatComplex((float)re, (float)im);
+}
+
+// partial[chunk][i][c] = sum_{nu in chunk} conj(V_i[nu][c]) W[nu][c], i < nv (V_i = V + i*stride);
+// per-thread sums in the vector's precision, partials written in FP64
 constexpr int MD_TX = 32, MD_TY = 8, MD_MAXV = 32;
-__global__ void multidot_kernel(const cplx* __restrict__ V, long long vstride, int nv,
-                                const cplx* __restrict__ W, long long D, int nb, long long rows_per_chunk,
-                                cplx* __restrict__ partial) {
+template <typename VT>
+__global__ void multidot_kernel(const VT* __restrict__ V, long long vstride, int nv, const VT* __restrict__ W,
+                                long long D, int nb, long long rows_per_chunk, cplx* __restrict__ partial) {
+  using R = typename RealOf<VT>::type;
   __shared__ cplx red[MD_TY][MD_TX];
   const int c = blockIdx.x * MD_TX + threadIdx.x;
   const long long r0 = blockIdx.y * rows_per_chunk;
   const long long r1 = min(D, r0 + rows_per_chunk);
-  cplx acc[MD_MAXV];
+  R ax[MD_MAXV], ay[MD_MAXV];
 #pragma unroll
-  for (int i = 0; i < MD_MAXV; ++i) acc[i] = make_cuDoubleComplex(0.0, 0.0);
+  for (int i = 0; i < MD_MAXV; ++i) { ax[i] = R(0); ay[i] = R(0); }
   if (c < nb) {
     for (long long nu = r0 + threadIdx.y; nu < r1; nu += MD_TY) {
-      cplx w = W[nu * nb + c];
+      const VT w = W[nu * nb + c];
 #pragma unroll
       for (int i = 0; i < MD_MAXV; ++i) {
         if (i < nv) {
-          cplx vv = V[i * vstride + nu * nb + c];
-          acc[i].x += vv.x * w.x + vv.y * w.y;
-          acc[i].y += vv.x * w.y - vv.y * w.x;
+          const VT vv = V[i * vstride + nu * nb + c];
+          ax[i] += vv.x * w.x + vv.y * w.y;
+          ay[i] += vv.x * w.y - vv.y * w.x;
         }
       }
     }
   }
-  for (int i = 0; i < nv; ++i) {
-    red[threadIdx.y][threadIdx.x] = acc[i];
-    __syncthreads();
-    if (threadIdx.y == 0 && c < nb) {
-      cplx s = red[0][threadIdx.x];
-      for (int k = 1; k < MD_TY; ++k) { s.x += red[k][threadIdx.x].x; s.y += red[k][threadIdx.x].y; }
-      partial[((long long)blockIdx.y * nv + i) * nb + c] = s;
+  // static indices only, so that the accumulators stay in registers
+#pragma unroll
+  for (int i = 0; i < MD_MAXV; ++i) {
+    if (i < nv) {
+      red[threadIdx.y][threadIdx.x] = make_cuDoubleComplex((double)ax[i], (double)ay[i]);
+      __syncthreads();
+      if (threadIdx.y == 0 && c < nb) {
+        cplx s = red[0][threadIdx.x];
+        for (int k = 1; k < MD_TY; ++k) { s.x += red[k][threadIdx.x].x; s.y += red[k][threadIdx.x].y; }
+        partial[((long long)blockIdx.y * nv + i) * nb + c] = s;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -78,23 +94,36 @@ __global__ void reduce_partial_kernel(const cplx* __restrict__ partial, int nchu
   if (accumulate) { dst->x += s.x; dst->y += s.y; } else { *dst = s; }
 }
 
-// W[nu][c] -= sum_{i<nv} V_i[nu][c] h[c*hld + hoff + i]   (or +=, sign)
-__global__ void update_kernel(const cplx* __restrict__ V, long long vstride, int nv, cplx* __restrict__ W,
+// W[nu][c] += sign * sum_{i<nv} V_i[nu][c] h[c*hld + hoff + i]
+template <typename VT>
+__global__ void update_kernel(const VT* __restrict__ V, long long vstride, int nv, VT* __restrict__ W,
                               long long D, int nb, const cplx* __restrict__ h, int hld, int hoff, double sign) {
+  using R = typename RealOf<VT>::type;
   long long total = D * nb;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     int c = (int)(t % nb);
-    cplx s = make_cuDoubleComplex(0.0, 0.0);
     const cplx* hc = h + (long long)c * hld + hoff;
-    for (int i = 0; i < nv; ++i) {
-      cplx vv = V[i * vstride + t];
-      cplx hh = hc[i];
-      s.x += vv.x * hh.x - vv.y * hh.y;
-      s.y += vv.x * hh.y + vv.y * hh.x;
+    // four independent partial sums keep several loads in flight
+    R sx[4] = {R(0), R(0), R(0), R(0)}, sy[4] = {R(0), R(0), R(0), R(0)};
+    int i = 0;
+    for (; i + 4 <= nv; i += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const VT vv = V[(long long)(i + u) * vstride + t];
+        const R hx = (R)hc[i + u].x, hy = (R)hc[i + u].y;
+        sx[u] += vv.x * hx - vv.y * hy;
+        sy[u] += vv.x * hy + vv.y * hx;
+      }
     }
-    W[t].x += sign * s.x;
-    W[t].y += sign * s.y;
+    for (; i < nv; ++i) {
+      const VT vv = V[(long long)i * vstride + t];
+      const R hx = (R)hc[i].x, hy = (R)hc[i].y;
+      sx[0] += vv.x * hx - vv.y * hy;
+      sy[0] += vv.x * hy + vv.y * hx;
+    }
+    W[t].x += (R)sign * ((sx[0] + sx[1]) + (sx[2] + sx[3]));
+    W[t].y += (R)sign * ((sy[0] + sy[1]) + (sy[2] + sy[3]));
   }
 }
 
@@ -116,20 +145,26 @@ __global__ void finalize_norm_kernel(const cplx* __restrict__ dots, int nb, doub
 }
 
 // Z[nu][c] = V[nu][c] / (shift_c + mdiag[nu])
-__global__ void precond_kernel(const cplx* __restrict__ V, cplx* __restrict__ Z, const double* __restrict__ md,
+template <typename VT>
+__global__ void precond_kernel(const VT* __restrict__ V, VT* __restrict__ Z, const double* __restrict__ md,
                                const cplx* __restrict__ shift, long long D, int nb) {
+  using R = typename RealOf<VT>::type;
   long long total = D * nb;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     int c = (int)(t % nb);
     long long nu = t / nb;
-    cplx d = make_cuDoubleComplex(shift[c].x + md[nu], shift[c].y);
-    Z[t] = cuCdiv(V[t], d);
+    const R dr = (R)(shift[c].x + md[nu]), di = (R)shift[c].y;
+    const R inv = R(1) / (dr * dr + di * di);
+    const VT v = V[t];
+    Z[t].x = (v.x * dr + v.y * di) * inv;
+    Z[t].y = (v.y * dr - v.x * di) * inv;
   }
 }
 
-// V[nu][c] = W[nu][c] * scale[c]  (scale = 1/norm, 0 for broken-down columns)
-__global__ void scale_cols_kernel(const cplx* __restrict__ W, cplx* __restrict__ V, const double* __restrict__ nrm,
+// V[nu][c] = W[nu][c] * scale[c]  (scale = 1/norm, 0 for broken-down columns), with conversion
+template <typename VI, typename VO>
+__global__ void scale_cols_kernel(const VI* __restrict__ W, VO* __restrict__ V, const double* __restrict__ nrm,
                                   long long D, int nb) {
   long long total = D * nb;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -137,7 +172,7 @@ __global__ void scale_cols_kernel(const cplx* __restrict__ W, cplx* __restrict__
     int c = (int)(t % nb);
     double n = nrm[c];
     double s = (n > 0.0 && isfinite(n)) ? 1.0 / n : 0.0;
-    V[t] = make_cuDoubleComplex(W[t].x * s, W[t].y * s);
+    V[t] = mk<VO>((double)W[t].x * s, (double)W[t].y * s);
   }
 }
 
@@ -154,7 +189,7 @@ __global__ void residual_kernel(const cplx* __restrict__ B, const cplx* __restri
 __global__ void givens_kernel(cplx* __restrict__ H, cplx* __restrict__ cs, cplx* __restrict__ sn,
                               cplx* __restrict__ g, const double* __restrict__ hnext,
                               const double* __restrict__ bnorm, int* __restrict__ kc, int* __restrict__ live,
-                              int nb, int k, int j, double tol, int* __restrict__ n_live) {
+                              int nb, int k, int j, const double* __restrict__ thr, int* __restrict__ n_live) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nb) return;
   if (!live[c]) return;
@@ -190,7 +225,7 @@ __global__ void givens_kernel(cplx* __restrict__ H, cplx* __restrict__ cs, cplx*
   gc[j] = cuCmul(cj, gj);
   kc[c] = j + 1;
   double est = cuCabs(gc[j + 1]) / bnorm[c];
-  if (!(est > 0.5 * tol) || den == 0.0 || !isfinite(est)) {
+  if (!(est > thr[c]) || den == 0.0 || !isfinite(est)) {
     live[c] = 0;   // converged (or broken down) within this cycle: stop extending its basis use
   } else {
     atomicAdd(n_live, 1);
@@ -214,8 +249,9 @@ __global__ void backsolve_kernel(const cplx* __restrict__ H, cplx* __restrict__ 
   for (int i = n; i <= k; ++i) gc[i] = make_cuDoubleComplex(0.0, 0.0);
 }
 
-// X[nu][c] += P_c[nu] * sum_i V_i[nu][c] y_i[c]
-__global__ void correct_kernel(const cplx* __restrict__ V, long long vstride, int nv, const cplx* __restrict__ y,
+// X[nu][c] += P_c[nu] * sum_i V_i[nu][c] y_i[c]   (FP64 accumulation)
+template <typename VT>
+__global__ void correct_kernel(const VT* __restrict__ V, long long vstride, int nv, const cplx* __restrict__ y,
                                int yld, cplx* __restrict__ X, const double* __restrict__ md,
                                const cplx* __restrict__ shift, long long D, int nb) {
   long long total = D * nb;
@@ -227,7 +263,10 @@ __global__ void correct_kernel(const cplx* __restrict__ V, long long vstride, in
     const cplx* yc = y + (long long)c * yld;
     for (int i = 0; i < nv; ++i) {
       cplx yi = yc[i];
-      if (yi.x != 0.0 || yi.y != 0.0) s = cuCadd(s, cuCmul(V[i * vstride + t], yi));
+      if (yi.x != 0.0 || yi.y != 0.0) {
+        const VT vv = V[i * vstride + t];
+        s = cuCadd(s, cuCmul(make_cuDoubleComplex((double)vv.x, (double)vv.y), yi));
+      }
     }
     cplx d = make_cuDoubleComplex(shift[c].x + md[nu], shift[c].y);
     cplx z = cuCdiv(s, d);
@@ -269,14 +308,15 @@ __global__ void nonfinite_cplx_kernel(const cplx* x, long long n, int* flag) {
 
 // ------------------------------------------------------------------------------------------------
 // column norms of a batch-minor block: out[c] = ||W_c||  (device array)
-static void col_norms(const cplx* W, long long D, int nb, double* out, DBuf<cplx>& partial,
-                      DBuf<cplx>& tmp, cudaStream_t s) {
+template <typename VT>
+static void col_norms(const VT* W, long long D, int nb, double* out, DBuf<cplx>& partial, DBuf<cplx>& tmp,
+                      cudaStream_t s) {
   const long long rows = std::max<long long>(256, (D + 511) / 512);
   const int nchunk = (int)((D + rows - 1) / rows);
   partial.alloc((long long)nchunk * nb);
   tmp.alloc(nb);
   dim3 grid((nb + MD_TX - 1) / MD_TX, nchunk);
-  multidot_kernel<<<grid, dim3(MD_TX, MD_TY), 0, s>>>(W, 0, 1, W, D, nb, rows, partial.p);
+  multidot_kernel<VT><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(W, 0, 1, W, D, nb, rows, partial.p);
   GFCC_LAUNCH_CHECK();
   reduce_partial_kernel<<<(nb + 255) / 256, 256, 0, s>>>(partial.p, nchunk, 1, nb, tmp.p, 1, 0, 0);
   GFCC_LAUNCH_CHECK();
@@ -285,16 +325,16 @@ static void col_norms(const cplx* W, long long D, int nb, double* out, DBuf<cplx
 }
 
 // h[c][hoff + i] (+)= V_i^H W_c for i < nv, with chunked partial sums
-static void multidot(const cplx* V, long long vstride, int nv, const cplx* W, long long D, int nb,
-                     cplx* h, int hld, int hoff, bool accumulate, DBuf<cplx>& partial, cudaStream_t s) {
+template <typename VT>
+static void multidot(const VT* V, long long vstride, int nv, const VT* W, long long D, int nb, cplx* h, int hld,
+                     int hoff, bool accumulate, DBuf<cplx>& partial, cudaStream_t s) {
   for (int i0 = 0; i0 < nv; i0 += MD_MAXV) {
     int n = std::min(MD_MAXV, nv - i0);
     const long long rows = std::max<long long>(256, (D + 255) / 256);
     const int nchunk = (int)((D + rows - 1) / rows);
     partial.alloc((long long)nchunk * n * nb);
     dim3 grid((nb + MD_TX - 1) / MD_TX, nchunk);
-    multidot_kernel<<<grid, dim3(MD_TX, MD_TY), 0, s>>>(V + i0 * vstride, vstride, n, W, D, nb, rows,
-                                                       partial.p);
+    multidot_kernel<VT><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(V + i0 * vstride, vstride, n, W, D, nb, rows, partial.p);
     GFCC_LAUNCH_CHECK();
     reduce_partial_kernel<<<(n * nb + 255) / 256, 256, 0, s>>>(partial.p, nchunk, n, nb, h, hld, hoff + i0,
                                                                accumulate ? 1 : 0);
@@ -302,33 +342,54 @@ static void multidot(const cplx* V, long long vstride, int nv, const cplx* W, lo
   }
 }
 
-void gmres_batched(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, const cplx* shifts_dev, int nb0,
-                   SolveStatus& st, bool transpose) {
+// inner action W = (shift + M) Z in the basis precision
+static void inner_sigma(gfcc_ctx* c, const cplx* Z, cplx* W, int nb, const cplx* sh, int prec, bool tr, cudaStream_t s) {
+  sigma_batch(c, Z, W, nb, nb, sh, prec, tr, s);
+}
+static void inner_sigma(gfcc_ctx* c, const cuFloatComplex* Z, cuFloatComplex* W, int nb, const cplx* sh, int prec,
+                        bool tr, cudaStream_t s) {
+  (void)prec;
+  (void)tr;
+  sigma_lowprec_f32(c, Z, W, nb, sh, s);
+}
+
+// Restarted GMRES with iterative refinement; VT is the precision of the Krylov basis (FP64 for the
+// plain FP64 path, FP32 when the inner sigma runs on the tensor cores: the residual of every cycle is
+// recomputed with the FP64-accurate sigma and the solution is accumulated in FP64, so the basis
+// precision only bounds the progress of one cycle, not the final accuracy).
+template <typename VT>
+static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, const cplx* shifts_dev, int nb0,
+                       SolveStatus& st, bool transpose) {
   cudaStream_t s = c->stream;
   const long long D = c->D;
   const int k = std::max(1, std::min(c->opts.restart, 256));
   const double tol = c->opts.tol;
   const int inner_prec = c->opts.precision;
+  int resid_prec = c->opts.residual_precision;
+  if (resid_prec < 0) resid_prec = inner_prec == GFCC_PREC_FP64 ? GFCC_PREC_FP64 : GFCC_PREC_FP64_TC;
+  // a cycle with a low-precision inner operator cannot gain more than about its rounding level: stop
+  // it once the inner estimate has dropped by this factor
+  const double inner_rtol = (inner_prec == GFCC_PREC_FP64) ? 0.0 : 1e-4;
   st.relres.assign(nb0, 0.0);
   st.iters.assign(nb0, 0);
   st.converged.assign(nb0, 0);
   if (nb0 == 0) return;
 
-  // shifts on host (for compaction bookkeeping)
   std::vector<cplx> hshift(nb0);
   GFCC_CUDA(cudaMemcpyAsync(hshift.data(), shifts_dev, sizeof(cplx) * nb0, cudaMemcpyDeviceToHost, s));
 
-  // working copies
-  DBuf<cplx> Bw, Xw, Rw, Yw, V, Zw, H, cs, sn, g, partial, tmpc, shw, hb;
-  DBuf<double> nrm, bnorm;
+  DBuf<cplx> Bw, Xw, Rw, Yw, Ztmp, H, cs, sn, g, partial, tmpc, shw, hb;
+  DBuf<VT> V, Zw, Ww;
+  DBuf<double> nrm, bnorm, thr;
   DBuf<int> kc, live, nlive, cols, flag;
-  Bw.alloc(D * nb0); Xw.alloc(D * nb0); Rw.alloc(D * nb0); Yw.alloc(D * nb0); Zw.alloc(D * nb0);
+  Bw.alloc(D * nb0); Xw.alloc(D * nb0); Rw.alloc(D * nb0); Yw.alloc(D * nb0); Ztmp.alloc(D * nb0);
+  Zw.alloc(D * nb0); Ww.alloc(D * nb0);
   V.alloc((long long)(k + 1) * D * nb0);
   V.zero(s);
   H.alloc((long long)nb0 * (k + 1) * k);
   cs.alloc((long long)nb0 * k); sn.alloc((long long)nb0 * k); g.alloc((long long)nb0 * (k + 1));
   hb.alloc((long long)nb0 * (k + 1));
-  nrm.alloc(nb0); bnorm.alloc(nb0); kc.alloc(nb0); live.alloc(nb0); nlive.alloc(1); cols.alloc(nb0);
+  nrm.alloc(nb0); bnorm.alloc(nb0); thr.alloc(nb0); kc.alloc(nb0); live.alloc(nb0); nlive.alloc(1); cols.alloc(nb0);
   shw.alloc(nb0);
   flag.alloc(1);
   GFCC_CUDA(cudaMemcpyAsync(Bw.p, Bin, sizeof(cplx) * D * nb0, cudaMemcpyDeviceToDevice, s));
@@ -337,6 +398,7 @@ void gmres_batched(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, const c
   {  // non-finite right-hand sides or shifts
     flag.zero(s);
     nonfinite_cplx_kernel<<<grid_for(D * nb0), 256, 0, s>>>(Bw.p, D * nb0, flag.p);
+    GFCC_LAUNCH_CHECK();
     nonfinite_cplx_kernel<<<1, 256, 0, s>>>(shw.p, nb0, flag.p);
     GFCC_LAUNCH_CHECK();
     int hf = 0;
@@ -344,7 +406,7 @@ void gmres_batched(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, const c
     GFCC_CUDA(cudaStreamSynchronize(s));
     GFCC_CHECK(hf == 0, GFCC_ERR_NONFINITE, "solve: non-finite right-hand side or frequency");
   }
-  col_norms(Bw.p, D, nb0, bnorm.p, partial, tmpc, s);
+  col_norms<cplx>(Bw.p, D, nb0, bnorm.p, partial, tmpc, s);
   std::vector<double> hbn(nb0);
   GFCC_CUDA(cudaMemcpyAsync(hbn.data(), bnorm.p, sizeof(double) * nb0, cudaMemcpyDeviceToHost, s));
   GFCC_CUDA(cudaStreamSynchronize(s));
@@ -356,14 +418,16 @@ void gmres_batched(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, const c
   const int max_cycles = std::max(1, c->opts.max_restarts);
 
   for (int cycle = 0; cycle <= max_cycles && nb > 0; ++cycle) {
-    // FP64 residual R = B - (shift X + M X)
-    sigma_batch(c, Xw.p, Yw.p, nb, nb, shw.p, GFCC_PREC_FP64, transpose, s);
+    // FP64-accurate residual R = B - (shift X + M X)
+    sigma_batch(c, Xw.p, Yw.p, nb, nb, shw.p, resid_prec, transpose, s);
     residual_kernel<<<grid_for(D * nb), 256, 0, s>>>(Bw.p, Yw.p, Rw.p, D * nb);
     GFCC_LAUNCH_CHECK();
-    col_norms(Rw.p, D, nb, nrm.p, partial, tmpc, s);
+    col_norms<cplx>(Rw.p, D, nb, nrm.p, partial, tmpc, s);
     GFCC_CUDA(cudaMemcpyAsync(hres.data(), nrm.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
     GFCC_CUDA(cudaStreamSynchronize(s));
     c->stats.restarts++;
+    if ((inner_prec != GFCC_PREC_FP64 || resid_prec != GFCC_PREC_FP64) && low_precision_error(c))
+      throw Error{GFCC_ERR_CUDA, "solve: a tensor-core pipeline wait timed out"};
 
     // classify columns
     std::vector<int> done, keep;
@@ -387,18 +451,20 @@ void gmres_batched(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, const c
       dsrc.alloc(hd.size()); ddst.alloc(ho.size());
       GFCC_CUDA(cudaMemcpyAsync(dsrc.p, hd.data(), sizeof(int) * hd.size(), cudaMemcpyHostToDevice, s));
       GFCC_CUDA(cudaMemcpyAsync(ddst.p, ho.data(), sizeof(int) * ho.size(), cudaMemcpyHostToDevice, s));
-      // gather done columns into Zw (scratch) then scatter to the outputs
-      gather_cols_kernel<<<grid_for(D * hd.size()), 256, 0, s>>>(Xw.p, nb, dsrc.p, (int)hd.size(), Zw.p,
+      gather_cols_kernel<<<grid_for(D * hd.size()), 256, 0, s>>>(Xw.p, nb, dsrc.p, (int)hd.size(), Ztmp.p,
                                                                   (int)hd.size(), D);
-      scatter_cols_kernel<<<grid_for(D * hd.size()), 256, 0, s>>>(Zw.p, (int)hd.size(), ddst.p, (int)hd.size(),
-                                                                   Xout, nb0, D);
-      if (Rout) {
-        gather_cols_kernel<<<grid_for(D * hd.size()), 256, 0, s>>>(Rw.p, nb, dsrc.p, (int)hd.size(), Zw.p,
-                                                                    (int)hd.size(), D);
-        scatter_cols_kernel<<<grid_for(D * hd.size()), 256, 0, s>>>(Zw.p, (int)hd.size(), ddst.p,
-                                                                     (int)hd.size(), Rout, nb0, D);
-      }
       GFCC_LAUNCH_CHECK();
+      scatter_cols_kernel<<<grid_for(D * hd.size()), 256, 0, s>>>(Ztmp.p, (int)hd.size(), ddst.p, (int)hd.size(),
+                                                                   Xout, nb0, D);
+      GFCC_LAUNCH_CHECK();
+      if (Rout) {
+        gather_cols_kernel<<<grid_for(D * hd.size()), 256, 0, s>>>(Rw.p, nb, dsrc.p, (int)hd.size(), Ztmp.p,
+                                                                    (int)hd.size(), D);
+        GFCC_LAUNCH_CHECK();
+        scatter_cols_kernel<<<grid_for(D * hd.size()), 256, 0, s>>>(Ztmp.p, (int)hd.size(), ddst.p,
+                                                                     (int)hd.size(), Rout, nb0, D);
+        GFCC_LAUNCH_CHECK();
+      }
       GFCC_CUDA(cudaStreamSynchronize(s));
     }
     if (keep.empty()) { nb = 0; break; }
@@ -406,36 +472,37 @@ void gmres_batched(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, const c
       int nk = (int)keep.size();
       GFCC_CUDA(cudaMemcpyAsync(cols.p, keep.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, s));
       for (DBuf<cplx>* b : {&Bw, &Xw, &Rw}) {
-        gather_cols_kernel<<<grid_for(D * nk), 256, 0, s>>>(b->p, nb, cols.p, nk, Zw.p, nk, D);
+        gather_cols_kernel<<<grid_for(D * nk), 256, 0, s>>>(b->p, nb, cols.p, nk, Ztmp.p, nk, D);
         GFCC_LAUNCH_CHECK();
-        GFCC_CUDA(cudaMemcpyAsync(b->p, Zw.p, sizeof(cplx) * D * nk, cudaMemcpyDeviceToDevice, s));
+        GFCC_CUDA(cudaMemcpyAsync(b->p, Ztmp.p, sizeof(cplx) * D * nk, cudaMemcpyDeviceToDevice, s));
       }
       std::vector<cplx> nsh(nk);
       std::vector<int> nmap(nk);
       for (int q = 0; q < nk; ++q) { nsh[q] = hshift[map[keep[q]]]; nmap[q] = map[keep[q]]; }
       GFCC_CUDA(cudaMemcpyAsync(shw.p, nsh.data(), sizeof(cplx) * nk, cudaMemcpyHostToDevice, s));
-      std::vector<double> nbn(nk), nres(nk);
+      std::vector<double> nres(nk);
       for (int q = 0; q < nk; ++q) nres[q] = hres[keep[q]];
       GFCC_CUDA(cudaMemcpyAsync(nrm.p, nres.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, s));
+      hres = nres;
       map = nmap;
       nb = nk;
       GFCC_CUDA(cudaStreamSynchronize(s));
     }
-    // bnorm of the working set (for the in-cycle estimate, relative to ||b||)
-    {
-      std::vector<double> wb(nb);
-      for (int q = 0; q < nb; ++q) wb[q] = hbn[map[q]];
+    {  // ||b|| of the working set and the per-column stopping level of this cycle
+      std::vector<double> wb(nb), th(nb);
+      for (int q = 0; q < nb; ++q) {
+        wb[q] = hbn[map[q]];
+        th[q] = std::max(0.5 * tol, inner_rtol * hres[q] / wb[q]);
+      }
       GFCC_CUDA(cudaMemcpyAsync(bnorm.p, wb.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s));
+      GFCC_CUDA(cudaMemcpyAsync(thr.p, th.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s));
     }
     // GMRES(k) on the correction: V0 = R / ||R||, g = (||R||, 0, ...)
-    scale_cols_kernel<<<grid_for(D * nb), 256, 0, s>>>(Rw.p, V.p, nrm.p, D, nb);
+    scale_cols_kernel<cplx, VT><<<grid_for(D * nb), 256, 0, s>>>(Rw.p, V.p, nrm.p, D, nb);
     GFCC_LAUNCH_CHECK();
     {
       std::vector<cplx> g0((size_t)nb * (k + 1), make_cuDoubleComplex(0.0, 0.0));
-      std::vector<double> rn(nb);
-      GFCC_CUDA(cudaMemcpyAsync(rn.data(), nrm.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
-      GFCC_CUDA(cudaStreamSynchronize(s));
-      for (int q = 0; q < nb; ++q) g0[(size_t)q * (k + 1)] = make_cuDoubleComplex(rn[q], 0.0);
+      for (int q = 0; q < nb; ++q) g0[(size_t)q * (k + 1)] = make_cuDoubleComplex(hres[q], 0.0);
       GFCC_CUDA(cudaMemcpyAsync(g.p, g0.data(), sizeof(cplx) * g0.size(), cudaMemcpyHostToDevice, s));
       std::vector<int> ones(nb, 1);
       GFCC_CUDA(cudaMemcpyAsync(live.p, ones.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s));
@@ -444,26 +511,30 @@ void gmres_batched(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, const c
     }
     const long long vstride = D * nb;
     for (int j = 0; j < k; ++j) {
-      cplx* Vj = V.p + j * vstride;
-      cplx* Vn = V.p + (j + 1) * vstride;
-      precond_kernel<<<grid_for(D * nb), 256, 0, s>>>(Vj, Zw.p, c->op.mdiag.p, shw.p, D, nb);
-      GFCC_LAUNCH_CHECK();
-      sigma_batch(c, Zw.p, Yw.p, nb, nb, shw.p, inner_prec, transpose, s);
+      VT* Vj = V.p + j * vstride;
+      VT* Vn = V.p + (j + 1) * vstride;
+      {
+        ProfScope pk(PROF_KRYLOV, 0.0, s);
+        precond_kernel<VT><<<grid_for(D * nb), 256, 0, s>>>(Vj, Zw.p, c->op.mdiag.p, shw.p, D, nb);
+        GFCC_LAUNCH_CHECK();
+      }
+      inner_sigma(c, Zw.p, Ww.p, nb, shw.p, inner_prec, transpose, s);
+      ProfScope pk2(PROF_KRYLOV, 0.0, s);
       // CGS with one re-orthogonalisation: h = V^H w, w -= V h, twice; H[:, j] = h1 + h2
       for (int pass = 0; pass < 2; ++pass) {
-        multidot(V.p, vstride, j + 1, Yw.p, D, nb, hb.p, k + 1, 0, false, partial, s);
-        update_kernel<<<grid_for(D * nb), 256, 0, s>>>(V.p, vstride, j + 1, Yw.p, D, nb, hb.p, k + 1, 0, -1.0);
+        multidot<VT>(V.p, vstride, j + 1, Ww.p, D, nb, hb.p, k + 1, 0, false, partial, s);
+        update_kernel<VT><<<grid_for(D * nb), 256, 0, s>>>(V.p, vstride, j + 1, Ww.p, D, nb, hb.p, k + 1, 0, -1.0);
         GFCC_LAUNCH_CHECK();
         add_h_kernel<<<(nb * (j + 1) + 255) / 256, 256, 0, s>>>(hb.p, k + 1, H.p + (long long)j * (k + 1),
                                                                 (k + 1) * k, j + 1, nb, pass == 0 ? 0 : 1);
         GFCC_LAUNCH_CHECK();
       }
-      col_norms(Yw.p, D, nb, nrm.p, partial, tmpc, s);
-      scale_cols_kernel<<<grid_for(D * nb), 256, 0, s>>>(Yw.p, Vn, nrm.p, D, nb);
+      col_norms<VT>(Ww.p, D, nb, nrm.p, partial, tmpc, s);
+      scale_cols_kernel<VT, VT><<<grid_for(D * nb), 256, 0, s>>>(Ww.p, Vn, nrm.p, D, nb);
       GFCC_LAUNCH_CHECK();
       GFCC_CUDA(cudaMemsetAsync(nlive.p, 0, sizeof(int), s));
       givens_kernel<<<(nb + 127) / 128, 128, 0, s>>>(H.p, cs.p, sn.p, g.p, nrm.p, bnorm.p, kc.p, live.p, nb, k, j,
-                                                     tol, nlive.p);
+                                                     thr.p, nlive.p);
       GFCC_LAUNCH_CHECK();
       int hl = 0;
       GFCC_CUDA(cudaMemcpyAsync(&hl, nlive.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -475,10 +546,17 @@ void gmres_batched(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, const c
     backsolve_kernel<<<(nb + 127) / 128, 128, 0, s>>>(H.p, g.p, kc.p, nb, k);
     GFCC_LAUNCH_CHECK();
     // X += P V y (only the first kc basis vectors carry weight; later y entries are zero)
-    correct_kernel<<<grid_for(D * nb), 256, 0, s>>>(V.p, vstride, k, g.p, k + 1, Xw.p, c->op.mdiag.p, shw.p, D, nb);
+    correct_kernel<VT><<<grid_for(D * nb), 256, 0, s>>>(V.p, vstride, k, g.p, k + 1, Xw.p, c->op.mdiag.p, shw.p, D, nb);
     GFCC_LAUNCH_CHECK();
   }
   GFCC_CUDA(cudaStreamSynchronize(s));
+}
+
+void gmres_batched(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, const cplx* shifts_dev, int nb0,
+                   SolveStatus& st, bool transpose) {
+  const bool f32 = (c->opts.precision == GFCC_PREC_TF32 || c->opts.precision == GFCC_PREC_BF16) && !transpose;
+  if (f32) gmres_impl<cuFloatComplex>(c, Bin, Xout, Rout, shifts_dev, nb0, st, transpose);
+  else gmres_impl<cplx>(c, Bin, Xout, Rout, shifts_dev, nb0, st, transpose);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -534,28 +612,56 @@ void batch_to_cols(const cplx* src, int ldb, int ncols, int D, cplx* dst, int ld
 
 // G[c][q] = sum_nu c_q[nu] X[nu][c]  as a complex GEMM with a real-valued left operand: do it as a
 // real GEMM on the interleaved columns: G'[q][2c+r] = sum_nu cvec[q][nu] X'[nu][2c+r]
+// G[c][q] = sum_nu c_q[nu] X[nu][c]: each block reduces a chunk of rows for every (q, c) pair
+// (threads over pairs, X rows read coalesced, c_q[nu] broadcast), then the chunks are summed.
+namespace {
+__global__ void green_partial_kernel(const double* __restrict__ cq, long long D, int nq, const cplx* __restrict__ X,
+                                     int ldb, int ncols, long long rows, cplx* __restrict__ part) {
+  const long long r0 = blockIdx.x * rows, r1 = min(D, r0 + rows);
+  const int npair = nq * ncols;
+  for (int t = threadIdx.x; t < npair; t += blockDim.x) {
+    const int q = t / ncols, c = t % ncols;
+    const double* cr = cq + (long long)q * D;
+    double sr = 0.0, si = 0.0;
+    for (long long nu = r0; nu < r1; ++nu) {
+      const double w = cr[nu];
+      const cplx x = X[nu * ldb + c];
+      sr = fma(w, x.x, sr);
+      si = fma(w, x.y, si);
+    }
+    part[(long long)blockIdx.x * npair + t] = make_cuDoubleComplex(sr, si);
+  }
+}
+__global__ void green_reduce_kernel(const cplx* __restrict__ part, int nchunk, int nq, int ncols, cplx* __restrict__ G) {
+  const int npair = nq * ncols;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npair) return;
+  double sr = 0.0, si = 0.0;
+  for (int k = 0; k < nchunk; ++k) {
+    sr += part[(long long)k * npair + t].x;
+    si += part[(long long)k * npair + t].y;
+  }
+  const int q = t / ncols, c = t % ncols;
+  G[(long long)c * nq + q] = make_cuDoubleComplex(sr, si);
+}
+}  // namespace
+
 void green_from_batch(const double* cvec, int D, const int* qrows_host, int nq, const cplx* X, int ldb,
                       int ncols, cplx* G, cudaStream_t s) {
   if (nq == 0 || ncols == 0) return;
   DBuf<double> Cq;
-  DBuf<cplx> tmp;
+  DBuf<cplx> part;
   Cq.alloc((long long)nq * D);
-  tmp.alloc((long long)nq * ncols);
   for (int q = 0; q < nq; ++q)
     GFCC_CUDA(cudaMemcpyAsync(Cq.p + (long long)q * D, cvec + (long long)qrows_host[q] * D, sizeof(double) * D,
                               cudaMemcpyDeviceToDevice, s));
-  // tmp'[q][2c+r] = sum_nu Cq[q][nu] X'[nu][2c+r]
-  GemmDesc gd;
-  gd.M = nq; gd.N = 2 * ncols; gd.K = D;
-  gd.A = Cq.p; gd.sam = D; gd.sak = 1;
-  gd.B = reinterpret_cast<const double*>(X); gd.sbk = 2LL * ldb; gd.sbn = 1;
-  gd.C = reinterpret_cast<double*>(tmp.p); gd.scm = 2LL * ncols; gd.scn = 1;
-  gd.alpha = 1.0; gd.beta = 0.0;
-  dgemm(gd, s);
-  // G[c][q] = tmp[q][c]
-  int dims[3] = {nq, ncols, 2};
-  int pm[3] = {1, 0, 2};
-  permute(reinterpret_cast<const double*>(tmp.p), dims, 3, pm, reinterpret_cast<double*>(G), 1.0, 0.0, s);
+  const long long rows = std::max<long long>(64, (D + 2 * 152 * 4 - 1) / (2 * 152 * 4));
+  const int nchunk = (int)((D + rows - 1) / rows);
+  part.alloc((long long)nchunk * nq * ncols);
+  green_partial_kernel<<<nchunk, 256, 0, s>>>(Cq.p, D, nq, X, ldb, ncols, rows, part.p);
+  GFCC_LAUNCH_CHECK();
+  green_reduce_kernel<<<(nq * ncols + 255) / 256, 256, 0, s>>>(part.p, nchunk, nq, ncols, G);
+  GFCC_LAUNCH_CHECK();
   GFCC_CUDA(cudaStreamSynchronize(s));
 }
 

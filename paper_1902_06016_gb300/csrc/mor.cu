@@ -467,6 +467,7 @@ std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cp
     colscale_kernel<<<grid_for(D), 256, 0, s>>>(Y, MY, nc, D, j, keep ? 1.0 / n1 : 0.0);
     GFCC_LAUNCH_CHECK();
     if (T && keep) set_entry_kernel<<<1, 1, 0, s>>>(T, (long long)j * nc + j, n1);
+    GFCC_LAUNCH_CHECK();
     if (keep) kept.push_back(j);
   }
   GFCC_CUDA(cudaStreamSynchronize(s));
@@ -569,6 +570,7 @@ void mor_init_basis(gfcc_ctx* c) {
 void mor_append(gfcc_ctx* c, const cplx* Xin, const cplx* MXin, int nc) {
   MorState& ms = c->mor;
   cudaStream_t s = c->stream;
+  ProfScope prof(PROF_MOR_ORTHO, 0.0, s);
   const long long D = c->D;
   const int np = (int)ms.porb.size(), nq = (int)ms.qorb.size();
   if (nc == 0) return;
@@ -593,8 +595,11 @@ void mor_append(gfcc_ctx* c, const cplx* Xin, const cplx* MXin, int nc) {
     for (int k = 0; k < acc; ++k) iota[k] = k;
     GFCC_CUDA(cudaMemcpyAsync(dk.p, kept.data(), sizeof(int) * acc, cudaMemcpyHostToDevice, s));
     append_cols_kernel<<<grid_for(D * acc), 256, 0, s>>>(Y.p, nc, dk.p, acc, ms.S.p, cap, m0, D);
+    GFCC_LAUNCH_CHECK();
     append_cols_kernel<<<grid_for(D * acc), 256, 0, s>>>(MY.p, nc, dk.p, acc, ms.Z.p, cap, m0, D);
+    GFCC_LAUNCH_CHECK();
     append_cols_kernel<<<grid_for(D * acc), 256, 0, s>>>(Y.p, nc, dk.p, acc, SZ.p, 2 * acc, 0, D);
+    GFCC_LAUNCH_CHECK();
     append_cols_kernel<<<grid_for(D * acc), 256, 0, s>>>(MY.p, nc, dk.p, acc, SZ.p, 2 * acc, acc, D);
     GFCC_LAUNCH_CHECK();
     GFCC_CUDA(cudaStreamSynchronize(s));
@@ -646,6 +651,7 @@ void mor_append(gfcc_ctx* c, const cplx* Xin, const cplx* MXin, int nc) {
 void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, double* A_dev, double* maxres_dev) {
   MorState& ms = c->mor;
   cudaStream_t s = c->stream;
+  ProfScope prof(PROF_MOR_EVAL, 0.0, s);
   const int m = ms.m, np = (int)ms.porb.size(), nq = (int)ms.qorb.size(), cap = ms.m_cap, qn = ms.qn;
   GFCC_CHECK(m > 0, GFCC_ERR_STATE, "mor_eval: empty reduced model");
   const bool want_res = maxres_dev != nullptr;
@@ -674,17 +680,26 @@ void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, doubl
     house_kernel<<<1, 256, 0, s>>>(Hw.p + (long long)j * m + j + 1, len, v.p, tau.p);
     GFCC_LAUNCH_CHECK();
     house_left_kernel<<<m - j, 256, 0, s>>>(Hw.p, m, j + 1, len, j, v.p, tau.p);
+    GFCC_LAUNCH_CHECK();
     house_left_kernel<<<np, 256, 0, s>>>(bw.p, m, j + 1, len, 0, v.p, tau.p);
     GFCC_LAUNCH_CHECK();
     house_right_w_kernel<<<(m + 127) / 128, 128, 0, s>>>(Hw.p, m, m, j + 1, len, v.p, wv.p);
+    GFCC_LAUNCH_CHECK();
     house_right_update_kernel<<<grid_for((long long)m * len), 256, 0, s>>>(Hw.p, m, m, j + 1, len, v.p, wv.p, tau.p);
+    GFCC_LAUNCH_CHECK();
     house_right_w_kernel<<<(nq + 127) / 128, 128, 0, s>>>(cw.p, nq, nq, j + 1, len, v.p, wv.p);
+    GFCC_LAUNCH_CHECK();
     house_right_update_kernel<<<grid_for((long long)nq * len), 256, 0, s>>>(cw.p, nq, nq, j + 1, len, v.p, wv.p, tau.p);
+    GFCC_LAUNCH_CHECK();
     if (want_res) {
       house_right_w_kernel<<<(qn + 127) / 128, 128, 0, s>>>(A1.p, qn, qn, j + 1, len, v.p, wv.p);
+      GFCC_LAUNCH_CHECK();
       house_right_update_kernel<<<grid_for((long long)qn * len), 256, 0, s>>>(A1.p, qn, qn, j + 1, len, v.p, wv.p, tau.p);
+      GFCC_LAUNCH_CHECK();
       house_right_w_kernel<<<(qn + 127) / 128, 128, 0, s>>>(A2.p, qn, qn, j + 1, len, v.p, wv.p);
+      GFCC_LAUNCH_CHECK();
       house_right_update_kernel<<<grid_for((long long)qn * len), 256, 0, s>>>(A2.p, qn, qn, j + 1, len, v.p, wv.p, tau.p);
+      GFCC_LAUNCH_CHECK();
     }
     GFCC_LAUNCH_CHECK();
   }

@@ -1,0 +1,84 @@
+// Launch counting and optional CUDA-event timing of the GEMM kernel classes (C ABI in gfcc.h).
+#include "gfcc_internal.cuh"
+
+#include <atomic>
+#include <mutex>
+
+namespace gfcc {
+namespace {
+std::atomic<long long> g_launches{0};
+struct Rec {
+  cudaEvent_t a, b;
+  int cls;
+  double flops;
+};
+std::mutex g_mu;
+bool g_on = false;
+std::vector<Rec> g_recs;
+}  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+ProfScope::ProfScope(int c, double f, cudaStream_t st) : cls(c), flops(f), s(st) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_on) return;
+  Rec* r = new Rec{};
+  r->cls = c;
+  r->flops = f;
+  if (cudaEventCreate(&r->a) != cudaSuccess || cudaEventCreate(&r->b) != cudaSuccess) {
+    cudaGetLastError();
+    delete r;
+    return;
+  }
+  cudaEventRecord(r->a, s);
+  rec = r;
+}
+ProfScope::~ProfScope() {
+  if (!rec) return;
+  Rec* r = static_cast<Rec*>(rec);
+  cudaEventRecord(r->b, s);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_recs.push_back(*r);
+  delete r;
+}
+
+}  // namespace gfcc
+
+extern "C" {
+
+long long gfcc_launch_count(void) { return gfcc::g_launches.load(); }
+
+int gfcc_profile(int enable) {
+  std::lock_guard<std::mutex> lk(gfcc::g_mu);
+  for (auto& r : gfcc::g_recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  gfcc::g_recs.clear();
+  gfcc::g_on = enable != 0;
+  return GFCC_OK;
+}
+
+int gfcc_profile_read(int cls, long long* launches, double* ms, double* flops) {
+  if (cls < 0 || cls >= gfcc::PROF_NCLASS) return GFCC_ERR_ARG;
+  std::lock_guard<std::mutex> lk(gfcc::g_mu);
+  long long n = 0;
+  double t = 0.0, f = 0.0;
+  for (auto& r : gfcc::g_recs) {
+    if (r.cls != cls) continue;
+    float e = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&e, r.a, r.b) != cudaSuccess) {
+      cudaGetLastError();
+      return GFCC_ERR_CUDA;
+    }
+    ++n;
+    t += e;
+    f += r.flops;
+  }
+  if (launches) *launches = n;
+  if (ms) *ms = t;
+  if (flops) *flops = f;
+  return GFCC_OK;
+}
+
+}  // extern "C"

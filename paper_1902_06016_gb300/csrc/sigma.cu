@@ -112,6 +112,18 @@ void sigma_batch(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, int ldb, const cpl
                  int precision, bool transpose, cudaStream_t s) {
   GFCC_CHECK(ldb == nb, GFCC_ERR_ARG, "sigma_batch: internal layout needs ldb == nb");
   if (nb == 0) return;
+  const bool lowp = (precision == GFCC_PREC_TF32 || precision == GFCC_PREC_BF16) && !transpose;
+  ProfScope prof(lowp ? PROF_SIGMA_LP : PROF_SIGMA_EX, 0.0, s);
+  if (precision == GFCC_PREC_FP64_TC && !transpose) {
+    sigma_emulated(c, X, Y, nb, shift, s);
+    return;
+  }
+  if (precision == GFCC_PREC_FP64_TC) precision = GFCC_PREC_FP64;
+  if (precision != GFCC_PREC_FP64 && !transpose) {   // the transposed action always runs in FP64
+    GFCC_CHECK(c->lp.kind == precision && c->lp.impl, GFCC_ERR_STATE, "sigma: low-precision operands not built");
+    sigma_lowprec(c, X, Y, nb, shift, s);
+    return;
+  }
   const int o = c->o, v = c->v, P = c->P;
   const long long D = c->D, Pv = (long long)P * v, ov = (long long)o * v;
   Operator& op = c->op;
@@ -160,9 +172,7 @@ void sigma_batch(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, int ldb, const cpl
   cplx* CT = reinterpret_cast<cplx*>(c->ws.ct.p);
   unpack_ring_kernel<<<grid_for(ov * o * nb), 256, 0, s>>>(X2 - (long long)o * nb, U, o, v, nb);
   GFCC_LAUNCH_CHECK();
-  if (precision != GFCC_PREC_FP64 && !transpose && c->lp.kind != 0) {
-    ring_lowprec(c, reinterpret_cast<const double*>(U), reinterpret_cast<double*>(CT), nb, s);
-  } else {
+  {
     GemmDesc g;
     g.M = (int)ov; g.N = 2 * o * nb; g.K = (int)ov;
     g.A = Wr; g.sam = ov; g.sak = 1;

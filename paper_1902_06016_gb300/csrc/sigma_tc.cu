@@ -1,17 +1,517 @@
-// Low-precision ring contraction on the tcgen05 tensor cores (mixed-precision inner solves).
+// Low-precision sigma on the tcgen05 tensor cores, for the inner (Krylov) steps of the iterative
+// refinement: every GEMM-shaped term of the sigma runs as one tc_gemm launch with bf16 or tf32
+// operands and FP32 accumulation; the Fock diagonal, the shift and the small 1h-1h block are applied
+// in FP64 in the final combine. The residuals that decide convergence always use the FP64 sigma.
+//
+//   up:   [Xe ; Y1'] ((v+o) x 2nb) = [Vt ; A12] ((v+o) x Pv) . r2          (split-K over Pv)
+//   oooo: C2[(pij,a)][(c,r)]       = Woo (P x P) . r2 arranged [(a,c,r)][pmn]
+//   down: C2 += [T2p | A21] (Pv x (v+o)) . [Xe ; r1]
+//   ring: CT[(a,i)][(j,c,r)]       = Wr (ov x ov) . U,  U[(j,c,r)][(m,e)] = r_mj^e
 #include "gfcc_internal.cuh"
+#include "ozaki.cuh"
+#include "tc_gemm.cuh"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
 
 namespace gfcc {
+namespace {
 
-void build_low_precision(gfcc_ctx* c, int kind) {
-  (void)c;
-  (void)kind;
-  throw Error{GFCC_ERR_ARG, "low-precision sigma is not available in this build"};
+int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  return (int)std::min<long long>(std::max<long long>(g, 1), 152LL * 32);
 }
 
-void ring_lowprec(gfcc_ctx* c, const double* ut, double* ct, int nb, cudaStream_t s) {
-  (void)c; (void)ut; (void)ct; (void)nb; (void)s;
-  throw Error{GFCC_ERR_STATE, "low-precision ring requested without operands"};
+__device__ __forceinline__ int pair_of(int i, int j) { return j * (j - 1) / 2 + i; }
+__device__ __forceinline__ void unpair(int p, int& i, int& j) {
+  int jj = (int)floor((1.0 + sqrt(1.0 + 8.0 * (double)p)) * 0.5);
+  while (jj * (jj - 1) / 2 > p) --jj;
+  while ((jj + 1) * jj / 2 <= p) ++jj;
+  j = jj;
+  i = p - jj * (jj - 1) / 2;
+}
+
+// complex vector element read as double precision, and written from double precision
+__device__ __forceinline__ cplx ld2(const cplx& x) { return x; }
+__device__ __forceinline__ cplx ld2(const cuFloatComplex& x) { return make_cuDoubleComplex(x.x, x.y); }
+__device__ __forceinline__ void st2(cplx& y, double re, double im) { y = make_cuDoubleComplex(re, im); }
+__device__ __forceinline__ void st2(cuFloatComplex& y, double re, double im) { y = make_cuFloatComplex((float)re, (float)im); }
+
+// element conversion (round to nearest)
+template <TcKind K> struct Elem;
+template <> struct Elem<TcKind::BF16> {
+  using T = __nv_bfloat16;
+  __device__ static T cvt(double x) { return __double2bfloat16(x); }
+};
+template <> struct Elem<TcKind::TF32> {
+  using T = float;
+  __device__ static T cvt(double x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)x));
+    return __uint_as_float(r);
+  }
+};
+struct F64Elem {   // FP64 staging for the exact-slice path
+  using T = double;
+  __device__ static T cvt(double x) { return x; }
+};
+
+// dst[r][k] = src[r*ld + k] for k < K, 0 for K <= k < kpad
+template <TcKind K>
+__global__ void convert_rows_kernel(const double* __restrict__ src, long long ld, long long rows, long long Kc,
+                                    typename Elem<K>::T* __restrict__ dst, int kpad) {
+  long long total = rows * kpad;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long r = t / kpad, k = t % kpad;
+    dst[t] = Elem<K>::cvt(k < Kc ? src[r * ld + k] : 0.0);
+  }
+}
+// [T2p | A21]: dst[row][e] = T2p[row][e] (e < v), dst[row][v+m] = A21[row][m] (m < o), rest 0
+template <typename E>
+__global__ void convert_down_kernel(const double* __restrict__ T2p, const double* __restrict__ A21, long long rows,
+                                    int v, int o, typename E::T* __restrict__ dst, int kpad) {
+  long long total = rows * kpad;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long r = t / kpad;
+    int k = (int)(t % kpad);
+    double x = 0.0;
+    if (k < v) x = T2p[r * v + k];
+    else if (k < v + o) x = A21[r * o + (k - v)];
+    dst[t] = E::cvt(x);
+  }
+}
+
+// ---- per-batch operand preparation from the FP64 batch-minor block X[nu][c] (complex) ----------
+// ring: U[(j*nb + c)*2 + r][m*v + e] = r_mj^e (component r), K padded
+template <typename E, typename VT>
+__global__ void prep_ring_kernel(const VT* __restrict__ X, int o, int v, int nb, typename E::T* __restrict__ U,
+                                 int kpad) {
+  const long long rows = 2LL * o * nb;
+  const long long total = rows * kpad;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long n = t / kpad;
+    int k = (int)(t % kpad);
+    double val = 0.0;
+    if (k < o * v) {
+      int r = (int)(n & 1);
+      long long jc = n >> 1;
+      int c = (int)(jc % nb), j = (int)(jc / nb);
+      int m = k / v, e = k % v;
+      if (m != j) {
+        int lo = min(m, j), hi = max(m, j);
+        cplx x = ld2(X[((long long)o + (long long)pair_of(lo, hi) * v + e) * nb + c]);
+        double comp = r ? x.y : x.x;
+        val = (m < j) ? comp : -comp;
+      }
+    }
+    U[t] = E::cvt(val);
+  }
+}
+// oooo: B[(a*nb + c)*2 + r][pmn] = X2[(pmn*v + a)][c].r
+template <typename E, typename VT>
+__global__ void prep_oooo_kernel(const VT* __restrict__ X, int o, int v, int P, int nb,
+                                 typename E::T* __restrict__ B, int kpad) {
+  const long long rows = 2LL * v * nb;
+  const long long total = rows * kpad;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long n = t / kpad;
+    int k = (int)(t % kpad);
+    double val = 0.0;
+    if (k < P) {
+      int r = (int)(n & 1);
+      long long ac = n >> 1;
+      int c = (int)(ac % nb), a = (int)(ac / nb);
+      cplx x = ld2(X[((long long)o + (long long)k * v + a) * nb + c]);
+      val = r ? x.y : x.x;
+    }
+    B[t] = E::cvt(val);
+  }
+}
+// up: B[c*2 + r][kk] = X2[kk][c].r  (kk = pmn*v + f)
+template <typename E, typename VT>
+__global__ void prep_up_kernel(const VT* __restrict__ X, int o, long long Pv, int nb, typename E::T* __restrict__ B,
+                               int kpad) {
+  const long long total = 2LL * nb * kpad;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long n = t / kpad;
+    long long k = t % kpad;
+    double val = 0.0;
+    if (k < Pv) {
+      int r = (int)(n & 1), c = (int)(n >> 1);
+      cplx x = ld2(X[((long long)o + k) * nb + c]);
+      val = r ? x.y : x.x;
+    }
+    B[t] = E::cvt(val);
+  }
+}
+// sum split-K partials: out[i] = sum_z part[z*stride + i]
+__global__ void reduce_splits_kernel(const float* __restrict__ part, int zs, long long stride, long long n,
+                                     float* __restrict__ out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < zs; ++z) s += part[z * stride + t];
+    out[t] = s;
+  }
+}
+// down operand: B[c*2 + r][e] = Xe[e][c*2 + r] (e < v), B[c*2+r][v+m] = X1[m][c].r
+template <typename E, typename U, typename VT>
+__global__ void prep_down_kernel(const U* __restrict__ up, long long ldu, const VT* __restrict__ X, int o, int v,
+                                 int nb, typename E::T* __restrict__ B, int kpad) {
+  const long long total = 2LL * nb * kpad;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int n = (int)(t / kpad);
+    int k = (int)(t % kpad);
+    double val = 0.0;
+    if (k < v) {
+      val = up[(long long)k * ldu + n];
+    } else if (k < v + o) {
+      cplx x = ld2(X[(long long)(k - v) * nb + (n >> 1)]);
+      val = (n & 1) ? x.y : x.x;
+    }
+    B[t] = E::cvt(val);
+  }
+}
+// final combine into the FP64 output (FP32 or FP64 GEMM results)
+template <typename F, typename VT>
+__global__ void combine_lp_kernel(const VT* __restrict__ X, VT* __restrict__ Y, const F* __restrict__ up,
+                                  long long ldu, const F* __restrict__ C2, const F* __restrict__ CT,
+                                  const double* __restrict__ A11, const double* __restrict__ diag,
+                                  const cplx* __restrict__ shift, int o, int v, long long D, int nb) {
+  const long long total = D * nb;
+  const long long ldct = 2LL * o * nb;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(t % nb);
+    const long long nu = t / nb;
+    cplx x = ld2(X[t]);
+    double dre = diag[nu], dim = 0.0;
+    if (shift) { dre += shift[c].x; dim = shift[c].y; }
+    double yr = dre * x.x - dim * x.y;
+    double yi = dre * x.y + dim * x.x;
+    if (nu < o) {
+      const int i = (int)nu;
+      yr += up[(long long)(v + i) * ldu + 2 * c];
+      yi += up[(long long)(v + i) * ldu + 2 * c + 1];
+      for (int m = 0; m < o; ++m) {
+        double a = A11[(long long)i * o + m];
+        cplx xm = ld2(X[(long long)m * nb + c]);
+        yr += a * xm.x;
+        yi += a * xm.y;
+      }
+    } else {
+      const long long row = nu - o;
+      yr += C2[row * 2 * nb + 2 * c];
+      yi += C2[row * 2 * nb + 2 * c + 1];
+      int pij = (int)(row / v), a = (int)(row % v);
+      int i, j;
+      unpair(pij, i, j);
+      const F* c1 = CT + ((long long)a * o + i) * ldct + ((long long)j * nb + c) * 2;
+      const F* c2 = CT + ((long long)a * o + j) * ldct + ((long long)i * nb + c) * 2;
+      yr += (double)c1[0] - (double)c2[0];
+      yi += (double)c1[1] - (double)c2[1];
+    }
+    st2(Y[t], yr, yi);
+  }
+}
+
+// dst[nu][k] = src[nu][c0 + k] (k < nk) and back
+__global__ void cols_gather_kernel(const cplx* __restrict__ src, int lds, int c0, int nk, cplx* __restrict__ dst,
+                                   long long D) {
+  const long long total = D * nk;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x)
+    dst[t] = src[(t / nk) * lds + c0 + (t % nk)];
+}
+__global__ void cols_scatter_kernel(const cplx* __restrict__ src, int nk, cplx* __restrict__ dst, int ldd, int c0,
+                                    long long D) {
+  const long long total = D * nk;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x)
+    dst[(t / nk) * ldd + c0 + (t % nk)] = src[t];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+struct LpState {
+  TcKind kind;
+  int Kr = 0, Kp = 0, Kpv = 0, Kvo = 0;
+  DBuf<uint8_t> Wr, Woo, Aup, Adn;            // operands (bf16 or fp32 elements)
+  DBuf<uint8_t> Bring, Boo, Bup, Bdn;         // per-batch operands
+  DBuf<float> CT, C2, up_part, up;            // outputs
+  DBuf<int> err;
+  int nb_cap = 0, ksplit = 1;
+};
+
+static LpState* lp_state(gfcc_ctx* c) { return reinterpret_cast<LpState*>(c->lp.impl); }
+
+// FP64-accurate sigma from exact bf16 slices (residuals of the iterative refinement)
+struct EmuState {
+  SlicedRows Wr, Woo, Aup, Adn;
+  DBuf<double> stage, CT, C2, up;
+  SlicedRows Bring, Boo, Bup, Bdn;
+  DBuf<cplx> Xc, Yc;
+  OzWork work;
+};
+static EmuState* emu_state(gfcc_ctx* c) { return reinterpret_cast<EmuState*>(c->lp.emu); }
+
+void free_low_precision(gfcc_ctx* c) {
+  delete lp_state(c);
+  c->lp.impl = nullptr;
+  c->lp.kind = 0;
+  delete emu_state(c);
+  c->lp.emu = nullptr;
+}
+
+void build_emulated(gfcc_ctx* c) {
+  if (c->lp.emu) return;
+  const int o = c->o, v = c->v, P = c->P;
+  const long long ov = (long long)o * v, Pv = (long long)P * v;
+  cudaStream_t s = c->stream;
+  auto* st = new EmuState();
+  c->lp.emu = st;
+  oz_slice(c->op.Wr.p, ov, ov, ov, false, st->Wr, s);
+  oz_slice(c->op.Woo.p, P, P, P, false, st->Woo, s);
+  st->Aup.rows = v + o;
+  st->Aup.kp = tc_pad_k(TcKind::BF16, Pv);
+  st->Aup.reversed = false;
+  st->Aup.ns = OZ_SLICES;
+  st->Aup.slices.alloc(2LL * (v + o) * OZ_SLICES * st->Aup.kp);
+  st->Aup.expo.alloc(v + o);
+  oz_slice_into(c->op.Vt.p, Pv, v, Pv, st->Aup, 0, s);
+  oz_slice_into(c->op.A12.p, Pv, o, Pv, st->Aup, v, s);
+  st->stage.alloc(Pv * (v + o));
+  convert_down_kernel<F64Elem><<<grid_for(Pv * (v + o)), 256, 0, s>>>(c->op.T2p.p, c->op.A21.p, Pv, v, o, st->stage.p,
+                                                                       v + o);
+  GFCC_LAUNCH_CHECK();
+  oz_slice(st->stage.p, v + o, Pv, v + o, false, st->Adn, s);
+  GFCC_CUDA(cudaStreamSynchronize(s));
+}
+
+void sigma_emulated(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shift, cudaStream_t s) {
+  build_emulated(c);
+  EmuState& st = *emu_state(c);
+  const int o = c->o, v = c->v, P = c->P;
+  const long long ov = (long long)o * v, Pv = (long long)P * v, D = c->D;
+  const int chunk = 64;
+  for (int c0 = 0; c0 < nb; c0 += chunk) {
+    const int nbc = std::min(chunk, nb - c0);
+    const long long nring = 2LL * o * nbc, noo = 2LL * v * nbc, nsm = 2LL * nbc;
+    st.Xc.alloc(D * chunk);
+    st.Yc.alloc(D * chunk);
+    st.stage.alloc(std::max({nring * ov, noo * (long long)P, nsm * Pv, nsm * (long long)(v + o), Pv * (v + o)}));
+    st.CT.alloc(ov * 2LL * o * chunk);
+    st.C2.alloc(Pv * 2LL * chunk);
+    st.up.alloc((long long)(v + o) * 2LL * chunk);
+    cols_gather_kernel<<<grid_for(D * nbc), 256, 0, s>>>(X, nb, c0, nbc, st.Xc.p, D);
+    GFCC_LAUNCH_CHECK();
+    // up: [Xe ; Y1'] = [Vt ; A12] r2
+    prep_up_kernel<F64Elem, cplx><<<grid_for(nsm * Pv), 256, 0, s>>>(st.Xc.p, o, Pv, nbc, st.stage.p, (int)Pv);
+    GFCC_LAUNCH_CHECK();
+    oz_slice(st.stage.p, Pv, nsm, Pv, true, st.Bup, s);
+    oz_gemm(st.Aup, st.Bup, v + o, nsm, st.up.p, nsm, 0.0, st.work, s);
+    // oooo into C2
+    prep_oooo_kernel<F64Elem, cplx><<<grid_for(noo * P), 256, 0, s>>>(st.Xc.p, o, v, P, nbc, st.stage.p, P);
+    GFCC_LAUNCH_CHECK();
+    oz_slice(st.stage.p, P, noo, P, true, st.Boo, s);
+    oz_gemm(st.Woo, st.Boo, P, noo, st.C2.p, noo, 0.0, st.work, s);
+    // down: C2 += [T2p | A21] [Xe ; r1]
+    prep_down_kernel<F64Elem, double, cplx><<<grid_for(nsm * (v + o)), 256, 0, s>>>(st.up.p, nsm, st.Xc.p, o, v, nbc,
+                                                                             st.stage.p, v + o);
+    GFCC_LAUNCH_CHECK();
+    oz_slice(st.stage.p, v + o, nsm, v + o, true, st.Bdn, s);
+    oz_gemm(st.Adn, st.Bdn, Pv, nsm, st.C2.p, nsm, 1.0, st.work, s);
+    // ring
+    prep_ring_kernel<F64Elem, cplx><<<grid_for(nring * ov), 256, 0, s>>>(st.Xc.p, o, v, nbc, st.stage.p, (int)ov);
+    GFCC_LAUNCH_CHECK();
+    oz_slice(st.stage.p, ov, nring, ov, true, st.Bring, s);
+    oz_gemm(st.Wr, st.Bring, ov, nring, st.CT.p, nring, 0.0, st.work, s);
+    combine_lp_kernel<double, cplx><<<grid_for(D * nbc), 256, 0, s>>>(st.Xc.p, st.Yc.p, st.up.p, nsm, st.C2.p, st.CT.p,
+                                                                c->op.A11.p, c->op.diag.p,
+                                                                shift ? shift + c0 : nullptr, o, v, D, nbc);
+    GFCC_LAUNCH_CHECK();
+    cols_scatter_kernel<<<grid_for(D * nbc), 256, 0, s>>>(st.Yc.p, nbc, Y, nb, c0, D);
+    GFCC_LAUNCH_CHECK();
+  }
+  c->stats.sigma_calls++;
+  c->stats.sigma_cols += nb;
+}
+
+int emulated_error(gfcc_ctx* c) {
+  EmuState* st = emu_state(c);
+  if (!st || st->work.err.n == 0) return 0;
+  int h = 0;
+  GFCC_CUDA(cudaMemcpyAsync(&h, st->work.err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  GFCC_CUDA(cudaStreamSynchronize(c->stream));
+  return h;
+}
+
+template <TcKind K>
+static void build_ops(gfcc_ctx* c, LpState& st) {
+  using T = typename Elem<K>::T;
+  const int o = c->o, v = c->v, P = c->P;
+  const long long ov = (long long)o * v, Pv = (long long)P * v;
+  cudaStream_t s = c->stream;
+  st.Kr = tc_pad_k(K, ov);
+  st.Kp = tc_pad_k(K, P);
+  st.Kpv = tc_pad_k(K, Pv);
+  st.Kvo = tc_pad_k(K, v + o);
+  st.Wr.alloc(sizeof(T) * ov * st.Kr);
+  convert_rows_kernel<K><<<grid_for(ov * st.Kr), 256, 0, s>>>(c->op.Wr.p, ov, ov, ov, reinterpret_cast<T*>(st.Wr.p), st.Kr);
+  GFCC_LAUNCH_CHECK();
+  st.Woo.alloc(sizeof(T) * (long long)P * st.Kp);
+  convert_rows_kernel<K><<<grid_for((long long)P * st.Kp), 256, 0, s>>>(c->op.Woo.p, P, P, P, reinterpret_cast<T*>(st.Woo.p),
+                                                                       st.Kp);
+  GFCC_LAUNCH_CHECK();
+  st.Aup.alloc(sizeof(T) * (long long)(v + o) * st.Kpv);
+  convert_rows_kernel<K><<<grid_for((long long)v * st.Kpv), 256, 0, s>>>(c->op.Vt.p, Pv, v, Pv,
+                                                                        reinterpret_cast<T*>(st.Aup.p), st.Kpv);
+  GFCC_LAUNCH_CHECK();
+  convert_rows_kernel<K><<<grid_for((long long)o * st.Kpv), 256, 0, s>>>(
+      c->op.A12.p, Pv, o, Pv, reinterpret_cast<T*>(st.Aup.p) + (long long)v * st.Kpv, st.Kpv);
+  GFCC_LAUNCH_CHECK();
+  st.Adn.alloc(sizeof(T) * Pv * st.Kvo);
+  convert_down_kernel<Elem<K>><<<grid_for(Pv * st.Kvo), 256, 0, s>>>(c->op.T2p.p, c->op.A21.p, Pv, v, o,
+                                                               reinterpret_cast<T*>(st.Adn.p), st.Kvo);
+  GFCC_LAUNCH_CHECK();
+  st.err.alloc(1);
+  st.err.zero(s);
+  GFCC_CUDA(cudaStreamSynchronize(s));
+}
+
+void build_low_precision(gfcc_ctx* c, int kind) {
+  GFCC_CHECK(kind == GFCC_PREC_BF16 || kind == GFCC_PREC_TF32, GFCC_ERR_ARG, "low precision: bf16 or tf32 only");
+  if (c->lp.kind == kind && c->lp.impl) return;
+  free_low_precision(c);
+  auto* st = new LpState();
+  c->lp.impl = st;
+  st->kind = kind == GFCC_PREC_BF16 ? TcKind::BF16 : TcKind::TF32;
+  if (st->kind == TcKind::BF16) build_ops<TcKind::BF16>(c, *st);
+  else build_ops<TcKind::TF32>(c, *st);
+  c->lp.kind = kind;
+}
+
+int low_precision_error(gfcc_ctx* c) {
+  LpState* st = lp_state(c);
+  if (!st) return emulated_error(c);
+  if (emulated_error(c)) return 1;
+  int h = 0;
+  GFCC_CUDA(cudaMemcpyAsync(&h, st->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  GFCC_CUDA(cudaStreamSynchronize(c->stream));
+  return h;
+}
+
+template <TcKind K, typename VT>
+static void sigma_lp_impl(gfcc_ctx* c, LpState& st, const VT* X, VT* Y, int nb, const cplx* shift, cudaStream_t s) {
+  using T = typename Elem<K>::T;
+  const int o = c->o, v = c->v, P = c->P;
+  const long long ov = (long long)o * v, Pv = (long long)P * v, D = c->D;
+  const long long nring = 2LL * o * nb, noo = 2LL * v * nb, nsm = 2LL * nb;
+  if (nb > st.nb_cap) {
+    st.Bring.alloc(sizeof(T) * nring * st.Kr);
+    st.Boo.alloc(sizeof(T) * noo * st.Kp);
+    st.Bup.alloc(sizeof(T) * nsm * st.Kpv);
+    st.Bdn.alloc(sizeof(T) * nsm * st.Kvo);
+    st.CT.alloc(ov * nring);
+    st.C2.alloc(Pv * nsm);
+    st.up.alloc((long long)(v + o) * nsm);
+    st.nb_cap = nb;
+  }
+  // split-K for the short-and-wide "up" GEMM: about two waves of CTAs
+  const int mt = (v + o + 127) / 128;
+  const int nk_up = st.Kpv / tc_kblock(K);
+  int ksplit = std::max(1, std::min(nk_up, (2 * 152) / std::max(1, mt * (int)((nsm + 255) / 256))));
+  const long long part_stride = (long long)(v + o) * nsm;
+  st.up_part.alloc(part_stride * ksplit);
+
+  T* Bring = reinterpret_cast<T*>(st.Bring.p);
+  T* Boo = reinterpret_cast<T*>(st.Boo.p);
+  T* Bup = reinterpret_cast<T*>(st.Bup.p);
+  T* Bdn = reinterpret_cast<T*>(st.Bdn.p);
+  prep_up_kernel<Elem<K>, VT><<<grid_for(nsm * st.Kpv), 256, 0, s>>>(X, o, Pv, nb, Bup, st.Kpv);
+  GFCC_LAUNCH_CHECK();
+  prep_oooo_kernel<Elem<K>, VT><<<grid_for(noo * st.Kp), 256, 0, s>>>(X, o, v, P, nb, Boo, st.Kp);
+  GFCC_LAUNCH_CHECK();
+  prep_ring_kernel<Elem<K>, VT><<<grid_for(nring * st.Kr), 256, 0, s>>>(X, o, v, nb, Bring, st.Kr);
+  GFCC_LAUNCH_CHECK();
+  // up (split-K) and its reduction
+  tc_gemm(K, TcOperand{st.Aup.p, v + o, st.Kpv}, TcOperand{Bup, nsm, st.Kpv}, st.up_part.p, nsm, v + o, nsm, 0, ksplit,
+          part_stride, st.err.p, s);
+  {
+    const int nk_split = (nk_up + ksplit - 1) / ksplit;
+    const int zs = (nk_up + nk_split - 1) / nk_split;
+    reduce_splits_kernel<<<grid_for(part_stride), 256, 0, s>>>(st.up_part.p, zs, part_stride, part_stride, st.up.p);
+    GFCC_LAUNCH_CHECK();
+  }
+  // oooo into C2 (as [P][(a,c,r)] = [(pij,a)][(c,r)])
+  tc_gemm(K, TcOperand{st.Woo.p, P, st.Kp}, TcOperand{Boo, noo, st.Kp}, st.C2.p, noo, P, noo, 0, 1, 0, st.err.p, s);
+  // down: C2 += [T2p | A21] [Xe ; r1]
+  prep_down_kernel<Elem<K>, float, VT><<<grid_for(nsm * st.Kvo), 256, 0, s>>>(st.up.p, nsm, X, o, v, nb, Bdn, st.Kvo);
+  GFCC_LAUNCH_CHECK();
+  tc_gemm(K, TcOperand{st.Adn.p, Pv, st.Kvo}, TcOperand{Bdn, nsm, st.Kvo}, st.C2.p, nsm, Pv, nsm, 1, 1, 0, st.err.p, s);
+  // ring
+  tc_gemm(K, TcOperand{st.Wr.p, ov, st.Kr}, TcOperand{Bring, nring, st.Kr}, st.CT.p, nring, ov, nring, 0, 1, 0,
+          st.err.p, s);
+  combine_lp_kernel<float, VT><<<grid_for(D * nb), 256, 0, s>>>(X, Y, st.up.p, nsm, st.C2.p, st.CT.p, c->op.A11.p, c->op.diag.p,
+                                                     shift, o, v, D, nb);
+  GFCC_LAUNCH_CHECK();
+}
+
+void sigma_lowprec(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shift, cudaStream_t s) {
+  LpState* st = lp_state(c);
+  GFCC_CHECK(st != nullptr, GFCC_ERR_STATE, "low-precision operator not built");
+  if (st->kind == TcKind::BF16) sigma_lp_impl<TcKind::BF16, cplx>(c, *st, X, Y, nb, shift, s);
+  else sigma_lp_impl<TcKind::TF32, cplx>(c, *st, X, Y, nb, shift, s);
+  c->stats.sigma_calls++;
+  c->stats.sigma_cols += nb;
+}
+
+void sigma_lowprec_f32(gfcc_ctx* c, const cuFloatComplex* X, cuFloatComplex* Y, int nb, const cplx* shift,
+                       cudaStream_t s) {
+  LpState* st = lp_state(c);
+  GFCC_CHECK(st != nullptr, GFCC_ERR_STATE, "low-precision operator not built");
+  ProfScope prof(PROF_SIGMA_LP, 0.0, s);
+  if (st->kind == TcKind::BF16) sigma_lp_impl<TcKind::BF16, cuFloatComplex>(c, *st, X, Y, nb, shift, s);
+  else sigma_lp_impl<TcKind::TF32, cuFloatComplex>(c, *st, X, Y, nb, shift, s);
+  c->stats.sigma_calls++;
+  c->stats.sigma_cols += nb;
+}
+
+// standalone low-precision GEMM check (C = A B^T) for tests of the tensor-core kernel itself
+void tc_selftest(int kind, const double* A, const double* B, int M, int N, int K, float* C, cudaStream_t s) {
+  const TcKind k = kind == GFCC_PREC_BF16 ? TcKind::BF16 : TcKind::TF32;
+  const int kp = tc_pad_k(k, K);
+  const size_t es = k == TcKind::BF16 ? 2 : 4;
+  DBuf<uint8_t> a, b;
+  DBuf<int> err;
+  a.alloc(es * (size_t)M * kp);
+  b.alloc(es * (size_t)N * kp);
+  err.alloc(1);
+  err.zero(s);
+  if (k == TcKind::BF16) {
+    convert_rows_kernel<TcKind::BF16><<<grid_for((long long)M * kp), 256, 0, s>>>(A, K, M, K, reinterpret_cast<__nv_bfloat16*>(a.p), kp);
+    GFCC_LAUNCH_CHECK();
+    convert_rows_kernel<TcKind::BF16><<<grid_for((long long)N * kp), 256, 0, s>>>(B, K, N, K, reinterpret_cast<__nv_bfloat16*>(b.p), kp);
+    GFCC_LAUNCH_CHECK();
+  } else {
+    convert_rows_kernel<TcKind::TF32><<<grid_for((long long)M * kp), 256, 0, s>>>(A, K, M, K, reinterpret_cast<float*>(a.p), kp);
+    GFCC_LAUNCH_CHECK();
+    convert_rows_kernel<TcKind::TF32><<<grid_for((long long)N * kp), 256, 0, s>>>(B, K, N, K, reinterpret_cast<float*>(b.p), kp);
+    GFCC_LAUNCH_CHECK();
+  }
+  GFCC_LAUNCH_CHECK();
+  tc_gemm(k, TcOperand{a.p, M, kp}, TcOperand{b.p, N, kp}, C, N, M, N, 0, 1, 0, err.p, s);
+  int h = 0;
+  GFCC_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GFCC_CUDA(cudaStreamSynchronize(s));
+  GFCC_CHECK(h == 0, GFCC_ERR_CUDA, "tensor-core pipeline wait timed out");
 }
 
 }  // namespace gfcc

@@ -1,0 +1,300 @@
+// tcgen05 GEMM kernel (see tc_gemm.cuh). Hand-written PTX: TMA (cp.async.bulk.tensor) loads into
+// 128-byte-swizzled shared memory, mbarrier pipeline, tcgen05.mma with the accumulator in TMEM,
+// tcgen05.ld epilogue. Every wait is bounded: on timeout the kernel records an error, skips the
+// remaining work, releases its TMEM and returns.
+#include "tc_gemm.cuh"
+
+#include <cuda.h>
+
+#include <algorithm>
+
+namespace gfcc {
+namespace {
+
+constexpr int BM = 128, BN = 256, STAGES = 4;
+constexpr int KB_BYTES = 128;                        // one swizzle row of K per operand row
+constexpr int A_BYTES = BM * KB_BYTES;               // 16 KB
+constexpr int B_BYTES = BN * KB_BYTES;               // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int TMEM_COLS = 256;                       // 128 lanes x 256 FP32 columns
+constexpr long long WAIT_CYCLES = 4000000000LL;      // about two seconds at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                  // leading byte offset (unused with 128-byte swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
+  d |= (uint64_t)1 << 46;                  // descriptor version
+  d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: FP32 accumulate, A/B format (bf16 = 1 for kind::f16, tf32 = 2 for
+// kind::tf32), both K-major, N = 256, M = 128
+template <TcKind K>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | ((K == TcKind::BF16 ? 1u : 2u) << 7) | ((K == TcKind::BF16 ? 1u : 2u) << 10) |
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+template <TcKind K>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  if constexpr (K == TcKind::BF16) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "l"(a), "l"(b), "r"(idesc<K>()), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "l"(a), "l"(b), "r"(idesc<K>()), "r"(acc)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <TcKind KIND>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float* C,
+                   long long ldc, long long M, long long N, int nk_total, int nk_split, long long split_stride,
+                   int beta, int* err) {
+  constexpr int KB_ELEMS = KIND == TcKind::BF16 ? 64 : 32;
+  constexpr int MMA_K_BYTES = 32;                            // K = 16 bf16 or 8 tf32 per instruction
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long m0 = (long long)blockIdx.y * BM, n0 = (long long)blockIdx.x * BN;
+  const int z = blockIdx.z;
+  const int kb0 = z * nk_split;
+  const int nk = max(0, min(nk_total, kb0 + nk_split) - kb0);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), accf = smem_u32(bars + 2 * STAGES);
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int st = 0; st < STAGES; ++st) {
+      mbar_init(full0 + 8 * st, 1);
+      mbar_init(empty0 + 8 * st, 1);
+    }
+    mbar_init(accf, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {   // TMA producer
+      for (int kb = 0; kb < nk; ++kb) {
+        const int st = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(empty0 + 8 * st, ph ^ 1)) { s_fail = 1; break; }
+        mbar_expect_tx(full0 + 8 * st, STAGE_BYTES);
+        tma_load_2d(smem_u32(sA + st * A_BYTES), &tmA, (kb0 + kb) * KB_ELEMS, (int)m0, full0 + 8 * st);
+        tma_load_2d(smem_u32(sB + st * B_BYTES), &tmB, (kb0 + kb) * KB_ELEMS, (int)n0, full0 + 8 * st);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {   // MMA issuer
+      bool ok = true;
+      for (int kb = 0; kb < nk && ok; ++kb) {
+        const int st = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(full0 + 8 * st, ph)) { s_fail = 1; ok = false; break; }
+        tc_fence_after();
+        const uint64_t ad = sdesc(smem_u32(sA + st * A_BYTES));
+        const uint64_t bd = sdesc(smem_u32(sB + st * B_BYTES));
+#pragma unroll
+        for (int kk = 0; kk < KB_BYTES / MMA_K_BYTES; ++kk)
+          mma<KIND>(taddr, ad + (uint64_t)(kk * MMA_K_BYTES >> 4), bd + (uint64_t)(kk * MMA_K_BYTES >> 4),
+                    (kb > 0 || kk > 0) ? 1u : 0u);
+        mma_commit(empty0 + 8 * st);   // frees the stage once these MMAs have read it
+      }
+      mma_commit(accf);                // accumulator complete
+    }
+  } else {   // warps 2..5: epilogue over TMEM lane quarters (warp % 4)
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(accf, 0));   // keep the warp converged for tcgen05.ld
+    if (!ok) {
+      if (lane == 0) s_fail = 1;
+    } else {
+      tc_fence_after();
+      const int q = warp & 3;
+      const long long grow = m0 + q * 32 + lane;
+      float* Cz = C + (long long)z * split_stride;
+      const bool vec = (ldc % 4 == 0);
+#pragma unroll 1
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        uint32_t r[32];
+        tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 32), r);
+        const long long gcol = n0 + ch * 32;
+        if (grow < M && gcol < N) {
+          float* p = Cz + grow * ldc + gcol;
+          if (vec && gcol + 32 <= N) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                     __uint_as_float(r[j + 3]));
+              if (nk == 0) v = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (beta) {
+                float4 o = *reinterpret_cast<float4*>(p + j);
+                v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+              }
+              *reinterpret_cast<float4*>(p + j) = v;
+            }
+          } else {
+            for (int j = 0; j < 32 && gcol + j < N; ++j) {
+              float v = nk == 0 ? 0.f : __uint_as_float(r[j]);
+              if (beta) v += p[j];
+              p[j] = v;
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TMEM_COLS) : "memory");
+  }
+  if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
+}
+
+// ---- host side ----------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    GFCC_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    GFCC_CHECK(q == cudaDriverEntryPointSuccess && p, GFCC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+CUtensorMap make_map(TcKind kind, const TcOperand& op, int box_rows) {
+  CUtensorMap m;
+  const int esize = kind == TcKind::BF16 ? 2 : 4;
+  GFCC_CHECK(op.k_pad % (KB_BYTES / esize) == 0, GFCC_ERR_ARG, "tc_gemm: K not padded to the k-block");
+  GFCC_CHECK((reinterpret_cast<uintptr_t>(op.ptr) & 15) == 0, GFCC_ERR_ARG, "tc_gemm: operand not 16-byte aligned");
+  GFCC_CHECK(op.ld >= op.k_pad && op.ld % (KB_BYTES / esize) == 0, GFCC_ERR_ARG, "tc_gemm: bad row stride");
+  cuuint64_t dims[2] = {(cuuint64_t)op.k_pad, (cuuint64_t)op.rows};
+  cuuint64_t strides[1] = {(cuuint64_t)op.ld * esize};
+  cuuint32_t box[2] = {(cuuint32_t)(KB_BYTES / esize), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, kind == TcKind::BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                           2, const_cast<void*>(op.ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  GFCC_CHECK(r == CUDA_SUCCESS, GFCC_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return m;
+}
+
+}  // namespace
+
+void tc_gemm(TcKind kind, const TcOperand& A, const TcOperand& B, float* C, long long ldc, long long M, long long N,
+             int beta, int ksplit, long long split_stride, int* err_dev, cudaStream_t s, int prof_class) {
+  if (M <= 0 || N <= 0) return;
+  GFCC_CHECK(A.k_pad == B.k_pad, GFCC_ERR_ARG, "tc_gemm: K mismatch");
+  GFCC_CHECK(A.rows >= M && B.rows >= N, GFCC_ERR_ARG, "tc_gemm: operand rows");
+  GFCC_CHECK(ksplit >= 1 && (ksplit == 1 || beta == 0), GFCC_ERR_ARG, "tc_gemm: split-K needs beta = 0");
+  GFCC_CHECK(A.rows < (1LL << 31) && B.rows < (1LL << 31), GFCC_ERR_ARG, "tc_gemm: too many rows");
+  const int kb_elems = tc_kblock(kind);
+  GFCC_CHECK(A.k_pad / kb_elems < (1LL << 30), GFCC_ERR_ARG, "tc_gemm: K too large");
+  const int nk_total = (int)(A.k_pad / kb_elems);
+  const int nk_split = (nk_total + ksplit - 1) / ksplit;
+  const int zs = (nk_total + nk_split - 1) / nk_split;
+  CUtensorMap ma = make_map(kind, A, BM);
+  CUtensorMap mb = make_map(kind, B, BN);
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)zs);
+  GFCC_CHECK(grid.y <= 65535 && grid.z <= 65535, GFCC_ERR_ARG, "tc_gemm: grid too large");
+  ProfScope prof(prof_class, 2.0 * (double)M * (double)N * (double)A.k_pad, s);
+  if (kind == TcKind::BF16) {
+    static bool attr = false;
+    if (!attr) {
+      GFCC_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<TcKind::BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+      attr = true;
+    }
+    tc_gemm_kernel<TcKind::BF16><<<grid, 192, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, nk_total, nk_split, split_stride,
+                                                                beta, err_dev);
+    GFCC_LAUNCH_CHECK();
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      GFCC_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<TcKind::TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+      attr = true;
+    }
+    tc_gemm_kernel<TcKind::TF32><<<grid, 192, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, nk_total, nk_split, split_stride,
+                                                                beta, err_dev);
+    GFCC_LAUNCH_CHECK();
+  }
+  GFCC_LAUNCH_CHECK();
+}
+
+}  // namespace gfcc

@@ -2,8 +2,10 @@
 // contraction (permute -> FP64 GEMM -> permute-accumulate) driven by index labels.
 #include "gfcc_internal.cuh"
 #include "tensor.h"
+#include "ozaki.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <map>
 
 namespace gfcc {
@@ -131,6 +133,45 @@ void contract(double alpha, const TV& A, const TV& B, double beta, const TV& C, 
     return true;
   };
   DBuf<double> Ap, Bp, Cp;
+  std::string lt0 = Ml + Nl;
+  std::vector<int> pc0 = perm_of(lt0, lc);
+  // contractions above this many multiply-adds use the tensor cores (GFCC_OZ_MIN_MACS overrides it,
+  // which the tests use to exercise this path at small sizes)
+  double min_macs = 2e9;
+  if (const char* env = getenv("GFCC_OZ_MIN_MACS")) min_macs = atof(env);
+  if ((double)M * (double)N * (double)K >= min_macs && M >= 64 && N >= 64) {
+    // FP64-accurate GEMM from exact bf16 slices on the tensor cores (8 slices: FP64-level accuracy)
+    const double* Aop2 = A.p;
+    std::vector<int> pa2 = perm_of(la, Ml + Kl);
+    if (!identity(pa2)) {
+      Ap.alloc(M * K);
+      permute(A.p, A.d.data(), (int)A.d.size(), pa2.data(), Ap.p, 1.0, 0.0, s);
+      Aop2 = Ap.p;
+    }
+    const double* Bop2 = B.p;
+    std::vector<int> pb2 = perm_of(lb, Nl + Kl);   // K-major rows for the tensor cores
+    if (!identity(pb2)) {
+      Bp.alloc(K * N);
+      permute(B.p, B.d.data(), (int)B.d.size(), pb2.data(), Bp.p, 1.0, 0.0, s);
+      Bop2 = Bp.p;
+    }
+    SlicedRows sa, sb;
+    oz_slice(Aop2, K, M, K, false, sa, s, OZ_SLICES_MAX);
+    oz_slice(Bop2, K, N, K, true, sb, s, OZ_SLICES_MAX);
+    Ap.release();
+    Bp.release();
+    Cp.alloc(M * N);
+    OzWork w;
+    oz_gemm(sa, sb, M, N, Cp.p, N, 0.0, w, s);
+    std::vector<int> dt;
+    for (char ch : lt0) dt.push_back(size[ch]);
+    permute(Cp.p, dt.data(), (int)dt.size(), pc0.data(), C.p, alpha, beta, s);
+    int herr = 0;
+    GFCC_CUDA(cudaMemcpyAsync(&herr, w.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GFCC_CUDA(cudaStreamSynchronize(s));
+    GFCC_CHECK(herr == 0, GFCC_ERR_CUDA, "contract: tensor-core pipeline wait timed out");
+    return;
+  }
   const double* Aop = A.p;
   std::vector<int> pa = perm_of(la, Ml + Kl);
   if (!identity(pa)) {

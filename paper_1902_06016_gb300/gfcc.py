@@ -16,8 +16,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgfcc.so")
 
-PREC_FP64, PREC_TF32, PREC_BF16, PREC_BF16X2 = 0, 1, 2, 3
-PRECISIONS = {"fp64": PREC_FP64, "tf32": PREC_TF32, "bf16": PREC_BF16, "bf16x2": PREC_BF16X2}
+PREC_FP64, PREC_TF32, PREC_BF16, PREC_FP64_TC = 0, 1, 2, 3
+PRECISIONS = {"fp64": PREC_FP64, "tf32": PREC_TF32, "bf16": PREC_BF16, "fp64_tc": PREC_FP64_TC}
 
 ERRORS = {-1: "GFCC_ERR_ARG", -2: "GFCC_ERR_NOT_CONVERGED", -3: "GFCC_ERR_RANK", -4: "GFCC_ERR_NONFINITE",
           -5: "GFCC_ERR_OOM", -6: "GFCC_ERR_CUDA", -7: "GFCC_ERR_STATE"}
@@ -34,7 +34,7 @@ class VBlocks(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_restarts", C.c_int),
                 ("precision", C.c_int), ("max_batch", C.c_int), ("drop_tol", C.c_double),
-                ("verbose", C.c_int)]
+                ("verbose", C.c_int), ("residual_precision", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -59,6 +59,10 @@ PROTOTYPES = {
     "gfcc_mor_info": (C.c_int, [_vp, _dp, C.c_int, _ip, _ip, _ip, _ip]),
     "gfcc_mor_save": (C.c_int, [_vp, C.c_char_p]),
     "gfcc_mor_load": (C.c_int, [_vp, C.c_char_p]),
+    "gfcc_tc_gemm": (C.c_int, [C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]),
+    "gfcc_launch_count": (C.c_longlong, []),
+    "gfcc_profile": (C.c_int, [C.c_int]),
+    "gfcc_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_longlong), _dp, _dp]),
     "gfcc_last_error": (C.c_char_p, [_vp]),
     "gfcc_free": (None, [_vp]),
 }
@@ -83,6 +87,37 @@ def load(path: str | None = None):
     return lib
 
 
+def tc_gemm(A, B, precision="bf16"):
+    """C = A B^T on the tensor cores (diagnostic): A [M, K], B [N, K] float64 host arrays."""
+    lib = load()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    M, K = A.shape
+    N = B.shape[0]
+    C = np.empty((M, N), dtype=np.float32)
+    rc = lib.gfcc_tc_gemm(PRECISIONS[precision], _ptr(A), _ptr(B), M, N, K, _ptr(C))
+    if rc != 0:
+        raise GfccError(rc, "gfcc_tc_gemm failed")
+    return C
+
+
+def launch_count():
+    return int(load().gfcc_launch_count())
+
+
+def profile(enable=True):
+    load().gfcc_profile(1 if enable else 0)
+
+
+def profile_read(cls):
+    """(launches, ms, flops) of kernel class cls (0 tensor-core GEMM, 1 FP64 SIMT GEMM)."""
+    n, ms, fl = C.c_longlong(), C.c_double(), C.c_double()
+    rc = load().gfcc_profile_read(int(cls), C.byref(n), C.byref(ms), C.byref(fl))
+    if rc != 0:
+        raise GfccError(rc, "gfcc_profile_read failed")
+    return n.value, ms.value, fl.value
+
+
 class GfccError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -101,8 +136,12 @@ def _ptr(a):
 
 
 def _c64(a):
-    a = np.ascontiguousarray(a, dtype=np.float64)
-    return a
+    """float64 contiguous host array, or a contiguous float64 torch tensor passed through as is."""
+    if hasattr(a, "data_ptr") and not isinstance(a, np.ndarray):
+        if not a.is_contiguous() or str(a.dtype) != "torch.float64":
+            raise TypeError("tensor inputs must be contiguous float64")
+        return a
+    return np.ascontiguousarray(a, dtype=np.float64)
 
 
 def _ints(a):
@@ -123,7 +162,7 @@ class Context:
     """One GFCC problem on the current CUDA device (wraps gfcc_t)."""
 
     def __init__(self, inputs, tol=1e-8, restart=30, max_restarts=200, precision="fp64", max_batch=0,
-                 drop_tol=1e-10, stream=None):
+                 drop_tol=1e-10, stream=None, residual_precision=None):
         lib = load()
         self._lib = lib
         o, v = inputs.o, inputs.v
@@ -133,6 +172,7 @@ class Context:
         opts.tol, opts.restart, opts.max_restarts = tol, restart, max_restarts
         opts.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         opts.max_batch, opts.drop_tol = max_batch, drop_tol
+        opts.residual_precision = -1 if residual_precision is None else PRECISIONS[residual_precision]
         self._keep = [_c64(x) for x in (inputs.eps, inputs.oooo, inputs.ooov, inputs.oovv, inputs.ovov,
                                          inputs.ovvv, inputs.t1, inputs.t2, inputs.l1, inputs.l2)]
         eps, oooo, ooov, oovv, ovov, ovvv, t1, t2, l1, l2 = self._keep

@@ -28,6 +28,7 @@ keep their shapes and structure):
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -94,16 +95,27 @@ def chem_eri(seed: int, scale: float, p, q, r, s) -> np.ndarray:
     return scale * normal(seed, STREAM_ERI, key)
 
 
-def antisym_block(seed: int, scale: float, P, Q, R, S, chunk: int = 8) -> np.ndarray:
-    """<pq||rs> for p in P, q in Q, r in R, s in S (index lists), chunked over P."""
+def antisym_block(seed: int, scale: float, P, Q, R, S, chunk: int = 1) -> np.ndarray:
+    """<pq||rs> for p in P, q in Q, r in R, s in S (index lists); slices of P are generated in
+    parallel threads (NumPy releases the GIL), each value depending only on its indices."""
     P, Q, R, S = (np.asarray(x, dtype=np.int64) for x in (P, Q, R, S))
     out = np.empty((len(P), len(Q), len(R), len(S)), dtype=np.float64)
     q = Q[None, :, None, None]
     r = R[None, None, :, None]
     s = S[None, None, None, :]
-    for i0 in range(0, len(P), chunk):
+
+    def fill(i0):
         p = P[i0:i0 + chunk, None, None, None]
         out[i0:i0 + chunk] = chem_eri(seed, scale, p, r, q, s) - chem_eri(seed, scale, p, s, q, r)
+
+    starts = list(range(0, len(P), chunk))
+    if out.size < (1 << 20) or len(starts) == 1:
+        for i0 in starts:
+            fill(i0)
+    else:
+        import concurrent.futures as cf
+        with cf.ThreadPoolExecutor(max_workers=min(len(starts), os.cpu_count() or 1)) as ex:
+            list(ex.map(fill, starts))
     return out
 
 
