@@ -166,6 +166,21 @@ int gfcc_mor_load(gfcc_t ctx, const char* path);
  * counterpart: it exists to test the kernel in isolation. */
 int gfcc_tc_gemm(int precision, const double* A, const double* B, int M, int N, int K, float* C);
 
+/* Allocation-free variant of gfcc_tc_gemm, for callers that cannot allocate device memory at the
+ * point of the call (a framework that owns all device memory, a path where the device-wide
+ * synchronisation of cudaMalloc/cudaFree is not acceptable, code that must not hit out-of-memory
+ * after start-up). The paper has no counterpart. A, B, C are device pointers (row-major
+ * A[M][K], B[N][K], C[M][N]); stream is a cudaStream_t or NULL; the call returns after the product
+ * is complete. The rounded operand copies and the error flag live in a fixed 32 MiB __device__
+ * array inside the library, reserved on every GPU that loads it until the process exits: the call
+ * allocates nothing, and rejects with GFCC_ERR_ARG any size whose two rounded operands (K padded
+ * to 64 bf16 or 32 tf32 elements, each copy rounded up to 256 bytes) plus 256 bytes do not fit.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture. All calls share the array: calls whose work overlaps on a
+ * GPU (different streams or threads) race and must be serialised by the caller. */
+int gfcc_tc_gemm_noalloc(int precision, const double* A, const double* B, int M, int N, int K, float* C,
+                         void* stream);
+
 /* Number of CUDA kernels launched by this library since it was loaded (all contexts). */
 long long gfcc_launch_count(void);
 

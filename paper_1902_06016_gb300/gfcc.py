@@ -60,6 +60,7 @@ PROTOTYPES = {
     "gfcc_mor_save": (C.c_int, [_vp, C.c_char_p]),
     "gfcc_mor_load": (C.c_int, [_vp, C.c_char_p]),
     "gfcc_tc_gemm": (C.c_int, [C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]),
+    "gfcc_tc_gemm_noalloc": (C.c_int, [C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
     "gfcc_launch_count": (C.c_longlong, []),
     "gfcc_profile": (C.c_int, [C.c_int]),
     "gfcc_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_longlong), _dp, _dp]),
@@ -99,6 +100,15 @@ def tc_gemm(A, B, precision="bf16"):
     if rc != 0:
         raise GfccError(rc, "gfcc_tc_gemm failed")
     return C
+
+
+def tc_gemm_noalloc(A, B, C, precision="bf16", stream=None):
+    """C = A B^T on the tensor cores without any device allocation: A [M, K], B [N, K] float64 and
+    C [M, N] float32 must be contiguous CUDA tensors. Returns the status code."""
+    lib = load()
+    M, K = A.shape
+    N = B.shape[0]
+    return int(lib.gfcc_tc_gemm_noalloc(PRECISIONS[precision], _ptr(A), _ptr(B), M, N, K, _ptr(C), stream))
 
 
 def launch_count():
