@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--solve-tol", type=float, default=1e-8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=2, help="(w, p) columns in the oracle sample")
+    ap.add_argument("--mode", default="pipeline", choices=["pipeline", "sigma"],
+                    help="pipeline: the whole MOR step (default); sigma: one batch of sigma applications")
+    ap.add_argument("--nvec", type=int, default=64, help="vectors per sigma batch (--mode sigma)")
     return ap.parse_args()
 
 
@@ -236,6 +239,51 @@ def run_ours(args, rank, world):
 
 
 # ---------------------------------------------------------------------------------------------
+def run_sigma(args):
+    """Micro-benchmark of the dominant kernels: the sigma on one batch of nvec complex vectors."""
+    import torch
+    from paper_1902_06016_gb300 import Context, load
+    from paper_1902_06016_gb300 import gfcc as G
+    torch.cuda.set_device(0)
+    load()
+    W = synth.WORKLOADS[args.workload]
+    inp = synth.make_inputs(W["o"], W["v"], W["seed"])
+    stream = torch.cuda.current_stream()
+    ctx = Context(inp, precision=args.precision, stream=stream.cuda_stream)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    X = torch.randn((args.nvec, ctx.D), dtype=torch.complex128, device="cuda", generator=g)
+    Y = torch.empty_like(X)
+    for _ in range(args.warmup):
+        ctx.sigma(X, precision=args.precision, out=Y)
+    torch.cuda.synchronize()
+    G.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.sigma(X, precision=args.precision, out=Y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    n, ms, fl = G.profile_read(0 if args.precision in ("tf32", "bf16") else 2)
+    G.profile(False)
+    o, v = W["o"], W["v"]
+    P = o * (o - 1) // 2
+    flop = 2.0 * args.nvec * (2 * (o * v) ** 2 * o + 2 * P * P * v + 4 * P * v * v + 4 * o * P * v)
+    step_ms = e0.elapsed_time(e1) / args.steps
+    peaks, kind = measured_peaks()
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    pk = bf16 * (0.5 if args.precision == "tf32" else 1.0)
+    ach = fl / (ms / 1e3) / 1e12 if ms else None
+    return {"metric": "sigma complex columns/s", "value": args.nvec / (step_ms / 1e3), "unit": "columns/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+            "higher_is_better": True, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": args.workload, "nvec": args.nvec, "mode": "sigma"},
+            "algorithmic_tflops": flop / (step_ms / 1e3) / 1e12,
+            "roofline": {"kernel": "tc_gemm_kernel", "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                         "frac": ach / pk if ach else None, "peak_kind": f"{kind} burst bf16" +
+                         (" x 0.5 (tf32 rate)" if args.precision == "tf32" else ""), "launches": n,
+                         "avg_launch_ms": ms / n if n else None}}
+
+
 def oracle_sample(args, ncols, inp=None):
     """Time the FP64 CPU oracle on a bounded sample: full GMRES solves of ncols (w, p) points."""
     from oracle import bc, hbar
@@ -280,6 +328,9 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return
+    if args.mode == "sigma":
+        print(json.dumps(run_sigma(args)), flush=True)
         return
     if world > 1:
         import torch.distributed as dist

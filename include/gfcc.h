@@ -128,6 +128,14 @@ int gfcc_solve_full(gfcc_t ctx, const double* omegas, int nw, double eta, const 
                     int np, const int* qorb, int nq, double* G, double* A, double* X, int ldx,
                     gfcc_stats* stats);
 
+/* Derivatives of G_pq(w) (Eq. gfcclineqn) with respect to the frequency and the broadening. With
+ * A(w) = w - i eta + M, x_p = A^{-1} b_p (forward solves, as gfcc_solve_full) and the adjoint solutions
+ * y_q = A^{-T} c_q (transposed sigma), G_pq = c_q^T x_p, dG_pq/dw = -y_q^T x_p and dG_pq/deta = i y_q^T x_p.
+ * Outputs (each optional, host or device, complex, layout [(w*np + p)*nq + q] as in gfcc_solve_full).
+ * The adjoint solves run with the FP64 transposed sigma. GFCC_ERR_NOT_CONVERGED if a solve hit the cap. */
+int gfcc_green_derivatives(gfcc_t ctx, const double* omegas, int nw, double eta, const int* orbitals, int np,
+                           const int* qorb, int nq, double* G, double* dG_domega, double* dG_deta);
+
 /* Start a reduced model (Eq. model): solve Eq. xplin at the seed frequencies for every p in
  * orbitals (host), orthonormalise the solutions into S (columns whose norm after two
  * Gram-Schmidt passes falls below opts.drop_tol of their norm before are dropped), and project:

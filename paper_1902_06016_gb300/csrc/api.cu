@@ -83,6 +83,34 @@ int grid_for(long long n) {
   return (int)std::min<long long>(std::max<long long>(g, 1), 152LL * 32);
 }
 
+// part[chunk][w][p][q] = sum_{nu in chunk} Y[nu][w*nq + q] X[nu][w*np + p]  (bilinear, no conjugation)
+__global__ void bilinear_partial_kernel(const cplx* __restrict__ X, const cplx* __restrict__ Y, long long D, int nw,
+                                        int np, int nq, long long rows, cplx* __restrict__ part) {
+  const long long r0 = blockIdx.x * rows, r1 = min(D, r0 + rows);
+  const int ntrip = nw * np * nq;
+  const int ldx = nw * np, ldy = nw * nq;
+  for (int t = threadIdx.x; t < ntrip; t += blockDim.x) {
+    const int w = t / (np * nq), p = (t / nq) % np, q = t % nq;
+    double sr = 0.0, si = 0.0;
+    for (long long nu = r0; nu < r1; ++nu) {
+      const cplx x = X[nu * ldx + w * np + p], y = Y[nu * ldy + w * nq + q];
+      sr += x.x * y.x - x.y * y.y;
+      si += x.x * y.y + x.y * y.x;
+    }
+    part[(long long)blockIdx.x * ntrip + t] = make_cuDoubleComplex(sr, si);
+  }
+}
+// dw = -sum_chunk part, de = i * sum_chunk part
+__global__ void bilinear_reduce_kernel(const cplx* __restrict__ part, int nchunk, int ntrip, cplx* __restrict__ dw,
+                                       cplx* __restrict__ de) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntrip) return;
+  double sr = 0.0, si = 0.0;
+  for (int k = 0; k < nchunk; ++k) { sr += part[(long long)k * ntrip + t].x; si += part[(long long)k * ntrip + t].y; }
+  if (dw) dw[t] = make_cuDoubleComplex(-sr, -si);
+  if (de) de[t] = make_cuDoubleComplex(-si, sr);
+}
+
 std::vector<int> q_positions(const std::vector<int>& porb, const std::vector<int>& qorb) {
   std::vector<int> qi(porb.size(), -1);
   for (size_t p = 0; p < porb.size(); ++p)
@@ -145,6 +173,39 @@ void solve_columns(gfcc_ctx* c, const std::vector<double>& ws, double eta, const
     st_out->max_rel_res = maxres;
     st_out->not_converged = notconv;
   }
+}
+
+// Adjoint solves (w - i eta + M)^T y = c_q for every (w, q): columns (w, q) of Yall [D][nw*nq].
+void solve_adjoint_columns(gfcc_ctx* c, const std::vector<double>& ws, double eta, const std::vector<int>& qorb,
+                           cplx* Yall) {
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  const int nq = (int)qorb.size();
+  const long long ncols = (long long)ws.size() * nq;
+  const int nbmax = choose_batch(c, ncols);
+  DBuf<cplx> B, Y, sh;
+  DBuf<int> rows;
+  B.alloc(D * nbmax); Y.alloc(D * nbmax); sh.alloc(nbmax); rows.alloc(nbmax);
+  for (long long c0 = 0; c0 < ncols; c0 += nbmax) {
+    const int nb = (int)std::min<long long>(nbmax, ncols - c0);
+    std::vector<int> hr(nb);
+    std::vector<cplx> hs(nb);
+    for (int k = 0; k < nb; ++k) {
+      const long long col = c0 + k;
+      hr[k] = qorb[col % nq];
+      hs[k] = make_cuDoubleComplex(ws[col / nq], -eta);
+    }
+    GFCC_CUDA(cudaMemcpyAsync(rows.p, hr.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s));
+    GFCC_CUDA(cudaMemcpyAsync(sh.p, hs.data(), sizeof(cplx) * nb, cudaMemcpyHostToDevice, s));
+    gfcc::gather_rows_real_to_cplx(c->cvec.p, (int)D, rows.p, nb, (int)D, B.p, nb, s);
+    gfcc::SolveStatus st;
+    gfcc::gmres_batched(c, B.p, Y.p, nullptr, sh.p, nb, st, true);
+    for (int k = 0; k < nb; ++k)
+      GFCC_CHECK(st.converged[k], GFCC_ERR_NOT_CONVERGED, "adjoint solve did not converge");
+    GFCC_CUDA(cudaMemcpy2DAsync(Yall + c0, sizeof(cplx) * ncols, Y.p, sizeof(cplx) * nb, sizeof(cplx) * nb, D,
+                                cudaMemcpyDeviceToDevice, s));
+  }
+  GFCC_CUDA(cudaStreamSynchronize(s));
 }
 
 // Solve at frequencies ws for the model's p set and append the solutions to the subspace.
@@ -391,6 +452,48 @@ int gfcc_solve_full(gfcc_t c, const double* omegas, int nw, double eta, const in
     c->last_error = "gfcc_solve_full: " + std::to_string(st.not_converged) + " column(s) not converged";
     return GFCC_ERR_NOT_CONVERGED;
   }
+  API_END(c)
+}
+
+int gfcc_green_derivatives(gfcc_t c, const double* omegas, int nw, double eta, const int* orbitals, int np,
+                           const int* qorb, int nq, double* G, double* dG_domega, double* dG_deta) {
+  if (!c) return GFCC_ERR_ARG;
+  if (nw <= 0 || !omegas || !std::isfinite(eta) || eta < 0.0) { c->last_error = "gfcc_green_derivatives: bad frequencies or eta"; return GFCC_ERR_ARG; }
+  int rc = check_orbitals(c, orbitals, np, "gfcc_green_derivatives");
+  if (rc) return rc;
+  if (qorb) { rc = check_orbitals(c, qorb, nq, "gfcc_green_derivatives(q)"); if (rc) return rc; }
+  for (int k = 0; k < nw; ++k)
+    if (!std::isfinite(omegas[k])) { c->last_error = "gfcc_green_derivatives: non-finite frequency"; return GFCC_ERR_NONFINITE; }
+  API_BEGIN
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  std::vector<int> porb(orbitals, orbitals + np);
+  std::vector<int> qv = qorb ? std::vector<int>(qorb, qorb + nq) : porb;
+  nq = (int)qv.size();
+  std::vector<double> ws(omegas, omegas + nw);
+  const long long nx = (long long)nw * np, ny = (long long)nw * nq;
+  DBuf<cplx> X, Y, Gd, dwd, ded, part;
+  X.alloc(D * nx);
+  Y.alloc(D * ny);
+  if (G) Gd.alloc(nx * nq);
+  gfcc_stats st{};
+  solve_columns(c, ws, eta, porb, qv, G ? Gd.p : nullptr, X.p, nullptr, &st);
+  GFCC_CHECK(st.not_converged == 0, GFCC_ERR_NOT_CONVERGED, "gfcc_green_derivatives: forward solve did not converge");
+  solve_adjoint_columns(c, ws, eta, qv, Y.p);
+  const int ntrip = (int)(nx * nq);
+  const long long rows = std::max<long long>(64, (D + 2 * 152 - 1) / (2 * 152));
+  const int nchunk = (int)((D + rows - 1) / rows);
+  part.alloc((long long)nchunk * ntrip);
+  dwd.alloc(ntrip);
+  ded.alloc(ntrip);
+  bilinear_partial_kernel<<<nchunk, 256, 0, s>>>(X.p, Y.p, D, nw, np, nq, rows, part.p);
+  GFCC_LAUNCH_CHECK();
+  bilinear_reduce_kernel<<<(ntrip + 255) / 256, 256, 0, s>>>(part.p, nchunk, ntrip, dwd.p, ded.p);
+  GFCC_LAUNCH_CHECK();
+  if (G) copy_out(G, Gd.p, sizeof(cplx) * ntrip, s);
+  if (dG_domega) copy_out(dG_domega, dwd.p, sizeof(cplx) * ntrip, s);
+  if (dG_deta) copy_out(dG_deta, ded.p, sizeof(cplx) * ntrip, s);
+  GFCC_CUDA(cudaStreamSynchronize(s));
   API_END(c)
 }
 

@@ -26,7 +26,8 @@ __device__ __forceinline__ int pair_of(int i, int j) { return j * (j - 1) / 2 + 
 
 // Decode pair index P -> (i, j), i < j.
 __device__ __forceinline__ void unpair(int p, int& i, int& j) {
-  int jj = (int)floor((1.0 + sqrt(1.0 + 8.0 * (double)p)) * 0.5);
+  // FP32 estimate (GB300's FP64 pipe is narrow), corrected to the exact integer below
+  int jj = (int)floorf((1.0f + sqrtf(1.0f + 8.0f * (float)p)) * 0.5f);
   while (jj * (jj - 1) / 2 > p) --jj;
   while ((jj + 1) * jj / 2 <= p) ++jj;
   j = jj;

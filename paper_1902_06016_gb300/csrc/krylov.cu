@@ -79,6 +79,110 @@ __global__ void multidot_kernel(const VT* __restrict__ V, long long vstride, int
   }
 }
 
+// Fused CGS sweep: w <- w - sum_i V_i h_i (h = pass-1 coefficients), then partial sums of the
+// pass-2 coefficients conj(V_i) w over the chunk (same layout as multidot_kernel's partials).
+template <typename VT>
+__global__ void update_dot_kernel(const VT* __restrict__ V, long long vstride, int nv, VT* __restrict__ W,
+                                  long long D, int nb, long long rows_per_chunk, const cplx* __restrict__ h, int hld,
+                                  cplx* __restrict__ partial) {
+  using R = typename RealOf<VT>::type;
+  __shared__ cplx red[MD_TY][MD_TX];
+  __shared__ VT hs[MD_MAXV][MD_TX];
+  const int c = blockIdx.x * MD_TX + threadIdx.x;
+  const long long r0 = blockIdx.y * rows_per_chunk;
+  const long long r1 = min(D, r0 + rows_per_chunk);
+  for (int i = threadIdx.y; i < MD_MAXV; i += MD_TY) {
+    VT v;
+    v.x = (c < nb && i < nv) ? (R)h[(long long)c * hld + i].x : R(0);
+    v.y = (c < nb && i < nv) ? (R)h[(long long)c * hld + i].y : R(0);
+    hs[i][threadIdx.x] = v;
+  }
+  __syncthreads();
+  R ax[MD_MAXV], ay[MD_MAXV];
+#pragma unroll
+  for (int i = 0; i < MD_MAXV; ++i) { ax[i] = R(0); ay[i] = R(0); }
+  if (c < nb) {
+    for (long long nu = r0 + threadIdx.y; nu < r1; nu += MD_TY) {
+      VT vv[MD_MAXV];
+      VT w = W[nu * nb + c];
+#pragma unroll
+      for (int i = 0; i < MD_MAXV; ++i) {
+        if (i < nv) {
+          vv[i] = V[i * vstride + nu * nb + c];
+          const VT hv = hs[i][threadIdx.x];
+          w.x -= vv[i].x * hv.x - vv[i].y * hv.y;
+          w.y -= vv[i].x * hv.y + vv[i].y * hv.x;
+        }
+      }
+      W[nu * nb + c] = w;
+#pragma unroll
+      for (int i = 0; i < MD_MAXV; ++i) {
+        if (i < nv) {
+          ax[i] += vv[i].x * w.x + vv[i].y * w.y;
+          ay[i] += vv[i].x * w.y - vv[i].y * w.x;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < MD_MAXV; ++i) {
+    if (i < nv) {
+      red[threadIdx.y][threadIdx.x] = make_cuDoubleComplex((double)ax[i], (double)ay[i]);
+      __syncthreads();
+      if (threadIdx.y == 0 && c < nb) {
+        cplx s = red[0][threadIdx.x];
+        for (int k = 1; k < MD_TY; ++k) { s.x += red[k][threadIdx.x].x; s.y += red[k][threadIdx.x].y; }
+        partial[((long long)blockIdx.y * nv + i) * nb + c] = s;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Fused final sweep: w <- w - sum_i V_i h_i, with partial sums of |w|^2 per column (nv = 1 layout)
+template <typename VT>
+__global__ void update_norm_kernel(const VT* __restrict__ V, long long vstride, int nv, VT* __restrict__ W,
+                                   long long D, int nb, long long rows_per_chunk, const cplx* __restrict__ h, int hld,
+                                   cplx* __restrict__ partial) {
+  using R = typename RealOf<VT>::type;
+  __shared__ cplx red[MD_TY][MD_TX];
+  __shared__ VT hs[MD_MAXV][MD_TX];
+  const int c = blockIdx.x * MD_TX + threadIdx.x;
+  const long long r0 = blockIdx.y * rows_per_chunk;
+  const long long r1 = min(D, r0 + rows_per_chunk);
+  for (int i = threadIdx.y; i < MD_MAXV; i += MD_TY) {
+    VT v;
+    v.x = (c < nb && i < nv) ? (R)h[(long long)c * hld + i].x : R(0);
+    v.y = (c < nb && i < nv) ? (R)h[(long long)c * hld + i].y : R(0);
+    hs[i][threadIdx.x] = v;
+  }
+  __syncthreads();
+  R acc = R(0);
+  if (c < nb) {
+    for (long long nu = r0 + threadIdx.y; nu < r1; nu += MD_TY) {
+      VT w = W[nu * nb + c];
+#pragma unroll
+      for (int i = 0; i < MD_MAXV; ++i) {
+        if (i < nv) {
+          const VT vv = V[i * vstride + nu * nb + c];
+          const VT hv = hs[i][threadIdx.x];
+          w.x -= vv.x * hv.x - vv.y * hv.y;
+          w.y -= vv.x * hv.y + vv.y * hv.x;
+        }
+      }
+      W[nu * nb + c] = w;
+      acc += w.x * w.x + w.y * w.y;
+    }
+  }
+  red[threadIdx.y][threadIdx.x] = make_cuDoubleComplex((double)acc, 0.0);
+  __syncthreads();
+  if (threadIdx.y == 0 && c < nb) {
+    double s = 0.0;
+    for (int k = 0; k < MD_TY; ++k) s += red[k][threadIdx.x].x;
+    partial[(long long)blockIdx.y * nb + c] = make_cuDoubleComplex(s, 0.0);
+  }
+}
+
 // h[c*hld + hoff + i] (+)= sum_chunk partial[chunk][i][c]
 __global__ void reduce_partial_kernel(const cplx* __restrict__ partial, int nchunk, int nv, int nb,
                                       cplx* __restrict__ h, int hld, int hoff, int accumulate) {
@@ -169,10 +273,12 @@ __global__ void scale_cols_kernel(const VI* __restrict__ W, VO* __restrict__ V, 
   long long total = D * nb;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
+    using R = typename RealOf<VO>::type;
     int c = (int)(t % nb);
     double n = nrm[c];
-    double s = (n > 0.0 && isfinite(n)) ? 1.0 / n : 0.0;
-    V[t] = mk<VO>((double)W[t].x * s, (double)W[t].y * s);
+    const R s = (n > 0.0 && isfinite(n)) ? (R)(1.0 / n) : R(0);
+    V[t].x = (R)W[t].x * s;
+    V[t].y = (R)W[t].y * s;
   }
 }
 
@@ -257,21 +363,25 @@ __global__ void correct_kernel(const VT* __restrict__ V, long long vstride, int 
   long long total = D * nb;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
+    // the correction is formed in the basis precision; only its addition to x is FP64
+    using R = typename RealOf<VT>::type;
     int c = (int)(t % nb);
     long long nu = t / nb;
-    cplx s = make_cuDoubleComplex(0.0, 0.0);
+    R sr = R(0), si = R(0);
     const cplx* yc = y + (long long)c * yld;
     for (int i = 0; i < nv; ++i) {
-      cplx yi = yc[i];
+      const cplx yi = yc[i];
       if (yi.x != 0.0 || yi.y != 0.0) {
         const VT vv = V[i * vstride + t];
-        s = cuCadd(s, cuCmul(make_cuDoubleComplex((double)vv.x, (double)vv.y), yi));
+        const R yr = (R)yi.x, yim = (R)yi.y;
+        sr += vv.x * yr - vv.y * yim;
+        si += vv.x * yim + vv.y * yr;
       }
     }
-    cplx d = make_cuDoubleComplex(shift[c].x + md[nu], shift[c].y);
-    cplx z = cuCdiv(s, d);
-    X[t].x += z.x;
-    X[t].y += z.y;
+    const R dr = (R)(shift[c].x + md[nu]), di = (R)shift[c].y;
+    const R inv = R(1) / (dr * dr + di * di);
+    X[t].x += (double)((sr * dr + si * di) * inv);
+    X[t].y += (double)((si * dr - sr * di) * inv);
   }
 }
 
@@ -389,6 +499,7 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
   H.alloc((long long)nb0 * (k + 1) * k);
   cs.alloc((long long)nb0 * k); sn.alloc((long long)nb0 * k); g.alloc((long long)nb0 * (k + 1));
   hb.alloc((long long)nb0 * (k + 1));
+  tmpc.alloc(nb0);
   nrm.alloc(nb0); bnorm.alloc(nb0); thr.alloc(nb0); kc.alloc(nb0); live.alloc(nb0); nlive.alloc(1); cols.alloc(nb0);
   shw.alloc(nb0);
   flag.alloc(1);
@@ -520,16 +631,50 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
       }
       inner_sigma(c, Zw.p, Ww.p, nb, shw.p, inner_prec, transpose, s);
       ProfScope pk2(PROF_KRYLOV, 0.0, s);
-      // CGS with one re-orthogonalisation: h = V^H w, w -= V h, twice; H[:, j] = h1 + h2
-      for (int pass = 0; pass < 2; ++pass) {
-        multidot<VT>(V.p, vstride, j + 1, Ww.p, D, nb, hb.p, k + 1, 0, false, partial, s);
-        update_kernel<VT><<<grid_for(D * nb), 256, 0, s>>>(V.p, vstride, j + 1, Ww.p, D, nb, hb.p, k + 1, 0, -1.0);
-        GFCC_LAUNCH_CHECK();
-        add_h_kernel<<<(nb * (j + 1) + 255) / 256, 256, 0, s>>>(hb.p, k + 1, H.p + (long long)j * (k + 1),
-                                                                (k + 1) * k, j + 1, nb, pass == 0 ? 0 : 1);
-        GFCC_LAUNCH_CHECK();
+      // CGS with one re-orthogonalisation: h1 = V^H w, w -= V h1, h2 = V^H w, w -= V h2; H[:, j] = h1 + h2.
+      // With an FP32 basis of at most MD_MAXV vectors this takes three sweeps: h1; the first update with
+      // h2 fused; the second update with ||w||^2 fused.
+      const int nv = j + 1;
+      bool fused = false;
+      if constexpr (sizeof(VT) == sizeof(cuFloatComplex)) {
+        if (nv <= MD_MAXV) {
+          fused = true;
+          const long long rows = std::max<long long>(256, (D + 255) / 256);
+          const int nchunk = (int)((D + rows - 1) / rows);
+          dim3 grid((nb + MD_TX - 1) / MD_TX, nchunk);
+          multidot<VT>(V.p, vstride, nv, Ww.p, D, nb, hb.p, k + 1, 0, false, partial, s);
+          add_h_kernel<<<(nb * nv + 255) / 256, 256, 0, s>>>(hb.p, k + 1, H.p + (long long)j * (k + 1), (k + 1) * k, nv,
+                                                             nb, 0);
+          GFCC_LAUNCH_CHECK();
+          partial.alloc((long long)nchunk * nv * nb);
+          update_dot_kernel<VT><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(V.p, vstride, nv, Ww.p, D, nb, rows, hb.p, k + 1,
+                                                                     partial.p);
+          GFCC_LAUNCH_CHECK();
+          reduce_partial_kernel<<<(nv * nb + 255) / 256, 256, 0, s>>>(partial.p, nchunk, nv, nb, hb.p, k + 1, 0, 0);
+          GFCC_LAUNCH_CHECK();
+          add_h_kernel<<<(nb * nv + 255) / 256, 256, 0, s>>>(hb.p, k + 1, H.p + (long long)j * (k + 1), (k + 1) * k, nv,
+                                                             nb, 1);
+          GFCC_LAUNCH_CHECK();
+          update_norm_kernel<VT><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(V.p, vstride, nv, Ww.p, D, nb, rows, hb.p, k + 1,
+                                                                      partial.p);
+          GFCC_LAUNCH_CHECK();
+          reduce_partial_kernel<<<(nb + 255) / 256, 256, 0, s>>>(partial.p, nchunk, 1, nb, tmpc.p, 1, 0, 0);
+          GFCC_LAUNCH_CHECK();
+          finalize_norm_kernel<<<(nb + 255) / 256, 256, 0, s>>>(tmpc.p, nb, nrm.p);
+          GFCC_LAUNCH_CHECK();
+        }
       }
-      col_norms<VT>(Ww.p, D, nb, nrm.p, partial, tmpc, s);
+      if (!fused) {
+        for (int pass = 0; pass < 2; ++pass) {
+          multidot<VT>(V.p, vstride, nv, Ww.p, D, nb, hb.p, k + 1, 0, false, partial, s);
+          update_kernel<VT><<<grid_for(D * nb), 256, 0, s>>>(V.p, vstride, nv, Ww.p, D, nb, hb.p, k + 1, 0, -1.0);
+          GFCC_LAUNCH_CHECK();
+          add_h_kernel<<<(nb * nv + 255) / 256, 256, 0, s>>>(hb.p, k + 1, H.p + (long long)j * (k + 1), (k + 1) * k,
+                                                             nv, nb, pass == 0 ? 0 : 1);
+          GFCC_LAUNCH_CHECK();
+        }
+        col_norms<VT>(Ww.p, D, nb, nrm.p, partial, tmpc, s);
+      }
       scale_cols_kernel<VT, VT><<<grid_for(D * nb), 256, 0, s>>>(Ww.p, Vn, nrm.p, D, nb);
       GFCC_LAUNCH_CHECK();
       GFCC_CUDA(cudaMemsetAsync(nlive.p, 0, sizeof(int), s));

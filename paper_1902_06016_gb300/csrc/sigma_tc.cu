@@ -25,30 +25,32 @@ int grid_for(long long n) {
 
 __device__ __forceinline__ int pair_of(int i, int j) { return j * (j - 1) / 2 + i; }
 __device__ __forceinline__ void unpair(int p, int& i, int& j) {
-  int jj = (int)floor((1.0 + sqrt(1.0 + 8.0 * (double)p)) * 0.5);
+  // FP32 estimate (GB300's FP64 pipe is narrow), corrected to the exact integer below
+  int jj = (int)floorf((1.0f + sqrtf(1.0f + 8.0f * (float)p)) * 0.5f);
   while (jj * (jj - 1) / 2 > p) --jj;
   while ((jj + 1) * jj / 2 <= p) ++jj;
   j = jj;
   i = p - jj * (jj - 1) / 2;
 }
 
-// complex vector element read as double precision, and written from double precision
-__device__ __forceinline__ cplx ld2(const cplx& x) { return x; }
-__device__ __forceinline__ cplx ld2(const cuFloatComplex& x) { return make_cuDoubleComplex(x.x, x.y); }
-__device__ __forceinline__ void st2(cplx& y, double re, double im) { y = make_cuDoubleComplex(re, im); }
-__device__ __forceinline__ void st2(cuFloatComplex& y, double re, double im) { y = make_cuFloatComplex((float)re, (float)im); }
+// real type of a complex vector element: the FP32 Krylov path keeps all its arithmetic in FP32
+template <typename VT> struct VReal;
+template <> struct VReal<cplx> { using type = double; };
+template <> struct VReal<cuFloatComplex> { using type = float; };
 
 // element conversion (round to nearest)
 template <TcKind K> struct Elem;
 template <> struct Elem<TcKind::BF16> {
   using T = __nv_bfloat16;
   __device__ static T cvt(double x) { return __double2bfloat16(x); }
+  __device__ static T cvt(float x) { return __float2bfloat16_rn(x); }
 };
 template <> struct Elem<TcKind::TF32> {
   using T = float;
-  __device__ static T cvt(double x) {
+  __device__ static T cvt(double x) { return cvt((float)x); }
+  __device__ static T cvt(float x) {
     uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)x));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
   }
 };
@@ -93,9 +95,10 @@ __global__ void prep_ring_kernel(const VT* __restrict__ X, int o, int v, int nb,
   const long long total = rows * kpad;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
+    using R = typename VReal<VT>::type;
     long long n = t / kpad;
     int k = (int)(t % kpad);
-    double val = 0.0;
+    R val = R(0);
     if (k < o * v) {
       int r = (int)(n & 1);
       long long jc = n >> 1;
@@ -103,8 +106,8 @@ __global__ void prep_ring_kernel(const VT* __restrict__ X, int o, int v, int nb,
       int m = k / v, e = k % v;
       if (m != j) {
         int lo = min(m, j), hi = max(m, j);
-        cplx x = ld2(X[((long long)o + (long long)pair_of(lo, hi) * v + e) * nb + c]);
-        double comp = r ? x.y : x.x;
+        const VT x = X[((long long)o + (long long)pair_of(lo, hi) * v + e) * nb + c];
+        const R comp = r ? x.y : x.x;
         val = (m < j) ? comp : -comp;
       }
     }
@@ -119,14 +122,15 @@ __global__ void prep_oooo_kernel(const VT* __restrict__ X, int o, int v, int P, 
   const long long total = rows * kpad;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
+    using R = typename VReal<VT>::type;
     long long n = t / kpad;
     int k = (int)(t % kpad);
-    double val = 0.0;
+    R val = R(0);
     if (k < P) {
       int r = (int)(n & 1);
       long long ac = n >> 1;
       int c = (int)(ac % nb), a = (int)(ac / nb);
-      cplx x = ld2(X[((long long)o + (long long)k * v + a) * nb + c]);
+      const VT x = X[((long long)o + (long long)k * v + a) * nb + c];
       val = r ? x.y : x.x;
     }
     B[t] = E::cvt(val);
@@ -139,12 +143,13 @@ __global__ void prep_up_kernel(const VT* __restrict__ X, int o, long long Pv, in
   const long long total = 2LL * nb * kpad;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
+    using R = typename VReal<VT>::type;
     long long n = t / kpad;
     long long k = t % kpad;
-    double val = 0.0;
+    R val = R(0);
     if (k < Pv) {
       int r = (int)(n & 1), c = (int)(n >> 1);
-      cplx x = ld2(X[((long long)o + k) * nb + c]);
+      const VT x = X[((long long)o + k) * nb + c];
       val = r ? x.y : x.x;
     }
     B[t] = E::cvt(val);
@@ -166,13 +171,14 @@ __global__ void prep_down_kernel(const U* __restrict__ up, long long ldu, const 
   const long long total = 2LL * nb * kpad;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
+    using R = typename VReal<VT>::type;
     int n = (int)(t / kpad);
     int k = (int)(t % kpad);
-    double val = 0.0;
+    R val = R(0);
     if (k < v) {
-      val = up[(long long)k * ldu + n];
+      val = (R)up[(long long)k * ldu + n];
     } else if (k < v + o) {
-      cplx x = ld2(X[(long long)(k - v) * nb + (n >> 1)]);
+      const VT x = X[(long long)(k - v) * nb + (n >> 1)];
       val = (n & 1) ? x.y : x.x;
     }
     B[t] = E::cvt(val);
@@ -188,36 +194,38 @@ __global__ void combine_lp_kernel(const VT* __restrict__ X, VT* __restrict__ Y, 
   const long long ldct = 2LL * o * nb;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
+    using R = typename VReal<VT>::type;
     const int c = (int)(t % nb);
     const long long nu = t / nb;
-    cplx x = ld2(X[t]);
-    double dre = diag[nu], dim = 0.0;
-    if (shift) { dre += shift[c].x; dim = shift[c].y; }
-    double yr = dre * x.x - dim * x.y;
-    double yi = dre * x.y + dim * x.x;
+    const VT x = X[t];
+    R dre = (R)diag[nu], dim = R(0);
+    if (shift) { dre += (R)shift[c].x; dim = (R)shift[c].y; }
+    R yr = dre * x.x - dim * x.y;
+    R yi = dre * x.y + dim * x.x;
     if (nu < o) {
       const int i = (int)nu;
-      yr += up[(long long)(v + i) * ldu + 2 * c];
-      yi += up[(long long)(v + i) * ldu + 2 * c + 1];
+      yr += (R)up[(long long)(v + i) * ldu + 2 * c];
+      yi += (R)up[(long long)(v + i) * ldu + 2 * c + 1];
       for (int m = 0; m < o; ++m) {
-        double a = A11[(long long)i * o + m];
-        cplx xm = ld2(X[(long long)m * nb + c]);
+        const R a = (R)A11[(long long)i * o + m];
+        const VT xm = X[(long long)m * nb + c];
         yr += a * xm.x;
         yi += a * xm.y;
       }
     } else {
       const long long row = nu - o;
-      yr += C2[row * 2 * nb + 2 * c];
-      yi += C2[row * 2 * nb + 2 * c + 1];
+      yr += (R)C2[row * 2 * nb + 2 * c];
+      yi += (R)C2[row * 2 * nb + 2 * c + 1];
       int pij = (int)(row / v), a = (int)(row % v);
       int i, j;
       unpair(pij, i, j);
       const F* c1 = CT + ((long long)a * o + i) * ldct + ((long long)j * nb + c) * 2;
       const F* c2 = CT + ((long long)a * o + j) * ldct + ((long long)i * nb + c) * 2;
-      yr += (double)c1[0] - (double)c2[0];
-      yi += (double)c1[1] - (double)c2[1];
+      yr += (R)c1[0] - (R)c2[0];
+      yi += (R)c1[1] - (R)c2[1];
     }
-    st2(Y[t], yr, yi);
+    Y[t].x = yr;
+    Y[t].y = yi;
   }
 }
 

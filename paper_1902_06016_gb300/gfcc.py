@@ -53,6 +53,7 @@ PROTOTYPES = {
     "gfcc_vectors": (C.c_int, [_vp, _vp, C.c_int, C.c_int, _vp, C.c_int]),
     "gfcc_solve_full": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, C.c_int, _vp, _vp, _vp,
                                   C.c_int, C.POINTER(Stats)]),
+    "gfcc_green_derivatives": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, C.c_int, _vp, _vp, _vp]),
     "gfcc_mor_build": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, C.c_int]),
     "gfcc_mor_refine": (C.c_int, [_vp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, _ip, _dp]),
     "gfcc_mor_eval": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp]),
@@ -267,6 +268,20 @@ class Context:
         stats = SolveStats(st.sigma_calls, st.sigma_cols, st.gmres_iters, st.restarts, st.max_rel_res,
                            st.not_converged)
         return {"G": G, "A": A, "X": X, "stats": stats, "converged": rc == 0}
+
+    def green_derivatives(self, omegas, eta, orbitals, qorb=None):
+        """(G, dG/dw, dG/deta), each [nw, np, nq] complex, from forward and adjoint solves."""
+        w = _c64(omegas)
+        porb = _ints(orbitals)
+        q = _ints(qorb) if qorb is not None else None
+        nq = len(q) if q is not None else len(porb)
+        shape = (len(w), len(porb), nq)
+        G = np.empty(shape, dtype=np.complex128)
+        dw = np.empty(shape, dtype=np.complex128)
+        de = np.empty(shape, dtype=np.complex128)
+        self._check(self._lib.gfcc_green_derivatives(self._h, _ptr(w), len(w), float(eta), _ptr(porb), len(porb),
+                                                     _ptr(q), nq, _ptr(G), _ptr(dw), _ptr(de)))
+        return G, dw, de
 
     def mor_build(self, seeds, eta, orbitals, qorb=None):
         s = _c64(seeds)

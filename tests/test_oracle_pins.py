@@ -199,3 +199,24 @@ def test_generator_blocks_are_slices_of_the_full_tensor():
     assert np.array_equal(inp.oovv, g[:o, :o, o:, o:])
     assert np.array_equal(inp.ovov, g[:o, o:, :o, o:])
     assert np.array_equal(inp.ovvv, g[:o, o:, o:, o:])
+
+
+def test_green_derivatives_match_finite_differences():
+    """dG/dw = -y^T x and dG/deta = i y^T x against central differences of the dense solves
+    (step 1e-5, error O(h^2))."""
+    from oracle import grad
+    inp = synth.make_inputs(4, 8, 1001)
+    hb = hbar.build(inp)
+    M = sg.dense_matrix(hb)
+    B, C = bc.b_vectors(inp, range(6)), bc.c_vectors(inp, range(6))
+    ws = np.array([-0.9, -0.55, -0.2])
+    eta, h = 0.02, 1e-5
+    G, dw, de = grad.derivatives(M, B, C, ws, eta)
+    Gp = sv.green(C, sv.dense_solve(M, B, ws + h, eta))
+    Gm = sv.green(C, sv.dense_solve(M, B, ws - h, eta))
+    assert np.abs((Gp - Gm) / (2 * h) - dw).max() <= 1e-6 * np.abs(dw).max()
+    Gp = sv.green(C, sv.dense_solve(M, B, ws, eta + h))
+    Gm = sv.green(C, sv.dense_solve(M, B, ws, eta - h))
+    assert np.abs((Gp - Gm) / (2 * h) - de).max() <= 1e-6 * np.abs(de).max()
+    # G itself is the forward product
+    assert np.abs(G - sv.green(C, sv.dense_solve(M, B, ws, eta))).max() <= 1e-12 * np.abs(G).max()
