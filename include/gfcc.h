@@ -192,10 +192,14 @@ int gfcc_tc_gemm_noalloc(int precision, const double* A, const double* B, int M,
 /* Number of CUDA kernels launched by this library since it was loaded (all contexts). */
 long long gfcc_launch_count(void);
 
-/* Turn per-launch CUDA-event timing of the GEMM kernel classes on (enable = 1) or off, clearing
- * earlier records. Class 0: tcgen05 GEMM with tf32/bf16-rounded operands (inner solves);
- * class 1: FP64 SIMT GEMM; class 2: tcgen05 GEMM on exact bf16 slices (FP64-accurate products).
- * Events are recorded on the stream each kernel is launched on. */
+/* Turn per-launch CUDA-event timing of the GEMM kernel classes and of the pipeline phases on
+ * (enable = 1) or off, clearing earlier records. Kernel classes: 0 tcgen05 GEMM with tf32/bf16-
+ * rounded operands (inner solves); 1 FP64 SIMT GEMM; 2 tcgen05 GEMM on exact bf16 slices
+ * (FP64-accurate products). Phases (whole regions, nested ones counted in both): 3 low-precision
+ * sigma; 4 FP64-accurate sigma; 5 Arnoldi orthogonalisation and updates; 6 MOR orthonormalisation
+ * and projections; 7 reduced-model evaluation; 8 H-bar build; 9 column-by-column Gram-Schmidt
+ * inside new blocks; 10 extension of the residual basis. Events are recorded on the stream each
+ * region is launched on. */
 int gfcc_profile(int enable);
 
 /* Sum over the recorded launches of class cls: number of launches, device milliseconds (CUDA

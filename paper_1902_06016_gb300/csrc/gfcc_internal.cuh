@@ -51,7 +51,9 @@ enum ProfClass {
   PROF_MOR_ORTHO = 6,    // subspace orthonormalisation and projections
   PROF_MOR_EVAL = 7,     // Hessenberg reduction and per-frequency reduced solves
   PROF_INIT = 8,         // H-bar build, b and c vectors
-  PROF_NCLASS = 9
+  PROF_MOR_PANEL = 9,    // column-by-column Gram-Schmidt inside the panels of a new block
+  PROF_MOR_BASIS = 10,   // extension of the orthonormal residual basis Q
+  PROF_NCLASS = 11
 };
 struct ProfScope {   // records CUDA events around one launch on stream s when profiling is on
   int cls;

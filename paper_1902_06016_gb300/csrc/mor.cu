@@ -15,6 +15,7 @@
 // * Residual estimate for refinement: r = (w - i eta) S y + Z y - b is orthogonal to S (Galerkin),
 //   so ||r||^2 = y^H (Z^H Z - Hhat^H Hhat) y - 2 Re y^H (Z^H b - Hhat^H bhat) + ||b||^2 - ||bhat||^2.
 #include "gfcc_internal.cuh"
+#include "ozaki.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -29,75 +30,6 @@ int grid_for(long long n) {
 
 __device__ __forceinline__ cplx cz() { return make_cuDoubleComplex(0.0, 0.0); }
 
-// ---- column operations on a batch-minor block Y[nu][c] (ld = nc) -------------------------------
-// partial[chunk][i] = sum_{nu in chunk} conj(Y[nu][i]) Y[nu][j], i < j
-__global__ void rowdot_kernel(const cplx* __restrict__ Y, int nc, long long D, int j, long long rows,
-                              cplx* __restrict__ partial) {
-  const long long r0 = blockIdx.y * rows, r1 = min(D, r0 + rows);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= j) return;
-  cplx acc = cz();
-  for (long long nu = r0; nu < r1; ++nu) {
-    cplx a = Y[nu * nc + i], b = Y[nu * nc + j];
-    acc.x += a.x * b.x + a.y * b.y;
-    acc.y += a.x * b.y - a.y * b.x;
-  }
-  partial[(long long)blockIdx.y * j + i] = acc;
-}
-__global__ void rowdot_reduce_kernel(const cplx* __restrict__ partial, int nchunk, int j, cplx* __restrict__ h) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= j) return;
-  cplx s = cz();
-  for (int k = 0; k < nchunk; ++k) { s.x += partial[(long long)k * j + i].x; s.y += partial[(long long)k * j + i].y; }
-  h[i] = s;
-}
-// Y[nu][j] -= sum_{i<j} Y[nu][i] h[i] (and the same for MY): one warp per row
-__global__ void rowupdate_kernel(cplx* __restrict__ Y, cplx* __restrict__ MY, int nc, long long D, int j,
-                                 const cplx* __restrict__ h) {
-  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= D) return;
-  cplx s1 = cz(), s2 = cz();
-  for (int i = lane; i < j; i += 32) {
-    cplx hh = h[i];
-    cplx a = Y[warp * nc + i];
-    s1.x += a.x * hh.x - a.y * hh.y; s1.y += a.x * hh.y + a.y * hh.x;
-    if (MY) {
-      cplx b = MY[warp * nc + i];
-      s2.x += b.x * hh.x - b.y * hh.y; s2.y += b.x * hh.y + b.y * hh.x;
-    }
-  }
-  for (int off = 16; off > 0; off >>= 1) {
-    s1.x += __shfl_down_sync(0xffffffffu, s1.x, off); s1.y += __shfl_down_sync(0xffffffffu, s1.y, off);
-    s2.x += __shfl_down_sync(0xffffffffu, s2.x, off); s2.y += __shfl_down_sync(0xffffffffu, s2.y, off);
-  }
-  if (lane == 0) {
-    Y[warp * nc + j].x -= s1.x; Y[warp * nc + j].y -= s1.y;
-    if (MY) { MY[warp * nc + j].x -= s2.x; MY[warp * nc + j].y -= s2.y; }
-  }
-}
-// partial sums of |Y[nu][j]|^2
-__global__ void colnorm_kernel(const cplx* __restrict__ Y, int nc, long long D, int j, double* __restrict__ out) {
-  __shared__ double red[256];
-  double s = 0.0;
-  for (long long nu = blockIdx.x * (long long)blockDim.x + threadIdx.x; nu < D; nu += (long long)gridDim.x * blockDim.x) {
-    cplx a = Y[nu * nc + j];
-    s += a.x * a.x + a.y * a.y;
-  }
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
-}
-__global__ void colscale_kernel(cplx* __restrict__ Y, cplx* __restrict__ MY, int nc, long long D, int j, double s) {
-  for (long long nu = blockIdx.x * (long long)blockDim.x + threadIdx.x; nu < D; nu += (long long)gridDim.x * blockDim.x) {
-    Y[nu * nc + j].x *= s; Y[nu * nc + j].y *= s;
-    if (MY) { MY[nu * nc + j].x *= s; MY[nu * nc + j].y *= s; }
-  }
-}
 // dst[nu][off + k] = src[nu][cols[k]]
 __global__ void append_cols_kernel(const cplx* __restrict__ src, int lds, const int* __restrict__ cols, int nk,
                                    cplx* __restrict__ dst, int ldd, int off, long long D) {
@@ -356,12 +288,6 @@ __global__ void __launch_bounds__(256) eval_kernel(EvalArgs a) {
 // ------------------------------------------------------------------------------------------------
 namespace {
 
-__global__ void add_cols_kernel(cplx* __restrict__ T, int ldt, int col, const cplx* __restrict__ h, int n) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) { T[i + (long long)col * ldt].x += h[i].x; T[i + (long long)col * ldt].y += h[i].y; }
-}
-__global__ void set_entry_kernel(cplx* __restrict__ T, long long idx, double v) { T[idx] = make_cuDoubleComplex(v, 0.0); }
-
 // reallocate a batch-minor [rows][old_cap] block as [rows][new_cap] keeping ncols columns
 void regrow_rows(DBuf<cplx>& b, long long rows, int old_cap, int new_cap, int ncols, cudaStream_t s) {
   DBuf<cplx> nb2;
@@ -387,90 +313,303 @@ void regrow_cm(DBuf<cplx>& b, int old_ld, int new_ld, int alloc_cols, int nrows,
   std::swap(b.n, nb2.n);
 }
 
-// Orthonormalise the nc columns of Y ([D][nc] batch-minor) against the n_cur columns of the basis
-// Bs ([D][cap]) by two block CGS passes, then against each other column by column (two passes),
-// dropping a column whose norm falls below drop_tol of its norm before. The same linear operations
-// are applied to MY when it is non-null. On return the kept columns of Y are orthonormal (dropped ones
-// are zero); Cold (device, n_cur x nc col-major, ld n_cur) and T (device, nc x nc col-major) hold the
-// coefficients y_j = Bs Cold[:, j] + sum_i T[i, j] ynew_i when the pointers are non-null.
-std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cplx* Y, cplx* MY, const cplx* MBs,
-                             int nc, cplx* Cold, cplx* T) {
-  cudaStream_t s = c->stream;
-  const long long D = c->D;
-  const int nblk = 304;
-  DBuf<double> nparts;
-  nparts.alloc(nblk);
-  auto colnorm = [&](int j) {
-    colnorm_kernel<<<nblk, 256, 0, s>>>(Y, nc, D, j, nparts.p);
-    GFCC_LAUNCH_CHECK();
-    std::vector<double> hp(nblk);
-    GFCC_CUDA(cudaMemcpyAsync(hp.data(), nparts.p, sizeof(double) * nblk, cudaMemcpyDeviceToHost, s));
-    GFCC_CUDA(cudaStreamSynchronize(s));
+// FP64 arithmetic runs on a narrow pipe on this GPU: every product of the orthonormalisation above a
+// small size goes to the exact-slice tensor-core GEMM (7 slices, 48 bits per row).
+void fp64_accurate_zgemm(const ZGemmDesc& g, cudaStream_t s) {
+  if ((double)g.M * (double)g.N * (double)g.K >= (double)(1 << 22) && g.batch == 1) zgemm_oz(g, 7, s);
+  else zgemm(g, s);
+}
+
+// ---- panel kernels: column-wise CGS2 inside a panel of at most PB columns -----------------------
+constexpr int PB = 32;            // panel width (one lane per panel column)
+constexpr int PTY = 8;            // warps per block, each sweeping its own rows
+
+// out[c] (partial[chunk][c]) = sum_{nu in chunk} |Y[nu][c]|^2 for c < nc; block (32, PTY)
+__global__ void colnorms_partial_kernel(const cplx* __restrict__ Y, int nc, long long D, long long rows,
+                                        double* __restrict__ partial) {
+  __shared__ double red[PTY][32];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  const long long r0 = blockIdx.y * rows, r1 = min(D, r0 + rows);
+  double acc = 0.0;
+  if (c < nc)
+    for (long long nu = r0 + threadIdx.y; nu < r1; nu += PTY) {
+      const cplx a = Y[nu * nc + c];
+      acc += a.x * a.x + a.y * a.y;
+    }
+  red[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < nc) {
     double t = 0.0;
-    for (double x : hp) t += x;
-    return std::sqrt(t);
-  };
-  std::vector<double> n0(nc);
-  for (int j = 0; j < nc; ++j) n0[j] = colnorm(j);
-  if (T) GFCC_CUDA(cudaMemsetAsync(T, 0, sizeof(cplx) * nc * nc, s));
-  if (n_cur > 0) {
-    DBuf<cplx> Cf;
-    Cf.alloc((long long)n_cur * nc);
-    if (Cold) GFCC_CUDA(cudaMemsetAsync(Cold, 0, sizeof(cplx) * n_cur * nc, s));
-    for (int pass = 0; pass < 2; ++pass) {
-      ZGemmDesc g;   // Cf(i, j) = sum_nu conj(Bs[nu][i]) Y[nu][j]   (row-major [n_cur][nc])
-      g.M = n_cur; g.N = nc; g.K = (int)D;
-      g.A = Bs; g.sam = 1; g.sak = cap; g.conjA = true;
-      g.B = Y; g.sbk = nc; g.sbn = 1;
-      g.C = Cf.p; g.scm = nc; g.scn = 1;
-      zgemm(g, s);
-      ZGemmDesc u;   // Y -= Bs Cf
-      u.M = (int)D; u.N = nc; u.K = n_cur;
-      u.A = Bs; u.sam = cap; u.sak = 1;
-      u.B = Cf.p; u.sbk = nc; u.sbn = 1;
-      u.C = Y; u.scm = nc; u.scn = 1;
-      u.alpha = make_cuDoubleComplex(-1.0, 0.0); u.beta = make_cuDoubleComplex(1.0, 0.0);
-      zgemm(u, s);
-      if (MY) { u.A = MBs; u.C = MY; zgemm(u, s); }
-      if (Cold) {   // Cold (col-major, ld n_cur) += Cf (row-major [n_cur][nc])
-        int dims[3] = {n_cur, nc, 2};
-        int pm[3] = {1, 0, 2};
-        permute(reinterpret_cast<const double*>(Cf.p), dims, 3, pm, reinterpret_cast<double*>(Cold), 1.0, 1.0, s);
+    for (int k = 0; k < PTY; ++k) t += red[k][threadIdx.x];
+    partial[(long long)blockIdx.y * nc + c] = t;
+  }
+}
+__global__ void colnorms_reduce_kernel(const double* __restrict__ partial, int nchunk, int nc, double* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  double t = 0.0;
+  for (int k = 0; k < nchunk; ++k) t += partial[(long long)k * nc + c];
+  out[c] = sqrt(t);
+}
+
+// partial[chunk][i] = sum_{nu in chunk} conj(Y[nu][c0 + i]) Y[nu][j] for i < n (n < PB); block (32, PTY)
+__global__ void pdot_kernel(const cplx* __restrict__ Y, int nc, long long D, int c0, int n, int j, long long rows,
+                            cplx* __restrict__ partial) {
+  __shared__ cplx red[PTY][32];
+  const int i = threadIdx.x;
+  const long long r0 = blockIdx.y * rows, r1 = min(D, r0 + rows);
+  cplx acc = cz();
+  if (i < n)
+#pragma unroll 4
+    for (long long nu = r0 + threadIdx.y; nu < r1; nu += PTY) {
+      const cplx a = Y[nu * nc + c0 + i], b = Y[nu * nc + j];
+      acc.x += a.x * b.x + a.y * b.y;
+      acc.y += a.x * b.y - a.y * b.x;
+    }
+  red[threadIdx.y][i] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && i < n) {
+    cplx t = cz();
+    for (int k = 0; k < PTY; ++k) { t.x += red[k][i].x; t.y += red[k][i].y; }
+    partial[(long long)blockIdx.y * PB + i] = t;
+  }
+}
+// h[i] = sum_chunk partial[chunk][i]; T[c0 + i][j] += h[i] (T col-major, ld ldt) when T is non-null
+// (block (32, PTY))
+__global__ void preduce_kernel(const cplx* __restrict__ partial, int nchunk, int n, cplx* __restrict__ h,
+                               cplx* __restrict__ T, int ldt, int c0, int j) {
+  __shared__ cplx red[PTY][32];
+  const int i = threadIdx.x;
+  cplx t = cz();
+  if (i < n)
+    for (int k = threadIdx.y; k < nchunk; k += PTY) {
+      t.x += partial[(long long)k * PB + i].x;
+      t.y += partial[(long long)k * PB + i].y;
+    }
+  red[threadIdx.y][i] = t;
+  __syncthreads();
+  if (threadIdx.y == 0 && i < n) {
+    for (int k = 1; k < PTY; ++k) { t.x += red[k][i].x; t.y += red[k][i].y; }
+    h[i] = t;
+    if (T) { T[c0 + i + (long long)j * ldt].x += t.x; T[c0 + i + (long long)j * ldt].y += t.y; }
+  }
+}
+// Y[nu][j] -= sum_{i<n} Y[nu][c0 + i] h[i] (and MY alike); then, for mode 0, the partial dot products
+// of the updated column with the panel columns (as pdot_kernel) or, for mode 1, partial[chunk][0].x =
+// sum |Y[nu][j]|^2. Lane i holds panel column c0 + i; each warp takes PU rows per step (independent
+// shuffle reductions in flight), block (32, PTY).
+constexpr int PU = 4;
+__global__ void pupdate_kernel(cplx* __restrict__ Y, cplx* __restrict__ MY, int nc, long long D, int c0, int n,
+                               int j, long long rows, const cplx* __restrict__ h, int mode,
+                               cplx* __restrict__ partial) {
+  __shared__ cplx red[PTY][32];
+  const int i = threadIdx.x;
+  const long long r0 = blockIdx.y * rows, r1 = min(D, r0 + rows);
+  const cplx hi = i < n ? h[i] : cz();
+  cplx acc = cz();
+  for (long long base = r0 + (long long)threadIdx.y * PU; base < r1; base += (long long)PTY * PU) {
+    cplx a[PU], y[PU];
+    double sx[PU], sy[PU];
+#pragma unroll
+    for (int u = 0; u < PU; ++u) {
+      const long long nu = base + u;
+      const bool in = nu < r1;
+      a[u] = (in && i < n) ? Y[nu * nc + c0 + i] : cz();
+      y[u] = in ? Y[nu * nc + j] : cz();   // read by every lane before lane 0 writes it (the shuffles order them)
+      sx[u] = a[u].x * hi.x - a[u].y * hi.y;
+      sy[u] = a[u].x * hi.y + a[u].y * hi.x;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+      for (int u = 0; u < PU; ++u) {
+        sx[u] += __shfl_xor_sync(0xffffffffu, sx[u], off);
+        sy[u] += __shfl_xor_sync(0xffffffffu, sy[u], off);
       }
     }
-    GFCC_CUDA(cudaStreamSynchronize(s));
-  }
-  std::vector<int> kept;
-  DBuf<cplx> partial, h;
-  const long long rows = std::max<long long>(512, (D + 255) / 256);
-  const int nchunk = (int)((D + rows - 1) / rows);
-  partial.alloc((long long)nchunk * std::max(nc, 1));
-  h.alloc(std::max(nc, 1));
-  for (int j = 0; j < nc; ++j) {
-    if (j > 0) {
-      for (int pass = 0; pass < 2; ++pass) {
-        dim3 grid((j + 127) / 128, nchunk);
-        rowdot_kernel<<<grid, 128, 0, s>>>(Y, nc, D, j, rows, partial.p);
-        GFCC_LAUNCH_CHECK();
-        rowdot_reduce_kernel<<<(j + 127) / 128, 128, 0, s>>>(partial.p, nchunk, j, h.p);
-        GFCC_LAUNCH_CHECK();
-        rowupdate_kernel<<<(int)((D * 32 + 255) / 256), 256, 0, s>>>(Y, MY, nc, D, j, h.p);
-        GFCC_LAUNCH_CHECK();
-        if (T) {
-          add_cols_kernel<<<(j + 127) / 128, 128, 0, s>>>(T, nc, j, h.p, j);
-          GFCC_LAUNCH_CHECK();
+#pragma unroll
+    for (int u = 0; u < PU; ++u) {
+      y[u].x -= sx[u];
+      y[u].y -= sy[u];
+      if (i == 0 && base + u < r1) Y[(base + u) * nc + j] = y[u];
+    }
+    if (MY) {
+#pragma unroll
+      for (int u = 0; u < PU; ++u) {
+        const long long nu = base + u;
+        const cplx b = (nu < r1 && i < n) ? MY[nu * nc + c0 + i] : cz();
+        sx[u] = b.x * hi.x - b.y * hi.y;
+        sy[u] = b.x * hi.y + b.y * hi.x;
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int u = 0; u < PU; ++u) {
+          sx[u] += __shfl_xor_sync(0xffffffffu, sx[u], off);
+          sy[u] += __shfl_xor_sync(0xffffffffu, sy[u], off);
         }
       }
+      if (i == 0) {
+#pragma unroll
+        for (int u = 0; u < PU; ++u)
+          if (base + u < r1) { MY[(base + u) * nc + j].x -= sx[u]; MY[(base + u) * nc + j].y -= sy[u]; }
+      }
     }
-    double n1 = colnorm(j);
-    bool keep = n0[j] > 0.0 && n1 >= c->opts.drop_tol * n0[j];
-    colscale_kernel<<<grid_for(D), 256, 0, s>>>(Y, MY, nc, D, j, keep ? 1.0 / n1 : 0.0);
-    GFCC_LAUNCH_CHECK();
-    if (T && keep) set_entry_kernel<<<1, 1, 0, s>>>(T, (long long)j * nc + j, n1);
-    GFCC_LAUNCH_CHECK();
-    if (keep) kept.push_back(j);
+#pragma unroll
+    for (int u = 0; u < PU; ++u) {
+      if (mode == 0) {
+        acc.x += a[u].x * y[u].x + a[u].y * y[u].y;
+        acc.y += a[u].x * y[u].y - a[u].y * y[u].x;
+      } else if (i == 0) {
+        acc.x += y[u].x * y[u].x + y[u].y * y[u].y;
+      }
+    }
   }
+  red[threadIdx.y][i] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && (mode == 0 ? i < n : i == 0)) {
+    cplx t = cz();
+    for (int k = 0; k < PTY; ++k) { t.x += red[k][i].x; t.y += red[k][i].y; }
+    partial[(long long)blockIdx.y * PB + i] = t;
+  }
+}
+// n1 = sqrt(sum_chunk partial[chunk][0].x); keep column j when n0[j] > 0 and n1 >= drop_tol n0[j];
+// scale[j] = keep ? 1 / n1 : 0; T[j][j] = n1 when kept
+__global__ void pfinish_kernel(const cplx* __restrict__ partial, int nchunk, const double* __restrict__ n0, int j,
+                               double drop_tol, double* __restrict__ scale, int* __restrict__ keep,
+                               cplx* __restrict__ T, int ldt) {
+  __shared__ double red[256];
+  double t = 0.0;
+  for (int k = threadIdx.x; k < nchunk; k += blockDim.x) t += partial[(long long)k * PB].x;
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double n1 = sqrt(red[0]);
+    const bool k = n0[j] > 0.0 && n1 >= drop_tol * n0[j];
+    scale[j] = k ? 1.0 / n1 : 0.0;
+    keep[j] = k ? 1 : 0;
+    if (T && k) T[j + (long long)j * ldt] = make_cuDoubleComplex(n1, 0.0);
+  }
+}
+__global__ void pscale_kernel(cplx* __restrict__ Y, cplx* __restrict__ MY, int nc, long long D, int j,
+                              const double* __restrict__ scale) {
+  const double sc = scale[j];
+  for (long long nu = blockIdx.x * (long long)blockDim.x + threadIdx.x; nu < D; nu += (long long)gridDim.x * blockDim.x) {
+    Y[nu * nc + j].x *= sc; Y[nu * nc + j].y *= sc;
+    if (MY) { MY[nu * nc + j].x *= sc; MY[nu * nc + j].y *= sc; }
+  }
+}
+// T[i][c0 + j] += Cf[i][j] for i < rows, j < pb (Cf row-major [rows][pb], T col-major ld ldt)
+__global__ void add_block_kernel(cplx* __restrict__ T, int ldt, int c0, const cplx* __restrict__ Cf, int rows, int pb) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * pb) return;
+  const int i = t / pb, j = t % pb;
+  T[i + (long long)(c0 + j) * ldt].x += Cf[t].x;
+  T[i + (long long)(c0 + j) * ldt].y += Cf[t].y;
+}
+
+// Orthonormalise the nc columns of Y ([D][nc] batch-minor) against the n_cur columns of the basis
+// Bs ([D][cap]) and against each other, column by column in order: each column loses its components
+// along all earlier columns by classical Gram-Schmidt applied twice, and is kept when its norm after
+// that is >= drop_tol times its norm before, else zeroed. The same linear operations are applied to
+// MY when it is non-null (MBs being the matching block of Bs). Cold (device, n_cur x nc col-major,
+// ld n_cur) and T (device, nc x nc col-major) receive the coefficients
+// y_j = Bs Cold[:, j] + sum_i T[i, j] ynew_i when the pointers are non-null. Returns the kept columns.
+//
+// Blocking (the same projections in exact arithmetic, since the subspaces are mutually orthogonal):
+// two passes of block CGS against Bs; then panels of PB columns, each projected twice against the
+// finished earlier panels by two GEMMs per pass, and finally column by column inside the panel, whose
+// PB columns stay resident in L2. The keep decisions are taken on the device.
+std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cplx* Y, cplx* MY, const cplx* MBs,
+                             int nc, cplx* Cold, cplx* T) {
+  if (nc <= 0) return {};
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  // one chunk of rows per block: one wave of two PTY-warp blocks per SM (pupdate_kernel's registers)
+  const long long rows = std::max<long long>(64, (D + 152 * 2 - 1) / (152 * 2));
+  const int nchunk = (int)((D + rows - 1) / rows);
+  DBuf<double> n0, scale, npart;
+  DBuf<int> keep;
+  n0.alloc(nc);
+  scale.alloc(nc);
+  keep.alloc(nc);
+  npart.alloc((long long)nchunk * nc);
+  colnorms_partial_kernel<<<dim3((nc + 31) / 32, nchunk), dim3(32, PTY), 0, s>>>(Y, nc, D, rows, npart.p);
+  GFCC_LAUNCH_CHECK();
+  colnorms_reduce_kernel<<<(nc + 127) / 128, 128, 0, s>>>(npart.p, nchunk, nc, n0.p);
+  GFCC_LAUNCH_CHECK();
+  if (T) GFCC_CUDA(cudaMemsetAsync(T, 0, sizeof(cplx) * nc * nc, s));
+  DBuf<cplx> Cf;
+  Cf.alloc((long long)std::max(std::max(n_cur, nc), 1) * std::max(nc, 1));
+  auto block_cgs = [&](const cplx* Pb, int ldp, int np_, const cplx* MPb, int col0, int ncols, bool to_cold) {
+    // two passes: Cf (row-major [np_][ncols]) = Pb^H Y[:, col0:col0+ncols]; Y[:, col0:...] -= Pb Cf
+    for (int pass = 0; pass < 2; ++pass) {
+      ZGemmDesc g;
+      g.M = np_; g.N = ncols; g.K = (int)D;
+      g.A = Pb; g.sam = 1; g.sak = ldp; g.conjA = true;
+      g.B = Y + col0; g.sbk = nc; g.sbn = 1;
+      g.C = Cf.p; g.scm = ncols; g.scn = 1;
+      fp64_accurate_zgemm(g, s);
+      ZGemmDesc u;
+      u.M = (int)D; u.N = ncols; u.K = np_;
+      u.A = Pb; u.sam = ldp; u.sak = 1;
+      u.B = Cf.p; u.sbk = ncols; u.sbn = 1;
+      u.C = Y + col0; u.scm = nc; u.scn = 1;
+      u.alpha = make_cuDoubleComplex(-1.0, 0.0); u.beta = make_cuDoubleComplex(1.0, 0.0);
+      fp64_accurate_zgemm(u, s);
+      if (MY) { u.A = MPb; u.C = MY + col0; fp64_accurate_zgemm(u, s); }
+      if (to_cold) {
+        if (Cold) {   // Cold (col-major, ld n_cur) += Cf (row-major [n_cur][nc])
+          int dims[3] = {np_, ncols, 2};
+          int pm[3] = {1, 0, 2};
+          permute(reinterpret_cast<const double*>(Cf.p), dims, 3, pm, reinterpret_cast<double*>(Cold), 1.0, 1.0, s);
+        }
+      } else if (T) {
+        add_block_kernel<<<(np_ * ncols + 255) / 256, 256, 0, s>>>(T, nc, col0, Cf.p, np_, ncols);
+        GFCC_LAUNCH_CHECK();
+      }
+    }
+  };
+  if (n_cur > 0) {
+    if (Cold) GFCC_CUDA(cudaMemsetAsync(Cold, 0, sizeof(cplx) * n_cur * nc, s));
+    block_cgs(Bs, cap, n_cur, MBs, 0, nc, true);
+  }
+  DBuf<cplx> partial, h;
+  partial.alloc((long long)nchunk * PB);
+  h.alloc(PB);
+  const dim3 pgrid(1, nchunk), pblock(32, PTY);
+  for (int c0 = 0; c0 < nc; c0 += PB) {
+    const int pb = std::min(PB, nc - c0);
+    if (c0 > 0) block_cgs(Y, nc, c0, MY, c0, pb, false);
+    ProfScope pp(PROF_MOR_PANEL, 0.0, s);
+    for (int j = c0; j < c0 + pb; ++j) {
+      const int n = j - c0;
+      if (n > 0) {
+        pdot_kernel<<<pgrid, pblock, 0, s>>>(Y, nc, D, c0, n, j, rows, partial.p);
+        GFCC_LAUNCH_CHECK();
+        preduce_kernel<<<1, pblock, 0, s>>>(partial.p, nchunk, n, h.p, T, nc, c0, j);
+        GFCC_LAUNCH_CHECK();
+        pupdate_kernel<<<pgrid, pblock, 0, s>>>(Y, MY, nc, D, c0, n, j, rows, h.p, 0, partial.p);
+        GFCC_LAUNCH_CHECK();
+        preduce_kernel<<<1, pblock, 0, s>>>(partial.p, nchunk, n, h.p, T, nc, c0, j);
+        GFCC_LAUNCH_CHECK();
+      }
+      pupdate_kernel<<<pgrid, pblock, 0, s>>>(Y, MY, nc, D, c0, n, j, rows, h.p, 1, partial.p);
+      GFCC_LAUNCH_CHECK();
+      pfinish_kernel<<<1, 256, 0, s>>>(partial.p, nchunk, n0.p, j, c->opts.drop_tol, scale.p, keep.p, T, nc);
+      GFCC_LAUNCH_CHECK();
+      pscale_kernel<<<grid_for(D), 256, 0, s>>>(Y, MY, nc, D, j, scale.p);
+      GFCC_LAUNCH_CHECK();
+    }
+  }
+  std::vector<int> hk(nc);
+  GFCC_CUDA(cudaMemcpyAsync(hk.data(), keep.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
   GFCC_CUDA(cudaStreamSynchronize(s));
+  std::vector<int> kept;
+  for (int j = 0; j < nc; ++j)
+    if (hk[j]) kept.push_back(j);
   return kept;
 }
 
@@ -510,6 +649,7 @@ static void grow_basis(gfcc_ctx* c, int need) {
 static std::vector<cplx> basis_append(gfcc_ctx* c, cplx* Ynew, int nc) {
   MorState& ms = c->mor;
   cudaStream_t s = c->stream;
+  ProfScope prof(PROF_MOR_BASIS, 0.0, s);
   const long long D = c->D;
   const int qn0 = ms.qn;
   DBuf<cplx> Cold, T;

@@ -121,7 +121,7 @@ def profile(enable=True):
 
 
 def profile_read(cls):
-    """(launches, ms, flops) of kernel class cls (0 tensor-core GEMM, 1 FP64 SIMT GEMM)."""
+    """(launches, ms, flops) of kernel class or phase cls (numbering as in gfcc_profile's comment)."""
     n, ms, fl = C.c_longlong(), C.c_double(), C.c_double()
     rc = load().gfcc_profile_read(int(cls), C.byref(n), C.byref(ms), C.byref(fl))
     if rc != 0:
