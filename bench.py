@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--m-max", type=int, default=1700)
     ap.add_argument("--solve-tol", type=float, default=1e-8)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--full-points", type=int, default=4,
+                    help="output frequencies (plus the oracle's) also solved full-dimension in FP64 for comparison")
     ap.add_argument("--cpu-sample", type=int, default=2, help="(w, p) columns in the oracle sample")
     ap.add_argument("--mode", default="pipeline", choices=["pipeline", "sigma"],
                     help="pipeline: the whole MOR step (default); sigma: one batch of sigma applications")
@@ -101,6 +103,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the captured launches) of
+# the roofline kernel, from ncu captures summarised under profiles/; valid only while the kernel's
+# source file is unchanged (its SHA-256 is recorded with the figure).
+TRAFFIC = {}
+
+
+def _sha256(path):
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def measured_traffic(workload, cls):
+    t = TRAFFIC.get((workload, cls))
+    if not t:
+        return None
+    src = os.path.join(ROOT, "paper_1902_06016_gb300", "csrc", "tc_gemm.cu")
+    return t if os.path.exists(src) and _sha256(src) == t["tc_gemm_sha256"] else None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -136,14 +158,16 @@ def run_ours(args, rank, world):
 
     stream = torch.cuda.current_stream(dev)
 
-    def step(inputs, G_out, A_out):
+    def step(inputs, G_out, A_out, keep=False):
         ctx = Context(inputs, tol=args.solve_tol, precision=args.precision, stream=stream.cuda_stream)
         ctx.mor_build(seeds, eta, porb)
         ref = ctx.mor_refine(W["wmin"], W["wmax"], args.ngrid, args.mor_tol, args.m_max)
         ctx.mor_eval(omega_host, G=G_out, A=A_out)
         info = ctx.mor_info()
+        if keep:
+            return ref, info, ctx
         ctx.close()
-        return ref, info
+        return ref, info, None
 
     def barrier():
         if world > 1:
@@ -163,13 +187,13 @@ def run_ours(args, rank, world):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        ref, info = step(dev_inputs, G_dev, A_dev)
+        ref, info, _ = step(dev_inputs, G_dev, A_dev)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
     launches = G.launch_count() - l0
     dev_ms = ev0.elapsed_time(ev1) / args.steps
-    classes = {k: G.profile_read(k) for k in (0, 1, 2)}   # (launches, ms, flops)
+    classes = {k: G.profile_read(k) for k in (0, 1, 2, 11)}   # (launches, ms, flops)
     phase_names = {3: "sigma_lowprec", 4: "sigma_fp64_accurate", 5: "krylov_arnoldi", 6: "mor_orthonormalise",
                    7: "mor_eval", 8: "hbar_build", 9: "mor_panel_columns", 10: "mor_residual_basis"}
     phases = {phase_names[k]: round(G.profile_read(k)[1], 1) for k in phase_names}
@@ -178,17 +202,28 @@ def run_ours(args, rank, world):
 
     # end to end: host inputs, host outputs, copies inside the timed region
     e2e = None
+    kept = None
     if not args.no_e2e:
         G_host = np.empty((nw, o, o), dtype=np.complex128)
         A_host = np.empty(nw)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        step(inp, G_host, A_host)
+        _, _, kept = step(inp, G_host, A_host, keep=True)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         h2d = sum(getattr(inp, k).nbytes for k in ("eps", "oooo", "ooov", "oovv", "ovov", "ovvv", "t1", "t2", "l1", "l2"))
         e2e = {"value": nw * o / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(G_host.nbytes + A_host.nbytes)}
+
+    # untimed by the line's value: full-dimension FP64 solves at a subset of the output grid (plus the
+    # frequency the oracle sample uses), their own rate, and the reduced model's error against them
+    full = None
+    if args.full_points > 0 and rank == 0:
+        if kept is None:
+            _, _, kept = step(dev_inputs, G_dev, A_dev, keep=True)
+        full = full_compare(args, kept, grid, porb, eta, stream)
+    if kept is not None:
+        kept.close()
 
     # max over ranks
     if world > 1:
@@ -200,9 +235,10 @@ def run_ours(args, rank, world):
 
     peaks, peak_kind = measured_peaks()
     bf16 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-    names = {0: f"tc_gemm_kernel<{args.precision}> (inner low-precision sigma GEMMs)",
+    names = {0: f"tc_gemm_kernel<{args.precision}> (inner low-precision sigma GEMMs: up, oooo, down)",
              1: "gemm_kernel<double> (FP64 SIMT GEMM)",
-             2: "tc_gemm_kernel<bf16> on exact slices (FP64-accurate residual / projection GEMMs)"}
+             2: "tc_gemm_kernel<bf16, exact> on exact slices (FP64-accurate residual / projection GEMMs)",
+             11: f"tc_gemm_kernel<{args.precision}> ring-term GEMM of the inner sigma"}
     ratio0 = 0.5 if args.precision == "tf32" else 1.0
     kernels = {}
     for k, (n, ms, fl) in classes.items():
@@ -212,19 +248,24 @@ def run_ours(args, rank, world):
         if k == 1:
             kernels[names[k]] = {"bound": "alu", "launches": n, "ms": ms, "achieved": ach, "unit": "TFLOP/s"}
         else:
-            pk = bf16 * (ratio0 if k == 0 else 1.0)
+            pk = bf16 * (ratio0 if k in (0, 11) else 1.0)
             kernels[names[k]] = {"bound": "tensor", "launches": n, "ms": ms, "achieved": ach, "peak": pk,
                                  "unit": "TFLOP/s", "frac": ach / pk}
     roof = None
-    dom = max((k for k in classes if classes[k][0] > 0 and k != 1), key=lambda k: classes[k][1], default=None)
+    # the roofline kernel: the ring-term GEMM (the largest single GEMM of the hot path), else the
+    # tensor-core class with the most time
+    dom = 11 if classes[11][0] > 0 else max((k for k in classes if classes[k][0] > 0 and k != 1),
+                                            key=lambda k: classes[k][1], default=None)
     if dom is not None:
         n, ms, fl = classes[dom]
         ach = fl / (ms / 1e3) / 1e12
-        pk = bf16 * (ratio0 if dom == 0 else 1.0)
+        pk = bf16 * (ratio0 if dom in (0, 11) else 1.0)
+        tr = measured_traffic(args.workload, dom)
         roof = {"kernel": names[dom], "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                "frac": ach / pk, "traffic": None,
-                "peak_kind": f"{peak_kind} sustained bf16" + (f" x {ratio0} (tf32 rate)" if dom == 0 and ratio0 != 1 else ""),
-                "launches": n, "avg_launch_ms": ms / n}
+                "frac": ach / pk, "traffic": tr["bytes_per_launch"] if tr else None,
+                "traffic_source": tr["source"] if tr else "no ncu capture of the current kernel source",
+                "peak_kind": f"{peak_kind} sustained bf16" + (f" x {ratio0} (tf32 rate)" if dom in (0, 11) and ratio0 != 1 else ""),
+                "launches": n, "avg_launch_ms": ms / n, "flops_per_launch": fl / n}
     return inp, {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dev_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -235,7 +276,38 @@ def run_ours(args, rank, world):
                    "l2": "working set (operators >= 0.5 GB, Krylov bases) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "gemm_classes": kernels, "phases_ms": phases, "clocks": clk,
+        "full_fp64": full,
     }
+
+
+def full_compare(args, ctx, grid, porb, eta, stream):
+    """Full-dimension FP64-accurate GMRES-IR solves (inner and residual sigma on exact bf16 slices) at
+    full_points frequencies of the output grid plus the middle of the window; returns their G points/s
+    and the reduced model's A and G errors against them (normwise relative, max over the subset)."""
+    import torch
+    W = synth.WORKLOADS[args.workload]
+    nw = len(grid)
+    idx = np.unique(np.linspace(0, nw - 1, args.full_points).round().astype(int))
+    w_mid = 0.5 * (W["wmin"] + W["wmax"])
+    sub = np.concatenate([grid[idx], [w_mid]])
+    ctx.set_opts(tol=args.solve_tol, precision="fp64_tc")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = ctx.solve_full(sub, eta, porb)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    mor = ctx.mor_eval(sub)
+    Af, Gf = r["A"], r["G"]
+    st = r["stats"]
+    return {"value": len(sub) * len(porb) / (ms / 1e3), "unit": UNIT, "ms": ms, "n_omega": int(len(sub)),
+            "n_p": len(porb), "solver": "GMRES-IR, FP64-accurate inner and residual sigma (exact bf16 slices)",
+            "converged": bool(r["converged"]), "max_rel_res": st.max_rel_res, "gmres_iters": st.gmres_iters,
+            "mor_A_rel_err": float(np.abs(mor["A"] - Af).max() / np.abs(Af).max()),
+            "mor_G_rel_err": float(np.abs(mor["G"] - Gf).max() / np.abs(Gf).max()),
+            "omegas": "every %d-th point of the output grid and w = %.2f Ha" % (max(1, nw // args.full_points), w_mid),
+            "_G_mid": Gf[-1], "_G_mor_mid": mor["G"][-1]}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -263,7 +335,8 @@ def run_sigma(args):
         ctx.sigma(X, precision=args.precision, out=Y)
     e1.record(stream)
     torch.cuda.synchronize()
-    n, ms, fl = G.profile_read(0 if args.precision in ("tf32", "bf16") else 2)
+    n, ms, fl = G.profile_read(11 if args.precision in ("tf32", "bf16") else 2)
+    n0, ms0, fl0 = G.profile_read(0)
     G.profile(False)
     o, v = W["o"], W["v"]
     P = o * (o - 1) // 2
@@ -278,10 +351,12 @@ def run_sigma(args):
             "higher_is_better": True, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": args.workload, "nvec": args.nvec, "mode": "sigma"},
             "algorithmic_tflops": flop / (step_ms / 1e3) / 1e12,
-            "roofline": {"kernel": "tc_gemm_kernel", "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                         "frac": ach / pk if ach else None, "peak_kind": f"{kind} burst bf16" +
+            "roofline": {"kernel": "tc_gemm_kernel ring-term GEMM", "bound": "tensor", "achieved": ach, "peak": pk,
+                         "unit": "TFLOP/s", "frac": ach / pk if ach else None, "peak_kind": f"{kind} burst bf16" +
                          (" x 0.5 (tf32 rate)" if args.precision == "tf32" else ""), "launches": n,
-                         "avg_launch_ms": ms / n if n else None}}
+                         "avg_launch_ms": ms / n if n else None},
+            "other_gemms": {"launches": n0, "ms": ms0,
+                            "achieved": fl0 / (ms0 / 1e3) / 1e12 if ms0 else None}}
 
 
 def oracle_sample(args, ncols, inp=None):
@@ -298,10 +373,11 @@ def oracle_sample(args, ncols, inp=None):
     t0 = time.perf_counter()
     X, res = sv.gmres_solve(hb, B, w, W["eta"], tol=args.solve_tol)
     dt = time.perf_counter() - t0
+    Gq = sv.green(bc.c_vectors(inp, list(range(W["o"]))), X)[0]     # [ncols, o]: p = 0..ncols-1, q occupied
     return {"value": ncols / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"{ncols} full-dimension FP64 GMRES solves (tol {args.solve_tol}) at w = {w[0]} Ha, "
                       f"p = 0..{ncols - 1}, {args.workload}; H-bar build and input generation untimed",
-            "seconds": dt}
+            "seconds": dt, "_G": Gq}
 
 
 def run_reference(args):
@@ -337,11 +413,25 @@ def main():
         dist.init_process_group("nccl")
     inp, out = run_ours(args, rank, world)
     if rank == 0:
+        full = out.get("full_fp64")
         if args.cpu_sample > 0:
             try:
-                out["cpu_baseline"] = oracle_sample(args, args.cpu_sample, inp)
+                cb = oracle_sample(args, args.cpu_sample, inp)
+                Go = cb.pop("_G")
+                if full is not None:   # the GPU results at the oracle's frequency, p = 0..ncols-1
+                    k = Go.shape[0]
+                    scale = np.abs(Go).max()
+                    out["oracle_check"] = {
+                        "points": int(Go.size), "omega": 0.5 * (synth.WORKLOADS[args.workload]["wmin"] +
+                                                                synth.WORKLOADS[args.workload]["wmax"]),
+                        "full_fp64_G_rel_err": float(np.abs(full["_G_mid"][:k] - Go).max() / scale),
+                        "mor_G_rel_err": float(np.abs(full["_G_mor_mid"][:k] - Go).max() / scale)}
+                out["cpu_baseline"] = cb
             except Exception as e:  # the baseline must not hide the GPU line
                 out["cpu_baseline"] = {"error": str(e)}
+        if full is not None:
+            full.pop("_G_mid", None)
+            full.pop("_G_mor_mid", None)
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

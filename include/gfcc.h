@@ -65,7 +65,8 @@ typedef struct {
   double tol;          /* relative residual ||b - A x|| / ||b|| at which a column is converged (1e-8) */
   int restart;         /* Krylov dimension per restart cycle (GMRES(k)); default 30 */
   int max_restarts;    /* cycle cap per column; default 200 */
-  int precision;       /* GFCC_PREC_* of the inner (Krylov) sigma; residuals are always FP64 */
+  int precision;       /* GFCC_PREC_* of the inner (Krylov) sigma; residuals are always FP64. With
+                          TF32/BF16 the Krylov basis is FP32, with FP64/FP64_TC it is FP64. */
   int max_batch;       /* max columns (p, w) per batched solve; 0 = choose from memory */
   double drop_tol;     /* subspace rank-truncation threshold (relative), default 1e-10 */
   int verbose;         /* 0 silent, 1 per-call summary on stderr */
@@ -198,8 +199,9 @@ long long gfcc_launch_count(void);
  * (FP64-accurate products). Phases (whole regions, nested ones counted in both): 3 low-precision
  * sigma; 4 FP64-accurate sigma; 5 Arnoldi orthogonalisation and updates; 6 MOR orthonormalisation
  * and projections; 7 reduced-model evaluation; 8 H-bar build; 9 column-by-column Gram-Schmidt
- * inside new blocks; 10 extension of the residual basis. Events are recorded on the stream each
- * region is launched on. */
+ * inside new blocks; 10 extension of the residual basis; 11 the ring-term GEMM of the low-precision
+ * sigma (counted here instead of class 0). Events are recorded on the stream each region is
+ * launched on. */
 int gfcc_profile(int enable);
 
 /* Sum over the recorded launches of class cls: number of launches, device milliseconds (CUDA

@@ -276,7 +276,7 @@ static int check_opts(const gfcc_opts* o, std::string& why) {
   if (!(o->tol > 0.0 && o->tol < 1.0)) { why = "opts.tol must be in (0, 1)"; return GFCC_ERR_ARG; }
   if (o->restart < 1 || o->restart > 256) { why = "opts.restart must be in [1, 256]"; return GFCC_ERR_ARG; }
   if (o->max_restarts < 1) { why = "opts.max_restarts must be >= 1"; return GFCC_ERR_ARG; }
-  if (o->precision < GFCC_PREC_FP64 || o->precision > GFCC_PREC_BF16) { why = "opts.precision unknown"; return GFCC_ERR_ARG; }
+  if (o->precision < GFCC_PREC_FP64 || o->precision > GFCC_PREC_FP64_TC) { why = "opts.precision unknown"; return GFCC_ERR_ARG; }
   if (o->max_batch < 0) { why = "opts.max_batch must be >= 0"; return GFCC_ERR_ARG; }
   if (!(o->drop_tol > 0.0 && o->drop_tol < 1.0)) { why = "opts.drop_tol must be in (0, 1)"; return GFCC_ERR_ARG; }
   if (o->residual_precision != -1 && o->residual_precision != GFCC_PREC_FP64 && o->residual_precision != GFCC_PREC_FP64_TC) {
@@ -309,7 +309,8 @@ int gfcc_init(gfcc_t* out, int o, int v, const double* eps, const gfcc_vblocks* 
     GFCC_CUDA(cudaGetDevice(&c->device));
     gfcc::HostInputs in{eps, vb->oooo, vb->ooov, vb->oovv, vb->ovov, vb->ovvv, t1, t2, l1, l2};
     gfcc::build_operator(c, in);
-    if (c->opts.precision != GFCC_PREC_FP64) gfcc::build_low_precision(c, c->opts.precision);
+    if (c->opts.precision == GFCC_PREC_TF32 || c->opts.precision == GFCC_PREC_BF16)
+      gfcc::build_low_precision(c, c->opts.precision);
   } catch (gfcc::Error& e) {
     status = e.code;
     fprintf(stderr, "gfcc_init: %s\n", e.msg.c_str());
@@ -334,7 +335,8 @@ int gfcc_set_opts(gfcc_t c, const gfcc_opts* opts) {
   if (rc != GFCC_OK) { c->last_error = why; return rc; }
   API_BEGIN
   c->opts = *opts;
-  if (opts->precision != GFCC_PREC_FP64 && c->lp.kind != opts->precision) gfcc::build_low_precision(c, opts->precision);
+  if ((opts->precision == GFCC_PREC_TF32 || opts->precision == GFCC_PREC_BF16) && c->lp.kind != opts->precision)
+    gfcc::build_low_precision(c, opts->precision);
   API_END(c)
 }
 

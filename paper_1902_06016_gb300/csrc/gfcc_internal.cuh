@@ -53,7 +53,8 @@ enum ProfClass {
   PROF_INIT = 8,         // H-bar build, b and c vectors
   PROF_MOR_PANEL = 9,    // column-by-column Gram-Schmidt inside the panels of a new block
   PROF_MOR_BASIS = 10,   // extension of the orthonormal residual basis Q
-  PROF_NCLASS = 11
+  PROF_TC_RING = 11,     // the ring-term GEMM of the low-precision sigma (tf32/bf16 tcgen05)
+  PROF_NCLASS = 12
 };
 struct ProfScope {   // records CUDA events around one launch on stream s when profiling is on
   int cls;

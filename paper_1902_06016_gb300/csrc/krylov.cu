@@ -479,7 +479,7 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
   if (resid_prec < 0) resid_prec = inner_prec == GFCC_PREC_FP64 ? GFCC_PREC_FP64 : GFCC_PREC_FP64_TC;
   // a cycle with a low-precision inner operator cannot gain more than about its rounding level: stop
   // it once the inner estimate has dropped by this factor
-  const double inner_rtol = (inner_prec == GFCC_PREC_FP64) ? 0.0 : 1e-4;
+  const double inner_rtol = (inner_prec == GFCC_PREC_FP64 || inner_prec == GFCC_PREC_FP64_TC) ? 0.0 : 1e-4;
   st.relres.assign(nb0, 0.0);
   st.iters.assign(nb0, 0);
   st.converged.assign(nb0, 0);

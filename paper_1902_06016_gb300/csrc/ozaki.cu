@@ -15,8 +15,6 @@ int grid_for(long long n) {
   return (int)std::min<long long>(std::max<long long>(g, 1), 152LL * 32);
 }
 
-constexpr int OZ_CHUNK_KB = 32;   // k-blocks of 64 per exact FP32 partial: 2048 products < 2^23
-
 // one block per row (grid-stride): row exponent from the largest |x|, then S integer slices
 __global__ void __launch_bounds__(256) slice_kernel(const double* __restrict__ X, long long ldx, long long rows,
                                                     long long K, long long kp, int reversed, int ns,
@@ -52,14 +50,15 @@ __global__ void __launch_bounds__(256) slice_kernel(const double* __restrict__ X
   }
 }
 
-// acc[m*N + n] (+)= scale * sum_z part[z*stride + m*N + n]
-__global__ void accumulate_kernel(const float* __restrict__ part, int zs, long long stride, long long total,
+// acc[t] (+)= scale * sum_z part[z*stride + t]: the int32 split sums of one diagonal, added exactly
+// in 64-bit integers, then weighted and accumulated in FP64
+__global__ void accumulate_kernel(const int* __restrict__ part, int zs, long long stride, long long total,
                                   double scale, int first, double* __restrict__ acc) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    double sum = 0.0;
-    for (int z = 0; z < zs; ++z) sum += (double)part[z * stride + t];
-    acc[t] = first ? scale * sum : acc[t] + scale * sum;
+    long long sum = 0;
+    for (int z = 0; z < zs; ++z) sum += part[z * stride + t];
+    acc[t] = first ? scale * (double)sum : acc[t] + scale * (double)sum;
   }
 }
 
@@ -185,13 +184,12 @@ void oz_gemm(const SlicedRows& A, const SlicedRows& B, long long M, long long N,
   GFCC_CHECK(A.rows >= M && B.rows >= N, GFCC_ERR_ARG, "oz_gemm: operand rows");
   const int ns = A.ns;
   const long long kp = A.kp, ld = (long long)ns * kp;
-  const int nkb = (int)(kp / 64);
-  // partial slabs for the largest diagonal, with N processed in column chunks to bound memory
-  const int max_splits = (ns * nkb + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
-  const long long slab_budget = 3LL << 30;   // bytes of FP32 partials at a time
+  // int32 split sums of the largest diagonal, with N processed in column chunks to bound memory
+  const int max_splits = tc_exact_splits(M, N, (long long)ns * kp);
+  const long long slab_budget = 2LL << 30;   // bytes of int32 split sums at a time
   long long nc = std::max<long long>(1, slab_budget / (4LL * M * max_splits));
   nc = std::min<long long>(N, std::max<long long>(256, nc / 256 * 256));
-  w.slabs.alloc((size_t)max_splits * M * nc);
+  w.islabs.alloc((size_t)max_splits * M * nc);
   w.acc.alloc((size_t)M * nc);
   if (w.err.n == 0) { w.err.alloc(1); w.err.zero(s); }
   const __nv_bfloat16* As = reinterpret_cast<const __nv_bfloat16*>(A.slices.p);
@@ -199,15 +197,13 @@ void oz_gemm(const SlicedRows& A, const SlicedRows& B, long long M, long long N,
   for (long long n0 = 0; n0 < N; n0 += nc) {
     const long long nn = std::min(nc, N - n0);
     for (int d = 0; d < ns; ++d) {
+      // diagonal d: A slices 0..d against B slices d..0, concatenated along K
       const long long kd = (long long)(d + 1) * kp;
-      const int nk = (int)(kd / 64);
-      const int ksplit = (nk + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
+      const int zs = std::min(tc_exact_splits(M, nn, kd), max_splits);
       TcOperand a(As, M, kd, ld);
       TcOperand b(Bs + (long long)n0 * ld + (long long)(ns - 1 - d) * kp, nn, kd, ld);
-      tc_gemm(TcKind::BF16, a, b, w.slabs.p, nn, M, nn, 0, ksplit, M * nn, w.err.p, s, PROF_TC_SLICE);
-      const int nk_split = (nk + ksplit - 1) / ksplit;
-      const int zs = (nk + nk_split - 1) / nk_split;
-      accumulate_kernel<<<grid_for(M * nn), 256, 0, s>>>(w.slabs.p, zs, M * nn, M * nn, ldexp(1.0, -7 * d),
+      const int zeff = tc_gemm_exact(a, b, w.islabs.p, nn, M, nn, zs, M * nn, w.err.p, s, PROF_TC_SLICE);
+      accumulate_kernel<<<grid_for(M * nn), 256, 0, s>>>(w.islabs.p, zeff, M * nn, M * nn, ldexp(1.0, -7 * d),
                                                           d == 0 ? 1 : 0, w.acc.p);
       GFCC_LAUNCH_CHECK();
     }

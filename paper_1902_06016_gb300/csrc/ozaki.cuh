@@ -6,8 +6,9 @@
 // A K-chunk of at most 2048 such products sums to an integer below 2^23, which the FP32 tensor-core
 // accumulator holds exactly. The slice pairs with i + j = d ("diagonal" d) are one GEMM with the
 // slices concatenated along K (A slices in order 0..d, B slices in order d..0); its K-chunks are
-// written as FP32 partials, summed exactly in FP64 with weight 2^(-7d), and the total is scaled by
-// 2^(e_A + e_B - 12). With S = 6 slices the representation keeps 41 bits of each row (relative to its
+// accumulated exactly inside the GEMM kernel in int32 (each chunk's FP32 sum is an exact integer),
+// the per-split int32 sums are added in 64-bit integers and weighted by 2^(-7d) in FP64, and the total
+// is scaled by 2^(e_A + e_B - 12). With S = 6 slices the representation keeps 41 bits of each row (relative to its
 // largest element) and the dropped pairs (i + j >= S) weigh at most 2^-42 of the leading term: the
 // result is accurate to about 2^-40 of sum_k |a_mk||b_nk|, far below what FP32 or TF32 give.
 // (Ozaki, Ogita, Oishi and Rump, "Error-free transformations of matrix multiplication by using fast
@@ -40,7 +41,7 @@ void oz_slice_into(const double* X, long long ldx, long long nrows, long long K,
 // out[m][n] = beta * out[m][n] + sum_k A[m][k] B[n][k] for m < M, n < N (out row stride ldo), with
 // A = sliced rows (normal order) and B = sliced rows (reversed order), same kp.
 struct OzWork {
-  DBuf<float> slabs;
+  DBuf<int> islabs;
   DBuf<double> acc;
   DBuf<int> err;
 };

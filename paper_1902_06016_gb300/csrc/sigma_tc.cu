@@ -11,6 +11,8 @@
 #include "ozaki.cuh"
 #include "tc_gemm.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -464,9 +466,11 @@ static void sigma_lp_impl(gfcc_ctx* c, LpState& st, const VT* X, VT* Y, int nb, 
   prep_down_kernel<Elem<K>, float, VT><<<grid_for(nsm * st.Kvo), 256, 0, s>>>(st.up.p, nsm, X, o, v, nb, Bdn, st.Kvo);
   GFCC_LAUNCH_CHECK();
   tc_gemm(K, TcOperand{st.Adn.p, Pv, st.Kvo}, TcOperand{Bdn, nsm, st.Kvo}, st.C2.p, nsm, Pv, nsm, 1, 1, 0, st.err.p, s);
-  // ring
+  // ring (its own profiling class and NVTX range, so that its launches can be timed and profiled alone)
+  nvtxRangePushA("gfcc_ring_gemm");
   tc_gemm(K, TcOperand{st.Wr.p, ov, st.Kr}, TcOperand{Bring, nring, st.Kr}, st.CT.p, nring, ov, nring, 0, 1, 0,
-          st.err.p, s);
+          st.err.p, s, PROF_TC_RING, ov);
+  nvtxRangePop();
   combine_lp_kernel<float, VT><<<grid_for(D * nb), 256, 0, s>>>(X, Y, st.up.p, nsm, st.C2.p, st.CT.p, c->op.A11.p, c->op.diag.p,
                                                      shift, o, v, D, nb);
   GFCC_LAUNCH_CHECK();

@@ -17,7 +17,7 @@ constexpr int A_BYTES = BM * KB_BYTES;               // 16 KB
 constexpr int B_BYTES = BN * KB_BYTES;               // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr int TMEM_COLS = 256;                       // 128 lanes x 256 FP32 columns
+constexpr int TMEM_COLS = 512;                       // 128 lanes x (2 x 256) FP32 columns
 constexpr long long WAIT_CYCLES = 4000000000LL;      // about two seconds at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -101,27 +101,56 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <TcKind KIND>
-__global__ void __launch_bounds__(192, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float* C,
-                   long long ldc, long long M, long long N, int nk_total, int nk_split, long long split_stride,
-                   int beta, int* err) {
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// work unit u -> (split z, M tile, N tile), N tiles fastest
+struct Unit {
+  int z, mt, nt;
+};
+__device__ __forceinline__ Unit decode_unit(int u, int tiles_m, int tiles_n) {
+  const int per_z = tiles_m * tiles_n;
+  Unit r;
+  r.z = u / per_z;
+  const int t = u - r.z * per_z;
+  r.mt = t / tiles_n;
+  r.nt = t - r.mt * tiles_n;
+  return r;
+}
+
+// Persistent kernel: CTA b processes the work units b, b + gridDim.x, ... (unit = split z x 128-row
+// M tile x 256-column N tile, K range [z nk_split, (z+1) nk_split) in k-blocks). Warp 0 is the TMA
+// producer (one k-block per stage), warp 1 issues the MMAs, the remaining warps drain TMEM. The
+// accumulator is double-buffered in TMEM (2 x 256 columns): while the epilogue reads buffer b of
+// one accumulation, the MMAs of the next run into the other buffer.
+//
+// EXACT = false: one accumulation per unit; the epilogue writes FP32 C (beta = 1 adds to C).
+// EXACT = true (bf16 operands holding small integers, see ozaki.cuh): the unit's K range is cut into
+// accumulations of at most CH k-blocks (2048 products, whose FP32 sum is exact), and the epilogue
+// adds each one, converted to int32, into per-thread integer registers; the unit writes int32 sums to
+// C (as int) + z * split_stride. The caller bounds a unit to 255 accumulations, so |sum| < 2^31.
+template <TcKind KIND, bool EXACT>
+__global__ void __launch_bounds__(EXACT ? 320 : 192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, void* Cv,
+                   long long ldc, long long M, long long N, int tiles_m, int tiles_n, int zs, int nk_total,
+                   int nk_split, long long split_stride, int beta, int* err) {
   constexpr int KB_ELEMS = KIND == TcKind::BF16 ? 64 : 32;
   constexpr int MMA_K_BYTES = 32;                            // K = 16 bf16 or 8 tf32 per instruction
+  constexpr int NEPI = EXACT ? 8 : 4;                        // epilogue warps
+  constexpr int CH = 32;                                     // k-blocks per exact accumulation
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
-  __shared__ int s_fail;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+  __shared__ volatile int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long m0 = (long long)blockIdx.y * BM, n0 = (long long)blockIdx.x * BN;
-  const int z = blockIdx.z;
-  const int kb0 = z * nk_split;
-  const int nk = max(0, min(nk_total, kb0 + nk_split) - kb0);
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), accf = smem_u32(bars + 2 * STAGES);
+  const int total = zs * tiles_m * tiles_n;
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t accf0 = smem_u32(bars + 2 * STAGES), acce0 = smem_u32(bars + 2 * STAGES + 2);
 
   if (threadIdx.x == 0) {
     s_fail = 0;
@@ -129,7 +158,10 @@ __global__ void __launch_bounds__(192, 1)
       mbar_init(full0 + 8 * st, 1);
       mbar_init(empty0 + 8 * st, 1);
     }
-    mbar_init(accf, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, NEPI);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -145,72 +177,152 @@ __global__ void __launch_bounds__(192, 1)
 
   if (warp == 0) {
     if (lane == 0) {   // TMA producer
-      for (int kb = 0; kb < nk; ++kb) {
-        const int st = kb % STAGES;
-        const uint32_t ph = (kb / STAGES) & 1;
-        if (!mbar_wait(empty0 + 8 * st, ph ^ 1)) { s_fail = 1; break; }
-        mbar_expect_tx(full0 + 8 * st, STAGE_BYTES);
-        tma_load_2d(smem_u32(sA + st * A_BYTES), &tmA, (kb0 + kb) * KB_ELEMS, (int)m0, full0 + 8 * st);
-        tma_load_2d(smem_u32(sB + st * B_BYTES), &tmB, (kb0 + kb) * KB_ELEMS, (int)n0, full0 + 8 * st);
+      long long g = 0;  // k-blocks issued by this CTA
+      for (int u = blockIdx.x; u < total && !s_fail; u += gridDim.x) {
+        const Unit w = decode_unit(u, tiles_m, tiles_n);
+        const int kb0 = w.z * nk_split;
+        const int nk = max(0, min(nk_total, kb0 + nk_split) - kb0);
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int st = (int)(g % STAGES);
+          const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+          if (!mbar_wait(empty0 + 8 * st, ph ^ 1)) { s_fail = 1; break; }
+          mbar_expect_tx(full0 + 8 * st, STAGE_BYTES);
+          tma_load_2d(smem_u32(sA + st * A_BYTES), &tmA, (kb0 + kb) * KB_ELEMS, w.mt * BM, full0 + 8 * st);
+          tma_load_2d(smem_u32(sB + st * B_BYTES), &tmB, (kb0 + kb) * KB_ELEMS, w.nt * BN, full0 + 8 * st);
+        }
       }
+      // no copy may still be in flight when the CTA exits: wait (bounded) for the last stages issued
+      for (long long i = (g > STAGES ? g - STAGES : 0); i < g; ++i)
+        if (!mbar_wait(full0 + 8 * (int)(i % STAGES), (uint32_t)((i / STAGES) & 1))) s_fail = 1;
     }
   } else if (warp == 1) {
     if (lane == 0) {   // MMA issuer
+      long long g = 0;  // k-blocks consumed
+      int seg = 0;      // accumulations started (TMEM buffer = seg & 1)
       bool ok = true;
-      for (int kb = 0; kb < nk && ok; ++kb) {
-        const int st = kb % STAGES;
-        const uint32_t ph = (kb / STAGES) & 1;
-        if (!mbar_wait(full0 + 8 * st, ph)) { s_fail = 1; ok = false; break; }
-        tc_fence_after();
-        const uint64_t ad = sdesc(smem_u32(sA + st * A_BYTES));
-        const uint64_t bd = sdesc(smem_u32(sB + st * B_BYTES));
+      for (int u = blockIdx.x; u < total && ok && !s_fail; u += gridDim.x) {
+        const Unit w = decode_unit(u, tiles_m, tiles_n);
+        const int kb0 = w.z * nk_split;
+        const int nk = max(0, min(nk_total, kb0 + nk_split) - kb0);
+        const int nseg = nk == 0 ? 1 : (EXACT ? (nk + CH - 1) / CH : 1);
+        for (int sgi = 0; sgi < nseg && ok; ++sgi, ++seg) {
+          const int buf = seg & 1;
+          if (seg >= 2 && !mbar_wait(acce0 + 8 * buf, (uint32_t)(((seg >> 1) - 1) & 1))) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t tacc = taddr + (uint32_t)(buf * BN);
+          const int k_lo = EXACT ? sgi * CH : 0;
+          const int k_hi = EXACT ? min(nk, k_lo + CH) : nk;
+          for (int kb = k_lo; kb < k_hi; ++kb, ++g) {
+            const int st = (int)(g % STAGES);
+            const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+            if (!mbar_wait(full0 + 8 * st, ph)) { ok = false; break; }
+            tc_fence_after();
+            const uint64_t ad = sdesc(smem_u32(sA + st * A_BYTES));
+            const uint64_t bd = sdesc(smem_u32(sB + st * B_BYTES));
 #pragma unroll
-        for (int kk = 0; kk < KB_BYTES / MMA_K_BYTES; ++kk)
-          mma<KIND>(taddr, ad + (uint64_t)(kk * MMA_K_BYTES >> 4), bd + (uint64_t)(kk * MMA_K_BYTES >> 4),
-                    (kb > 0 || kk > 0) ? 1u : 0u);
-        mma_commit(empty0 + 8 * st);   // frees the stage once these MMAs have read it
+            for (int kk = 0; kk < KB_BYTES / MMA_K_BYTES; ++kk)
+              mma<KIND>(tacc, ad + (uint64_t)(kk * MMA_K_BYTES >> 4), bd + (uint64_t)(kk * MMA_K_BYTES >> 4),
+                        (kb > k_lo || kk > 0) ? 1u : 0u);
+            mma_commit(empty0 + 8 * st);   // frees the stage once these MMAs have read it
+          }
+          if (!ok) break;
+          mma_commit(accf0 + 8 * buf);     // accumulation complete (immediately for an empty K range)
+        }
       }
-      mma_commit(accf);                // accumulator complete
+      if (!ok) s_fail = 1;
     }
-  } else {   // warps 2..5: epilogue over TMEM lane quarters (warp % 4)
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(accf, 0));   // keep the warp converged for tcgen05.ld
-    if (!ok) {
-      if (lane == 0) s_fail = 1;
-    } else {
-      tc_fence_after();
-      const int q = warp & 3;
-      const long long grow = m0 + q * 32 + lane;
-      float* Cz = C + (long long)z * split_stride;
-      const bool vec = (ldc % 4 == 0);
-#pragma unroll 1
-      for (int ch = 0; ch < BN / 32; ++ch) {
-        uint32_t r[32];
-        tmem_ld32(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 32), r);
-        const long long gcol = n0 + ch * 32;
-        if (grow < M && gcol < N) {
-          float* p = Cz + grow * ldc + gcol;
-          if (vec && gcol + 32 <= N) {
+  } else {   // epilogue warps: TMEM lane quarter warp % 4; in EXACT mode two warps per quarter split N
+    const int q = warp & 3;
+    const int half = EXACT ? (warp - 2) / 4 : 0;
+    constexpr int NCOL = EXACT ? BN / 2 : BN;   // columns per thread
+    int seg = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
+      const Unit w = decode_unit(u, tiles_m, tiles_n);
+      const int kb0 = w.z * nk_split;
+      const int nk = max(0, min(nk_total, kb0 + nk_split) - kb0);
+      const int nseg = nk == 0 ? 1 : (EXACT ? (nk + CH - 1) / CH : 1);
+      const long long grow = (long long)w.mt * BM + q * 32 + lane;
+      const long long gcol0 = (long long)w.nt * BN + half * NCOL;
+      int iacc[EXACT ? NCOL : 1];
+      if constexpr (EXACT) {
 #pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                                     __uint_as_float(r[j + 3]));
-              if (nk == 0) v = make_float4(0.f, 0.f, 0.f, 0.f);
-              if (beta) {
-                float4 o = *reinterpret_cast<float4*>(p + j);
-                v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+        for (int j = 0; j < NCOL; ++j) iacc[j] = 0;
+      }
+      for (int sgi = 0; sgi < nseg; ++sgi, ++seg) {
+        const int buf = seg & 1;
+        ok = __all_sync(0xffffffffu, mbar_wait(accf0 + 8 * buf, (uint32_t)((seg >> 1) & 1)) && !s_fail);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t trow = taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + half * NCOL);
+        if constexpr (EXACT) {
+#pragma unroll
+          for (int ch = 0; ch < NCOL / 32; ++ch) {
+            uint32_t r[32];
+            tmem_ld32(trow + (uint32_t)(ch * 32), r);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              // exact integer |v| < 2^23: add 1.5 * 2^23 and read the low mantissa bits
+              const float v = nk == 0 ? 0.f : __uint_as_float(r[j]);
+              iacc[ch * 32 + j] += __float_as_int(v + 12582912.0f) - 0x4B400000;
+            }
+          }
+        } else {
+          float* Cz = reinterpret_cast<float*>(Cv) + (long long)w.z * split_stride;
+          const bool vec = (ldc % 4 == 0);
+#pragma unroll 1
+          for (int ch = 0; ch < NCOL / 32; ++ch) {
+            uint32_t r[32];
+            tmem_ld32(trow + (uint32_t)(ch * 32), r);
+            const long long gcol = gcol0 + ch * 32;
+            if (grow < M && gcol < N) {
+              float* p = Cz + grow * ldc + gcol;
+              if (vec && gcol + 32 <= N) {
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                  float4 v = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                         __uint_as_float(r[j + 3]));
+                  if (nk == 0) v = make_float4(0.f, 0.f, 0.f, 0.f);
+                  if (beta) {
+                    float4 o = *reinterpret_cast<float4*>(p + j);
+                    v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+                  }
+                  *reinterpret_cast<float4*>(p + j) = v;
+                }
+              } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                  if (gcol + j < N) {
+                    float v = nk == 0 ? 0.f : __uint_as_float(r[j]);
+                    if (beta) v += p[j];
+                    p[j] = v;
+                  }
+                }
               }
-              *reinterpret_cast<float4*>(p + j) = v;
             }
+          }
+        }
+        // this warp's reads of the buffer are complete (tcgen05.wait::ld in tmem_ld32): release it
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acce0 + 8 * buf);
+      }
+      if constexpr (EXACT) {
+        if (ok && grow < M) {
+          int* Pz = reinterpret_cast<int*>(Cv) + (long long)w.z * split_stride + grow * ldc;
+          if (ldc % 4 == 0 && gcol0 + NCOL <= N) {
+#pragma unroll
+            for (int j = 0; j < NCOL; j += 4)
+              *reinterpret_cast<int4*>(Pz + gcol0 + j) = make_int4(iacc[j], iacc[j + 1], iacc[j + 2], iacc[j + 3]);
           } else {
-            for (int j = 0; j < 32 && gcol + j < N; ++j) {
-              float v = nk == 0 ? 0.f : __uint_as_float(r[j]);
-              if (beta) v += p[j];
-              p[j] = v;
-            }
+#pragma unroll
+            for (int j = 0; j < NCOL; ++j)
+              if (gcol0 + j < N) Pz[gcol0 + j] = iacc[j];
           }
         }
       }
     }
+    if (!ok && lane == 0) s_fail = 1;
   }
   tc_fence_before();
   __syncthreads();
@@ -256,10 +368,36 @@ CUtensorMap make_map(TcKind kind, const TcOperand& op, int box_rows) {
   return m;
 }
 
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  GFCC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (cached[dev] == 0) GFCC_CUDA(cudaDeviceGetAttribute(&cached[dev], cudaDevAttrMultiProcessorCount, dev));
+  return cached[dev];
+}
+
+template <TcKind K, bool EXACT>
+void launch(const CUtensorMap& ma, const CUtensorMap& mb, void* C, long long ldc, long long M, long long N,
+            int tiles_m, int tiles_n, int zs, int nk_total, int nk_split, long long split_stride, int beta, int* err,
+            cudaStream_t s) {
+  static bool attr = false;   // set once per process (the attribute is per function, all devices alike)
+  if (!attr) {
+    GFCC_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<K, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr = true;
+  }
+  const long long units = (long long)zs * tiles_m * tiles_n;
+  const int grid = (int)std::min<long long>(units, sm_count());
+  tc_gemm_kernel<K, EXACT><<<grid, EXACT ? 320 : 192, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, tiles_m, tiles_n, zs,
+                                                                       nk_total, nk_split, split_stride, beta, err);
+  GFCC_LAUNCH_CHECK();
+}
+
 }  // namespace
 
 void tc_gemm(TcKind kind, const TcOperand& A, const TcOperand& B, float* C, long long ldc, long long M, long long N,
-             int beta, int ksplit, long long split_stride, int* err_dev, cudaStream_t s, int prof_class) {
+             int beta, int ksplit, long long split_stride, int* err_dev, cudaStream_t s, int prof_class,
+             long long k_alg) {
   if (M <= 0 || N <= 0) return;
   GFCC_CHECK(A.k_pad == B.k_pad, GFCC_ERR_ARG, "tc_gemm: K mismatch");
   GFCC_CHECK(A.rows >= M && B.rows >= N, GFCC_ERR_ARG, "tc_gemm: operand rows");
@@ -269,32 +407,50 @@ void tc_gemm(TcKind kind, const TcOperand& A, const TcOperand& B, float* C, long
   GFCC_CHECK(A.k_pad / kb_elems < (1LL << 30), GFCC_ERR_ARG, "tc_gemm: K too large");
   const int nk_total = (int)(A.k_pad / kb_elems);
   const int nk_split = (nk_total + ksplit - 1) / ksplit;
-  const int zs = (nk_total + nk_split - 1) / nk_split;
+  const int zs = std::max(1, (nk_total + nk_split - 1) / nk_split);
+  const long long tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
+  GFCC_CHECK(tiles_m * tiles_n * zs < (1LL << 31), GFCC_ERR_ARG, "tc_gemm: too many tiles");
   CUtensorMap ma = make_map(kind, A, BM);
   CUtensorMap mb = make_map(kind, B, BN);
-  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)zs);
-  GFCC_CHECK(grid.y <= 65535 && grid.z <= 65535, GFCC_ERR_ARG, "tc_gemm: grid too large");
+  ProfScope prof(prof_class, 2.0 * (double)M * (double)N * (double)(k_alg > 0 ? k_alg : A.k_pad), s);
+  if (kind == TcKind::BF16)
+    launch<TcKind::BF16, false>(ma, mb, C, ldc, M, N, (int)tiles_m, (int)tiles_n, zs, nk_total, nk_split,
+                                split_stride, beta, err_dev, s);
+  else
+    launch<TcKind::TF32, false>(ma, mb, C, ldc, M, N, (int)tiles_m, (int)tiles_n, zs, nk_total, nk_split,
+                                split_stride, beta, err_dev, s);
+}
+
+int tc_gemm_exact(const TcOperand& A, const TcOperand& B, int* P, long long ldp, long long M, long long N, int zs,
+                  long long split_stride, int* err_dev, cudaStream_t s, int prof_class) {
+  if (M <= 0 || N <= 0) return 0;
+  GFCC_CHECK(zs >= 1, GFCC_ERR_ARG, "tc_gemm_exact: zs < 1");
+  GFCC_CHECK(A.k_pad == B.k_pad, GFCC_ERR_ARG, "tc_gemm_exact: K mismatch");
+  GFCC_CHECK(A.rows >= M && B.rows >= N, GFCC_ERR_ARG, "tc_gemm_exact: operand rows");
+  GFCC_CHECK(A.rows < (1LL << 31) && B.rows < (1LL << 31), GFCC_ERR_ARG, "tc_gemm_exact: too many rows");
+  GFCC_CHECK(A.k_pad / 64 < (1LL << 30), GFCC_ERR_ARG, "tc_gemm_exact: K too large");
+  const int nk_total = (int)(A.k_pad / 64);
+  const int nk_split = std::max(1, (nk_total + zs - 1) / std::max(zs, 1));
+  GFCC_CHECK(nk_split <= TC_EXACT_MAX_KB, GFCC_ERR_ARG, "tc_gemm_exact: split too long for exact int32 sums");
+  const int z_eff = std::max(1, (nk_total + nk_split - 1) / nk_split);
+  const long long tiles_m = (M + BM - 1) / BM, tiles_n = (N + BN - 1) / BN;
+  GFCC_CHECK(tiles_m * tiles_n * z_eff < (1LL << 31), GFCC_ERR_ARG, "tc_gemm_exact: too many tiles");
+  CUtensorMap ma = make_map(TcKind::BF16, A, BM);
+  CUtensorMap mb = make_map(TcKind::BF16, B, BN);
   ProfScope prof(prof_class, 2.0 * (double)M * (double)N * (double)A.k_pad, s);
-  if (kind == TcKind::BF16) {
-    static bool attr = false;
-    if (!attr) {
-      GFCC_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<TcKind::BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-      attr = true;
-    }
-    tc_gemm_kernel<TcKind::BF16><<<grid, 192, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, nk_total, nk_split, split_stride,
-                                                                beta, err_dev);
-    GFCC_LAUNCH_CHECK();
-  } else {
-    static bool attr = false;
-    if (!attr) {
-      GFCC_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<TcKind::TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-      attr = true;
-    }
-    tc_gemm_kernel<TcKind::TF32><<<grid, 192, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, nk_total, nk_split, split_stride,
-                                                                beta, err_dev);
-    GFCC_LAUNCH_CHECK();
-  }
-  GFCC_LAUNCH_CHECK();
+  GFCC_CHECK(z_eff <= zs, GFCC_ERR_ARG, "tc_gemm_exact: split count");
+  launch<TcKind::BF16, true>(ma, mb, P, ldp, M, N, (int)tiles_m, (int)tiles_n, z_eff, nk_total, nk_split,
+                             split_stride, 0, err_dev, s);
+  return z_eff;
+}
+
+int tc_exact_splits(long long M, long long N, long long k_pad) {
+  const long long nk = k_pad / 64;
+  const long long tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  long long zs = std::max<long long>(1, (sm_count() + tiles - 1) / tiles);   // about one wave of units
+  zs = std::min<long long>(zs, std::max<long long>(1, nk / 32));              // at least 32 k-blocks per split
+  zs = std::max<long long>(zs, (nk + TC_EXACT_MAX_KB - 1) / TC_EXACT_MAX_KB);
+  return (int)zs;
 }
 
 }  // namespace gfcc

@@ -51,6 +51,22 @@ def test_tc_gemm_matches_rounded_fp64(torch, prec, M, N, K):
     assert np.all(np.abs(C - ref) <= bound)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+@pytest.mark.parametrize("M,N,K", [(1000, 9000, 200), (2000, 3000, 1100)])
+def test_tc_gemm_more_tiles_than_sms(torch, prec, M, N, K):
+    """Several output tiles per persistent CTA (288 and 192 tiles on 152 SMs): the double-buffered
+    TMEM accumulators are handed between the MMA issuer and the epilogue warps many times."""
+    from paper_1902_06016_gb300.gfcc import tc_gemm
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((N, K))
+    C = tc_gemm(A, B, prec)
+    rnd = round_bf16 if prec == "bf16" else round_tf32
+    ref = rnd(A) @ rnd(B).T
+    bound = 2.0 ** -17 * (np.abs(rnd(A)) @ np.abs(rnd(B)).T) + 1e-6
+    assert np.all(np.abs(C - ref) <= bound)
+
+
 @pytest.mark.parametrize("prec,lo,hi", [("bf16", 1e-6, 3e-2), ("tf32", 1e-7, 4e-3)])
 @pytest.mark.parametrize("o,v,seed", [(4, 8, 1001), (7, 13, 103), (14, 42, 1002)])
 def test_lowprec_sigma_error_is_rounding_sized(torch, prec, lo, hi, o, v, seed):
@@ -99,6 +115,37 @@ def test_exact_slice_sigma_is_fp64_accurate(torch, o, v, seed):
     # and per column, relative to that column
     for k in (0, 33, 69):
         assert np.abs(Y[k] - Yo[k]).max() <= 1e-12 * np.abs(Yo[k]).max()
+
+
+def test_exact_slice_sigma_many_tiles(torch):
+    """200 vectors at o=14, v=42: the exact-slice ring GEMM has 110 output tiles x 2 K splits, so the
+    persistent exact kernel runs several work units per CTA, each over several exact accumulations."""
+    from paper_1902_06016_gb300 import Context
+    inp = inputs(14, 42, 1002)
+    hb = hbar.build(inp)
+    ctx = Context(inp)
+    X = random_vectors(inp.dim, 200, 7)
+    Yo = sg.sigma(hb, X)
+    Y = ctx.sigma(X, precision="fp64_tc")
+    assert rel_err(Y, Yo) <= 1e-12
+    for k in (0, 101, 199):
+        assert np.abs(Y[k] - Yo[k]).max() <= 1e-12 * np.abs(Yo[k]).max()
+
+
+def test_solve_with_exact_slice_inner_sigma(torch):
+    """GFCC_PREC_FP64_TC as the inner precision: FP64 Krylov basis, FP64-accurate sigma throughout."""
+    from paper_1902_06016_gb300 import Context
+    inp = inputs(7, 13, 103)
+    M = sg.dense_matrix(hbar.build(inp))
+    porb = list(range(inp.n))
+    ws = np.linspace(-1.0, 0.0, 4)
+    ctx = Context(inp, tol=1e-11, precision="fp64_tc", restart=20)
+    r = ctx.solve_full(ws, 0.01, porb, want_X=True)
+    assert r["converged"] and r["stats"].max_rel_res <= 1e-11
+    Xo = sv.dense_solve(M, bc.b_vectors(inp, porb), ws, 0.01)
+    Go = sv.green(bc.c_vectors(inp, porb), Xo)
+    assert rel_err(r["X"], Xo) <= 1e-8
+    assert rel_err(r["A"], sv.spectral(Go)) <= 1e-8
 
 
 def test_mixed_solve_with_exact_slice_residuals(torch):
