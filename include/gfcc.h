@@ -200,7 +200,8 @@ long long gfcc_launch_count(void);
  * sigma; 4 FP64-accurate sigma; 5 Arnoldi orthogonalisation and updates; 6 MOR orthonormalisation
  * and projections; 7 reduced-model evaluation; 8 H-bar build; 9 column-by-column Gram-Schmidt
  * inside new blocks; 10 extension of the residual basis; 11 the ring-term GEMM of the low-precision
- * sigma (counted here instead of class 0). Events are recorded on the stream each region is
+ * sigma (counted here instead of class 0); 12 whole FP64-accurate complex GEMMs on exact slices;
+ * 13 splitting of FP64 rows into exact slices. Events are recorded on the stream each region is
  * launched on. */
 int gfcc_profile(int enable);
 

@@ -54,7 +54,9 @@ enum ProfClass {
   PROF_MOR_PANEL = 9,    // column-by-column Gram-Schmidt inside the panels of a new block
   PROF_MOR_BASIS = 10,   // extension of the orthonormal residual basis Q
   PROF_TC_RING = 11,     // the ring-term GEMM of the low-precision sigma (tf32/bf16 tcgen05)
-  PROF_NCLASS = 12
+  PROF_OZ_ZGEMM = 12,    // whole FP64-accurate complex GEMMs on exact slices (operand gathers to scatter)
+  PROF_OZ_SLICE = 13,    // splitting FP64 rows into exact bf16 slices (every use)
+  PROF_NCLASS = 14
 };
 struct ProfScope {   // records CUDA events around one launch on stream s when profiling is on
   int cls;

@@ -15,35 +15,187 @@ int grid_for(long long n) {
   return (int)std::min<long long>(std::max<long long>(g, 1), 152LL * 32);
 }
 
-// one block per row (grid-stride): row exponent from the largest |x|, then S integer slices
+// ---- integer slicing -----------------------------------------------------------------------------
+// Every step below is integer arithmetic on the FP64 bit patterns (FP64 instructions run on a narrow
+// pipe on this GPU). For non-negative doubles the bit patterns order like the values, so the row
+// maximum of |x| is an integer maximum, and the row exponent e (max |x| < 2^e, as frexp) is read
+// from its exponent field; a row whose maximum is zero or subnormal is treated as zero.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL;
+}
+constexpr int ZERO_ROW = -100000;   // row exponent marker of a zero (or subnormal-only) row
+__device__ __forceinline__ int row_exponent(unsigned long long maxbits) {
+  const int ex = (int)(maxbits >> 52);
+  return ex == 0 ? ZERO_ROW : ex - 1022;
+}
+// Balanced base-128 digits of x relative to 2^(e - 6):  x ~ 2^(e-6) sum_{i<ns} a_i 2^(-7i), |a_i| <= 64.
+// V = round(|x| 2^(6 - e + 7(ns-1))) is formed exactly from the mantissa (|V| <= 2^(6 + 7(ns-1)) < 2^56);
+// digit i is V / 2^(7(ns-1-i)) rounded half up, V keeps the remainder (|remainder| <= 2^(shift-1)), and
+// the signs of all digits follow x (so -x gives exactly the negated digits). a[i] holds digit i.
+__device__ __forceinline__ void digits(double x, int e, int ns, int (&a)[OZ_SLICES_MAX]) {
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  long long V = 0;
+  if (ex != 0 && e != ZERO_ROW) {
+    const long long m = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+    const int t = ex - 1075 + 6 - e + 7 * (ns - 1);   // t <= 7 ns - 53 <= 3
+    if (t >= 0) V = m << t;
+    else if (t > -62) V = (m + (1LL << (-t - 1))) >> (-t);
+  }
+  const bool neg = bits < 0;
+#pragma unroll
+  for (int i = 0; i < OZ_SLICES_MAX; ++i) {
+    if (i < ns) {
+      const int shift = 7 * (ns - 1 - i);
+      const long long d = (i < ns - 1) ? ((V + (1LL << (shift - 1))) >> shift) : V;
+      V -= d << shift;
+      a[i] = neg ? -(int)d : (int)d;
+    }
+  }
+}
+
+// Real rows (row-major, row stride ldx, K used columns): one block per row (grid-stride) for long
+// rows; slices [r][slot][kp] with slot = i (or ns-1-i when reversed), zeros for K <= k < kp.
 __global__ void __launch_bounds__(256) slice_kernel(const double* __restrict__ X, long long ldx, long long rows,
                                                     long long K, long long kp, int reversed, int ns,
                                                     __nv_bfloat16* __restrict__ out, int* __restrict__ expo) {
-  __shared__ double red[256];
+  __shared__ unsigned long long red[8];
   for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
     const double* x = X + r * ldx;
-    double mx = 0.0;
-    for (long long k = threadIdx.x; k < K; k += blockDim.x) mx = fmax(mx, fabs(x[k]));
-    red[threadIdx.x] = mx;
+    unsigned long long mx = 0;
+    for (long long k = threadIdx.x; k < K; k += blockDim.x) mx = max(mx, abs_bits(x[k]));
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-      if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
-      __syncthreads();
-    }
-    int e = 0;
-    if (red[0] > 0.0) frexp(red[0], &e);   // max < 2^e
+    mx = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, red[w]);
+    const int e = row_exponent(mx);
     __syncthreads();
-    if (threadIdx.x == 0) expo[r] = e;
+    if (threadIdx.x == 0) expo[r] = e == ZERO_ROW ? 0 : e;
     __nv_bfloat16* o = out + r * (long long)ns * kp;
     for (long long k = threadIdx.x; k < kp; k += blockDim.x) {
-      double v = k < K ? ldexp(x[k], 6 - e) : 0.0;   // |v| < 64
+      int a[OZ_SLICES_MAX];
+      digits(k < K ? x[k] : 0.0, e, ns, a);
+#pragma unroll
+      for (int i = 0; i < OZ_SLICES_MAX; ++i)
+        if (i < ns) o[(long long)(reversed ? ns - 1 - i : i) * kp + k] = __int2bfloat16_rn(a[i]);
+    }
+  }
+}
+// The same for short rows: one warp per row.
+__global__ void __launch_bounds__(256) slice_rows_warp_kernel(const double* __restrict__ X, long long ldx,
+                                                              long long rows, long long K, long long kp, int reversed,
+                                                              int ns, __nv_bfloat16* __restrict__ out,
+                                                              int* __restrict__ expo) {
+  const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  const double* x = X + r * ldx;
+  unsigned long long mx = 0;
+  for (long long k = lane; k < K; k += 32) mx = max(mx, abs_bits(x[k]));
+  for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  const int e = row_exponent(mx);
+  if (lane == 0) expo[r] = e == ZERO_ROW ? 0 : e;
+  __nv_bfloat16* o = out + r * (long long)ns * kp;
+  for (long long k = lane; k < kp; k += 32) {
+    int a[OZ_SLICES_MAX];
+    digits(k < K ? x[k] : 0.0, e, ns, a);
+#pragma unroll
+    for (int i = 0; i < OZ_SLICES_MAX; ++i)
+      if (i < ns) o[(long long)(reversed ? ns - 1 - i : i) * kp + k] = __int2bfloat16_rn(a[i]);
+  }
+}
+
+// ---- complex operands of zgemm_oz, sliced straight from their strided storage ----------------------
+// Operand element (r, k) = Z[r * s_r + k * s_k] (complex), conjugated when conj. Real rows written:
+//   mode 0 (left operand):  row r      = (Re, Im) interleaved along k
+//   mode 1 (right operand): row r      = (Re, -Im)    and row R + r = (Im, Re)
+// so that sum over the 2K real columns of left row m times right row n (or R + n) gives the real
+// (imaginary) part of the complex product. Tiles of 32 rows x 64 complex k go through shared memory
+// so that both the strided reads and the row-contiguous slice writes are coalesced.
+constexpr int ZT_R = 32, ZT_K = 64;
+
+__device__ __forceinline__ void load_ztile(const cplx* __restrict__ Z, long long s_r, long long s_k, int conj,
+                                           long long R, long long K, long long r0, long long k0,
+                                           cplx (*tile)[ZT_K + 1]) {
+  if (s_r == 1) {   // consecutive rows are adjacent: threads along r
+    const int tr = threadIdx.x & 31;
+    for (int tk = threadIdx.x >> 5; tk < ZT_K; tk += blockDim.x >> 5) {
+      const long long r = r0 + tr, k = k0 + tk;
+      cplx v = make_cuDoubleComplex(0.0, 0.0);
+      if (r < R && k < K) v = Z[r + k * s_k];
+      if (conj) v.y = -v.y;
+      tile[tr][tk] = v;
+    }
+  } else {          // threads along k
+    for (int i = threadIdx.x; i < ZT_R * ZT_K; i += blockDim.x) {
+      const int tr = i / ZT_K, tk = i % ZT_K;
+      const long long r = r0 + tr, k = k0 + tk;
+      cplx v = make_cuDoubleComplex(0.0, 0.0);
+      if (r < R && k < K) v = Z[r * s_r + k * s_k];
+      if (conj) v.y = -v.y;
+      tile[tr][tk] = v;
+    }
+  }
+}
+
+// rowmax[r] = max over k of the bit patterns of |Re|, |Im| (atomic; rowmax zeroed by the caller)
+__global__ void __launch_bounds__(256) zrowmax_kernel(const cplx* __restrict__ Z, long long s_r, long long s_k,
+                                                      long long R, long long K,
+                                                      unsigned long long* __restrict__ rowmax) {
+  __shared__ cplx tile[ZT_R][ZT_K + 1];
+  const long long r0 = (long long)blockIdx.y * ZT_R, k0 = (long long)blockIdx.x * ZT_K;
+  load_ztile(Z, s_r, s_k, 0, R, K, r0, k0, tile);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int tr = warp; tr < ZT_R; tr += blockDim.x >> 5) {
+    unsigned long long mx = 0;
+    for (int tk = lane; tk < ZT_K; tk += 32) mx = max(mx, max(abs_bits(tile[tr][tk].x), abs_bits(tile[tr][tk].y)));
+    for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0 && r0 + tr < R && mx > 0) atomicMax(rowmax + r0 + tr, mx);
+  }
+}
+
+__global__ void __launch_bounds__(256) zslice_kernel(const cplx* __restrict__ Z, long long s_r, long long s_k,
+                                                     int conj, long long R, long long K, int mode,
+                                                     const unsigned long long* __restrict__ rowmax, long long kp,
+                                                     int reversed, int ns, __nv_bfloat16* __restrict__ out,
+                                                     int* __restrict__ expo) {
+  __shared__ cplx tile[ZT_R][ZT_K + 1];
+  const long long r0 = (long long)blockIdx.y * ZT_R, k0 = (long long)blockIdx.x * ZT_K;
+  load_ztile(Z, s_r, s_k, conj, R, K, r0, k0, tile);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int tr = warp; tr < ZT_R; tr += blockDim.x >> 5) {
+    const long long r = r0 + tr;
+    if (r >= R) break;
+    const int e = row_exponent(rowmax[r]);
+    if (k0 == 0 && lane == 0) {
+      expo[r] = e == ZERO_ROW ? 0 : e;
+      if (mode == 1) expo[R + r] = e == ZERO_ROW ? 0 : e;
+    }
+    __nv_bfloat16* o0 = out + r * (long long)ns * kp;
+    __nv_bfloat16* o1 = out + (R + r) * (long long)ns * kp;
+    for (int tk = lane; tk < ZT_K; tk += 32) {
+      const long long k = k0 + tk;
+      if (2 * k >= kp) break;
+      const cplx v = tile[tr][tk];
+      int are[OZ_SLICES_MAX], aim[OZ_SLICES_MAX];
+      digits(v.x, e, ns, are);
+      digits(v.y, e, ns, aim);
 #pragma unroll
       for (int i = 0; i < OZ_SLICES_MAX; ++i) {
         if (i < ns) {
-          double a = rint(v);
-          v = (v - a) * 128.0;
-          const int slot = reversed ? ns - 1 - i : i;
-          o[(long long)slot * kp + k] = __float2bfloat16_rn((float)a);
+          const long long off = (long long)(reversed ? ns - 1 - i : i) * kp + 2 * k;
+          if (mode == 0) {
+            *reinterpret_cast<__nv_bfloat162*>(o0 + off) = __halves2bfloat162(__int2bfloat16_rn(are[i]),
+                                                                               __int2bfloat16_rn(aim[i]));
+          } else {
+            *reinterpret_cast<__nv_bfloat162*>(o0 + off) = __halves2bfloat162(__int2bfloat16_rn(are[i]),
+                                                                               __int2bfloat16_rn(-aim[i]));
+            *reinterpret_cast<__nv_bfloat162*>(o1 + off) = __halves2bfloat162(__int2bfloat16_rn(aim[i]),
+                                                                               __int2bfloat16_rn(are[i]));
+          }
         }
       }
     }
@@ -75,34 +227,6 @@ __global__ void finalize_kernel(const double* __restrict__ acc, const int* __res
   }
 }
 
-// A'[m][2k + r] = (re, im) of op(A)(m, k), conj applied
-__global__ void zgather_a_kernel(const cplx* __restrict__ A, long long sam, long long sak, int conjA, long long M,
-                                 long long K, double* __restrict__ out) {
-  const long long total = M * K;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long m = t / K, k = t % K;
-    const cplx a = A[m * sam + k * sak];
-    out[m * 2 * K + 2 * k] = a.x;
-    out[m * 2 * K + 2 * k + 1] = conjA ? -a.y : a.y;
-  }
-}
-// B'[n][2k + r]: rows n < N give the real part of the product (Br, -Bi), rows N + n the imaginary
-// part (Bi, Br), with B(k, n) conjugated first when asked
-__global__ void zgather_b_kernel(const cplx* __restrict__ B, long long sbk, long long sbn, int conjB, long long K,
-                                 long long N, double* __restrict__ out) {
-  const long long total = N * K;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long n = t / K, k = t % K;
-    cplx b = B[k * sbk + n * sbn];
-    if (conjB) b.y = -b.y;
-    out[n * 2 * K + 2 * k] = b.x;
-    out[n * 2 * K + 2 * k + 1] = -b.y;
-    out[(N + n) * 2 * K + 2 * k] = b.y;
-    out[(N + n) * 2 * K + 2 * k + 1] = b.x;
-  }
-}
 // C(m, n) = alpha (T[m][n] + i T[m][N + n]) + beta C(m, n)
 __global__ void zscatter_kernel(const double* __restrict__ T, long long M, long long N, cplx* __restrict__ C,
                                 long long scm, long long scn, cplx alpha, cplx beta) {
@@ -129,19 +253,41 @@ double oz_min_macs() {
 void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s) {
   const long long M = g.M, N = g.N, K = g.K;
   GFCC_CHECK(g.batch == 1, GFCC_ERR_ARG, "zgemm_oz: no batches");
-  DBuf<double> Ar, Br, T;
-  Ar.alloc(M * 2 * K);
-  Br.alloc(2 * N * 2 * K);
-  zgather_a_kernel<<<grid_for(M * K), 256, 0, s>>>(g.A, g.sam, g.sak, g.conjA ? 1 : 0, M, K, Ar.p);
-  GFCC_LAUNCH_CHECK();
-  zgather_b_kernel<<<grid_for(N * K), 256, 0, s>>>(g.B, g.sbk, g.sbn, g.conjB ? 1 : 0, K, N, Br.p);
-  GFCC_LAUNCH_CHECK();
+  GFCC_CHECK(ns >= 2 && ns <= OZ_SLICES_MAX, GFCC_ERR_ARG, "zgemm_oz: 2..8 slices");
+  if (M <= 0 || N <= 0) return;
+  ProfScope prof(PROF_OZ_ZGEMM, 8.0 * (double)M * (double)N * (double)K, s);
   SlicedRows sa, sb;
-  oz_slice(Ar.p, 2 * K, M, 2 * K, false, sa, s, ns);
-  oz_slice(Br.p, 2 * K, 2 * N, 2 * K, true, sb, s, ns);
-  GFCC_CUDA(cudaStreamSynchronize(s));
-  Ar.release();
-  Br.release();
+  sa.rows = M; sa.kp = tc_pad_k(TcKind::BF16, 2 * K); sa.ns = ns; sa.reversed = false;
+  sb.rows = 2 * N; sb.kp = sa.kp; sb.ns = ns; sb.reversed = true;
+  sa.slices.alloc(sizeof(__nv_bfloat16) * M * ns * sa.kp);
+  sb.slices.alloc(sizeof(__nv_bfloat16) * 2 * N * ns * sb.kp);
+  sa.expo.alloc(M);
+  sb.expo.alloc(2 * N);
+  {
+    ProfScope ps(PROF_OZ_SLICE, 0.0, s);
+    DBuf<unsigned long long> mxa, mxb;
+    mxa.alloc(M);
+    mxb.alloc(N);
+    mxa.zero(s);
+    mxb.zero(s);
+    const long long kt = (sa.kp / 2 + ZT_K - 1) / ZT_K;   // k tiles covering the padded width
+    const long long kt_in = (K + ZT_K - 1) / ZT_K;
+    GFCC_CHECK((M + ZT_R - 1) / ZT_R <= 65535 && (N + ZT_R - 1) / ZT_R <= 65535, GFCC_ERR_ARG, "zgemm_oz: too many rows");
+    // A(m, k) = A[m sam + k sak]; B rows n: B(k, n) = B[k sbk + n sbn] -> r = n, s_r = sbn, s_k = sbk
+    zrowmax_kernel<<<dim3((unsigned)kt_in, (unsigned)((M + ZT_R - 1) / ZT_R)), 256, 0, s>>>(g.A, g.sam, g.sak, M, K, mxa.p);
+    GFCC_LAUNCH_CHECK();
+    zrowmax_kernel<<<dim3((unsigned)kt_in, (unsigned)((N + ZT_R - 1) / ZT_R)), 256, 0, s>>>(g.B, g.sbn, g.sbk, N, K, mxb.p);
+    GFCC_LAUNCH_CHECK();
+    zslice_kernel<<<dim3((unsigned)kt, (unsigned)((M + ZT_R - 1) / ZT_R)), 256, 0, s>>>(
+        g.A, g.sam, g.sak, g.conjA ? 1 : 0, M, K, 0, mxa.p, sa.kp, 0, ns,
+        reinterpret_cast<__nv_bfloat16*>(sa.slices.p), sa.expo.p);
+    GFCC_LAUNCH_CHECK();
+    zslice_kernel<<<dim3((unsigned)kt, (unsigned)((N + ZT_R - 1) / ZT_R)), 256, 0, s>>>(
+        g.B, g.sbn, g.sbk, g.conjB ? 1 : 0, N, K, 1, mxb.p, sb.kp, 1, ns,
+        reinterpret_cast<__nv_bfloat16*>(sb.slices.p), sb.expo.p);
+    GFCC_LAUNCH_CHECK();
+  }
+  DBuf<double> T;
   T.alloc(M * 2 * N);
   OzWork w;
   oz_gemm(sa, sb, M, 2 * N, T.p, 2 * N, 0.0, w, s);
@@ -157,10 +303,16 @@ void oz_slice_into(const double* X, long long ldx, long long nrows, long long K,
                    cudaStream_t s) {
   GFCC_CHECK(row0 >= 0 && row0 + nrows <= out.rows && K <= out.kp, GFCC_ERR_ARG, "oz_slice_into: out of range");
   if (nrows == 0) return;
-  const int grid = (int)std::min<long long>(nrows, 152LL * 16);
-  slice_kernel<<<grid, 256, 0, s>>>(X, ldx, nrows, K, out.kp, out.reversed ? 1 : 0, out.ns,
-                                    reinterpret_cast<__nv_bfloat16*>(out.slices.p) + row0 * out.ns * out.kp,
-                                    out.expo.p + row0);
+  ProfScope prof(PROF_OZ_SLICE, 0.0, s);
+  __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out.slices.p) + row0 * out.ns * out.kp;
+  if (out.kp <= 2048) {   // short rows: a warp per row
+    slice_rows_warp_kernel<<<(unsigned)((nrows * 32 + 255) / 256), 256, 0, s>>>(X, ldx, nrows, K, out.kp,
+                                                                                 out.reversed ? 1 : 0, out.ns, o,
+                                                                                 out.expo.p + row0);
+  } else {
+    const int grid = (int)std::min<long long>(nrows, 152LL * 16);
+    slice_kernel<<<grid, 256, 0, s>>>(X, ldx, nrows, K, out.kp, out.reversed ? 1 : 0, out.ns, o, out.expo.p + row0);
+  }
   GFCC_LAUNCH_CHECK();
 }
 
