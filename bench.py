@@ -198,6 +198,7 @@ def run_ours(args, rank, world):
                    7: "mor_eval", 8: "hbar_build", 9: "mor_panel_columns", 10: "mor_residual_basis",
                    12: "exact_slice_complex_gemms", 13: "exact_slicing"}
     phases = {phase_names[k]: round(G.profile_read(k)[1], 1) for k in phase_names}
+    cgs = G.profile_read(14)   # (launch groups, ms, algorithmic bytes) of the Arnoldi sweeps
     G.profile(False)
     clk = clocks.stop()
 
@@ -276,7 +277,13 @@ def run_ours(args, rank, world):
                    "solve_tol": args.solve_tol, "model_order": info["m"], "sampled_freqs": len(info["sampled"]),
                    "l2": "working set (operators >= 0.5 GB, Krylov bases) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
-        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "gemm_classes": kernels, "phases_ms": phases, "clocks": clk,
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "gemm_classes": kernels, "phases_ms": phases,
+        "hbm_kernels": {"arnoldi_cgs_sweeps (multidot, update_dot, update_norm)": {
+            "bound": "hbm", "steps": cgs[0], "ms": cgs[1], "algorithmic_bytes": cgs[2],
+            "achieved": cgs[2] / (cgs[1] / 1e3) / 1e9 if cgs[1] > 0 else None, "unit": "GB/s",
+            "peak": peaks.get("hbm_gbs"), "frac": (cgs[2] / (cgs[1] / 1e3) / 1e9) / peaks["hbm_gbs"]
+            if cgs[1] > 0 and peaks.get("hbm_gbs") else None}},
+        "clocks": clk,
         "full_fp64": full,
     }
 

@@ -201,8 +201,9 @@ long long gfcc_launch_count(void);
  * and projections; 7 reduced-model evaluation; 8 H-bar build; 9 column-by-column Gram-Schmidt
  * inside new blocks; 10 extension of the residual basis; 11 the ring-term GEMM of the low-precision
  * sigma (counted here instead of class 0); 12 whole FP64-accurate complex GEMMs on exact slices;
- * 13 splitting of FP64 rows into exact slices. Events are recorded on the stream each region is
- * launched on. */
+ * 13 splitting of FP64 rows into exact slices; 14 the fused Gram-Schmidt sweeps of FP32-basis Arnoldi
+ * steps (its "flops" field counts algorithmic HBM bytes instead). Events are recorded on the stream
+ * each region is launched on. */
 int gfcc_profile(int enable);
 
 /* Sum over the recorded launches of class cls: number of launches, device milliseconds (CUDA

@@ -56,7 +56,8 @@ enum ProfClass {
   PROF_TC_RING = 11,     // the ring-term GEMM of the low-precision sigma (tf32/bf16 tcgen05)
   PROF_OZ_ZGEMM = 12,    // whole FP64-accurate complex GEMMs on exact slices (operand gathers to scatter)
   PROF_OZ_SLICE = 13,    // splitting FP64 rows into exact bf16 slices (every use)
-  PROF_NCLASS = 14
+  PROF_KRYLOV_CGS = 14,  // the three fused Gram-Schmidt sweeps of an FP32-basis Arnoldi step (bytes)
+  PROF_NCLASS = 15
 };
 struct ProfScope {   // records CUDA events around one launch on stream s when profiling is on
   int cls;

@@ -639,6 +639,9 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
       if constexpr (sizeof(VT) == sizeof(cuFloatComplex)) {
         if (nv <= MD_MAXV) {
           fused = true;
+          // algorithmic HBM bytes of the three sweeps: V read three times, w read three times and
+          // written twice
+          ProfScope pcgs(PROF_KRYLOV_CGS, (3.0 * nv + 5.0) * (double)D * nb * sizeof(VT), s);
           const long long rows = std::max<long long>(256, (D + 255) / 256);
           const int nchunk = (int)((D + rows - 1) / rows);
           dim3 grid((nb + MD_TX - 1) / MD_TX, nchunk);

@@ -105,17 +105,24 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// work unit u -> (split z, M tile, N tile), N tiles fastest
+// work unit u -> (split z, M tile, N tile). Within a split the M tiles are taken in groups of gm:
+// a group runs through all N tiles with its gm M tiles fastest, so that the CTAs working at the same
+// time share gm A tiles (kept in L2) and about (grid / gm) B tiles, each read from DRAM about once
+// per group instead of once per wave.
 struct Unit {
   int z, mt, nt;
 };
-__device__ __forceinline__ Unit decode_unit(int u, int tiles_m, int tiles_n) {
+__device__ __forceinline__ Unit decode_unit(int u, int tiles_m, int tiles_n, int gm) {
   const int per_z = tiles_m * tiles_n;
   Unit r;
   r.z = u / per_z;
   const int t = u - r.z * per_z;
-  r.mt = t / tiles_n;
-  r.nt = t - r.mt * tiles_n;
+  const int g = t / (gm * tiles_n);
+  const int m0 = g * gm;
+  const int gsz = min(gm, tiles_m - m0);
+  const int w = t - m0 * tiles_n;
+  r.nt = w / gsz;
+  r.mt = m0 + (w - r.nt * gsz);
   return r;
 }
 
@@ -133,8 +140,8 @@ __device__ __forceinline__ Unit decode_unit(int u, int tiles_m, int tiles_n) {
 template <TcKind KIND, bool EXACT>
 __global__ void __launch_bounds__(EXACT ? 320 : 192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, void* Cv,
-                   long long ldc, long long M, long long N, int tiles_m, int tiles_n, int zs, int nk_total,
-                   int nk_split, long long split_stride, int beta, int* err) {
+                   long long ldc, long long M, long long N, int tiles_m, int tiles_n, int gm, int zs,
+                   int nk_total, int nk_split, long long split_stride, int beta, int* err) {
   constexpr int KB_ELEMS = KIND == TcKind::BF16 ? 64 : 32;
   constexpr int MMA_K_BYTES = 32;                            // K = 16 bf16 or 8 tf32 per instruction
   constexpr int NEPI = EXACT ? 8 : 4;                        // epilogue warps
@@ -179,7 +186,7 @@ __global__ void __launch_bounds__(EXACT ? 320 : 192, 1)
     if (lane == 0) {   // TMA producer
       long long g = 0;  // k-blocks issued by this CTA
       for (int u = blockIdx.x; u < total && !s_fail; u += gridDim.x) {
-        const Unit w = decode_unit(u, tiles_m, tiles_n);
+        const Unit w = decode_unit(u, tiles_m, tiles_n, gm);
         const int kb0 = w.z * nk_split;
         const int nk = max(0, min(nk_total, kb0 + nk_split) - kb0);
         for (int kb = 0; kb < nk; ++kb, ++g) {
@@ -201,7 +208,7 @@ __global__ void __launch_bounds__(EXACT ? 320 : 192, 1)
       int seg = 0;      // accumulations started (TMEM buffer = seg & 1)
       bool ok = true;
       for (int u = blockIdx.x; u < total && ok && !s_fail; u += gridDim.x) {
-        const Unit w = decode_unit(u, tiles_m, tiles_n);
+        const Unit w = decode_unit(u, tiles_m, tiles_n, gm);
         const int kb0 = w.z * nk_split;
         const int nk = max(0, min(nk_total, kb0 + nk_split) - kb0);
         const int nseg = nk == 0 ? 1 : (EXACT ? (nk + CH - 1) / CH : 1);
@@ -238,7 +245,7 @@ __global__ void __launch_bounds__(EXACT ? 320 : 192, 1)
     int seg = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < total && ok; u += gridDim.x) {
-      const Unit w = decode_unit(u, tiles_m, tiles_n);
+      const Unit w = decode_unit(u, tiles_m, tiles_n, gm);
       const int kb0 = w.z * nk_split;
       const int nk = max(0, min(nk_total, kb0 + nk_split) - kb0);
       const int nseg = nk == 0 ? 1 : (EXACT ? (nk + CH - 1) / CH : 1);
@@ -388,8 +395,11 @@ void launch(const CUtensorMap& ma, const CUtensorMap& mb, void* C, long long ldc
   }
   const long long units = (long long)zs * tiles_m * tiles_n;
   const int grid = (int)std::min<long long>(units, sm_count());
-  tc_gemm_kernel<K, EXACT><<<grid, EXACT ? 320 : 192, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, tiles_m, tiles_n, zs,
-                                                                       nk_total, nk_split, split_stride, beta, err);
+  // M-tile group: the A tiles of one group (128 rows x the split's K) fit in about 40 MB of L2
+  const long long a_tile_bytes = (long long)BM * nk_split * KB_BYTES;
+  const int gm = (int)std::max<long long>(1, std::min<long long>(tiles_m, (40LL << 20) / std::max(a_tile_bytes, 1LL)));
+  tc_gemm_kernel<K, EXACT><<<grid, EXACT ? 320 : 192, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, tiles_m, tiles_n, gm,
+                                                                       zs, nk_total, nk_split, split_stride, beta, err);
   GFCC_LAUNCH_CHECK();
 }
 
