@@ -10,6 +10,8 @@
 // solver reaches the same solution of Eq. xplin.
 #include "gfcc_internal.cuh"
 
+#include <type_traits>
+
 #include <algorithm>
 #include <cmath>
 
@@ -39,22 +41,31 @@ template <> __device__ __forceinline__ cuFloatComplex mk<cuFloatComplex>(double 
 // partial[chunk][i][c] = sum_{nu in chunk} conj(V_i[nu][c]) W[nu][c], i < nv (V_i = V + i*stride);
 // per-thread sums in the vector's precision, partials written in FP64
 constexpr int MD_TX = 32, MD_TY = 8, MD_MAXV = 32;
-template <typename VT>
-__global__ void multidot_kernel(const VT* __restrict__ V, long long vstride, int nv, const VT* __restrict__ W,
+// The kernels below are instantiated for NV = 4, 8, 16, 32 basis vectors (nv <= NV used): the
+// per-thread accumulators are NV long, so short bases run with fewer registers and more warps.
+template <typename F>
+void with_nv(int nv, F&& f) {
+  if (nv <= 4) f(std::integral_constant<int, 4>{});
+  else if (nv <= 8) f(std::integral_constant<int, 8>{});
+  else if (nv <= 16) f(std::integral_constant<int, 16>{});
+  else f(std::integral_constant<int, 32>{});
+}
+template <typename VT, int NV>
+__global__ void __launch_bounds__(256, NV <= 16 ? 2 : 1) multidot_kernel(const VT* __restrict__ V, long long vstride, int nv, const VT* __restrict__ W,
                                 long long D, int nb, long long rows_per_chunk, cplx* __restrict__ partial) {
   using R = typename RealOf<VT>::type;
   __shared__ cplx red[MD_TY][MD_TX];
   const int c = blockIdx.x * MD_TX + threadIdx.x;
   const long long r0 = blockIdx.y * rows_per_chunk;
   const long long r1 = min(D, r0 + rows_per_chunk);
-  R ax[MD_MAXV], ay[MD_MAXV];
+  R ax[NV], ay[NV];
 #pragma unroll
-  for (int i = 0; i < MD_MAXV; ++i) { ax[i] = R(0); ay[i] = R(0); }
+  for (int i = 0; i < NV; ++i) { ax[i] = R(0); ay[i] = R(0); }
   if (c < nb) {
     for (long long nu = r0 + threadIdx.y; nu < r1; nu += MD_TY) {
       const VT w = W[nu * nb + c];
 #pragma unroll
-      for (int i = 0; i < MD_MAXV; ++i) {
+      for (int i = 0; i < NV; ++i) {
         if (i < nv) {
           const VT vv = V[i * vstride + nu * nb + c];
           ax[i] += vv.x * w.x + vv.y * w.y;
@@ -65,7 +76,7 @@ __global__ void multidot_kernel(const VT* __restrict__ V, long long vstride, int
   }
   // static indices only, so that the accumulators stay in registers
 #pragma unroll
-  for (int i = 0; i < MD_MAXV; ++i) {
+  for (int i = 0; i < NV; ++i) {
     if (i < nv) {
       red[threadIdx.y][threadIdx.x] = make_cuDoubleComplex((double)ax[i], (double)ay[i]);
       __syncthreads();
@@ -81,51 +92,53 @@ __global__ void multidot_kernel(const VT* __restrict__ V, long long vstride, int
 
 // Fused CGS sweep: w <- w - sum_i V_i h_i (h = pass-1 coefficients), then partial sums of the
 // pass-2 coefficients conj(V_i) w over the chunk (same layout as multidot_kernel's partials).
-template <typename VT>
-__global__ void update_dot_kernel(const VT* __restrict__ V, long long vstride, int nv, VT* __restrict__ W,
+template <typename VT, int NV>
+__global__ void __launch_bounds__(256, NV <= 16 ? 2 : 1) update_dot_kernel(const VT* __restrict__ V, long long vstride, int nv, VT* __restrict__ W,
                                   long long D, int nb, long long rows_per_chunk, const cplx* __restrict__ h, int hld,
                                   cplx* __restrict__ partial) {
   using R = typename RealOf<VT>::type;
   __shared__ cplx red[MD_TY][MD_TX];
-  __shared__ VT hs[MD_MAXV][MD_TX];
+  __shared__ VT hs[NV][MD_TX];
   const int c = blockIdx.x * MD_TX + threadIdx.x;
   const long long r0 = blockIdx.y * rows_per_chunk;
   const long long r1 = min(D, r0 + rows_per_chunk);
-  for (int i = threadIdx.y; i < MD_MAXV; i += MD_TY) {
+  for (int i = threadIdx.y; i < NV; i += MD_TY) {
     VT v;
     v.x = (c < nb && i < nv) ? (R)h[(long long)c * hld + i].x : R(0);
     v.y = (c < nb && i < nv) ? (R)h[(long long)c * hld + i].y : R(0);
     hs[i][threadIdx.x] = v;
   }
   __syncthreads();
-  R ax[MD_MAXV], ay[MD_MAXV];
+  R ax[NV], ay[NV];
 #pragma unroll
-  for (int i = 0; i < MD_MAXV; ++i) { ax[i] = R(0); ay[i] = R(0); }
+  for (int i = 0; i < NV; ++i) { ax[i] = R(0); ay[i] = R(0); }
   if (c < nb) {
     for (long long nu = r0 + threadIdx.y; nu < r1; nu += MD_TY) {
-      VT vv[MD_MAXV];
       VT w = W[nu * nb + c];
 #pragma unroll
-      for (int i = 0; i < MD_MAXV; ++i) {
+      for (int i = 0; i < NV; ++i) {
         if (i < nv) {
-          vv[i] = V[i * vstride + nu * nb + c];
+          const VT vv = V[i * vstride + nu * nb + c];
           const VT hv = hs[i][threadIdx.x];
-          w.x -= vv[i].x * hv.x - vv[i].y * hv.y;
-          w.y -= vv[i].x * hv.y + vv[i].y * hv.x;
+          w.x -= vv.x * hv.x - vv.y * hv.y;
+          w.y -= vv.x * hv.y + vv.y * hv.x;
         }
       }
       W[nu * nb + c] = w;
+      // the basis entries are read again (from L1: this thread loaded them just above) instead of
+      // being held in registers, which keeps the kernel at two blocks per SM
 #pragma unroll
-      for (int i = 0; i < MD_MAXV; ++i) {
+      for (int i = 0; i < NV; ++i) {
         if (i < nv) {
-          ax[i] += vv[i].x * w.x + vv[i].y * w.y;
-          ay[i] += vv[i].x * w.y - vv[i].y * w.x;
+          const VT vv = V[i * vstride + nu * nb + c];
+          ax[i] += vv.x * w.x + vv.y * w.y;
+          ay[i] += vv.x * w.y - vv.y * w.x;
         }
       }
     }
   }
 #pragma unroll
-  for (int i = 0; i < MD_MAXV; ++i) {
+  for (int i = 0; i < NV; ++i) {
     if (i < nv) {
       red[threadIdx.y][threadIdx.x] = make_cuDoubleComplex((double)ax[i], (double)ay[i]);
       __syncthreads();
@@ -140,17 +153,17 @@ __global__ void update_dot_kernel(const VT* __restrict__ V, long long vstride, i
 }
 
 // Fused final sweep: w <- w - sum_i V_i h_i, with partial sums of |w|^2 per column (nv = 1 layout)
-template <typename VT>
-__global__ void update_norm_kernel(const VT* __restrict__ V, long long vstride, int nv, VT* __restrict__ W,
+template <typename VT, int NV>
+__global__ void __launch_bounds__(256, NV <= 16 ? 2 : 1) update_norm_kernel(const VT* __restrict__ V, long long vstride, int nv, VT* __restrict__ W,
                                    long long D, int nb, long long rows_per_chunk, const cplx* __restrict__ h, int hld,
                                    cplx* __restrict__ partial) {
   using R = typename RealOf<VT>::type;
   __shared__ cplx red[MD_TY][MD_TX];
-  __shared__ VT hs[MD_MAXV][MD_TX];
+  __shared__ VT hs[NV][MD_TX];
   const int c = blockIdx.x * MD_TX + threadIdx.x;
   const long long r0 = blockIdx.y * rows_per_chunk;
   const long long r1 = min(D, r0 + rows_per_chunk);
-  for (int i = threadIdx.y; i < MD_MAXV; i += MD_TY) {
+  for (int i = threadIdx.y; i < NV; i += MD_TY) {
     VT v;
     v.x = (c < nb && i < nv) ? (R)h[(long long)c * hld + i].x : R(0);
     v.y = (c < nb && i < nv) ? (R)h[(long long)c * hld + i].y : R(0);
@@ -162,7 +175,7 @@ __global__ void update_norm_kernel(const VT* __restrict__ V, long long vstride, 
     for (long long nu = r0 + threadIdx.y; nu < r1; nu += MD_TY) {
       VT w = W[nu * nb + c];
 #pragma unroll
-      for (int i = 0; i < MD_MAXV; ++i) {
+      for (int i = 0; i < NV; ++i) {
         if (i < nv) {
           const VT vv = V[i * vstride + nu * nb + c];
           const VT hv = hs[i][threadIdx.x];
@@ -426,7 +439,7 @@ static void col_norms(const VT* W, long long D, int nb, double* out, DBuf<cplx>&
   partial.alloc((long long)nchunk * nb);
   tmp.alloc(nb);
   dim3 grid((nb + MD_TX - 1) / MD_TX, nchunk);
-  multidot_kernel<VT><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(W, 0, 1, W, D, nb, rows, partial.p);
+  multidot_kernel<VT, 4><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(W, 0, 1, W, D, nb, rows, partial.p);
   GFCC_LAUNCH_CHECK();
   reduce_partial_kernel<<<(nb + 255) / 256, 256, 0, s>>>(partial.p, nchunk, 1, nb, tmp.p, 1, 0, 0);
   GFCC_LAUNCH_CHECK();
@@ -444,7 +457,10 @@ static void multidot(const VT* V, long long vstride, int nv, const VT* W, long l
     const int nchunk = (int)((D + rows - 1) / rows);
     partial.alloc((long long)nchunk * n * nb);
     dim3 grid((nb + MD_TX - 1) / MD_TX, nchunk);
-    multidot_kernel<VT><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(V + i0 * vstride, vstride, n, W, D, nb, rows, partial.p);
+    with_nv(n, [&](auto NVc) {
+      multidot_kernel<VT, decltype(NVc)::value><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(V + i0 * vstride, vstride, n, W, D,
+                                                                                  nb, rows, partial.p);
+    });
     GFCC_LAUNCH_CHECK();
     reduce_partial_kernel<<<(n * nb + 255) / 256, 256, 0, s>>>(partial.p, nchunk, n, nb, h, hld, hoff + i0,
                                                                accumulate ? 1 : 0);
@@ -650,16 +666,22 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
                                                              nb, 0);
           GFCC_LAUNCH_CHECK();
           partial.alloc((long long)nchunk * nv * nb);
-          update_dot_kernel<VT><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(V.p, vstride, nv, Ww.p, D, nb, rows, hb.p, k + 1,
-                                                                     partial.p);
+          with_nv(nv, [&](auto NVc) {
+            update_dot_kernel<VT, decltype(NVc)::value><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(V.p, vstride, nv, Ww.p, D,
+                                                                                           nb, rows, hb.p, k + 1,
+                                                                                           partial.p);
+          });
           GFCC_LAUNCH_CHECK();
           reduce_partial_kernel<<<(nv * nb + 255) / 256, 256, 0, s>>>(partial.p, nchunk, nv, nb, hb.p, k + 1, 0, 0);
           GFCC_LAUNCH_CHECK();
           add_h_kernel<<<(nb * nv + 255) / 256, 256, 0, s>>>(hb.p, k + 1, H.p + (long long)j * (k + 1), (k + 1) * k, nv,
                                                              nb, 1);
           GFCC_LAUNCH_CHECK();
-          update_norm_kernel<VT><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(V.p, vstride, nv, Ww.p, D, nb, rows, hb.p, k + 1,
-                                                                      partial.p);
+          with_nv(nv, [&](auto NVc) {
+            update_norm_kernel<VT, decltype(NVc)::value><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(V.p, vstride, nv, Ww.p, D,
+                                                                                            nb, rows, hb.p, k + 1,
+                                                                                            partial.p);
+          });
           GFCC_LAUNCH_CHECK();
           reduce_partial_kernel<<<(nb + 255) / 256, 256, 0, s>>>(partial.p, nchunk, 1, nb, tmpc.p, 1, 0, 0);
           GFCC_LAUNCH_CHECK();
