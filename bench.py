@@ -199,6 +199,9 @@ def run_ours(args, rank, world):
                    12: "exact_slice_complex_gemms", 13: "exact_slicing"}
     phases = {phase_names[k]: round(G.profile_read(k)[1], 1) for k in phase_names}
     cgs = G.profile_read(14)   # (launch groups, ms, algorithmic bytes) of the Arnoldi sweeps
+    cgs_parts = {name: G.profile_read(k) for k, name in
+                 ((15, "multidot_kernel"), (16, "update_dot_kernel"), (17, "update_norm_kernel"),
+                  (18, "all three, batches < 32 columns"))}
     G.profile(False)
     clk = clocks.stop()
 
@@ -282,7 +285,9 @@ def run_ours(args, rank, world):
             "bound": "hbm", "steps": cgs[0], "ms": cgs[1], "algorithmic_bytes": cgs[2],
             "achieved": cgs[2] / (cgs[1] / 1e3) / 1e9 if cgs[1] > 0 else None, "unit": "GB/s",
             "peak": peaks.get("hbm_gbs"), "frac": (cgs[2] / (cgs[1] / 1e3) / 1e9) / peaks["hbm_gbs"]
-            if cgs[1] > 0 and peaks.get("hbm_gbs") else None}},
+            if cgs[1] > 0 and peaks.get("hbm_gbs") else None,
+            "parts": {name: {"launches": n, "ms": round(ms, 2), "achieved_gbs": round(b / (ms / 1e3) / 1e9, 1)
+                             if ms > 0 else None} for name, (n, ms, b) in cgs_parts.items()}}},
         "clocks": clk,
         "full_fp64": full,
     }

@@ -760,7 +760,10 @@ void gfcc_free(gfcc_t c) { delete c; }
 
 }  // extern "C"
 
-gfcc_ctx::~gfcc_ctx() { gfcc::free_low_precision(this); }
+gfcc_ctx::~gfcc_ctx() {
+  gfcc::free_low_precision(this);
+  gfcc::zgemm_work_free(this);
+}
 
 extern "C" {
 

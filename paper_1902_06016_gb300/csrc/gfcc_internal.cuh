@@ -57,7 +57,11 @@ enum ProfClass {
   PROF_OZ_ZGEMM = 12,    // whole FP64-accurate complex GEMMs on exact slices (operand gathers to scatter)
   PROF_OZ_SLICE = 13,    // splitting FP64 rows into exact bf16 slices (every use)
   PROF_KRYLOV_CGS = 14,  // the three fused Gram-Schmidt sweeps of an FP32-basis Arnoldi step (bytes)
-  PROF_NCLASS = 15
+  PROF_CGS_MULTIDOT = 15,     // first sweep alone (batches of >= 32 columns; bytes)
+  PROF_CGS_UPDATE_DOT = 16,   // second sweep alone (batches of >= 32 columns; bytes)
+  PROF_CGS_UPDATE_NORM = 17,  // third sweep alone (batches of >= 32 columns; bytes)
+  PROF_CGS_SMALL_NB = 18,     // the three sweeps of batches of fewer than 32 columns (bytes)
+  PROF_NCLASS = 19
 };
 struct ProfScope {   // records CUDA events around one launch on stream s when profiling is on
   int cls;
@@ -187,6 +191,7 @@ struct gfcc_ctx {
   gfcc::DBuf<double> bvec;   // [n][D]  b_p rows
   gfcc::DBuf<double> cvec;   // [n][D]  c_q rows
   gfcc::DBuf<double> t1, t2; // kept for derivative work
+  void* zwork = nullptr;     // grow-only workspace of the exact-slice complex GEMMs (ozaki.cu)
   ~gfcc_ctx();
 };
 
@@ -212,8 +217,12 @@ struct ZGemmDesc {
   const cplx* B = nullptr; long long sbk = 0, sbn = 0, bsb = 0; bool conjB = false;
   cplx* C = nullptr; long long scm = 0, scn = 0, bsc = 0;
   cplx alpha = {1.0, 0.0}, beta = {0.0, 0.0};
+  void* work = nullptr;   // optional grow-only workspace (zgemm_work(ctx)) for the exact-slice path
 };
 void zgemm(const ZGemmDesc& g, cudaStream_t s);
+// the context's workspace for exact-slice complex GEMMs (created on first use, freed with the context)
+void* zgemm_work(gfcc_ctx* c);
+void zgemm_work_free(gfcc_ctx* c);
 
 // row-major contiguous helpers
 void dgemm_rm(int M, int N, int K, double alpha, const double* A, int lda, bool transA,

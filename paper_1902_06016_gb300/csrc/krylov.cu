@@ -38,11 +38,8 @@ template <> __device__ __forceinline__ cuFloatComplex mk<cuFloatComplex>(double 
   return make_cuFloatComplex((float)re, (float)im);
 }
 
-// partial[chunk][i][c] = sum_{nu in chunk} conj(V_i[nu][c]) W[nu][c], i < nv (V_i = V + i*stride);
-// per-thread sums in the vector's precision, partials written in FP64
 constexpr int MD_TX = 32, MD_TY = 8, MD_MAXV = 32;
-// The kernels below are instantiated for NV = 4, 8, 16, 32 basis vectors (nv <= NV used): the
-// per-thread accumulators are NV long, so short bases run with fewer registers and more warps.
+// The kernels below are instantiated for NV = 4, 8, 16, 32 basis vectors (nv <= NV used).
 template <typename F>
 void with_nv(int nv, F&& f) {
   if (nv <= 4) f(std::integral_constant<int, 4>{});
@@ -50,106 +47,141 @@ void with_nv(int nv, F&& f) {
   else if (nv <= 16) f(std::integral_constant<int, 16>{});
   else f(std::integral_constant<int, 32>{});
 }
+
+// partial[chunk][i][c] = sum_{nu in chunk} conj(V_i[nu][c]) W[nu][c], i < nv (V_i = V + i*stride);
+// per-thread sums in the vector's precision, partials written in FP64.
+// Block (MD_TX columns) x (MD_TY): the MD_TY thread rows form IG = NV/8 groups (at least 1); group g
+// owns the accumulators of basis vectors [g NPG, (g+1) NPG), NPG = NV / IG, and its threads stride the
+// chunk's rows by MD_TY / IG. Fewer accumulators per thread keep the registers, and so the number of
+// resident warps, independent of the basis size.
+template <int NV> struct MdGroups {
+  static constexpr int IG = NV >= 16 ? NV / 8 : 1;
+  static constexpr int NPG = NV / IG;
+  static constexpr int RPG = MD_TY / IG;   // thread rows per group
+};
+// sum the per-thread values acc[li] of group g over its RPG thread rows; partial for i = g NPG + li
+template <typename VT, int NV, typename R>
+__device__ __forceinline__ void md_reduce(const R (&ax)[MdGroups<NV>::NPG], const R (&ay)[MdGroups<NV>::NPG], int nv,
+                                          int c, int nb, cplx* __restrict__ partial, cplx (*red)[MD_TX]) {
+  using G = MdGroups<NV>;
+  const int g = threadIdx.y / G::RPG, yr = threadIdx.y % G::RPG;
+#pragma unroll
+  for (int li = 0; li < G::NPG; ++li) {
+    red[threadIdx.y][threadIdx.x] = make_cuDoubleComplex((double)ax[li], (double)ay[li]);
+    __syncthreads();
+    const int i = g * G::NPG + li;
+    if (yr == 0 && c < nb && i < nv) {
+      cplx s = red[threadIdx.y][threadIdx.x];
+      for (int k = 1; k < G::RPG; ++k) { s.x += red[threadIdx.y + k][threadIdx.x].x; s.y += red[threadIdx.y + k][threadIdx.x].y; }
+      partial[((long long)blockIdx.y * nv + i) * nb + c] = s;
+    }
+    __syncthreads();
+  }
+}
+
 template <typename VT, int NV>
-__global__ void __launch_bounds__(256, NV <= 16 ? 2 : 1) multidot_kernel(const VT* __restrict__ V, long long vstride, int nv, const VT* __restrict__ W,
-                                long long D, int nb, long long rows_per_chunk, cplx* __restrict__ partial) {
+__global__ void __launch_bounds__(256, 2) multidot_kernel(const VT* __restrict__ V, long long vstride, int nv,
+                                                          const VT* __restrict__ W, long long D, int nb,
+                                                          long long rows_per_chunk, cplx* __restrict__ partial) {
   using R = typename RealOf<VT>::type;
+  using G = MdGroups<NV>;
   __shared__ cplx red[MD_TY][MD_TX];
   const int c = blockIdx.x * MD_TX + threadIdx.x;
+  const int g = threadIdx.y / G::RPG, yr = threadIdx.y % G::RPG;
   const long long r0 = blockIdx.y * rows_per_chunk;
   const long long r1 = min(D, r0 + rows_per_chunk);
-  R ax[NV], ay[NV];
+  const VT* Vg = V + (long long)g * G::NPG * vstride;
+  const int ng = nv - g * G::NPG;   // vectors of this group present (may be <= 0)
+  R ax[G::NPG], ay[G::NPG];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) { ax[i] = R(0); ay[i] = R(0); }
-  if (c < nb) {
-    for (long long nu = r0 + threadIdx.y; nu < r1; nu += MD_TY) {
+  for (int i = 0; i < G::NPG; ++i) { ax[i] = R(0); ay[i] = R(0); }
+  if (c < nb && ng > 0) {
+    for (long long nu = r0 + yr; nu < r1; nu += G::RPG) {
       const VT w = W[nu * nb + c];
 #pragma unroll
-      for (int i = 0; i < NV; ++i) {
-        if (i < nv) {
-          const VT vv = V[i * vstride + nu * nb + c];
+      for (int i = 0; i < G::NPG; ++i) {
+        if (i < ng) {
+          const VT vv = Vg[i * vstride + nu * nb + c];
           ax[i] += vv.x * w.x + vv.y * w.y;
           ay[i] += vv.x * w.y - vv.y * w.x;
         }
       }
     }
   }
-  // static indices only, so that the accumulators stay in registers
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    if (i < nv) {
-      red[threadIdx.y][threadIdx.x] = make_cuDoubleComplex((double)ax[i], (double)ay[i]);
-      __syncthreads();
-      if (threadIdx.y == 0 && c < nb) {
-        cplx s = red[0][threadIdx.x];
-        for (int k = 1; k < MD_TY; ++k) { s.x += red[k][threadIdx.x].x; s.y += red[k][threadIdx.x].y; }
-        partial[((long long)blockIdx.y * nv + i) * nb + c] = s;
-      }
-      __syncthreads();
-    }
-  }
+  md_reduce<VT, NV, R>(ax, ay, nv, c, nb, partial, red);
 }
 
 // Fused CGS sweep: w <- w - sum_i V_i h_i (h = pass-1 coefficients), then partial sums of the
 // pass-2 coefficients conj(V_i) w over the chunk (same layout as multidot_kernel's partials).
+// Thread (x, y) walks rows y, y + MD_TY, ... of column x: it keeps the row's basis entries in
+// registers for the update and adds conj(V_i) w' into its own shared-memory accumulators
+// acc[y][i][x] (no synchronisation inside the loop, no per-thread accumulator arrays), which are
+// summed over y at the end.
 template <typename VT, int NV>
-__global__ void __launch_bounds__(256, NV <= 16 ? 2 : 1) update_dot_kernel(const VT* __restrict__ V, long long vstride, int nv, VT* __restrict__ W,
-                                  long long D, int nb, long long rows_per_chunk, const cplx* __restrict__ h, int hld,
-                                  cplx* __restrict__ partial) {
+__global__ void __launch_bounds__(256, 2) update_dot_kernel(const VT* __restrict__ V, long long vstride, int nv,
+                                                            VT* __restrict__ W, long long D, int nb,
+                                                            long long rows_per_chunk, const cplx* __restrict__ h,
+                                                            int hld, cplx* __restrict__ partial) {
   using R = typename RealOf<VT>::type;
-  __shared__ cplx red[MD_TY][MD_TX];
-  __shared__ VT hs[NV][MD_TX];
-  const int c = blockIdx.x * MD_TX + threadIdx.x;
+  extern __shared__ __align__(16) unsigned char ud_smem[];
+  VT* acc = reinterpret_cast<VT*>(ud_smem);         // [MD_TY][NV][MD_TX]
+  VT* hs = acc + MD_TY * NV * MD_TX;                // [NV][MD_TX] coefficients
+  const int x = threadIdx.x, y = threadIdx.y;
+  const int c = blockIdx.x * MD_TX + x;
   const long long r0 = blockIdx.y * rows_per_chunk;
   const long long r1 = min(D, r0 + rows_per_chunk);
-  for (int i = threadIdx.y; i < NV; i += MD_TY) {
+  for (int i = y; i < NV; i += MD_TY) {
     VT v;
     v.x = (c < nb && i < nv) ? (R)h[(long long)c * hld + i].x : R(0);
     v.y = (c < nb && i < nv) ? (R)h[(long long)c * hld + i].y : R(0);
-    hs[i][threadIdx.x] = v;
+    hs[i * MD_TX + x] = v;
   }
-  __syncthreads();
-  R ax[NV], ay[NV];
+  VT* my = acc + (long long)y * NV * MD_TX + x;     // acc[y][i][x] at my[i * MD_TX]
 #pragma unroll
-  for (int i = 0; i < NV; ++i) { ax[i] = R(0); ay[i] = R(0); }
+  for (int i = 0; i < NV; ++i) { VT z; z.x = R(0); z.y = R(0); my[i * MD_TX] = z; }
+  __syncthreads();
   if (c < nb) {
-    for (long long nu = r0 + threadIdx.y; nu < r1; nu += MD_TY) {
+    for (long long nu = r0 + y; nu < r1; nu += MD_TY) {
+      VT vv[NV];
       VT w = W[nu * nb + c];
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
         if (i < nv) {
-          const VT vv = V[i * vstride + nu * nb + c];
-          const VT hv = hs[i][threadIdx.x];
-          w.x -= vv.x * hv.x - vv.y * hv.y;
-          w.y -= vv.x * hv.y + vv.y * hv.x;
+          vv[i] = V[i * vstride + nu * nb + c];
+          const VT hv = hs[i * MD_TX + x];
+          w.x -= vv[i].x * hv.x - vv[i].y * hv.y;
+          w.y -= vv[i].x * hv.y + vv[i].y * hv.x;
         }
       }
       W[nu * nb + c] = w;
-      // the basis entries are read again (from L1: this thread loaded them just above) instead of
-      // being held in registers, which keeps the kernel at two blocks per SM
 #pragma unroll
       for (int i = 0; i < NV; ++i) {
         if (i < nv) {
-          const VT vv = V[i * vstride + nu * nb + c];
-          ax[i] += vv.x * w.x + vv.y * w.y;
-          ay[i] += vv.x * w.y - vv.y * w.x;
+          VT a = my[i * MD_TX];
+          a.x += vv[i].x * w.x + vv[i].y * w.y;
+          a.y += vv[i].x * w.y - vv[i].y * w.x;
+          my[i * MD_TX] = a;
         }
       }
     }
   }
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    if (i < nv) {
-      red[threadIdx.y][threadIdx.x] = make_cuDoubleComplex((double)ax[i], (double)ay[i]);
-      __syncthreads();
-      if (threadIdx.y == 0 && c < nb) {
-        cplx s = red[0][threadIdx.x];
-        for (int k = 1; k < MD_TY; ++k) { s.x += red[k][threadIdx.x].x; s.y += red[k][threadIdx.x].y; }
-        partial[((long long)blockIdx.y * nv + i) * nb + c] = s;
+  __syncthreads();
+  for (int t = y * MD_TX + x; t < NV * MD_TX; t += MD_TX * MD_TY) {
+    const int i = t / MD_TX, xx = t % MD_TX, cc = blockIdx.x * MD_TX + xx;
+    if (i < nv && cc < nb) {
+      double sx = 0.0, sy = 0.0;
+      for (int yy = 0; yy < MD_TY; ++yy) {
+        const VT a = acc[((long long)yy * NV + i) * MD_TX + xx];
+        sx += (double)a.x;
+        sy += (double)a.y;
       }
-      __syncthreads();
+      partial[((long long)blockIdx.y * nv + i) * nb + cc] = make_cuDoubleComplex(sx, sy);
     }
   }
+}
+template <typename VT, int NV>
+constexpr size_t update_dot_smem() {
+  return sizeof(VT) * ((size_t)MD_TY * NV * MD_TX + (size_t)NV * MD_TX);
 }
 
 // Fused final sweep: w <- w - sum_i V_i h_i, with partial sums of |w|^2 per column (nv = 1 layout)
@@ -519,6 +551,11 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
   nrm.alloc(nb0); bnorm.alloc(nb0); thr.alloc(nb0); kc.alloc(nb0); live.alloc(nb0); nlive.alloc(1); cols.alloc(nb0);
   shw.alloc(nb0);
   flag.alloc(1);
+  {  // chunk partial sums of the Gram-Schmidt sweeps and norms, at their largest (no regrowth per step)
+    const long long rows_md = std::max<long long>(256, (D + 255) / 256), rows_cn = std::max<long long>(256, (D + 511) / 512);
+    const long long nch = std::max((D + rows_md - 1) / rows_md * (k + 1), (D + rows_cn - 1) / rows_cn);
+    partial.alloc(nch * nb0);
+  }
   GFCC_CUDA(cudaMemcpyAsync(Bw.p, Bin, sizeof(cplx) * D * nb0, cudaMemcpyDeviceToDevice, s));
   GFCC_CUDA(cudaMemcpyAsync(shw.p, shifts_dev, sizeof(cplx) * nb0, cudaMemcpyDeviceToDevice, s));
   Xw.zero(s);
@@ -661,28 +698,46 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
           const long long rows = std::max<long long>(256, (D + 255) / 256);
           const int nchunk = (int)((D + rows - 1) / rows);
           dim3 grid((nb + MD_TX - 1) / MD_TX, nchunk);
-          multidot<VT>(V.p, vstride, nv, Ww.p, D, nb, hb.p, k + 1, 0, false, partial, s);
+          const double vbytes = (double)D * nb * sizeof(VT);   // one basis vector of the batch
+          const int small = nb < MD_TX ? 1 : 0;
+          {
+            ProfScope pk(small ? PROF_CGS_SMALL_NB : PROF_CGS_MULTIDOT, (nv + 1.0) * vbytes, s);
+            multidot<VT>(V.p, vstride, nv, Ww.p, D, nb, hb.p, k + 1, 0, false, partial, s);
+          }
           add_h_kernel<<<(nb * nv + 255) / 256, 256, 0, s>>>(hb.p, k + 1, H.p + (long long)j * (k + 1), (k + 1) * k, nv,
                                                              nb, 0);
           GFCC_LAUNCH_CHECK();
           partial.alloc((long long)nchunk * nv * nb);
-          with_nv(nv, [&](auto NVc) {
-            update_dot_kernel<VT, decltype(NVc)::value><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(V.p, vstride, nv, Ww.p, D,
-                                                                                           nb, rows, hb.p, k + 1,
-                                                                                           partial.p);
-          });
-          GFCC_LAUNCH_CHECK();
+          {
+            ProfScope pk(small ? PROF_CGS_SMALL_NB : PROF_CGS_UPDATE_DOT, (nv + 2.0) * vbytes, s);
+            with_nv(nv, [&](auto NVc) {
+              constexpr int NVv = decltype(NVc)::value;
+              constexpr size_t smem = update_dot_smem<VT, NVv>();
+              static bool attr = false;   // per instantiation, once per process
+              if (!attr) {
+                GFCC_CUDA(cudaFuncSetAttribute(update_dot_kernel<VT, NVv>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+                attr = true;
+              }
+              update_dot_kernel<VT, NVv><<<grid, dim3(MD_TX, MD_TY), smem, s>>>(V.p, vstride, nv, Ww.p, D, nb, rows,
+                                                                                hb.p, k + 1, partial.p);
+            });
+            GFCC_LAUNCH_CHECK();
+          }
           reduce_partial_kernel<<<(nv * nb + 255) / 256, 256, 0, s>>>(partial.p, nchunk, nv, nb, hb.p, k + 1, 0, 0);
           GFCC_LAUNCH_CHECK();
           add_h_kernel<<<(nb * nv + 255) / 256, 256, 0, s>>>(hb.p, k + 1, H.p + (long long)j * (k + 1), (k + 1) * k, nv,
                                                              nb, 1);
           GFCC_LAUNCH_CHECK();
-          with_nv(nv, [&](auto NVc) {
-            update_norm_kernel<VT, decltype(NVc)::value><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(V.p, vstride, nv, Ww.p, D,
-                                                                                            nb, rows, hb.p, k + 1,
-                                                                                            partial.p);
-          });
-          GFCC_LAUNCH_CHECK();
+          {
+            ProfScope pk(small ? PROF_CGS_SMALL_NB : PROF_CGS_UPDATE_NORM, (nv + 2.0) * vbytes, s);
+            with_nv(nv, [&](auto NVc) {
+              update_norm_kernel<VT, decltype(NVc)::value><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(V.p, vstride, nv, Ww.p,
+                                                                                              D, nb, rows, hb.p, k + 1,
+                                                                                              partial.p);
+            });
+            GFCC_LAUNCH_CHECK();
+          }
           reduce_partial_kernel<<<(nb + 255) / 256, 256, 0, s>>>(partial.p, nchunk, 1, nb, tmpc.p, 1, 0, 0);
           GFCC_LAUNCH_CHECK();
           finalize_norm_kernel<<<(nb + 255) / 256, 256, 0, s>>>(tmpc.p, nb, nrm.p);

@@ -1,19 +1,24 @@
 // Model-order reduction of the MIMO system (Eqs. gfcclineqn and model) on the GPU, FP64.
 //
 // * Subspace: S holds orthonormalised solutions X_p(w_k). New columns lose their components along
-//   the current S by block classical Gram-Schmidt (two passes), then along each other column by
-//   column (two passes); a column is kept when its norm after the passes is >= drop_tol times its
-//   norm before, else dropped. Orthonormality is in the complex inner product, so the projections
-//   written S^T in Eq. model are applied as S^H.
+//   the current S by block classical Gram-Schmidt (two passes), then within the block panel by panel:
+//   Cholesky QR twice for well-conditioned panels, otherwise column by column (two passes); a column is
+//   kept when its norm after the passes is >= drop_tol times its norm before, else dropped.
+//   Orthonormality is in the complex inner product, so the projections written S^T in Eq. model are
+//   applied as S^H.
 // * Z = M S comes for free: every solved column satisfies M x = b - (w - i eta) x - r with the FP64
 //   residual r of the solver, and every linear combination applied to S is applied to Z as well.
 // * Reduced model: Hhat = S^H Z, bhat = S^H b, chat = c^T S, updated incrementally.
 // * Evaluation at many frequencies: Hhat is reduced once to upper Hessenberg form by Householder
-//   reflections (applied alongside to bhat, chat and the residual Gram data); each frequency is then
-//   an O(m^2) shifted Hessenberg solve (one CTA per frequency, partial pivoting between adjacent
-//   rows), followed by Ghat_pq = chat_q^T yhat_p and A = -(1/pi) sum_p Im Ghat_pp.
-// * Residual estimate for refinement: r = (w - i eta) S y + Z y - b is orthogonal to S (Galerkin),
-//   so ||r||^2 = y^H (Z^H Z - Hhat^H Hhat) y - 2 Re y^H (Z^H b - Hhat^H bhat) + ||b||^2 - ||bhat||^2.
+//   reflections (applied alongside to bhat, chat and the residual coefficients); each frequency is
+//   then an O(m^2) shifted Hessenberg solve (one CTA per frequency, partial pivoting between adjacent
+//   rows). Ghat_pq = chat_q^T yhat_p for all frequencies is one complex GEMM, and A = -(1/pi) sum_p
+//   Im Ghat_pp.
+// * Residual estimate for refinement: the columns of [B, S, Z] are kept as coefficients in an
+//   orthonormal basis Q of their span (extended with every new block), so that the residual
+//   r = (w - i eta) S y + Z y - b has the coefficient vector (w - i eta) R_S y + R_Z y - R_B e_p and
+//   ||r|| is its 2-norm, without the cancellation of a Gram-matrix formula; the coefficients of all
+//   frequencies are two complex GEMMs.
 #include "gfcc_internal.cuh"
 #include "ozaki.cuh"
 
@@ -121,44 +126,38 @@ __global__ void house_right_update_kernel(cplx* __restrict__ A, long long lda, i
 
 // ---- per-frequency shifted Hessenberg solve --------------------------------------------------------
 struct EvalArgs {
-  int m, np, nq, nw;
+  int m, np, nw;
   const cplx* H;      // m x m col-major (ld m), upper Hessenberg
   const cplx* bw;     // m x np col-major (ld m)
-  const cplx* cw;     // nq x m col-major (ld nq)
-  const cplx* A1;     // qn x m col-major (ld qn): RS rotated into the Hessenberg basis, may be null
-  const cplx* A2;     // qn x m col-major: RZ rotated
-  const cplx* RB;     // qn x np col-major: coefficients of b_p
-  int qn;
-  const double* bn;   // np: ||b||
-  const int* qidx;    // np: position of p in the q set (-1: none)
   const double* omegas;
   double eta;
-  cplx* scratch;      // per CTA: U (m(m+1)/2) | R (m*np) | rows (2m) | T (max(qn*np, np*nq))
+  cplx* scratch;      // per CTA: U (m(m+1)/2) | rows (2m)
   long long scratch_per_cta;
-  cplx* G;            // [nw][np][nq] or null
-  double* A;          // [nw] or null
-  double* maxres;     // [nw] or null
+  cplx* Y;            // solutions: Y[k * ldy + w * np + p] = yhat_p(w)[k]
+  long long ldy;
   int* singular;
 };
 
 __device__ __forceinline__ double cabs2(cplx a) { return a.x * a.x + a.y * a.y; }
 
-__global__ void __launch_bounds__(256) eval_kernel(EvalArgs a) {
-  const int m = a.m, np = a.np, nq = a.nq;
+// One CTA per frequency (grid-stride): LU of (w - i eta + H) with partial pivoting between adjacent
+// rows (the only pivots a Hessenberg matrix needs), applied to the np right-hand sides, then back
+// substitution. Everything after the solves (Ghat, A, residual norms) is a GEMM over all
+// frequencies at once and runs outside this kernel.
+__global__ void __launch_bounds__(256) eval_solve_kernel(EvalArgs a) {
+  const int m = a.m, np = a.np;
   cplx* U = a.scratch + blockIdx.x * a.scratch_per_cta;
-  cplx* R = U + (long long)m * (m + 1) / 2;
-  cplx* rowA = R + (long long)m * np;
+  cplx* rowA = U + (long long)m * (m + 1) / 2;
   cplx* rowB = rowA + m;
-  cplx* T = rowB + m;
+  const long long ldr = a.ldy;
   __shared__ int s_swap;
   __shared__ cplx s_l;
-  __shared__ double s_red[256];
   for (int w = blockIdx.x; w < a.nw; w += gridDim.x) {
     const cplx sig = make_cuDoubleComplex(a.omegas[w], -a.eta);
-    // RHS rows R[k*np + p] = bw[k + p*m]
+    cplx* R = a.Y + (long long)w * np;   // R[k * ldr + p]
     for (long long t = threadIdx.x; t < (long long)m * np; t += blockDim.x) {
       int k = (int)(t / np), p = (int)(t % np);
-      R[t] = a.bw[k + (long long)p * m];
+      R[k * ldr + p] = a.bw[k + (long long)p * m];
     }
     for (int col = threadIdx.x; col < m; col += blockDim.x) {
       cplx h = a.H[(long long)col * m + 0];
@@ -184,9 +183,9 @@ __global__ void __launch_bounds__(256) eval_kernel(EvalArgs a) {
       if (s_swap) {
         cplx* tmp = cur; cur = nxt; nxt = tmp;
         for (int p = threadIdx.x; p < np; p += blockDim.x) {
-          cplx t0 = R[(long long)j * np + p];
-          R[(long long)j * np + p] = R[(long long)(j + 1) * np + p];
-          R[(long long)(j + 1) * np + p] = t0;
+          cplx t0 = R[j * ldr + p];
+          R[j * ldr + p] = R[(j + 1) * ldr + p];
+          R[(j + 1) * ldr + p] = t0;
         }
       }
       __syncthreads();
@@ -202,7 +201,7 @@ __global__ void __launch_bounds__(256) eval_kernel(EvalArgs a) {
         const cplx l = s_l;
         for (int col = j + 1 + threadIdx.x; col < m; col += blockDim.x) nxt[col] = cuCsub(nxt[col], cuCmul(l, cur[col]));
         for (int p = threadIdx.x; p < np; p += blockDim.x)
-          R[(long long)(j + 1) * np + p] = cuCsub(R[(long long)(j + 1) * np + p], cuCmul(l, R[(long long)j * np + p]));
+          R[(j + 1) * ldr + p] = cuCsub(R[(j + 1) * ldr + p], cuCmul(l, R[j * ldr + p]));
         __syncthreads();
         cplx* tmp = cur; cur = nxt; nxt = tmp;
       }
@@ -213,74 +212,65 @@ __global__ void __launch_bounds__(256) eval_kernel(EvalArgs a) {
       const long long offj = (long long)j * m - (long long)j * (j - 1) / 2;
       cplx d = U[offj];
       for (int p = threadIdx.x; p < np; p += blockDim.x) {
-        cplx y = (d.x == 0.0 && d.y == 0.0) ? cz() : cuCdiv(R[(long long)j * np + p], d);
-        R[(long long)j * np + p] = y;
+        cplx y = (d.x == 0.0 && d.y == 0.0) ? cz() : cuCdiv(R[j * ldr + p], d);
+        R[j * ldr + p] = y;
       }
       __syncthreads();
-      // R[i][p] -= U[i][j] y_j[p] for i < j
       for (long long t = threadIdx.x; t < (long long)j * np; t += blockDim.x) {
         int i = (int)(t / np), p = (int)(t % np);
         const long long offi = (long long)i * m - (long long)i * (i - 1) / 2;
         cplx u = U[offi + (j - i)];
-        R[t] = cuCsub(R[t], cuCmul(u, R[(long long)j * np + p]));
+        R[i * ldr + p] = cuCsub(R[i * ldr + p], cuCmul(u, R[j * ldr + p]));
       }
       __syncthreads();
     }
-    // Ghat[p][q] = sum_k cw[q][k] y[k][p]
-    if (a.G || a.A) {
-      for (int t = threadIdx.x; t < np * nq; t += blockDim.x) {
-        int p = t / nq, q = t % nq;
-        cplx s = cz();
-        for (int k = 0; k < m; ++k) s = cuCadd(s, cuCmul(a.cw[q + (long long)k * nq], R[(long long)k * np + p]));
-        if (a.G) a.G[((long long)w * np + p) * nq + q] = s;
-        T[t] = s;
-      }
-      __syncthreads();
-      if (a.A) {
-        double acc = 0.0;
-        for (int p = threadIdx.x; p < np; p += blockDim.x) {
-          int qi = a.qidx[p];
-          if (qi >= 0) acc += T[(long long)p * nq + qi].y;
-        }
-        s_red[threadIdx.x] = acc;
-        __syncthreads();
-        for (int s2 = 128; s2 > 0; s2 >>= 1) {
-          if (threadIdx.x < s2) s_red[threadIdx.x] += s_red[threadIdx.x + s2];
-          __syncthreads();
-        }
-        if (threadIdx.x == 0) a.A[w] = -s_red[0] / 3.14159265358979323846;
-      }
-      __syncthreads();
-    }
-    // residual norm: u_p = sigma A1 y_p + A2 y_p - RB e_p  (coefficients of r_p in an orthonormal basis)
-    if (a.maxres) {
-      for (long long t = threadIdx.x; t < (long long)a.qn * np; t += blockDim.x) {
-        int r = (int)(t / np), p = (int)(t % np);
-        cplx s = make_cuDoubleComplex(-a.RB[r + (long long)p * a.qn].x, -a.RB[r + (long long)p * a.qn].y);
-        for (int k = 0; k < m; ++k) {
-          cplx coef = cuCadd(cuCmul(sig, a.A1[r + (long long)k * a.qn]), a.A2[r + (long long)k * a.qn]);
-          s = cuCadd(s, cuCmul(coef, R[(long long)k * np + p]));
-        }
-        T[t] = s;
-      }
-      __syncthreads();
-      double mx = 0.0;
-      for (int p = 0; p < np; ++p) {
-        double part = 0.0;
-        for (int r = threadIdx.x; r < a.qn; r += blockDim.x) part += cabs2(T[(long long)r * np + p]);
-        s_red[threadIdx.x] = part;
-        __syncthreads();
-        for (int s2 = 128; s2 > 0; s2 >>= 1) {
-          if (threadIdx.x < s2) s_red[threadIdx.x] += s_red[threadIdx.x + s2];
-          __syncthreads();
-        }
-        mx = fmax(mx, sqrt(s_red[0]) / a.bn[p]);
-        __syncthreads();
-      }
-      if (threadIdx.x == 0) a.maxres[w] = mx;
-    }
-    __syncthreads();
   }
+}
+
+// A[w] = -(1/pi) sum_p Im G[w][p][qidx[p]] (p with a matching q only)
+__global__ void spectral_from_G_kernel(const cplx* __restrict__ G, int nw, int np, int nq, const int* __restrict__ qidx,
+                                       double* __restrict__ A) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nw) return;
+  double acc = 0.0;
+  for (int p = 0; p < np; ++p) {
+    const int qi = qidx[p];
+    if (qi >= 0) acc += G[((long long)w * np + p) * nq + qi].y;
+  }
+  A[w] = -acc / 3.14159265358979323846;
+}
+
+// Ys[k][w np + p] = (w - i eta) Y[k][w np + p]
+__global__ void shift_scale_kernel(const cplx* __restrict__ Y, long long ldy, int m, int np, int nw,
+                                   const double* __restrict__ omegas, double eta, cplx* __restrict__ Ys) {
+  const long long total = (long long)m * nw * np;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long k = t / ((long long)nw * np), n = t % ((long long)nw * np);
+    const int w = (int)(n / np);
+    Ys[k * ldy + n] = cuCmul(make_cuDoubleComplex(omegas[w], -eta), Y[k * ldy + n]);
+  }
+}
+
+// res[w np + p] = || C[:, w np + p] - RB[:, p] || / bn[p]   (C row-major [qn][ldc])
+__global__ void resnorm_kernel(const cplx* __restrict__ C, long long ldc, int qn, const cplx* __restrict__ RB,
+                               int np, int nw, const double* __restrict__ bn, double* __restrict__ res) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= (long long)nw * np) return;
+  const int p = (int)(n % np);
+  double s = 0.0;
+  for (int r = 0; r < qn; ++r) {
+    const cplx d = cuCsub(C[(long long)r * ldc + n], RB[r + (long long)p * qn]);
+    s += d.x * d.x + d.y * d.y;
+  }
+  res[n] = sqrt(s) / bn[p];
+}
+__global__ void rowmax_kernel(const double* __restrict__ res, int np, int nw, double* __restrict__ out) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nw) return;
+  double mx = 0.0;
+  for (int p = 0; p < np; ++p) mx = fmax(mx, res[(long long)w * np + p]);
+  out[w] = mx;
 }
 
 }  // namespace
@@ -510,6 +500,118 @@ __global__ void add_block_kernel(cplx* __restrict__ T, int ldt, int c0, const cp
   T[i + (long long)(c0 + j) * ldt].y += Cf[t].y;
 }
 
+// Complex Cholesky G = R^H R of a Hermitian positive definite n x n matrix (row-major); returns false
+// when a pivot is not positive.
+bool cholesky_upper(const std::vector<cplx>& G, int n, std::vector<cplx>& R) {
+  R.assign((size_t)n * n, make_cuDoubleComplex(0.0, 0.0));
+  for (int j = 0; j < n; ++j) {
+    double d = G[(size_t)j * n + j].x;
+    for (int i = 0; i < j; ++i) d -= R[(size_t)i * n + j].x * R[(size_t)i * n + j].x + R[(size_t)i * n + j].y * R[(size_t)i * n + j].y;
+    if (!(d > 0.0)) return false;
+    const double rjj = std::sqrt(d);
+    R[(size_t)j * n + j] = make_cuDoubleComplex(rjj, 0.0);
+    for (int k = j + 1; k < n; ++k) {
+      cplx t = G[(size_t)j * n + k];
+      for (int i = 0; i < j; ++i) t = cuCsub(t, cuCmul(cuConj(R[(size_t)i * n + j]), R[(size_t)i * n + k]));
+      R[(size_t)j * n + k] = make_cuDoubleComplex(t.x / rjj, t.y / rjj);
+    }
+  }
+  return true;
+}
+// inverse of an upper triangular n x n matrix (row-major)
+std::vector<cplx> inverse_upper(const std::vector<cplx>& R, int n) {
+  std::vector<cplx> X((size_t)n * n, make_cuDoubleComplex(0.0, 0.0));
+  for (int j = n - 1; j >= 0; --j) {
+    X[(size_t)j * n + j] = cuCdiv(make_cuDoubleComplex(1.0, 0.0), R[(size_t)j * n + j]);
+    for (int k = j + 1; k < n; ++k) {
+      cplx t = make_cuDoubleComplex(0.0, 0.0);
+      for (int i = j + 1; i <= k; ++i) t = cuCadd(t, cuCmul(R[(size_t)j * n + i], X[(size_t)i * n + k]));
+      X[(size_t)j * n + k] = cuCmul(cuCsub(make_cuDoubleComplex(0.0, 0.0), t), X[(size_t)j * n + j]);
+    }
+  }
+  return X;
+}
+
+// Panel of pb columns Y[:, c0:c0+pb] (already orthogonal to every earlier column): Cholesky QR twice
+// (Y = Q R2 R1 with the Gram matrices formed by FP64-accurate GEMMs). In exact arithmetic this is the
+// column-by-column Gram-Schmidt of the panel (the same Q and R with a positive diagonal). It is taken
+// only when the panel is well conditioned: every first-pass pivot R1_jj at least 1e-5 of the largest
+// column norm of the panel and at least 1e-7 of the column's norm before any projection (n0), so
+// that two passes give orthonormality to rounding and no column is near the drop threshold; otherwise
+// the caller runs the column-by-column passes. Writes T[c0:c0+pb, c0:c0+pb] = R2 R1 and keep = 1.
+struct PanelWork {
+  DBuf<cplx> Gd, Rinv, tmp;
+};
+bool panel_cholqr2(gfcc_ctx* c, cplx* Y, cplx* MY, int nc, long long D, int c0, int pb, const double* n0,
+                   cplx* T, int* keep_dev, PanelWork& pw) {
+  cudaStream_t s = c->stream;
+  std::vector<cplx> G((size_t)pb * pb), R1, R2;
+  DBuf<cplx>& Gd = pw.Gd;
+  DBuf<cplx>& Rinv = pw.Rinv;
+  DBuf<cplx>& tmp = pw.tmp;
+  Gd.alloc((long long)pb * pb);
+  Rinv.alloc((long long)pb * pb);
+  tmp.alloc(D * pb);
+  auto gram = [&]() {
+    ZGemmDesc g;
+    g.M = pb; g.N = pb; g.K = (int)D;
+    g.A = Y + c0; g.sam = 1; g.sak = nc; g.conjA = true;
+    g.B = Y + c0; g.sbk = nc; g.sbn = 1;
+    g.C = Gd.p; g.scm = pb; g.scn = 1;
+    g.work = zgemm_work(c);
+    fp64_accurate_zgemm(g, s);
+    GFCC_CUDA(cudaMemcpyAsync(G.data(), Gd.p, sizeof(cplx) * pb * pb, cudaMemcpyDeviceToHost, s));
+    GFCC_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < pb; ++i) {   // exact Hermitian symmetry and a real diagonal
+      G[(size_t)i * pb + i].y = 0.0;
+      for (int k = i + 1; k < pb; ++k) G[(size_t)k * pb + i] = cuConj(G[(size_t)i * pb + k]);
+    }
+  };
+  auto apply = [&](const std::vector<cplx>& R) {   // Y (and MY) <- Y R^{-1}
+    std::vector<cplx> X = inverse_upper(R, pb);
+    GFCC_CUDA(cudaMemcpyAsync(Rinv.p, X.data(), sizeof(cplx) * pb * pb, cudaMemcpyHostToDevice, s));
+    for (cplx* Z : {Y, MY}) {
+      if (!Z) continue;
+      ZGemmDesc u;
+      u.M = (int)D; u.N = pb; u.K = pb;
+      u.A = Z + c0; u.sam = nc; u.sak = 1;
+      u.B = Rinv.p; u.sbk = pb; u.sbn = 1;
+      u.C = tmp.p; u.scm = pb; u.scn = 1;
+      u.work = zgemm_work(c);
+      fp64_accurate_zgemm(u, s);
+      GFCC_CUDA(cudaMemcpy2DAsync(Z + c0, sizeof(cplx) * nc, tmp.p, sizeof(cplx) * pb, sizeof(cplx) * pb, D,
+                                  cudaMemcpyDeviceToDevice, s));
+    }
+  };
+  gram();
+  if (!cholesky_upper(G, pb, R1)) return false;
+  double cmax = 0.0;
+  for (int j = 0; j < pb; ++j) cmax = std::max(cmax, std::sqrt(G[(size_t)j * pb + j].x));
+  for (int j = 0; j < pb; ++j) {
+    const double r = R1[(size_t)j * pb + j].x;
+    if (!(r >= 1e-5 * cmax) || !(r >= 1e-7 * n0[j])) return false;
+  }
+  apply(R1);
+  gram();
+  if (!cholesky_upper(G, pb, R2)) return false;   // cannot happen after a well-conditioned first pass
+  apply(R2);
+  if (T) {   // T block = R2 R1 (upper triangular), column-major in T (ld nc)
+    std::vector<cplx> Tb((size_t)pb * pb, make_cuDoubleComplex(0.0, 0.0));
+    for (int i = 0; i < pb; ++i)
+      for (int k = i; k < pb; ++k) {
+        cplx t = make_cuDoubleComplex(0.0, 0.0);
+        for (int l = i; l <= k; ++l) t = cuCadd(t, cuCmul(R2[(size_t)i * pb + l], R1[(size_t)l * pb + k]));
+        Tb[(size_t)k * pb + i] = t;   // column k, row i
+      }
+    GFCC_CUDA(cudaMemcpy2DAsync(T + c0 + (long long)c0 * nc, sizeof(cplx) * nc, Tb.data(), sizeof(cplx) * pb,
+                                sizeof(cplx) * pb, pb, cudaMemcpyHostToDevice, s));
+  }
+  std::vector<int> ones(pb, 1);
+  GFCC_CUDA(cudaMemcpyAsync(keep_dev + c0, ones.data(), sizeof(int) * pb, cudaMemcpyHostToDevice, s));
+  GFCC_CUDA(cudaStreamSynchronize(s));
+  return true;
+}
+
 // Orthonormalise the nc columns of Y ([D][nc] batch-minor) against the n_cur columns of the basis
 // Bs ([D][cap]) and against each other, column by column in order: each column loses its components
 // along all earlier columns by classical Gram-Schmidt applied twice, and is kept when its norm after
@@ -551,6 +653,7 @@ std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cp
       g.A = Pb; g.sam = 1; g.sak = ldp; g.conjA = true;
       g.B = Y + col0; g.sbk = nc; g.sbn = 1;
       g.C = Cf.p; g.scm = ncols; g.scn = 1;
+      g.work = zgemm_work(c);
       fp64_accurate_zgemm(g, s);
       ZGemmDesc u;
       u.M = (int)D; u.N = ncols; u.K = np_;
@@ -558,6 +661,7 @@ std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cp
       u.B = Cf.p; u.sbk = ncols; u.sbn = 1;
       u.C = Y + col0; u.scm = nc; u.scn = 1;
       u.alpha = make_cuDoubleComplex(-1.0, 0.0); u.beta = make_cuDoubleComplex(1.0, 0.0);
+      u.work = zgemm_work(c);
       fp64_accurate_zgemm(u, s);
       if (MY) { u.A = MPb; u.C = MY + col0; fp64_accurate_zgemm(u, s); }
       if (to_cold) {
@@ -580,10 +684,15 @@ std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cp
   partial.alloc((long long)nchunk * PB);
   h.alloc(PB);
   const dim3 pgrid(1, nchunk), pblock(32, PTY);
+  PanelWork pwork;
+  std::vector<double> hn0(nc);
+  GFCC_CUDA(cudaMemcpyAsync(hn0.data(), n0.p, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+  GFCC_CUDA(cudaStreamSynchronize(s));
   for (int c0 = 0; c0 < nc; c0 += PB) {
     const int pb = std::min(PB, nc - c0);
     if (c0 > 0) block_cgs(Y, nc, c0, MY, c0, pb, false);
     ProfScope pp(PROF_MOR_PANEL, 0.0, s);
+    if (panel_cholqr2(c, Y, MY, nc, D, c0, pb, hn0.data() + c0, T, keep.p, pwork)) continue;
     for (int j = c0; j < c0 + pb; ++j) {
       const int n = j - c0;
       if (n > 0) {
@@ -752,6 +861,7 @@ void mor_append(gfcc_ctx* c, const cplx* Xin, const cplx* MXin, int nc) {
     g.A = Lp + l0; g.sam = 1; g.sak = cap; g.conjA = true;
     g.B = Rp + r0; g.sbk = ldr_rows; g.sbn = 1;
     g.C = Cp; g.scm = scm; g.scn = scn;
+    g.work = zgemm_work(c);
     zgemm(g, s);
   };
   // Hhat[0:m1, m0:m1] = S^H Z_new ; Hhat[m0:m1, 0:m0] = S_new^H Z_old
@@ -776,6 +886,7 @@ void mor_append(gfcc_ctx* c, const cplx* Xin, const cplx* MXin, int nc) {
     g.A = Cc.p; g.sam = 1; g.sak = nq;
     g.B = ms.S.p + m0; g.sbk = cap; g.sbn = 1;
     g.C = ms.ch.p + (long long)m0 * nq; g.scm = 1; g.scn = nq;
+    g.work = zgemm_work(c);
     zgemm(g, s);
   }
   GFCC_CUDA(cudaStreamSynchronize(s));
@@ -854,25 +965,67 @@ void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, doubl
   GFCC_CUDA(cudaMemcpyAsync(dq.p, qidx.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
   GFCC_CUDA(cudaMemcpyAsync(dom.p, omegas_host, sizeof(double) * nw, cudaMemcpyHostToDevice, s));
   GFCC_CUDA(cudaMemcpyAsync(dbn.p, ms.bnorm.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s));
-  // per-CTA scratch, grid bounded by memory
-  const long long tsz = std::max<long long>((long long)np * nq, want_res ? (long long)qn * np : 0);
-  const long long per = (long long)m * (m + 1) / 2 + (long long)m * np + 2LL * m + tsz + 64;
-  size_t freeb = 0, totalb = 0;
-  GFCC_CUDA(cudaMemGetInfo(&freeb, &totalb));
-  long long maxcta = std::max<long long>(1, (long long)(0.4 * (double)freeb) / (per * (long long)sizeof(cplx)));
-  int ncta = (int)std::min<long long>({(long long)nw, 2LL * 152, maxcta});
-  DBuf<cplx> scratch;
+  // frequencies in batches: solutions Y [m][nb np] of a batch (about 2 GB at most), then Ghat = chat^T Y
+  // and the residual coefficients (w - i eta) RS Y + RZ Y - RB as complex GEMMs over the whole batch
+  const long long per = (long long)m * (m + 1) / 2 + 2LL * m + 64;
+  const long long bw_max = std::max<long long>(1, (2LL << 30) / ((long long)m * np * (long long)sizeof(cplx)));
+  const int nbw = (int)std::min<long long>(nw, bw_max);
+  const int ncta = (int)std::min<long long>(nbw, 2LL * 152);
+  DBuf<cplx> scratch, Y, Ys, Cr, Gt;
+  DBuf<double> rcol;
   scratch.alloc(per * ncta);
-  EvalArgs ea;
-  ea.m = m; ea.np = np; ea.nq = nq; ea.nw = nw;
-  ea.H = Hw.p; ea.bw = bw.p; ea.cw = cw.p;
-  ea.A1 = want_res ? A1.p : nullptr; ea.A2 = want_res ? A2.p : nullptr; ea.RB = want_res ? RBw.p : nullptr;
-  ea.qn = qn;
-  ea.bn = dbn.p; ea.qidx = dq.p; ea.omegas = dom.p; ea.eta = ms.eta;
-  ea.scratch = scratch.p; ea.scratch_per_cta = per;
-  ea.G = G_dev; ea.A = A_dev; ea.maxres = maxres_dev; ea.singular = dsing.p;
-  eval_kernel<<<ncta, 256, 0, s>>>(ea);
-  GFCC_LAUNCH_CHECK();
+  Y.alloc((long long)m * nbw * np);
+  const bool want_G = G_dev != nullptr || A_dev != nullptr;
+  if (want_G && !G_dev) Gt.alloc((long long)nbw * np * nq);
+  if (want_res) {
+    Ys.alloc((long long)m * nbw * np);
+    Cr.alloc((long long)qn * nbw * np);
+    rcol.alloc((long long)nbw * np);
+  }
+  for (int w0 = 0; w0 < nw; w0 += nbw) {
+    const int nb = std::min(nbw, nw - w0);
+    const long long ldy = (long long)nb * np;
+    EvalArgs ea;
+    ea.m = m; ea.np = np; ea.nw = nb;
+    ea.H = Hw.p; ea.bw = bw.p;
+    ea.omegas = dom.p + w0; ea.eta = ms.eta;
+    ea.scratch = scratch.p; ea.scratch_per_cta = per;
+    ea.Y = Y.p; ea.ldy = ldy; ea.singular = dsing.p;
+    eval_solve_kernel<<<std::min(ncta, nb), 256, 0, s>>>(ea);
+    GFCC_LAUNCH_CHECK();
+    if (want_G) {   // G(q, n) = sum_k cw[q][k] Y[k][n], stored at Gb[n nq + q]
+      cplx* Gb = G_dev ? G_dev + (long long)w0 * np * nq : Gt.p;
+      ZGemmDesc g;
+      g.M = nq; g.N = (int)ldy; g.K = m;
+      g.A = cw.p; g.sam = 1; g.sak = nq;
+      g.B = Y.p; g.sbk = ldy; g.sbn = 1;
+      g.C = Gb; g.scm = 1; g.scn = nq;
+      g.work = zgemm_work(c);
+      zgemm(g, s);
+      if (A_dev) {
+        spectral_from_G_kernel<<<(nb + 127) / 128, 128, 0, s>>>(Gb, nb, np, nq, dq.p, A_dev + w0);
+        GFCC_LAUNCH_CHECK();
+      }
+    }
+    if (want_res) {   // coefficients of r = (w - i eta) S y + Z y - b in the orthonormal residual basis
+      shift_scale_kernel<<<grid_for((long long)m * ldy), 256, 0, s>>>(Y.p, ldy, m, np, nb, dom.p + w0, ms.eta, Ys.p);
+      GFCC_LAUNCH_CHECK();
+      ZGemmDesc g;
+      g.M = qn; g.N = (int)ldy; g.K = m;
+      g.A = A1.p; g.sam = 1; g.sak = qn;
+      g.B = Ys.p; g.sbk = ldy; g.sbn = 1;
+      g.C = Cr.p; g.scm = ldy; g.scn = 1;
+      g.work = zgemm_work(c);
+      zgemm(g, s);
+      g.A = A2.p; g.B = Y.p; g.beta = make_cuDoubleComplex(1.0, 0.0);
+      g.work = zgemm_work(c);
+      zgemm(g, s);
+      resnorm_kernel<<<(unsigned)((ldy + 255) / 256), 256, 0, s>>>(Cr.p, ldy, qn, RBw.p, np, nb, dbn.p, rcol.p);
+      GFCC_LAUNCH_CHECK();
+      rowmax_kernel<<<(nb + 127) / 128, 128, 0, s>>>(rcol.p, np, nb, maxres_dev + w0);
+      GFCC_LAUNCH_CHECK();
+    }
+  }
   int hs = 0;
   GFCC_CUDA(cudaMemcpyAsync(&hs, dsing.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   GFCC_CUDA(cudaStreamSynchronize(s));

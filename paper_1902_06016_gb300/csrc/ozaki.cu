@@ -250,13 +250,34 @@ double oz_min_macs() {
   return v;
 }
 
+namespace {
+struct ZWork {          // buffers of zgemm_oz, kept between calls (grow-only)
+  SlicedRows sa, sb;
+  DBuf<unsigned long long> mxa, mxb;
+  DBuf<double> T;
+  OzWork w;
+};
+}  // namespace
+
+void* zgemm_work(gfcc_ctx* c) {
+  if (!c->zwork) c->zwork = new ZWork();
+  return c->zwork;
+}
+void zgemm_work_free(gfcc_ctx* c) {
+  delete static_cast<ZWork*>(c->zwork);
+  c->zwork = nullptr;
+}
+
 void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s) {
   const long long M = g.M, N = g.N, K = g.K;
   GFCC_CHECK(g.batch == 1, GFCC_ERR_ARG, "zgemm_oz: no batches");
   GFCC_CHECK(ns >= 2 && ns <= OZ_SLICES_MAX, GFCC_ERR_ARG, "zgemm_oz: 2..8 slices");
   if (M <= 0 || N <= 0) return;
   ProfScope prof(PROF_OZ_ZGEMM, 8.0 * (double)M * (double)N * (double)K, s);
-  SlicedRows sa, sb;
+  ZWork local;
+  ZWork& z = g.work ? *static_cast<ZWork*>(g.work) : local;
+  SlicedRows& sa = z.sa;
+  SlicedRows& sb = z.sb;
   sa.rows = M; sa.kp = tc_pad_k(TcKind::BF16, 2 * K); sa.ns = ns; sa.reversed = false;
   sb.rows = 2 * N; sb.kp = sa.kp; sb.ns = ns; sb.reversed = true;
   sa.slices.alloc(sizeof(__nv_bfloat16) * M * ns * sa.kp);
@@ -265,11 +286,12 @@ void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s) {
   sb.expo.alloc(2 * N);
   {
     ProfScope ps(PROF_OZ_SLICE, 0.0, s);
-    DBuf<unsigned long long> mxa, mxb;
+    DBuf<unsigned long long>& mxa = z.mxa;
+    DBuf<unsigned long long>& mxb = z.mxb;
     mxa.alloc(M);
     mxb.alloc(N);
-    mxa.zero(s);
-    mxb.zero(s);
+    GFCC_CUDA(cudaMemsetAsync(mxa.p, 0, sizeof(unsigned long long) * M, s));
+    GFCC_CUDA(cudaMemsetAsync(mxb.p, 0, sizeof(unsigned long long) * N, s));
     const long long kt = (sa.kp / 2 + ZT_K - 1) / ZT_K;   // k tiles covering the padded width
     const long long kt_in = (K + ZT_K - 1) / ZT_K;
     GFCC_CHECK((M + ZT_R - 1) / ZT_R <= 65535 && (N + ZT_R - 1) / ZT_R <= 65535, GFCC_ERR_ARG, "zgemm_oz: too many rows");
@@ -287,9 +309,9 @@ void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s) {
         reinterpret_cast<__nv_bfloat16*>(sb.slices.p), sb.expo.p);
     GFCC_LAUNCH_CHECK();
   }
-  DBuf<double> T;
+  DBuf<double>& T = z.T;
   T.alloc(M * 2 * N);
-  OzWork w;
+  OzWork& w = z.w;
   oz_gemm(sa, sb, M, 2 * N, T.p, 2 * N, 0.0, w, s);
   zscatter_kernel<<<grid_for(M * N), 256, 0, s>>>(T.p, M, N, g.C, g.scm, g.scn, g.alpha, g.beta);
   GFCC_LAUNCH_CHECK();

@@ -88,75 +88,89 @@ __global__ void convert_down_kernel(const double* __restrict__ T2p, const double
   }
 }
 
-// ---- per-batch operand preparation from the FP64 batch-minor block X[nu][c] (complex) ----------
+// ---- per-batch operand preparation from the batch-minor block X[nu][c] (complex) ----------------
+// Each prepared operand is a transpose of blocks of X into K-major real rows:
+//   up:   B[c*2 + r][k]             = r-component of X[o + k][c],                 k < P v
+//   oooo: B[(a*nb + c)*2 + r][k]    = r-component of X[o + k v + a][c],           k < P
+//   ring: U[(j*nb + c)*2 + r][m v + e] = +-r-component of X[o + pair(m,j) v + e][c] (+ for m < j,
+//         - for m > j, 0 for m = j),                                              e < v
+// Tiles of 32 k x 32 c go through shared memory, so that X is read along c and the operand written
+// along k (both coalesced); the K padding columns are zeroed by zero_pad_kernel.
+enum PrepKind { PREP_UP = 0, PREP_OOOO = 1, PREP_RING = 2 };
+constexpr int PT = 32;
+template <typename E, typename VT, int KIND>
+__global__ void __launch_bounds__(256) prep_tiled_kernel(const VT* __restrict__ X, int o, int v, int nb,
+                                                         typename E::T* __restrict__ out, int kpad) {
+  using R = typename VReal<VT>::type;
+  __shared__ VT tile[PT][PT + 1];
+  const int g = blockIdx.z;
+  const int k0 = blockIdx.x * PT, c0 = blockIdx.y * PT;
+  const long long P = (long long)o * (o - 1) / 2;
+  long long rowblk = 0, kofs = 0, xbase = o, xstep = 1;
+  int klen = 0;
+  bool neg = false, zero = false;
+  if (KIND == PREP_UP) {
+    klen = (int)(P * v);
+  } else if (KIND == PREP_OOOO) {
+    rowblk = g; klen = (int)P; xbase = o + g; xstep = v;
+  } else {
+    const int j = g / o, m = g % o;
+    rowblk = j; kofs = (long long)m * v; klen = v;
+    zero = (m == j);
+    neg = m > j;
+    const int lo = min(m, j), hi = max(m, j);
+    xbase = o + (long long)pair_of(lo, hi) * v;
+  }
+  if (k0 >= klen) return;
+  for (int kk = threadIdx.y; kk < PT; kk += blockDim.y) {
+    const int k = k0 + kk, c = c0 + threadIdx.x;
+    VT x;
+    x.x = R(0); x.y = R(0);
+    if (!zero && k < klen && c < nb) x = X[(xbase + (long long)k * xstep) * nb + c];
+    tile[kk][threadIdx.x] = x;
+  }
+  __syncthreads();
+  const int k = k0 + threadIdx.x;
+  if (k >= klen) return;
+  for (int rr = threadIdx.y; rr < 2 * PT; rr += blockDim.y) {
+    const int cc = rr >> 1, r = rr & 1, c = c0 + cc;
+    if (c < nb) {
+      const VT x = tile[threadIdx.x][cc];
+      const R comp = r ? x.y : x.x;
+      out[((rowblk * nb + c) * 2 + r) * (long long)kpad + kofs + k] = E::cvt(neg ? -comp : comp);
+    }
+  }
+}
+// out[row][k] = 0 for kfrom <= k < kpad
+template <typename E>
+__global__ void zero_pad_kernel(typename E::T* __restrict__ out, long long rows, int kfrom, int kpad) {
+  const int w = kpad - kfrom;
+  const long long total = rows * w;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x)
+    out[(t / w) * kpad + kfrom + t % w] = E::cvt(0.0);
+}
+template <typename E, typename VT, int KIND>
+void prep_operand(const VT* X, int o, int v, int nb, typename E::T* out, int kpad, cudaStream_t s) {
+  const long long P = (long long)o * (o - 1) / 2;
+  const long long klen = KIND == PREP_UP ? P * v : (KIND == PREP_OOOO ? P : v);
+  const int groups = KIND == PREP_UP ? 1 : (KIND == PREP_OOOO ? v : o * o);
+  const long long rows = 2LL * nb * (KIND == PREP_UP ? 1 : (KIND == PREP_OOOO ? v : o));
+  const long long kused = KIND == PREP_RING ? (long long)o * v : klen;
+  GFCC_CHECK(groups <= 65535 && (klen + PT - 1) / PT < (1LL << 31), GFCC_ERR_ARG, "prep_operand: size");
+  dim3 grid((unsigned)((klen + PT - 1) / PT), (unsigned)((nb + PT - 1) / PT), (unsigned)groups);
+  prep_tiled_kernel<E, VT, KIND><<<grid, dim3(PT, 8), 0, s>>>(X, o, v, nb, out, kpad);
+  GFCC_LAUNCH_CHECK();
+  if (kpad > kused) {
+    zero_pad_kernel<E><<<grid_for(rows * (kpad - kused)), 256, 0, s>>>(out, rows, (int)kused, kpad);
+    GFCC_LAUNCH_CHECK();
+  }
+}
+
+
 // ring: U[(j*nb + c)*2 + r][m*v + e] = r_mj^e (component r), K padded
-template <typename E, typename VT>
-__global__ void prep_ring_kernel(const VT* __restrict__ X, int o, int v, int nb, typename E::T* __restrict__ U,
-                                 int kpad) {
-  const long long rows = 2LL * o * nb;
-  const long long total = rows * kpad;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    using R = typename VReal<VT>::type;
-    long long n = t / kpad;
-    int k = (int)(t % kpad);
-    R val = R(0);
-    if (k < o * v) {
-      int r = (int)(n & 1);
-      long long jc = n >> 1;
-      int c = (int)(jc % nb), j = (int)(jc / nb);
-      int m = k / v, e = k % v;
-      if (m != j) {
-        int lo = min(m, j), hi = max(m, j);
-        const VT x = X[((long long)o + (long long)pair_of(lo, hi) * v + e) * nb + c];
-        const R comp = r ? x.y : x.x;
-        val = (m < j) ? comp : -comp;
-      }
-    }
-    U[t] = E::cvt(val);
-  }
-}
 // oooo: B[(a*nb + c)*2 + r][pmn] = X2[(pmn*v + a)][c].r
-template <typename E, typename VT>
-__global__ void prep_oooo_kernel(const VT* __restrict__ X, int o, int v, int P, int nb,
-                                 typename E::T* __restrict__ B, int kpad) {
-  const long long rows = 2LL * v * nb;
-  const long long total = rows * kpad;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    using R = typename VReal<VT>::type;
-    long long n = t / kpad;
-    int k = (int)(t % kpad);
-    R val = R(0);
-    if (k < P) {
-      int r = (int)(n & 1);
-      long long ac = n >> 1;
-      int c = (int)(ac % nb), a = (int)(ac / nb);
-      const VT x = X[((long long)o + (long long)k * v + a) * nb + c];
-      val = r ? x.y : x.x;
-    }
-    B[t] = E::cvt(val);
-  }
-}
 // up: B[c*2 + r][kk] = X2[kk][c].r  (kk = pmn*v + f)
-template <typename E, typename VT>
-__global__ void prep_up_kernel(const VT* __restrict__ X, int o, long long Pv, int nb, typename E::T* __restrict__ B,
-                               int kpad) {
-  const long long total = 2LL * nb * kpad;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    using R = typename VReal<VT>::type;
-    long long n = t / kpad;
-    long long k = t % kpad;
-    R val = R(0);
-    if (k < Pv) {
-      int r = (int)(n & 1), c = (int)(n >> 1);
-      const VT x = X[((long long)o + k) * nb + c];
-      val = r ? x.y : x.x;
-    }
-    B[t] = E::cvt(val);
-  }
-}
 // sum split-K partials: out[i] = sum_z part[z*stride + i]
 __global__ void reduce_splits_kernel(const float* __restrict__ part, int zs, long long stride, long long n,
                                      float* __restrict__ out) {
@@ -323,13 +337,11 @@ void sigma_emulated(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shi
     cols_gather_kernel<<<grid_for(D * nbc), 256, 0, s>>>(X, nb, c0, nbc, st.Xc.p, D);
     GFCC_LAUNCH_CHECK();
     // up: [Xe ; Y1'] = [Vt ; A12] r2
-    prep_up_kernel<F64Elem, cplx><<<grid_for(nsm * Pv), 256, 0, s>>>(st.Xc.p, o, Pv, nbc, st.stage.p, (int)Pv);
-    GFCC_LAUNCH_CHECK();
+    prep_operand<F64Elem, cplx, PREP_UP>(st.Xc.p, o, v, nbc, st.stage.p, (int)Pv, s);
     oz_slice(st.stage.p, Pv, nsm, Pv, true, st.Bup, s);
     oz_gemm(st.Aup, st.Bup, v + o, nsm, st.up.p, nsm, 0.0, st.work, s);
     // oooo into C2
-    prep_oooo_kernel<F64Elem, cplx><<<grid_for(noo * P), 256, 0, s>>>(st.Xc.p, o, v, P, nbc, st.stage.p, P);
-    GFCC_LAUNCH_CHECK();
+    prep_operand<F64Elem, cplx, PREP_OOOO>(st.Xc.p, o, v, nbc, st.stage.p, P, s);
     oz_slice(st.stage.p, P, noo, P, true, st.Boo, s);
     oz_gemm(st.Woo, st.Boo, P, noo, st.C2.p, noo, 0.0, st.work, s);
     // down: C2 += [T2p | A21] [Xe ; r1]
@@ -339,8 +351,7 @@ void sigma_emulated(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shi
     oz_slice(st.stage.p, v + o, nsm, v + o, true, st.Bdn, s);
     oz_gemm(st.Adn, st.Bdn, Pv, nsm, st.C2.p, nsm, 1.0, st.work, s);
     // ring
-    prep_ring_kernel<F64Elem, cplx><<<grid_for(nring * ov), 256, 0, s>>>(st.Xc.p, o, v, nbc, st.stage.p, (int)ov);
-    GFCC_LAUNCH_CHECK();
+    prep_operand<F64Elem, cplx, PREP_RING>(st.Xc.p, o, v, nbc, st.stage.p, (int)ov, s);
     oz_slice(st.stage.p, ov, nring, ov, true, st.Bring, s);
     oz_gemm(st.Wr, st.Bring, ov, nring, st.CT.p, nring, 0.0, st.work, s);
     combine_lp_kernel<double, cplx><<<grid_for(D * nbc), 256, 0, s>>>(st.Xc.p, st.Yc.p, st.up.p, nsm, st.C2.p, st.CT.p,
@@ -445,12 +456,9 @@ static void sigma_lp_impl(gfcc_ctx* c, LpState& st, const VT* X, VT* Y, int nb, 
   T* Boo = reinterpret_cast<T*>(st.Boo.p);
   T* Bup = reinterpret_cast<T*>(st.Bup.p);
   T* Bdn = reinterpret_cast<T*>(st.Bdn.p);
-  prep_up_kernel<Elem<K>, VT><<<grid_for(nsm * st.Kpv), 256, 0, s>>>(X, o, Pv, nb, Bup, st.Kpv);
-  GFCC_LAUNCH_CHECK();
-  prep_oooo_kernel<Elem<K>, VT><<<grid_for(noo * st.Kp), 256, 0, s>>>(X, o, v, P, nb, Boo, st.Kp);
-  GFCC_LAUNCH_CHECK();
-  prep_ring_kernel<Elem<K>, VT><<<grid_for(nring * st.Kr), 256, 0, s>>>(X, o, v, nb, Bring, st.Kr);
-  GFCC_LAUNCH_CHECK();
+  prep_operand<Elem<K>, VT, PREP_UP>(X, o, v, nb, Bup, st.Kpv, s);
+  prep_operand<Elem<K>, VT, PREP_OOOO>(X, o, v, nb, Boo, st.Kp, s);
+  prep_operand<Elem<K>, VT, PREP_RING>(X, o, v, nb, Bring, st.Kr, s);
   // up (split-K) and its reduction
   tc_gemm(K, TcOperand{st.Aup.p, v + o, st.Kpv}, TcOperand{Bup, nsm, st.Kpv}, st.up_part.p, nsm, v + o, nsm, 0, ksplit,
           part_stride, st.err.p, s);
