@@ -106,7 +106,14 @@ class ClockSampler:
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the captured launches) of
 # the roofline kernel, from ncu captures summarised under profiles/; valid only while the kernel's
 # source file is unchanged (its SHA-256 is recorded with the figure).
-TRAFFIC = {}
+TRAFFIC = {
+    ("benzene_o42_v186", 11): {
+        "bytes_per_launch": 4.0456e9,
+        "tc_gemm_sha256": "e8b4793c88921d9b36fdd8eda013c1e93f702e9069ceb46dabf54a98e20f7790",
+        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over all 239 ring-GEMM launches of one "
+                  "benchmark step (NVTX range gfcc_ring_gemm), averaged; profiles/tc_gemm_tf32_ring_benzene.md",
+    },
+}
 
 
 def _sha256(path):
