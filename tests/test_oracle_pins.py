@@ -220,3 +220,40 @@ def test_green_derivatives_match_finite_differences():
     assert np.abs((Gp - Gm) / (2 * h) - de).max() <= 1e-6 * np.abs(de).max()
     # G itself is the forward product
     assert np.abs(G - sv.green(C, sv.dense_solve(M, B, ws, eta))).max() <= 1e-12 * np.abs(G).max()
+
+
+def test_t2_gradient_matches_finite_differences_of_the_loss():
+    """dL/dt_ij^ab (L = Re sum conj(Gbar) G) from the chain rule with exact operator derivatives,
+    against central differences of L itself (step 1e-5: O(h^2) truncation), with p and q sets that
+    include virtual orbitals (b_a and c_i depend on T2)."""
+    from oracle import grad
+    inp = synth.random_amplitudes(synth.make_inputs(3, 5, 11), 7)
+    porb, qorb = list(range(8)), [0, 2, 5, 7]
+    ws, eta = np.array([-0.7, -0.3]), 0.05
+    rng = np.random.default_rng(0)
+    Gb = rng.standard_normal((2, 8, 4)) + 1j * rng.standard_normal((2, 8, 4))
+    g = grad.green_t2_gradient(inp, porb, qorb, ws, eta, Gb)
+    h = 1e-5
+    for (i, j, a, b) in [(0, 1, 0, 1), (0, 2, 1, 4), (1, 2, 2, 3), (0, 1, 3, 4)]:
+        Lp = grad.green_loss(grad._perturbed(inp, i, j, a, b, h), porb, qorb, ws, eta, Gb)
+        Lm = grad.green_loss(grad._perturbed(inp, i, j, a, b, -h), porb, qorb, ws, eta, Gb)
+        assert abs((Lp - Lm) / (2 * h) - g[i, j, a, b]) <= 1e-7 * np.abs(g).max()
+    # entries that are not independent amplitudes stay zero
+    assert np.all(g[1, 0] == 0.0) and np.all(g[:, :, 2, 1] == 0.0)
+
+
+def test_operator_is_affine_in_t2():
+    """M, b and c are affine in T2 at fixed T1 (every H-bar element is at most linear in T2), so
+    central differences of any step give the same derivative; this is what makes the oracle's
+    operator derivatives exact."""
+    from oracle import grad
+    inp = synth.random_amplitudes(synth.make_inputs(3, 5, 12), 8)
+    porb = qorb = list(range(8))
+    for (i, j, a, b) in [(0, 1, 0, 1), (1, 2, 3, 4)]:
+        d = []
+        for h in (1e-3, 0.3):
+            Mp, Bp, Cp = grad._operators(grad._perturbed(inp, i, j, a, b, h), porb, qorb)
+            Mm, Bm, Cm = grad._operators(grad._perturbed(inp, i, j, a, b, -h), porb, qorb)
+            d.append([(Mp - Mm) / (2 * h), (Bp - Bm) / (2 * h), (Cp - Cm) / (2 * h)])
+        for x, y in zip(d[0], d[1]):
+            assert np.abs(x - y).max() <= 1e-9 * max(np.abs(y).max(), 1.0)
