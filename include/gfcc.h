@@ -137,6 +137,22 @@ int gfcc_solve_full(gfcc_t ctx, const double* omegas, int nw, double eta, const 
 int gfcc_green_derivatives(gfcc_t ctx, const double* omegas, int nw, double eta, const int* orbitals, int np,
                            const int* qorb, int nq, double* G, double* dG_domega, double* dG_deta);
 
+/* Gradient of L = Re sum_{w,p,q} conj(Gbar[w][p][q]) G_pq(w) with respect to the doubles amplitudes
+ * t2[i][j][a][b] (the vector-Jacobian product of an autograd backward pass; G_pq(w) = c_q^T A(w)^{-1} b_p
+ * as in Eq. gfcclineqn, with M, b_p and c_q built from T by the H-bar expressions of the text after
+ * Eq. gfxn1 and Eqs. xplin, gfxn2). Adjoint method: forward solves x, adjoint solves
+ * u = A^{-T} sum_q conj(Gbar) c_q with the transposed sigma, the sigma bilinear form in u and x, then back
+ * through the H-bar build; the forward solutions are recomputed here. Lambda and T1 are held fixed.
+ *   omegas[nw], orbitals[np], qorb[nq] (NULL = p set) as in gfcc_solve_full.
+ *   Gbar (host or device): complex [nw][np][nq] weights.
+ *   G (optional, host or device): the forward G, layout as in gfcc_solve_full.
+ *   grad_t2 (host or device): [o][o][v][v] real, dL/dt2 with every array element treated as independent
+ *   (for antisymmetric amplitudes the derivative along t_ij^ab, i<j, a<b, is
+ *   g[i][j][a][b] - g[j][i][a][b] - g[i][j][b][a] + g[j][i][b][a]).
+ * Errors: GFCC_ERR_ARG, GFCC_ERR_NOT_CONVERGED (a forward or adjoint solve hit the cap), GFCC_ERR_CUDA. */
+int gfcc_green_grad_t2(gfcc_t ctx, const double* omegas, int nw, double eta, const int* orbitals, int np,
+                       const int* qorb, int nq, const double* Gbar, double* G, double* grad_t2);
+
 /* Start a reduced model (Eq. model): solve Eq. xplin at the seed frequencies for every p in
  * orbitals (host), orthonormalise the solutions into S (columns whose norm after two
  * Gram-Schmidt passes falls below opts.drop_tol of their norm before are dropped), and project:

@@ -25,10 +25,6 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// copy n bytes from a user buffer (host or device) to device memory
-void copy_in(void* dst_dev, const void* src, size_t n, cudaStream_t s) {
-  GFCC_CUDA(cudaMemcpyAsync(dst_dev, src, n, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-}
 void copy_out(void* dst, const void* src_dev, size_t n, cudaStream_t s) {
   GFCC_CUDA(cudaMemcpyAsync(dst, src_dev, n, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
 }
@@ -203,6 +199,32 @@ void solve_adjoint_columns(gfcc_ctx* c, const std::vector<double>& ws, double et
     for (int k = 0; k < nb; ++k)
       GFCC_CHECK(st.converged[k], GFCC_ERR_NOT_CONVERGED, "adjoint solve did not converge");
     GFCC_CUDA(cudaMemcpy2DAsync(Yall + c0, sizeof(cplx) * ncols, Y.p, sizeof(cplx) * nb, sizeof(cplx) * nb, D,
+                                cudaMemcpyDeviceToDevice, s));
+  }
+  GFCC_CUDA(cudaStreamSynchronize(s));
+}
+
+// Adjoint solves A(w)^T U = W for general right sides: W, U batch-minor [D][nw np], column w np + p
+// at frequency ws[w].
+void solve_adjoint_rhs(gfcc_ctx* c, const std::vector<double>& ws, double eta, int np, const cplx* Wall, cplx* Uall) {
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  const long long ncols = (long long)ws.size() * np;
+  const int nbmax = choose_batch(c, ncols);
+  DBuf<cplx> B, Y, sh;
+  B.alloc(D * nbmax); Y.alloc(D * nbmax); sh.alloc(nbmax);
+  for (long long c0 = 0; c0 < ncols; c0 += nbmax) {
+    const int nb = (int)std::min<long long>(nbmax, ncols - c0);
+    std::vector<cplx> hs(nb);
+    for (int k = 0; k < nb; ++k) hs[k] = make_cuDoubleComplex(ws[(c0 + k) / np], -eta);
+    GFCC_CUDA(cudaMemcpyAsync(sh.p, hs.data(), sizeof(cplx) * nb, cudaMemcpyHostToDevice, s));
+    GFCC_CUDA(cudaMemcpy2DAsync(B.p, sizeof(cplx) * nb, Wall + c0, sizeof(cplx) * ncols, sizeof(cplx) * nb, D,
+                                cudaMemcpyDeviceToDevice, s));
+    gfcc::SolveStatus st;
+    gfcc::gmres_batched(c, B.p, Y.p, nullptr, sh.p, nb, st, true);
+    for (int k = 0; k < nb; ++k)
+      GFCC_CHECK(st.converged[k], GFCC_ERR_NOT_CONVERGED, "adjoint solve did not converge");
+    GFCC_CUDA(cudaMemcpy2DAsync(Uall + c0, sizeof(cplx) * ncols, Y.p, sizeof(cplx) * nb, sizeof(cplx) * nb, D,
                                 cudaMemcpyDeviceToDevice, s));
   }
   GFCC_CUDA(cudaStreamSynchronize(s));
@@ -499,6 +521,46 @@ int gfcc_green_derivatives(gfcc_t c, const double* omegas, int nw, double eta, c
   API_END(c)
 }
 
+int gfcc_green_grad_t2(gfcc_t c, const double* omegas, int nw, double eta, const int* orbitals, int np,
+                       const int* qorb, int nq, const double* Gbar, double* G, double* grad_t2) {
+  if (!c) return GFCC_ERR_ARG;
+  if (nw <= 0 || !omegas || !std::isfinite(eta) || eta < 0.0 || !Gbar || !grad_t2) {
+    c->last_error = "gfcc_green_grad_t2: bad frequencies, eta or null pointers";
+    return GFCC_ERR_ARG;
+  }
+  int rc = check_orbitals(c, orbitals, np, "gfcc_green_grad_t2");
+  if (rc) return rc;
+  if (qorb) { rc = check_orbitals(c, qorb, nq, "gfcc_green_grad_t2(q)"); if (rc) return rc; }
+  for (int k = 0; k < nw; ++k)
+    if (!std::isfinite(omegas[k])) { c->last_error = "gfcc_green_grad_t2: non-finite frequency"; return GFCC_ERR_NONFINITE; }
+  API_BEGIN
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  std::vector<int> porb(orbitals, orbitals + np);
+  std::vector<int> qv = qorb ? std::vector<int>(qorb, qorb + nq) : porb;
+  nq = (int)qv.size();
+  std::vector<double> ws(omegas, omegas + nw);
+  const long long S = (long long)nw * np;
+  DBuf<cplx> X, W, U, Gb, Gd;
+  DBuf<double> t2b;
+  X.alloc(D * S); W.alloc(D * S); U.alloc(D * S);
+  Gb.alloc(S * nq);
+  GFCC_CUDA(cudaMemcpyAsync(Gb.p, Gbar, sizeof(cplx) * S * nq, cudaMemcpyDefault, s));
+  if (G) Gd.alloc(S * nq);
+  gfcc_stats st{};
+  solve_columns(c, ws, eta, porb, qv, G ? Gd.p : nullptr, X.p, nullptr, &st);
+  GFCC_CHECK(st.not_converged == 0, GFCC_ERR_NOT_CONVERGED, "gfcc_green_grad_t2: forward solve did not converge");
+  gfcc::green_adjoint_rhs(c, qv, Gb.p, S, W.p);
+  solve_adjoint_rhs(c, ws, eta, np, W.p, U.p);
+  const long long n2 = (long long)c->o * c->o * c->v * c->v;
+  t2b.alloc(n2);
+  gfcc::green_grad_t2_core(c, nw, porb, qv, Gb.p, X.p, U.p, t2b.p);
+  copy_out(grad_t2, t2b.p, sizeof(double) * n2, s);
+  if (G) copy_out(G, Gd.p, sizeof(cplx) * S * nq, s);
+  GFCC_CUDA(cudaStreamSynchronize(s));
+  API_END(c)
+}
+
 int gfcc_mor_build(gfcc_t c, const double* seeds, int ns, double eta, const int* orbitals, int np,
                    const int* qorb, int nq) {
   if (!c) return GFCC_ERR_ARG;
@@ -735,7 +797,6 @@ int gfcc_mor_load(gfcc_t c, const char* path) {
 int gfcc_tc_gemm(int precision, const double* A, const double* B, int M, int N, int K, float* C) {
   if (!A || !B || !C || M < 1 || N < 1 || K < 1 || (precision != GFCC_PREC_BF16 && precision != GFCC_PREC_TF32))
     return GFCC_ERR_ARG;
-  gfcc_ctx* ctx = nullptr;
   try {
     DBuf<double> a, b;
     DBuf<float> cdev;
@@ -750,7 +811,6 @@ int gfcc_tc_gemm(int precision, const double* A, const double* B, int M, int N, 
     fprintf(stderr, "gfcc_tc_gemm: %s\n", e.msg.c_str());
     return e.code;
   }
-  (void)ctx;
   return GFCC_OK;
 }
 

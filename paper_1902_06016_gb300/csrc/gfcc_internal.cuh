@@ -191,6 +191,8 @@ struct gfcc_ctx {
   gfcc::DBuf<double> bvec;   // [n][D]  b_p rows
   gfcc::DBuf<double> cvec;   // [n][D]  c_q rows
   gfcc::DBuf<double> t1, t2; // kept for derivative work
+  // kept for the T2 gradient: <mn||ef>, <mn||ie>, <ma||ef>, lambda2, F_me (row-major as the inputs)
+  gfcc::DBuf<double> k_oovv, k_ooov, k_ovvv, k_l2, k_Fme;
   void* zwork = nullptr;     // grow-only workspace of the exact-slice complex GEMMs (ozaki.cu)
   ~gfcc_ctx();
 };
@@ -223,6 +225,13 @@ void zgemm(const ZGemmDesc& g, cudaStream_t s);
 // the context's workspace for exact-slice complex GEMMs (created on first use, freed with the context)
 void* zgemm_work(gfcc_ctx* c);
 void zgemm_work_free(gfcc_ctx* c);
+
+// ---- grad.cu: T2 gradient of L = Re sum conj(Gbar) G ------------------------------------------
+// W[nu][w np + p] = sum_q conj(Gbar[w][p][q]) c_q[nu]   (right sides of the adjoint solves)
+void green_adjoint_rhs(gfcc_ctx* c, const std::vector<int>& qorb, const cplx* Gbar_dev, long long S, cplx* W);
+// from the forward solutions X and adjoint solutions U ([D][nw np] batch-minor): t2bar[o][o][v][v]
+void green_grad_t2_core(gfcc_ctx* c, int nw, const std::vector<int>& porb, const std::vector<int>& qorb,
+                        const cplx* Gbar_dev, const cplx* X, const cplx* U, double* t2bar_dev);
 
 // row-major contiguous helpers
 void dgemm_rm(int M, int N, int K, double alpha, const double* A, int lda, bool transA,

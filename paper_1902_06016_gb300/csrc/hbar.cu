@@ -22,8 +22,6 @@
 namespace gfcc {
 namespace {
 
-__device__ __forceinline__ int pair_of(int i, int j) { return j * (j - 1) / 2 + i; }  // i < j
-
 // Decode pair index P -> (i, j), i < j.
 __device__ __forceinline__ void unpair(int p, int& i, int& j) {
   // FP32 estimate (GB300's FP64 pipe is narrow), corrected to the exact integer below
@@ -416,6 +414,15 @@ void build_operator(gfcc_ctx* c, const HostInputs& in) {
   c->t2.alloc(ov * ov);
   GFCC_CUDA(cudaMemcpyAsync(c->t1.p, t1->p(), sizeof(double) * ov, cudaMemcpyDeviceToDevice, s));
   GFCC_CUDA(cudaMemcpyAsync(c->t2.p, t2->p(), sizeof(double) * ov * ov, cudaMemcpyDeviceToDevice, s));
+  auto keep = [&](DBuf<double>& dst, const Tensor& t) {
+    dst.alloc(t.size());
+    GFCC_CUDA(cudaMemcpyAsync(dst.p, t.p(), sizeof(double) * t.size(), cudaMemcpyDeviceToDevice, s));
+  };
+  keep(c->k_oovv, *v_oovv);
+  keep(c->k_ooov, *v_ooov);
+  keep(c->k_ovvv, *v_ovvv);
+  keep(c->k_l2, *l2);
+  keep(c->k_Fme, Fme);
   GFCC_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -54,6 +54,7 @@ PROTOTYPES = {
     "gfcc_solve_full": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, C.c_int, _vp, _vp, _vp,
                                   C.c_int, C.POINTER(Stats)]),
     "gfcc_green_derivatives": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, C.c_int, _vp, _vp, _vp]),
+    "gfcc_green_grad_t2": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, C.c_int, _vp, _vp, _vp]),
     "gfcc_mor_build": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, C.c_int]),
     "gfcc_mor_refine": (C.c_int, [_vp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, _ip, _dp]),
     "gfcc_mor_eval": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp]),
@@ -282,6 +283,21 @@ class Context:
         self._check(self._lib.gfcc_green_derivatives(self._h, _ptr(w), len(w), float(eta), _ptr(porb), len(porb),
                                                      _ptr(q), nq, _ptr(G), _ptr(dw), _ptr(de)))
         return G, dw, de
+
+    def green_grad_t2(self, omegas, eta, orbitals, Gbar, qorb=None):
+        """(G, dL/dt2) for L = Re sum conj(Gbar) G: G [nw, np, nq] complex, dL/dt2 [o, o, v, v]."""
+        w = _c64(omegas)
+        porb = _ints(orbitals)
+        q = _ints(qorb) if qorb is not None else None
+        nq = len(q) if q is not None else len(porb)
+        Gb = np.ascontiguousarray(Gbar, dtype=np.complex128)
+        if Gb.shape != (len(w), len(porb), nq):
+            raise ValueError("Gbar must have shape [nw, np, nq]")
+        G = np.empty(Gb.shape, dtype=np.complex128)
+        g = np.empty((self.o, self.o, self.v, self.v))
+        self._check(self._lib.gfcc_green_grad_t2(self._h, _ptr(w), len(w), float(eta), _ptr(porb), len(porb),
+                                                 _ptr(q), nq, _ptr(Gb), _ptr(G), _ptr(g)))
+        return G, g
 
     def mor_build(self, seeds, eta, orbitals, qorb=None):
         s = _c64(seeds)
