@@ -23,20 +23,10 @@ int grid_for(long long n) {
   return (int)std::min<long long>(std::max<long long>(g, 1), 152LL * 32);
 }
 
-__device__ __forceinline__ cplx cmul(cplx a, cplx b) { return cuCmul(a, b); }
-__device__ __forceinline__ cplx cconjmul(cplx a, cplx b) {  // conj(a) * b
-  return make_cuDoubleComplex(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
-}
-
 // real component type of a complex vector element
 template <typename VT> struct RealOf;
 template <> struct RealOf<cplx> { using type = double; };
 template <> struct RealOf<cuFloatComplex> { using type = float; };
-template <typename VT> __device__ __forceinline__ VT mk(double re, double im);
-template <> __device__ __forceinline__ cplx mk<cplx>(double re, double im) { return make_cuDoubleComplex(re, im); }
-template <> __device__ __forceinline__ cuFloatComplex mk<cuFloatComplex>(double re, double im) {
-  return make_cuFloatComplex((float)re, (float)im);
-}
 
 constexpr int MD_TX = 32, MD_TY = 8, MD_MAXV = 32;
 // The kernels below are instantiated for NV = 4, 8, 16, 32 basis vectors (nv <= NV used).
@@ -113,12 +103,11 @@ __global__ void __launch_bounds__(256, 2) multidot_kernel(const VT* __restrict__
 
 // Fused CGS sweep: w <- w - sum_i V_i h_i (h = pass-1 coefficients), then partial sums of the
 // pass-2 coefficients conj(V_i) w over the chunk (same layout as multidot_kernel's partials).
-// Thread (x, y) walks rows y, y + MD_TY, ... of column x: it keeps the row's basis entries in
-// registers for the update and adds conj(V_i) w' into its own shared-memory accumulators
-// acc[y][i][x] (no synchronisation inside the loop, no per-thread accumulator arrays), which are
-// summed over y at the end.
+// Thread (x, y) walks rows y, y + MD_TY, ... of column x: it updates the row and adds conj(V_i) w'
+// into its own shared-memory accumulators acc[y][i][x] (no synchronisation inside the loop, no
+// per-thread accumulator arrays), which are summed over y at the end.
 template <typename VT, int NV>
-__global__ void __launch_bounds__(256, 2) update_dot_kernel(const VT* __restrict__ V, long long vstride, int nv,
+__global__ void __launch_bounds__(256, 3) update_dot_kernel(const VT* __restrict__ V, long long vstride, int nv,
                                                             VT* __restrict__ W, long long D, int nb,
                                                             long long rows_per_chunk, const cplx* __restrict__ h,
                                                             int hld, cplx* __restrict__ partial) {
@@ -142,26 +131,24 @@ __global__ void __launch_bounds__(256, 2) update_dot_kernel(const VT* __restrict
   __syncthreads();
   if (c < nb) {
     for (long long nu = r0 + y; nu < r1; nu += MD_TY) {
-      VT vv[NV];
       VT w = W[nu * nb + c];
-#pragma unroll
-      for (int i = 0; i < NV; ++i) {
-        if (i < nv) {
-          vv[i] = V[i * vstride + nu * nb + c];
-          const VT hv = hs[i * MD_TX + x];
-          w.x -= vv[i].x * hv.x - vv[i].y * hv.y;
-          w.y -= vv[i].x * hv.y + vv[i].y * hv.x;
-        }
+#pragma unroll 8
+      for (int i = 0; i < nv; ++i) {
+        const VT hv = hs[i * MD_TX + x];
+        const VT va = V[i * vstride + nu * nb + c];
+        w.x -= va.x * hv.x - va.y * hv.y;
+        w.y -= va.x * hv.y + va.y * hv.x;
       }
       W[nu * nb + c] = w;
-#pragma unroll
-      for (int i = 0; i < NV; ++i) {
-        if (i < nv) {
-          VT a = my[i * MD_TX];
-          a.x += vv[i].x * w.x + vv[i].y * w.y;
-          a.y += vv[i].x * w.y - vv[i].y * w.x;
-          my[i * MD_TX] = a;
-        }
+      // the basis entries are read again for the coefficient sums (L1/L2 hits: this thread loaded
+      // them just before), which keeps the registers low enough for three blocks per SM
+#pragma unroll 8
+      for (int i = 0; i < nv; ++i) {
+        const VT va = V[i * vstride + nu * nb + c];
+        VT a = my[i * MD_TX];
+        a.x += va.x * w.x + va.y * w.y;
+        a.y += va.x * w.y - va.y * w.x;
+        my[i * MD_TX] = a;
       }
     }
   }
