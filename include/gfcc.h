@@ -73,6 +73,9 @@ typedef struct {
   int residual_precision; /* sigma of the refinement residuals: GFCC_PREC_FP64 (FP64 CUDA cores) or
                              GFCC_PREC_FP64_TC; -1 (default) = FP64_TC when precision is a tensor-core
                              kind, FP64 otherwise */
+  int deriv_indicator;  /* 1: the refinement also compares dG/dw of the reduced model with the exact
+                           dG/dw = -c^T A^{-1} x at every sampled frequency (one more solve per column
+                           at each new sample); default 0 */
 } gfcc_opts;
 
 typedef struct {
@@ -165,6 +168,10 @@ int gfcc_mor_build(gfcc_t ctx, const double* seeds, int ns, double eta, const in
  * residual ||(w - i eta + M) S yhat_p - b_p|| / ||b_p|| (grid points strictly inside, all p); add
  * the midpoints of intervals above tol (largest first, ties to the lower frequency) while the
  * model order stays <= m_max; re-solve, re-project and repeat until every estimate is <= tol.
+ * With opts.deriv_indicator the estimate of an interval is the larger of the residual estimate and
+ * d_k, d_{k+1} at its ends, d_k = max_pq |dGhat/dw - dG/dw| / max_pq |dG/dw| at the sampled w_k
+ * (exact derivatives from the extra solves made when w_k was added; samples added before the option
+ * was set, or restored by gfcc_mor_load, count d_k = 0).
  * m_out (host, optional) receives the final order; max_err (host, optional) the last estimate.
  * Returns GFCC_ERR_NOT_CONVERGED if m_max stopped the refinement first. */
 int gfcc_mor_refine(gfcc_t ctx, double wmin, double wmax, int ngrid, double tol, int m_max,

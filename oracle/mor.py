@@ -118,6 +118,25 @@ def choose_midpoints(sampled, errors, tol: float, max_new: int):
     return sorted(w for _, w in cand[:max(max_new, 0)])
 
 
+def reduced_green_derivative(rm: ReducedModel, omegas, eta: float) -> np.ndarray:
+    """dGhat/dw [w, p, q] = -chat_q^T (w - i eta + Hhat)^{-2} bhat_p."""
+    I = np.eye(rm.m)
+    out = []
+    for w in omegas:
+        A = (w - 1j * eta) * I + rm.Hhat
+        Y = np.linalg.solve(A, np.linalg.solve(A, rm.bhat))      # [m, np]
+        out.append(-(rm.chat @ Y).T)
+    return np.array(out)
+
+
+def derivative_mismatch(rm: ReducedModel, sampled, dG_exact: dict, eta: float) -> np.ndarray:
+    """d_k = max_pq |dGhat/dw - dG/dw| / max_pq |dG/dw| at every sampled frequency (sorted)."""
+    s = sorted(sampled)
+    dh = reduced_green_derivative(rm, s, eta)
+    return np.array([np.abs(dh[k] - dG_exact[w]).max() / max(np.abs(dG_exact[w]).max(), 1e-300)
+                     for k, w in enumerate(s)])
+
+
 @dataclass
 class MorResult:
     model: ReducedModel
@@ -128,8 +147,13 @@ class MorResult:
 
 def build_and_refine(hb, B: np.ndarray, C: np.ndarray, seeds, wmin: float, wmax: float,
                      ngrid: int, eta: float, tol: float, m_max: int, solver="dense",
-                     M: np.ndarray | None = None, solve_tol: float = 1e-10) -> MorResult:
-    """Adaptive MOR: solve at the seeds, orthonormalise, project, refine until tolerance."""
+                     M: np.ndarray | None = None, solve_tol: float = 1e-10, deriv: bool = False) -> MorResult:
+    """Adaptive MOR: solve at the seeds, orthonormalise, project, refine until tolerance.
+
+    deriv: add the frequency-derivative indicator (reading of the derivative-driven selection): at
+    every sampled w_k the exact dG/dw = -c^T A^{-1} x (one more solve per column) is compared with the
+    reduced model's, d_k = max |dGhat/dw - dG/dw| / max |dG/dw|, and an interval's error becomes
+    max(e_k, d_k, d_{k+1})."""
     grid = np.linspace(wmin, wmax, ngrid)
     npp = B.shape[0]
 
@@ -139,8 +163,22 @@ def build_and_refine(hb, B: np.ndarray, C: np.ndarray, seeds, wmin: float, wmax:
         X, _ = sv.gmres_solve(hb, B, ws, eta, tol=solve_tol)
         return X
 
+    def dfull(ws, X):
+        """exact dG/dw [p, q] per w: -C A^{-1} x_p (dense or GMRES solves of A z = x)."""
+        out = {}
+        for k, w in enumerate(ws):
+            if solver == "dense":
+                A = (w - 1j * eta) * np.eye(M.shape[0]) + M
+                Zk = np.linalg.solve(A, X[k].T).T                 # [np, D]
+            else:
+                Zk, _ = sv.gmres_solve(hb, X[k], [w], eta, tol=solve_tol)
+                Zk = Zk[0]
+            out[float(w)] = -(C @ Zk.T).T
+        return out
+
     sampled = sorted(float(w) for w in seeds)
     X = full(sampled)                                    # [nw, np, D]
+    dG = dfull(sampled, X) if deriv else {}
     S, _ = orthonormalise(None, X.reshape(-1, X.shape[-1]).T)
     rm = project(hb, S, B, C)
     history = []
@@ -148,6 +186,9 @@ def build_and_refine(hb, B: np.ndarray, C: np.ndarray, seeds, wmin: float, wmax:
     while True:
         res = residuals(rm, B, grid, eta)
         e = interval_errors(sampled, grid, res)
+        if deriv:
+            d = derivative_mismatch(rm, sampled, dG, eta)
+            e = np.maximum(e, np.maximum(d[:-1], d[1:]))
         emax = float(e.max()) if len(e) else 0.0
         history.append((rm.m, emax))
         if emax <= tol:
@@ -158,6 +199,8 @@ def build_and_refine(hb, B: np.ndarray, C: np.ndarray, seeds, wmin: float, wmax:
         if not new:
             break
         Xn = full(new)
+        if deriv:
+            dG.update(dfull(new, Xn))
         S, _ = orthonormalise(rm.S, Xn.reshape(-1, Xn.shape[-1]).T)
         sampled = sorted(sampled + new)
         rm = project(hb, S, B, C)

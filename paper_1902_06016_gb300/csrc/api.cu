@@ -204,9 +204,10 @@ void solve_adjoint_columns(gfcc_ctx* c, const std::vector<double>& ws, double et
   GFCC_CUDA(cudaStreamSynchronize(s));
 }
 
-// Adjoint solves A(w)^T U = W for general right sides: W, U batch-minor [D][nw np], column w np + p
-// at frequency ws[w].
-void solve_adjoint_rhs(gfcc_ctx* c, const std::vector<double>& ws, double eta, int np, const cplx* Wall, cplx* Uall) {
+// Solves A(w) U = W (transpose: A(w)^T U = W) for general right sides: W, U batch-minor [D][nw np],
+// column w np + p at frequency ws[w].
+void solve_rhs(gfcc_ctx* c, const std::vector<double>& ws, double eta, int np, const cplx* Wall, cplx* Uall,
+               bool transpose) {
   cudaStream_t s = c->stream;
   const long long D = c->D;
   const long long ncols = (long long)ws.size() * np;
@@ -221,9 +222,10 @@ void solve_adjoint_rhs(gfcc_ctx* c, const std::vector<double>& ws, double eta, i
     GFCC_CUDA(cudaMemcpy2DAsync(B.p, sizeof(cplx) * nb, Wall + c0, sizeof(cplx) * ncols, sizeof(cplx) * nb, D,
                                 cudaMemcpyDeviceToDevice, s));
     gfcc::SolveStatus st;
-    gfcc::gmres_batched(c, B.p, Y.p, nullptr, sh.p, nb, st, true);
+    gfcc::gmres_batched(c, B.p, Y.p, nullptr, sh.p, nb, st, transpose);
     for (int k = 0; k < nb; ++k)
-      GFCC_CHECK(st.converged[k], GFCC_ERR_NOT_CONVERGED, "adjoint solve did not converge");
+      GFCC_CHECK(st.converged[k], GFCC_ERR_NOT_CONVERGED, transpose ? "adjoint solve did not converge"
+                                                                     : "derivative solve did not converge");
     GFCC_CUDA(cudaMemcpy2DAsync(Uall + c0, sizeof(cplx) * ncols, Y.p, sizeof(cplx) * nb, sizeof(cplx) * nb, D,
                                 cudaMemcpyDeviceToDevice, s));
   }
@@ -254,6 +256,22 @@ void mor_add_frequencies(gfcc_ctx* c, const std::vector<double>& ws) {
   mx_kernel<<<grid_for(D * ncols), 256, 0, s>>>(B.p, X.p, R.p, sh.p, MX.p, D, (int)ncols);
   GFCC_LAUNCH_CHECK();
   GFCC_CUDA(cudaStreamSynchronize(s));
+  if (c->opts.deriv_indicator) {   // exact dG/dw = -c_q^T A^{-1} x_p at the new samples
+    DBuf<cplx> Zd, dG;
+    const int nq = (int)ms.qorb.size();
+    Zd.alloc(D * ncols);
+    dG.alloc(ncols * nq);
+    solve_rhs(c, ws, ms.eta, np, X.p, Zd.p, false);
+    gfcc::green_from_batch(c->cvec.p, (int)D, ms.qorb.data(), nq, Zd.p, (int)ncols, (int)ncols, dG.p, s);
+    std::vector<cplx> h((size_t)ncols * nq);
+    GFCC_CUDA(cudaMemcpyAsync(h.data(), dG.p, sizeof(cplx) * h.size(), cudaMemcpyDeviceToHost, s));
+    GFCC_CUDA(cudaStreamSynchronize(s));
+    for (size_t k = 0; k < ws.size(); ++k) {
+      std::vector<cplx> d(h.begin() + (long long)k * np * nq, h.begin() + (long long)(k + 1) * np * nq);
+      for (cplx& z : d) z = make_cuDoubleComplex(-z.x, -z.y);
+      ms.dG_exact.push_back({ws[k], std::move(d)});
+    }
+  }
   gfcc::mor_append(c, X.p, MX.p, (int)ncols);
   for (double w : ws) ms.sampled.push_back(w);
   std::sort(ms.sampled.begin(), ms.sampled.end());
@@ -291,6 +309,7 @@ int gfcc_default_opts(gfcc_opts* o) {
   o->drop_tol = 1e-10;
   o->verbose = 0;
   o->residual_precision = -1;
+  o->deriv_indicator = 0;
   return GFCC_OK;
 }
 
@@ -301,6 +320,7 @@ static int check_opts(const gfcc_opts* o, std::string& why) {
   if (o->precision < GFCC_PREC_FP64 || o->precision > GFCC_PREC_FP64_TC) { why = "opts.precision unknown"; return GFCC_ERR_ARG; }
   if (o->max_batch < 0) { why = "opts.max_batch must be >= 0"; return GFCC_ERR_ARG; }
   if (!(o->drop_tol > 0.0 && o->drop_tol < 1.0)) { why = "opts.drop_tol must be in (0, 1)"; return GFCC_ERR_ARG; }
+  if (o->deriv_indicator != 0 && o->deriv_indicator != 1) { why = "opts.deriv_indicator must be 0 or 1"; return GFCC_ERR_ARG; }
   if (o->residual_precision != -1 && o->residual_precision != GFCC_PREC_FP64 && o->residual_precision != GFCC_PREC_FP64_TC) {
     why = "opts.residual_precision must be -1, GFCC_PREC_FP64 or GFCC_PREC_FP64_TC";
     return GFCC_ERR_ARG;
@@ -551,7 +571,7 @@ int gfcc_green_grad_t2(gfcc_t c, const double* omegas, int nw, double eta, const
   solve_columns(c, ws, eta, porb, qv, G ? Gd.p : nullptr, X.p, nullptr, &st);
   GFCC_CHECK(st.not_converged == 0, GFCC_ERR_NOT_CONVERGED, "gfcc_green_grad_t2: forward solve did not converge");
   gfcc::green_adjoint_rhs(c, qv, Gb.p, S, W.p);
-  solve_adjoint_rhs(c, ws, eta, np, W.p, U.p);
+  solve_rhs(c, ws, eta, np, W.p, U.p, true);
   const long long n2 = (long long)c->o * c->o * c->v * c->v;
   t2b.alloc(n2);
   gfcc::green_grad_t2_core(c, nw, porb, qv, Gb.p, X.p, U.p, t2b.p);
@@ -626,6 +646,31 @@ int gfcc_mor_refine(gfcc_t c, double wmin, double wmax, int ngrid, double tol, i
     for (size_t k = 0; k + 1 < smp.size(); ++k)
       for (int g = 0; g < ngrid; ++g)
         if (grid[g] > smp[k] && grid[g] < smp[k + 1]) e[k] = std::max(e[k], res[g]);
+    if (c->opts.deriv_indicator && smp.size() > 1) {   // derivative mismatch at the sampled ends
+      const int nq = (int)ms.qorb.size();
+      const int ns = (int)smp.size();
+      DBuf<cplx> dGh;
+      dGh.alloc((long long)ns * np * nq);
+      gfcc::mor_eval(c, smp.data(), ns, nullptr, nullptr, nullptr, dGh.p);
+      std::vector<cplx> h((size_t)ns * np * nq);
+      GFCC_CUDA(cudaMemcpyAsync(h.data(), dGh.p, sizeof(cplx) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+      GFCC_CUDA(cudaStreamSynchronize(c->stream));
+      std::vector<double> d(ns, 0.0);
+      for (int k = 0; k < ns; ++k) {
+        const std::vector<cplx>* ex = nullptr;
+        for (auto& pr : ms.dG_exact)
+          if (pr.first == smp[k]) { ex = &pr.second; break; }
+        if (!ex) continue;
+        double num = 0.0, den = 0.0;
+        for (int t = 0; t < np * nq; ++t) {
+          const cplx a = h[(size_t)k * np * nq + t], b = (*ex)[t];
+          num = std::max(num, std::hypot(a.x - b.x, a.y - b.y));
+          den = std::max(den, std::hypot(b.x, b.y));
+        }
+        d[k] = den > 0.0 ? num / den : 0.0;
+      }
+      for (size_t k = 0; k < e.size(); ++k) e[k] = std::max(e[k], std::max(d[k], d[k + 1]));
+    }
     emax = 0.0;
     for (double x : e) emax = std::max(emax, x);
     ms.history.push_back({ms.m, emax});

@@ -157,12 +157,14 @@ struct MorState {
   DBuf<cplx> RS, RZ;               // [q_cap x m_cap] col-major (ld q_cap)
   DBuf<cplx> RB;                   // [q_cap x np]    col-major (ld q_cap)
   std::vector<double> bnorm;       // ||b_p||
+  // exact dG/dw [np x nq] at the sampled frequencies (only with opts.deriv_indicator)
+  std::vector<std::pair<double, std::vector<cplx>>> dG_exact;
   std::vector<std::pair<int, double>> history;
   double last_max_err = -1.0;
   void reset() {
     built = false;
     eta = 0.0;
-    porb.clear(); qorb.clear(); sampled.clear(); bnorm.clear(); history.clear();
+    porb.clear(); qorb.clear(); sampled.clear(); bnorm.clear(); history.clear(); dG_exact.clear();
     m = 0; m_cap = 0; qn = 0; q_cap = 0;
     for (DBuf<cplx>* b : {&S, &Z, &Hh, &bh, &ch, &Q, &RS, &RZ, &RB}) b->release();
     last_max_err = -1.0;
@@ -294,7 +296,8 @@ void green_from_batch(const double* cvec, int D, const int* qrows, int nq, const
 // mor.cu
 void mor_init_basis(gfcc_ctx* c);   // Q <- orth(B), after porb/qorb/eta are set
 void mor_append(gfcc_ctx* c, const cplx* X, const cplx* MX, int ncols);
+// Ghat, A and residual estimates at the frequencies omegas (host); dG_dev (optional): dGhat/dw
 void mor_eval(gfcc_ctx* c, const double* omegas, int nw, cplx* G_dev, double* A_dev,
-              double* maxres_dev);
+              double* maxres_dev, cplx* dG_dev = nullptr);
 
 }  // namespace gfcc

@@ -136,6 +136,7 @@ struct EvalArgs {
   cplx* Y;            // solutions: Y[k * ldy + w * np + p] = yhat_p(w)[k]
   long long ldy;
   int* singular;
+  int rhs_in_Y = 0;   // 1: the right-hand sides are already in Y (per frequency), solved in place
 };
 
 __device__ __forceinline__ double cabs2(cplx a) { return a.x * a.x + a.y * a.y; }
@@ -155,9 +156,11 @@ __global__ void __launch_bounds__(256) eval_solve_kernel(EvalArgs a) {
   for (int w = blockIdx.x; w < a.nw; w += gridDim.x) {
     const cplx sig = make_cuDoubleComplex(a.omegas[w], -a.eta);
     cplx* R = a.Y + (long long)w * np;   // R[k * ldr + p]
-    for (long long t = threadIdx.x; t < (long long)m * np; t += blockDim.x) {
-      int k = (int)(t / np), p = (int)(t % np);
-      R[k * ldr + p] = a.bw[k + (long long)p * m];
+    if (!a.rhs_in_Y) {
+      for (long long t = threadIdx.x; t < (long long)m * np; t += blockDim.x) {
+        int k = (int)(t / np), p = (int)(t % np);
+        R[k * ldr + p] = a.bw[k + (long long)p * m];
+      }
     }
     for (int col = threadIdx.x; col < m; col += blockDim.x) {
       cplx h = a.H[(long long)col * m + 0];
@@ -899,7 +902,8 @@ void mor_append(gfcc_ctx* c, const cplx* Xin, const cplx* MXin, int nc) {
   put_cols(ms.RZ, ms.q_cap, m0, coef, ms.qn, acc, acc, s);
 }
 
-void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, double* A_dev, double* maxres_dev) {
+void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, double* A_dev, double* maxres_dev,
+              cplx* dG_dev) {
   MorState& ms = c->mor;
   cudaStream_t s = c->stream;
   ProfScope prof(PROF_MOR_EVAL, 0.0, s);
@@ -971,12 +975,13 @@ void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, doubl
   const long long bw_max = std::max<long long>(1, (2LL << 30) / ((long long)m * np * (long long)sizeof(cplx)));
   const int nbw = (int)std::min<long long>(nw, bw_max);
   const int ncta = (int)std::min<long long>(nbw, 2LL * 152);
-  DBuf<cplx> scratch, Y, Ys, Cr, Gt;
+  DBuf<cplx> scratch, Y, Ys, Cr, Gt, Yd;
   DBuf<double> rcol;
   scratch.alloc(per * ncta);
   Y.alloc((long long)m * nbw * np);
   const bool want_G = G_dev != nullptr || A_dev != nullptr;
   if (want_G && !G_dev) Gt.alloc((long long)nbw * np * nq);
+  if (dG_dev) Yd.alloc((long long)m * nbw * np);
   if (want_res) {
     Ys.alloc((long long)m * nbw * np);
     Cr.alloc((long long)qn * nbw * np);
@@ -1006,6 +1011,22 @@ void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, doubl
         spectral_from_G_kernel<<<(nb + 127) / 128, 128, 0, s>>>(Gb, nb, np, nq, dq.p, A_dev + w0);
         GFCC_LAUNCH_CHECK();
       }
+    }
+    if (dG_dev) {   // dGhat/dw = -chat^T (w - i eta + H)^{-2} bhat: a second solve with y as right side
+      GFCC_CUDA(cudaMemcpyAsync(Yd.p, Y.p, sizeof(cplx) * m * ldy, cudaMemcpyDeviceToDevice, s));
+      EvalArgs eb = ea;
+      eb.Y = Yd.p;
+      eb.rhs_in_Y = 1;
+      eval_solve_kernel<<<std::min(ncta, nb), 256, 0, s>>>(eb);
+      GFCC_LAUNCH_CHECK();
+      ZGemmDesc g;
+      g.M = nq; g.N = (int)ldy; g.K = m;
+      g.A = cw.p; g.sam = 1; g.sak = nq;
+      g.B = Yd.p; g.sbk = ldy; g.sbn = 1;
+      g.C = dG_dev + (long long)w0 * np * nq; g.scm = 1; g.scn = nq;
+      g.alpha = make_cuDoubleComplex(-1.0, 0.0);
+      g.work = zgemm_work(c);
+      zgemm(g, s);
     }
     if (want_res) {   // coefficients of r = (w - i eta) S y + Z y - b in the orthonormal residual basis
       shift_scale_kernel<<<grid_for((long long)m * ldy), 256, 0, s>>>(Y.p, ldy, m, np, nb, dom.p + w0, ms.eta, Ys.p);

@@ -34,7 +34,7 @@ class VBlocks(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_restarts", C.c_int),
                 ("precision", C.c_int), ("max_batch", C.c_int), ("drop_tol", C.c_double),
-                ("verbose", C.c_int), ("residual_precision", C.c_int)]
+                ("verbose", C.c_int), ("residual_precision", C.c_int), ("deriv_indicator", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -174,7 +174,7 @@ class Context:
     """One GFCC problem on the current CUDA device (wraps gfcc_t)."""
 
     def __init__(self, inputs, tol=1e-8, restart=30, max_restarts=200, precision="fp64", max_batch=0,
-                 drop_tol=1e-10, stream=None, residual_precision=None):
+                 drop_tol=1e-10, stream=None, residual_precision=None, deriv_indicator=False):
         lib = load()
         self._lib = lib
         o, v = inputs.o, inputs.v
@@ -185,6 +185,7 @@ class Context:
         opts.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         opts.max_batch, opts.drop_tol = max_batch, drop_tol
         opts.residual_precision = -1 if residual_precision is None else PRECISIONS[residual_precision]
+        opts.deriv_indicator = int(bool(deriv_indicator))
         self._keep = [_c64(x) for x in (inputs.eps, inputs.oooo, inputs.ooov, inputs.oovv, inputs.ovov,
                                          inputs.ovvv, inputs.t1, inputs.t2, inputs.l1, inputs.l2)]
         eps, oooo, ooov, oovv, ovov, ovvv, t1, t2, l1, l2 = self._keep
@@ -218,9 +219,11 @@ class Context:
         except Exception:
             pass
 
-    def set_opts(self, tol=1e-8, restart=30, max_restarts=200, precision="fp64", max_batch=0, drop_tol=1e-10):
+    def set_opts(self, tol=1e-8, restart=30, max_restarts=200, precision="fp64", max_batch=0, drop_tol=1e-10,
+                 deriv_indicator=False):
         opts = Opts()
         self._lib.gfcc_default_opts(C.byref(opts))
+        opts.deriv_indicator = int(bool(deriv_indicator))
         opts.tol, opts.restart, opts.max_restarts = tol, restart, max_restarts
         opts.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         opts.max_batch, opts.drop_tol = max_batch, drop_tol

@@ -132,6 +132,37 @@ def test_mor_matches_oracle_and_full(torch, o, v, seed):
     assert rel_err(ctx.mor_eval(info["sampled"])["G"], Gs) <= 1e-8
 
 
+@pytest.mark.parametrize("o,v,seed", [(4, 8, 1001), (7, 13, 103)])
+def test_mor_derivative_indicator_matches_oracle(torch, o, v, seed):
+    """Refinement driven by the dG/dw mismatch at the sampled frequencies: with a two-point residual
+    grid (no interior points, so the residual estimate alone stops at the seeds) the derivative
+    indicator adds midpoints; the GPU must choose the same frequencies as the oracle."""
+    inp = inputs(o, v, seed)
+    hb = hbar.build(inp)
+    M = sg.dense_matrix(hb)
+    porb = list(range(3))
+    B, C = bc.b_vectors(inp, porb), bc.c_vectors(inp, porb)
+    seeds, eta, tol = [-1.0, -0.6, -0.2], 0.02, 1e-6
+    orc = mor.build_and_refine(hb, B, C, seeds, -1.0, -0.2, 2, eta, tol, 10 ** 6, solver="dense", M=M, deriv=True)
+    assert len(orc.sampled) > len(seeds)
+    ctx = ctx_for(inp, tol=1e-11, deriv_indicator=True)
+    ctx.mor_build(seeds, eta, porb)
+    res = ctx.mor_refine(-1.0, -0.2, 2, tol, 10 ** 6)
+    assert res["converged"]
+    info = ctx.mor_info()
+    assert np.array_equal(info["sampled"], np.array(orc.sampled))
+    # the reduced model's dG/dw at the samples now matches the exact one within the tolerance
+    dG = mor.reduced_green_derivative(orc.model, orc.sampled, eta)
+    grid = np.linspace(-1.0, -0.2, 41)
+    assert rel_err(ctx.mor_eval(grid)["G"], mor.reduced_green(orc.model, grid, eta)) <= 1e-8
+    assert np.isfinite(dG).all()
+    # without the indicator the same call stops at the seeds
+    ctx2 = ctx_for(inp, tol=1e-11)
+    ctx2.mor_build(seeds, eta, porb)
+    ctx2.mor_refine(-1.0, -0.2, 2, tol, 10 ** 6)
+    assert np.array_equal(ctx2.mor_info()["sampled"], np.array(seeds))
+
+
 def test_mor_save_load_roundtrip(torch, tmp_path):
     inp = inputs(4, 8, 1001)
     porb = list(range(4))
