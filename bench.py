@@ -171,6 +171,7 @@ def run_ours(args, rank, world):
         ref = ctx.mor_refine(W["wmin"], W["wmax"], args.ngrid, args.mor_tol, args.m_max)
         ctx.mor_eval(omega_host, G=G_out, A=A_out)
         info = ctx.mor_info()
+        info.update(ctx.mor_stats())
         if keep:
             return ref, info, ctx
         ctx.close()
@@ -285,6 +286,7 @@ def run_ours(args, rank, world):
         "config": {"workload": args.workload, "o": o, "v": v, "D": inp.dim, "n_omega": nw, "n_p": o, "n_q": o,
                    "eta": eta, "window_ha": [W["wmin"], W["wmax"]], "seeds": args.seeds, "mor_tol": args.mor_tol,
                    "solve_tol": args.solve_tol, "model_order": info["m"], "sampled_freqs": len(info["sampled"]),
+                   "arnoldi_steps": info["arnoldi_steps"], "columns_solved": info["columns"],
                    "l2": "working set (operators >= 0.5 GB, Krylov bases) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "gemm_classes": kernels, "phases_ms": phases,

@@ -76,6 +76,9 @@ typedef struct {
   int deriv_indicator;  /* 1: the refinement also compares dG/dw of the reduced model with the exact
                            dG/dw = -c^T A^{-1} x at every sampled frequency (one more solve per column
                            at each new sample); default 0 */
+  int mor_guess;        /* 1 (default): solves at frequencies added by gfcc_mor_refine start from the
+                           current reduced model's prediction x0_p(w) = S yhat_p(w); 0: from zero.
+                           The solutions agree to the solver tolerance either way. */
 } gfcc_opts;
 
 typedef struct {
@@ -186,6 +189,10 @@ int gfcc_mor_eval(gfcc_t ctx, const double* omegas, int nw, double* G, double* A
  * *ns; *m receives the model order, *np and *nq the sizes of the p and q orbital sets. Any output
  * pointer may be NULL. */
 int gfcc_mor_info(gfcc_t ctx, double* w, int cap, int* ns, int* m, int* np, int* nq);
+
+/* Work of the full-dimension solves made by gfcc_mor_build and gfcc_mor_refine since the last build:
+ * Arnoldi steps summed over the solver's batches and columns solved (either pointer may be NULL). */
+int gfcc_mor_stats(gfcc_t ctx, long long* arnoldi_steps, long long* columns);
 
 /* Save / load the reduced model (sampled frequencies, S, Z = M S and the projected matrices) so that
  * refinement resumes without re-solving. The file is a flat binary written by this library. */

@@ -147,20 +147,28 @@ class MorResult:
 
 def build_and_refine(hb, B: np.ndarray, C: np.ndarray, seeds, wmin: float, wmax: float,
                      ngrid: int, eta: float, tol: float, m_max: int, solver="dense",
-                     M: np.ndarray | None = None, solve_tol: float = 1e-10, deriv: bool = False) -> MorResult:
+                     M: np.ndarray | None = None, solve_tol: float = 1e-10, deriv: bool = False,
+                     guess: bool = False, stats: dict | None = None) -> MorResult:
     """Adaptive MOR: solve at the seeds, orthonormalise, project, refine until tolerance.
 
     deriv: add the frequency-derivative indicator (reading of the derivative-driven selection): at
     every sampled w_k the exact dG/dw = -c^T A^{-1} x (one more solve per column) is compared with the
     reduced model's, d_k = max |dGhat/dw - dG/dw| / max |dG/dw|, and an interval's error becomes
-    max(e_k, d_k, d_{k+1})."""
+    max(e_k, d_k, d_{k+1}).
+    guess: (GMRES solver) solves at added frequencies start from the current model's prediction
+    x0_p(w) = S yhat_p(w) instead of zero; stats["gmres_iters"] counts the iterations of those solves."""
     grid = np.linspace(wmin, wmax, ngrid)
     npp = B.shape[0]
 
-    def full(ws):
+    def full(ws, model=None):
         if solver == "dense":
             return sv.dense_solve(M, B, ws, eta)
-        X, _ = sv.gmres_solve(hb, B, ws, eta, tol=solve_tol)
+        if model is None or not guess:
+            X, _ = sv.gmres_solve(hb, B, ws, eta, tol=solve_tol, stats=stats)
+            return X
+        Y = reduced_solve(model, ws, eta)                      # [nw, np, m]
+        X0 = np.einsum("dm,wpm->wpd", model.S, Y)
+        X, _ = sv.gmres_solve(hb, B, ws, eta, tol=solve_tol, x0=X0, stats=stats)
         return X
 
     def dfull(ws, X):
@@ -198,7 +206,7 @@ def build_and_refine(hb, B: np.ndarray, C: np.ndarray, seeds, wmin: float, wmax:
         new = choose_midpoints(sampled, e, tol, max_new)
         if not new:
             break
-        Xn = full(new)
+        Xn = full(new, rm)
         if deriv:
             dG.update(dfull(new, Xn))
         S, _ = orthonormalise(rm.S, Xn.reshape(-1, Xn.shape[-1]).T)

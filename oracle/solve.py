@@ -90,8 +90,9 @@ def gmres(matvec, b: np.ndarray, shift: complex, diag: np.ndarray, tol: float = 
 
 
 def gmres_solve(hb, B: np.ndarray, omegas, eta: float, tol: float = 1e-10, restart: int = 30,
-                maxiter: int = 3000) -> tuple[np.ndarray, np.ndarray]:
-    """X[w, p, :] by GMRES for every (w, p), with the oracle sigma as the matvec.
+                maxiter: int = 3000, x0=None, stats: dict | None = None) -> tuple[np.ndarray, np.ndarray]:
+    """X[w, p, :] by GMRES for every (w, p), with the oracle sigma as the matvec; x0[w, p, :] (optional)
+    initial guesses; stats["gmres_iters"] (optional) accumulates the iterations.
 
     Returns (X, final relative residuals [nw, np])."""
     diag = sg.diagonal(hb)
@@ -101,7 +102,9 @@ def gmres_solve(hb, B: np.ndarray, omegas, eta: float, tol: float = 1e-10, resta
     for k, w in enumerate(omegas):
         for p in range(B.shape[0]):
             x, hist, _ = gmres(mv, B[p], w - 1j * eta, diag, tol=tol, restart=restart,
-                               maxiter=maxiter)
+                               maxiter=maxiter, x0=None if x0 is None else x0[k, p])
+            if stats is not None:
+                stats["gmres_iters"] = stats.get("gmres_iters", 0) + len(hist) - 1
             X[k, p] = x
             res[k, p] = hist[-1]
     return X, res

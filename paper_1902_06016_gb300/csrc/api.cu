@@ -118,14 +118,15 @@ std::vector<int> q_positions(const std::vector<int>& porb, const std::vector<int
 // Solve all (w, p) columns; writes X (batch-minor, [D][ncols]) and R into caller-provided device
 // buffers when non-null, and G [ncols][nq] when Gdev is non-null.
 void solve_columns(gfcc_ctx* c, const std::vector<double>& ws, double eta, const std::vector<int>& porb,
-                   const std::vector<int>& qorb, cplx* Gdev, cplx* Xall, cplx* Rall, gfcc_stats* st_out) {
+                   const std::vector<int>& qorb, cplx* Gdev, cplx* Xall, cplx* Rall, gfcc_stats* st_out,
+                   const cplx* X0all = nullptr) {
   cudaStream_t s = c->stream;
   const long long D = c->D;
   const int np = (int)porb.size(), nq = (int)qorb.size();
   const long long ncols = (long long)ws.size() * np;
   const int nbmax = choose_batch(c, ncols);
   c->stats = gfcc::Stats{};
-  DBuf<cplx> B, X, R, sh;
+  DBuf<cplx> B, X, R, sh, X0;
   DBuf<int> rows;
   B.alloc(D * nbmax); X.alloc(D * nbmax); R.alloc(D * nbmax); sh.alloc(nbmax); rows.alloc(nbmax);
   double maxres = 0.0;
@@ -142,8 +143,13 @@ void solve_columns(gfcc_ctx* c, const std::vector<double>& ws, double eta, const
     GFCC_CUDA(cudaMemcpyAsync(rows.p, hr.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s));
     GFCC_CUDA(cudaMemcpyAsync(sh.p, hs.data(), sizeof(cplx) * nb, cudaMemcpyHostToDevice, s));
     gfcc::gather_rows_real_to_cplx(c->bvec.p, (int)D, rows.p, nb, (int)D, B.p, nb, s);
+    if (X0all) {   // initial guesses of this batch (columns c0 .. c0+nb of [D][ncols])
+      X0.alloc(D * nbmax);
+      GFCC_CUDA(cudaMemcpy2DAsync(X0.p, sizeof(cplx) * nb, X0all + c0, sizeof(cplx) * ncols, sizeof(cplx) * nb, D,
+                                  cudaMemcpyDeviceToDevice, s));
+    }
     gfcc::SolveStatus st;
-    gfcc::gmres_batched(c, B.p, X.p, R.p, sh.p, nb, st, false);
+    gfcc::gmres_batched(c, B.p, X.p, R.p, sh.p, nb, st, false, X0all ? X0.p : nullptr);
     for (int k = 0; k < nb; ++k) {
       maxres = std::max(maxres, st.relres[k]);
       if (!st.converged[k]) ++notconv;
@@ -243,7 +249,14 @@ void mor_add_frequencies(gfcc_ctx* c, const std::vector<double>& ws) {
   DBuf<int> rows;
   X.alloc(D * ncols); R.alloc(D * ncols); MX.alloc(D * ncols); B.alloc(D * ncols); sh.alloc(ncols);
   rows.alloc(ncols);
-  solve_columns(c, ws, ms.eta, ms.porb, ms.qorb, nullptr, X.p, R.p, nullptr);
+  DBuf<cplx> X0;
+  if (ms.m > 0 && c->opts.mor_guess) {   // initial guesses x0_p(w) = S yhat_p(w) from the current model
+    X0.alloc(D * ncols);
+    gfcc::mor_extrapolate(c, ws.data(), (int)ws.size(), X0.p);
+  }
+  solve_columns(c, ws, ms.eta, ms.porb, ms.qorb, nullptr, X.p, R.p, nullptr, X0.p);
+  ms.solve_iters += c->stats.gmres_iters;
+  ms.solve_cols += ncols;
   std::vector<int> hr(ncols);
   std::vector<cplx> hs(ncols);
   for (long long k = 0; k < ncols; ++k) {
@@ -310,6 +323,7 @@ int gfcc_default_opts(gfcc_opts* o) {
   o->verbose = 0;
   o->residual_precision = -1;
   o->deriv_indicator = 0;
+  o->mor_guess = 1;
   return GFCC_OK;
 }
 
@@ -321,6 +335,7 @@ static int check_opts(const gfcc_opts* o, std::string& why) {
   if (o->max_batch < 0) { why = "opts.max_batch must be >= 0"; return GFCC_ERR_ARG; }
   if (!(o->drop_tol > 0.0 && o->drop_tol < 1.0)) { why = "opts.drop_tol must be in (0, 1)"; return GFCC_ERR_ARG; }
   if (o->deriv_indicator != 0 && o->deriv_indicator != 1) { why = "opts.deriv_indicator must be 0 or 1"; return GFCC_ERR_ARG; }
+  if (o->mor_guess != 0 && o->mor_guess != 1) { why = "opts.mor_guess must be 0 or 1"; return GFCC_ERR_ARG; }
   if (o->residual_precision != -1 && o->residual_precision != GFCC_PREC_FP64 && o->residual_precision != GFCC_PREC_FP64_TC) {
     why = "opts.residual_precision must be -1, GFCC_PREC_FP64 or GFCC_PREC_FP64_TC";
     return GFCC_ERR_ARG;
@@ -729,6 +744,13 @@ int gfcc_mor_info(gfcc_t c, double* w, int cap, int* ns, int* m, int* np, int* n
   if (nq) *nq = (int)ms.qorb.size();
   if (w)
     for (int k = 0; k < cap && k < (int)ms.sampled.size(); ++k) w[k] = ms.sampled[k];
+  return GFCC_OK;
+}
+
+int gfcc_mor_stats(gfcc_t c, long long* arnoldi_steps, long long* columns) {
+  if (!c) return GFCC_ERR_ARG;
+  if (arnoldi_steps) *arnoldi_steps = c->mor.solve_iters;
+  if (columns) *columns = c->mor.solve_cols;
   return GFCC_OK;
 }
 

@@ -160,11 +160,13 @@ struct MorState {
   // exact dG/dw [np x nq] at the sampled frequencies (only with opts.deriv_indicator)
   std::vector<std::pair<double, std::vector<cplx>>> dG_exact;
   std::vector<std::pair<int, double>> history;
+  long long solve_iters = 0, solve_cols = 0;   // Arnoldi steps (summed over batches) and columns solved
   double last_max_err = -1.0;
   void reset() {
     built = false;
     eta = 0.0;
     porb.clear(); qorb.clear(); sampled.clear(); bnorm.clear(); history.clear(); dG_exact.clear();
+    solve_iters = 0; solve_cols = 0;
     m = 0; m_cap = 0; qn = 0; q_cap = 0;
     for (DBuf<cplx>* b : {&S, &Z, &Hh, &bh, &ch, &Q, &RS, &RZ, &RB}) b->release();
     last_max_err = -1.0;
@@ -279,9 +281,10 @@ struct SolveStatus {
   std::vector<int> iters;       // per column
   std::vector<int> converged;   // per column
 };
-// Solve (shift_c + M) x_c = b_c for nb columns (batch-minor layout, ld = nb).
+// Solve (shift_c + M) x_c = b_c for nb columns (batch-minor layout, ld = nb), starting from X0 (same
+// layout) when it is non-null, else from zero.
 void gmres_batched(gfcc_ctx* c, const cplx* B, cplx* X, cplx* R, const cplx* shifts, int nb,
-                   SolveStatus& st, bool transpose);
+                   SolveStatus& st, bool transpose, const cplx* X0 = nullptr);
 
 // ---- kernels shared between units ------------------------------------------------------------
 void gather_rows_real_to_cplx(const double* src, int ld_src, const int* rows, int nrows, int D,
@@ -296,6 +299,8 @@ void green_from_batch(const double* cvec, int D, const int* qrows, int nq, const
 // mor.cu
 void mor_init_basis(gfcc_ctx* c);   // Q <- orth(B), after porb/qorb/eta are set
 void mor_append(gfcc_ctx* c, const cplx* X, const cplx* MX, int ncols);
+// x0_p(w) = S yhat_p(w) from the current reduced model, X0 [D][nw np] (device)
+void mor_extrapolate(gfcc_ctx* c, const double* omegas, int nw, cplx* X0);
 // Ghat, A and residual estimates at the frequencies omegas (host); dG_dev (optional): dGhat/dw
 void mor_eval(gfcc_ctx* c, const double* omegas, int nw, cplx* G_dev, double* A_dev,
               double* maxres_dev, cplx* dG_dev = nullptr);

@@ -504,7 +504,7 @@ static void inner_sigma(gfcc_ctx* c, const cuFloatComplex* Z, cuFloatComplex* W,
 // precision only bounds the progress of one cycle, not the final accuracy).
 template <typename VT>
 static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, const cplx* shifts_dev, int nb0,
-                       SolveStatus& st, bool transpose) {
+                       SolveStatus& st, bool transpose, const cplx* X0) {
   cudaStream_t s = c->stream;
   const long long D = c->D;
   const int k = std::max(1, std::min(c->opts.restart, 256));
@@ -545,7 +545,8 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
   }
   GFCC_CUDA(cudaMemcpyAsync(Bw.p, Bin, sizeof(cplx) * D * nb0, cudaMemcpyDeviceToDevice, s));
   GFCC_CUDA(cudaMemcpyAsync(shw.p, shifts_dev, sizeof(cplx) * nb0, cudaMemcpyDeviceToDevice, s));
-  Xw.zero(s);
+  if (X0) GFCC_CUDA(cudaMemcpyAsync(Xw.p, X0, sizeof(cplx) * D * nb0, cudaMemcpyDeviceToDevice, s));
+  else Xw.zero(s);
   {  // non-finite right-hand sides or shifts
     flag.zero(s);
     nonfinite_cplx_kernel<<<grid_for(D * nb0), 256, 0, s>>>(Bw.p, D * nb0, flag.p);
@@ -577,6 +578,11 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
     GFCC_CUDA(cudaMemcpyAsync(hres.data(), nrm.p, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
     GFCC_CUDA(cudaStreamSynchronize(s));
     c->stats.restarts++;
+    if (c->opts.verbose) {
+      double mx = 0.0;
+      for (int w = 0; w < nb; ++w) mx = std::max(mx, hbn[map[w]] > 0.0 ? hres[w] / hbn[map[w]] : 0.0);
+      fprintf(stderr, "gfcc gmres: cycle %d, %d columns, max relative residual %.3e\n", cycle, nb, mx);
+    }
     if ((inner_prec != GFCC_PREC_FP64 || resid_prec != GFCC_PREC_FP64) && low_precision_error(c))
       throw Error{GFCC_ERR_CUDA, "solve: a tensor-core pipeline wait timed out"};
 
@@ -765,10 +771,10 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
 }
 
 void gmres_batched(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, const cplx* shifts_dev, int nb0,
-                   SolveStatus& st, bool transpose) {
+                   SolveStatus& st, bool transpose, const cplx* X0) {
   const bool f32 = (c->opts.precision == GFCC_PREC_TF32 || c->opts.precision == GFCC_PREC_BF16) && !transpose;
-  if (f32) gmres_impl<cuFloatComplex>(c, Bin, Xout, Rout, shifts_dev, nb0, st, transpose);
-  else gmres_impl<cplx>(c, Bin, Xout, Rout, shifts_dev, nb0, st, transpose);
+  if (f32) gmres_impl<cuFloatComplex>(c, Bin, Xout, Rout, shifts_dev, nb0, st, transpose, X0);
+  else gmres_impl<cplx>(c, Bin, Xout, Rout, shifts_dev, nb0, st, transpose, X0);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -124,6 +124,25 @@ __global__ void house_right_update_kernel(cplx* __restrict__ A, long long lda, i
   }
 }
 
+// Y[r0 + i][n] -= tau v[i] sum_k conj(v[k]) Y[r0 + k][n] for every column n < N (Y row-major, ld ldy)
+__global__ void house_rows_kernel(cplx* __restrict__ Y, long long ldy, long long N, int r0, int len,
+                                  const cplx* __restrict__ v, const double* __restrict__ tau) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  cplx sdot = cz();
+  for (int k = 0; k < len; ++k) {
+    const cplx vv = v[k], yy = Y[(long long)(r0 + k) * ldy + n];
+    sdot.x += vv.x * yy.x + vv.y * yy.y;
+    sdot.y += vv.x * yy.y - vv.y * yy.x;
+  }
+  const double t = *tau;
+  for (int k = 0; k < len; ++k) {
+    const cplx d = cuCmul(v[k], sdot);
+    Y[(long long)(r0 + k) * ldy + n].x -= t * d.x;
+    Y[(long long)(r0 + k) * ldy + n].y -= t * d.y;
+  }
+}
+
 // ---- per-frequency shifted Hessenberg solve --------------------------------------------------------
 struct EvalArgs {
   int m, np, nw;
@@ -1051,6 +1070,75 @@ void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, doubl
   GFCC_CUDA(cudaMemcpyAsync(&hs, dsing.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   GFCC_CUDA(cudaStreamSynchronize(s));
   GFCC_CHECK(hs == 0, GFCC_ERR_NONFINITE, "mor_eval: singular reduced system at a requested frequency");
+}
+
+// Initial guesses for new frequencies: x0_p(w) = S yhat_p(w) with (w - i eta + Hhat) yhat_p = bhat_p.
+// Hhat is reduced to Hessenberg form H = P^H Hhat P by Householder reflections (recorded), each
+// frequency is the shifted Hessenberg solve of eval_solve_kernel, yhat = P y_H applies the reflections
+// in reverse order, and X0 = S yhat is one complex GEMM. X0: [D][nw np] batch-minor (column w np + p).
+void mor_extrapolate(gfcc_ctx* c, const double* omegas_host, int nw, cplx* X0) {
+  MorState& ms = c->mor;
+  cudaStream_t s = c->stream;
+  const int m = ms.m, np = (int)ms.porb.size(), cap = ms.m_cap;
+  GFCC_CHECK(m > 0, GFCC_ERR_STATE, "mor_extrapolate: empty reduced model");
+  const long long N = (long long)nw * np;
+  DBuf<cplx> Hw, bw, Vr, Y, scratch;
+  DBuf<double> taus, dom;
+  DBuf<int> dsing;
+  Hw.alloc((long long)m * m); bw.alloc((long long)m * np);
+  Vr.alloc((long long)m * m); taus.alloc(m);
+  GFCC_CUDA(cudaMemcpy2DAsync(Hw.p, sizeof(cplx) * m, ms.Hh.p, sizeof(cplx) * cap, sizeof(cplx) * m, m,
+                              cudaMemcpyDeviceToDevice, s));
+  GFCC_CUDA(cudaMemcpy2DAsync(bw.p, sizeof(cplx) * m, ms.bh.p, sizeof(cplx) * cap, sizeof(cplx) * m, np,
+                              cudaMemcpyDeviceToDevice, s));
+  DBuf<cplx> wv;
+  wv.alloc(m);
+  for (int j = 0; j + 2 < m; ++j) {
+    const int len = m - j - 1;
+    cplx* v = Vr.p + (long long)j * m;
+    double* tau = taus.p + j;
+    house_kernel<<<1, 256, 0, s>>>(Hw.p + (long long)j * m + j + 1, len, v, tau);
+    GFCC_LAUNCH_CHECK();
+    house_left_kernel<<<m - j, 256, 0, s>>>(Hw.p, m, j + 1, len, j, v, tau);
+    GFCC_LAUNCH_CHECK();
+    house_left_kernel<<<np, 256, 0, s>>>(bw.p, m, j + 1, len, 0, v, tau);
+    GFCC_LAUNCH_CHECK();
+    house_right_w_kernel<<<(m + 127) / 128, 128, 0, s>>>(Hw.p, m, m, j + 1, len, v, wv.p);
+    GFCC_LAUNCH_CHECK();
+    house_right_update_kernel<<<grid_for((long long)m * len), 256, 0, s>>>(Hw.p, m, m, j + 1, len, v, wv.p, tau);
+    GFCC_LAUNCH_CHECK();
+  }
+  const long long per = (long long)m * (m + 1) / 2 + 2LL * m + 64;
+  const int ncta = (int)std::min<long long>(nw, 2LL * 152);
+  scratch.alloc(per * ncta);
+  Y.alloc((long long)m * N);
+  dom.alloc(nw); dsing.alloc(1);
+  dsing.zero(s);
+  GFCC_CUDA(cudaMemcpyAsync(dom.p, omegas_host, sizeof(double) * nw, cudaMemcpyHostToDevice, s));
+  EvalArgs ea;
+  ea.m = m; ea.np = np; ea.nw = nw;
+  ea.H = Hw.p; ea.bw = bw.p;
+  ea.omegas = dom.p; ea.eta = ms.eta;
+  ea.scratch = scratch.p; ea.scratch_per_cta = per;
+  ea.Y = Y.p; ea.ldy = N; ea.singular = dsing.p;
+  eval_solve_kernel<<<ncta, 256, 0, s>>>(ea);
+  GFCC_LAUNCH_CHECK();
+  for (int j = m - 3; j >= 0; --j) {   // yhat = P y_H, P = H_0 H_1 ... (Hermitian reflectors)
+    house_rows_kernel<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(Y.p, N, N, j + 1, m - j - 1, Vr.p + (long long)j * m,
+                                                                  taus.p + j);
+    GFCC_LAUNCH_CHECK();
+  }
+  ZGemmDesc g;   // X0[nu][n] = sum_k S[nu][k] yhat[k][n]
+  g.M = (int)c->D; g.N = (int)N; g.K = m;
+  g.A = ms.S.p; g.sam = cap; g.sak = 1;
+  g.B = Y.p; g.sbk = N; g.sbn = 1;
+  g.C = X0; g.scm = N; g.scn = 1;
+  g.work = zgemm_work(c);
+  zgemm(g, s);
+  int hs = 0;
+  GFCC_CUDA(cudaMemcpyAsync(&hs, dsing.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GFCC_CUDA(cudaStreamSynchronize(s));
+  GFCC_CHECK(hs == 0, GFCC_ERR_NONFINITE, "mor_extrapolate: singular reduced system at a new frequency");
 }
 
 }  // namespace gfcc

@@ -137,9 +137,9 @@ void contract(double alpha, const TV& A, const TV& B, double beta, const TV& C, 
   std::vector<int> pc0 = perm_of(lt0, lc);
   // contractions above this many multiply-adds use the tensor cores (GFCC_OZ_MIN_MACS overrides it,
   // which the tests use to exercise this path at small sizes)
-  double min_macs = 2e9;
+  double min_macs = 5e8;
   if (const char* env = getenv("GFCC_OZ_MIN_MACS")) min_macs = atof(env);
-  if ((double)M * (double)N * (double)K >= min_macs && M >= 64 && N >= 64) {
+  if ((double)M * (double)N * (double)K >= min_macs && M >= 16 && N >= 16) {
     // FP64-accurate GEMM from exact bf16 slices on the tensor cores (8 slices: FP64-level accuracy)
     const double* Aop2 = A.p;
     std::vector<int> pa2 = perm_of(la, Ml + Kl);

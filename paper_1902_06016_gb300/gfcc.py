@@ -34,7 +34,8 @@ class VBlocks(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_restarts", C.c_int),
                 ("precision", C.c_int), ("max_batch", C.c_int), ("drop_tol", C.c_double),
-                ("verbose", C.c_int), ("residual_precision", C.c_int), ("deriv_indicator", C.c_int)]
+                ("verbose", C.c_int), ("residual_precision", C.c_int), ("deriv_indicator", C.c_int),
+                ("mor_guess", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -59,6 +60,7 @@ PROTOTYPES = {
     "gfcc_mor_refine": (C.c_int, [_vp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, _ip, _dp]),
     "gfcc_mor_eval": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp]),
     "gfcc_mor_info": (C.c_int, [_vp, _dp, C.c_int, _ip, _ip, _ip, _ip]),
+    "gfcc_mor_stats": (C.c_int, [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "gfcc_mor_save": (C.c_int, [_vp, C.c_char_p]),
     "gfcc_mor_load": (C.c_int, [_vp, C.c_char_p]),
     "gfcc_tc_gemm": (C.c_int, [C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]),
@@ -174,7 +176,8 @@ class Context:
     """One GFCC problem on the current CUDA device (wraps gfcc_t)."""
 
     def __init__(self, inputs, tol=1e-8, restart=30, max_restarts=200, precision="fp64", max_batch=0,
-                 drop_tol=1e-10, stream=None, residual_precision=None, deriv_indicator=False):
+                 drop_tol=1e-10, stream=None, residual_precision=None, deriv_indicator=False, mor_guess=True,
+                 verbose=False):
         lib = load()
         self._lib = lib
         o, v = inputs.o, inputs.v
@@ -186,6 +189,8 @@ class Context:
         opts.max_batch, opts.drop_tol = max_batch, drop_tol
         opts.residual_precision = -1 if residual_precision is None else PRECISIONS[residual_precision]
         opts.deriv_indicator = int(bool(deriv_indicator))
+        opts.mor_guess = int(bool(mor_guess))
+        opts.verbose = int(bool(verbose))
         self._keep = [_c64(x) for x in (inputs.eps, inputs.oooo, inputs.ooov, inputs.oovv, inputs.ovov,
                                          inputs.ovvv, inputs.t1, inputs.t2, inputs.l1, inputs.l2)]
         eps, oooo, ooov, oovv, ovov, ovvv, t1, t2, l1, l2 = self._keep
@@ -220,10 +225,11 @@ class Context:
             pass
 
     def set_opts(self, tol=1e-8, restart=30, max_restarts=200, precision="fp64", max_batch=0, drop_tol=1e-10,
-                 deriv_indicator=False):
+                 deriv_indicator=False, mor_guess=True):
         opts = Opts()
         self._lib.gfcc_default_opts(C.byref(opts))
         opts.deriv_indicator = int(bool(deriv_indicator))
+        opts.mor_guess = int(bool(mor_guess))
         opts.tol, opts.restart, opts.max_restarts = tol, restart, max_restarts
         opts.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         opts.max_batch, opts.drop_tol = max_batch, drop_tol
@@ -338,6 +344,12 @@ class Context:
         self._check(self._lib.gfcc_mor_info(self._h, w.ctypes.data_as(_dp), ns.value, C.byref(ns), C.byref(m),
                                             C.byref(npp), C.byref(nq)))
         return {"sampled": w[:ns.value].copy(), "m": m.value, "np": npp.value, "nq": nq.value}
+
+    def mor_stats(self):
+        """{"arnoldi_steps", "columns"} of the full solves made by mor_build / mor_refine."""
+        a, b = C.c_longlong(), C.c_longlong()
+        self._check(self._lib.gfcc_mor_stats(self._h, C.byref(a), C.byref(b)))
+        return {"arnoldi_steps": a.value, "columns": b.value}
 
     def mor_save(self, path):
         self._check(self._lib.gfcc_mor_save(self._h, os.fsencode(path)))

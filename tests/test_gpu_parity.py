@@ -201,3 +201,23 @@ def test_errors_are_status_codes(torch):
     ctx3 = ctx_for(inp, tol=1e-14, restart=2, max_restarts=2)
     r = ctx3.solve_full([-0.5], 0.01, [0, 1])
     assert not r["converged"] and r["stats"].not_converged > 0 and np.all(np.isfinite(r["A"]))
+
+
+def test_mor_extrapolated_guess_same_model_less_work(torch):
+    """Refinement solves started from the reduced model's prediction: same sampled frequencies and the
+    same reduced Green's function as from zero guesses, with fewer Arnoldi steps."""
+    inp = inputs(7, 13, 103)
+    porb = list(range(7))
+    out = {}
+    for guess in (False, True):
+        # solver tolerance 1e-9: well above the floor of the FP64-accurate residuals, so that the step
+        # counts measure convergence and not stagnation at that floor
+        ctx = ctx_for(inp, tol=1e-9, precision="tf32", mor_guess=guess)
+        ctx.mor_build([-1.0, -0.2], 0.01, porb)
+        s0 = ctx.mor_stats()["arnoldi_steps"]
+        ctx.mor_refine(-1.0, -0.2, 201, 1e-6, 10 ** 6)
+        out[guess] = (ctx.mor_info()["sampled"], ctx.mor_eval(np.linspace(-1.0, -0.2, 51))["G"],
+                      ctx.mor_stats()["arnoldi_steps"] - s0)
+    assert np.array_equal(out[True][0], out[False][0]) and len(out[True][0]) > 2
+    assert rel_err(out[True][1], out[False][1]) <= 1e-7
+    assert out[True][2] < out[False][2]

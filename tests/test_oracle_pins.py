@@ -285,3 +285,31 @@ def test_reduced_green_derivative_and_derivative_indicator():
         A = (w - 0.02j) * np.eye(M.shape[0]) + M
         dG[w] = -(C @ np.linalg.solve(A, X.T)).T
     assert mor.derivative_mismatch(r1.model, r1.sampled, dG, 0.02).max() <= 1e-6
+
+
+def test_model_extrapolated_initial_guess():
+    """Solves at refinement frequencies started from the reduced model's prediction x0 = S yhat: the
+    initial residual equals the model's residual estimate (Galerkin), the refined model and samples are
+    the same as from zero guesses, and the GMRES iterations of those solves drop."""
+    from oracle import mor
+    inp = synth.make_inputs(7, 13, 103)
+    hb = hbar.build(inp)
+    porb = list(range(3))
+    B, C = bc.b_vectors(inp, porb), bc.c_vectors(inp, porb)
+    S, _ = mor.orthonormalise(None, sv.gmres_solve(hb, B, [-0.9, -0.3], 0.02, tol=1e-11)[0].reshape(-1, inp.dim).T)
+    rm = mor.project(hb, S, B, C)
+    w = -0.6
+    x0 = S @ mor.reduced_solve(rm, [w], 0.02)[0].T                 # [D, np]
+    r0 = np.linalg.norm(B.T - ((w - 0.02j) * x0 + sg.sigma(hb, x0.T).T), axis=0) / np.linalg.norm(B, axis=1)
+    assert np.allclose(r0, mor.residuals(rm, B, [w], 0.02)[0], rtol=1e-8)
+    runs = {}
+    for g in (False, True):
+        st = {}
+        runs[g] = (mor.build_and_refine(hb, B, C, [-1.0, -0.2], -1.0, -0.2, 41, 0.02, 1e-6, 10 ** 6,
+                                        solver="gmres", solve_tol=1e-11, guess=g, stats=st), st)
+    assert runs[True][0].sampled == runs[False][0].sampled
+    grid = np.linspace(-1.0, -0.2, 17)
+    G0 = mor.reduced_green(runs[False][0].model, grid, 0.02)
+    G1 = mor.reduced_green(runs[True][0].model, grid, 0.02)
+    assert np.abs(G1 - G0).max() <= 1e-8 * np.abs(G0).max()
+    assert runs[True][1]["gmres_iters"] < runs[False][1]["gmres_iters"]
