@@ -234,7 +234,9 @@ long long gfcc_launch_count(void);
  * 13 splitting of FP64 rows into exact slices; 14 the fused Gram-Schmidt sweeps of FP32-basis Arnoldi
  * steps; 15, 16, 17 the first, second and third of those sweeps alone for batches of at least 32
  * columns; 18 the three sweeps of batches of fewer than 32 columns (classes 14-18 count algorithmic
- * HBM bytes in the "flops" field). Events are recorded on the stream each region is launched on. */
+ * HBM bytes in the "flops" field); 19 Householder reductions of Hhat to Hessenberg form; 20 the
+ * per-frequency shifted Hessenberg solves. Events are recorded on the stream each region is launched
+ * on. */
 int gfcc_profile(int enable);
 
 /* Sum over the recorded launches of class cls: number of launches, device milliseconds (CUDA

@@ -858,6 +858,7 @@ int gfcc_mor_load(gfcc_t c, const char* path) {
   ms.m = m;
   ms.qn = qn;
   ms.built = true;
+  ++ms.version;
   API_END(c)
 }
 

@@ -61,7 +61,9 @@ enum ProfClass {
   PROF_CGS_UPDATE_DOT = 16,   // second sweep alone (batches of >= 32 columns; bytes)
   PROF_CGS_UPDATE_NORM = 17,  // third sweep alone (batches of >= 32 columns; bytes)
   PROF_CGS_SMALL_NB = 18,     // the three sweeps of batches of fewer than 32 columns (bytes)
-  PROF_NCLASS = 19
+  PROF_EVAL_HESS = 19,        // Householder reduction of Hhat to Hessenberg form (evaluation, guesses)
+  PROF_EVAL_SOLVE = 20,       // per-frequency shifted Hessenberg solves
+  PROF_NCLASS = 21
 };
 struct ProfScope {   // records CUDA events around one launch on stream s when profiling is on
   int cls;
@@ -161,12 +163,23 @@ struct MorState {
   std::vector<std::pair<double, std::vector<cplx>>> dG_exact;
   std::vector<std::pair<int, double>> history;
   long long solve_iters = 0, solve_cols = 0;   // Arnoldi steps (summed over batches) and columns solved
+  // Hessenberg form of the current model (mor.cu: hessenberg()), valid while hess_version == version:
+  // H = P^H Hhat P, P^H bhat, chat P, RS P, RZ P, RB, and the reflectors (column j of hV, tau in htau)
+  long long version = 0, hess_version = -1;
+  bool hess_res = false;
+  int hess_qn = 0;
+  DBuf<cplx> hH, hb, hc, hA1, hA2, hRB, hV;
+  DBuf<double> htau;
   double last_max_err = -1.0;
   void reset() {
     built = false;
     eta = 0.0;
     porb.clear(); qorb.clear(); sampled.clear(); bnorm.clear(); history.clear(); dG_exact.clear();
     solve_iters = 0; solve_cols = 0;
+    ++version;
+    hess_version = -1;
+    for (DBuf<cplx>* b : {&hH, &hb, &hc, &hA1, &hA2, &hRB, &hV}) b->release();
+    htau.release();
     m = 0; m_cap = 0; qn = 0; q_cap = 0;
     for (DBuf<cplx>* b : {&S, &Z, &Hh, &bh, &ch, &Q, &RS, &RZ, &RB}) b->release();
     last_max_err = -1.0;
@@ -229,6 +242,8 @@ void zgemm(const ZGemmDesc& g, cudaStream_t s);
 // the context's workspace for exact-slice complex GEMMs (created on first use, freed with the context)
 void* zgemm_work(gfcc_ctx* c);
 void zgemm_work_free(gfcc_ctx* c);
+// throws GFCC_ERR_CUDA if a tensor-core wait of a GEMM that used the context's workspace timed out
+void zgemm_work_check(gfcc_ctx* c);
 
 // ---- grad.cu: T2 gradient of L = Re sum conj(Gbar) G ------------------------------------------
 // W[nu][w np + p] = sum_q conj(Gbar[w][p][q]) c_q[nu]   (right sides of the adjoint solves)

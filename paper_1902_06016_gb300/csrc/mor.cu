@@ -72,53 +72,67 @@ __global__ void house_kernel(const cplx* __restrict__ x, int len, cplx* __restri
     *tau = (nx > 0.0 && vn2 > 0.0) ? 2.0 / vn2 : 0.0;
   }
 }
-// left: A[r0+i][col] -= tau v[i] (sum_k conj(v[k]) A[r0+k][col]) for col in [c0, c0+ncols); one block per column
-__global__ void house_left_kernel(cplx* __restrict__ A, long long lda, int r0, int len, int c0,
-                                  const cplx* __restrict__ v, const double* __restrict__ tau) {
+// A reflection H = I - tau v v^H applied to several column-major matrices at once (one launch per side
+// and Householder step):
+//   left:  A[r0+i][col] -= tau v[i] (sum_k conj(v[k]) A[r0+k][col]) on the columns of A (from c0a) and B
+//   right: w[row] = sum_k A[row][c0+k] v[k]; A[row][c0+k] -= tau w[row] conj(v[k]) on up to four matrices
+struct RightMats {
+  cplx* p[4];
+  long long ld[4];
+  int rows[4];
+  int n;
+};
+__global__ void house_left2_kernel(cplx* __restrict__ A, long long lda, int c0a, int na, cplx* __restrict__ B,
+                                   long long ldb, int nbc, int r0, int len, const cplx* __restrict__ v,
+                                   const double* __restrict__ tau) {
   __shared__ cplx red[256];
-  const int col = c0 + blockIdx.x;
-  cplx* a = A + (long long)col * lda + r0;
-  cplx s = cz();
+  const bool inA = (int)blockIdx.x < na;
+  cplx* a = inA ? A + (long long)(c0a + blockIdx.x) * lda + r0 : B + (long long)(blockIdx.x - na) * ldb + r0;
+  (void)nbc;
+  cplx sdot = cz();
   for (int i = threadIdx.x; i < len; i += blockDim.x) {
-    cplx vv = v[i], aa = a[i];
-    s.x += vv.x * aa.x + vv.y * aa.y;
-    s.y += vv.x * aa.y - vv.y * aa.x;
+    const cplx vv = v[i], aa = a[i];
+    sdot.x += vv.x * aa.x + vv.y * aa.y;
+    sdot.y += vv.x * aa.y - vv.y * aa.x;
   }
-  red[threadIdx.x] = s;
+  red[threadIdx.x] = sdot;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < w) { red[threadIdx.x].x += red[threadIdx.x + w].x; red[threadIdx.x].y += red[threadIdx.x + w].y; }
     __syncthreads();
   }
-  cplx wsum = red[0];
-  double t = *tau;
+  const cplx wsum = red[0];
+  const double t = *tau;
   for (int i = threadIdx.x; i < len; i += blockDim.x) {
-    cplx vv = v[i];
-    cplx d = cuCmul(vv, wsum);
+    const cplx d = cuCmul(v[i], wsum);
     a[i].x -= t * d.x;
     a[i].y -= t * d.y;
   }
 }
-// right: w[row] = sum_k A[row][c0+k] v[k]; A[row][c0+k] -= tau w[row] conj(v[k]); rows [0, nrows)
-__global__ void house_right_w_kernel(const cplx* __restrict__ A, long long lda, int nrows, int c0, int len,
-                                     const cplx* __restrict__ v, cplx* __restrict__ w) {
+// w[k][row] = sum_j A_k[row][c0 + j] v[j] for every matrix k and row (w rows stacked, matrix k at woff[k])
+__global__ void house_right_w4_kernel(RightMats m, int c0, int len, const cplx* __restrict__ v, cplx* __restrict__ w) {
   int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= nrows) return;
-  cplx s = cz();
-  for (int k = 0; k < len; ++k) s = cuCadd(s, cuCmul(A[(long long)(c0 + k) * lda + row], v[k]));
-  w[row] = s;
+  int k = 0, off = 0;
+  while (k < m.n && row >= m.rows[k]) { row -= m.rows[k]; off += m.rows[k]; ++k; }
+  if (k >= m.n) return;
+  const cplx* A = m.p[k];
+  cplx sum = cz();
+  for (int j = 0; j < len; ++j) sum = cuCadd(sum, cuCmul(A[(long long)(c0 + j) * m.ld[k] + row], v[j]));
+  w[off + row] = sum;
 }
-__global__ void house_right_update_kernel(cplx* __restrict__ A, long long lda, int nrows, int c0, int len,
-                                          const cplx* __restrict__ v, const cplx* __restrict__ w,
-                                          const double* __restrict__ tau) {
-  long long total = (long long)nrows * len;
-  double t = *tau;
+// A_k[row][c0 + j] -= tau w[k][row] conj(v[j])
+__global__ void house_right_update4_kernel(RightMats m, int c0, int len, const cplx* __restrict__ v,
+                                           const cplx* __restrict__ w, const double* __restrict__ tau, long long total) {
+  const double t = *tau;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
        q += (long long)gridDim.x * blockDim.x) {
-    int row = (int)(q % nrows);
-    int k = (int)(q / nrows);
-    cplx d = cuCmul(w[row], cuConj(v[k]));
-    cplx* p = A + (long long)(c0 + k) * lda + row;
+    long long r = q;
+    int k = 0, off = 0;
+    while (k < m.n && r >= (long long)m.rows[k] * len) { r -= (long long)m.rows[k] * len; off += m.rows[k]; ++k; }
+    if (k >= m.n) return;
+    const int row = (int)(r % m.rows[k]), j = (int)(r / m.rows[k]);
+    const cplx d = cuCmul(w[off + row], cuConj(v[j]));
+    cplx* p = m.p[k] + (long long)(c0 + j) * m.ld[k] + row;
     p->x -= t * d.x;
     p->y -= t * d.y;
   }
@@ -735,6 +749,7 @@ std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cp
       GFCC_LAUNCH_CHECK();
     }
   }
+  zgemm_work_check(c);
   std::vector<int> hk(nc);
   GFCC_CUDA(cudaMemcpyAsync(hk.data(), keep.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
   GFCC_CUDA(cudaStreamSynchronize(s));
@@ -823,6 +838,7 @@ static void put_cols(DBuf<cplx>& R, int ld, int col0, const std::vector<cplx>& h
 
 void mor_init_basis(gfcc_ctx* c) {
   MorState& ms = c->mor;
+  ++ms.version;
   cudaStream_t s = c->stream;
   const long long D = c->D;
   const int np = (int)ms.porb.size();
@@ -840,6 +856,7 @@ void mor_init_basis(gfcc_ctx* c) {
 
 void mor_append(gfcc_ctx* c, const cplx* Xin, const cplx* MXin, int nc) {
   MorState& ms = c->mor;
+  ++ms.version;   // the model changes: its cached Hessenberg form is stale
   cudaStream_t s = c->stream;
   ProfScope prof(PROF_MOR_ORTHO, 0.0, s);
   const long long D = c->D;
@@ -919,6 +936,70 @@ void mor_append(gfcc_ctx* c, const cplx* Xin, const cplx* MXin, int nc) {
   grow_model(c, m1);
   put_cols(ms.RS, ms.q_cap, m0, coef, ms.qn, 0, acc, s);
   put_cols(ms.RZ, ms.q_cap, m0, coef, ms.qn, acc, acc, s);
+  zgemm_work_check(c);
+}
+
+// Hessenberg form of the current reduced model, computed once per model version and reused by every
+// evaluation and extrapolation: Householder reflections H_j = I - tau_j v_j v_j^H (j = 0..m-3),
+// H = P^H Hhat P with P = H_0 H_1 ...; the left reflections go to bhat, the right ones to chat and
+// (want_res) to the residual coefficient matrices.
+static void hessenberg(gfcc_ctx* c, bool want_res) {
+  MorState& ms = c->mor;
+  if (ms.hess_version == ms.version && (!want_res || (ms.hess_res && ms.hess_qn == ms.qn))) return;
+  cudaStream_t s = c->stream;
+  ProfScope prof_h(PROF_EVAL_HESS, 0.0, s);
+  const int m = ms.m, np = (int)ms.porb.size(), nq = (int)ms.qorb.size(), cap = ms.m_cap, qn = ms.qn;
+  ms.hH.alloc((long long)m * m); ms.hb.alloc((long long)m * np); ms.hc.alloc((long long)nq * m);
+  ms.hV.alloc((long long)m * m); ms.htau.alloc(m);
+  cplx *Hw = ms.hH.p, *bw = ms.hb.p, *cw = ms.hc.p;
+  GFCC_CUDA(cudaMemcpy2DAsync(Hw, sizeof(cplx) * m, ms.Hh.p, sizeof(cplx) * cap, sizeof(cplx) * m, m,
+                              cudaMemcpyDeviceToDevice, s));
+  GFCC_CUDA(cudaMemcpy2DAsync(bw, sizeof(cplx) * m, ms.bh.p, sizeof(cplx) * cap, sizeof(cplx) * m, np,
+                              cudaMemcpyDeviceToDevice, s));
+  GFCC_CUDA(cudaMemcpyAsync(cw, ms.ch.p, sizeof(cplx) * nq * m, cudaMemcpyDeviceToDevice, s));
+  cplx *A1 = nullptr, *A2 = nullptr;
+  if (want_res) {
+    ms.hA1.alloc((long long)qn * m); ms.hA2.alloc((long long)qn * m); ms.hRB.alloc((long long)qn * np);
+    A1 = ms.hA1.p; A2 = ms.hA2.p;
+    GFCC_CUDA(cudaMemcpy2DAsync(A1, sizeof(cplx) * qn, ms.RS.p, sizeof(cplx) * ms.q_cap, sizeof(cplx) * qn, m,
+                                cudaMemcpyDeviceToDevice, s));
+    GFCC_CUDA(cudaMemcpy2DAsync(A2, sizeof(cplx) * qn, ms.RZ.p, sizeof(cplx) * ms.q_cap, sizeof(cplx) * qn, m,
+                                cudaMemcpyDeviceToDevice, s));
+    GFCC_CUDA(cudaMemcpy2DAsync(ms.hRB.p, sizeof(cplx) * qn, ms.RB.p, sizeof(cplx) * ms.q_cap, sizeof(cplx) * qn, np,
+                                cudaMemcpyDeviceToDevice, s));
+  }
+  DBuf<cplx> wv;
+  wv.alloc((long long)m + nq + 2LL * qn + 1);
+  RightMats rm;
+  rm.n = 0;
+  auto add = [&](cplx* p, long long ld, int rows) {
+    if (rows > 0) { rm.p[rm.n] = p; rm.ld[rm.n] = ld; rm.rows[rm.n] = rows; ++rm.n; }
+  };
+  add(Hw, m, m);
+  add(cw, nq, nq);
+  if (want_res) { add(A1, qn, qn); add(A2, qn, qn); }
+  long long rows_all = 0;
+  for (int k = 0; k < rm.n; ++k) rows_all += rm.rows[k];
+  for (int j = 0; j + 2 < m; ++j) {
+    const int len = m - j - 1;
+    cplx* v = ms.hV.p + (long long)j * m;
+    double* tau = ms.htau.p + j;
+    house_kernel<<<1, 256, 0, s>>>(Hw + (long long)j * m + j + 1, len, v, tau);
+    GFCC_LAUNCH_CHECK();
+    // left: columns j.. of H and all np columns of bhat
+    house_left2_kernel<<<(m - j) + np, 256, 0, s>>>(Hw, m, j, m - j, bw, m, np, j + 1, len, v, tau);
+    GFCC_LAUNCH_CHECK();
+    // right: H, chat and the residual coefficient matrices
+    house_right_w4_kernel<<<(unsigned)((rows_all + 127) / 128), 128, 0, s>>>(rm, j + 1, len, v, wv.p);
+    GFCC_LAUNCH_CHECK();
+    house_right_update4_kernel<<<grid_for(rows_all * len), 256, 0, s>>>(rm, j + 1, len, v, wv.p, tau,
+                                                                        rows_all * len);
+    GFCC_LAUNCH_CHECK();
+  }
+  GFCC_CUDA(cudaStreamSynchronize(s));   // wv is released on return
+  ms.hess_version = ms.version;
+  ms.hess_res = want_res;
+  ms.hess_qn = qn;
 }
 
 void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, double* A_dev, double* maxres_dev,
@@ -926,57 +1007,13 @@ void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, doubl
   MorState& ms = c->mor;
   cudaStream_t s = c->stream;
   ProfScope prof(PROF_MOR_EVAL, 0.0, s);
-  const int m = ms.m, np = (int)ms.porb.size(), nq = (int)ms.qorb.size(), cap = ms.m_cap, qn = ms.qn;
+  const int m = ms.m, np = (int)ms.porb.size(), nq = (int)ms.qorb.size(), qn = ms.qn;
   GFCC_CHECK(m > 0, GFCC_ERR_STATE, "mor_eval: empty reduced model");
   const bool want_res = maxres_dev != nullptr;
-  DBuf<cplx> Hw, bw, cw, A1, A2, RBw, v, wv;
-  DBuf<double> tau, dbn;
-  Hw.alloc((long long)m * m); bw.alloc((long long)m * np); cw.alloc((long long)nq * m);
-  GFCC_CUDA(cudaMemcpy2DAsync(Hw.p, sizeof(cplx) * m, ms.Hh.p, sizeof(cplx) * cap, sizeof(cplx) * m, m,
-                              cudaMemcpyDeviceToDevice, s));
-  GFCC_CUDA(cudaMemcpy2DAsync(bw.p, sizeof(cplx) * m, ms.bh.p, sizeof(cplx) * cap, sizeof(cplx) * m, np,
-                              cudaMemcpyDeviceToDevice, s));
-  GFCC_CUDA(cudaMemcpyAsync(cw.p, ms.ch.p, sizeof(cplx) * nq * m, cudaMemcpyDeviceToDevice, s));
-  if (want_res) {
-    A1.alloc((long long)qn * m); A2.alloc((long long)qn * m); RBw.alloc((long long)qn * np);
-    GFCC_CUDA(cudaMemcpy2DAsync(A1.p, sizeof(cplx) * qn, ms.RS.p, sizeof(cplx) * ms.q_cap, sizeof(cplx) * qn, m,
-                                cudaMemcpyDeviceToDevice, s));
-    GFCC_CUDA(cudaMemcpy2DAsync(A2.p, sizeof(cplx) * qn, ms.RZ.p, sizeof(cplx) * ms.q_cap, sizeof(cplx) * qn, m,
-                                cudaMemcpyDeviceToDevice, s));
-    GFCC_CUDA(cudaMemcpy2DAsync(RBw.p, sizeof(cplx) * qn, ms.RB.p, sizeof(cplx) * ms.q_cap, sizeof(cplx) * qn, np,
-                                cudaMemcpyDeviceToDevice, s));
-  }
-  // Householder reduction to upper Hessenberg form: H = P^H Hhat P, P = P_0 P_1 ...; the left
-  // reflections go to bhat, the right ones to chat and to the residual coefficient matrices.
-  v.alloc(m); wv.alloc(std::max({m, nq, qn, 1})); tau.alloc(1);
-  for (int j = 0; j + 2 < m; ++j) {
-    const int len = m - j - 1;
-    house_kernel<<<1, 256, 0, s>>>(Hw.p + (long long)j * m + j + 1, len, v.p, tau.p);
-    GFCC_LAUNCH_CHECK();
-    house_left_kernel<<<m - j, 256, 0, s>>>(Hw.p, m, j + 1, len, j, v.p, tau.p);
-    GFCC_LAUNCH_CHECK();
-    house_left_kernel<<<np, 256, 0, s>>>(bw.p, m, j + 1, len, 0, v.p, tau.p);
-    GFCC_LAUNCH_CHECK();
-    house_right_w_kernel<<<(m + 127) / 128, 128, 0, s>>>(Hw.p, m, m, j + 1, len, v.p, wv.p);
-    GFCC_LAUNCH_CHECK();
-    house_right_update_kernel<<<grid_for((long long)m * len), 256, 0, s>>>(Hw.p, m, m, j + 1, len, v.p, wv.p, tau.p);
-    GFCC_LAUNCH_CHECK();
-    house_right_w_kernel<<<(nq + 127) / 128, 128, 0, s>>>(cw.p, nq, nq, j + 1, len, v.p, wv.p);
-    GFCC_LAUNCH_CHECK();
-    house_right_update_kernel<<<grid_for((long long)nq * len), 256, 0, s>>>(cw.p, nq, nq, j + 1, len, v.p, wv.p, tau.p);
-    GFCC_LAUNCH_CHECK();
-    if (want_res) {
-      house_right_w_kernel<<<(qn + 127) / 128, 128, 0, s>>>(A1.p, qn, qn, j + 1, len, v.p, wv.p);
-      GFCC_LAUNCH_CHECK();
-      house_right_update_kernel<<<grid_for((long long)qn * len), 256, 0, s>>>(A1.p, qn, qn, j + 1, len, v.p, wv.p, tau.p);
-      GFCC_LAUNCH_CHECK();
-      house_right_w_kernel<<<(qn + 127) / 128, 128, 0, s>>>(A2.p, qn, qn, j + 1, len, v.p, wv.p);
-      GFCC_LAUNCH_CHECK();
-      house_right_update_kernel<<<grid_for((long long)qn * len), 256, 0, s>>>(A2.p, qn, qn, j + 1, len, v.p, wv.p, tau.p);
-      GFCC_LAUNCH_CHECK();
-    }
-    GFCC_LAUNCH_CHECK();
-  }
+  hessenberg(c, want_res);
+  const cplx *Hw = ms.hH.p, *bw = ms.hb.p, *cw = ms.hc.p;
+  const cplx *A1 = ms.hA1.p, *A2 = ms.hA2.p, *RBw = ms.hRB.p;
+  DBuf<double> dbn;
   std::vector<int> qidx(np, -1);
   for (int p = 0; p < np; ++p)
     for (int q = 0; q < nq; ++q)
@@ -1011,17 +1048,20 @@ void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, doubl
     const long long ldy = (long long)nb * np;
     EvalArgs ea;
     ea.m = m; ea.np = np; ea.nw = nb;
-    ea.H = Hw.p; ea.bw = bw.p;
+    ea.H = Hw; ea.bw = bw;
     ea.omegas = dom.p + w0; ea.eta = ms.eta;
     ea.scratch = scratch.p; ea.scratch_per_cta = per;
     ea.Y = Y.p; ea.ldy = ldy; ea.singular = dsing.p;
-    eval_solve_kernel<<<std::min(ncta, nb), 256, 0, s>>>(ea);
-    GFCC_LAUNCH_CHECK();
+    {
+      ProfScope ps(PROF_EVAL_SOLVE, 0.0, s);
+      eval_solve_kernel<<<std::min(ncta, nb), 256, 0, s>>>(ea);
+      GFCC_LAUNCH_CHECK();
+    }
     if (want_G) {   // G(q, n) = sum_k cw[q][k] Y[k][n], stored at Gb[n nq + q]
       cplx* Gb = G_dev ? G_dev + (long long)w0 * np * nq : Gt.p;
       ZGemmDesc g;
       g.M = nq; g.N = (int)ldy; g.K = m;
-      g.A = cw.p; g.sam = 1; g.sak = nq;
+      g.A = cw; g.sam = 1; g.sak = nq;
       g.B = Y.p; g.sbk = ldy; g.sbn = 1;
       g.C = Gb; g.scm = 1; g.scn = nq;
       g.work = zgemm_work(c);
@@ -1040,7 +1080,7 @@ void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, doubl
       GFCC_LAUNCH_CHECK();
       ZGemmDesc g;
       g.M = nq; g.N = (int)ldy; g.K = m;
-      g.A = cw.p; g.sam = 1; g.sak = nq;
+      g.A = cw; g.sam = 1; g.sak = nq;
       g.B = Yd.p; g.sbk = ldy; g.sbn = 1;
       g.C = dG_dev + (long long)w0 * np * nq; g.scm = 1; g.scn = nq;
       g.alpha = make_cuDoubleComplex(-1.0, 0.0);
@@ -1052,15 +1092,15 @@ void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, doubl
       GFCC_LAUNCH_CHECK();
       ZGemmDesc g;
       g.M = qn; g.N = (int)ldy; g.K = m;
-      g.A = A1.p; g.sam = 1; g.sak = qn;
+      g.A = A1; g.sam = 1; g.sak = qn;
       g.B = Ys.p; g.sbk = ldy; g.sbn = 1;
       g.C = Cr.p; g.scm = ldy; g.scn = 1;
       g.work = zgemm_work(c);
       zgemm(g, s);
-      g.A = A2.p; g.B = Y.p; g.beta = make_cuDoubleComplex(1.0, 0.0);
+      g.A = A2; g.B = Y.p; g.beta = make_cuDoubleComplex(1.0, 0.0);
       g.work = zgemm_work(c);
       zgemm(g, s);
-      resnorm_kernel<<<(unsigned)((ldy + 255) / 256), 256, 0, s>>>(Cr.p, ldy, qn, RBw.p, np, nb, dbn.p, rcol.p);
+      resnorm_kernel<<<(unsigned)((ldy + 255) / 256), 256, 0, s>>>(Cr.p, ldy, qn, RBw, np, nb, dbn.p, rcol.p);
       GFCC_LAUNCH_CHECK();
       rowmax_kernel<<<(nb + 127) / 128, 128, 0, s>>>(rcol.p, np, nb, maxres_dev + w0);
       GFCC_LAUNCH_CHECK();
@@ -1070,6 +1110,7 @@ void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, doubl
   GFCC_CUDA(cudaMemcpyAsync(&hs, dsing.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   GFCC_CUDA(cudaStreamSynchronize(s));
   GFCC_CHECK(hs == 0, GFCC_ERR_NONFINITE, "mor_eval: singular reduced system at a requested frequency");
+  zgemm_work_check(c);
 }
 
 // Initial guesses for new frequencies: x0_p(w) = S yhat_p(w) with (w - i eta + Hhat) yhat_p = bhat_p.
@@ -1082,32 +1123,10 @@ void mor_extrapolate(gfcc_ctx* c, const double* omegas_host, int nw, cplx* X0) {
   const int m = ms.m, np = (int)ms.porb.size(), cap = ms.m_cap;
   GFCC_CHECK(m > 0, GFCC_ERR_STATE, "mor_extrapolate: empty reduced model");
   const long long N = (long long)nw * np;
-  DBuf<cplx> Hw, bw, Vr, Y, scratch;
-  DBuf<double> taus, dom;
+  hessenberg(c, false);
+  DBuf<cplx> Y, scratch;
+  DBuf<double> dom;
   DBuf<int> dsing;
-  Hw.alloc((long long)m * m); bw.alloc((long long)m * np);
-  Vr.alloc((long long)m * m); taus.alloc(m);
-  GFCC_CUDA(cudaMemcpy2DAsync(Hw.p, sizeof(cplx) * m, ms.Hh.p, sizeof(cplx) * cap, sizeof(cplx) * m, m,
-                              cudaMemcpyDeviceToDevice, s));
-  GFCC_CUDA(cudaMemcpy2DAsync(bw.p, sizeof(cplx) * m, ms.bh.p, sizeof(cplx) * cap, sizeof(cplx) * m, np,
-                              cudaMemcpyDeviceToDevice, s));
-  DBuf<cplx> wv;
-  wv.alloc(m);
-  for (int j = 0; j + 2 < m; ++j) {
-    const int len = m - j - 1;
-    cplx* v = Vr.p + (long long)j * m;
-    double* tau = taus.p + j;
-    house_kernel<<<1, 256, 0, s>>>(Hw.p + (long long)j * m + j + 1, len, v, tau);
-    GFCC_LAUNCH_CHECK();
-    house_left_kernel<<<m - j, 256, 0, s>>>(Hw.p, m, j + 1, len, j, v, tau);
-    GFCC_LAUNCH_CHECK();
-    house_left_kernel<<<np, 256, 0, s>>>(bw.p, m, j + 1, len, 0, v, tau);
-    GFCC_LAUNCH_CHECK();
-    house_right_w_kernel<<<(m + 127) / 128, 128, 0, s>>>(Hw.p, m, m, j + 1, len, v, wv.p);
-    GFCC_LAUNCH_CHECK();
-    house_right_update_kernel<<<grid_for((long long)m * len), 256, 0, s>>>(Hw.p, m, m, j + 1, len, v, wv.p, tau);
-    GFCC_LAUNCH_CHECK();
-  }
   const long long per = (long long)m * (m + 1) / 2 + 2LL * m + 64;
   const int ncta = (int)std::min<long long>(nw, 2LL * 152);
   scratch.alloc(per * ncta);
@@ -1117,15 +1136,15 @@ void mor_extrapolate(gfcc_ctx* c, const double* omegas_host, int nw, cplx* X0) {
   GFCC_CUDA(cudaMemcpyAsync(dom.p, omegas_host, sizeof(double) * nw, cudaMemcpyHostToDevice, s));
   EvalArgs ea;
   ea.m = m; ea.np = np; ea.nw = nw;
-  ea.H = Hw.p; ea.bw = bw.p;
+  ea.H = ms.hH.p; ea.bw = ms.hb.p;
   ea.omegas = dom.p; ea.eta = ms.eta;
   ea.scratch = scratch.p; ea.scratch_per_cta = per;
   ea.Y = Y.p; ea.ldy = N; ea.singular = dsing.p;
   eval_solve_kernel<<<ncta, 256, 0, s>>>(ea);
   GFCC_LAUNCH_CHECK();
   for (int j = m - 3; j >= 0; --j) {   // yhat = P y_H, P = H_0 H_1 ... (Hermitian reflectors)
-    house_rows_kernel<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(Y.p, N, N, j + 1, m - j - 1, Vr.p + (long long)j * m,
-                                                                  taus.p + j);
+    house_rows_kernel<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(Y.p, N, N, j + 1, m - j - 1,
+                                                                  ms.hV.p + (long long)j * m, ms.htau.p + j);
     GFCC_LAUNCH_CHECK();
   }
   ZGemmDesc g;   // X0[nu][n] = sum_k S[nu][k] yhat[k][n]
@@ -1139,6 +1158,7 @@ void mor_extrapolate(gfcc_ctx* c, const double* omegas_host, int nw, cplx* X0) {
   GFCC_CUDA(cudaMemcpyAsync(&hs, dsing.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   GFCC_CUDA(cudaStreamSynchronize(s));
   GFCC_CHECK(hs == 0, GFCC_ERR_NONFINITE, "mor_extrapolate: singular reduced system at a new frequency");
+  zgemm_work_check(c);
 }
 
 }  // namespace gfcc

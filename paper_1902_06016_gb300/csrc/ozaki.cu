@@ -315,10 +315,21 @@ void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s) {
   oz_gemm(sa, sb, M, 2 * N, T.p, 2 * N, 0.0, w, s);
   zscatter_kernel<<<grid_for(M * N), 256, 0, s>>>(T.p, M, N, g.C, g.scm, g.scn, g.alpha, g.beta);
   GFCC_LAUNCH_CHECK();
+  if (g.work) return;   // the caller checks the workspace's error flag (zgemm_work_check) later
   int herr = 0;
   GFCC_CUDA(cudaMemcpyAsync(&herr, w.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   GFCC_CUDA(cudaStreamSynchronize(s));
   GFCC_CHECK(herr == 0, GFCC_ERR_CUDA, "zgemm_oz: tensor-core pipeline wait timed out");
+}
+
+void zgemm_work_check(gfcc_ctx* c) {
+  if (!c->zwork) return;
+  ZWork* z = static_cast<ZWork*>(c->zwork);
+  if (z->w.err.n == 0) return;
+  int herr = 0;
+  GFCC_CUDA(cudaMemcpyAsync(&herr, z->w.err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  GFCC_CUDA(cudaStreamSynchronize(c->stream));
+  GFCC_CHECK(herr == 0, GFCC_ERR_CUDA, "exact-slice GEMM: tensor-core pipeline wait timed out");
 }
 
 void oz_slice_into(const double* X, long long ldx, long long nrows, long long K, SlicedRows& out, long long row0,
