@@ -150,7 +150,7 @@ def run_ours(args, rank, world):
     W = synth.WORKLOADS[args.workload]
     o, v, eta = W["o"], W["v"], W["eta"]
     nw = args.nomega or W["nw"]
-    inp = synth.make_inputs(o, v, W["seed"] + rank)       # weak scaling: one problem per rank
+    inp = synth.make_inputs(o, v, rank_seed(W["seed"], rank))   # weak scaling: one problem per rank
     porb = list(range(o))
     seeds = synth.omega_grid(W["wmin"], W["wmax"], args.seeds)
     grid = np.linspace(W["wmin"], W["wmax"], nw)
@@ -239,13 +239,9 @@ def run_ours(args, rank, world):
     if kept is not None:
         kept.close()
 
-    # max over ranks
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dev_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = float(t.item())
-    value = world * nw * o / (dev_ms / 1e3)
+    # max over ranks; every rank solved its own problem (weak scaling)
+    dev_ms = max_over_ranks(dev_ms, dev, world)
+    value = job_value(nw, o, world, dev_ms)
 
     peaks, peak_kind = measured_peaks()
     bf16 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
@@ -301,6 +297,27 @@ def run_ours(args, rank, world):
         "clocks": clk,
         "full_fp64": full,
     }
+
+
+def max_over_ranks(x: float, device, world: int) -> float:
+    """The largest x over the ranks of the process group (x itself for a single process)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_omega: int, n_p: int, world: int, ms_per_step: float) -> float:
+    """Whole-job G points/s: every rank evaluates n_omega x n_p points of its own problem per step."""
+    return world * n_omega * n_p / (ms_per_step / 1e3)
+
+
+def rank_seed(base_seed: int, rank: int) -> int:
+    """Seed of the synthetic problem of a rank (independent replicas)."""
+    return base_seed + rank
 
 
 def full_compare(args, ctx, grid, porb, eta, stream):
