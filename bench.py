@@ -425,7 +425,9 @@ def run_reference(args):
     for _ in range(args.warmup):
         pass   # the oracle has no warm-up effects worth a full sample; samples are bounded
     for _ in range(max(1, args.steps)):
-        vals.append(oracle_sample(args, args.cpu_sample))
+        r = oracle_sample(args, args.cpu_sample)
+        r.pop("_G", None)
+        vals.append(r)
     v = statistics.median(x["value"] for x in vals)
     cb = dict(vals[0])
     cb["value"] = v
