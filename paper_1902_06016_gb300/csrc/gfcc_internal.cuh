@@ -63,7 +63,10 @@ enum ProfClass {
   PROF_CGS_SMALL_NB = 18,     // the three sweeps of batches of fewer than 32 columns (bytes)
   PROF_EVAL_HESS = 19,        // Householder reduction of Hhat to Hessenberg form (evaluation, guesses)
   PROF_EVAL_SOLVE = 20,       // per-frequency shifted Hessenberg solves
-  PROF_NCLASS = 21
+  PROF_ORTHO_GRAM = 21,       // block Gram-Schmidt coefficient products (basis^H block)
+  PROF_ORTHO_UPDATE = 22,     // block Gram-Schmidt updates (block -= basis coefficients)
+  PROF_ORTHO_CHOLQR = 23,     // Cholesky QR of the panels
+  PROF_NCLASS = 24
 };
 struct ProfScope {   // records CUDA events around one launch on stream s when profiling is on
   int cls;

@@ -340,7 +340,9 @@ void regrow_cm(DBuf<cplx>& b, int old_ld, int new_ld, int alloc_cols, int nrows,
 }
 
 // FP64 arithmetic runs on a narrow pipe on this GPU: every product of the orthonormalisation above a
-// small size goes to the exact-slice tensor-core GEMM (7 slices, 48 bits per row).
+// small size goes to the exact-slice tensor-core GEMM (7 slices, 48 bits per row). Fewer slices are
+// not enough: the residual basis resolves the solver-residual directions of Z = M S, about 1e-8 of
+// the columns' norms, and 41-bit products perturb them enough to spoil the refinement estimates.
 void fp64_accurate_zgemm(const ZGemmDesc& g, cudaStream_t s) {
   if ((double)g.M * (double)g.N * (double)g.K >= (double)(1 << 22) && g.batch == 1) zgemm_oz(g, 7, s);
   else zgemm(g, s);
@@ -571,10 +573,11 @@ std::vector<cplx> inverse_upper(const std::vector<cplx>& R, int n) {
 // Panel of pb columns Y[:, c0:c0+pb] (already orthogonal to every earlier column): Cholesky QR twice
 // (Y = Q R2 R1 with the Gram matrices formed by FP64-accurate GEMMs). In exact arithmetic this is the
 // column-by-column Gram-Schmidt of the panel (the same Q and R with a positive diagonal). It is taken
-// only when the panel is well conditioned: every first-pass pivot R1_jj at least 1e-5 of the largest
-// column norm of the panel and at least 1e-7 of the column's norm before any projection (n0), so
-// that two passes give orthonormality to rounding and no column is near the drop threshold; otherwise
-// the caller runs the column-by-column passes. Writes T[c0:c0+pb, c0:c0+pb] = R2 R1 and keep = 1.
+// only when the panel is well conditioned: every first-pass pivot R1_jj at least 1e-5 of its column's
+// norm (a bound on the conditioning of the column-scaled panel, which is what Cholesky QR's accuracy
+// depends on) and at least 10 drop_tol of the column's norm before any projection (n0), so that two
+// passes give orthonormality to rounding and no column is within a factor 10 of the drop threshold;
+// otherwise the caller runs the column-by-column passes. Writes T[c0:c0+pb, c0:c0+pb] = R2 R1 and keep = 1.
 struct PanelWork {
   DBuf<cplx> Gd, Rinv, tmp;
 };
@@ -621,11 +624,9 @@ bool panel_cholqr2(gfcc_ctx* c, cplx* Y, cplx* MY, int nc, long long D, int c0, 
   };
   gram();
   if (!cholesky_upper(G, pb, R1)) return false;
-  double cmax = 0.0;
-  for (int j = 0; j < pb; ++j) cmax = std::max(cmax, std::sqrt(G[(size_t)j * pb + j].x));
-  for (int j = 0; j < pb; ++j) {
+  for (int j = 0; j < pb; ++j) {   // pivot relative to the column's own norm (scale-invariant test)
     const double r = R1[(size_t)j * pb + j].x;
-    if (!(r >= 1e-5 * cmax) || !(r >= 1e-7 * n0[j])) return false;
+    if (!(r >= 1e-5 * std::sqrt(G[(size_t)j * pb + j].x)) || !(r >= 10.0 * c->opts.drop_tol * n0[j])) return false;
   }
   apply(R1);
   gram();
@@ -690,7 +691,10 @@ std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cp
       g.B = Y + col0; g.sbk = nc; g.sbn = 1;
       g.C = Cf.p; g.scm = ncols; g.scn = 1;
       g.work = zgemm_work(c);
-      fp64_accurate_zgemm(g, s);
+      {
+        ProfScope pg(PROF_ORTHO_GRAM, 0.0, s);
+        fp64_accurate_zgemm(g, s);
+      }
       ZGemmDesc u;
       u.M = (int)D; u.N = ncols; u.K = np_;
       u.A = Pb; u.sam = ldp; u.sak = 1;
@@ -698,8 +702,11 @@ std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cp
       u.C = Y + col0; u.scm = nc; u.scn = 1;
       u.alpha = make_cuDoubleComplex(-1.0, 0.0); u.beta = make_cuDoubleComplex(1.0, 0.0);
       u.work = zgemm_work(c);
-      fp64_accurate_zgemm(u, s);
-      if (MY) { u.A = MPb; u.C = MY + col0; fp64_accurate_zgemm(u, s); }
+      {
+        ProfScope pu(PROF_ORTHO_UPDATE, 0.0, s);
+        fp64_accurate_zgemm(u, s);
+        if (MY) { u.A = MPb; u.C = MY + col0; fp64_accurate_zgemm(u, s); }
+      }
       if (to_cold) {
         if (Cold) {   // Cold (col-major, ld n_cur) += Cf (row-major [n_cur][nc])
           int dims[3] = {np_, ncols, 2};
@@ -728,7 +735,12 @@ std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cp
     const int pb = std::min(PB, nc - c0);
     if (c0 > 0) block_cgs(Y, nc, c0, MY, c0, pb, false);
     ProfScope pp(PROF_MOR_PANEL, 0.0, s);
-    if (panel_cholqr2(c, Y, MY, nc, D, c0, pb, hn0.data() + c0, T, keep.p, pwork)) continue;
+    bool done;
+    {
+      ProfScope pq(PROF_ORTHO_CHOLQR, 0.0, s);
+      done = panel_cholqr2(c, Y, MY, nc, D, c0, pb, hn0.data() + c0, T, keep.p, pwork);
+    }
+    if (done) continue;
     for (int j = c0; j < c0 + pb; ++j) {
       const int n = j - c0;
       if (n > 0) {
