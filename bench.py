@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--ngrid", type=int, default=500, help="refinement check grid")
     ap.add_argument("--m-max", type=int, default=1700)
     ap.add_argument("--solve-tol", type=float, default=1e-8)
+    ap.add_argument("--restart", type=int, default=30, help="GMRES(k) Krylov dimension per cycle")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--full-points", type=int, default=4,
                     help="output frequencies (plus the oracle's) also solved full-dimension in FP64 for comparison")
@@ -166,7 +167,8 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream(dev)
 
     def step(inputs, G_out, A_out, keep=False):
-        ctx = Context(inputs, tol=args.solve_tol, precision=args.precision, stream=stream.cuda_stream)
+        ctx = Context(inputs, tol=args.solve_tol, precision=args.precision, stream=stream.cuda_stream,
+                      restart=args.restart)
         ctx.mor_build(seeds, eta, porb)
         ref = ctx.mor_refine(W["wmin"], W["wmax"], args.ngrid, args.mor_tol, args.m_max)
         ctx.mor_eval(omega_host, G=G_out, A=A_out)
@@ -283,7 +285,8 @@ def run_ours(args, rank, world):
         "dtype": f"c128 (f64 residuals, {args.precision} tensor-core inner sigma)", "data": "synthetic",
         "config": {"workload": args.workload, "o": o, "v": v, "D": inp.dim, "n_omega": nw, "n_p": o, "n_q": o,
                    "eta": eta, "window_ha": [W["wmin"], W["wmax"]], "seeds": args.seeds, "mor_tol": args.mor_tol,
-                   "solve_tol": args.solve_tol, "model_order": info["m"], "sampled_freqs": len(info["sampled"]),
+                   "solve_tol": args.solve_tol, "restart": args.restart, "model_order": info["m"],
+                   "sampled_freqs": len(info["sampled"]),
                    "arnoldi_steps": info["arnoldi_steps"], "columns_solved": info["columns"],
                    "l2": "working set (operators >= 0.5 GB, Krylov bases) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
