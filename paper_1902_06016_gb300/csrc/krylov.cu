@@ -101,118 +101,118 @@ __global__ void __launch_bounds__(256, 2) multidot_kernel(const VT* __restrict__
   md_reduce<VT, NV, R>(ax, ay, nv, c, nb, partial, red);
 }
 
-// Fused CGS sweep: w <- w - sum_i V_i h_i (h = pass-1 coefficients), then partial sums of the
-// pass-2 coefficients conj(V_i) w over the chunk (same layout as multidot_kernel's partials).
-// Thread (x, y) walks rows y, y + MD_TY, ... of column x: it updates the row and adds conj(V_i) w'
-// into its own shared-memory accumulators acc[y][i][x] (no synchronisation inside the loop, no
-// per-thread accumulator arrays), which are summed over y at the end.
-template <typename VT, int NV>
-__global__ void __launch_bounds__(256, 3) update_dot_kernel(const VT* __restrict__ V, long long vstride, int nv,
+// Fused CGS sweeps over a chunk of rows: w <- w - sum_i V_i h_i, then either (DOT) partial sums of
+// the next coefficients conj(V_i) w (multidot_kernel's partial layout) or (!DOT) partial sums of |w|^2
+// (layout [chunk][c]). The thread rows form MdGroups<NV>'s IG groups; group g loads its NPG basis
+// vectors of a row once into registers, forms its share of sum_i V_i h_i, and the shares are added
+// through shared memory (double-buffered, one barrier per step), after which every group holds the
+// updated w and, for DOT, accumulates its own coefficients from the registers it already holds.
+// Group 0 writes w. Each step covers CU_U rows per group so that more loads are in flight.
+constexpr int CU_U = 2;
+template <typename VT, int NV, bool DOT>
+__global__ void __launch_bounds__(256, 2) cgs_update_kernel(const VT* __restrict__ V, long long vstride, int nv,
                                                             VT* __restrict__ W, long long D, int nb,
                                                             long long rows_per_chunk, const cplx* __restrict__ h,
                                                             int hld, cplx* __restrict__ partial) {
   using R = typename RealOf<VT>::type;
-  extern __shared__ __align__(16) unsigned char ud_smem[];
-  VT* acc = reinterpret_cast<VT*>(ud_smem);         // [MD_TY][NV][MD_TX]
-  VT* hs = acc + MD_TY * NV * MD_TX;                // [NV][MD_TX] coefficients
-  const int x = threadIdx.x, y = threadIdx.y;
-  const int c = blockIdx.x * MD_TX + x;
+  using G = MdGroups<NV>;
+  constexpr int NPG = G::NPG, RPG = G::RPG, IG = G::IG;
+  __shared__ VT share[2][CU_U][MD_TY][MD_TX];
+  __shared__ cplx red[MD_TY][MD_TX];
+  const int x = threadIdx.x, c = blockIdx.x * MD_TX + x;
+  const int g = threadIdx.y / RPG, yr = threadIdx.y % RPG;
+  const int i0 = g * NPG, ng = nv - i0;   // vectors of this group present (may be <= 0)
   const long long r0 = blockIdx.y * rows_per_chunk;
   const long long r1 = min(D, r0 + rows_per_chunk);
-  for (int i = y; i < NV; i += MD_TY) {
-    VT v;
-    v.x = (c < nb && i < nv) ? (R)h[(long long)c * hld + i].x : R(0);
-    v.y = (c < nb && i < nv) ? (R)h[(long long)c * hld + i].y : R(0);
-    hs[i * MD_TX + x] = v;
-  }
-  VT* my = acc + (long long)y * NV * MD_TX + x;     // acc[y][i][x] at my[i * MD_TX]
+  const VT* Vg = V + (long long)i0 * vstride;
+  VT hv[NPG];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) { VT z; z.x = R(0); z.y = R(0); my[i * MD_TX] = z; }
-  __syncthreads();
-  if (c < nb) {
-    for (long long nu = r0 + y; nu < r1; nu += MD_TY) {
-      VT w = W[nu * nb + c];
-#pragma unroll 8
-      for (int i = 0; i < nv; ++i) {
-        const VT hv = hs[i * MD_TX + x];
-        const VT va = V[i * vstride + nu * nb + c];
-        w.x -= va.x * hv.x - va.y * hv.y;
-        w.y -= va.x * hv.y + va.y * hv.x;
+  for (int li = 0; li < NPG; ++li) {
+    const bool on = c < nb && li < ng;
+    hv[li].x = on ? (R)h[(long long)c * hld + i0 + li].x : R(0);
+    hv[li].y = on ? (R)h[(long long)c * hld + i0 + li].y : R(0);
+  }
+  R ax[NPG], ay[NPG];
+#pragma unroll
+  for (int li = 0; li < NPG; ++li) { ax[li] = R(0); ay[li] = R(0); }
+  R nrm = R(0);
+  int buf = 0;
+  // the trip count is the same for every thread of the block (barriers inside)
+  for (long long base = r0; base < r1; base += (long long)CU_U * RPG, buf ^= 1) {
+    VT v[CU_U][NPG], w[CU_U];
+    bool ok[CU_U];
+#pragma unroll
+    for (int u = 0; u < CU_U; ++u) {
+      const long long nu = base + u * RPG + yr;
+      ok[u] = c < nb && nu < r1;
+      w[u].x = R(0); w[u].y = R(0);
+      if (ok[u]) w[u] = W[nu * nb + c];
+#pragma unroll
+      for (int li = 0; li < NPG; ++li) {
+        v[u][li].x = R(0); v[u][li].y = R(0);
+        if (ok[u] && li < ng) v[u][li] = Vg[li * vstride + nu * nb + c];
       }
-      W[nu * nb + c] = w;
-      // the basis entries are read again for the coefficient sums (L1/L2 hits: this thread loaded
-      // them just before), which keeps the registers low enough for three blocks per SM
-#pragma unroll 8
-      for (int i = 0; i < nv; ++i) {
-        const VT va = V[i * vstride + nu * nb + c];
-        VT a = my[i * MD_TX];
-        a.x += va.x * w.x + va.y * w.y;
-        a.y += va.x * w.y - va.y * w.x;
-        my[i * MD_TX] = a;
+    }
+#pragma unroll
+    for (int u = 0; u < CU_U; ++u) {
+      VT s;
+      s.x = R(0); s.y = R(0);
+#pragma unroll
+      for (int li = 0; li < NPG; ++li) {
+        s.x += v[u][li].x * hv[li].x - v[u][li].y * hv[li].y;
+        s.y += v[u][li].x * hv[li].y + v[u][li].y * hv[li].x;
+      }
+      if constexpr (IG == 1) {
+        w[u].x -= s.x; w[u].y -= s.y;
+      } else {
+        share[buf][u][threadIdx.y][x] = s;
+      }
+    }
+    if constexpr (IG > 1) {
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < CU_U; ++u)
+#pragma unroll
+        for (int gg = 0; gg < IG; ++gg) {
+          const VT s = share[buf][u][gg * RPG + yr][x];
+          w[u].x -= s.x; w[u].y -= s.y;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < CU_U; ++u) {
+      if (!ok[u]) continue;
+      if (g == 0) W[(base + u * RPG + yr) * nb + c] = w[u];
+      if constexpr (DOT) {
+#pragma unroll
+        for (int li = 0; li < NPG; ++li) {
+          ax[li] += v[u][li].x * w[u].x + v[u][li].y * w[u].y;
+          ay[li] += v[u][li].x * w[u].y - v[u][li].y * w[u].x;
+        }
+      } else {
+        nrm += w[u].x * w[u].x + w[u].y * w[u].y;
       }
     }
   }
-  __syncthreads();
-  for (int t = y * MD_TX + x; t < NV * MD_TX; t += MD_TX * MD_TY) {
-    const int i = t / MD_TX, xx = t % MD_TX, cc = blockIdx.x * MD_TX + xx;
-    if (i < nv && cc < nb) {
-      double sx = 0.0, sy = 0.0;
-      for (int yy = 0; yy < MD_TY; ++yy) {
-        const VT a = acc[((long long)yy * NV + i) * MD_TX + xx];
-        sx += (double)a.x;
-        sy += (double)a.y;
-      }
-      partial[((long long)blockIdx.y * nv + i) * nb + cc] = make_cuDoubleComplex(sx, sy);
+  if constexpr (DOT) {
+    md_reduce<VT, NV, R>(ax, ay, nv, c, nb, partial, red);
+  } else {
+    red[threadIdx.y][x] = make_cuDoubleComplex(g == 0 ? (double)nrm : 0.0, 0.0);
+    __syncthreads();
+    if (threadIdx.y == 0 && c < nb) {
+      double t = 0.0;
+      for (int k = 0; k < RPG; ++k) t += red[k][x].x;
+      partial[(long long)blockIdx.y * nb + c] = make_cuDoubleComplex(t, 0.0);
     }
   }
-}
-template <typename VT, int NV>
-constexpr size_t update_dot_smem() {
-  return sizeof(VT) * ((size_t)MD_TY * NV * MD_TX + (size_t)NV * MD_TX);
 }
 
-// Fused final sweep: w <- w - sum_i V_i h_i, with partial sums of |w|^2 per column (nv = 1 layout)
-template <typename VT, int NV>
-__global__ void __launch_bounds__(256, NV <= 16 ? 2 : 1) update_norm_kernel(const VT* __restrict__ V, long long vstride, int nv, VT* __restrict__ W,
-                                   long long D, int nb, long long rows_per_chunk, const cplx* __restrict__ h, int hld,
-                                   cplx* __restrict__ partial) {
-  using R = typename RealOf<VT>::type;
-  __shared__ cplx red[MD_TY][MD_TX];
-  __shared__ VT hs[NV][MD_TX];
-  const int c = blockIdx.x * MD_TX + threadIdx.x;
-  const long long r0 = blockIdx.y * rows_per_chunk;
-  const long long r1 = min(D, r0 + rows_per_chunk);
-  for (int i = threadIdx.y; i < NV; i += MD_TY) {
-    VT v;
-    v.x = (c < nb && i < nv) ? (R)h[(long long)c * hld + i].x : R(0);
-    v.y = (c < nb && i < nv) ? (R)h[(long long)c * hld + i].y : R(0);
-    hs[i][threadIdx.x] = v;
-  }
-  __syncthreads();
-  R acc = R(0);
-  if (c < nb) {
-    for (long long nu = r0 + threadIdx.y; nu < r1; nu += MD_TY) {
-      VT w = W[nu * nb + c];
-#pragma unroll
-      for (int i = 0; i < NV; ++i) {
-        if (i < nv) {
-          const VT vv = V[i * vstride + nu * nb + c];
-          const VT hv = hs[i][threadIdx.x];
-          w.x -= vv.x * hv.x - vv.y * hv.y;
-          w.y -= vv.x * hv.y + vv.y * hv.x;
-        }
-      }
-      W[nu * nb + c] = w;
-      acc += w.x * w.x + w.y * w.y;
-    }
-  }
-  red[threadIdx.y][threadIdx.x] = make_cuDoubleComplex((double)acc, 0.0);
-  __syncthreads();
-  if (threadIdx.y == 0 && c < nb) {
-    double s = 0.0;
-    for (int k = 0; k < MD_TY; ++k) s += red[k][threadIdx.x].x;
-    partial[(long long)blockIdx.y * nb + c] = make_cuDoubleComplex(s, 0.0);
-  }
+// rows per chunk of the CGS sweeps: at least 256 chunks and two waves of blocks (two resident blocks
+// per SM), with the chunk count trimmed so that the blocks fill their last wave
+long long cgs_rows(long long D, int nb) {
+  const long long gx = (nb + MD_TX - 1) / MD_TX, slots = 152LL * 2;
+  long long nchunk = std::max<long long>(256, 2 * slots / gx);
+  nchunk = std::max<long long>(1, (nchunk * gx + slots - 1) / slots * slots / gx);
+  return std::max<long long>(64, (D + nchunk - 1) / nchunk);
 }
 
 // h[c*hld + hoff + i] (+)= sum_chunk partial[chunk][i][c]
@@ -472,7 +472,7 @@ static void multidot(const VT* V, long long vstride, int nv, const VT* W, long l
                      int hoff, bool accumulate, DBuf<cplx>& partial, cudaStream_t s) {
   for (int i0 = 0; i0 < nv; i0 += MD_MAXV) {
     int n = std::min(MD_MAXV, nv - i0);
-    const long long rows = std::max<long long>(256, (D + 255) / 256);
+    const long long rows = cgs_rows(D, nb);
     const int nchunk = (int)((D + rows - 1) / rows);
     partial.alloc((long long)nchunk * n * nb);
     dim3 grid((nb + MD_TX - 1) / MD_TX, nchunk);
@@ -539,9 +539,10 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
   shw.alloc(nb0);
   flag.alloc(1);
   {  // chunk partial sums of the Gram-Schmidt sweeps and norms, at their largest (no regrowth per step)
-    const long long rows_md = std::max<long long>(256, (D + 255) / 256), rows_cn = std::max<long long>(256, (D + 511) / 512);
-    const long long nch = std::max((D + rows_md - 1) / rows_md * (k + 1), (D + rows_cn - 1) / rows_cn);
-    partial.alloc(nch * nb0);
+    const long long rows_cn = std::max<long long>(256, (D + 511) / 512);
+    long long md = 0;   // the chunk count of the sweeps depends on the batch width
+    for (int b = 1; b <= nb0; ++b) md = std::max(md, (D + cgs_rows(D, b) - 1) / cgs_rows(D, b) * b);
+    partial.alloc(std::max(md * (k + 1), (D + rows_cn - 1) / rows_cn * nb0));
   }
   GFCC_CUDA(cudaMemcpyAsync(Bw.p, Bin, sizeof(cplx) * D * nb0, cudaMemcpyDeviceToDevice, s));
   GFCC_CUDA(cudaMemcpyAsync(shw.p, shifts_dev, sizeof(cplx) * nb0, cudaMemcpyDeviceToDevice, s));
@@ -688,7 +689,7 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
           // algorithmic HBM bytes of the three sweeps: V read three times, w read three times and
           // written twice
           ProfScope pcgs(PROF_KRYLOV_CGS, (3.0 * nv + 5.0) * (double)D * nb * sizeof(VT), s);
-          const long long rows = std::max<long long>(256, (D + 255) / 256);
+          const long long rows = cgs_rows(D, nb);
           const int nchunk = (int)((D + rows - 1) / rows);
           dim3 grid((nb + MD_TX - 1) / MD_TX, nchunk);
           const double vbytes = (double)D * nb * sizeof(VT);   // one basis vector of the batch
@@ -704,16 +705,8 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
           {
             ProfScope pk(small ? PROF_CGS_SMALL_NB : PROF_CGS_UPDATE_DOT, (nv + 2.0) * vbytes, s);
             with_nv(nv, [&](auto NVc) {
-              constexpr int NVv = decltype(NVc)::value;
-              constexpr size_t smem = update_dot_smem<VT, NVv>();
-              static bool attr = false;   // per instantiation, once per process
-              if (!attr) {
-                GFCC_CUDA(cudaFuncSetAttribute(update_dot_kernel<VT, NVv>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem));
-                attr = true;
-              }
-              update_dot_kernel<VT, NVv><<<grid, dim3(MD_TX, MD_TY), smem, s>>>(V.p, vstride, nv, Ww.p, D, nb, rows,
-                                                                                hb.p, k + 1, partial.p);
+              cgs_update_kernel<VT, decltype(NVc)::value, true><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(
+                  V.p, vstride, nv, Ww.p, D, nb, rows, hb.p, k + 1, partial.p);
             });
             GFCC_LAUNCH_CHECK();
           }
@@ -725,9 +718,8 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
           {
             ProfScope pk(small ? PROF_CGS_SMALL_NB : PROF_CGS_UPDATE_NORM, (nv + 2.0) * vbytes, s);
             with_nv(nv, [&](auto NVc) {
-              update_norm_kernel<VT, decltype(NVc)::value><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(V.p, vstride, nv, Ww.p,
-                                                                                              D, nb, rows, hb.p, k + 1,
-                                                                                              partial.p);
+              cgs_update_kernel<VT, decltype(NVc)::value, false><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(
+                  V.p, vstride, nv, Ww.p, D, nb, rows, hb.p, k + 1, partial.p);
             });
             GFCC_LAUNCH_CHECK();
           }

@@ -343,8 +343,11 @@ void regrow_cm(DBuf<cplx>& b, int old_ld, int new_ld, int alloc_cols, int nrows,
 // small size goes to the exact-slice tensor-core GEMM (7 slices, 48 bits per row). Fewer slices are
 // not enough: the residual basis resolves the solver-residual directions of Z = M S, about 1e-8 of
 // the columns' norms, and 41-bit products perturb them enough to spoil the refinement estimates.
-void fp64_accurate_zgemm(const ZGemmDesc& g, cudaStream_t s) {
-  if ((double)g.M * (double)g.N * (double)g.K >= (double)(1 << 22) && g.batch == 1) zgemm_oz(g, 7, s);
+// The coefficients of the first Gram-Schmidt pass are the exception (ns = 5, 34 bits): the reconstruction
+// y = Q (C1 + C2) + y'' holds for whatever C1 the first update subtracts, and the second pass, whose
+// coefficients and both updates keep 7 slices, removes what a less accurate C1 leaves along Q.
+void fp64_accurate_zgemm(const ZGemmDesc& g, cudaStream_t s, int ns = 7) {
+  if ((double)g.M * (double)g.N * (double)g.K >= (double)(1 << 22) && g.batch == 1) zgemm_oz(g, ns, s);
   else zgemm(g, s);
 }
 
@@ -693,7 +696,7 @@ std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cp
       g.work = zgemm_work(c);
       {
         ProfScope pg(PROF_ORTHO_GRAM, 0.0, s);
-        fp64_accurate_zgemm(g, s);
+        fp64_accurate_zgemm(g, s, pass == 0 ? 5 : 7);
       }
       ZGemmDesc u;
       u.M = (int)D; u.N = ncols; u.K = np_;
