@@ -162,9 +162,106 @@ __global__ void splitk_reduce_kernel(const T* __restrict__ P, int ksplit, int M,
   }
 }
 
+// Matrix-vector shapes (M == 1; N == 1 is mapped onto it by exchanging the operands): out[n] =
+// sum_k opA[k] opB[k][n] over this block's K range, one HBM pass over B instead of 64x64 tiles that
+// would be 1/64 occupied. Threads run along whichever B index is contiguous: along n (one thread per
+// n) or along k (one warp per n, shuffle-reduced). With ksplit > 1 the sums are partials [z][n].
+template <typename T>
+__device__ __forceinline__ void gemv_store(const Args<T>& g, long long bz, int split, int n, T acc) {
+  if (g.ksplit > 1) {
+    g.C[(bz * g.ksplit + split) * (long long)g.N + n] = acc;
+    return;
+  }
+  T* cp = g.C + bz * g.bsc + n * g.scn;
+  T v = scal_mul(g.alpha, acc);
+  if (!is_zero(g.beta)) v = scal_add(v, scal_mul(g.beta, *cp));
+  *cp = v;
+}
+template <typename T>
+__global__ void __launch_bounds__(256) gemv_n_kernel(Args<T> g) {
+  const int n = blockIdx.x * 256 + threadIdx.x;
+  const long long bz = blockIdx.z / g.ksplit;
+  const int split = blockIdx.z % g.ksplit;
+  const int kbeg = split * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
+  if (n >= g.N) return;
+  const T* A = g.A + bz * g.bsa;
+  const T* B = g.B + bz * g.bsb + n * g.sbn;
+  T acc = Ops<T>::zero();
+#pragma unroll 4
+  for (int k = kbeg; k < kend; ++k)
+    acc = Ops<T>::fma(Ops<T>::cj(A[k * g.sak], g.conjA), Ops<T>::cj(B[k * g.sbk], g.conjB), acc);
+  gemv_store(g, bz, split, n, acc);
+}
+__device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ cplx shfl_down(cplx v, int o) {
+  return make_cuDoubleComplex(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o));
+}
+template <typename T>
+__global__ void __launch_bounds__(256) gemv_k_kernel(Args<T> g) {
+  const int n = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const long long bz = blockIdx.z / g.ksplit;
+  const int split = blockIdx.z % g.ksplit;
+  const int kbeg = split * g.kchunk, kend = min(g.K, kbeg + g.kchunk);
+  if (n >= g.N) return;   // whole warps leave together
+  const T* A = g.A + bz * g.bsa;
+  const T* B = g.B + bz * g.bsb + n * g.sbn;
+  T acc = Ops<T>::zero();
+  for (int k = kbeg + lane; k < kend; k += 32)
+    acc = Ops<T>::fma(Ops<T>::cj(A[k * g.sak], g.conjA), Ops<T>::cj(B[k * g.sbk], g.conjB), acc);
+  for (int o = 16; o > 0; o >>= 1) acc = scal_add(acc, shfl_down(acc, o));
+  if (lane == 0) gemv_store(g, bz, split, n, acc);
+}
+
+template <typename T>
+void launch_gemv(Args<T> a, int batch, cudaStream_t s) {
+  ProfScope prof(PROF_F64_GEMM, (sizeof(T) == 8 ? 2.0 : 8.0) * (double)a.M * (double)a.N * (double)a.K * batch, s);
+  if (a.M != 1) {   // N == 1: C^T = op(B)^T op(A)^T, a row vector times a matrix
+    std::swap(a.M, a.N);
+    std::swap(a.A, a.B);
+    std::swap(a.sam, a.sbn);
+    std::swap(a.sak, a.sbk);
+    std::swap(a.bsa, a.bsb);
+    std::swap(a.conjA, a.conjB);
+    std::swap(a.scm, a.scn);
+  }
+  const bool along_n = a.sbn <= a.sbk;
+  const long long bx = along_n ? (a.N + 255) / 256 : (a.N + 7) / 8;
+  GFCC_CHECK(bx <= 0x7fffffffLL, GFCC_ERR_ARG, "gemv N too large");
+  const long long per_split = bx * batch;
+  int ksplit = (int)std::max<long long>(1, std::min<long long>((4 * 152 + per_split - 1) / per_split, a.K / 64));
+  ksplit = std::max(1, std::min(ksplit, 65535 / std::max(batch, 1)));
+  const int kchunk = (a.K + ksplit - 1) / ksplit;
+  ksplit = (a.K + kchunk - 1) / kchunk;
+  GFCC_CHECK((long long)batch * ksplit <= 65535, GFCC_ERR_ARG, "gemv batch too large");
+  const dim3 grid((unsigned)bx, 1, (unsigned)(batch * ksplit));
+  Args<T> p = a;
+  p.ksplit = ksplit;
+  p.kchunk = kchunk;
+  DBuf<T> part;
+  if (ksplit > 1) {
+    part.alloc((long long)a.N * ksplit * batch);
+    p.C = part.p;
+  }
+  if (along_n) gemv_n_kernel<T><<<grid, 256, 0, s>>>(p);
+  else gemv_k_kernel<T><<<grid, 256, 0, s>>>(p);
+  GFCC_LAUNCH_CHECK();
+  if (ksplit == 1) return;
+  const long long total = (long long)a.N * batch;
+  const int rgrid = (int)std::min<long long>((total + 255) / 256, 152LL * 32);
+  // partials [batch][ksplit][1][N]; C row 0, column n at C + n scn
+  splitk_reduce_kernel<T><<<rgrid, 256, 0, s>>>(part.p, ksplit, 1, a.N, batch, a.C, a.scm, a.scn, a.bsc, a.alpha,
+                                                a.beta);
+  GFCC_LAUNCH_CHECK();
+  GFCC_CUDA(cudaStreamSynchronize(s));   // the partial buffer is released on return
+}
+
 template <typename T>
 void launch(Args<T> a, int batch, cudaStream_t s) {
   if (a.M <= 0 || a.N <= 0 || batch <= 0) return;
+  if (a.M == 1 || a.N == 1) {
+    launch_gemv(a, batch, s);
+    return;
+  }
   dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, batch);
   GFCC_CHECK(grid.y <= 65535, GFCC_ERR_ARG, "gemm M too large");
   constexpr int BK = sizeof(T) == 8 ? 16 : 8;   // 33 KB of static shared memory either way
