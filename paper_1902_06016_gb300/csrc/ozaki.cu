@@ -202,46 +202,156 @@ __global__ void __launch_bounds__(256) zslice_kernel(const cplx* __restrict__ Z,
   }
 }
 
-// acc[t] (+)= scale * sum_z part[z*stride + t]: the int32 split sums of one diagonal, added exactly
-// in 64-bit integers, then weighted and accumulated in FP64
-__global__ void accumulate_kernel(const int* __restrict__ part, int zs, long long stride, long long total,
-                                  double scale, int first, double* __restrict__ acc) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    long long sum = 0;
-    for (int z = 0; z < zs; ++z) sum += part[z * stride + t];
-    acc[t] = first ? scale * (double)sum : acc[t] + scale * (double)sum;
+// Output of an exact-slice product: real, out[m ldo + n] = beta out + P[m][n]; or complex (the real
+// columns n and N + n of P hold the real and imaginary parts), C(m, n) = alpha P(m, n) + beta C(m, n).
+struct OzOut {
+  bool complex_out = false;
+  double* out = nullptr;
+  long long ldo = 0;
+  double beta = 0.0;
+  cplx* C = nullptr;
+  long long scm = 0, scn = 0;
+  cplx alpha = {1.0, 0.0}, cbeta = {0.0, 0.0};
+};
+
+// sum over the zs int32 split sums p[z stride], exactly in 64-bit integers; WARP: the lanes share the
+// splits and every lane returns the total (integer sums do not depend on the grouping)
+template <bool WARP>
+__device__ __forceinline__ long long split_sum(const int* __restrict__ p, int zs, long long stride, int lane) {
+  long long sum = 0;
+  if constexpr (WARP) {
+    for (int z = lane; z < zs; z += 32) sum += p[(long long)z * stride];
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  } else {
+    (void)lane;
+    for (int z = 0; z < zs; ++z) sum += p[(long long)z * stride];
   }
+  return sum;
 }
 
-// out[m*ldo + n] = beta * out + 2^(ea[m] + eb[n] - 12) * acc[m*N + n]
-__global__ void finalize_kernel(const double* __restrict__ acc, const int* __restrict__ ea, const int* __restrict__ eb,
-                                long long M, long long N, double* __restrict__ out, long long ldo, double beta) {
-  const long long total = M * N;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long m = t / N, n = t % N;
-    double v = ldexp(acc[t], ea[m] + eb[n] - 12);
-    double* p = out + m * ldo + n;
-    *p = (beta == 0.0) ? v : beta * (*p) + v;
+// One diagonal of a column chunk (Np real columns): its split sums, weighted by scale = 2^(-7d), are
+// added to the FP64 accumulator acc[m][n'] (MODE 0; first: acc is set), or, on the last diagonal, added
+// to acc, scaled by 2^(ea[m] + eb[n'] - 12) and written to a real (MODE 1) or complex (MODE 2) output.
+// One thread per element, or (WARP) one warp for outputs too small to occupy the GPU that have many K
+// splits. Only the last diagonal needs the (m, n) of an element; 32-bit division when it fits.
+template <typename I>
+__device__ __forceinline__ void divmod(long long t, long long N, long long& m, long long& n) {
+  m = (long long)((I)t / (I)N);
+  n = t - m * N;
+}
+template <bool WARP, int MODE, typename I>
+__global__ void __launch_bounds__(256) oz_accumulate_kernel(const int* __restrict__ part, int zs, long long M,
+                                                            long long Np, double scale, int first,
+                                                            double* __restrict__ acc, const int* __restrict__ ea,
+                                                            const int* __restrict__ eb, OzOut o) {
+  const long long stride = M * Np;
+  const long long total = MODE == 2 ? M * (Np / 2) : stride;
+  const int lane = threadIdx.x & 31;
+  const bool writer = !WARP || lane == 0;
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nthreads = (long long)gridDim.x * blockDim.x;
+  const long long start = WARP ? gid >> 5 : gid, step = WARP ? nthreads >> 5 : nthreads;
+  for (long long t = start; t < total; t += step) {
+    if constexpr (MODE == 0) {
+      double a = scale * (double)split_sum<WARP>(part + t, zs, stride, lane);
+      if (!first) a = acc[t] + a;
+      if (writer) acc[t] = a;
+    } else if constexpr (MODE == 1) {
+      double a = scale * (double)split_sum<WARP>(part + t, zs, stride, lane);
+      if (!first) a = acc[t] + a;
+      long long m, n;
+      divmod<I>(t, Np, m, n);
+      const double v = ldexp(a, ea[m] + eb[n] - 12);
+      if (writer) {
+        double* p = o.out + m * o.ldo + n;
+        *p = (o.beta == 0.0) ? v : o.beta * (*p) + v;
+      }
+    } else {
+      const long long N = Np / 2;
+      long long m, n;
+      divmod<I>(t, N, m, n);
+      const long long tr = m * Np + n, ti = tr + N;
+      double ar = scale * (double)split_sum<WARP>(part + tr, zs, stride, lane);
+      double ai = scale * (double)split_sum<WARP>(part + ti, zs, stride, lane);
+      if (!first) {
+        ar = acc[tr] + ar;
+        ai = acc[ti] + ai;
+      }
+      const double re = ldexp(ar, ea[m] + eb[n] - 12), im = ldexp(ai, ea[m] + eb[N + n] - 12);
+      if (writer) {
+        cplx* p = o.C + m * o.scm + n * o.scn;
+        cplx r = cuCmul(o.alpha, make_cuDoubleComplex(re, im));
+        if (o.cbeta.x != 0.0 || o.cbeta.y != 0.0) r = cuCadd(r, cuCmul(o.cbeta, *p));
+        *p = r;
+      }
+    }
   }
 }
-
-// C(m, n) = alpha (T[m][n] + i T[m][N + n]) + beta C(m, n)
-__global__ void zscatter_kernel(const double* __restrict__ T, long long M, long long N, cplx* __restrict__ C,
-                                long long scm, long long scn, cplx alpha, cplx beta) {
-  const long long total = M * N;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const long long m = t / N, n = t % N;
-    const cplx v = make_cuDoubleComplex(T[m * 2 * N + n], T[m * 2 * N + N + n]);
-    cplx* p = C + m * scm + n * scn;
-    cplx r = cuCmul(alpha, v);
-    if (beta.x != 0.0 || beta.y != 0.0) r = cuCadd(r, cuCmul(beta, *p));
-    *p = r;
-  }
+template <bool WARP, int MODE>
+void launch_accumulate(bool small, int grid, cudaStream_t s, const int* part, int zs, long long M, long long Np,
+                       double scale, int first, double* acc, const int* ea, const int* eb, const OzOut& o) {
+  if (small)
+    oz_accumulate_kernel<WARP, MODE, unsigned><<<grid, 256, 0, s>>>(part, zs, M, Np, scale, first, acc, ea, eb, o);
+  else
+    oz_accumulate_kernel<WARP, MODE, unsigned long long><<<grid, 256, 0, s>>>(part, zs, M, Np, scale, first, acc, ea,
+                                                                             eb, o);
 }
 
+}  // namespace
+
+namespace {
+// Exact product of sliced rows into o. The diagonal GEMMs run one at a time, each followed by its
+// accumulation, so that a diagonal's split sums are read back from L2 where they fit; the real
+// columns go in chunks that bound the split-sum memory (a complex output is one chunk, its real and
+// imaginary columns being finalised together).
+void oz_run(const SlicedRows& A, const SlicedRows& B, long long M, long long Np, const OzOut& o, OzWork& w,
+            cudaStream_t s) {
+  const int ns = A.ns;
+  const long long kp = A.kp, ld = (long long)ns * kp;
+  const int max_splits = tc_exact_splits(M, Np, (long long)ns * kp);
+  const long long slab_budget = 2LL << 30;   // bytes of int32 split sums at a time
+  long long nc = std::max<long long>(1, slab_budget / (4LL * M * max_splits));
+  nc = std::min<long long>(Np, std::max<long long>(256, nc / 256 * 256));
+  if (o.complex_out) nc = Np;
+  w.islabs.alloc((size_t)max_splits * M * nc);
+  w.acc.alloc((size_t)M * nc);
+  if (w.err.n == 0) { w.err.alloc(1); w.err.zero(s); }
+  const __nv_bfloat16* As = reinterpret_cast<const __nv_bfloat16*>(A.slices.p);
+  const __nv_bfloat16* Bs = reinterpret_cast<const __nv_bfloat16*>(B.slices.p);
+  for (long long n0 = 0; n0 < Np; n0 += nc) {
+    const long long nn = std::min(nc, Np - n0);
+    OzOut oc = o;
+    if (!o.complex_out) oc.out = o.out + n0;
+    for (int d = 0; d < ns; ++d) {
+      // diagonal d: A slices 0..d against B slices d..0, concatenated along K
+      const long long kd = (long long)(d + 1) * kp;
+      const int zs = std::min(tc_exact_splits(M, nn, kd), max_splits);
+      TcOperand a(As, M, kd, ld);
+      TcOperand b(Bs + n0 * ld + (long long)(ns - 1 - d) * kp, nn, kd, ld);
+      const int zeff = tc_gemm_exact(a, b, w.islabs.p, nn, M, nn, zs, M * nn, w.err.p, s, PROF_TC_SLICE);
+      const double scale = ldexp(1.0, -7 * d);
+      const int first = d == 0 ? 1 : 0;
+      const int mode = d < ns - 1 ? 0 : (o.complex_out ? 2 : 1);
+      const long long elements = mode == 2 ? M * (nn / 2) : M * nn;
+      const bool warp = elements < 152LL * 256 && zeff > 8;
+      const int grid = warp ? (int)std::min<long long>(std::max<long long>((elements * 32 + 255) / 256, 1), 152LL * 32)
+                            : grid_for(elements);
+      const bool small = M * nn < (1LL << 32);
+      const int* eb = B.expo.p + n0;
+      if (mode == 0) {
+        if (warp) launch_accumulate<true, 0>(small, grid, s, w.islabs.p, zeff, M, nn, scale, first, w.acc.p, A.expo.p, eb, oc);
+        else launch_accumulate<false, 0>(small, grid, s, w.islabs.p, zeff, M, nn, scale, first, w.acc.p, A.expo.p, eb, oc);
+      } else if (mode == 1) {
+        if (warp) launch_accumulate<true, 1>(small, grid, s, w.islabs.p, zeff, M, nn, scale, first, w.acc.p, A.expo.p, eb, oc);
+        else launch_accumulate<false, 1>(small, grid, s, w.islabs.p, zeff, M, nn, scale, first, w.acc.p, A.expo.p, eb, oc);
+      } else {
+        if (warp) launch_accumulate<true, 2>(small, grid, s, w.islabs.p, zeff, M, nn, scale, first, w.acc.p, A.expo.p, eb, oc);
+        else launch_accumulate<false, 2>(small, grid, s, w.islabs.p, zeff, M, nn, scale, first, w.acc.p, A.expo.p, eb, oc);
+      }
+      GFCC_LAUNCH_CHECK();
+    }
+  }
+}
 }  // namespace
 
 double oz_min_macs() {
@@ -254,7 +364,6 @@ namespace {
 struct ZWork {          // buffers of zgemm_oz, kept between calls (grow-only)
   SlicedRows sa, sb;
   DBuf<unsigned long long> mxa, mxb;
-  DBuf<double> T;
   OzWork w;
 };
 }  // namespace
@@ -309,12 +418,15 @@ void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s) {
         reinterpret_cast<__nv_bfloat16*>(sb.slices.p), sb.expo.p);
     GFCC_LAUNCH_CHECK();
   }
-  DBuf<double>& T = z.T;
-  T.alloc(M * 2 * N);
+  OzOut o;
+  o.complex_out = true;
+  o.C = g.C;
+  o.scm = g.scm;
+  o.scn = g.scn;
+  o.alpha = g.alpha;
+  o.cbeta = g.beta;
   OzWork& w = z.w;
-  oz_gemm(sa, sb, M, 2 * N, T.p, 2 * N, 0.0, w, s);
-  zscatter_kernel<<<grid_for(M * N), 256, 0, s>>>(T.p, M, N, g.C, g.scm, g.scn, g.alpha, g.beta);
-  GFCC_LAUNCH_CHECK();
+  oz_run(sa, sb, M, 2 * N, o, w, s);
   if (g.work) return;   // the caller checks the workspace's error flag (zgemm_work_check) later
   int herr = 0;
   GFCC_CUDA(cudaMemcpyAsync(&herr, w.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -367,34 +479,11 @@ void oz_gemm(const SlicedRows& A, const SlicedRows& B, long long M, long long N,
   GFCC_CHECK(!A.reversed && B.reversed && A.kp == B.kp && A.ns == B.ns, GFCC_ERR_ARG,
              "oz_gemm: operand slicing mismatch");
   GFCC_CHECK(A.rows >= M && B.rows >= N, GFCC_ERR_ARG, "oz_gemm: operand rows");
-  const int ns = A.ns;
-  const long long kp = A.kp, ld = (long long)ns * kp;
-  // int32 split sums of the largest diagonal, with N processed in column chunks to bound memory
-  const int max_splits = tc_exact_splits(M, N, (long long)ns * kp);
-  const long long slab_budget = 2LL << 30;   // bytes of int32 split sums at a time
-  long long nc = std::max<long long>(1, slab_budget / (4LL * M * max_splits));
-  nc = std::min<long long>(N, std::max<long long>(256, nc / 256 * 256));
-  w.islabs.alloc((size_t)max_splits * M * nc);
-  w.acc.alloc((size_t)M * nc);
-  if (w.err.n == 0) { w.err.alloc(1); w.err.zero(s); }
-  const __nv_bfloat16* As = reinterpret_cast<const __nv_bfloat16*>(A.slices.p);
-  const __nv_bfloat16* Bs = reinterpret_cast<const __nv_bfloat16*>(B.slices.p);
-  for (long long n0 = 0; n0 < N; n0 += nc) {
-    const long long nn = std::min(nc, N - n0);
-    for (int d = 0; d < ns; ++d) {
-      // diagonal d: A slices 0..d against B slices d..0, concatenated along K
-      const long long kd = (long long)(d + 1) * kp;
-      const int zs = std::min(tc_exact_splits(M, nn, kd), max_splits);
-      TcOperand a(As, M, kd, ld);
-      TcOperand b(Bs + (long long)n0 * ld + (long long)(ns - 1 - d) * kp, nn, kd, ld);
-      const int zeff = tc_gemm_exact(a, b, w.islabs.p, nn, M, nn, zs, M * nn, w.err.p, s, PROF_TC_SLICE);
-      accumulate_kernel<<<grid_for(M * nn), 256, 0, s>>>(w.islabs.p, zeff, M * nn, M * nn, ldexp(1.0, -7 * d),
-                                                          d == 0 ? 1 : 0, w.acc.p);
-      GFCC_LAUNCH_CHECK();
-    }
-    finalize_kernel<<<grid_for(M * nn), 256, 0, s>>>(w.acc.p, A.expo.p, B.expo.p + n0, M, nn, out + n0, ldo, beta);
-    GFCC_LAUNCH_CHECK();
-  }
+  OzOut o;
+  o.out = out;
+  o.ldo = ldo;
+  o.beta = beta;
+  oz_run(A, B, M, N, o, w, s);
 }
 
 }  // namespace gfcc

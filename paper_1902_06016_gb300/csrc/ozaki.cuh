@@ -41,8 +41,8 @@ void oz_slice_into(const double* X, long long ldx, long long nrows, long long K,
 // out[m][n] = beta * out[m][n] + sum_k A[m][k] B[n][k] for m < M, n < N (out row stride ldo), with
 // A = sliced rows (normal order) and B = sliced rows (reversed order), same kp.
 struct OzWork {
-  DBuf<int> islabs;
-  DBuf<double> acc;
+  DBuf<int> islabs;   // int32 split sums of one diagonal of a column chunk
+  DBuf<double> acc;   // FP64 sum of the diagonals so far
   DBuf<int> err;
 };
 void oz_gemm(const SlicedRows& A, const SlicedRows& B, long long M, long long N, double* out, long long ldo,
