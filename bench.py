@@ -208,7 +208,8 @@ def run_ours(args, rank, world):
                    7: "mor_eval", 8: "hbar_build", 9: "mor_panel_columns", 10: "mor_residual_basis",
                    12: "exact_slice_complex_gemms", 13: "exact_slicing", 19: "eval_hessenberg_reduction",
                    20: "eval_shifted_solves", 21: "ortho_gram_products", 22: "ortho_updates",
-                   23: "ortho_panel_cholqr"}
+                   23: "ortho_panel_cholqr", 24: "exact_slice_accumulate", 25: "lowprec_operand_prep",
+                   26: "lowprec_combine"}
     phases = {phase_names[k]: round(G.profile_read(k)[1], 1) for k in phase_names}
     cgs = G.profile_read(14)   # (launch groups, ms, algorithmic bytes) of the Arnoldi sweeps
     cgs_parts = {name: G.profile_read(k) for k, name in

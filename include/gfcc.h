@@ -236,8 +236,9 @@ long long gfcc_launch_count(void);
  * columns; 18 the three sweeps of batches of fewer than 32 columns (classes 14-18 count algorithmic
  * HBM bytes in the "flops" field); 19 Householder reductions of Hhat to Hessenberg form; 20 the
  * per-frequency shifted Hessenberg solves; 21, 22 the coefficient products and updates of the block
- * Gram-Schmidt passes; 23 the Cholesky QR of the panels. Events are recorded on the stream each region
- * is launched on. */
+ * Gram-Schmidt passes; 23 the Cholesky QR of the panels; 24 the accumulation and output passes of the
+ * exact-slice products; 25 the operand preparation and 26 the combine pass of the low-precision sigma.
+ * Events are recorded on the stream each region is launched on. */
 int gfcc_profile(int enable);
 
 /* Sum over the recorded launches of class cls: number of launches, device milliseconds (CUDA

@@ -66,7 +66,10 @@ enum ProfClass {
   PROF_ORTHO_GRAM = 21,       // block Gram-Schmidt coefficient products (basis^H block)
   PROF_ORTHO_UPDATE = 22,     // block Gram-Schmidt updates (block -= basis coefficients)
   PROF_ORTHO_CHOLQR = 23,     // Cholesky QR of the panels
-  PROF_NCLASS = 24
+  PROF_OZ_ACCUM = 24,         // accumulation of the exact-slice diagonals and the output pass (every use)
+  PROF_LP_PREP = 25,          // operand preparation of the low-precision sigma (K-major operands)
+  PROF_LP_COMBINE = 26,       // the combine pass of the low-precision sigma (up reduction, final sum)
+  PROF_NCLASS = 27
 };
 struct ProfScope {   // records CUDA events around one launch on stream s when profiling is on
   int cls;

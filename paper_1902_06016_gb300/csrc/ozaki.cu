@@ -224,7 +224,16 @@ __device__ __forceinline__ long long split_sum(const int* __restrict__ p, int zs
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   } else {
     (void)lane;
-    for (int z = 0; z < zs; ++z) sum += p[(long long)z * stride];
+    long long s1 = 0, s2 = 0, s3 = 0;   // four independent loads in flight
+    int z = 0;
+    for (; z + 4 <= zs; z += 4) {
+      sum += p[(long long)z * stride];
+      s1 += p[(long long)(z + 1) * stride];
+      s2 += p[(long long)(z + 2) * stride];
+      s3 += p[(long long)(z + 3) * stride];
+    }
+    for (; z < zs; ++z) sum += p[(long long)z * stride];
+    sum += s1 + s2 + s3;
   }
   return sum;
 }
@@ -287,6 +296,128 @@ __global__ void __launch_bounds__(256) oz_accumulate_kernel(const int* __restric
     }
   }
 }
+// All diagonals at once (their split sums held side by side: diagonal d at slabs + off[d], zs[d]
+// splits of stride M Np each), summed and written to the output in one pass (MODE 1 real, 2 complex).
+struct OzDiags {
+  long long off[OZ_SLICES_MAX];
+  int zs[OZ_SLICES_MAX];
+  double scale[OZ_SLICES_MAX];
+  int nd;
+};
+template <bool WARP>
+__device__ __forceinline__ double diag_total(const int* __restrict__ slabs, const OzDiags& dg, long long stride,
+                                             long long t, int lane) {
+  double a = 0.0;
+  for (int d = 0; d < dg.nd; ++d) {
+    const double v = dg.scale[d] * (double)split_sum<WARP>(slabs + dg.off[d] + t, dg.zs[d], stride, lane);
+    a = d == 0 ? v : a + v;
+  }
+  return a;
+}
+template <bool WARP, int MODE, typename I>
+__global__ void __launch_bounds__(256) oz_output_kernel(const int* __restrict__ slabs, OzDiags dg, long long M,
+                                                        long long Np, const int* __restrict__ ea,
+                                                        const int* __restrict__ eb, OzOut o) {
+  const long long stride = M * Np;
+  const long long total = MODE == 2 ? M * (Np / 2) : stride;
+  const int lane = threadIdx.x & 31;
+  const bool writer = !WARP || lane == 0;
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nthreads = (long long)gridDim.x * blockDim.x;
+  const long long start = WARP ? gid >> 5 : gid, step = WARP ? nthreads >> 5 : nthreads;
+  for (long long t = start; t < total; t += step) {
+    if constexpr (MODE == 1) {
+      long long m, n;
+      divmod<I>(t, Np, m, n);
+      const double v = ldexp(diag_total<WARP>(slabs, dg, stride, t, lane), ea[m] + eb[n] - 12);
+      if (writer) {
+        double* p = o.out + m * o.ldo + n;
+        *p = (o.beta == 0.0) ? v : o.beta * (*p) + v;
+      }
+    } else {
+      const long long N = Np / 2;
+      long long m, n;
+      divmod<I>(t, N, m, n);
+      const long long tr = m * Np + n;
+      const double re = ldexp(diag_total<WARP>(slabs, dg, stride, tr, lane), ea[m] + eb[n] - 12);
+      const double im = ldexp(diag_total<WARP>(slabs, dg, stride, tr + N, lane), ea[m] + eb[N + n] - 12);
+      if (writer) {
+        cplx* p = o.C + m * o.scm + n * o.scn;
+        cplx r = cuCmul(o.alpha, make_cuDoubleComplex(re, im));
+        if (o.cbeta.x != 0.0 || o.cbeta.y != 0.0) r = cuCadd(r, cuCmul(o.cbeta, *p));
+        *p = r;
+      }
+    }
+  }
+}
+// The common case of one split per diagonal (a short K): the NS loads of an element are issued
+// together, so that each thread keeps NS (complex: 2 NS) independent loads in flight.
+template <int NS, int MODE, typename I>
+__global__ void __launch_bounds__(256) oz_output1_kernel(const int* __restrict__ slabs, OzDiags dg, long long M,
+                                                         long long Np, const int* __restrict__ ea,
+                                                         const int* __restrict__ eb, OzOut o) {
+  const long long stride = M * Np;
+  const long long total = MODE == 2 ? M * (Np / 2) : stride;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    if constexpr (MODE == 1) {
+      int v[NS];
+#pragma unroll
+      for (int d = 0; d < NS; ++d) v[d] = slabs[dg.off[d] + t];
+      double a = dg.scale[0] * (double)v[0];
+#pragma unroll
+      for (int d = 1; d < NS; ++d) a = a + dg.scale[d] * (double)v[d];
+      long long m, n;
+      divmod<I>(t, Np, m, n);
+      const double r = ldexp(a, ea[m] + eb[n] - 12);
+      double* p = o.out + m * o.ldo + n;
+      *p = (o.beta == 0.0) ? r : o.beta * (*p) + r;
+    } else {
+      const long long N = Np / 2;
+      long long m, n;
+      divmod<I>(t, N, m, n);
+      const long long tr = m * Np + n, ti = tr + N;
+      int vr[NS], vi[NS];
+#pragma unroll
+      for (int d = 0; d < NS; ++d) {
+        vr[d] = slabs[dg.off[d] + tr];
+        vi[d] = slabs[dg.off[d] + ti];
+      }
+      double ar = dg.scale[0] * (double)vr[0], ai = dg.scale[0] * (double)vi[0];
+#pragma unroll
+      for (int d = 1; d < NS; ++d) {
+        ar = ar + dg.scale[d] * (double)vr[d];
+        ai = ai + dg.scale[d] * (double)vi[d];
+      }
+      const double re = ldexp(ar, ea[m] + eb[n] - 12), im = ldexp(ai, ea[m] + eb[N + n] - 12);
+      cplx* p = o.C + m * o.scm + n * o.scn;
+      cplx r = cuCmul(o.alpha, make_cuDoubleComplex(re, im));
+      if (o.cbeta.x != 0.0 || o.cbeta.y != 0.0) r = cuCadd(r, cuCmul(o.cbeta, *p));
+      *p = r;
+    }
+  }
+}
+template <int MODE, typename I>
+void launch_output1(int ns, int grid, cudaStream_t s, const int* slabs, const OzDiags& dg, long long M, long long Np,
+                    const int* ea, const int* eb, const OzOut& o) {
+  switch (ns) {
+    case 2: oz_output1_kernel<2, MODE, I><<<grid, 256, 0, s>>>(slabs, dg, M, Np, ea, eb, o); break;
+    case 3: oz_output1_kernel<3, MODE, I><<<grid, 256, 0, s>>>(slabs, dg, M, Np, ea, eb, o); break;
+    case 4: oz_output1_kernel<4, MODE, I><<<grid, 256, 0, s>>>(slabs, dg, M, Np, ea, eb, o); break;
+    case 5: oz_output1_kernel<5, MODE, I><<<grid, 256, 0, s>>>(slabs, dg, M, Np, ea, eb, o); break;
+    case 6: oz_output1_kernel<6, MODE, I><<<grid, 256, 0, s>>>(slabs, dg, M, Np, ea, eb, o); break;
+    case 7: oz_output1_kernel<7, MODE, I><<<grid, 256, 0, s>>>(slabs, dg, M, Np, ea, eb, o); break;
+    default: oz_output1_kernel<8, MODE, I><<<grid, 256, 0, s>>>(slabs, dg, M, Np, ea, eb, o); break;
+  }
+}
+
+template <bool WARP, int MODE>
+void launch_output(bool small, int grid, cudaStream_t s, const int* slabs, const OzDiags& dg, long long M,
+                   long long Np, const int* ea, const int* eb, const OzOut& o) {
+  if (small) oz_output_kernel<WARP, MODE, unsigned><<<grid, 256, 0, s>>>(slabs, dg, M, Np, ea, eb, o);
+  else oz_output_kernel<WARP, MODE, unsigned long long><<<grid, 256, 0, s>>>(slabs, dg, M, Np, ea, eb, o);
+}
+
 template <bool WARP, int MODE>
 void launch_accumulate(bool small, int grid, cudaStream_t s, const int* part, int zs, long long M, long long Np,
                        double scale, int first, double* acc, const int* ea, const int* eb, const OzOut& o) {
@@ -300,15 +431,62 @@ void launch_accumulate(bool small, int grid, cudaStream_t s, const int* part, in
 }  // namespace
 
 namespace {
-// Exact product of sliced rows into o. The diagonal GEMMs run one at a time, each followed by its
-// accumulation, so that a diagonal's split sums are read back from L2 where they fit; the real
-// columns go in chunks that bound the split-sum memory (a complex output is one chunk, its real and
-// imaginary columns being finalised together).
+// Exact product of sliced rows into o. When the int32 split sums of all diagonals fit in 4 GB they are
+// kept side by side and summed into the output in one pass. Otherwise the diagonal GEMMs run one at a
+// time, each followed by its accumulation into an FP64 buffer, over column chunks that bound the
+// split-sum memory (a complex output is one chunk, its real and imaginary columns being finalised
+// together).
 void oz_run(const SlicedRows& A, const SlicedRows& B, long long M, long long Np, const OzOut& o, OzWork& w,
             cudaStream_t s) {
   const int ns = A.ns;
   const long long kp = A.kp, ld = (long long)ns * kp;
   const int max_splits = tc_exact_splits(M, Np, (long long)ns * kp);
+  const __nv_bfloat16* As = reinterpret_cast<const __nv_bfloat16*>(A.slices.p);
+  const __nv_bfloat16* Bs = reinterpret_cast<const __nv_bfloat16*>(B.slices.p);
+  if (4.0 * ns * max_splits * (double)M * (double)Np <= 4.0 * (1LL << 30)) {
+    // every diagonal's split sums side by side, then one pass that sums them into the output: the
+    // output is touched once instead of once per diagonal
+    w.islabs.alloc((size_t)ns * max_splits * M * Np);
+    if (w.err.n == 0) { w.err.alloc(1); w.err.zero(s); }
+    OzDiags dg;
+    dg.nd = ns;
+    long long off = 0;
+    for (int d = 0; d < ns; ++d) {
+      const long long kd = (long long)(d + 1) * kp;
+      const int zs = std::min(tc_exact_splits(M, Np, kd), max_splits);
+      TcOperand a(As, M, kd, ld);
+      TcOperand b(Bs + (long long)(ns - 1 - d) * kp, Np, kd, ld);
+      dg.off[d] = off;
+      dg.zs[d] = tc_gemm_exact(a, b, w.islabs.p + off, Np, M, Np, zs, M * Np, w.err.p, s, PROF_TC_SLICE);
+      dg.scale[d] = ldexp(1.0, -7 * d);
+      off += (long long)zs * M * Np;
+    }
+    int splits = 0;
+    for (int d = 0; d < ns; ++d) splits += dg.zs[d];
+    const long long elements = o.complex_out ? M * (Np / 2) : M * Np;
+    const bool warp = elements < 152LL * 256 && splits > 8 * ns;
+    const int grid = warp ? (int)std::min<long long>(std::max<long long>((elements * 32 + 255) / 256, 1), 152LL * 32)
+                          : grid_for(elements);
+    const bool small = M * Np < (1LL << 32);
+    ProfScope pa(PROF_OZ_ACCUM, 0.0, s);
+    if (splits == ns) {   // one split per diagonal
+      if (o.complex_out) {
+        if (small) launch_output1<2, unsigned>(ns, grid, s, w.islabs.p, dg, M, Np, A.expo.p, B.expo.p, o);
+        else launch_output1<2, unsigned long long>(ns, grid, s, w.islabs.p, dg, M, Np, A.expo.p, B.expo.p, o);
+      } else {
+        if (small) launch_output1<1, unsigned>(ns, grid, s, w.islabs.p, dg, M, Np, A.expo.p, B.expo.p, o);
+        else launch_output1<1, unsigned long long>(ns, grid, s, w.islabs.p, dg, M, Np, A.expo.p, B.expo.p, o);
+      }
+    } else if (o.complex_out) {
+      if (warp) launch_output<true, 2>(small, grid, s, w.islabs.p, dg, M, Np, A.expo.p, B.expo.p, o);
+      else launch_output<false, 2>(small, grid, s, w.islabs.p, dg, M, Np, A.expo.p, B.expo.p, o);
+    } else {
+      if (warp) launch_output<true, 1>(small, grid, s, w.islabs.p, dg, M, Np, A.expo.p, B.expo.p, o);
+      else launch_output<false, 1>(small, grid, s, w.islabs.p, dg, M, Np, A.expo.p, B.expo.p, o);
+    }
+    GFCC_LAUNCH_CHECK();
+    return;
+  }
   const long long slab_budget = 2LL << 30;   // bytes of int32 split sums at a time
   long long nc = std::max<long long>(1, slab_budget / (4LL * M * max_splits));
   nc = std::min<long long>(Np, std::max<long long>(256, nc / 256 * 256));
@@ -316,8 +494,6 @@ void oz_run(const SlicedRows& A, const SlicedRows& B, long long M, long long Np,
   w.islabs.alloc((size_t)max_splits * M * nc);
   w.acc.alloc((size_t)M * nc);
   if (w.err.n == 0) { w.err.alloc(1); w.err.zero(s); }
-  const __nv_bfloat16* As = reinterpret_cast<const __nv_bfloat16*>(A.slices.p);
-  const __nv_bfloat16* Bs = reinterpret_cast<const __nv_bfloat16*>(B.slices.p);
   for (long long n0 = 0; n0 < Np; n0 += nc) {
     const long long nn = std::min(nc, Np - n0);
     OzOut oc = o;
@@ -338,6 +514,7 @@ void oz_run(const SlicedRows& A, const SlicedRows& B, long long M, long long Np,
                             : grid_for(elements);
       const bool small = M * nn < (1LL << 32);
       const int* eb = B.expo.p + n0;
+      ProfScope pa(PROF_OZ_ACCUM, 0.0, s);
       if (mode == 0) {
         if (warp) launch_accumulate<true, 0>(small, grid, s, w.islabs.p, zeff, M, nn, scale, first, w.acc.p, A.expo.p, eb, oc);
         else launch_accumulate<false, 0>(small, grid, s, w.islabs.p, zeff, M, nn, scale, first, w.acc.p, A.expo.p, eb, oc);

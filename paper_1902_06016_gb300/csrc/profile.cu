@@ -15,6 +15,22 @@ struct Rec {
 std::mutex g_mu;
 bool g_on = false;
 std::vector<Rec> g_recs;
+// events are created once and reused by later profiling runs (creating two per region would put
+// host work into the timed stream's gaps)
+std::vector<cudaEvent_t> g_pool;
+size_t g_used = 0;
+bool take_event(cudaEvent_t* e) {
+  if (g_used == g_pool.size()) {
+    cudaEvent_t n;
+    if (cudaEventCreate(&n) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    g_pool.push_back(n);
+  }
+  *e = g_pool[g_used++];
+  return true;
+}
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -25,8 +41,7 @@ ProfScope::ProfScope(int c, double f, cudaStream_t st) : cls(c), flops(f), s(st)
   Rec* r = new Rec{};
   r->cls = c;
   r->flops = f;
-  if (cudaEventCreate(&r->a) != cudaSuccess || cudaEventCreate(&r->b) != cudaSuccess) {
-    cudaGetLastError();
+  if (!take_event(&r->a) || !take_event(&r->b)) {
     delete r;
     return;
   }
@@ -50,11 +65,12 @@ long long gfcc_launch_count(void) { return gfcc::g_launches.load(); }
 
 int gfcc_profile(int enable) {
   std::lock_guard<std::mutex> lk(gfcc::g_mu);
-  for (auto& r : gfcc::g_recs) {
-    cudaEventDestroy(r.a);
-    cudaEventDestroy(r.b);
+  for (auto& r : gfcc::g_recs) {   // the pooled events are reused once their records have completed
+    cudaEventSynchronize(r.b);
   }
+  cudaGetLastError();
   gfcc::g_recs.clear();
+  gfcc::g_used = 0;
   gfcc::g_on = enable != 0;
   return GFCC_OK;
 }

@@ -456,13 +456,17 @@ static void sigma_lp_impl(gfcc_ctx* c, LpState& st, const VT* X, VT* Y, int nb, 
   T* Boo = reinterpret_cast<T*>(st.Boo.p);
   T* Bup = reinterpret_cast<T*>(st.Bup.p);
   T* Bdn = reinterpret_cast<T*>(st.Bdn.p);
-  prep_operand<Elem<K>, VT, PREP_UP>(X, o, v, nb, Bup, st.Kpv, s);
-  prep_operand<Elem<K>, VT, PREP_OOOO>(X, o, v, nb, Boo, st.Kp, s);
-  prep_operand<Elem<K>, VT, PREP_RING>(X, o, v, nb, Bring, st.Kr, s);
+  {
+    ProfScope pp(PROF_LP_PREP, 0.0, s);
+    prep_operand<Elem<K>, VT, PREP_UP>(X, o, v, nb, Bup, st.Kpv, s);
+    prep_operand<Elem<K>, VT, PREP_OOOO>(X, o, v, nb, Boo, st.Kp, s);
+    prep_operand<Elem<K>, VT, PREP_RING>(X, o, v, nb, Bring, st.Kr, s);
+  }
   // up (split-K) and its reduction
   tc_gemm(K, TcOperand{st.Aup.p, v + o, st.Kpv}, TcOperand{Bup, nsm, st.Kpv}, st.up_part.p, nsm, v + o, nsm, 0, ksplit,
           part_stride, st.err.p, s);
   {
+    ProfScope pc(PROF_LP_COMBINE, 0.0, s);
     const int nk_split = (nk_up + ksplit - 1) / ksplit;
     const int zs = (nk_up + nk_split - 1) / nk_split;
     reduce_splits_kernel<<<grid_for(part_stride), 256, 0, s>>>(st.up_part.p, zs, part_stride, part_stride, st.up.p);
@@ -471,14 +475,18 @@ static void sigma_lp_impl(gfcc_ctx* c, LpState& st, const VT* X, VT* Y, int nb, 
   // oooo into C2 (as [P][(a,c,r)] = [(pij,a)][(c,r)])
   tc_gemm(K, TcOperand{st.Woo.p, P, st.Kp}, TcOperand{Boo, noo, st.Kp}, st.C2.p, noo, P, noo, 0, 1, 0, st.err.p, s);
   // down: C2 += [T2p | A21] [Xe ; r1]
-  prep_down_kernel<Elem<K>, float, VT><<<grid_for(nsm * st.Kvo), 256, 0, s>>>(st.up.p, nsm, X, o, v, nb, Bdn, st.Kvo);
-  GFCC_LAUNCH_CHECK();
+  {
+    ProfScope pp(PROF_LP_PREP, 0.0, s);
+    prep_down_kernel<Elem<K>, float, VT><<<grid_for(nsm * st.Kvo), 256, 0, s>>>(st.up.p, nsm, X, o, v, nb, Bdn, st.Kvo);
+    GFCC_LAUNCH_CHECK();
+  }
   tc_gemm(K, TcOperand{st.Adn.p, Pv, st.Kvo}, TcOperand{Bdn, nsm, st.Kvo}, st.C2.p, nsm, Pv, nsm, 1, 1, 0, st.err.p, s);
   // ring (its own profiling class and NVTX range, so that its launches can be timed and profiled alone)
   nvtxRangePushA("gfcc_ring_gemm");
   tc_gemm(K, TcOperand{st.Wr.p, ov, st.Kr}, TcOperand{Bring, nring, st.Kr}, st.CT.p, nring, ov, nring, 0, 1, 0,
           st.err.p, s, PROF_TC_RING, ov);
   nvtxRangePop();
+  ProfScope pc(PROF_LP_COMBINE, 0.0, s);
   combine_lp_kernel<float, VT><<<grid_for(D * nb), 256, 0, s>>>(X, Y, st.up.p, nsm, st.C2.p, st.CT.p, c->op.A11.p, c->op.diag.p,
                                                      shift, o, v, D, nb);
   GFCC_LAUNCH_CHECK();
