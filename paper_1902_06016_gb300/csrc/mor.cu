@@ -174,15 +174,77 @@ struct EvalArgs {
 
 __device__ __forceinline__ double cabs2(cplx a) { return a.x * a.x + a.y * a.y; }
 
+// ---- double-float arithmetic (value = h + l, two FP32 numbers) ------------------------------------
+// GB300 issues FP32 operations at many times its FP64 rate, so the O(m^2 np) back substitution runs
+// on pairs of floats (about 48 significant bits; Dekker 1971, Knuth's two-sum). The explicitly
+// rounded intrinsics keep the compiler from contracting the error-free transformations.
+struct df2 {
+  float h, l;
+};
+__device__ __forceinline__ df2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df2 fast_two_sum(float a, float b) {   // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df2 df_from(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(float h, float l) { return (double)h + (double)l; }
+// c + a1 b1 + a2 b2 (all double-float): the leading products exactly (fma), the rest in FP32
+__device__ __forceinline__ df2 df_dot2(df2 c, df2 a1, df2 b1, df2 a2, df2 b2) {
+  const float p1 = __fmul_rn(a1.h, b1.h), p2 = __fmul_rn(a2.h, b2.h);
+  const float e1 = __fmaf_rn(a1.h, b1.h, -p1), e2 = __fmaf_rn(a2.h, b2.h, -p2);
+  float cross = __fmul_rn(a2.l, b2.h);
+  cross = __fmaf_rn(a2.h, b2.l, cross);
+  cross = __fmaf_rn(a1.l, b1.h, cross);
+  cross = __fmaf_rn(a1.h, b1.l, cross);
+  const df2 s1 = two_sum(c.h, p1);
+  const df2 s2 = two_sum(s1.h, p2);
+  float low = __fadd_rn(c.l, e1);
+  low = __fadd_rn(low, e2);
+  low = __fadd_rn(low, cross);
+  low = __fadd_rn(low, s1.l);
+  low = __fadd_rn(low, s2.l);
+  return fast_two_sum(s2.h, low);
+}
+// complex double-float in a float4 (re.h, re.l, im.h, im.l)
+__device__ __forceinline__ float4 dfc_from(cplx z) {
+  const df2 r = df_from(z.x), i = df_from(z.y);
+  return make_float4(r.h, r.l, i.h, i.l);
+}
+__device__ __forceinline__ cplx dfc_to(float4 v) { return make_cuDoubleComplex(df_to(v.x, v.y), df_to(v.z, v.w)); }
+// c - u y
+__device__ __forceinline__ float4 dfc_sub_mul(float4 c, float4 u, float4 y) {
+  const df2 cr{c.x, c.y}, ci{c.z, c.w};
+  const df2 nur{-u.x, -u.y}, ui{u.z, u.w}, nui{-u.z, -u.w};
+  const df2 yr{y.x, y.y}, yi{y.z, y.w};
+  const df2 r = df_dot2(cr, nur, yr, ui, yi);     // cr - ur yr + ui yi
+  const df2 i = df_dot2(ci, nur, yi, nui, yr);    // ci - ur yi - ui yr
+  return make_float4(r.h, r.l, i.h, i.l);
+}
+
 // One CTA per frequency (grid-stride): LU of (w - i eta + H) with partial pivoting between adjacent
-// rows (the only pivots a Hessenberg matrix needs), applied to the np right-hand sides, then back
-// substitution. Everything after the solves (Ghat, A, residual norms) is a GEMM over all
-// frequencies at once and runs outside this kernel.
+// rows (the only pivots a Hessenberg matrix needs), applied to the np right-hand sides, in FP64 (O(m^2
+// + m np) work); then the back substitution (O(m^2 np)) in double-float, P right-hand sides at a time
+// held in shared memory, with U stored column by column. Everything after the solves (Ghat, A,
+// residual norms) is a GEMM over all frequencies at once and runs outside this kernel.
+// Scratch per CTA (16-byte units): U (m(m+1)/2, double-float, column j at j(j+1)/2) | two FP64 rows
+// (2m) | the FP64 diagonal of U (m). Dynamic shared memory: m P double-float complex values.
+template <int P>
 __global__ void __launch_bounds__(256) eval_solve_kernel(EvalArgs a) {
+  static_assert(256 % P == 0, "P divides the block");
+  extern __shared__ float4 Rs[];   // [m][P]
   const int m = a.m, np = a.np;
-  cplx* U = a.scratch + blockIdx.x * a.scratch_per_cta;
-  cplx* rowA = U + (long long)m * (m + 1) / 2;
+  float4* Ud = reinterpret_cast<float4*>(a.scratch + blockIdx.x * a.scratch_per_cta);
+  cplx* rowA = reinterpret_cast<cplx*>(Ud + (long long)m * (m + 1) / 2);
   cplx* rowB = rowA + m;
+  cplx* dU = rowB + m;
   const long long ldr = a.ldy;
   __shared__ int s_swap;
   __shared__ cplx s_l;
@@ -225,8 +287,10 @@ __global__ void __launch_bounds__(256) eval_solve_kernel(EvalArgs a) {
         }
       }
       __syncthreads();
-      const long long off = (long long)j * m - (long long)j * (j - 1) / 2;   // packed row j starts here
-      for (int col = j + threadIdx.x; col < m; col += blockDim.x) U[off + (col - j)] = cur[col];
+      // row j of U: U(j, col) at column col's offset col(col+1)/2 + j
+      for (int col = j + threadIdx.x; col < m; col += blockDim.x)
+        Ud[(long long)col * (col + 1) / 2 + j] = dfc_from(cur[col]);
+      if (threadIdx.x == 0) dU[j] = cur[j];
       if (j + 1 < m) {
         if (threadIdx.x == 0) {
           cplx piv = cur[j];
@@ -243,24 +307,66 @@ __global__ void __launch_bounds__(256) eval_solve_kernel(EvalArgs a) {
       }
     }
     __syncthreads();
-    // back substitution, column oriented: y_j = R_j / U_jj ; R_i -= U_ij y_j for i < j
-    for (int j = m - 1; j >= 0; --j) {
-      const long long offj = (long long)j * m - (long long)j * (j - 1) / 2;
-      cplx d = U[offj];
-      for (int p = threadIdx.x; p < np; p += blockDim.x) {
-        cplx y = (d.x == 0.0 && d.y == 0.0) ? cz() : cuCdiv(R[j * ldr + p], d);
-        R[j * ldr + p] = y;
+    // back substitution, column oriented, P right-hand sides at a time: y_j = R_j / U_jj (FP64);
+    // R_i -= U_ij y_j for i < j (double-float)
+    const int p = threadIdx.x % P, i0 = threadIdx.x / P;
+    constexpr int ISTEP = 256 / P;
+    for (int pc0 = 0; pc0 < np; pc0 += P) {
+      const int pn = min(P, np - pc0);
+      for (int t = threadIdx.x; t < m * P; t += blockDim.x) {
+        const int i = t / P, pp = t % P;
+        Rs[t] = pp < pn ? dfc_from(R[i * ldr + pc0 + pp]) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       __syncthreads();
-      for (long long t = threadIdx.x; t < (long long)j * np; t += blockDim.x) {
-        int i = (int)(t / np), p = (int)(t % np);
-        const long long offi = (long long)i * m - (long long)i * (i - 1) / 2;
-        cplx u = U[offi + (j - i)];
-        R[i * ldr + p] = cuCsub(R[i * ldr + p], cuCmul(u, R[j * ldr + p]));
+      for (int j = m - 1; j >= 0; --j) {
+        if (threadIdx.x < pn) {
+          const cplx d = dU[j];
+          const cplx y = (d.x == 0.0 && d.y == 0.0) ? cz() : cuCdiv(dfc_to(Rs[j * P + threadIdx.x]), d);
+          Rs[j * P + threadIdx.x] = dfc_from(y);
+        }
+        __syncthreads();
+        if (p < pn) {
+          const float4 yj = Rs[j * P + p];
+          const float4* Uc = Ud + (long long)j * (j + 1) / 2;
+          for (int i = i0; i < j; i += ISTEP) Rs[i * P + p] = dfc_sub_mul(Rs[i * P + p], Uc[i], yj);
+        }
+        __syncthreads();
+      }
+      for (int t = threadIdx.x; t < m * P; t += blockDim.x) {
+        const int i = t / P, pp = t % P;
+        if (pp < pn) R[i * ldr + pc0 + pp] = dfc_to(Rs[t]);
       }
       __syncthreads();
     }
   }
+}
+
+// scratch per CTA of eval_solve_kernel (16-byte units)
+long long eval_scratch_per_cta(int m) { return (long long)m * (m + 1) / 2 + 3LL * m + 64; }
+
+// launch with the widest right-hand-side chunk whose double-float block fits in shared memory
+void launch_eval_solve(const EvalArgs& ea, int grid, cudaStream_t s) {
+  const size_t cap = 200 * 1024;
+  auto go = [&](auto Pc) {
+    constexpr int P = decltype(Pc)::value;
+    const size_t bytes = sizeof(float4) * (size_t)ea.m * P;
+    static bool attr = false;   // per instantiation, once per process
+    if (!attr) {
+      GFCC_CUDA(cudaFuncSetAttribute(eval_solve_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+      attr = true;
+    }
+    eval_solve_kernel<P><<<grid, 256, bytes, s>>>(ea);
+  };
+  const size_t row = sizeof(float4) * (size_t)ea.m;
+  if (row * 16 <= cap) go(std::integral_constant<int, 16>{});
+  else if (row * 8 <= cap) go(std::integral_constant<int, 8>{});
+  else if (row * 4 <= cap) go(std::integral_constant<int, 4>{});
+  else if (row * 2 <= cap) go(std::integral_constant<int, 2>{});
+  else {
+    GFCC_CHECK(row <= cap, GFCC_ERR_ARG, "reduced model too large for the evaluation kernel");
+    go(std::integral_constant<int, 1>{});
+  }
+  GFCC_LAUNCH_CHECK();
 }
 
 // A[w] = -(1/pi) sum_p Im G[w][p][qidx[p]] (p with a matching q only)
@@ -345,7 +451,9 @@ void regrow_cm(DBuf<cplx>& b, int old_ld, int new_ld, int alloc_cols, int nrows,
 // the columns' norms, and 41-bit products perturb them enough to spoil the refinement estimates.
 // The coefficients of the first Gram-Schmidt pass are the exception (ns = 5, 34 bits): the reconstruction
 // y = Q (C1 + C2) + y'' holds for whatever C1 the first update subtracts, and the second pass, whose
-// coefficients and both updates keep 7 slices, removes what a less accurate C1 leaves along Q.
+// coefficients and both updates keep 7 slices, removes what a less accurate C1 leaves along Q. The
+// second-pass and panel Gram products need the 7 slices even for the residual basis: with 5 the
+// refinement no longer converged (the model grew to the size limit).
 void fp64_accurate_zgemm(const ZGemmDesc& g, cudaStream_t s, int ns = 7) {
   if ((double)g.M * (double)g.N * (double)g.K >= (double)(1 << 22) && g.batch == 1) zgemm_oz(g, ns, s);
   else zgemm(g, s);
@@ -1042,7 +1150,7 @@ void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, doubl
   GFCC_CUDA(cudaMemcpyAsync(dbn.p, ms.bnorm.data(), sizeof(double) * np, cudaMemcpyHostToDevice, s));
   // frequencies in batches: solutions Y [m][nb np] of a batch (about 2 GB at most), then Ghat = chat^T Y
   // and the residual coefficients (w - i eta) RS Y + RZ Y - RB as complex GEMMs over the whole batch
-  const long long per = (long long)m * (m + 1) / 2 + 2LL * m + 64;
+  const long long per = eval_scratch_per_cta(m);
   const long long bw_max = std::max<long long>(1, (2LL << 30) / ((long long)m * np * (long long)sizeof(cplx)));
   const int nbw = (int)std::min<long long>(nw, bw_max);
   const int ncta = (int)std::min<long long>(nbw, 2LL * 152);
@@ -1069,8 +1177,7 @@ void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, doubl
     ea.Y = Y.p; ea.ldy = ldy; ea.singular = dsing.p;
     {
       ProfScope ps(PROF_EVAL_SOLVE, 0.0, s);
-      eval_solve_kernel<<<std::min(ncta, nb), 256, 0, s>>>(ea);
-      GFCC_LAUNCH_CHECK();
+      launch_eval_solve(ea, std::min(ncta, nb), s);
     }
     if (want_G) {   // G(q, n) = sum_k cw[q][k] Y[k][n], stored at Gb[n nq + q]
       cplx* Gb = G_dev ? G_dev + (long long)w0 * np * nq : Gt.p;
@@ -1091,8 +1198,7 @@ void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, doubl
       EvalArgs eb = ea;
       eb.Y = Yd.p;
       eb.rhs_in_Y = 1;
-      eval_solve_kernel<<<std::min(ncta, nb), 256, 0, s>>>(eb);
-      GFCC_LAUNCH_CHECK();
+      launch_eval_solve(eb, std::min(ncta, nb), s);
       ZGemmDesc g;
       g.M = nq; g.N = (int)ldy; g.K = m;
       g.A = cw; g.sam = 1; g.sak = nq;
@@ -1142,7 +1248,7 @@ void mor_extrapolate(gfcc_ctx* c, const double* omegas_host, int nw, cplx* X0) {
   DBuf<cplx> Y, scratch;
   DBuf<double> dom;
   DBuf<int> dsing;
-  const long long per = (long long)m * (m + 1) / 2 + 2LL * m + 64;
+  const long long per = eval_scratch_per_cta(m);
   const int ncta = (int)std::min<long long>(nw, 2LL * 152);
   scratch.alloc(per * ncta);
   Y.alloc((long long)m * N);
@@ -1155,8 +1261,7 @@ void mor_extrapolate(gfcc_ctx* c, const double* omegas_host, int nw, cplx* X0) {
   ea.omegas = dom.p; ea.eta = ms.eta;
   ea.scratch = scratch.p; ea.scratch_per_cta = per;
   ea.Y = Y.p; ea.ldy = N; ea.singular = dsing.p;
-  eval_solve_kernel<<<ncta, 256, 0, s>>>(ea);
-  GFCC_LAUNCH_CHECK();
+  launch_eval_solve(ea, ncta, s);
   for (int j = m - 3; j >= 0; --j) {   // yhat = P y_H, P = H_0 H_1 ... (Hermitian reflectors)
     house_rows_kernel<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(Y.p, N, N, j + 1, m - j - 1,
                                                                   ms.hV.p + (long long)j * m, ms.htau.p + j);
