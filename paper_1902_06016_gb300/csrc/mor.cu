@@ -344,15 +344,20 @@ __global__ void __launch_bounds__(256) eval_solve_kernel(EvalArgs a) {
 // scratch per CTA of eval_solve_kernel (16-byte units)
 long long eval_scratch_per_cta(int m) { return (long long)m * (m + 1) / 2 + 3LL * m + 64; }
 
-// launch with the widest right-hand-side chunk whose double-float block fits in shared memory
+// CTAs per SM of the evaluation solves: the steps of one solve are a chain of barriers and memory
+// round trips, so several solves share each SM
+constexpr int EVAL_CTAS_PER_SM = 4;
+// launch with the widest right-hand-side chunk whose double-float block lets EVAL_CTAS_PER_SM CTAs
+// share an SM (narrower chunks, down to one column, for large models)
 void launch_eval_solve(const EvalArgs& ea, int grid, cudaStream_t s) {
-  const size_t cap = 200 * 1024;
+  const size_t cap = std::max<size_t>(200 * 1024 / EVAL_CTAS_PER_SM, sizeof(float4) * (size_t)ea.m);
+  GFCC_CHECK(cap <= 200 * 1024, GFCC_ERR_ARG, "reduced model too large for the evaluation kernel");
   auto go = [&](auto Pc) {
     constexpr int P = decltype(Pc)::value;
     const size_t bytes = sizeof(float4) * (size_t)ea.m * P;
     static bool attr = false;   // per instantiation, once per process
     if (!attr) {
-      GFCC_CUDA(cudaFuncSetAttribute(eval_solve_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+      GFCC_CUDA(cudaFuncSetAttribute(eval_solve_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
       attr = true;
     }
     eval_solve_kernel<P><<<grid, 256, bytes, s>>>(ea);
@@ -362,10 +367,7 @@ void launch_eval_solve(const EvalArgs& ea, int grid, cudaStream_t s) {
   else if (row * 8 <= cap) go(std::integral_constant<int, 8>{});
   else if (row * 4 <= cap) go(std::integral_constant<int, 4>{});
   else if (row * 2 <= cap) go(std::integral_constant<int, 2>{});
-  else {
-    GFCC_CHECK(row <= cap, GFCC_ERR_ARG, "reduced model too large for the evaluation kernel");
-    go(std::integral_constant<int, 1>{});
-  }
+  else go(std::integral_constant<int, 1>{});
   GFCC_LAUNCH_CHECK();
 }
 
@@ -1153,7 +1155,7 @@ void mor_eval(gfcc_ctx* c, const double* omegas_host, int nw, cplx* G_dev, doubl
   const long long per = eval_scratch_per_cta(m);
   const long long bw_max = std::max<long long>(1, (2LL << 30) / ((long long)m * np * (long long)sizeof(cplx)));
   const int nbw = (int)std::min<long long>(nw, bw_max);
-  const int ncta = (int)std::min<long long>(nbw, 2LL * 152);
+  const int ncta = (int)std::min<long long>(nbw, (long long)EVAL_CTAS_PER_SM * 152);
   DBuf<cplx> scratch, Y, Ys, Cr, Gt, Yd;
   DBuf<double> rcol;
   scratch.alloc(per * ncta);
@@ -1249,7 +1251,7 @@ void mor_extrapolate(gfcc_ctx* c, const double* omegas_host, int nw, cplx* X0) {
   DBuf<double> dom;
   DBuf<int> dsing;
   const long long per = eval_scratch_per_cta(m);
-  const int ncta = (int)std::min<long long>(nw, 2LL * 152);
+  const int ncta = (int)std::min<long long>(nw, (long long)EVAL_CTAS_PER_SM * 152);
   scratch.alloc(per * ncta);
   Y.alloc((long long)m * N);
   dom.alloc(nw); dsing.alloc(1);
