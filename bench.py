@@ -109,9 +109,9 @@ class ClockSampler:
 # source file is unchanged (its SHA-256 is recorded with the figure).
 TRAFFIC = {
     ("benzene_o42_v186", 11): {
-        "bytes_per_launch": 4.0456e9,
+        "bytes_per_launch": 5.1091e9,
         "tc_gemm_sha256": "e8b4793c88921d9b36fdd8eda013c1e93f702e9069ceb46dabf54a98e20f7790",
-        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over all 239 ring-GEMM launches of one "
+        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over all 175 ring-GEMM launches of one "
                   "benchmark step (NVTX range gfcc_ring_gemm), averaged; profiles/tc_gemm_tf32_ring_benzene.md",
     },
 }
