@@ -156,11 +156,13 @@ __global__ void __launch_bounds__(256) zrowmax_kernel(const cplx* __restrict__ Z
   }
 }
 
+// Slices of row r at (r ns + slot) kp (row-major), or with slot_major at (slot rows_total + r) kp, where
+// rows_total = R (mode 0) or 2R (mode 1): then slots 0..j of all rows form one contiguous block of rows.
 __global__ void __launch_bounds__(256) zslice_kernel(const cplx* __restrict__ Z, long long s_r, long long s_k,
                                                      int conj, long long R, long long K, int mode,
                                                      const unsigned long long* __restrict__ rowmax, long long kp,
                                                      int reversed, int ns, __nv_bfloat16* __restrict__ out,
-                                                     int* __restrict__ expo) {
+                                                     int* __restrict__ expo, int slot_major = 0) {
   __shared__ cplx tile[ZT_R][ZT_K + 1];
   const long long r0 = (long long)blockIdx.y * ZT_R, k0 = (long long)blockIdx.x * ZT_K;
   load_ztile(Z, s_r, s_k, conj, R, K, r0, k0, tile);
@@ -174,8 +176,13 @@ __global__ void __launch_bounds__(256) zslice_kernel(const cplx* __restrict__ Z,
       expo[r] = e == ZERO_ROW ? 0 : e;
       if (mode == 1) expo[R + r] = e == ZERO_ROW ? 0 : e;
     }
-    __nv_bfloat16* o0 = out + r * (long long)ns * kp;
-    __nv_bfloat16* o1 = out + (R + r) * (long long)ns * kp;
+    const long long rows_total = mode == 1 ? 2 * R : R;
+    // element offset of slot 0 of a row and the distance between its slots
+    const long long b0 = slot_major ? r * kp : r * (long long)ns * kp;
+    const long long b1 = slot_major ? (R + r) * kp : (R + r) * (long long)ns * kp;
+    const long long sstep = slot_major ? rows_total * kp : kp;
+    __nv_bfloat16* o0 = out + b0;
+    __nv_bfloat16* o1 = out + b1;
     for (int tk = lane; tk < ZT_K; tk += 32) {
       const long long k = k0 + tk;
       if (2 * k >= kp) break;
@@ -186,7 +193,7 @@ __global__ void __launch_bounds__(256) zslice_kernel(const cplx* __restrict__ Z,
 #pragma unroll
       for (int i = 0; i < OZ_SLICES_MAX; ++i) {
         if (i < ns) {
-          const long long off = (long long)(reversed ? ns - 1 - i : i) * kp + 2 * k;
+          const long long off = (long long)(reversed ? ns - 1 - i : i) * sstep + 2 * k;
           if (mode == 0) {
             *reinterpret_cast<__nv_bfloat162*>(o0 + off) = __halves2bfloat162(__int2bfloat16_rn(are[i]),
                                                                                __int2bfloat16_rn(aim[i]));
@@ -418,6 +425,110 @@ void launch_output(bool small, int grid, cudaStream_t s, const int* slabs, const
   else oz_output_kernel<WARP, MODE, unsigned long long><<<grid, 256, 0, s>>>(slabs, dg, M, Np, ea, eb, o);
 }
 
+// ---- stacked form for a narrow right operand --------------------------------------------------------
+// When B has few rows and A is large, one GEMM per A slice i multiplies it by B slices 0..ns-1-i
+// stacked as rows (B sliced slot-major), so that A is read ns times instead of ns(ns+1)/2 times and the
+// narrow B fills more of each tile. Partials of slice i: slabs + off[i], [zs[i]][M][ncol[i]] with
+// ncol[i] = (ns - i) Np, B slice j in columns [j Np, (j + 1) Np). Diagonal d = i + j is summed exactly
+// in 64-bit integers before the FP64 weighting, so the result equals the diagonal-by-diagonal one.
+struct OzStack {
+  long long off[OZ_SLICES_MAX];
+  long long ncol[OZ_SLICES_MAX];
+  int zs[OZ_SLICES_MAX];
+  double scale[OZ_SLICES_MAX];
+  int ns;
+};
+template <bool WARP>
+__device__ __forceinline__ double stack_total(const int* __restrict__ slabs, const OzStack& st, long long M,
+                                              long long Np, long long m, long long col, int lane) {
+  double acc = 0.0;
+  for (int d = 0; d < st.ns; ++d) {
+    long long S = 0;
+    for (int i = 0; i <= d; ++i)
+      S += split_sum<WARP>(slabs + st.off[i] + m * st.ncol[i] + (d - i) * Np + col, st.zs[i], M * st.ncol[i], lane);
+    const double v = st.scale[d] * (double)S;
+    acc = d == 0 ? v : acc + v;
+  }
+  return acc;
+}
+// complex output C(m, n) = alpha (re + i im) + beta C (real columns n and N + n of the Np = 2N)
+template <bool WARP, typename I>
+__global__ void __launch_bounds__(256) oz_stack_output_kernel(const int* __restrict__ slabs, OzStack st, long long M,
+                                                              long long Np, const int* __restrict__ ea,
+                                                              const int* __restrict__ eb, OzOut o) {
+  const long long N = Np / 2, total = M * N;
+  const int lane = threadIdx.x & 31;
+  const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nthreads = (long long)gridDim.x * blockDim.x;
+  const long long start = WARP ? gid >> 5 : gid, step = WARP ? nthreads >> 5 : nthreads;
+  for (long long t = start; t < total; t += step) {
+    long long m, n;
+    divmod<I>(t, N, m, n);
+    const double re = ldexp(stack_total<WARP>(slabs, st, M, Np, m, n, lane), ea[m] + eb[n] - 12);
+    const double im = ldexp(stack_total<WARP>(slabs, st, M, Np, m, N + n, lane), ea[m] + eb[N + n] - 12);
+    if (!WARP || lane == 0) {
+      cplx* p = o.C + m * o.scm + n * o.scn;
+      cplx r = cuCmul(o.alpha, make_cuDoubleComplex(re, im));
+      if (o.cbeta.x != 0.0 || o.cbeta.y != 0.0) r = cuCadd(r, cuCmul(o.cbeta, *p));
+      *p = r;
+    }
+  }
+}
+// one split per slice product: all NS (NS + 1) / 2 loads of each part issued together
+template <int NS, typename I>
+__global__ void __launch_bounds__(256) oz_stack_output1_kernel(const int* __restrict__ slabs, OzStack st, long long M,
+                                                               long long Np, const int* __restrict__ ea,
+                                                               const int* __restrict__ eb, OzOut o) {
+  constexpr int NQ = NS * (NS + 1) / 2;
+  const long long N = Np / 2, total = M * N;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long m, n;
+    divmod<I>(t, N, m, n);
+    int vr[NQ], vi[NQ];
+#pragma unroll
+    for (int d = 0, q = 0; d < NS; ++d)
+#pragma unroll
+      for (int i = 0; i <= d; ++i, ++q) {
+        const int* p = slabs + st.off[i] + m * st.ncol[i] + (d - i) * Np + n;
+        vr[q] = p[0];
+        vi[q] = p[N];
+      }
+    double ar = 0.0, ai = 0.0;
+#pragma unroll
+    for (int d = 0, q = 0; d < NS; ++d) {
+      long long sr = 0, si = 0;
+#pragma unroll
+      for (int i = 0; i <= d; ++i, ++q) {
+        sr += vr[q];
+        si += vi[q];
+      }
+      const double xr = st.scale[d] * (double)sr, xi = st.scale[d] * (double)si;
+      ar = d == 0 ? xr : ar + xr;
+      ai = d == 0 ? xi : ai + xi;
+    }
+    const double re = ldexp(ar, ea[m] + eb[n] - 12), im = ldexp(ai, ea[m] + eb[N + n] - 12);
+    cplx* p = o.C + m * o.scm + n * o.scn;
+    cplx r = cuCmul(o.alpha, make_cuDoubleComplex(re, im));
+    if (o.cbeta.x != 0.0 || o.cbeta.y != 0.0) r = cuCadd(r, cuCmul(o.cbeta, *p));
+    *p = r;
+  }
+}
+template <typename I>
+void launch_stack_output(int ns, bool one_split, bool warp, int grid, cudaStream_t s, const int* slabs,
+                         const OzStack& st, long long M, long long Np, const int* ea, const int* eb, const OzOut& o) {
+  if (one_split) {
+    switch (ns) {
+      case 5: oz_stack_output1_kernel<5, I><<<grid, 256, 0, s>>>(slabs, st, M, Np, ea, eb, o); return;
+      case 6: oz_stack_output1_kernel<6, I><<<grid, 256, 0, s>>>(slabs, st, M, Np, ea, eb, o); return;
+      case 7: oz_stack_output1_kernel<7, I><<<grid, 256, 0, s>>>(slabs, st, M, Np, ea, eb, o); return;
+      default: break;
+    }
+  }
+  if (warp) oz_stack_output_kernel<true, I><<<grid, 256, 0, s>>>(slabs, st, M, Np, ea, eb, o);
+  else oz_stack_output_kernel<false, I><<<grid, 256, 0, s>>>(slabs, st, M, Np, ea, eb, o);
+}
+
 template <bool WARP, int MODE>
 void launch_accumulate(bool small, int grid, cudaStream_t s, const int* part, int zs, long long M, long long Np,
                        double scale, int first, double* acc, const int* ea, const int* eb, const OzOut& o) {
@@ -446,7 +557,7 @@ void oz_run(const SlicedRows& A, const SlicedRows& B, long long M, long long Np,
   if (4.0 * ns * max_splits * (double)M * (double)Np <= 4.0 * (1LL << 30)) {
     // every diagonal's split sums side by side, then one pass that sums them into the output: the
     // output is touched once instead of once per diagonal
-    w.islabs.alloc((size_t)ns * max_splits * M * Np);
+    w.islabs.alloc((size_t)ns * max_splits * M * Np + 4 * ns);
     if (w.err.n == 0) { w.err.alloc(1); w.err.zero(s); }
     OzDiags dg;
     dg.nd = ns;
@@ -459,7 +570,7 @@ void oz_run(const SlicedRows& A, const SlicedRows& B, long long M, long long Np,
       dg.off[d] = off;
       dg.zs[d] = tc_gemm_exact(a, b, w.islabs.p + off, Np, M, Np, zs, M * Np, w.err.p, s, PROF_TC_SLICE);
       dg.scale[d] = ldexp(1.0, -7 * d);
-      off += (long long)zs * M * Np;
+      off = (off + (long long)zs * M * Np + 3) / 4 * 4;   // 16-byte aligned blocks (vector epilogue stores)
     }
     int splits = 0;
     for (int d = 0; d < ns; ++d) splits += dg.zs[d];
@@ -529,6 +640,69 @@ void oz_run(const SlicedRows& A, const SlicedRows& B, long long M, long long Np,
     }
   }
 }
+
+// Split counts of the stacked form (one GEMM per A slice against B slices 0..ns-1-i) and the bytes of
+// their int32 partials.
+void stack_splits(long long M, long long Np, long long kp, int ns, int (&zs)[OZ_SLICES_MAX], double& bytes) {
+  bytes = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    zs[i] = tc_exact_splits(M, (ns - i) * Np, kp);
+    bytes += 4.0 * zs[i] * (double)M * (double)((ns - i) * Np) + 16.0;   // + alignment of each block
+  }
+}
+// The stacked form pays when the A rows saved from re-reading, ns(ns-1)/2 kp bf16 per row, outweigh the
+// extra partial sums it writes and reads back, about the same count times Np int32 per split, and its
+// partials fit in 4 GB.
+bool use_stacked(long long M, long long Np, long long kp, int ns) {
+  int zs[OZ_SLICES_MAX];
+  double bytes;
+  stack_splits(M, Np, kp, ns, zs, bytes);
+  return kp >= 4LL * Np * zs[0] && bytes <= 4.0 * (1LL << 30);
+}
+// Exact complex product in the stacked form: A sliced row-major (normal order), Bsm sliced slot-major
+// (normal order) with Np = 2N rows per slot.
+void oz_run_stacked(const SlicedRows& A, const SlicedRows& Bsm, long long M, long long Np, const OzOut& o,
+                    OzWork& w, cudaStream_t s) {
+  const int ns = A.ns;
+  const long long kp = A.kp, ld = (long long)ns * kp;
+  int zs[OZ_SLICES_MAX];
+  double bytes;
+  stack_splits(M, Np, kp, ns, zs, bytes);
+  w.islabs.alloc((size_t)(bytes / 4.0));
+  if (w.err.n == 0) { w.err.alloc(1); w.err.zero(s); }
+  const __nv_bfloat16* As = reinterpret_cast<const __nv_bfloat16*>(A.slices.p);
+  const __nv_bfloat16* Bs = reinterpret_cast<const __nv_bfloat16*>(Bsm.slices.p);
+  OzStack st;
+  st.ns = ns;
+  long long off = 0;
+  bool one_split = true;
+  int splits = 0;
+  for (int i = 0; i < ns; ++i) {
+    const long long nc = (ns - i) * Np;
+    TcOperand a(As + (long long)i * kp, M, kp, ld);
+    TcOperand b(Bs, nc, kp, kp);
+    st.off[i] = off;
+    st.ncol[i] = nc;
+    st.zs[i] = tc_gemm_exact(a, b, w.islabs.p + off, nc, M, nc, zs[i], M * nc, w.err.p, s, PROF_TC_SLICE);
+    st.scale[i] = ldexp(1.0, -7 * i);
+    // the GEMM epilogue stores rows of four int32 at once where ncol is a multiple of 4: every block
+    // of partials starts on 16 bytes
+    off = (off + (long long)zs[i] * M * nc + 3) / 4 * 4;
+    one_split = one_split && st.zs[i] == 1;
+    splits += st.zs[i];
+  }
+  const long long elements = M * (Np / 2);
+  const bool warp = !one_split && elements < 152LL * 256 && splits > 8 * ns;
+  const int grid = warp ? (int)std::min<long long>(std::max<long long>((elements * 32 + 255) / 256, 1), 152LL * 32)
+                        : grid_for(elements);
+  ProfScope pa(PROF_OZ_ACCUM, 0.0, s);
+  if (M * Np < (1LL << 32))
+    launch_stack_output<unsigned>(ns, one_split, warp, grid, s, w.islabs.p, st, M, Np, A.expo.p, Bsm.expo.p, o);
+  else
+    launch_stack_output<unsigned long long>(ns, one_split, warp, grid, s, w.islabs.p, st, M, Np, A.expo.p,
+                                            Bsm.expo.p, o);
+  GFCC_LAUNCH_CHECK();
+}
 }  // namespace
 
 double oz_min_macs() {
@@ -565,7 +739,8 @@ void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s) {
   SlicedRows& sa = z.sa;
   SlicedRows& sb = z.sb;
   sa.rows = M; sa.kp = tc_pad_k(TcKind::BF16, 2 * K); sa.ns = ns; sa.reversed = false;
-  sb.rows = 2 * N; sb.kp = sa.kp; sb.ns = ns; sb.reversed = true;
+  const bool stacked = use_stacked(M, 2 * N, sa.kp, ns);
+  sb.rows = 2 * N; sb.kp = sa.kp; sb.ns = ns; sb.reversed = !stacked;
   sa.slices.alloc(sizeof(__nv_bfloat16) * M * ns * sa.kp);
   sb.slices.alloc(sizeof(__nv_bfloat16) * 2 * N * ns * sb.kp);
   sa.expo.alloc(M);
@@ -591,8 +766,8 @@ void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s) {
         reinterpret_cast<__nv_bfloat16*>(sa.slices.p), sa.expo.p);
     GFCC_LAUNCH_CHECK();
     zslice_kernel<<<dim3((unsigned)kt, (unsigned)((N + ZT_R - 1) / ZT_R)), 256, 0, s>>>(
-        g.B, g.sbn, g.sbk, g.conjB ? 1 : 0, N, K, 1, mxb.p, sb.kp, 1, ns,
-        reinterpret_cast<__nv_bfloat16*>(sb.slices.p), sb.expo.p);
+        g.B, g.sbn, g.sbk, g.conjB ? 1 : 0, N, K, 1, mxb.p, sb.kp, stacked ? 0 : 1, ns,
+        reinterpret_cast<__nv_bfloat16*>(sb.slices.p), sb.expo.p, stacked ? 1 : 0);
     GFCC_LAUNCH_CHECK();
   }
   OzOut o;
@@ -603,7 +778,8 @@ void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s) {
   o.alpha = g.alpha;
   o.cbeta = g.beta;
   OzWork& w = z.w;
-  oz_run(sa, sb, M, 2 * N, o, w, s);
+  if (stacked) oz_run_stacked(sa, sb, M, 2 * N, o, w, s);
+  else oz_run(sa, sb, M, 2 * N, o, w, s);
   if (g.work) return;   // the caller checks the workspace's error flag (zgemm_work_check) later
   int herr = 0;
   GFCC_CUDA(cudaMemcpyAsync(&herr, w.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
