@@ -243,6 +243,9 @@ struct ZGemmDesc {
   cplx* C = nullptr; long long scm = 0, scn = 0, bsc = 0;
   cplx alpha = {1.0, 0.0}, beta = {0.0, 0.0};
   void* work = nullptr;   // optional grow-only workspace (zgemm_work(ctx)) for the exact-slice path
+  // optional cache of the exact slices of A (zgemm_slice_cache(ctx, i)): sliced on the first call after
+  // zgemm_slice_cache_reset and reused by later calls until the next reset (A's data must not change)
+  void* a_cache = nullptr;
 };
 void zgemm(const ZGemmDesc& g, cudaStream_t s);
 // the context's workspace for exact-slice complex GEMMs (created on first use, freed with the context)
@@ -250,6 +253,9 @@ void* zgemm_work(gfcc_ctx* c);
 void zgemm_work_free(gfcc_ctx* c);
 // throws GFCC_ERR_CUDA if a tensor-core wait of a GEMM that used the context's workspace timed out
 void zgemm_work_check(gfcc_ctx* c);
+// slice cache i (0 or 1) of the context's workspace, and its invalidation
+void* zgemm_slice_cache(gfcc_ctx* c, int i);
+void zgemm_slice_cache_reset(void* cache);
 
 // ---- grad.cu: T2 gradient of L = Re sum conj(Gbar) G ------------------------------------------
 // W[nu][w np + p] = sum_q conj(Gbar[w][p][q]) c_q[nu]   (right sides of the adjoint solves)

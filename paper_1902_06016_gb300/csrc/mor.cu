@@ -796,7 +796,13 @@ std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cp
   DBuf<cplx> Cf;
   Cf.alloc((long long)std::max(std::max(n_cur, nc), 1) * std::max(nc, 1));
   auto block_cgs = [&](const cplx* Pb, int ldp, int np_, const cplx* MPb, int col0, int ncols, bool to_cold) {
-    // two passes: Cf (row-major [np_][ncols]) = Pb^H Y[:, col0:col0+ncols]; Y[:, col0:...] -= Pb Cf
+    // two passes: Cf (row-major [np_][ncols]) = Pb^H Y[:, col0:col0+ncols]; Y[:, col0:...] -= Pb Cf.
+    // Pb and MPb do not change between the passes: their slices as left operands of the updates are
+    // made once.
+    void* cache_p = zgemm_slice_cache(c, 0);
+    void* cache_m = zgemm_slice_cache(c, 1);
+    zgemm_slice_cache_reset(cache_p);
+    zgemm_slice_cache_reset(cache_m);
     for (int pass = 0; pass < 2; ++pass) {
       ZGemmDesc g;
       g.M = np_; g.N = ncols; g.K = (int)D;
@@ -815,10 +821,11 @@ std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cp
       u.C = Y + col0; u.scm = nc; u.scn = 1;
       u.alpha = make_cuDoubleComplex(-1.0, 0.0); u.beta = make_cuDoubleComplex(1.0, 0.0);
       u.work = zgemm_work(c);
+      u.a_cache = cache_p;
       {
         ProfScope pu(PROF_ORTHO_UPDATE, 0.0, s);
         fp64_accurate_zgemm(u, s);
-        if (MY) { u.A = MPb; u.C = MY + col0; fp64_accurate_zgemm(u, s); }
+        if (MY) { u.A = MPb; u.C = MY + col0; u.a_cache = cache_m; fp64_accurate_zgemm(u, s); }
       }
       if (to_cold) {
         if (Cold) {   // Cold (col-major, ld n_cur) += Cf (row-major [n_cur][nc])

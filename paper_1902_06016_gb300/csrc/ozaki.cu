@@ -712,10 +712,19 @@ double oz_min_macs() {
 }
 
 namespace {
+struct ZSliceCache {   // slices of a left operand kept for several products with it
+  SlicedRows sa;
+  bool valid = false;
+  const cplx* A = nullptr;   // the operand they were made from (checked on reuse)
+  long long M = 0, K = 0, sam = 0, sak = 0;
+  int ns = 0;
+  bool conjA = false;
+};
 struct ZWork {          // buffers of zgemm_oz, kept between calls (grow-only)
   SlicedRows sa, sb;
   DBuf<unsigned long long> mxa, mxb;
   OzWork w;
+  ZSliceCache cache[2];
 };
 }  // namespace
 
@@ -723,6 +732,11 @@ void* zgemm_work(gfcc_ctx* c) {
   if (!c->zwork) c->zwork = new ZWork();
   return c->zwork;
 }
+void* zgemm_slice_cache(gfcc_ctx* c, int i) {
+  GFCC_CHECK(i == 0 || i == 1, GFCC_ERR_ARG, "zgemm_slice_cache: index");
+  return &static_cast<ZWork*>(zgemm_work(c))->cache[i];
+}
+void zgemm_slice_cache_reset(void* cache) { static_cast<ZSliceCache*>(cache)->valid = false; }
 void zgemm_work_free(gfcc_ctx* c) {
   delete static_cast<ZWork*>(c->zwork);
   c->zwork = nullptr;
@@ -736,14 +750,19 @@ void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s) {
   ProfScope prof(PROF_OZ_ZGEMM, 8.0 * (double)M * (double)N * (double)K, s);
   ZWork local;
   ZWork& z = g.work ? *static_cast<ZWork*>(g.work) : local;
-  SlicedRows& sa = z.sa;
+  ZSliceCache* cache = static_cast<ZSliceCache*>(g.a_cache);
+  const bool reuse = cache && cache->valid && cache->A == g.A && cache->M == M && cache->K == K &&
+                     cache->sam == g.sam && cache->sak == g.sak && cache->ns == ns && cache->conjA == g.conjA;
+  SlicedRows& sa = cache ? cache->sa : z.sa;
   SlicedRows& sb = z.sb;
   sa.rows = M; sa.kp = tc_pad_k(TcKind::BF16, 2 * K); sa.ns = ns; sa.reversed = false;
   const bool stacked = use_stacked(M, 2 * N, sa.kp, ns);
   sb.rows = 2 * N; sb.kp = sa.kp; sb.ns = ns; sb.reversed = !stacked;
-  sa.slices.alloc(sizeof(__nv_bfloat16) * M * ns * sa.kp);
+  if (!reuse) {
+    sa.slices.alloc(sizeof(__nv_bfloat16) * M * ns * sa.kp);
+    sa.expo.alloc(M);
+  }
   sb.slices.alloc(sizeof(__nv_bfloat16) * 2 * N * ns * sb.kp);
-  sa.expo.alloc(M);
   sb.expo.alloc(2 * N);
   {
     ProfScope ps(PROF_OZ_SLICE, 0.0, s);
@@ -757,14 +776,24 @@ void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s) {
     const long long kt_in = (K + ZT_K - 1) / ZT_K;
     GFCC_CHECK((M + ZT_R - 1) / ZT_R <= 65535 && (N + ZT_R - 1) / ZT_R <= 65535, GFCC_ERR_ARG, "zgemm_oz: too many rows");
     // A(m, k) = A[m sam + k sak]; B rows n: B(k, n) = B[k sbk + n sbn] -> r = n, s_r = sbn, s_k = sbk
-    zrowmax_kernel<<<dim3((unsigned)kt_in, (unsigned)((M + ZT_R - 1) / ZT_R)), 256, 0, s>>>(g.A, g.sam, g.sak, M, K, mxa.p);
-    GFCC_LAUNCH_CHECK();
+    if (!reuse) {
+      zrowmax_kernel<<<dim3((unsigned)kt_in, (unsigned)((M + ZT_R - 1) / ZT_R)), 256, 0, s>>>(g.A, g.sam, g.sak, M, K,
+                                                                                           mxa.p);
+      GFCC_LAUNCH_CHECK();
+    }
     zrowmax_kernel<<<dim3((unsigned)kt_in, (unsigned)((N + ZT_R - 1) / ZT_R)), 256, 0, s>>>(g.B, g.sbn, g.sbk, N, K, mxb.p);
     GFCC_LAUNCH_CHECK();
-    zslice_kernel<<<dim3((unsigned)kt, (unsigned)((M + ZT_R - 1) / ZT_R)), 256, 0, s>>>(
-        g.A, g.sam, g.sak, g.conjA ? 1 : 0, M, K, 0, mxa.p, sa.kp, 0, ns,
-        reinterpret_cast<__nv_bfloat16*>(sa.slices.p), sa.expo.p);
-    GFCC_LAUNCH_CHECK();
+    if (!reuse) {
+      zslice_kernel<<<dim3((unsigned)kt, (unsigned)((M + ZT_R - 1) / ZT_R)), 256, 0, s>>>(
+          g.A, g.sam, g.sak, g.conjA ? 1 : 0, M, K, 0, mxa.p, sa.kp, 0, ns,
+          reinterpret_cast<__nv_bfloat16*>(sa.slices.p), sa.expo.p);
+      GFCC_LAUNCH_CHECK();
+      if (cache) {
+        cache->valid = true;
+        cache->A = g.A; cache->M = M; cache->K = K; cache->sam = g.sam; cache->sak = g.sak;
+        cache->ns = ns; cache->conjA = g.conjA;
+      }
+    }
     zslice_kernel<<<dim3((unsigned)kt, (unsigned)((N + ZT_R - 1) / ZT_R)), 256, 0, s>>>(
         g.B, g.sbn, g.sbk, g.conjB ? 1 : 0, N, K, 1, mxb.p, sb.kp, stacked ? 0 : 1, ns,
         reinterpret_cast<__nv_bfloat16*>(sb.slices.p), sb.expo.p, stacked ? 1 : 0);
