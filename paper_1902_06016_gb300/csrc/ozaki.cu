@@ -106,6 +106,43 @@ __global__ void __launch_bounds__(256) slice_rows_warp_kernel(const double* __re
   }
 }
 
+// The same for a few long rows (fewer rows than it takes to occupy the GPU with a block each): the
+// row maxima over chunks of SL_CH elements (atomic integer maxima of the bit patterns; rowmax zeroed by
+// the caller), then the digits chunk by chunk.
+constexpr long long SL_CH = 8192;
+__global__ void __launch_bounds__(256) rowmax_chunk_kernel(const double* __restrict__ X, long long ldx, long long K,
+                                                           unsigned long long* __restrict__ rowmax) {
+  __shared__ unsigned long long red[8];
+  const long long r = blockIdx.y, k0 = blockIdx.x * SL_CH, k1 = min(K, k0 + SL_CH);
+  const double* x = X + r * ldx;
+  unsigned long long mx = 0;
+  for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) mx = max(mx, abs_bits(x[k]));
+  for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, red[w]);
+    if (mx > 0) atomicMax(rowmax + r, mx);
+  }
+}
+__global__ void __launch_bounds__(256) slice_chunk_kernel(const double* __restrict__ X, long long ldx, long long K,
+                                                          long long kp, int reversed, int ns,
+                                                          const unsigned long long* __restrict__ rowmax,
+                                                          __nv_bfloat16* __restrict__ out, int* __restrict__ expo) {
+  const long long r = blockIdx.y, k0 = blockIdx.x * SL_CH, k1 = min(kp, k0 + SL_CH);
+  const double* x = X + r * ldx;
+  const int e = row_exponent(rowmax[r]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) expo[r] = e == ZERO_ROW ? 0 : e;
+  __nv_bfloat16* o = out + r * (long long)ns * kp;
+  for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    int a[OZ_SLICES_MAX];
+    digits(k < K ? x[k] : 0.0, e, ns, a);
+#pragma unroll
+    for (int i = 0; i < OZ_SLICES_MAX; ++i)
+      if (i < ns) o[(long long)(reversed ? ns - 1 - i : i) * kp + k] = __int2bfloat16_rn(a[i]);
+  }
+}
+
 // ---- complex operands of zgemm_oz, sliced straight from their strided storage ----------------------
 // Operand element (r, k) = Z[r * s_r + k * s_k] (complex), conjugated when conj. Real rows written:
 //   mode 0 (left operand):  row r      = (Re, Im) interleaved along k
@@ -836,6 +873,19 @@ void oz_slice_into(const double* X, long long ldx, long long nrows, long long K,
     slice_rows_warp_kernel<<<(unsigned)((nrows * 32 + 255) / 256), 256, 0, s>>>(X, ldx, nrows, K, out.kp,
                                                                                  out.reversed ? 1 : 0, out.ns, o,
                                                                                  out.expo.p + row0);
+  } else if (nrows < 152LL * 4 && nrows <= 65535) {   // few long rows: split each row over blocks
+    DBuf<unsigned long long> mx;
+    mx.alloc(nrows);
+    mx.zero(s);
+    const long long chunks_in = (K + SL_CH - 1) / SL_CH, chunks = (out.kp + SL_CH - 1) / SL_CH;
+    rowmax_chunk_kernel<<<dim3((unsigned)std::max<long long>(chunks_in, 1), (unsigned)nrows), 256, 0, s>>>(X, ldx, K,
+                                                                                                         mx.p);
+    GFCC_LAUNCH_CHECK();
+    slice_chunk_kernel<<<dim3((unsigned)chunks, (unsigned)nrows), 256, 0, s>>>(
+        X, ldx, K, out.kp, out.reversed ? 1 : 0, out.ns, mx.p, o, out.expo.p + row0);
+    GFCC_LAUNCH_CHECK();
+    GFCC_CUDA(cudaStreamSynchronize(s));   // mx is released on return
+    return;
   } else {
     const int grid = (int)std::min<long long>(nrows, 152LL * 16);
     slice_kernel<<<grid, 256, 0, s>>>(X, ldx, nrows, K, out.kp, out.reversed ? 1 : 0, out.ns, o, out.expo.p + row0);
