@@ -691,19 +691,45 @@ std::vector<cplx> inverse_upper(const std::vector<cplx>& R, int n) {
 // depends on) and at least 10 drop_tol of the column's norm before any projection (n0), so that two
 // passes give orthonormality to rounding and no column is within a factor 10 of the drop threshold;
 // otherwise the caller runs the column-by-column passes. Writes T[c0:c0+pb, c0:c0+pb] = R2 R1 and keep = 1.
+// Z[nu][j] <- sum_{k <= j} Z[nu][k] X[k][j] for the pb (<= 32) columns of a panel: X upper
+// triangular, double-float, row-major pb x pb. One warp per row, in place; each lane forms one output
+// column in double-float (the row's entries are split once by their own lanes and broadcast).
+__global__ void __launch_bounds__(256) panel_apply_kernel(cplx* __restrict__ Z, int nc, int pb, long long D,
+                                                          const float4* __restrict__ Xdf) {
+  __shared__ float4 xs[32 * 32];
+  for (int t = threadIdx.x; t < pb * pb; t += blockDim.x) xs[t] = Xdf[t];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (long long nu = blockIdx.x * 8LL + warp; nu < D; nu += gridDim.x * 8LL) {
+    cplx* row = Z + nu * nc;
+    const float4 zk = lane < pb ? dfc_from(row[lane]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    df2 ar{0.f, 0.f}, ai{0.f, 0.f};
+    for (int k = 0; k < pb; ++k) {
+      const float zrh = __shfl_sync(0xffffffffu, zk.x, k), zrl = __shfl_sync(0xffffffffu, zk.y, k);
+      const float zih = __shfl_sync(0xffffffffu, zk.z, k), zil = __shfl_sync(0xffffffffu, zk.w, k);
+      if (lane >= k && lane < pb) {
+        const float4 x = xs[k * pb + lane];
+        const df2 zr{zrh, zrl}, zi{zih, zil}, nzi{-zih, -zil}, xr{x.x, x.y}, xi{x.z, x.w};
+        ar = df_dot2(ar, zr, xr, nzi, xi);   // re += zr xr - zi xi
+        ai = df_dot2(ai, zr, xi, zi, xr);    // im += zr xi + zi xr
+      }
+    }
+    if (lane < pb) row[lane] = make_cuDoubleComplex(df_to(ar.h, ar.l), df_to(ai.h, ai.l));
+  }
+}
+
 struct PanelWork {
-  DBuf<cplx> Gd, Rinv, tmp;
+  DBuf<cplx> Gd;
+  DBuf<float4> Rdf;
 };
 bool panel_cholqr2(gfcc_ctx* c, cplx* Y, cplx* MY, int nc, long long D, int c0, int pb, const double* n0,
                    cplx* T, int* keep_dev, PanelWork& pw) {
   cudaStream_t s = c->stream;
   std::vector<cplx> G((size_t)pb * pb), R1, R2;
   DBuf<cplx>& Gd = pw.Gd;
-  DBuf<cplx>& Rinv = pw.Rinv;
-  DBuf<cplx>& tmp = pw.tmp;
+  DBuf<float4>& Rdf = pw.Rdf;
   Gd.alloc((long long)pb * pb);
-  Rinv.alloc((long long)pb * pb);
-  tmp.alloc(D * pb);
+  Rdf.alloc((long long)pb * pb);
   auto gram = [&]() {
     ZGemmDesc g;
     g.M = pb; g.N = pb; g.K = (int)D;
@@ -719,21 +745,22 @@ bool panel_cholqr2(gfcc_ctx* c, cplx* Y, cplx* MY, int nc, long long D, int c0, 
       for (int k = i + 1; k < pb; ++k) G[(size_t)k * pb + i] = cuConj(G[(size_t)i * pb + k]);
     }
   };
-  auto apply = [&](const std::vector<cplx>& R) {   // Y (and MY) <- Y R^{-1}
+  auto apply = [&](const std::vector<cplx>& R) {   // Y (and MY) <- Y R^{-1}, in double-float
+    GFCC_CHECK(pb <= 32, GFCC_ERR_ARG, "panel wider than a warp");
     std::vector<cplx> X = inverse_upper(R, pb);
-    GFCC_CUDA(cudaMemcpyAsync(Rinv.p, X.data(), sizeof(cplx) * pb * pb, cudaMemcpyHostToDevice, s));
+    std::vector<float4> Xf((size_t)pb * pb);
+    for (size_t t = 0; t < Xf.size(); ++t) {   // the same split as on the device: h = fl(x), l = fl(x - h)
+      const float rh = (float)X[t].x, ih = (float)X[t].y;
+      Xf[t] = make_float4(rh, (float)(X[t].x - (double)rh), ih, (float)(X[t].y - (double)ih));
+    }
+    GFCC_CUDA(cudaMemcpyAsync(Rdf.p, Xf.data(), sizeof(float4) * pb * pb, cudaMemcpyHostToDevice, s));
+    const int grid = (int)std::min<long long>((D + 7) / 8, 152LL * 16);
     for (cplx* Z : {Y, MY}) {
       if (!Z) continue;
-      ZGemmDesc u;
-      u.M = (int)D; u.N = pb; u.K = pb;
-      u.A = Z + c0; u.sam = nc; u.sak = 1;
-      u.B = Rinv.p; u.sbk = pb; u.sbn = 1;
-      u.C = tmp.p; u.scm = pb; u.scn = 1;
-      u.work = zgemm_work(c);
-      fp64_accurate_zgemm(u, s);
-      GFCC_CUDA(cudaMemcpy2DAsync(Z + c0, sizeof(cplx) * nc, tmp.p, sizeof(cplx) * pb, sizeof(cplx) * pb, D,
-                                  cudaMemcpyDeviceToDevice, s));
+      panel_apply_kernel<<<grid, 256, 0, s>>>(Z + c0, nc, pb, D, Rdf.p);
+      GFCC_LAUNCH_CHECK();
     }
+    GFCC_CUDA(cudaStreamSynchronize(s));   // Xf is host memory of this scope
   };
   gram();
   if (!cholesky_upper(G, pb, R1)) return false;
