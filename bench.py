@@ -213,7 +213,7 @@ def run_ours(args, rank, world):
     phases = {phase_names[k]: round(G.profile_read(k)[1], 1) for k in phase_names}
     cgs = G.profile_read(14)   # (launch groups, ms, algorithmic bytes) of the Arnoldi sweeps
     cgs_parts = {name: G.profile_read(k) for k, name in
-                 ((15, "multidot_kernel"), (16, "update_dot_kernel"), (17, "update_norm_kernel"),
+                 ((15, "multidot_kernel"), (16, "cgs_update_kernel<dot>"), (17, "cgs_update_kernel<norm>"),
                   (18, "all three, batches < 32 columns"))}
     G.profile(False)
     clk = clocks.stop()
@@ -292,7 +292,7 @@ def run_ours(args, rank, world):
                    "l2": "working set (operators >= 0.5 GB, Krylov bases) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "gemm_classes": kernels, "phases_ms": phases,
-        "hbm_kernels": {"arnoldi_cgs_sweeps (multidot, update_dot, update_norm)": {
+        "hbm_kernels": {"arnoldi_cgs_sweeps (multidot_kernel, cgs_update_kernel x2)": {
             "bound": "hbm", "steps": cgs[0], "ms": cgs[1], "algorithmic_bytes": cgs[2],
             "achieved": cgs[2] / (cgs[1] / 1e3) / 1e9 if cgs[1] > 0 else None, "unit": "GB/s",
             "peak": peaks.get("hbm_gbs"), "frac": (cgs[2] / (cgs[1] / 1e3) / 1e9) / peaks["hbm_gbs"]
