@@ -50,12 +50,23 @@ def parse():
     ap.add_argument("--m-max", type=int, default=1700)
     ap.add_argument("--solve-tol", type=float, default=1e-8)
     ap.add_argument("--restart", type=int, default=30, help="GMRES(k) Krylov dimension per cycle")
+    ap.add_argument("--siso", action="store_true",
+                    help="one reduced model of G_pp per orbital (gfcc_mor_build_siso) instead of one MIMO model")
+    ap.add_argument("--krylov", type=int, default=0,
+                    help="K > 0: reduced model on the block Krylov space of M on the b_p (gfcc_mor_build_krylov, K "
+                         "initial blocks, grown by the refinement) instead of solutions at sampled frequencies")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--full-points", type=int, default=4,
-                    help="output frequencies (plus the oracle's) also solved full-dimension in FP64 for comparison")
-    ap.add_argument("--cpu-sample", type=int, default=2, help="(w, p) columns in the oracle sample")
-    ap.add_argument("--mode", default="pipeline", choices=["pipeline", "sigma"],
-                    help="pipeline: the whole MOR step (default); sigma: one batch of sigma applications")
+    ap.add_argument("--e2e-steps", type=int, default=5,
+                    help="timed end-to-end steps through host buffers (at most --steps), after one warm-up step")
+    ap.add_argument("--full-stride", type=int, default=50,
+                    help="every k-th output frequency, plus the sampled ones and the middle of the window, is also "
+                         "solved full-dimension in FP64 for comparison (0: skip)")
+    ap.add_argument("--cpu-sample", type=int, default=1, help="(w, p) columns in the oracle sample")
+    ap.add_argument("--ref-iters", type=int, default=6,
+                    help="--impl reference: GMRES iterations of the oracle per timed step")
+    ap.add_argument("--mode", default="pipeline", choices=["pipeline", "sigma", "peaks"],
+                    help="pipeline: the whole MOR step (default); sigma: one batch of sigma applications; "
+                         "peaks: FP64, TF32 and BF16 GEMM rates of this GPU (library GEMMs, timing only)")
     ap.add_argument("--nvec", type=int, default=64, help="vectors per sigma batch (--mode sigma)")
     return ap.parse_args()
 
@@ -105,15 +116,9 @@ class ClockSampler:
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the captured launches) of
-# the roofline kernel, from ncu captures summarised under profiles/; valid only while the kernel's
-# source file is unchanged (its SHA-256 is recorded with the figure).
+# the roofline kernel, from an ncu capture of the same kernel; valid only while the kernel's source file
+# is unchanged (its SHA-256 is recorded with the figure).
 TRAFFIC = {
-    ("benzene_o42_v186", 11): {
-        "bytes_per_launch": 5.1091e9,
-        "tc_gemm_sha256": "e8b4793c88921d9b36fdd8eda013c1e93f702e9069ceb46dabf54a98e20f7790",
-        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over all 175 ring-GEMM launches of one "
-                  "benchmark step (NVTX range gfcc_ring_gemm), averaged; profiles/tc_gemm_tf32_ring_benzene.md",
-    },
 }
 
 
@@ -131,6 +136,15 @@ def measured_traffic(workload, cls):
     return t if os.path.exists(src) and _sha256(src) == t["tc_gemm_sha256"] else None
 
 
+# Dense GEMM rates measured on a GB300 of this machine with `python bench.py --mode peaks` (cuBLAS through
+# torch.matmul, 8192^3, CUDA events, SM clock 2070 MHz, sw_power_cap only): the TF32 and FP64 rates that
+# the driver does not measure. The roofline's `peak` for a TF32 contraction follows the rule "measured
+# bf16 x the nominal tf32/bf16 ratio (1.1 / 2.25 PFLOP/s)"; these figures are reported beside it.
+OWN_PEAKS = {"tf32_tflops": 1008.3, "tf32_tflops_sustained": 897.0, "fp64_tflops": 1.099,
+             "bf16_tflops": 1871.5, "bf16_tflops_sustained": 1678.3}
+TF32_OVER_BF16 = 1.1 / 2.25
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -140,6 +154,39 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------------------------
+# p set of each workload (q set = p set): the occupied spin-orbitals, or all spin-orbitals where the
+# workload's configuration asks for every orbital
+P_SET = {"co_o14_v42": "all"}
+
+
+def orbital_set(workload, o, n):
+    return list(range(n)) if P_SET.get(workload) == "all" else list(range(o))
+
+
+def pinned_copy(arr):
+    """Page-locked host copy of a NumPy array (returned as a NumPy view of a pinned torch tensor)."""
+    import torch
+    t = torch.empty(arr.shape, dtype=torch.from_numpy(arr[:0].copy()).dtype, pin_memory=True)
+    view = t.numpy()
+    view[...] = arr
+    return view, t
+
+
+def pinned_empty(shape, dtype):
+    import torch
+    t = torch.empty(shape, dtype=dtype, pin_memory=True)
+    return t.numpy(), t
+
+
+def spectrum_peaks(A, grid, rel=0.01):
+    """Peaks of the spectral function on the output grid. A = -(1/pi) sum Im G_pp is negative at poles
+    (the -i eta convention), so the peaks are local minima of A deeper than rel * max |A|."""
+    a = -np.asarray(A)
+    thr = rel * np.abs(a).max()
+    k = np.where((a[1:-1] > a[:-2]) & (a[1:-1] >= a[2:]) & (a[1:-1] > thr))[0] + 1
+    return {"count": int(len(k)), "threshold_rel": rel, "positions_ha": [round(float(grid[i]), 5) for i in k[:40]]}
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_1902_06016_gb300 import Context, load
@@ -152,7 +199,8 @@ def run_ours(args, rank, world):
     o, v, eta = W["o"], W["v"], W["eta"]
     nw = args.nomega or W["nw"]
     inp = synth.make_inputs(o, v, rank_seed(W["seed"], rank))   # weak scaling: one problem per rank
-    porb = list(range(o))
+    porb = orbital_set(args.workload, o, o + v)
+    npp = len(porb)
     seeds = synth.omega_grid(W["wmin"], W["wmax"], args.seeds)
     grid = np.linspace(W["wmin"], W["wmax"], nw)
 
@@ -160,7 +208,7 @@ def run_ours(args, rank, world):
     dev_inputs = synth.Inputs(**{k: (torch.from_numpy(np.ascontiguousarray(getattr(inp, k))).to(dev)
                                      if isinstance(getattr(inp, k), np.ndarray) else getattr(inp, k))
                                  for k in inp.__dataclass_fields__})
-    G_dev = torch.empty((nw, o, o), dtype=torch.complex128, device=dev)
+    G_dev = torch.empty((nw, npp, npp), dtype=torch.complex128, device=dev)
     A_dev = torch.empty((nw,), dtype=torch.float64, device=dev)
     omega_host = np.ascontiguousarray(grid)
 
@@ -169,7 +217,12 @@ def run_ours(args, rank, world):
     def step(inputs, G_out, A_out, keep=False):
         ctx = Context(inputs, tol=args.solve_tol, precision=args.precision, stream=stream.cuda_stream,
                       restart=args.restart)
-        ctx.mor_build(seeds, eta, porb)
+        if args.siso:
+            ctx.mor_build_siso(seeds, eta, porb)
+        elif args.krylov > 0:
+            ctx.mor_build_krylov(args.krylov, eta, porb)
+        else:
+            ctx.mor_build(seeds, eta, porb)
         ref = ctx.mor_refine(W["wmin"], W["wmax"], args.ngrid, args.mor_tol, args.m_max)
         ctx.mor_eval(omega_host, G=G_out, A=A_out)
         info = ctx.mor_info()
@@ -209,34 +262,68 @@ def run_ours(args, rank, world):
                    12: "exact_slice_complex_gemms", 13: "exact_slicing", 19: "eval_hessenberg_reduction",
                    20: "eval_shifted_solves", 21: "ortho_gram_products", 22: "ortho_updates",
                    23: "ortho_panel_cholqr", 24: "exact_slice_accumulate", 25: "lowprec_operand_prep",
-                   26: "lowprec_combine"}
-    phases = {phase_names[k]: round(G.profile_read(k)[1], 1) for k in phase_names}
+                   26: "lowprec_combine", 27: "input_upload", 28: "output_copies"}
+    phases = {phase_names[k]: round(G.profile_read(k)[1] / args.steps, 1) for k in phase_names}
     cgs = G.profile_read(14)   # (launch groups, ms, algorithmic bytes) of the Arnoldi sweeps
     cgs_parts = {name: G.profile_read(k) for k, name in
                  ((15, "multidot_kernel"), (16, "cgs_update_kernel<dot>"), (17, "cgs_update_kernel<norm>"),
                   (18, "all three, batches < 32 columns"))}
     G.profile(False)
     clk = clocks.stop()
+    spectrum = spectrum_peaks(A_dev.cpu().numpy(), grid)
 
-    # end to end: host inputs, host outputs, copies inside the timed region
+    # end to end through the public API with host buffers: the inputs are copied from page-locked host
+    # memory inside gfcc_init and G, A are written to page-locked host arrays, every step; one warm-up
+    # step, then the median of e2e_steps timed steps (wall clock around each, device synchronised)
     e2e = None
     kept = None
     if not args.no_e2e:
-        G_host = np.empty((nw, o, o), dtype=np.complex128)
-        A_host = np.empty(nw)
+        keep_alive = []
+        host_fields = {}
+        for k in inp.__dataclass_fields__:
+            a = getattr(inp, k)
+            if isinstance(a, np.ndarray):
+                view, t = pinned_copy(np.ascontiguousarray(a))
+                keep_alive.append(t)
+                host_fields[k] = view
+            else:
+                host_fields[k] = a
+        host_inputs = synth.Inputs(**host_fields)
+        G_host, tg = pinned_empty((nw, npp, npp), torch.complex128)
+        A_host, ta = pinned_empty((nw,), torch.float64)
+        keep_alive += [tg, ta]
+        n_e2e = max(1, min(args.steps, args.e2e_steps))
+        step(host_inputs, G_host, A_host)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, _, kept = step(inp, G_host, A_host, keep=True)
-        torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
+        times = []
+        G.profile(True)
+        for k in range(n_e2e):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, kc = step(host_inputs, G_host, A_host, keep=(k == n_e2e - 1))
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            if kc is not None:
+                kept = kc
+        e2e_phases = {"input_upload": G.profile_read(27)[1] / n_e2e, "output_copies": G.profile_read(28)[1] / n_e2e,
+                      "hbar_build": G.profile_read(8)[1] / n_e2e}
+        G.profile(False)
+        e2e_s = statistics.median(times)
         h2d = sum(getattr(inp, k).nbytes for k in ("eps", "oooo", "ooov", "oovv", "ovov", "ovvv", "t1", "t2", "l1", "l2"))
-        e2e = {"value": nw * o / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(G_host.nbytes + A_host.nbytes)}
+        e2e = {"value": nw * npp / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(G_host.nbytes + A_host.nbytes), "steps": n_e2e, "warmup": 1,
+               "median_s": e2e_s, "min_s": min(times), "max_s": max(times),
+               "host_memory": "page-locked (pinned) input and output arrays",
+               "phases_ms": {k: round(val, 1) for k, val in e2e_phases.items()},
+               "h2d_gbs": h2d / (e2e_phases["input_upload"] / 1e3) / 1e9 if e2e_phases["input_upload"] > 0 else None}
+        if kept is not None:
+            e2e["G_matches_device_run"] = bool(np.array_equal(G_host, G_dev.cpu().numpy()))
 
-    # untimed by the line's value: full-dimension FP64 solves at a subset of the output grid (plus the
-    # frequency the oracle sample uses), their own rate, and the reduced model's error against them
+    # untimed by the line's value: full-dimension FP64-accurate solves at a stratified subset of the output
+    # grid (every full_stride-th point), at every sampled frequency and at the oracle sample's frequency;
+    # their own rate, and the reduced model's A and G errors against them
     full = None
-    if args.full_points > 0 and rank == 0:
+    if args.full_stride > 0 and rank == 0:
         if kept is None:
             _, _, kept = step(dev_inputs, G_dev, A_dev, keep=True)
         full = full_compare(args, kept, grid, porb, eta, stream)
@@ -245,7 +332,7 @@ def run_ours(args, rank, world):
 
     # max over ranks; every rank solved its own problem (weak scaling)
     dev_ms = max_over_ranks(dev_ms, dev, world)
-    value = job_value(nw, o, world, dev_ms)
+    value = job_value(nw, npp, world, dev_ms)
 
     peaks, peak_kind = measured_peaks()
     bf16 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
@@ -253,14 +340,16 @@ def run_ours(args, rank, world):
              1: "gemm_kernel<double> (FP64 SIMT GEMM)",
              2: "tc_gemm_kernel<bf16, exact> on exact slices (FP64-accurate residual / projection GEMMs)",
              11: f"tc_gemm_kernel<{args.precision}> ring-term GEMM of the inner sigma"}
-    ratio0 = 0.5 if args.precision == "tf32" else 1.0
+    ratio0 = TF32_OVER_BF16 if args.precision == "tf32" else 1.0
     kernels = {}
     for k, (n, ms, fl) in classes.items():
         if n == 0 or ms <= 0:
             continue
         ach = fl / (ms / 1e3) / 1e12
         if k == 1:
-            kernels[names[k]] = {"bound": "alu", "launches": n, "ms": ms, "achieved": ach, "unit": "TFLOP/s"}
+            kernels[names[k]] = {"bound": "alu", "launches": n, "ms": ms, "achieved": ach, "unit": "TFLOP/s",
+                                 "peak": OWN_PEAKS["fp64_tflops"], "frac": ach / OWN_PEAKS["fp64_tflops"],
+                                 "peak_kind": "FP64 DGEMM rate measured with --mode peaks (cuBLAS)"}
         else:
             pk = bf16 * (ratio0 if k in (0, 11) else 1.0)
             kernels[names[k]] = {"bound": "tensor", "launches": n, "ms": ms, "achieved": ach, "peak": pk,
@@ -278,20 +367,29 @@ def run_ours(args, rank, world):
         roof = {"kernel": names[dom], "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                 "frac": ach / pk, "traffic": tr["bytes_per_launch"] if tr else None,
                 "traffic_source": tr["source"] if tr else "no ncu capture of the current kernel source",
-                "peak_kind": f"{peak_kind} sustained bf16" + (f" x {ratio0} (tf32 rate)" if dom in (0, 11) and ratio0 != 1 else ""),
+                "peak_kind": f"{peak_kind} sustained bf16" + (f" x {ratio0:.4f} (nominal tf32/bf16 ratio)"
+                                                              if dom in (0, 11) and ratio0 != 1 else ""),
                 "launches": n, "avg_launch_ms": ms / n, "flops_per_launch": fl / n}
+        if dom in (0, 11) and args.precision == "tf32":
+            roof["frac_of_measured_tf32_sustained"] = ach / OWN_PEAKS["tf32_tflops_sustained"]
     return inp, {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dev_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": f"c128 (f64 residuals, {args.precision} tensor-core inner sigma)", "data": "synthetic",
-        "config": {"workload": args.workload, "o": o, "v": v, "D": inp.dim, "n_omega": nw, "n_p": o, "n_q": o,
+        "config": {"workload": args.workload, "o": o, "v": v, "D": inp.dim, "n_omega": nw, "n_p": npp, "n_q": npp,
+                   "p_set": "all spin-orbitals" if npp == o + v else "occupied spin-orbitals",
                    "eta": eta, "window_ha": [W["wmin"], W["wmax"]], "seeds": args.seeds, "mor_tol": args.mor_tol,
-                   "solve_tol": args.solve_tol, "restart": args.restart, "model_order": info["m"],
+                   "solve_tol": args.solve_tol, "restart": args.restart,
+                   "reduced_model": "one SISO model of G_pp per orbital" if args.siso else
+                   (f"block Krylov space of M on the b_p ({args.krylov} initial blocks)" if args.krylov > 0 else
+                    "one MIMO model"),
+                   "model_order": info["m"],
                    "sampled_freqs": len(info["sampled"]),
                    "arnoldi_steps": info["arnoldi_steps"], "columns_solved": info["columns"],
                    "l2": "working set (operators >= 0.5 GB, Krylov bases) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
-        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "gemm_classes": kernels, "phases_ms": phases,
+        "e2e": e2e, "gpu_launches": int(launches), "gpu_launches_per_step": int(launches // args.steps),
+        "roofline": roof, "gemm_classes": kernels, "phases_ms": phases,
         "hbm_kernels": {"arnoldi_cgs_sweeps (multidot_kernel, cgs_update_kernel x2)": {
             "bound": "hbm", "steps": cgs[0], "ms": cgs[1], "algorithmic_bytes": cgs[2],
             "achieved": cgs[2] / (cgs[1] / 1e3) / 1e9 if cgs[1] > 0 else None, "unit": "GB/s",
@@ -300,6 +398,7 @@ def run_ours(args, rank, world):
             "parts": {name: {"launches": n, "ms": round(ms, 2), "achieved_gbs": round(b / (ms / 1e3) / 1e9, 1)
                              if ms > 0 else None} for name, (n, ms, b) in cgs_parts.items()}}},
         "clocks": clk,
+        "spectrum": spectrum,
         "full_fp64": full,
     }
 
@@ -326,15 +425,18 @@ def rank_seed(base_seed: int, rank: int) -> int:
 
 
 def full_compare(args, ctx, grid, porb, eta, stream):
-    """Full-dimension FP64-accurate GMRES-IR solves (inner and residual sigma on exact bf16 slices) at
-    full_points frequencies of the output grid plus the middle of the window; returns their G points/s
-    and the reduced model's A and G errors against them (normwise relative, max over the subset)."""
+    """Full-dimension FP64-accurate GMRES-IR solves (inner and residual sigma on exact bf16 slices) at every
+    full_stride-th frequency of the output grid, at every frequency the reduced model sampled and at the
+    middle of the window; returns their G points/s and the reduced model's A and G errors against them
+    (normwise relative: max over the subset of |error| / max |full|)."""
     import torch
     W = synth.WORKLOADS[args.workload]
     nw = len(grid)
-    idx = np.unique(np.linspace(0, nw - 1, args.full_points).round().astype(int))
+    w_grid = grid[::args.full_stride]
+    sampled = np.asarray(ctx.mor_info()["sampled"])
     w_mid = 0.5 * (W["wmin"] + W["wmax"])
-    sub = np.concatenate([grid[idx], [w_mid]])
+    sub = np.concatenate([w_grid, sampled, [w_mid]])
+    ng, ns = len(w_grid), len(sampled)
     ctx.set_opts(tol=args.solve_tol, precision="fp64_tc")
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -346,12 +448,21 @@ def full_compare(args, ctx, grid, porb, eta, stream):
     mor = ctx.mor_eval(sub)
     Af, Gf = r["A"], r["G"]
     st = r["stats"]
+    if args.siso:   # per-orbital models give the diagonal G_pp only: compare those
+        Gf = np.diagonal(Gf, axis1=1, axis2=2)[:, :, None]
+        mor = dict(mor, G=np.diagonal(mor["G"], axis1=1, axis2=2)[:, :, None])
+
+    def err(a, b):
+        return float(np.abs(a - b).max() / np.abs(b).max())
+
     return {"value": len(sub) * len(porb) / (ms / 1e3), "unit": UNIT, "ms": ms, "n_omega": int(len(sub)),
             "n_p": len(porb), "solver": "GMRES-IR, FP64-accurate inner and residual sigma (exact bf16 slices)",
             "converged": bool(r["converged"]), "max_rel_res": st.max_rel_res, "gmres_iters": st.gmres_iters,
-            "mor_A_rel_err": float(np.abs(mor["A"] - Af).max() / np.abs(Af).max()),
-            "mor_G_rel_err": float(np.abs(mor["G"] - Gf).max() / np.abs(Gf).max()),
-            "omegas": "every %d-th point of the output grid and w = %.2f Ha" % (max(1, nw // args.full_points), w_mid),
+            "mor_A_rel_err": err(mor["A"][:ng], Af[:ng]), "mor_G_rel_err": err(mor["G"][:ng], Gf[:ng]),
+            "mor_A_rel_err_at_samples": err(mor["A"][ng:ng + ns], Af[ng:ng + ns]) if ns else None,
+            "mor_G_rel_err_at_samples": err(mor["G"][ng:ng + ns], Gf[ng:ng + ns]) if ns else None,
+            "omegas": f"{ng} points (every {args.full_stride}-th of the {nw}-point output grid), the {ns} sampled "
+                      f"frequencies and w = {w_mid:.2f} Ha",
             "_G_mid": Gf[-1], "_G_mor_mid": mor["G"][-1]}
 
 
@@ -389,7 +500,7 @@ def run_sigma(args):
     step_ms = e0.elapsed_time(e1) / args.steps
     peaks, kind = measured_peaks()
     bf16 = peaks.get("bf16_tflops", 1900.0)
-    pk = bf16 * (0.5 if args.precision == "tf32" else 1.0)
+    pk = bf16 * (TF32_OVER_BF16 if args.precision == "tf32" else 1.0)
     ach = fl / (ms / 1e3) / 1e12 if ms else None
     return {"metric": "sigma complex columns/s", "value": args.nvec / (step_ms / 1e3), "unit": "columns/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
@@ -398,10 +509,52 @@ def run_sigma(args):
             "algorithmic_tflops": flop / (step_ms / 1e3) / 1e12,
             "roofline": {"kernel": "tc_gemm_kernel ring-term GEMM", "bound": "tensor", "achieved": ach, "peak": pk,
                          "unit": "TFLOP/s", "frac": ach / pk if ach else None, "peak_kind": f"{kind} burst bf16" +
-                         (" x 0.5 (tf32 rate)" if args.precision == "tf32" else ""), "launches": n,
+                         (" x 1.1/2.25 (nominal tf32/bf16 ratio)" if args.precision == "tf32" else ""), "launches": n,
                          "avg_launch_ms": ms / n if n else None},
             "other_gemms": {"launches": n0, "ms": ms0,
                             "achieved": fl0 / (ms0 / 1e3) / 1e12 if ms0 else None}}
+
+
+def run_peaks(args):
+    """Dense GEMM rates of this GPU for the roofline denominators the driver does not measure: FP64 and
+    TF32 (and BF16 for comparison with the driver's figure), square GEMMs through torch.matmul (cuBLAS),
+    CUDA events on the launching stream; burst = best of 10, sustained = back to back for about 3 s."""
+    import torch
+    torch.cuda.set_device(0)
+    out = {"metric": "dense GEMM rate", "unit": "TFLOP/s", "mode": "peaks", "kernels": "cuBLAS via torch.matmul"}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for name, dt, n, tf32 in (("fp64", torch.float64, 8192, False), ("tf32", torch.float32, 8192, True),
+                              ("bf16", torch.bfloat16, 8192, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn((n, n), device="cuda").to(dt)
+        b = torch.randn((n, n), device="cuda").to(dt)
+        c = torch.empty((n, n), device="cuda", dtype=dt)
+        for _ in range(3):
+            torch.matmul(a, b, out=c)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        reps = max(3, int(3000.0 / best))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        fl = 2.0 * n ** 3
+        out[name] = {"n": n, "burst_tflops": fl / (best / 1e3) / 1e12,
+                     "sustained_tflops": fl * reps / (e0.elapsed_time(e1) / 1e3) / 1e12, "reps": reps}
+        del a, b, c
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out["clocks"] = clocks.stop()
+    return out
 
 
 def oracle_sample(args, ncols, inp=None):
@@ -418,29 +571,61 @@ def oracle_sample(args, ncols, inp=None):
     t0 = time.perf_counter()
     X, res = sv.gmres_solve(hb, B, w, W["eta"], tol=args.solve_tol)
     dt = time.perf_counter() - t0
-    Gq = sv.green(bc.c_vectors(inp, list(range(W["o"]))), X)[0]     # [ncols, o]: p = 0..ncols-1, q occupied
+    qset = orbital_set(args.workload, W["o"], W["o"] + W["v"])
+    Gq = sv.green(bc.c_vectors(inp, qset), X)[0]     # [ncols, nq]: p = 0..ncols-1
     return {"value": ncols / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{ncols} full-dimension FP64 GMRES solves (tol {args.solve_tol}) at w = {w[0]} Ha, "
+            "sample": f"{ncols} full-dimension FP64 GMRES solve(s) (tol {args.solve_tol}) at w = {w[0]} Ha, "
                       f"p = 0..{ncols - 1}, {args.workload}; H-bar build and input generation untimed",
             "seconds": dt, "_G": Gq}
 
 
 def run_reference(args):
-    vals = []
-    for _ in range(args.warmup):
-        pass   # the oracle has no warm-up effects worth a full sample; samples are bounded
-    for _ in range(max(1, args.steps)):
-        r = oracle_sample(args, args.cpu_sample)
-        r.pop("_G", None)
-        vals.append(r)
-    v = statistics.median(x["value"] for x in vals)
-    cb = dict(vals[0])
-    cb["value"] = v
+    """The oracle on the host cores, in bounded steps. Set-up (untimed): inputs, the oracle's H-bar
+    build, and one full GMRES solve of (w_mid, p = 0) that gives the number of operator applications a
+    G point costs. Each warm-up and timed step then runs ref_iters GMRES iterations of the same system
+    (the oracle's own solver, capped), i.e. a known fraction of one G point; value = that fraction / the
+    median step time, in G points per second."""
+    from oracle import bc, hbar
+    from oracle import sigma as sg
+    from oracle import solve as sv
     W = synth.WORKLOADS[args.workload]
+    inp = synth.make_inputs(W["o"], W["v"], W["seed"])
+    hb = hbar.build(inp)
+    b0 = bc.b_vectors(inp, [0])[0]
+    w = 0.5 * (W["wmin"] + W["wmax"])
+    diag = sg.diagonal(hb)
+    calls = [0]
+
+    def mv(x):
+        calls[0] += 1
+        return sg.sigma(hb, x)
+
+    t0 = time.perf_counter()
+    _, hist, ok = sv.gmres(mv, b0, w - 1j * W["eta"], diag, tol=args.solve_tol, restart=30, maxiter=3000)
+    t_full = time.perf_counter() - t0
+    n_full = calls[0]
+    times, fracs = [], []
+    for k in range(args.warmup + max(1, args.steps)):
+        calls[0] = 0
+        t0 = time.perf_counter()
+        sv.gmres(mv, b0, w - 1j * W["eta"], diag, tol=args.solve_tol, restart=30, maxiter=args.ref_iters)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            fracs.append(calls[0] / n_full)
+    t_med = statistics.median(times)
+    v = statistics.median(fracs) / t_med
+    cb = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+          "sample": f"{args.workload}, w = {w} Ha, p = 0: per step {args.ref_iters} GMRES iterations of the oracle "
+                    f"({int(round(statistics.median(fracs) * n_full))} of the {n_full} operator applications of the "
+                    f"full solve to tol {args.solve_tol}, which took {t_full:.1f} s untimed); inputs and H-bar build "
+                    f"untimed", "full_solve_s": t_full, "full_solve_converged": bool(ok),
+          "step_s_median": t_med}
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": t_med * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": args.workload, "o": W["o"], "v": W["v"]}, "cpu_baseline": cb,
+            "config": {"workload": args.workload, "o": W["o"], "v": W["v"], "D": inp.dim, "eta": W["eta"]},
+            "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -454,6 +639,9 @@ def main():
         return
     if args.mode == "sigma":
         print(json.dumps(run_sigma(args)), flush=True)
+        return
+    if args.mode == "peaks":
+        print(json.dumps(run_peaks(args)), flush=True)
         return
     if world > 1:
         import torch.distributed as dist
@@ -471,8 +659,10 @@ def main():
                     out["oracle_check"] = {
                         "points": int(Go.size), "omega": 0.5 * (synth.WORKLOADS[args.workload]["wmin"] +
                                                                 synth.WORKLOADS[args.workload]["wmax"]),
-                        "full_fp64_G_rel_err": float(np.abs(full["_G_mid"][:k] - Go).max() / scale),
-                        "mor_G_rel_err": float(np.abs(full["_G_mor_mid"][:k] - Go).max() / scale)}
+                        "full_fp64_G_rel_err": None if args.siso else float(np.abs(full["_G_mid"][:k] - Go).max() / scale),
+                        "mor_G_rel_err": float(np.abs(full["_G_mor_mid"][:k, 0] - Go[np.arange(k), np.arange(k)]).max()
+                                               / scale) if args.siso else
+                        float(np.abs(full["_G_mor_mid"][:k] - Go).max() / scale)}
                 out["cpu_baseline"] = cb
             except Exception as e:  # the baseline must not hide the GPU line
                 out["cpu_baseline"] = {"error": str(e)}

@@ -135,6 +135,19 @@ int gfcc_solve_full(gfcc_t ctx, const double* omegas, int nw, double eta, const 
                     int np, const int* qorb, int nq, double* G, double* A, double* X, int ldx,
                     gfcc_stats* stats);
 
+/* Spectral function A(w) = -(1/pi) sum_p Im G_pp(w) (the definition after Eq. gfxn0, returned as
+ * written) from G [nw][np][nq] complex laid out as in gfcc_solve_full: the sum runs over the orbitals p
+ * of the p set that also appear in the q set (qorb NULL: the same set, nq ignored).
+ *   adjoint = 0: reads G, writes A[nw].
+ *   adjoint = 1: the adjoint map (the vector-Jacobian product of a backward pass): reads A as the
+ *                upstream gradient Abar[nw] and writes G[w][p][q] = -(i/pi) Abar[w] where q is the
+ *                position of p in the q set, 0 elsewhere.
+ * G and A: host or device (copied with cudaMemcpyDefault); stream: cudaStream_t or NULL. The call
+ * returns when the result has been written. No context is needed.
+ * Errors: GFCC_ERR_ARG (null pointers, empty orbital sets), GFCC_ERR_OOM, GFCC_ERR_CUDA. */
+int gfcc_spectral(const double* G, int nw, const int* orbitals, int np, const int* qorb, int nq, double* A,
+                  int adjoint, void* stream);
+
 /* Derivatives of G_pq(w) (Eq. gfcclineqn) with respect to the frequency and the broadening. With
  * A(w) = w - i eta + M, x_p = A^{-1} b_p (forward solves, as gfcc_solve_full) and the adjoint solutions
  * y_q = A^{-T} c_q (transposed sigma), G_pq = c_q^T x_p, dG_pq/dw = -y_q^T x_p and dG_pq/deta = i y_q^T x_p.
@@ -165,6 +178,40 @@ int gfcc_green_grad_t2(gfcc_t ctx, const double* omegas, int nw, double eta, con
  * Hhat = S^H M S, bhat = S^H b, chat = c^T S. qorb/nq as in gfcc_solve_full. */
 int gfcc_mor_build(gfcc_t ctx, const double* seeds, int ns, double eta, const int* orbitals,
                    int np, const int* qorb, int nq);
+
+/* Per-orbital (single-input single-output) reduced models of the diagonal elements G_pp, the variant
+ * the paper's conclusion proposes (separate models for the diagonal elements): for each orbital p of
+ * orbitals (host, np distinct entries) a model as in gfcc_mor_build with the single orbital p as both
+ * p and q set, its subspace spanned by X_p(w_k) alone. All models start from the same seeds; their
+ * seed solutions run as one batched solve. gfcc_mor_refine then refines every model on its own
+ * frequencies (all models' new solutions again in one batched solve per round; m_max bounds each
+ * model's order; the derivative indicator is not available), gfcc_mor_eval writes Ghat_pp on the
+ * diagonal of G [nw][np][np] (zeros elsewhere), A from those diagonals and maxres as the max over the
+ * models; gfcc_mor_info reports the union of the sampled frequencies and the total order, and
+ * gfcc_mor_model_info each model. gfcc_mor_build replaces such a set by one MIMO model; sets are not
+ * saved by gfcc_mor_save (GFCC_ERR_STATE).
+ * Errors: GFCC_ERR_ARG (bad seeds, eta, orbitals), GFCC_ERR_RANK (all seed solutions of an orbital
+ * dropped), GFCC_ERR_NOT_CONVERGED, GFCC_ERR_CUDA. */
+int gfcc_mor_build_siso(gfcc_t ctx, const double* seeds, int ns, double eta, const int* orbitals, int np);
+
+/* Reduced model on a block Krylov subspace instead of solutions at sampled frequencies (multi-shift
+ * reuse; not in the paper, next to its Eq. model): S = orth[B, M B, ..., M^(k-1) B] for B = [b_p], k =
+ * nblocks, each block orthonormalised against the previous ones as in gfcc_mor_build (columns that fall
+ * below opts.drop_tol are dropped, and the next block starts from M applied to the kept ones), with
+ * M X from the FP64-accurate sigma (opts.residual_precision). The Krylov space of M is that of every
+ * shifted matrix w - i eta + M, so the Galerkin model Hhat = S^H M S, bhat, chat gives the block FOM
+ * solution of Eq. xplin at every frequency from one subspace. gfcc_mor_refine on such a model adds
+ * max(1, floor(k/4)) blocks per round until the largest residual estimate over all its grid points is
+ * <= tol (m_max bounds the order; no derivative indicator); gfcc_mor_eval, gfcc_mor_info (no sampled
+ * frequencies) and gfcc_mor_model_info work as for gfcc_mor_build; gfcc_mor_save returns
+ * GFCC_ERR_STATE. orbitals / qorb as in gfcc_mor_build.
+ * Errors: GFCC_ERR_ARG, GFCC_ERR_RANK (empty subspace), GFCC_ERR_CUDA. */
+int gfcc_mor_build_krylov(gfcc_t ctx, int nblocks, double eta, const int* orbitals, int np, const int* qorb, int nq);
+
+/* Model k of the current set (a per-orbital set: k < np; a MIMO model: k = 0): its orbital (-1 for a
+ * MIMO model), up to cap sampled frequencies (host), their count and the model order. Any output
+ * pointer may be NULL. GFCC_ERR_ARG if there is no model k. */
+int gfcc_mor_model_info(gfcc_t ctx, int k, int* orbital, double* w, int cap, int* ns, int* m);
 
 /* Adaptive refinement (MOR text after Eq. model): on a uniform grid of ngrid points over
  * [wmin, wmax], estimate for each interval between adjacent sampled frequencies the largest relative
@@ -208,14 +255,16 @@ int gfcc_tc_gemm(int precision, const double* A, const double* B, int M, int N, 
 /* Allocation-free variant of gfcc_tc_gemm, for callers that cannot allocate device memory at the
  * point of the call (a framework that owns all device memory, a path where the device-wide
  * synchronisation of cudaMalloc/cudaFree is not acceptable, code that must not hit out-of-memory
- * after start-up). The paper has no counterpart. A, B, C are device pointers (row-major
- * A[M][K], B[N][K], C[M][N]); stream is a cudaStream_t or NULL; the call returns after the product
- * is complete. The rounded operand copies and the error flag live in a fixed 32 MiB __device__
+ * after start-up). The paper has no counterpart. A, B, C are device pointers on the current device
+ * (row-major A[M][K], B[N][K], C[M][N]); C must be 16-byte aligned (GFCC_ERR_ARG otherwise, before any
+ * device work); stream is a cudaStream_t or NULL. The call is synchronous: it waits on the stream and
+ * returns after the product is complete. The rounded operand copies and the error flag live in a fixed 32 MiB __device__
  * array inside the library, reserved on every GPU that loads it until the process exits: the call
  * allocates nothing, and rejects with GFCC_ERR_ARG any size whose two rounded operands (K padded
  * to 64 bf16 or 32 tf32 elements, each copy rounded up to 256 bytes) plus 256 bytes do not fit.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture. All calls share the array: calls whose work overlaps on a
+ * first call before any stream capture. The address is kept for the life of the CUDA context: do not
+ * call this entry point on a device after resetting it (cudaDeviceReset). All calls share the array: calls whose work overlaps on a
  * GPU (different streams or threads) race and must be serialised by the caller. */
 int gfcc_tc_gemm_noalloc(int precision, const double* A, const double* B, int M, int N, int K, float* C,
                          void* stream);
@@ -237,7 +286,9 @@ long long gfcc_launch_count(void);
  * HBM bytes in the "flops" field); 19 Householder reductions of Hhat to Hessenberg form; 20 the
  * per-frequency shifted Hessenberg solves; 21, 22 the coefficient products and updates of the block
  * Gram-Schmidt passes; 23 the Cholesky QR of the panels; 24 the accumulation and output passes of the
- * exact-slice products; 25 the operand preparation and 26 the combine pass of the low-precision sigma.
+ * exact-slice products; 25 the operand preparation and 26 the combine pass of the low-precision sigma;
+ * 27 the copies of the caller's inputs to the device in gfcc_init; 28 the copies of results into the
+ * caller's output buffers (device to host for host buffers).
  * Events are recorded on the stream each region is launched on. */
 int gfcc_profile(int enable);
 

@@ -214,3 +214,84 @@ def build_and_refine(hb, B: np.ndarray, C: np.ndarray, seeds, wmin: float, wmax:
         rm = project(hb, S, B, C)
     rm.sampled = sampled
     return MorResult(model=rm, sampled=sampled, history=history, converged=converged)
+
+
+def build_and_refine_siso(hb, B: np.ndarray, C: np.ndarray, seeds, wmin: float, wmax: float, ngrid: int,
+                          eta: float, tol: float, m_max: int, solver="dense", M: np.ndarray | None = None,
+                          solve_tol: float = 1e-10) -> list:
+    """Separate single-input single-output reduced models of the diagonal elements G_pp (the conclusion's
+    proposal): for every orbital p (row p of B and of C, the same orbital), the adaptive reduced model
+    above built from X_p(w_k) alone, with b_p as its only input and c_p as its only output. Returns one
+    MorResult per orbital; each model refines its own frequencies, and m_max bounds each model's order."""
+    return [build_and_refine(hb, B[p:p + 1], C[p:p + 1], seeds, wmin, wmax, ngrid, eta, tol, m_max,
+                             solver=solver, M=M, solve_tol=solve_tol) for p in range(B.shape[0])]
+
+
+def siso_green(results: list, omegas, eta: float) -> np.ndarray:
+    """G[w, p, q] with Ghat_pp of the per-orbital models on the diagonal and zeros elsewhere."""
+    npp = len(results)
+    G = np.zeros((len(omegas), npp, npp), dtype=complex)
+    for p, r in enumerate(results):
+        G[:, p, p] = reduced_green(r.model, omegas, eta)[:, 0, 0]
+    return G
+
+
+class KrylovState:
+    """Block Krylov basis under construction: S (orthonormal columns so far), X (the next block to add),
+    blocks added, and the number of columns the newest block kept."""
+
+    def __init__(self, B: np.ndarray):
+        self.S = None
+        self.X = B.T.astype(complex)                     # first block: [D, np]
+        self.blocks = 0
+        self.newest = 0
+
+    @property
+    def m(self) -> int:
+        return 0 if self.S is None else self.S.shape[1]
+
+    def extend(self, hb, nblocks: int, m_max: int, drop_tol: float = 1e-10) -> None:
+        """Add up to nblocks blocks; stop before a block whose columns would exceed m_max, or when the
+        space is invariant (a block keeps no column). Each block is orthonormalised against the basis
+        (two classical Gram-Schmidt passes per column, rank truncation as in orthonormalise); the next
+        block is M applied to the columns just kept."""
+        for _ in range(nblocks):
+            if self.X.shape[1] == 0 or self.m + self.X.shape[1] > m_max:
+                return
+            m0 = self.m
+            self.S, _ = orthonormalise(self.S, self.X, drop_tol)
+            self.blocks += 1
+            self.newest = self.S.shape[1] - m0
+            self.X = sg.sigma(hb, self.S[:, m0:].T).T    # M times the new orthonormal columns
+            if self.newest == 0:
+                return
+
+
+def build_krylov(hb, B: np.ndarray, C: np.ndarray, nblocks: int, drop_tol: float = 1e-10):
+    """Reduced model on the block Krylov space K_k(M, B) = span[B, M B, ..., M^(k-1) B], k = nblocks
+    (multi-shift reuse: the space is the same for every shifted matrix w - i eta + M)."""
+    st = KrylovState(B)
+    st.extend(hb, nblocks, 2 ** 31 - 1, drop_tol)
+    return project(hb, st.S, B, C), st
+
+
+def refine_krylov(hb, B: np.ndarray, C: np.ndarray, nblocks0: int, wmin: float, wmax: float, ngrid: int,
+                  eta: float, tol: float, m_max: int, drop_tol: float = 1e-10):
+    """Grow the Krylov model until the largest relative residual over the whole grid is <= tol: each round
+    adds max(1, floor(k/4)) blocks (k the blocks so far) within the order bound m_max. Returns (model,
+    KrylovState, history of (m, max residual), converged)."""
+    grid = np.linspace(wmin, wmax, ngrid)
+    st = KrylovState(B)
+    st.extend(hb, nblocks0, 2 ** 31 - 1, drop_tol)
+    rm = project(hb, st.S, B, C)
+    history = []
+    while True:
+        e = float(residuals(rm, B, grid, eta).max())
+        history.append((rm.m, e))
+        if e <= tol:
+            return rm, st, history, True
+        m0 = st.m
+        st.extend(hb, max(1, st.blocks // 4), m_max, drop_tol)
+        if st.m == m0:
+            return rm, st, history, False
+        rm = project(hb, st.S, B, C)

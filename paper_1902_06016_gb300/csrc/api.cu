@@ -26,6 +26,7 @@ bool is_device_ptr(const void* p) {
 }
 
 void copy_out(void* dst, const void* src_dev, size_t n, cudaStream_t s) {
+  gfcc::ProfScope prof(gfcc::PROF_DOWNLOAD, 0.0, s);
   GFCC_CUDA(cudaMemcpyAsync(dst, src_dev, n, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
 }
 
@@ -47,6 +48,15 @@ __global__ void spectral_kernel(const cplx* G, int nw, int np, int nq, const int
   for (int p = 0; p < np; ++p)
     if (qidx[p] >= 0) s += G[((long long)w * np + p) * nq + qidx[p]].y;
   A[w] = -s / 3.14159265358979323846;
+}
+
+// Gbar[w][p][q] = -(i/pi) Abar[w] where q = qidx[p] >= 0, 0 elsewhere (adjoint of spectral_kernel)
+__global__ void spectral_adjoint_kernel(const double* Abar, int nw, int np, int nq, const int* qidx, cplx* Gbar) {
+  const long long total = (long long)nw * np * nq;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int w = (int)(t / ((long long)np * nq)), p = (int)((t / nq) % np), q = (int)(t % nq);
+    Gbar[t] = make_cuDoubleComplex(0.0, qidx[p] == q ? -Abar[w] / 3.14159265358979323846 : 0.0);
+  }
 }
 
 // MX = B - shift X - R   (all batch-minor [D][nb])
@@ -115,15 +125,15 @@ std::vector<int> q_positions(const std::vector<int>& porb, const std::vector<int
   return qi;
 }
 
-// Solve all (w, p) columns; writes X (batch-minor, [D][ncols]) and R into caller-provided device
-// buffers when non-null, and G [ncols][nq] when Gdev is non-null.
-void solve_columns(gfcc_ctx* c, const std::vector<double>& ws, double eta, const std::vector<int>& porb,
-                   const std::vector<int>& qorb, cplx* Gdev, cplx* Xall, cplx* Rall, gfcc_stats* st_out,
-                   const cplx* X0all = nullptr) {
+// Solve the columns (wcol[k] - i eta + M) x_k = b_{pcol[k]}; writes X (batch-minor, [D][ncols]) and R
+// into caller-provided device buffers when non-null, and G [ncols][nq] when Gdev is non-null.
+void solve_pairs(gfcc_ctx* c, const std::vector<double>& wcol, const std::vector<int>& pcol, double eta,
+                 const std::vector<int>& qorb, cplx* Gdev, cplx* Xall, cplx* Rall, gfcc_stats* st_out,
+                 const cplx* X0all = nullptr) {
   cudaStream_t s = c->stream;
   const long long D = c->D;
-  const int np = (int)porb.size(), nq = (int)qorb.size();
-  const long long ncols = (long long)ws.size() * np;
+  const int nq = (int)qorb.size();
+  const long long ncols = (long long)wcol.size();
   const int nbmax = choose_batch(c, ncols);
   c->stats = gfcc::Stats{};
   DBuf<cplx> B, X, R, sh, X0;
@@ -136,9 +146,9 @@ void solve_columns(gfcc_ctx* c, const std::vector<double>& ws, double eta, const
     std::vector<int> hr(nb);
     std::vector<cplx> hs(nb);
     for (int k = 0; k < nb; ++k) {
-      long long col = c0 + k;
-      hr[k] = porb[col % np];
-      hs[k] = make_cuDoubleComplex(ws[col / np], -eta);
+      const long long col = c0 + k;
+      hr[k] = pcol[col];
+      hs[k] = make_cuDoubleComplex(wcol[col], -eta);
     }
     GFCC_CUDA(cudaMemcpyAsync(rows.p, hr.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s));
     GFCC_CUDA(cudaMemcpyAsync(sh.p, hs.data(), sizeof(cplx) * nb, cudaMemcpyHostToDevice, s));
@@ -175,6 +185,20 @@ void solve_columns(gfcc_ctx* c, const std::vector<double>& ws, double eta, const
     st_out->max_rel_res = maxres;
     st_out->not_converged = notconv;
   }
+}
+
+// Solve all (w, p) columns, column w * np + p (see solve_pairs).
+void solve_columns(gfcc_ctx* c, const std::vector<double>& ws, double eta, const std::vector<int>& porb,
+                   const std::vector<int>& qorb, cplx* Gdev, cplx* Xall, cplx* Rall, gfcc_stats* st_out,
+                   const cplx* X0all = nullptr) {
+  const size_t np = porb.size();
+  std::vector<double> wcol(ws.size() * np);
+  std::vector<int> pcol(ws.size() * np);
+  for (size_t k = 0; k < wcol.size(); ++k) {
+    wcol[k] = ws[k / np];
+    pcol[k] = porb[k % np];
+  }
+  solve_pairs(c, wcol, pcol, eta, qorb, Gdev, Xall, Rall, st_out, X0all);
 }
 
 // Adjoint solves (w - i eta + M)^T y = c_q for every (w, q): columns (w, q) of Yall [D][nw*nq].
@@ -288,6 +312,158 @@ void mor_add_frequencies(gfcc_ctx* c, const std::vector<double>& ws) {
   gfcc::mor_append(c, X.p, MX.p, (int)ncols);
   for (double w : ws) ms.sampled.push_back(w);
   std::sort(ms.sampled.begin(), ms.sampled.end());
+}
+
+// ---- block Krylov subspace (multi-shift reuse) ------------------------------------------------
+// Extend the subspace of a kind-1 model by up to nblocks Krylov blocks: the next block is M applied to
+// the newest orthonormal block (its columns of Z = M S), or B for the first one; each block's images
+// M X come from the FP64-accurate sigma. The space K_k(M, B) is the same for every shift w - i eta, so the
+// Galerkin model over it gives the block FOM solution of Eq. xplin at every frequency at once.
+void krylov_extend(gfcc_ctx* c, int nblocks, int m_max) {
+  gfcc::MorState& ms = c->mor;
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  const int np = (int)ms.porb.size();
+  int prec = c->opts.residual_precision;
+  if (prec < 0) prec = c->opts.precision == GFCC_PREC_FP64 ? GFCC_PREC_FP64 : GFCC_PREC_FP64_TC;
+  DBuf<cplx> X, MX;
+  for (int j = 0; j < nblocks; ++j) {
+    const int nc = ms.kblocks == 0 ? np : ms.knext;
+    if (nc == 0 || ms.m + nc > m_max) break;
+    X.alloc(D * nc);
+    MX.alloc(D * nc);
+    if (ms.kblocks == 0) {
+      DBuf<int> rows;
+      rows.alloc(np);
+      GFCC_CUDA(cudaMemcpyAsync(rows.p, ms.porb.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+      gfcc::gather_rows_real_to_cplx(c->bvec.p, (int)D, rows.p, np, (int)D, X.p, np, s);
+      GFCC_CUDA(cudaStreamSynchronize(s));
+    } else {
+      GFCC_CUDA(cudaMemcpy2DAsync(X.p, sizeof(cplx) * nc, ms.Z.p + (ms.m - nc), sizeof(cplx) * ms.m_cap,
+                                  sizeof(cplx) * nc, D, cudaMemcpyDeviceToDevice, s));
+    }
+    gfcc::sigma_batch(c, X.p, MX.p, nc, nc, nullptr, prec, false, s);
+    const int m0 = ms.m;
+    gfcc::mor_append(c, X.p, MX.p, nc);
+    ms.knext = ms.m - m0;
+    ++ms.kblocks;
+    if (ms.knext == 0) break;   // the Krylov space is invariant: nothing new to add
+  }
+  if (prec != GFCC_PREC_FP64) {
+    GFCC_CHECK(gfcc::emulated_error(c) == 0, GFCC_ERR_CUDA, "exact-slice sigma: tensor-core pipeline wait timed out");
+  }
+}
+
+// ---- per-orbital (SISO) reduced models -------------------------------------------------------
+// Model k of c->siso is an ordinary reduced model with the single orbital p = q = porb_k; the routines of
+// mor.cu act on c->mor, so a model is swapped into c->mor for the duration of each call on it.
+struct ModelSwap {
+  gfcc_ctx* c;
+  gfcc::MorState* m;
+  ModelSwap(gfcc_ctx* c_, gfcc::MorState* m_) : c(c_), m(m_) { std::swap(c->mor, *m); }
+  ~ModelSwap() { std::swap(c->mor, *m); }
+  ModelSwap(const ModelSwap&) = delete;
+  ModelSwap& operator=(const ModelSwap&) = delete;
+};
+
+// Solve every (model k, w) pair of add (sorted by model, then frequency) in one batched solve and append
+// each model's solutions to its own subspace.
+void siso_add_frequencies(gfcc_ctx* c, const std::vector<std::pair<int, double>>& add, double eta) {
+  cudaStream_t s = c->stream;
+  const long long D = c->D;
+  const long long ncols = (long long)add.size();
+  if (ncols == 0) return;
+  std::vector<double> wcol(ncols);
+  std::vector<int> pcol(ncols);
+  std::vector<long long> first(c->siso.size() + 1, 0);   // columns [first[k], first[k+1]) belong to model k
+  for (long long j = 0; j < ncols; ++j) {
+    wcol[j] = add[j].second;
+    pcol[j] = c->siso[add[j].first].porb[0];
+    ++first[add[j].first + 1];
+  }
+  for (size_t k = 0; k < c->siso.size(); ++k) first[k + 1] += first[k];
+  DBuf<cplx> X, R, MX, B, sh, X0, Xk, MXk;
+  DBuf<int> rows;
+  X.alloc(D * ncols); R.alloc(D * ncols); MX.alloc(D * ncols); B.alloc(D * ncols); sh.alloc(ncols);
+  rows.alloc(ncols);
+  if (c->opts.mor_guess) {   // each model's prediction x0_p(w) = S yhat_p(w) at its new frequencies
+    X0.alloc(D * ncols);
+    for (size_t k = 0; k < c->siso.size(); ++k) {
+      const long long nk = first[k + 1] - first[k];
+      if (nk == 0) continue;
+      DBuf<cplx> tmp;
+      tmp.alloc(D * nk);
+      {
+        ModelSwap sw(c, &c->siso[k]);
+        gfcc::mor_extrapolate(c, wcol.data() + first[k], (int)nk, tmp.p);
+      }
+      GFCC_CUDA(cudaMemcpy2DAsync(X0.p + first[k], sizeof(cplx) * ncols, tmp.p, sizeof(cplx) * nk, sizeof(cplx) * nk, D,
+                                  cudaMemcpyDeviceToDevice, s));
+      GFCC_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+  solve_pairs(c, wcol, pcol, eta, {}, nullptr, X.p, R.p, nullptr, c->opts.mor_guess ? X0.p : nullptr);
+  c->siso_iters += c->stats.gmres_iters;
+  c->siso_cols += ncols;
+  std::vector<cplx> hs(ncols);
+  for (long long j = 0; j < ncols; ++j) hs[j] = make_cuDoubleComplex(wcol[j], -eta);
+  GFCC_CUDA(cudaMemcpyAsync(rows.p, pcol.data(), sizeof(int) * ncols, cudaMemcpyHostToDevice, s));
+  GFCC_CUDA(cudaMemcpyAsync(sh.p, hs.data(), sizeof(cplx) * ncols, cudaMemcpyHostToDevice, s));
+  gfcc::gather_rows_real_to_cplx(c->bvec.p, (int)D, rows.p, (int)ncols, (int)D, B.p, (int)ncols, s);
+  mx_kernel<<<grid_for(D * ncols), 256, 0, s>>>(B.p, X.p, R.p, sh.p, MX.p, D, (int)ncols);
+  GFCC_LAUNCH_CHECK();
+  for (size_t k = 0; k < c->siso.size(); ++k) {
+    const long long nk = first[k + 1] - first[k];
+    if (nk == 0) continue;
+    Xk.alloc(D * nk);
+    MXk.alloc(D * nk);
+    GFCC_CUDA(cudaMemcpy2DAsync(Xk.p, sizeof(cplx) * nk, X.p + first[k], sizeof(cplx) * ncols, sizeof(cplx) * nk, D,
+                                cudaMemcpyDeviceToDevice, s));
+    GFCC_CUDA(cudaMemcpy2DAsync(MXk.p, sizeof(cplx) * nk, MX.p + first[k], sizeof(cplx) * ncols, sizeof(cplx) * nk, D,
+                                cudaMemcpyDeviceToDevice, s));
+    GFCC_CUDA(cudaStreamSynchronize(s));
+    ModelSwap sw(c, &c->siso[k]);
+    gfcc::mor_append(c, Xk.p, MXk.p, (int)nk);
+    for (long long j = first[k]; j < first[k + 1]; ++j) c->mor.sampled.push_back(wcol[j]);
+    std::sort(c->mor.sampled.begin(), c->mor.sampled.end());
+  }
+}
+
+// interval error estimates of the current model c->mor on the grid (residual indicator, as in
+// gfcc_mor_refine): e[k] = largest relative residual estimate at grid points strictly inside
+// (sampled[k], sampled[k+1])
+std::vector<double> interval_errors(gfcc_ctx* c, const std::vector<double>& grid, DBuf<double>& dres) {
+  const int ngrid = (int)grid.size();
+  std::vector<double> res(ngrid);
+  gfcc::mor_eval(c, grid.data(), ngrid, nullptr, nullptr, dres.p);
+  GFCC_CUDA(cudaMemcpyAsync(res.data(), dres.p, sizeof(double) * ngrid, cudaMemcpyDeviceToHost, c->stream));
+  GFCC_CUDA(cudaStreamSynchronize(c->stream));
+  const std::vector<double>& smp = c->mor.sampled;
+  std::vector<double> e(smp.size() > 0 ? smp.size() - 1 : 0, 0.0);
+  for (size_t k = 0; k + 1 < smp.size(); ++k)
+    for (int g = 0; g < ngrid; ++g)
+      if (grid[g] > smp[k] && grid[g] < smp[k + 1]) e[k] = std::max(e[k], res[g]);
+  return e;
+}
+
+// midpoints of the intervals whose estimate is above tol, largest estimate first (ties: lower frequency),
+// at most max_new of them, returned in increasing order
+std::vector<double> choose_midpoints(const std::vector<double>& smp, const std::vector<double>& e, double tol,
+                                     int max_new) {
+  std::vector<std::pair<double, double>> cand;   // (-error, midpoint)
+  for (size_t k = 0; k < e.size(); ++k)
+    if (e[k] > tol) cand.push_back({-e[k], 0.5 * (smp[k] + smp[k + 1])});
+  std::sort(cand.begin(), cand.end());
+  std::vector<double> nw;
+  for (int k = 0; k < (int)cand.size() && k < max_new; ++k) nw.push_back(cand[k].second);
+  std::sort(nw.begin(), nw.end());
+  return nw;
+}
+
+// elementwise out[i] = max(out[i], x[i])
+__global__ void max_into_kernel(const double* __restrict__ x, double* __restrict__ out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = fmax(out[i], x[i]);
 }
 
 }  // namespace
@@ -606,6 +782,7 @@ int gfcc_mor_build(gfcc_t c, const double* seeds, int ns, double eta, const int*
   for (int k = 0; k < ns; ++k)
     if (!std::isfinite(seeds[k])) { c->last_error = "gfcc_mor_build: non-finite seed"; return GFCC_ERR_NONFINITE; }
   API_BEGIN
+  c->siso.clear();
   gfcc::MorState& ms = c->mor;
   ms.reset();
   ms.eta = eta;
@@ -637,30 +814,83 @@ int gfcc_mor_build(gfcc_t c, const double* seeds, int ns, double eta, const int*
 int gfcc_mor_refine(gfcc_t c, double wmin, double wmax, int ngrid, double tol, int m_max, int* m_out,
                     double* max_err) {
   if (!c) return GFCC_ERR_ARG;
-  if (!c->mor.built) { c->last_error = "gfcc_mor_refine: call gfcc_mor_build first"; return GFCC_ERR_STATE; }
+  if (!c->mor.built && c->siso.empty()) { c->last_error = "gfcc_mor_refine: call gfcc_mor_build first"; return GFCC_ERR_STATE; }
   if (!(wmax > wmin) || ngrid < 2 || !(tol > 0.0) || m_max < 1 || !std::isfinite(wmin) || !std::isfinite(wmax)) {
     c->last_error = "gfcc_mor_refine: bad arguments";
     return GFCC_ERR_ARG;
   }
+  if (!c->siso.empty() && c->opts.deriv_indicator) {
+    c->last_error = "gfcc_mor_refine: the derivative indicator is not available for per-orbital models";
+    return GFCC_ERR_ARG;
+  }
   API_BEGIN
-  gfcc::MorState& ms = c->mor;
-  const int np = (int)ms.porb.size();
   std::vector<double> grid(ngrid);
   for (int k = 0; k < ngrid; ++k) grid[k] = wmin + (wmax - wmin) * (double)k / (double)(ngrid - 1);
   DBuf<double> dres;
   dres.alloc(ngrid);
-  std::vector<double> res(ngrid);
   bool converged = false;
   double emax = 0.0;
+  if (!c->siso.empty()) {   // per-orbital models: each refines its own frequencies, all solved together
+    const double eta = c->siso[0].eta;
+    for (int round = 0; round < 10000; ++round) {
+      emax = 0.0;
+      std::vector<std::pair<int, double>> add;
+      for (size_t k = 0; k < c->siso.size(); ++k) {
+        ModelSwap sw(c, &c->siso[k]);
+        gfcc::MorState& ms = c->mor;
+        std::vector<double> e = interval_errors(c, grid, dres);
+        double ek = 0.0;
+        for (double x : e) ek = std::max(ek, x);
+        ms.history.push_back({ms.m, ek});
+        ms.last_max_err = ek;
+        emax = std::max(emax, ek);
+        if (ek <= tol) continue;
+        for (double w : choose_midpoints(ms.sampled, e, tol, m_max - ms.m)) add.push_back({(int)k, w});
+      }
+      if (emax <= tol) { converged = true; break; }
+      if (add.empty()) break;
+      siso_add_frequencies(c, add, eta);
+    }
+    int m = 0;
+    for (const gfcc::MorState& ms : c->siso) m += ms.m;
+    if (m_out) *m_out = m;
+    if (max_err) *max_err = emax;
+    if (!converged) {
+      c->last_error = "gfcc_mor_refine: model order bound reached before the tolerance";
+      return GFCC_ERR_NOT_CONVERGED;
+    }
+    return GFCC_OK;
+  }
+  gfcc::MorState& ms = c->mor;
+  const int np = (int)ms.porb.size();
+  if (ms.kind == 1) {   // Krylov subspace: grow it until the residual estimate meets tol on the whole grid
+    GFCC_CHECK(!c->opts.deriv_indicator, GFCC_ERR_ARG,
+               "gfcc_mor_refine: the derivative indicator needs sampled frequencies (not a Krylov model)");
+    std::vector<double> res(ngrid);
+    for (int round = 0; round < 100000; ++round) {
+      gfcc::mor_eval(c, grid.data(), ngrid, nullptr, nullptr, dres.p);
+      GFCC_CUDA(cudaMemcpyAsync(res.data(), dres.p, sizeof(double) * ngrid, cudaMemcpyDeviceToHost, c->stream));
+      GFCC_CUDA(cudaStreamSynchronize(c->stream));
+      emax = 0.0;
+      for (double x : res) emax = std::max(emax, x);
+      ms.history.push_back({ms.m, emax});
+      ms.last_max_err = emax;
+      if (emax <= tol) { converged = true; break; }
+      const int m0 = ms.m;
+      krylov_extend(c, std::max(1, ms.kblocks / 4), m_max);   // about 25 % more blocks per round
+      if (ms.m == m0) break;                                   // order bound reached or space exhausted
+    }
+    if (m_out) *m_out = ms.m;
+    if (max_err) *max_err = emax;
+    if (!converged) {
+      c->last_error = "gfcc_mor_refine: model order bound reached before the tolerance";
+      return GFCC_ERR_NOT_CONVERGED;
+    }
+    return GFCC_OK;
+  }
   for (int round = 0; round < 10000; ++round) {
-    gfcc::mor_eval(c, grid.data(), ngrid, nullptr, nullptr, dres.p);
-    GFCC_CUDA(cudaMemcpyAsync(res.data(), dres.p, sizeof(double) * ngrid, cudaMemcpyDeviceToHost, c->stream));
-    GFCC_CUDA(cudaStreamSynchronize(c->stream));
+    std::vector<double> e = interval_errors(c, grid, dres);
     const std::vector<double>& smp = ms.sampled;
-    std::vector<double> e(smp.size() > 0 ? smp.size() - 1 : 0, 0.0);
-    for (size_t k = 0; k + 1 < smp.size(); ++k)
-      for (int g = 0; g < ngrid; ++g)
-        if (grid[g] > smp[k] && grid[g] < smp[k + 1]) e[k] = std::max(e[k], res[g]);
     if (c->opts.deriv_indicator && smp.size() > 1) {   // derivative mismatch at the sampled ends
       const int nq = (int)ms.qorb.size();
       const int ns = (int)smp.size();
@@ -691,15 +921,8 @@ int gfcc_mor_refine(gfcc_t c, double wmin, double wmax, int ngrid, double tol, i
     ms.history.push_back({ms.m, emax});
     ms.last_max_err = emax;
     if (emax <= tol) { converged = true; break; }
-    int max_new = (m_max - ms.m) / np;
-    std::vector<std::pair<double, double>> cand;   // (-error, midpoint)
-    for (size_t k = 0; k < e.size(); ++k)
-      if (e[k] > tol) cand.push_back({-e[k], 0.5 * (smp[k] + smp[k + 1])});
-    std::sort(cand.begin(), cand.end());
-    std::vector<double> nw;
-    for (int k = 0; k < (int)cand.size() && k < max_new; ++k) nw.push_back(cand[k].second);
+    std::vector<double> nw = choose_midpoints(smp, e, tol, (m_max - ms.m) / np);
     if (nw.empty()) break;
-    std::sort(nw.begin(), nw.end());
     mor_add_frequencies(c, nw);
   }
   if (m_out) *m_out = ms.m;
@@ -713,14 +936,53 @@ int gfcc_mor_refine(gfcc_t c, double wmin, double wmax, int ngrid, double tol, i
 
 int gfcc_mor_eval(gfcc_t c, const double* omegas, int nw, double* G, double* A, double* maxres) {
   if (!c) return GFCC_ERR_ARG;
-  if (!c->mor.built) { c->last_error = "gfcc_mor_eval: no reduced model"; return GFCC_ERR_STATE; }
+  if (!c->mor.built && c->siso.empty()) { c->last_error = "gfcc_mor_eval: no reduced model"; return GFCC_ERR_STATE; }
   if (nw < 0 || (nw > 0 && !omegas)) { c->last_error = "gfcc_mor_eval: bad frequencies"; return GFCC_ERR_ARG; }
   for (int k = 0; k < nw; ++k)
     if (!std::isfinite(omegas[k])) { c->last_error = "gfcc_mor_eval: non-finite frequency"; return GFCC_ERR_NONFINITE; }
   API_BEGIN
   if (nw == 0) return GFCC_OK;
-  gfcc::MorState& ms = c->mor;
   cudaStream_t s = c->stream;
+  if (!c->siso.empty()) {   // per-orbital models: G_pp on the diagonal of [nw][np][np], zero elsewhere
+    const int np = (int)c->siso.size();
+    DBuf<cplx> Gd, Gk;
+    DBuf<double> Ad, Rd, Rk;
+    DBuf<int> dq;
+    Gd.alloc((long long)nw * np * np);
+    Gk.alloc(nw);
+    Gd.zero(s);
+    if (maxres) {
+      Rd.alloc(nw);
+      Rk.alloc(nw);
+      Rd.zero(s);
+    }
+    for (int k = 0; k < np; ++k) {
+      ModelSwap sw(c, &c->siso[k]);
+      gfcc::mor_eval(c, omegas, nw, Gk.p, nullptr, maxres ? Rk.p : nullptr);
+      GFCC_CUDA(cudaMemcpy2DAsync(Gd.p + (long long)k * (np + 1), sizeof(cplx) * np * np, Gk.p, sizeof(cplx),
+                                  sizeof(cplx), nw, cudaMemcpyDeviceToDevice, s));
+      if (maxres) {
+        max_into_kernel<<<(nw + 255) / 256, 256, 0, s>>>(Rk.p, Rd.p, nw);
+        GFCC_LAUNCH_CHECK();
+      }
+      GFCC_CUDA(cudaStreamSynchronize(s));
+    }
+    if (A) {
+      std::vector<int> qi(np);
+      for (int k = 0; k < np; ++k) qi[k] = k;
+      dq.alloc(np);
+      Ad.alloc(nw);
+      GFCC_CUDA(cudaMemcpyAsync(dq.p, qi.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+      spectral_kernel<<<(nw + 127) / 128, 128, 0, s>>>(Gd.p, nw, np, np, dq.p, Ad.p);
+      GFCC_LAUNCH_CHECK();
+      copy_out(A, Ad.p, sizeof(double) * nw, s);
+    }
+    if (G) copy_out(G, Gd.p, sizeof(cplx) * nw * np * np, s);
+    if (maxres) copy_out(maxres, Rd.p, sizeof(double) * nw, s);
+    GFCC_CUDA(cudaStreamSynchronize(s));
+    return GFCC_OK;
+  }
+  gfcc::MorState& ms = c->mor;
   const int np = (int)ms.porb.size(), nq = (int)ms.qorb.size();
   DBuf<cplx> Gd;
   DBuf<double> Ad, Rd;
@@ -737,6 +999,23 @@ int gfcc_mor_eval(gfcc_t c, const double* omegas, int nw, double* G, double* A, 
 
 int gfcc_mor_info(gfcc_t c, double* w, int cap, int* ns, int* m, int* np, int* nq) {
   if (!c) return GFCC_ERR_ARG;
+  if (!c->siso.empty()) {   // union of the per-orbital models' frequencies, total order
+    std::vector<double> all;
+    int mt = 0;
+    for (const gfcc::MorState& ms : c->siso) {
+      all.insert(all.end(), ms.sampled.begin(), ms.sampled.end());
+      mt += ms.m;
+    }
+    std::sort(all.begin(), all.end());
+    all.erase(std::unique(all.begin(), all.end()), all.end());
+    if (ns) *ns = (int)all.size();
+    if (m) *m = mt;
+    if (np) *np = (int)c->siso.size();
+    if (nq) *nq = (int)c->siso.size();
+    if (w)
+      for (int k = 0; k < cap && k < (int)all.size(); ++k) w[k] = all[k];
+    return GFCC_OK;
+  }
   const gfcc::MorState& ms = c->mor;
   if (ns) *ns = (int)ms.sampled.size();
   if (m) *m = ms.m;
@@ -747,15 +1026,117 @@ int gfcc_mor_info(gfcc_t c, double* w, int cap, int* ns, int* m, int* np, int* n
   return GFCC_OK;
 }
 
+int gfcc_mor_model_info(gfcc_t c, int k, int* orbital, double* w, int cap, int* ns, int* m) {
+  if (!c) return GFCC_ERR_ARG;
+  const int nmod = c->siso.empty() ? (c->mor.built ? 1 : 0) : (int)c->siso.size();
+  if (k < 0 || k >= nmod) { c->last_error = "gfcc_mor_model_info: no such model"; return GFCC_ERR_ARG; }
+  const gfcc::MorState& ms = c->siso.empty() ? c->mor : c->siso[k];
+  if (orbital) *orbital = c->siso.empty() ? -1 : ms.porb[0];
+  if (ns) *ns = (int)ms.sampled.size();
+  if (m) *m = ms.m;
+  if (w)
+    for (int j = 0; j < cap && j < (int)ms.sampled.size(); ++j) w[j] = ms.sampled[j];
+  return GFCC_OK;
+}
+
 int gfcc_mor_stats(gfcc_t c, long long* arnoldi_steps, long long* columns) {
   if (!c) return GFCC_ERR_ARG;
-  if (arnoldi_steps) *arnoldi_steps = c->mor.solve_iters;
-  if (columns) *columns = c->mor.solve_cols;
+  const bool siso = !c->siso.empty();
+  if (arnoldi_steps) *arnoldi_steps = siso ? c->siso_iters : c->mor.solve_iters;
+  if (columns) *columns = siso ? c->siso_cols : c->mor.solve_cols;
   return GFCC_OK;
+}
+
+int gfcc_mor_build_siso(gfcc_t c, const double* seeds, int ns, double eta, const int* orbitals, int np) {
+  if (!c) return GFCC_ERR_ARG;
+  if (ns <= 0 || !seeds || !std::isfinite(eta) || eta <= 0.0) { c->last_error = "gfcc_mor_build_siso: bad seeds or eta"; return GFCC_ERR_ARG; }
+  int rc = check_orbitals(c, orbitals, np, "gfcc_mor_build_siso");
+  if (rc) return rc;
+  for (int k = 0; k < ns; ++k)
+    if (!std::isfinite(seeds[k])) { c->last_error = "gfcc_mor_build_siso: non-finite seed"; return GFCC_ERR_NONFINITE; }
+  for (int a = 0; a < np; ++a)
+    for (int b = a + 1; b < np; ++b)
+      if (orbitals[a] == orbitals[b]) { c->last_error = "gfcc_mor_build_siso: repeated orbital"; return GFCC_ERR_ARG; }
+  API_BEGIN
+  c->mor.reset();
+  c->siso.clear();
+  c->siso.resize(np);
+  c->siso_iters = 0;
+  c->siso_cols = 0;
+  std::vector<int> idx(orbitals, orbitals + np);
+  std::vector<double> bn(np);
+  {  // ||b_p||^2
+    DBuf<int> di;
+    DBuf<double> out;
+    di.alloc(np); out.alloc(np);
+    GFCC_CUDA(cudaMemcpyAsync(di.p, idx.data(), sizeof(int) * np, cudaMemcpyHostToDevice, c->stream));
+    rownorm2_kernel<<<np, 256, 0, c->stream>>>(c->bvec.p, c->D, di.p, np, out.p);
+    GFCC_LAUNCH_CHECK();
+    GFCC_CUDA(cudaMemcpyAsync(bn.data(), out.p, sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
+    GFCC_CUDA(cudaStreamSynchronize(c->stream));
+  }
+  for (int k = 0; k < np; ++k) {
+    GFCC_CHECK(bn[k] > 0.0, GFCC_ERR_ARG, "gfcc_mor_build_siso: zero right-hand side");
+    ModelSwap sw(c, &c->siso[k]);
+    gfcc::MorState& ms = c->mor;
+    ms.eta = eta;
+    ms.porb = {orbitals[k]};
+    ms.qorb = {orbitals[k]};
+    ms.bnorm = {std::sqrt(bn[k])};
+    gfcc::mor_init_basis(c);
+  }
+  std::vector<double> ws(seeds, seeds + ns);
+  std::sort(ws.begin(), ws.end());
+  ws.erase(std::unique(ws.begin(), ws.end()), ws.end());
+  std::vector<std::pair<int, double>> add;
+  for (int k = 0; k < np; ++k)
+    for (double w : ws) add.push_back({k, w});
+  siso_add_frequencies(c, add, eta);
+  for (gfcc::MorState& ms : c->siso) {
+    GFCC_CHECK(ms.m > 0, GFCC_ERR_RANK, "gfcc_mor_build_siso: every seed solution of an orbital was dropped");
+    ms.built = true;
+  }
+  API_END(c)
+}
+
+int gfcc_mor_build_krylov(gfcc_t c, int nblocks, double eta, const int* orbitals, int np, const int* qorb, int nq) {
+  if (!c) return GFCC_ERR_ARG;
+  if (nblocks < 1 || !std::isfinite(eta) || eta <= 0.0) { c->last_error = "gfcc_mor_build_krylov: bad block count or eta"; return GFCC_ERR_ARG; }
+  int rc = check_orbitals(c, orbitals, np, "gfcc_mor_build_krylov");
+  if (rc) return rc;
+  if (qorb) { rc = check_orbitals(c, qorb, nq, "gfcc_mor_build_krylov(q)"); if (rc) return rc; }
+  API_BEGIN
+  c->siso.clear();
+  gfcc::MorState& ms = c->mor;
+  ms.reset();
+  ms.kind = 1;
+  ms.eta = eta;
+  ms.porb.assign(orbitals, orbitals + np);
+  ms.qorb = qorb ? std::vector<int>(qorb, qorb + nq) : ms.porb;
+  {  // ||b_p||^2
+    DBuf<int> idx;
+    DBuf<double> out;
+    idx.alloc(np); out.alloc(np);
+    GFCC_CUDA(cudaMemcpyAsync(idx.p, ms.porb.data(), sizeof(int) * np, cudaMemcpyHostToDevice, c->stream));
+    rownorm2_kernel<<<np, 256, 0, c->stream>>>(c->bvec.p, c->D, idx.p, np, out.p);
+    GFCC_LAUNCH_CHECK();
+    ms.bnorm.resize(np);
+    GFCC_CUDA(cudaMemcpyAsync(ms.bnorm.data(), out.p, sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream));
+    GFCC_CUDA(cudaStreamSynchronize(c->stream));
+    for (double& x : ms.bnorm) x = std::sqrt(x);
+    for (double x : ms.bnorm) GFCC_CHECK(x > 0.0, GFCC_ERR_ARG, "gfcc_mor_build_krylov: zero right-hand side");
+  }
+  gfcc::mor_init_basis(c);
+  krylov_extend(c, nblocks, 2147483647);   // no order bound here: dependent columns are dropped anyway
+  GFCC_CHECK(ms.m > 0, GFCC_ERR_RANK, "gfcc_mor_build_krylov: empty subspace");
+  ms.built = true;
+  API_END(c)
 }
 
 int gfcc_mor_save(gfcc_t c, const char* path) {
   if (!c || !path) return GFCC_ERR_ARG;
+  if (!c->siso.empty()) { c->last_error = "gfcc_mor_save: per-orbital model sets are not saved"; return GFCC_ERR_STATE; }
+  if (c->mor.kind != 0) { c->last_error = "gfcc_mor_save: Krylov models are not saved"; return GFCC_ERR_STATE; }
   if (!c->mor.built) { c->last_error = "gfcc_mor_save: no reduced model"; return GFCC_ERR_STATE; }
   API_BEGIN
   const gfcc::MorState& ms = c->mor;
@@ -810,6 +1191,7 @@ int gfcc_mor_load(gfcc_t c, const char* path) {
   const int m = hdr[3], np = hdr[4], nq = hdr[5], qn = hdr[6];
   GFCC_CHECK(m > 0 && np > 0 && nq > 0 && qn >= m && np <= c->n && nq <= c->n && m <= c->D, GFCC_ERR_ARG,
              "gfcc_mor_load: corrupt header");
+  c->siso.clear();
   gfcc::MorState& ms = c->mor;
   ms.reset();
   f.read(reinterpret_cast<char*>(&ms.eta), sizeof(double));
@@ -877,6 +1259,43 @@ int gfcc_tc_gemm(int precision, const double* A, const double* B, int M, int N, 
     GFCC_CUDA(cudaMemcpy(C, cdev.p, sizeof(float) * M * N, cudaMemcpyDeviceToHost));
   } catch (gfcc::Error& e) {
     fprintf(stderr, "gfcc_tc_gemm: %s\n", e.msg.c_str());
+    return e.code;
+  }
+  return GFCC_OK;
+}
+
+int gfcc_spectral(const double* G, int nw, const int* orbitals, int np, const int* qorb, int nq, double* A,
+                  int adjoint, void* stream) {
+  if (nw < 0 || np < 1 || !orbitals || (qorb && nq < 1) || !G || !A) return GFCC_ERR_ARG;
+  if (nw == 0) return GFCC_OK;
+  try {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<int> porb(orbitals, orbitals + np);
+    std::vector<int> qv = qorb ? std::vector<int>(qorb, qorb + nq) : porb;
+    nq = (int)qv.size();
+    std::vector<int> qi = q_positions(porb, qv);
+    const long long ng = (long long)nw * np * nq;
+    DBuf<int> dq;
+    DBuf<cplx> Gd;
+    DBuf<double> Ad;
+    dq.alloc(np);
+    Gd.alloc(ng);
+    Ad.alloc(nw);
+    GFCC_CUDA(cudaMemcpyAsync(dq.p, qi.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+    if (!adjoint) {
+      GFCC_CUDA(cudaMemcpyAsync(Gd.p, G, sizeof(cplx) * ng, cudaMemcpyDefault, s));
+      spectral_kernel<<<(nw + 127) / 128, 128, 0, s>>>(Gd.p, nw, np, nq, dq.p, Ad.p);
+      GFCC_LAUNCH_CHECK();
+      GFCC_CUDA(cudaMemcpyAsync(A, Ad.p, sizeof(double) * nw, cudaMemcpyDefault, s));
+    } else {
+      GFCC_CUDA(cudaMemcpyAsync(Ad.p, A, sizeof(double) * nw, cudaMemcpyDefault, s));
+      spectral_adjoint_kernel<<<grid_for(ng), 256, 0, s>>>(Ad.p, nw, np, nq, dq.p, Gd.p);
+      GFCC_LAUNCH_CHECK();
+      GFCC_CUDA(cudaMemcpyAsync(const_cast<double*>(G), Gd.p, sizeof(cplx) * ng, cudaMemcpyDefault, s));
+    }
+    GFCC_CUDA(cudaStreamSynchronize(s));
+  } catch (gfcc::Error& e) {
+    fprintf(stderr, "gfcc_spectral: %s\n", e.msg.c_str());
     return e.code;
   }
   return GFCC_OK;

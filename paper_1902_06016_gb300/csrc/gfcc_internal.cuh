@@ -69,7 +69,9 @@ enum ProfClass {
   PROF_OZ_ACCUM = 24,         // accumulation of the exact-slice diagonals and the output pass (every use)
   PROF_LP_PREP = 25,          // operand preparation of the low-precision sigma (K-major operands)
   PROF_LP_COMBINE = 26,       // the combine pass of the low-precision sigma (up reduction, final sum)
-  PROF_NCLASS = 27
+  PROF_UPLOAD = 27,           // copies of the caller's inputs to the device in gfcc_init
+  PROF_DOWNLOAD = 28,         // copies of results into the caller's output buffers
+  PROF_NCLASS = 29
 };
 struct ProfScope {   // records CUDA events around one launch on stream s when profiling is on
   int cls;
@@ -90,6 +92,15 @@ struct DBuf {
   DBuf() = default;
   DBuf(const DBuf&) = delete;
   DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p; n = o.n;
+      o.p = nullptr; o.n = 0;
+    }
+    return *this;
+  }
   ~DBuf() { release(); }
   void release() {
     if (p) cudaFree(p);
@@ -150,6 +161,9 @@ struct Workspace {
 
 struct MorState {
   bool built = false;
+  int kind = 0;                    // subspace: 0 solutions at sampled frequencies, 1 block Krylov space of M on B
+  int kblocks = 0;                 // (kind 1) Krylov blocks in the subspace
+  int knext = 0;                   // (kind 1) columns of the newest block, whose M-images start the next one
   double eta = 0.0;
   std::vector<int> porb, qorb;     // orbital sets
   std::vector<double> sampled;     // sampled frequencies (sorted)
@@ -179,6 +193,9 @@ struct MorState {
   double last_max_err = -1.0;
   void reset() {
     built = false;
+    kind = 0;
+    kblocks = 0;
+    knext = 0;
     eta = 0.0;
     porb.clear(); qorb.clear(); sampled.clear(); bnorm.clear(); history.clear(); dG_exact.clear();
     solve_iters = 0; solve_cols = 0;
@@ -209,7 +226,9 @@ struct gfcc_ctx {
   gfcc::Operator op;
   gfcc::LowPrecision lp;
   gfcc::Workspace ws;
-  gfcc::MorState mor;
+  gfcc::MorState mor;                 // the reduced model (MIMO, Eq. model), or the model being worked on
+  std::vector<gfcc::MorState> siso;   // per-orbital (SISO) reduced models of G_pp (gfcc_mor_build_siso)
+  long long siso_iters = 0, siso_cols = 0;   // Arnoldi steps and columns of the SISO models' solves
   gfcc::Stats stats;
   gfcc::DBuf<double> bvec;   // [n][D]  b_p rows
   gfcc::DBuf<double> cvec;   // [n][D]  c_q rows

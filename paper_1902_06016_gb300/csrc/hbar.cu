@@ -270,16 +270,20 @@ void build_operator(gfcc_ctx* c, const HostInputs& in) {
     GFCC_CUDA(cudaMemcpyAsync(t->p(), h, t->size() * sizeof(double), cudaMemcpyDefault, s));   // host or device
     return t;
   };
-  auto eps = up({n}, in.eps);
-  auto v_oooo = up({o, o, o, o}, in.oooo);
-  auto v_ooov = up({o, o, o, v}, in.ooov);
-  auto v_oovv = up({o, o, v, v}, in.oovv);
-  auto v_ovov = up({o, v, o, v}, in.ovov);
-  auto v_ovvv = up({o, v, v, v}, in.ovvv);
-  auto t1 = up({o, v}, in.t1);
-  auto t2 = up({o, o, v, v}, in.t2);
-  auto l1 = up({o, v}, in.l1);
-  auto l2 = up({o, o, v, v}, in.l2);
+  std::unique_ptr<Tensor> eps, v_oooo, v_ooov, v_oovv, v_ovov, v_ovvv, t1, t2, l1, l2;
+  {
+    ProfScope pu(PROF_UPLOAD, 0.0, s);
+    eps = up({n}, in.eps);
+    v_oooo = up({o, o, o, o}, in.oooo);
+    v_ooov = up({o, o, o, v}, in.ooov);
+    v_oovv = up({o, o, v, v}, in.oovv);
+    v_ovov = up({o, v, o, v}, in.ovov);
+    v_ovvv = up({o, v, v, v}, in.ovvv);
+    t1 = up({o, v}, in.t1);
+    t2 = up({o, o, v, v}, in.t2);
+    l1 = up({o, v}, in.l1);
+    l2 = up({o, o, v, v}, in.l2);
+  }
   {  // reject non-finite inputs before any arithmetic
     DBuf<int> flag;
     flag.alloc(1);

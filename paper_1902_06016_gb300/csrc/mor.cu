@@ -355,10 +355,13 @@ void launch_eval_solve(const EvalArgs& ea, int grid, cudaStream_t s) {
   auto go = [&](auto Pc) {
     constexpr int P = decltype(Pc)::value;
     const size_t bytes = sizeof(float4) * (size_t)ea.m * P;
-    static bool attr = false;   // per instantiation, once per process
-    if (!attr) {
+    static bool attr[64] = {};   // per instantiation, once per device (attributes live in each context)
+    int dev = 0;
+    GFCC_CUDA(cudaGetDevice(&dev));
+    GFCC_CHECK(dev >= 0 && dev < 64, GFCC_ERR_ARG, "device ordinal above 63");
+    if (!attr[dev]) {
       GFCC_CUDA(cudaFuncSetAttribute(eval_solve_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr = true;
+      attr[dev] = true;
     }
     eval_solve_kernel<P><<<grid, 256, bytes, s>>>(ea);
   };

@@ -23,6 +23,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 // Device address of the scratch array, looked up once per device. The name g_noalloc_scratch in host
 // code is only a host-side stand-in for the symbol; kernels must be given this address instead.
+// The cached address stays valid for the life of the CUDA context: a caller that resets a device
+// (cudaDeviceReset) must not call this entry point on that device afterwards.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
@@ -63,13 +65,14 @@ __global__ void round_rows_kernel(const double* __restrict__ src, long long rows
   }
 }
 
-bool on_device(const void* p) {
+// true when p is device (or managed) memory of device dev
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 }  // namespace
@@ -79,7 +82,15 @@ extern "C" int gfcc_tc_gemm_noalloc(int precision, const double* A, const double
   using gfcc::TcKind;
   if (!A || !B || !C || M < 1 || N < 1 || K < 1 || (precision != GFCC_PREC_BF16 && precision != GFCC_PREC_TF32))
     return GFCC_ERR_ARG;
-  if (!on_device(A) || !on_device(B) || !on_device(C)) return GFCC_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return GFCC_ERR_CUDA; }
+  if (!on_device(A, dev) || !on_device(B, dev) || !on_device(C, dev)) return GFCC_ERR_ARG;
+  // the GEMM epilogue stores four floats at a time wherever N is a multiple of 4, so C must start on
+  // 16 bytes (an offset view of a larger buffer may not); A and B are read element by element
+  if ((reinterpret_cast<uintptr_t>(C) & 15) != 0) {
+    fprintf(stderr, "gfcc_tc_gemm_noalloc: C must be 16-byte aligned\n");
+    return GFCC_ERR_ARG;
+  }
   const TcKind kind = precision == GFCC_PREC_BF16 ? TcKind::BF16 : TcKind::TF32;
   const size_t es = kind == TcKind::BF16 ? 2 : 4;
   const long long kp = gfcc::tc_pad_k(kind, K);

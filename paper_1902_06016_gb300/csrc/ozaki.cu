@@ -587,11 +587,12 @@ namespace {
 void oz_run(const SlicedRows& A, const SlicedRows& B, long long M, long long Np, const OzOut& o, OzWork& w,
             cudaStream_t s) {
   const int ns = A.ns;
+  const double slab_bytes = oz_slab_bytes();
   const long long kp = A.kp, ld = (long long)ns * kp;
   const int max_splits = tc_exact_splits(M, Np, (long long)ns * kp);
   const __nv_bfloat16* As = reinterpret_cast<const __nv_bfloat16*>(A.slices.p);
   const __nv_bfloat16* Bs = reinterpret_cast<const __nv_bfloat16*>(B.slices.p);
-  if (4.0 * ns * max_splits * (double)M * (double)Np <= 4.0 * (1LL << 30)) {
+  if (4.0 * ns * max_splits * (double)M * (double)Np <= slab_bytes) {
     // every diagonal's split sums side by side, then one pass that sums them into the output: the
     // output is touched once instead of once per diagonal
     w.islabs.alloc((size_t)ns * max_splits * M * Np + 4 * ns);
@@ -635,7 +636,8 @@ void oz_run(const SlicedRows& A, const SlicedRows& B, long long M, long long Np,
     GFCC_LAUNCH_CHECK();
     return;
   }
-  const long long slab_budget = 2LL << 30;   // bytes of int32 split sums at a time
+  // bytes of int32 split sums at a time (half the bound above)
+  const long long slab_budget = (long long)std::max(1.0, std::min(2.0 * (1LL << 30), 0.5 * slab_bytes));
   long long nc = std::max<long long>(1, slab_budget / (4LL * M * max_splits));
   nc = std::min<long long>(Np, std::max<long long>(256, nc / 256 * 256));
   if (o.complex_out) nc = Np;
@@ -694,7 +696,7 @@ bool use_stacked(long long M, long long Np, long long kp, int ns) {
   int zs[OZ_SLICES_MAX];
   double bytes;
   stack_splits(M, Np, kp, ns, zs, bytes);
-  return kp >= 4LL * Np * zs[0] && bytes <= 4.0 * (1LL << 30);
+  return kp >= 4LL * Np * zs[0] && bytes <= oz_slab_bytes();
 }
 // Exact complex product in the stacked form: A sliced row-major (normal order), Bsm sliced slot-major
 // (normal order) with Np = 2N rows per slot.
@@ -741,6 +743,12 @@ void oz_run_stacked(const SlicedRows& A, const SlicedRows& Bsm, long long M, lon
   GFCC_LAUNCH_CHECK();
 }
 }  // namespace
+
+double oz_slab_bytes() {
+  double v = 4.0 * (1LL << 30);
+  if (const char* env = getenv("GFCC_OZ_SLAB_BYTES")) v = atof(env);
+  return v;
+}
 
 double oz_min_macs() {
   double v = 1e9;

@@ -53,5 +53,9 @@ void oz_gemm(const SlicedRows& A, const SlicedRows& B, long long M, long long N,
 void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s);
 // multiply-adds above which zgemm() uses zgemm_oz (GFCC_OZ_MIN_MACS overrides)
 double oz_min_macs();
+// bytes of int32 split sums up to which all diagonals of an exact product are kept side by side and
+// summed into the output in one pass (default 4 GiB; GFCC_OZ_SLAB_BYTES overrides, so that tests can
+// run the per-diagonal FP64 accumulation over column chunks at small sizes)
+double oz_slab_bytes();
 
 }  // namespace gfcc

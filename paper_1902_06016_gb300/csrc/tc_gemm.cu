@@ -150,14 +150,17 @@ __global__ void __launch_bounds__(EXACT ? 320 : 192, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
+  // barriers: full[STAGES], empty[STAGES], accumulator full[2] and empty[2], and one that the MMA
+  // issuer's final commit arrives on (all of its MMAs complete) before TMEM is released
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
   __shared__ volatile int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int total = zs * tiles_m * tiles_n;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
   const uint32_t accf0 = smem_u32(bars + 2 * STAGES), acce0 = smem_u32(bars + 2 * STAGES + 2);
+  const uint32_t drain = smem_u32(bars + 2 * STAGES + 4);
 
   if (threadIdx.x == 0) {
     s_fail = 0;
@@ -169,6 +172,7 @@ __global__ void __launch_bounds__(EXACT ? 320 : 192, 1)
       mbar_init(accf0 + 8 * b, 1);
       mbar_init(acce0 + 8 * b, NEPI);
     }
+    mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -237,6 +241,11 @@ __global__ void __launch_bounds__(EXACT ? 320 : 192, 1)
         }
       }
       if (!ok) s_fail = 1;
+      // When a wait gave up above, MMAs issued before it may still be running; the CTA must not free
+      // TMEM under them. The commit arrives once every MMA this thread issued has completed (at once
+      // if there are none); the wait for it is bounded like every other.
+      mma_commit(drain);
+      if (!mbar_wait(drain, 0)) s_fail = 1;
     }
   } else {   // epilogue warps: TMEM lane quarter warp % 4; in EXACT mode two warps per quarter split N
     const int q = warp & 3;
@@ -388,10 +397,13 @@ template <TcKind K, bool EXACT>
 void launch(const CUtensorMap& ma, const CUtensorMap& mb, void* C, long long ldc, long long M, long long N,
             int tiles_m, int tiles_n, int zs, int nk_total, int nk_split, long long split_stride, int beta, int* err,
             cudaStream_t s) {
-  static bool attr = false;   // set once per process (the attribute is per function, all devices alike)
-  if (!attr) {
+  static bool attr[64] = {};   // function attributes belong to each device's context: set once per device
+  int dev = 0;
+  GFCC_CUDA(cudaGetDevice(&dev));
+  GFCC_CHECK(dev >= 0 && dev < 64, GFCC_ERR_ARG, "tc_gemm: device ordinal above 63");
+  if (!attr[dev]) {
     GFCC_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<K, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr = true;
+    attr[dev] = true;
   }
   const long long units = (long long)zs * tiles_m * tiles_n;
   const int grid = (int)std::min<long long>(units, sm_count());

@@ -57,12 +57,16 @@ PROTOTYPES = {
     "gfcc_green_derivatives": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, C.c_int, _vp, _vp, _vp]),
     "gfcc_green_grad_t2": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, C.c_int, _vp, _vp, _vp]),
     "gfcc_mor_build": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, C.c_int, _vp, C.c_int]),
+    "gfcc_mor_build_siso": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, C.c_int]),
+    "gfcc_mor_build_krylov": (C.c_int, [_vp, C.c_int, C.c_double, _vp, C.c_int, _vp, C.c_int]),
+    "gfcc_mor_model_info": (C.c_int, [_vp, C.c_int, _ip, _dp, C.c_int, _ip, _ip]),
     "gfcc_mor_refine": (C.c_int, [_vp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, _ip, _dp]),
     "gfcc_mor_eval": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp]),
     "gfcc_mor_info": (C.c_int, [_vp, _dp, C.c_int, _ip, _ip, _ip, _ip]),
     "gfcc_mor_stats": (C.c_int, [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "gfcc_mor_save": (C.c_int, [_vp, C.c_char_p]),
     "gfcc_mor_load": (C.c_int, [_vp, C.c_char_p]),
+    "gfcc_spectral": (C.c_int, [_vp, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp]),
     "gfcc_tc_gemm": (C.c_int, [C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]),
     "gfcc_tc_gemm_noalloc": (C.c_int, [C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
     "gfcc_launch_count": (C.c_longlong, []),
@@ -108,11 +112,60 @@ def tc_gemm(A, B, precision="bf16"):
 
 def tc_gemm_noalloc(A, B, C, precision="bf16", stream=None):
     """C = A B^T on the tensor cores without any device allocation: A [M, K], B [N, K] float64 and
-    C [M, N] float32 must be contiguous CUDA tensors. Returns the status code."""
+    C [M, N] float32 must be contiguous CUDA tensors (the library reads A and B as row-major with K
+    contiguous and writes M x N floats into C). Raises ValueError/TypeError on anything else; returns
+    the library's status code."""
     lib = load()
+    for name, t in (("A", A), ("B", B), ("C", C)):
+        if not hasattr(t, "is_cuda") or not t.is_cuda:
+            raise TypeError(f"tc_gemm_noalloc: {name} must be a CUDA tensor")
+        if not t.is_contiguous() or t.dim() != 2:
+            raise ValueError(f"tc_gemm_noalloc: {name} must be a contiguous 2-D tensor")
+    if str(A.dtype) != "torch.float64" or str(B.dtype) != "torch.float64" or str(C.dtype) != "torch.float32":
+        raise TypeError("tc_gemm_noalloc: A and B must be float64, C float32")
     M, K = A.shape
     N = B.shape[0]
+    if B.shape[1] != K or tuple(C.shape) != (M, N):
+        raise ValueError(f"tc_gemm_noalloc: shapes A {tuple(A.shape)}, B {tuple(B.shape)}, C {tuple(C.shape)} "
+                         "do not match C[M, N] = A[M, K] B[N, K]^T")
     return int(lib.gfcc_tc_gemm_noalloc(PRECISIONS[precision], _ptr(A), _ptr(B), M, N, K, _ptr(C), stream))
+
+
+def spectral(G, orbitals, qorb=None, A=None, stream=None):
+    """A(w) = -(1/pi) sum_p Im G_pp(w) from G [nw, np, nq] complex128 (NumPy or contiguous CUDA tensor)."""
+    orb = _ints(orbitals)
+    q = _ints(qorb) if qorb is not None else None
+    nw = G.shape[0]
+    if A is None:
+        if isinstance(G, np.ndarray):
+            A = np.empty(nw)
+        else:
+            import torch
+            A = torch.empty((nw,), dtype=torch.float64, device=G.device)
+    rc = load().gfcc_spectral(_ptr(G), nw, _ptr(orb), len(orb), _ptr(q), len(q) if q is not None else 0, _ptr(A), 0,
+                              stream)
+    if rc != 0:
+        raise GfccError(rc, "gfcc_spectral failed")
+    return A
+
+
+def spectral_adjoint(Abar, orbitals, nq, qorb=None, Gbar=None, stream=None):
+    """Gbar [nw, np, nq] complex128 = the adjoint of the spectral function applied to Abar [nw]."""
+    orb = _ints(orbitals)
+    q = _ints(qorb) if qorb is not None else None
+    nw = Abar.shape[0]
+    if Gbar is None:
+        shape = (nw, len(orb), nq)
+        if isinstance(Abar, np.ndarray):
+            Gbar = np.empty(shape, dtype=np.complex128)
+        else:
+            import torch
+            Gbar = torch.empty(shape, dtype=torch.complex128, device=Abar.device)
+    rc = load().gfcc_spectral(_ptr(Gbar), nw, _ptr(orb), len(orb), _ptr(q), len(q) if q is not None else 0,
+                              _ptr(Abar), 1, stream)
+    if rc != 0:
+        raise GfccError(rc, "gfcc_spectral (adjoint) failed")
+    return Gbar
 
 
 def launch_count():
@@ -314,6 +367,28 @@ class Context:
         q = _ints(qorb) if qorb is not None else None
         self._check(self._lib.gfcc_mor_build(self._h, _ptr(s), len(s), float(eta), _ptr(porb), len(porb), _ptr(q),
                                              len(q) if q is not None else 0))
+
+    def mor_build_siso(self, seeds, eta, orbitals):
+        """One reduced model of G_pp per orbital p (gfcc_mor_build_siso)."""
+        s = _c64(seeds)
+        porb = _ints(orbitals)
+        self._check(self._lib.gfcc_mor_build_siso(self._h, _ptr(s), len(s), float(eta), _ptr(porb), len(porb)))
+
+    def mor_build_krylov(self, nblocks, eta, orbitals, qorb=None):
+        """Reduced model on the block Krylov space K_nblocks(M, [b_p]) (gfcc_mor_build_krylov)."""
+        porb = _ints(orbitals)
+        q = _ints(qorb) if qorb is not None else None
+        self._check(self._lib.gfcc_mor_build_krylov(self._h, int(nblocks), float(eta), _ptr(porb), len(porb), _ptr(q),
+                                                    len(q) if q is not None else 0))
+
+    def mor_model_info(self, k):
+        """{"orbital", "sampled", "m"} of model k of the current set."""
+        orb, ns, m = C.c_int(), C.c_int(), C.c_int()
+        self._check(self._lib.gfcc_mor_model_info(self._h, int(k), C.byref(orb), None, 0, C.byref(ns), C.byref(m)))
+        w = np.empty(max(ns.value, 1))
+        self._check(self._lib.gfcc_mor_model_info(self._h, int(k), C.byref(orb), w.ctypes.data_as(_dp), ns.value,
+                                                  C.byref(ns), C.byref(m)))
+        return {"orbital": orb.value, "sampled": w[:ns.value].copy(), "m": m.value}
 
     def mor_refine(self, wmin, wmax, ngrid, tol, m_max):
         m = C.c_int()

@@ -22,3 +22,18 @@ def test_reference_arm_prints_one_json_line():
     assert d["impl"] == "reference" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_spectrum_peak_count_on_known_poles():
+    """The bench counts peaks of -A (A = -(1/pi) sum Im G_pp is negative at poles with the -i eta sign):
+    three Lorentzians of different weights on a grid give three peaks at their positions."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    grid = np.linspace(-1.0, -0.2, 5000)
+    poles, wts, eta = [-0.9, -0.55, -0.31], [1.0, 0.3, 0.05], 0.01
+    G = sum(w / (grid - p - 1j * eta) for p, w in zip(poles, wts))
+    A = -G.imag / np.pi
+    pk = bench.spectrum_peaks(A, grid)
+    assert pk["count"] == 3
+    assert np.allclose(pk["positions_ha"], poles, atol=2e-4)

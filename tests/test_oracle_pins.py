@@ -179,6 +179,28 @@ def test_refinement_respects_order_bound():
     assert r.model.m <= 20 and not r.converged
 
 
+def test_siso_models_interpolate_their_diagonal_and_refine():
+    """Per-orbital models: model p is built from X_p(w_k) alone, so by the Galerkin property its Ghat_pp
+    equals the full G_pp at each of its own sampled frequencies; each model refines to the tolerance,
+    its order is at most its number of samples, and A from the diagonal models matches the full A."""
+    inp, hb, B, C, M = _mor_case()
+    res = mor.build_and_refine_siso(hb, B, C, [-1.2, -0.75, -0.3], -1.2, -0.3, 300, 0.01, 1e-6, 10 ** 6,
+                                    solver="dense", M=M)
+    assert len(res) == B.shape[0]
+    for p, r in enumerate(res):
+        assert r.converged and r.model.m <= len(r.sampled)
+        Gs = sv.green(C[p:p + 1], sv.dense_solve(M, B[p:p + 1], r.sampled, 0.01))[:, 0, 0]
+        Gh = mor.reduced_green(r.model, r.sampled, 0.01)[:, 0, 0]
+        assert np.abs(Gh - Gs).max() <= 1e-10 * np.abs(Gs).max()
+    grid = np.linspace(-1.2, -0.3, 300)
+    Gf = sv.green(C, sv.dense_solve(M, B, grid, 0.01))
+    Gd = mor.siso_green(res, grid, 0.01)
+    assert np.all(Gd[:, 0, 1] == 0.0)
+    assert np.abs(sv.spectral(Gd) - sv.spectral(Gf)).max() <= 1e-5 * np.abs(sv.spectral(Gf)).max()
+    # the refinement ran (frequencies beyond the three seeds)
+    assert all(len(r.sampled) > 3 for r in res)
+
+
 def test_splitmix64_published_value_and_normals():
     # SplitMix64 from state 0: first output 0xE220A8397B1DCDAF (Steele et al. reference code)
     assert int(synth._mix(np.array([0x9E3779B97F4A7C15], dtype=np.uint64))[0]) == 0xE220A8397B1DCDAF
@@ -313,3 +335,30 @@ def test_model_extrapolated_initial_guess():
     G1 = mor.reduced_green(runs[True][0].model, grid, 0.02)
     assert np.abs(G1 - G0).max() <= 1e-8 * np.abs(G0).max()
     assert runs[True][1]["gmres_iters"] < runs[False][1]["gmres_iters"]
+
+
+def test_krylov_model_matches_moments_and_is_exact_when_complete():
+    """Galerkin projection onto K_k(M, B): the reduced model reproduces the moments c_q^T M^j b_p for
+    j = 0 .. k-1 (the leading terms of G's expansion in 1/(w - i eta)), for every p, q; once the space
+    is invariant (it holds every M^j b_p) the model is exact at every frequency; and the refinement
+    grows the space until its residuals meet the tolerance."""
+    inp, hb, B, C, M = _mor_case()
+    k = 4
+    rm, st = mor.build_krylov(hb, B, C, k)
+    assert st.blocks == k and rm.m == k * B.shape[0]
+    Mj_B = B.T.astype(complex)
+    Hj_b = rm.bhat
+    for j in range(k):
+        ref = C @ Mj_B                                   # [nq, np]
+        assert np.abs(rm.chat @ Hj_b - ref).max() <= 1e-10 * np.abs(ref).max(), j
+        Mj_B = M @ Mj_B
+        Hj_b = rm.Hhat @ Hj_b
+    # moment k is not matched in general (the test is not vacuous)
+    assert np.abs(rm.chat @ Hj_b - C @ Mj_B).max() > 1e-8 * np.abs(C @ Mj_B).max()
+    rm_full, st_full = mor.build_krylov(hb, B, C, 200)
+    assert rm_full.m == M.shape[0] and st_full.newest == 0
+    ws = np.linspace(-1.2, -0.3, 11)
+    G = sv.green(C, sv.dense_solve(M, B, ws, 0.01))
+    assert np.abs(mor.reduced_green(rm_full, ws, 0.01) - G).max() <= 1e-9 * np.abs(G).max()
+    rm_r, st_r, hist, ok = mor.refine_krylov(hb, B, C, 2, -1.2, -0.3, 200, 0.01, 1e-6, 10 ** 6)
+    assert ok and hist[-1][1] <= 1e-6 and hist[0][1] > 1e-6 and rm_r.m < M.shape[0]

@@ -54,3 +54,37 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(torch):
     assert tc_gemm_noalloc(A, B, C, "bf16") == -1          # 2 x 32 MiB of bf16 operands > 32 MiB
     small = torch.zeros((8, 8), dtype=torch.float32, device="cuda")
     assert tc_gemm_noalloc(A[:8], B[:8], small, "bf16") == 0
+
+
+def test_noalloc_rejects_misaligned_output_before_any_launch(torch):
+    """The epilogue stores four floats at a time, so an output that does not start on 16 bytes (an
+    offset view into a larger buffer) is refused on the host, before anything runs on the device."""
+    from paper_1902_06016_gb300.gfcc import launch_count, tc_gemm_noalloc
+    M, N, K = 16, 32, 64
+    A = torch.zeros((M, K), dtype=torch.float64, device="cuda")
+    B = torch.zeros((N, K), dtype=torch.float64, device="cuda")
+    big = torch.zeros(M * N + 4, dtype=torch.float32, device="cuda")
+    C = big[1:1 + M * N].view(M, N)                  # contiguous, 4 bytes past a 16-byte boundary
+    assert C.is_contiguous() and C.data_ptr() % 16 == 4
+    n0 = launch_count()
+    assert tc_gemm_noalloc(A, B, C, "bf16") == -1
+    assert launch_count() == n0
+    assert torch.count_nonzero(big).item() == 0
+
+
+def test_noalloc_wrapper_checks_its_arguments(torch):
+    from paper_1902_06016_gb300.gfcc import tc_gemm_noalloc
+    A = torch.zeros((8, 16), dtype=torch.float64, device="cuda")
+    B = torch.zeros((4, 16), dtype=torch.float64, device="cuda")
+    C = torch.zeros((8, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        tc_gemm_noalloc(A, B, torch.zeros((8, 5), dtype=torch.float32, device="cuda"))   # C too small / wrong
+    with pytest.raises(ValueError):
+        tc_gemm_noalloc(torch.zeros((16, 8), dtype=torch.float64, device="cuda").t(), B, C)   # transposed A
+    with pytest.raises(ValueError):
+        tc_gemm_noalloc(A, torch.zeros((4, 15), dtype=torch.float64, device="cuda"), C)     # K mismatch
+    with pytest.raises(TypeError):
+        tc_gemm_noalloc(A.float(), B, C)
+    with pytest.raises(TypeError):
+        tc_gemm_noalloc(A.cpu(), B, C)
+    assert tc_gemm_noalloc(A, B, C) == 0
