@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--restart", type=int, default=30, help="GMRES(k) Krylov dimension per cycle")
     ap.add_argument("--siso", action="store_true",
                     help="one reduced model of G_pp per orbital (gfcc_mor_build_siso) instead of one MIMO model")
+    ap.add_argument("--pset", default="", choices=["", "occupied", "all"],
+                    help="orbital set p (= q set): the workload's default, the occupied or all spin-orbitals")
     ap.add_argument("--krylov", type=int, default=0,
                     help="K > 0: reduced model on the block Krylov space of M on the b_p (gfcc_mor_build_krylov, K "
                          "initial blocks, grown by the refinement) instead of solutions at sampled frequencies")
@@ -64,9 +66,11 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1, help="(w, p) columns in the oracle sample")
     ap.add_argument("--ref-iters", type=int, default=6,
                     help="--impl reference: GMRES iterations of the oracle per timed step")
-    ap.add_argument("--mode", default="pipeline", choices=["pipeline", "sigma", "peaks"],
+    ap.add_argument("--mode", default="pipeline", choices=["pipeline", "sigma", "peaks", "autograd"],
                     help="pipeline: the whole MOR step (default); sigma: one batch of sigma applications; "
-                         "peaks: FP64, TF32 and BF16 GEMM rates of this GPU (library GEMMs, timing only)")
+                         "peaks: FP64, TF32 and BF16 GEMM rates of this GPU (library GEMMs, timing only); "
+                         "autograd: gradients by the adjoint solves against finite differences, and the "
+                         "derivative-driven reduced model (run it with --workload adenine_o70_v250)")
     ap.add_argument("--nvec", type=int, default=64, help="vectors per sigma batch (--mode sigma)")
     return ap.parse_args()
 
@@ -187,6 +191,16 @@ def spectrum_peaks(A, grid, rel=0.01):
     return {"count": int(len(k)), "threshold_rel": rel, "positions_ha": [round(float(grid[i]), 5) for i in k[:40]]}
 
 
+def autotune_summary(decisions):
+    """Condensed autotuner report: bucket counts, the time the chosen group sizes save over the default
+    (one launch per bucket, as tuned), and the decisions for the low-precision (inner sigma) GEMMs."""
+    changed = [d for d in decisions if d["gm"] != d["gm_default"]]
+    return {"buckets": len(decisions), "changed_from_default": len(changed),
+            "tuned_ms_sum": round(sum(d["ms_best"] for d in decisions), 3),
+            "default_ms_sum": round(sum(d["ms_default"] for d in decisions), 3),
+            "inner_sigma_gemms": [d for d in decisions if not d["exact_slices"]]}
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_1902_06016_gb300 import Context, load
@@ -199,7 +213,8 @@ def run_ours(args, rank, world):
     o, v, eta = W["o"], W["v"], W["eta"]
     nw = args.nomega or W["nw"]
     inp = synth.make_inputs(o, v, rank_seed(W["seed"], rank))   # weak scaling: one problem per rank
-    porb = orbital_set(args.workload, o, o + v)
+    porb = list(range(o + v)) if args.pset == "all" else (list(range(o)) if args.pset == "occupied"
+                                                           else orbital_set(args.workload, o, o + v))
     npp = len(porb)
     seeds = synth.omega_grid(W["wmin"], W["wmax"], args.seeds)
     grid = np.linspace(W["wmin"], W["wmax"], nw)
@@ -265,12 +280,14 @@ def run_ours(args, rank, world):
                    26: "lowprec_combine", 27: "input_upload", 28: "output_copies"}
     phases = {phase_names[k]: round(G.profile_read(k)[1] / args.steps, 1) for k in phase_names}
     cgs = G.profile_read(14)   # (launch groups, ms, algorithmic bytes) of the Arnoldi sweeps
+    slicing, accum = G.profile_read(13), G.profile_read(24)   # exact-slice passes (bytes in the third field)
     cgs_parts = {name: G.profile_read(k) for k, name in
                  ((15, "multidot_kernel"), (16, "cgs_update_kernel<dot>"), (17, "cgs_update_kernel<norm>"),
                   (18, "all three, batches < 32 columns"))}
     G.profile(False)
     clk = clocks.stop()
     spectrum = spectrum_peaks(A_dev.cpu().numpy(), grid)
+    tuned = autotune_summary(G.autotune_report())
 
     # end to end through the public API with host buffers: the inputs are copied from page-locked host
     # memory inside gfcc_init and G, A are written to page-locked host arrays, every step; one warm-up
@@ -396,9 +413,17 @@ def run_ours(args, rank, world):
             "peak": peaks.get("hbm_gbs"), "frac": (cgs[2] / (cgs[1] / 1e3) / 1e9) / peaks["hbm_gbs"]
             if cgs[1] > 0 and peaks.get("hbm_gbs") else None,
             "parts": {name: {"launches": n, "ms": round(ms, 2), "achieved_gbs": round(b / (ms / 1e3) / 1e9, 1)
-                             if ms > 0 else None} for name, (n, ms, b) in cgs_parts.items()}}},
+                             if ms > 0 else None} for name, (n, ms, b) in cgs_parts.items()}},
+            **{name: {"bound": "hbm", "launches": n, "ms": ms, "algorithmic_bytes": b, "unit": "GB/s",
+                      "achieved": b / (ms / 1e3) / 1e9 if ms > 0 else None, "peak": peaks.get("hbm_gbs"),
+                      "frac": b / (ms / 1e3) / 1e9 / peaks["hbm_gbs"] if ms > 0 and peaks.get("hbm_gbs") else None}
+               for name, (n, ms, b) in (("exact_slicing (FP64 rows -> bf16 integer slices)", slicing),
+                                        ("exact_slice_accumulate (int32 split sums -> FP64 output)", accum))}},
         "clocks": clk,
         "spectrum": spectrum,
+        "autotune": {"enabled": os.environ.get("GFCC_AUTOTUNE", "1") != "0",
+                     "what": "M-tile group size of the tcgen05 GEMM per shape bucket, timed on first use",
+                     **tuned},
         "full_fp64": full,
     }
 
@@ -557,6 +582,126 @@ def run_peaks(args):
     return out
 
 
+def run_autograd(args):
+    """Differentiation at size (default: the adenine-sized workload, o = 70, v = 250, D = 603,820).
+
+    1. torch.autograd through gfcc: G_pq(w) on 20 frequencies of the window for the p set, loss
+       L = sum_w A(w)^2 + sum |G|^2, backward to w, eta and t2 (adjoint solves with the transposed sigma;
+       the forward solutions are recomputed for the t2 gradient). Timed.
+    2. Central finite differences, step 1e-5: dG/dw and dG/deta at all 20 frequencies (every p, q) from
+       forward solves at w +- h and eta +- h against the adjoint-solve derivatives, and dL/dt2 along a
+       random antisymmetric direction (two more contexts at t2 +- h dt2) against the autograd gradient.
+    3. dG/dw-driven MOR: the derivative indicator on, 8 seeds, refined to 1e-6 on 500 points, evaluated
+       on the workload's output grid (2000 points for adenine); its G points/s, and its A and G errors
+       against the full solutions at the 20 frequencies of step 1."""
+    import torch
+    from paper_1902_06016_gb300 import Context, load
+    from paper_1902_06016_gb300.autograd import green, spectral
+    torch.cuda.set_device(0)
+    load()
+    W = synth.WORKLOADS[args.workload]
+    o, v, eta0 = W["o"], W["v"], W["eta"]
+    nw = args.nomega or W["nw"]
+    t_gen = time.perf_counter()
+    inp = synth.make_inputs(o, v, W["seed"])
+    t_gen = time.perf_counter() - t_gen
+    porb = list(range(o + v)) if args.pset == "all" else list(range(o))
+    ws = np.linspace(W["wmin"], W["wmax"], 20)
+    h = 1e-5
+    stream = torch.cuda.current_stream()
+    tol = 1e-10   # GMRES-IR reaches about 1e-11 with 41-bit exact-slice residuals; 1e-10 leaves a margin
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = Context(inp, tol=tol, precision=args.precision, stream=stream.cuda_stream, restart=args.restart)
+    torch.cuda.synchronize()
+    t_init = time.perf_counter() - t0
+    # 1. autograd forward + backward
+    w_t = torch.tensor(ws, dtype=torch.float64, requires_grad=True)
+    e_t = torch.tensor(eta0, dtype=torch.float64, requires_grad=True)
+    t2_t = torch.tensor(inp.t2, dtype=torch.float64, requires_grad=True)
+    t0 = time.perf_counter()
+    G = green(w_t, e_t, ctx, porb, t2=t2_t)
+    loss = (spectral(G) ** 2).sum() + (G.abs() ** 2).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    t_ad = time.perf_counter() - t0
+    G_np = G.detach().numpy()
+    # 2. finite differences
+    _, dw, de = ctx.green_derivatives(ws, eta0, porb)
+    t0 = time.perf_counter()
+    Gp = ctx.solve_full(ws + h, eta0, porb, want_A=False)["G"]
+    Gm = ctx.solve_full(ws - h, eta0, porb, want_A=False)["G"]
+    fd_w = (Gp - Gm) / (2 * h)
+    Gp = ctx.solve_full(ws, eta0 + h, porb, want_A=False)["G"]
+    Gm = ctx.solve_full(ws, eta0 - h, porb, want_A=False)["G"]
+    fd_e = (Gp - Gm) / (2 * h)
+    rng = np.random.default_rng(7)
+    dt2 = rng.standard_normal(inp.t2.shape)
+    dt2 = dt2 - dt2.transpose(1, 0, 2, 3)
+    dt2 = dt2 - dt2.transpose(0, 1, 3, 2)
+    dt2 *= np.abs(inp.t2).max() / np.abs(dt2).max()
+
+    def loss_at(t2x):
+        fields = {k: getattr(inp, k) for k in inp.__dataclass_fields__}
+        fields["t2"] = t2x                     # lambda_2 held fixed at the original amplitudes
+        cx = Context(synth.Inputs(**fields), tol=tol, precision=args.precision, stream=stream.cuda_stream,
+                     restart=args.restart)
+        Gx = cx.solve_full(ws, eta0, porb, want_A=False)["G"]
+        cx.close()
+        Ax = -np.imag(np.einsum("wpp->w", Gx)) / np.pi
+        return float((Ax ** 2).sum() + (np.abs(Gx) ** 2).sum())
+
+    fd_t2 = (loss_at(inp.t2 + h * dt2) - loss_at(inp.t2 - h * dt2)) / (2 * h)
+    t_fd = time.perf_counter() - t0
+    ad_t2 = float((t2_t.grad.numpy() * dt2).sum())
+    # the scalar derivatives of the loss with respect to w_k and eta, from the finite differences of G
+    A_np = -np.imag(np.einsum("wpp->w", G_np)) / np.pi
+
+    def dloss(dG):
+        dA = -np.imag(np.einsum("wpp->w", dG)) / np.pi
+        return 2 * A_np * dA + 2 * np.real(np.conj(G_np) * dG).sum(axis=(1, 2))
+
+    fd_loss_w = dloss(fd_w)
+    fd_loss_e = float(dloss(fd_e).sum())
+
+    def rel(a, b):
+        return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+    # 3. derivative-driven MOR on the output grid
+    grid = np.linspace(W["wmin"], W["wmax"], nw)
+    ctx.set_opts(tol=args.solve_tol, precision=args.precision, restart=args.restart, deriv_indicator=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.mor_build(synth.omega_grid(W["wmin"], W["wmax"], args.seeds), eta0, porb)
+    ref = ctx.mor_refine(W["wmin"], W["wmax"], args.ngrid, args.mor_tol, args.m_max)
+    ev = ctx.mor_eval(grid)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mor_ms = e0.elapsed_time(e1)
+    at20 = ctx.mor_eval(ws)
+    info = ctx.mor_info()
+    ctx.close()
+    return {"metric": "G_pq(w) points/s, dG/dw-driven MOR + mixed precision", "value": nw * len(porb) / (mor_ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "mode": "autograd", "higher_is_better": True, "data": "synthetic",
+            "dtype": f"c128 (f64 residuals, {args.precision} tensor-core inner sigma, adjoint on the transposed sigma)",
+            "config": {"workload": args.workload, "o": o, "v": v, "D": inp.dim, "n_p": len(porb), "eta": eta0,
+                       "fd_omegas": 20, "fd_step": h, "solve_tol": tol, "n_omega": nw},
+            "seconds": {"input_generation_host": t_gen, "gfcc_init": t_init,
+                        "autograd_forward_backward": t_ad, "finite_differences": t_fd, "mor_ms": mor_ms},
+            "autograd_vs_fd": {
+                "dG_domega_rel_err": rel(dw, fd_w), "dG_deta_rel_err": rel(de, fd_e),
+                "dL_domega_rel_err": rel(w_t.grad.numpy(), fd_loss_w),
+                "dL_deta_rel_err": abs(float(e_t.grad) - fd_loss_e) / max(abs(fd_loss_e), 1e-300),
+                "dL_dt2_directional": {"autograd": ad_t2, "finite_difference": fd_t2,
+                                       "rel_err": abs(ad_t2 - fd_t2) / max(abs(fd_t2), 1e-300)}},
+            "mor": {"model_order": info["m"], "sampled_freqs": len(info["sampled"]), "converged": ref["converged"],
+                    "max_err": ref["max_err"], "deriv_indicator": True,
+                    "A_rel_err_vs_full_at_fd_omegas": rel(at20["A"], A_np),
+                    "G_rel_err_vs_full_at_fd_omegas": rel(at20["G"], G_np),
+                    "spectrum": spectrum_peaks(ev["A"], grid)}}
+
+
 def oracle_sample(args, ncols, inp=None):
     """Time the FP64 CPU oracle on a bounded sample: full GMRES solves of ncols (w, p) points."""
     from oracle import bc, hbar
@@ -642,6 +787,9 @@ def main():
         return
     if args.mode == "peaks":
         print(json.dumps(run_peaks(args)), flush=True)
+        return
+    if args.mode == "autograd":
+        print(json.dumps(run_autograd(args)), flush=True)
         return
     if world > 1:
         import torch.distributed as dist

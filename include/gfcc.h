@@ -152,7 +152,9 @@ int gfcc_spectral(const double* G, int nw, const int* orbitals, int np, const in
  * A(w) = w - i eta + M, x_p = A^{-1} b_p (forward solves, as gfcc_solve_full) and the adjoint solutions
  * y_q = A^{-T} c_q (transposed sigma), G_pq = c_q^T x_p, dG_pq/dw = -y_q^T x_p and dG_pq/deta = i y_q^T x_p.
  * Outputs (each optional, host or device, complex, layout [(w*np + p)*nq + q] as in gfcc_solve_full).
- * The adjoint solves run with the FP64 transposed sigma. GFCC_ERR_NOT_CONVERGED if a solve hit the cap. */
+ * The adjoint solves use the transposed sigma in the context's precision (with a TF32/BF16 context, GMRES-IR
+ * with the low-precision M^T inside and exact-slice FP64-accurate residuals, like the forward solves).
+ * GFCC_ERR_NOT_CONVERGED if a solve hit the cap. */
 int gfcc_green_derivatives(gfcc_t ctx, const double* omegas, int nw, double eta, const int* orbitals, int np,
                            const int* qorb, int nq, double* G, double* dG_domega, double* dG_deta);
 
@@ -269,6 +271,17 @@ int gfcc_tc_gemm(int precision, const double* A, const double* B, int M, int N, 
 int gfcc_tc_gemm_noalloc(int precision, const double* A, const double* B, int M, int N, int K, float* C,
                          void* stream);
 
+/* Autotuner of the tensor-core GEMM (the paper has no counterpart): on the first launch of each shape
+ * bucket (precision, exact-slice or not, M tiles, ceil(log2(N tiles)), K per split, splits) whose output
+ * is overwritten, every distinct M-tile group size of the L2 budgets 16, 40, 64, 96 and 128 MB is timed
+ * twice with CUDA events on the launching stream and the fastest is kept for the rest of the process
+ * (the group size orders the work units without changing their arithmetic; no tuning under stream
+ * capture; environment variable GFCC_AUTOTUNE=0 keeps the 40 MB default). Entry i (in tuning order):
+ * the bucket, the chosen and the default group size, and their best times in milliseconds. Any output
+ * pointer may be NULL. GFCC_ERR_ARG when there is no entry i. */
+int gfcc_autotune_info(int i, int* kind, int* exact, int* tiles_m, int* tiles_n_log2, int* gm, int* gm_default,
+                       double* ms_best, double* ms_default);
+
 /* Number of CUDA kernels launched by this library since it was loaded (all contexts). */
 long long gfcc_launch_count(void);
 
@@ -283,7 +296,7 @@ long long gfcc_launch_count(void);
  * 13 splitting of FP64 rows into exact slices; 14 the fused Gram-Schmidt sweeps of FP32-basis Arnoldi
  * steps; 15, 16, 17 the first, second and third of those sweeps alone for batches of at least 32
  * columns; 18 the three sweeps of batches of fewer than 32 columns (classes 14-18 count algorithmic
- * HBM bytes in the "flops" field); 19 Householder reductions of Hhat to Hessenberg form; 20 the
+ * HBM bytes in the "flops" field, as do classes 13 and 24); 19 Householder reductions of Hhat to Hessenberg form; 20 the
  * per-frequency shifted Hessenberg solves; 21, 22 the coefficient products and updates of the block
  * Gram-Schmidt passes; 23 the Cholesky QR of the panels; 24 the accumulation and output passes of the
  * exact-slice products; 25 the operand preparation and 26 the combine pass of the low-precision sigma;

@@ -368,7 +368,16 @@ struct ModelSwap {
 
 // Solve every (model k, w) pair of add (sorted by model, then frequency) in one batched solve and append
 // each model's solutions to its own subspace.
+void siso_add_chunk(gfcc_ctx* c, const std::vector<std::pair<int, double>>& add, double eta);
 void siso_add_frequencies(gfcc_ctx* c, const std::vector<std::pair<int, double>>& add, double eta) {
+  // bounded memory: at most kSisoChunk columns (their solutions, residuals and images) at a time
+  constexpr size_t kSisoChunk = 256;
+  for (size_t i0 = 0; i0 < add.size(); i0 += kSisoChunk) {
+    const std::vector<std::pair<int, double>> part(add.begin() + i0, add.begin() + std::min(add.size(), i0 + kSisoChunk));
+    siso_add_chunk(c, part, eta);
+  }
+}
+void siso_add_chunk(gfcc_ctx* c, const std::vector<std::pair<int, double>>& add, double eta) {
   cudaStream_t s = c->stream;
   const long long D = c->D;
   const long long ncols = (long long)add.size();
@@ -386,11 +395,15 @@ void siso_add_frequencies(gfcc_ctx* c, const std::vector<std::pair<int, double>>
   DBuf<int> rows;
   X.alloc(D * ncols); R.alloc(D * ncols); MX.alloc(D * ncols); B.alloc(D * ncols); sh.alloc(ncols);
   rows.alloc(ncols);
-  if (c->opts.mor_guess) {   // each model's prediction x0_p(w) = S yhat_p(w) at its new frequencies
+  bool guess = false;   // initial guesses from the models that already have a subspace (none at the seeds)
+  for (size_t k = 0; k < c->siso.size(); ++k) guess = guess || (first[k + 1] > first[k] && c->siso[k].m > 0);
+  guess = guess && c->opts.mor_guess;
+  if (guess) {   // each model's prediction x0_p(w) = S yhat_p(w) at its new frequencies, zero for empty models
     X0.alloc(D * ncols);
+    X0.zero(s);
     for (size_t k = 0; k < c->siso.size(); ++k) {
       const long long nk = first[k + 1] - first[k];
-      if (nk == 0) continue;
+      if (nk == 0 || c->siso[k].m == 0) continue;
       DBuf<cplx> tmp;
       tmp.alloc(D * nk);
       {
@@ -402,7 +415,7 @@ void siso_add_frequencies(gfcc_ctx* c, const std::vector<std::pair<int, double>>
       GFCC_CUDA(cudaStreamSynchronize(s));
     }
   }
-  solve_pairs(c, wcol, pcol, eta, {}, nullptr, X.p, R.p, nullptr, c->opts.mor_guess ? X0.p : nullptr);
+  solve_pairs(c, wcol, pcol, eta, {}, nullptr, X.p, R.p, nullptr, guess ? X0.p : nullptr);
   c->siso_iters += c->stats.gmres_iters;
   c->siso_cols += ncols;
   std::vector<cplx> hs(ncols);

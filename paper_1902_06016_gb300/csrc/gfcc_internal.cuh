@@ -143,6 +143,11 @@ struct Operator {
   // transposed-action copies are built lazily (adjoint systems)
   bool have_T = false;
   DBuf<double> WrT, WooT, A12T, A21T, VtT, T2pT;
+  // explicitly transposed blocks for the tensor-core operands of M^T (built lazily): the roles of the
+  // forward blocks in M^T, stored in the forward layouts: WooX = Woo^T [P][P], VtX = T2p^T [v][Pv],
+  // A12X = A21^T [o][Pv], T2pX = Vt^T [Pv][v], A21X = A12^T [Pv][o], A11X = A11^T [o][o]
+  bool have_X = false;
+  DBuf<double> WooX, VtX, A12X, T2pX, A21X, A11X;
 };
 
 // low-precision (tensor-core) copies of the sigma operands; the state lives in sigma_tc.cu
@@ -150,6 +155,8 @@ struct LowPrecision {
   int kind = 0;          // GFCC_PREC_* of the built operands (0: none)
   void* impl = nullptr;
   void* emu = nullptr;   // exact-slice (FP64-accurate) operands
+  void* implT = nullptr; // the same for the transposed action M^T (adjoint systems), built on first use
+  void* emuT = nullptr;
 };
 
 struct Workspace {
@@ -311,14 +318,16 @@ void build_transpose_operator(gfcc_ctx* c);
 // ---- sigma_tc.cu (tcgen05 low-precision sigma for the inner solves) ---------------------------
 void build_low_precision(gfcc_ctx* c, int kind);
 void free_low_precision(gfcc_ctx* c);
-void sigma_lowprec(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shift, cudaStream_t s);
+void sigma_lowprec(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shift, cudaStream_t s,
+                   bool transpose = false);
 // the same with FP32 complex vectors (the FP32 Krylov basis of the mixed-precision solver)
 void sigma_lowprec_f32(gfcc_ctx* c, const cuFloatComplex* X, cuFloatComplex* Y, int nb, const cplx* shift,
-                       cudaStream_t s);
+                       cudaStream_t s, bool transpose = false);
 int low_precision_error(gfcc_ctx* c);   // 1 if a tensor-core pipeline wait timed out
 int emulated_error(gfcc_ctx* c);
 void build_emulated(gfcc_ctx* c);
-void sigma_emulated(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shift, cudaStream_t s);
+void sigma_emulated(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shift, cudaStream_t s,
+                    bool transpose = false);
 void tc_selftest(int kind, const double* A, const double* B, int M, int N, int K, float* C, cudaStream_t s);
 
 // ---- krylov.cu ---------------------------------------------------------------------------------

@@ -101,109 +101,192 @@ __global__ void __launch_bounds__(256, 2) multidot_kernel(const VT* __restrict__
   md_reduce<VT, NV, R>(ax, ay, nv, c, nb, partial, red);
 }
 
-// Fused CGS sweeps over a chunk of rows: w <- w - sum_i V_i h_i, then either (DOT) partial sums of
-// the next coefficients conj(V_i) w (multidot_kernel's partial layout) or (!DOT) partial sums of |w|^2
-// (layout [chunk][c]). The thread rows form MdGroups<NV>'s IG groups; group g loads its NPG basis
-// vectors of a row once into registers, forms its share of sum_i V_i h_i, and the shares are added
-// through shared memory (double-buffered, one barrier per step), after which every group holds the
-// updated w and, for DOT, accumulates its own coefficients from the registers it already holds.
-// Group 0 writes w. Each step covers CU_U rows per group so that more loads are in flight.
-constexpr int CU_U = 2;
-template <typename VT, int NV, bool DOT>
-__global__ void __launch_bounds__(256, 2) cgs_update_kernel(const VT* __restrict__ V, long long vstride, int nv,
-                                                            VT* __restrict__ W, long long D, int nb,
-                                                            long long rows_per_chunk, const cplx* __restrict__ h,
-                                                            int hld, cplx* __restrict__ partial) {
-  using R = typename RealOf<VT>::type;
-  using G = MdGroups<NV>;
-  constexpr int NPG = G::NPG, RPG = G::RPG, IG = G::IG;
-  __shared__ VT share[2][CU_U][MD_TY][MD_TX];
-  __shared__ cplx red[MD_TY][MD_TX];
-  const int x = threadIdx.x, c = blockIdx.x * MD_TX + x;
-  const int g = threadIdx.y / RPG, yr = threadIdx.y % RPG;
-  const int i0 = g * NPG, ng = nv - i0;   // vectors of this group present (may be <= 0)
+// ---- pipelined Gram-Schmidt sweeps of the FP32 basis ---------------------------------------------
+// The three sweeps of a CGS2 Arnoldi step with an FP32 basis (MODE 0: partial sums of conj(V_i) w, the
+// layout of multidot_kernel's partials; 1: w -= V h, then partial sums
+// of conj(V_i) w; 2: w -= V h, then partial sums of |w|^2), with the loads decoupled from the
+// arithmetic: every thread streams its own elements (its NPG basis vectors and w at one row per step)
+// through a SW_STAGES-deep ring in shared memory by 8-byte asynchronous copies (cp.async, zero-filled
+// outside the batch), so that about three steps of loads are in flight per block without holding
+// registers. A block is CW columns wide (32, 16, 8 or 4: narrow batches keep every thread busy) and
+// SW_THREADS / CW thread rows high; the thread rows form MdGroups-like groups that each own NPG basis
+// vectors (IG groups), and the groups' shares of V h are added through shared memory as above. Each
+// thread reads only the ring slots it filled itself.
+constexpr int SW_THREADS = 256, SW_STAGES = 4;
+template <int NV> struct SwGroups {
+  static constexpr int IG = NV >= 16 ? NV / 8 : 1;
+  static constexpr int NPG = NV / IG;
+};
+template <int NV, int CW> constexpr size_t sweep_smem_bytes() {
+  return sizeof(float2) * (size_t)SW_STAGES * (SwGroups<NV>::NPG + 1) * SW_THREADS   // load ring
+         + sizeof(float2) * 2 * SW_THREADS                                           // shares
+         + sizeof(cplx) * SW_THREADS;                                                // reductions
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gmem), "r"(pred ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int NV, int MODE, int CW>
+__global__ void __launch_bounds__(SW_THREADS, 2) sweep_kernel(const float2* __restrict__ V, long long vstride, int nv,
+                                                              float2* __restrict__ W, long long D, int nb,
+                                                              long long rows_per_chunk, const cplx* __restrict__ h,
+                                                              int hld, cplx* __restrict__ partial) {
+  constexpr int TY = SW_THREADS / CW, IG = SwGroups<NV>::IG, NPG = SwGroups<NV>::NPG, RPG = TY / IG;
+  constexpr int SLOTS = NPG + 1;
+  static_assert(TY % IG == 0, "thread rows per group");
+  extern __shared__ __align__(16) unsigned char sw_raw[];
+  float2* ring = reinterpret_cast<float2*>(sw_raw);                       // [SW_STAGES][SLOTS][SW_THREADS]
+  float2* share = ring + (size_t)SW_STAGES * SLOTS * SW_THREADS;          // [2][TY][CW]
+  cplx* red = reinterpret_cast<cplx*>(share + 2 * SW_THREADS);            // [TY][CW]
+  const int tid = threadIdx.x, x = tid % CW, y = tid / CW;
+  const int g = y / RPG, yr = y % RPG;
+  const int c = blockIdx.x * CW + x;
+  const int i0 = g * NPG, ng = nv - i0;
   const long long r0 = blockIdx.y * rows_per_chunk;
   const long long r1 = min(D, r0 + rows_per_chunk);
-  const VT* Vg = V + (long long)i0 * vstride;
-  VT hv[NPG];
+  const long long nsteps = (r1 - r0 + RPG - 1) / RPG;   // the same for every thread (barriers inside)
+  const float2* Vg = V + (long long)i0 * vstride;
+  auto issue = [&](long long t) {
+    float2* st = ring + (size_t)(t % SW_STAGES) * SLOTS * SW_THREADS + tid;
+    const long long nu = r0 + t * RPG + yr;
+    const bool ok = c < nb && nu < r1;
+    const long long off = ok ? nu * nb + c : 0;
+    // predicated-off copies zero-fill and read nothing; they are given the valid base address V
+#pragma unroll
+    for (int li = 0; li < NPG; ++li) {
+      const bool on = ok && li < ng;
+      cp_async8(st + li * SW_THREADS, on ? Vg + li * vstride + off : V, on);
+    }
+    cp_async8(st + NPG * SW_THREADS, W + off, ok);
+  };
+  float2 hv[NPG];
 #pragma unroll
   for (int li = 0; li < NPG; ++li) {
-    const bool on = c < nb && li < ng;
-    hv[li].x = on ? (R)h[(long long)c * hld + i0 + li].x : R(0);
-    hv[li].y = on ? (R)h[(long long)c * hld + i0 + li].y : R(0);
+    const bool on = MODE != 0 && c < nb && li < ng;
+    hv[li] = on ? make_float2((float)h[(long long)c * hld + i0 + li].x, (float)h[(long long)c * hld + i0 + li].y)
+                : make_float2(0.f, 0.f);
   }
-  R ax[NPG], ay[NPG];
+  float ax[NPG], ay[NPG];
 #pragma unroll
-  for (int li = 0; li < NPG; ++li) { ax[li] = R(0); ay[li] = R(0); }
-  R nrm = R(0);
-  int buf = 0;
-  // the trip count is the same for every thread of the block (barriers inside)
-  for (long long base = r0; base < r1; base += (long long)CU_U * RPG, buf ^= 1) {
-    VT v[CU_U][NPG], w[CU_U];
-    bool ok[CU_U];
+  for (int li = 0; li < NPG; ++li) { ax[li] = 0.f; ay[li] = 0.f; }
+  float nrm = 0.f;
 #pragma unroll
-    for (int u = 0; u < CU_U; ++u) {
-      const long long nu = base + u * RPG + yr;
-      ok[u] = c < nb && nu < r1;
-      w[u].x = R(0); w[u].y = R(0);
-      if (ok[u]) w[u] = W[nu * nb + c];
+  for (int t = 0; t < SW_STAGES - 1; ++t) {
+    if (t < nsteps) issue(t);
+    cp_async_commit();
+  }
+  for (long long t = 0; t < nsteps; ++t) {
+    if (t + SW_STAGES - 1 < nsteps) issue(t + SW_STAGES - 1);
+    cp_async_commit();
+    cp_async_wait<SW_STAGES - 1>();   // this thread's copies of step t have landed
+    const float2* st = ring + (size_t)(t % SW_STAGES) * SLOTS * SW_THREADS + tid;
+    float2 w = st[NPG * SW_THREADS];
+    float2 v[NPG];
 #pragma unroll
-      for (int li = 0; li < NPG; ++li) {
-        v[u][li].x = R(0); v[u][li].y = R(0);
-        if (ok[u] && li < ng) v[u][li] = Vg[li * vstride + nu * nb + c];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < CU_U; ++u) {
-      VT s;
-      s.x = R(0); s.y = R(0);
+    for (int li = 0; li < NPG; ++li) v[li] = st[li * SW_THREADS];
+    const long long nu = r0 + t * RPG + yr;
+    const bool ok = c < nb && nu < r1;
+    if constexpr (MODE != 0) {
+      float sx = 0.f, sy = 0.f;
 #pragma unroll
       for (int li = 0; li < NPG; ++li) {
-        s.x += v[u][li].x * hv[li].x - v[u][li].y * hv[li].y;
-        s.y += v[u][li].x * hv[li].y + v[u][li].y * hv[li].x;
+        sx += v[li].x * hv[li].x - v[li].y * hv[li].y;
+        sy += v[li].x * hv[li].y + v[li].y * hv[li].x;
       }
       if constexpr (IG == 1) {
-        w[u].x -= s.x; w[u].y -= s.y;
+        w.x -= sx; w.y -= sy;
       } else {
-        share[buf][u][threadIdx.y][x] = s;
-      }
-    }
-    if constexpr (IG > 1) {
-      __syncthreads();
-#pragma unroll
-      for (int u = 0; u < CU_U; ++u)
+        float2* sh = share + (size_t)(t & 1) * SW_THREADS;
+        sh[tid] = make_float2(sx, sy);
+        __syncthreads();
 #pragma unroll
         for (int gg = 0; gg < IG; ++gg) {
-          const VT s = share[buf][u][gg * RPG + yr][x];
-          w[u].x -= s.x; w[u].y -= s.y;
+          const float2 o = sh[(gg * RPG + yr) * CW + x];
+          w.x -= o.x; w.y -= o.y;
         }
+      }
+      if (g == 0 && ok) W[nu * nb + c] = w;
     }
+    if constexpr (MODE == 0 || MODE == 1) {
 #pragma unroll
-    for (int u = 0; u < CU_U; ++u) {
-      if (!ok[u]) continue;
-      if (g == 0) W[(base + u * RPG + yr) * nb + c] = w[u];
-      if constexpr (DOT) {
+      for (int li = 0; li < NPG; ++li) {
+        ax[li] += v[li].x * w.x + v[li].y * w.y;
+        ay[li] += v[li].x * w.y - v[li].y * w.x;
+      }
+    } else {
+      nrm += w.x * w.x + w.y * w.y;
+    }
+  }
+  cp_async_wait<0>();
+  if constexpr (MODE == 2) {
+    red[tid] = make_cuDoubleComplex(g == 0 ? (double)nrm : 0.0, 0.0);
+    __syncthreads();
+    if (y == 0 && c < nb) {
+      double t2 = 0.0;
+      for (int k = 0; k < RPG; ++k) t2 += red[k * CW + x].x;
+      partial[(long long)blockIdx.y * nb + c] = make_cuDoubleComplex(t2, 0.0);
+    }
+  } else {
 #pragma unroll
-        for (int li = 0; li < NPG; ++li) {
-          ax[li] += v[u][li].x * w[u].x + v[u][li].y * w[u].y;
-          ay[li] += v[u][li].x * w[u].y - v[u][li].y * w[u].x;
-        }
-      } else {
-        nrm += w[u].x * w[u].x + w[u].y * w[u].y;
+    for (int li = 0; li < NPG; ++li) {
+      __syncthreads();
+      red[tid] = make_cuDoubleComplex((double)ax[li], (double)ay[li]);
+      __syncthreads();
+      const int i = i0 + li;
+      if (yr == 0 && c < nb && i < nv) {
+        cplx sum = red[tid];
+        for (int k = 1; k < RPG; ++k) { sum.x += red[tid + k * CW].x; sum.y += red[tid + k * CW].y; }
+        partial[((long long)blockIdx.y * nv + i) * nb + c] = sum;
       }
     }
   }
-  if constexpr (DOT) {
-    md_reduce<VT, NV, R>(ax, ay, nv, c, nb, partial, red);
-  } else {
-    red[threadIdx.y][x] = make_cuDoubleComplex(g == 0 ? (double)nrm : 0.0, 0.0);
-    __syncthreads();
-    if (threadIdx.y == 0 && c < nb) {
-      double t = 0.0;
-      for (int k = 0; k < RPG; ++k) t += red[k][x].x;
-      partial[(long long)blockIdx.y * nb + c] = make_cuDoubleComplex(t, 0.0);
-    }
+}
+
+// column width of the sweep blocks for a batch of nb columns
+int sweep_cw(int nb) { return nb >= 32 ? 32 : nb > 8 ? 16 : nb > 4 ? 8 : 4; }
+// rows per chunk of the pipelined sweeps: at most one wave of two resident blocks per SM (a block count
+// just above the resident slots would leave a short second wave that takes as long as the first)
+long long sweep_rows(long long D, int nb) {
+  const int cw = sweep_cw(nb);
+  const long long gx = (nb + cw - 1) / cw;
+  const long long nchunk = std::max<long long>(1, (152LL * 2) / gx);
+  return std::max<long long>(64, (D + nchunk - 1) / nchunk);
+}
+
+template <int NV, int MODE, int CW>
+void launch_sweep_cw(const float2* V, long long vstride, int nv, float2* W, long long D, int nb, const cplx* h, int hld,
+                     cplx* partial, cudaStream_t s) {
+  static bool attr[64] = {};   // dynamic shared memory above 48 KB: set once per device
+  int dev = 0;
+  GFCC_CUDA(cudaGetDevice(&dev));
+  GFCC_CHECK(dev >= 0 && dev < 64, GFCC_ERR_ARG, "device ordinal above 63");
+  constexpr size_t bytes = sweep_smem_bytes<NV, CW>();
+  if (!attr[dev]) {
+    GFCC_CUDA(cudaFuncSetAttribute(sweep_kernel<NV, MODE, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    attr[dev] = true;
   }
+  const long long rows = sweep_rows(D, nb);
+  const dim3 grid((unsigned)((nb + CW - 1) / CW), (unsigned)((D + rows - 1) / rows));
+  sweep_kernel<NV, MODE, CW><<<grid, SW_THREADS, bytes, s>>>(V, vstride, nv, W, D, nb, rows, h, hld, partial);
+}
+template <int MODE>
+void launch_sweep(const float2* V, long long vstride, int nv, float2* W, long long D, int nb, const cplx* h, int hld,
+                  cplx* partial, cudaStream_t s) {
+  with_nv(nv, [&](auto NVc) {
+    constexpr int NV = decltype(NVc)::value;
+    switch (sweep_cw(nb)) {
+      case 32: launch_sweep_cw<NV, MODE, 32>(V, vstride, nv, W, D, nb, h, hld, partial, s); break;
+      case 16: launch_sweep_cw<NV, MODE, 16>(V, vstride, nv, W, D, nb, h, hld, partial, s); break;
+      case 8: launch_sweep_cw<NV, MODE, 8>(V, vstride, nv, W, D, nb, h, hld, partial, s); break;
+      default: launch_sweep_cw<NV, MODE, 4>(V, vstride, nv, W, D, nb, h, hld, partial, s); break;
+    }
+  });
+  GFCC_LAUNCH_CHECK();
 }
 
 // rows per chunk of the CGS sweeps: at least 256 chunks and two waves of blocks (two resident blocks
@@ -494,8 +577,7 @@ static void inner_sigma(gfcc_ctx* c, const cplx* Z, cplx* W, int nb, const cplx*
 static void inner_sigma(gfcc_ctx* c, const cuFloatComplex* Z, cuFloatComplex* W, int nb, const cplx* sh, int prec,
                         bool tr, cudaStream_t s) {
   (void)prec;
-  (void)tr;
-  sigma_lowprec_f32(c, Z, W, nb, sh, s);
+  sigma_lowprec_f32(c, Z, W, nb, sh, s, tr);
 }
 
 // Restarted GMRES with iterative refinement; VT is the precision of the Krylov basis (FP64 for the
@@ -541,7 +623,10 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
   {  // chunk partial sums of the Gram-Schmidt sweeps and norms, at their largest (no regrowth per step)
     const long long rows_cn = std::max<long long>(256, (D + 511) / 512);
     long long md = 0;   // the chunk count of the sweeps depends on the batch width
-    for (int b = 1; b <= nb0; ++b) md = std::max(md, (D + cgs_rows(D, b) - 1) / cgs_rows(D, b) * b);
+    for (int b = 1; b <= nb0; ++b) {
+      md = std::max(md, (D + cgs_rows(D, b) - 1) / cgs_rows(D, b) * b);
+      md = std::max(md, (D + sweep_rows(D, b) - 1) / sweep_rows(D, b) * b);
+    }
     partial.alloc(std::max(md * (k + 1), (D + rows_cn - 1) / rows_cn * nb0));
   }
   GFCC_CUDA(cudaMemcpyAsync(Bw.p, Bin, sizeof(cplx) * D * nb0, cudaMemcpyDeviceToDevice, s));
@@ -689,26 +774,24 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
           // algorithmic HBM bytes of the three sweeps: V read three times, w read three times and
           // written twice
           ProfScope pcgs(PROF_KRYLOV_CGS, (3.0 * nv + 5.0) * (double)D * nb * sizeof(VT), s);
-          const long long rows = cgs_rows(D, nb);
+          const long long rows = sweep_rows(D, nb);
           const int nchunk = (int)((D + rows - 1) / rows);
-          dim3 grid((nb + MD_TX - 1) / MD_TX, nchunk);
           const double vbytes = (double)D * nb * sizeof(VT);   // one basis vector of the batch
           const int small = nb < MD_TX ? 1 : 0;
+          const float2* Vf = reinterpret_cast<const float2*>(V.p);
+          float2* Wf = reinterpret_cast<float2*>(Ww.p);
           {
             ProfScope pk(small ? PROF_CGS_SMALL_NB : PROF_CGS_MULTIDOT, (nv + 1.0) * vbytes, s);
-            multidot<VT>(V.p, vstride, nv, Ww.p, D, nb, hb.p, k + 1, 0, false, partial, s);
+            launch_sweep<0>(Vf, vstride, nv, Wf, D, nb, nullptr, 0, partial.p, s);
           }
+          reduce_partial_kernel<<<(nv * nb + 255) / 256, 256, 0, s>>>(partial.p, nchunk, nv, nb, hb.p, k + 1, 0, 0);
+          GFCC_LAUNCH_CHECK();
           add_h_kernel<<<(nb * nv + 255) / 256, 256, 0, s>>>(hb.p, k + 1, H.p + (long long)j * (k + 1), (k + 1) * k, nv,
                                                              nb, 0);
           GFCC_LAUNCH_CHECK();
-          partial.alloc((long long)nchunk * nv * nb);
           {
             ProfScope pk(small ? PROF_CGS_SMALL_NB : PROF_CGS_UPDATE_DOT, (nv + 2.0) * vbytes, s);
-            with_nv(nv, [&](auto NVc) {
-              cgs_update_kernel<VT, decltype(NVc)::value, true><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(
-                  V.p, vstride, nv, Ww.p, D, nb, rows, hb.p, k + 1, partial.p);
-            });
-            GFCC_LAUNCH_CHECK();
+            launch_sweep<1>(Vf, vstride, nv, Wf, D, nb, hb.p, k + 1, partial.p, s);
           }
           reduce_partial_kernel<<<(nv * nb + 255) / 256, 256, 0, s>>>(partial.p, nchunk, nv, nb, hb.p, k + 1, 0, 0);
           GFCC_LAUNCH_CHECK();
@@ -717,11 +800,7 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
           GFCC_LAUNCH_CHECK();
           {
             ProfScope pk(small ? PROF_CGS_SMALL_NB : PROF_CGS_UPDATE_NORM, (nv + 2.0) * vbytes, s);
-            with_nv(nv, [&](auto NVc) {
-              cgs_update_kernel<VT, decltype(NVc)::value, false><<<grid, dim3(MD_TX, MD_TY), 0, s>>>(
-                  V.p, vstride, nv, Ww.p, D, nb, rows, hb.p, k + 1, partial.p);
-            });
-            GFCC_LAUNCH_CHECK();
+            launch_sweep<2>(Vf, vstride, nv, Wf, D, nb, hb.p, k + 1, partial.p, s);
           }
           reduce_partial_kernel<<<(nb + 255) / 256, 256, 0, s>>>(partial.p, nchunk, 1, nb, tmpc.p, 1, 0, 0);
           GFCC_LAUNCH_CHECK();
@@ -764,7 +843,7 @@ static void gmres_impl(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, con
 
 void gmres_batched(gfcc_ctx* c, const cplx* Bin, cplx* Xout, cplx* Rout, const cplx* shifts_dev, int nb0,
                    SolveStatus& st, bool transpose, const cplx* X0) {
-  const bool f32 = (c->opts.precision == GFCC_PREC_TF32 || c->opts.precision == GFCC_PREC_BF16) && !transpose;
+  const bool f32 = c->opts.precision == GFCC_PREC_TF32 || c->opts.precision == GFCC_PREC_BF16;
   if (f32) gmres_impl<cuFloatComplex>(c, Bin, Xout, Rout, shifts_dev, nb0, st, transpose, X0);
   else gmres_impl<cplx>(c, Bin, Xout, Rout, shifts_dev, nb0, st, transpose, X0);
 }

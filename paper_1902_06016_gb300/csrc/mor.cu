@@ -110,15 +110,35 @@ __global__ void house_left2_kernel(cplx* __restrict__ A, long long lda, int c0a,
   }
 }
 // w[k][row] = sum_j A_k[row][c0 + j] v[j] for every matrix k and row (w rows stacked, matrix k at woff[k])
-__global__ void house_right_w4_kernel(RightMats m, int c0, int len, const cplx* __restrict__ v, cplx* __restrict__ w) {
-  int row = blockIdx.x * blockDim.x + threadIdx.x;
-  int k = 0, off = 0;
-  while (k < m.n && row >= m.rows[k]) { row -= m.rows[k]; off += m.rows[k]; ++k; }
-  if (k >= m.n) return;
+// w[row] = sum_j A[row][c0 + j] v[j] over the rows of all right-side matrices: a block takes a tile of 32
+// rows (lanes, coalesced along the column-major rows) and its 8 warps split the reflector's length, so
+// that short and long reflectors alike keep many warps in flight; the warps' sums meet in shared memory
+__global__ void __launch_bounds__(256) house_right_w4_kernel(RightMats m, int c0, int len, const cplx* __restrict__ v,
+                                                             cplx* __restrict__ w) {
+  __shared__ cplx red[8][32];
+  int t = blockIdx.x, k = 0, off = 0;
+  while (k < m.n) {   // tile t -> matrix k (tiles do not cross matrices)
+    const int nt = (m.rows[k] + 31) / 32;
+    if (t < nt) break;
+    t -= nt;
+    off += m.rows[k];
+    ++k;
+  }
+  if (k >= m.n) return;   // uniform for the whole block
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int row = t * 32 + lane;
+  const bool ok = row < m.rows[k];
   const cplx* A = m.p[k];
   cplx sum = cz();
-  for (int j = 0; j < len; ++j) sum = cuCadd(sum, cuCmul(A[(long long)(c0 + j) * m.ld[k] + row], v[j]));
-  w[off + row] = sum;
+  if (ok)
+    for (int j = wid; j < len; j += 8) sum = cuCadd(sum, cuCmul(A[(long long)(c0 + j) * m.ld[k] + row], v[j]));
+  red[wid][lane] = sum;
+  __syncthreads();
+  if (wid == 0 && ok) {
+    cplx r = red[0][lane];
+    for (int q = 1; q < 8; ++q) r = cuCadd(r, red[q][lane]);
+    w[off + row] = r;
+  }
 }
 // A_k[row][c0 + j] -= tau w[k][row] conj(v[j])
 __global__ void house_right_update4_kernel(RightMats m, int c0, int len, const cplx* __restrict__ v,
@@ -1140,8 +1160,11 @@ static void hessenberg(gfcc_ctx* c, bool want_res) {
   add(Hw, m, m);
   add(cw, nq, nq);
   if (want_res) { add(A1, qn, qn); add(A2, qn, qn); }
-  long long rows_all = 0;
-  for (int k = 0; k < rm.n; ++k) rows_all += rm.rows[k];
+  long long rows_all = 0, tiles_all = 0;
+  for (int k = 0; k < rm.n; ++k) {
+    rows_all += rm.rows[k];
+    tiles_all += (rm.rows[k] + 31) / 32;
+  }
   for (int j = 0; j + 2 < m; ++j) {
     const int len = m - j - 1;
     cplx* v = ms.hV.p + (long long)j * m;
@@ -1152,7 +1175,7 @@ static void hessenberg(gfcc_ctx* c, bool want_res) {
     house_left2_kernel<<<(m - j) + np, 256, 0, s>>>(Hw, m, j, m - j, bw, m, np, j + 1, len, v, tau);
     GFCC_LAUNCH_CHECK();
     // right: H, chat and the residual coefficient matrices
-    house_right_w4_kernel<<<(unsigned)((rows_all + 127) / 128), 128, 0, s>>>(rm, j + 1, len, v, wv.p);
+    house_right_w4_kernel<<<(unsigned)tiles_all, 256, 0, s>>>(rm, j + 1, len, v, wv.p);
     GFCC_LAUNCH_CHECK();
     house_right_update4_kernel<<<grid_for(rows_all * len), 256, 0, s>>>(rm, j + 1, len, v, wv.p, tau,
                                                                         rows_all * len);

@@ -579,6 +579,16 @@ void launch_accumulate(bool small, int grid, cudaStream_t s, const int* part, in
 }  // namespace
 
 namespace {
+// algorithmic bytes of writing an M x Np output (a complex output holds Np / 2 complex columns), with a
+// read of the old values when it is accumulated into
+double out_bytes(const OzOut& o, long long M, long long Np) {
+  if (o.complex_out) {
+    const bool rd = o.cbeta.x != 0.0 || o.cbeta.y != 0.0;
+    return (rd ? 2.0 : 1.0) * 16.0 * (double)M * (double)(Np / 2);
+  }
+  return (o.beta != 0.0 ? 2.0 : 1.0) * 8.0 * (double)M * (double)Np;
+}
+
 // Exact product of sliced rows into o. When the int32 split sums of all diagonals fit in 4 GB they are
 // kept side by side and summed into the output in one pass. Otherwise the diagonal GEMMs run one at a
 // time, each followed by its accumulation into an FP64 buffer, over column chunks that bound the
@@ -617,7 +627,8 @@ void oz_run(const SlicedRows& A, const SlicedRows& B, long long M, long long Np,
     const int grid = warp ? (int)std::min<long long>(std::max<long long>((elements * 32 + 255) / 256, 1), 152LL * 32)
                           : grid_for(elements);
     const bool small = M * Np < (1LL << 32);
-    ProfScope pa(PROF_OZ_ACCUM, 0.0, s);
+    // bytes: every int32 split sum read once, the output written once
+    ProfScope pa(PROF_OZ_ACCUM, 4.0 * splits * (double)M * (double)Np + out_bytes(o, M, Np), s);
     if (splits == ns) {   // one split per diagonal
       if (o.complex_out) {
         if (small) launch_output1<2, unsigned>(ns, grid, s, w.islabs.p, dg, M, Np, A.expo.p, B.expo.p, o);
@@ -664,7 +675,10 @@ void oz_run(const SlicedRows& A, const SlicedRows& B, long long M, long long Np,
                             : grid_for(elements);
       const bool small = M * nn < (1LL << 32);
       const int* eb = B.expo.p + n0;
-      ProfScope pa(PROF_OZ_ACCUM, 0.0, s);
+      // bytes: the split sums read, the FP64 accumulator read (after the first diagonal) and written (or,
+      // on the last diagonal, the output written)
+      ProfScope pa(PROF_OZ_ACCUM, 4.0 * zeff * (double)M * (double)nn + (first ? 0.0 : 8.0 * (double)M * (double)nn) +
+                                      (mode == 0 ? 8.0 * (double)M * (double)nn : out_bytes(oc, M, nn)), s);
       if (mode == 0) {
         if (warp) launch_accumulate<true, 0>(small, grid, s, w.islabs.p, zeff, M, nn, scale, first, w.acc.p, A.expo.p, eb, oc);
         else launch_accumulate<false, 0>(small, grid, s, w.islabs.p, zeff, M, nn, scale, first, w.acc.p, A.expo.p, eb, oc);
@@ -734,7 +748,9 @@ void oz_run_stacked(const SlicedRows& A, const SlicedRows& Bsm, long long M, lon
   const bool warp = !one_split && elements < 152LL * 256 && splits > 8 * ns;
   const int grid = warp ? (int)std::min<long long>(std::max<long long>((elements * 32 + 255) / 256, 1), 152LL * 32)
                         : grid_for(elements);
-  ProfScope pa(PROF_OZ_ACCUM, 0.0, s);
+  double part_bytes = 0.0;
+  for (int i = 0; i < ns; ++i) part_bytes += 4.0 * st.zs[i] * (double)M * (double)st.ncol[i];
+  ProfScope pa(PROF_OZ_ACCUM, part_bytes + out_bytes(o, M, Np), s);
   if (M * Np < (1LL << 32))
     launch_stack_output<unsigned>(ns, one_split, warp, grid, s, w.islabs.p, st, M, Np, A.expo.p, Bsm.expo.p, o);
   else
@@ -810,7 +826,10 @@ void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s) {
   sb.slices.alloc(sizeof(__nv_bfloat16) * 2 * N * ns * sb.kp);
   sb.expo.alloc(2 * N);
   {
-    ProfScope ps(PROF_OZ_SLICE, 0.0, s);
+    // bytes: each complex operand read once and its slices written once (A only when not cached)
+    const double sb_bytes = 16.0 * (double)N * (double)K + 2.0 * (double)(2 * N) * ns * (double)sb.kp;
+    const double sa_bytes = reuse ? 0.0 : 16.0 * (double)M * (double)K + 2.0 * (double)M * ns * (double)sa.kp;
+    ProfScope ps(PROF_OZ_SLICE, sa_bytes + sb_bytes, s);
     DBuf<unsigned long long>& mxa = z.mxa;
     DBuf<unsigned long long>& mxb = z.mxb;
     mxa.alloc(M);
@@ -875,7 +894,8 @@ void oz_slice_into(const double* X, long long ldx, long long nrows, long long K,
                    cudaStream_t s) {
   GFCC_CHECK(row0 >= 0 && row0 + nrows <= out.rows && K <= out.kp, GFCC_ERR_ARG, "oz_slice_into: out of range");
   if (nrows == 0) return;
-  ProfScope prof(PROF_OZ_SLICE, 0.0, s);
+  // bytes: the FP64 rows read once, their slices written once
+  ProfScope prof(PROF_OZ_SLICE, 8.0 * (double)nrows * (double)K + 2.0 * (double)nrows * out.ns * (double)out.kp, s);
   __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out.slices.p) + row0 * out.ns * out.kp;
   if (out.kp <= 2048) {   // short rows: a warp per row
     slice_rows_warp_kernel<<<(unsigned)((nrows * 32 + 255) / 256), 256, 0, s>>>(X, ldx, nrows, K, out.kp,

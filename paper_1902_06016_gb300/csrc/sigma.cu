@@ -113,16 +113,15 @@ void sigma_batch(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, int ldb, const cpl
                  int precision, bool transpose, cudaStream_t s) {
   GFCC_CHECK(ldb == nb, GFCC_ERR_ARG, "sigma_batch: internal layout needs ldb == nb");
   if (nb == 0) return;
-  const bool lowp = (precision == GFCC_PREC_TF32 || precision == GFCC_PREC_BF16) && !transpose;
+  const bool lowp = precision == GFCC_PREC_TF32 || precision == GFCC_PREC_BF16;
   ProfScope prof(lowp ? PROF_SIGMA_LP : PROF_SIGMA_EX, 0.0, s);
-  if (precision == GFCC_PREC_FP64_TC && !transpose) {
-    sigma_emulated(c, X, Y, nb, shift, s);
+  if (precision == GFCC_PREC_FP64_TC) {
+    sigma_emulated(c, X, Y, nb, shift, s, transpose);
     return;
   }
-  if (precision == GFCC_PREC_FP64_TC) precision = GFCC_PREC_FP64;
-  if (precision != GFCC_PREC_FP64 && !transpose) {   // the transposed action always runs in FP64
+  if (lowp) {
     GFCC_CHECK(c->lp.kind == precision && c->lp.impl, GFCC_ERR_STATE, "sigma: low-precision operands not built");
-    sigma_lowprec(c, X, Y, nb, shift, s);
+    sigma_lowprec(c, X, Y, nb, shift, s, transpose);
     return;
   }
   const int o = c->o, v = c->v, P = c->P;

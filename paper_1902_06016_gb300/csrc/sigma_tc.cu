@@ -264,6 +264,39 @@ __global__ void cols_scatter_kernel(const cplx* __restrict__ src, int nk, cplx* 
 }  // namespace
 
 // ------------------------------------------------------------------------------------------------
+// The operator blocks in the roles the sigma GEMMs give them. M^T has the same structure as M with the
+// blocks permuted: the ring runs on WrT (as in the FP64 transposed sigma), xe = T2p^T r2 replaces
+// xe = Vt r2, the 1h <- 2h1p block is A21^T, the 2h1p <- 1h block A12^T, the three-body output block
+// Vt^T, and Woo and A11 are transposed.
+struct OpView {
+  const double *Wr, *Woo, *Vt, *A12, *T2p, *A21, *A11;
+};
+static OpView op_view(gfcc_ctx* c, bool transpose) {
+  Operator& op = c->op;
+  if (!transpose) return {op.Wr.p, op.Woo.p, op.Vt.p, op.A12.p, op.T2p.p, op.A21.p, op.A11.p};
+  build_transpose_operator(c);
+  if (!op.have_X) {
+    const int o = c->o, v = c->v, P = c->P;
+    const long long Pv = (long long)P * v;
+    cudaStream_t s = c->stream;
+    auto tr = [&](const double* src, int rows, int cols, DBuf<double>& dst) {   // dst[cols][rows] = src^T
+      dst.alloc((long long)rows * cols);
+      int dims[2] = {rows, cols};
+      int pm[2] = {1, 0};
+      permute(src, dims, 2, pm, dst.p, 1.0, 0.0, s);
+    };
+    tr(op.Woo.p, P, P, op.WooX);
+    tr(op.T2p.p, (int)Pv, v, op.VtX);     // T2p [Pv][v] -> [v][Pv]
+    tr(op.A21.p, (int)Pv, o, op.A12X);    // A21 [Pv][o] -> [o][Pv]
+    tr(op.Vt.p, v, (int)Pv, op.T2pX);     // Vt [v][Pv]  -> [Pv][v]
+    tr(op.A12.p, o, (int)Pv, op.A21X);    // A12 [o][Pv] -> [Pv][o]
+    tr(op.A11.p, o, o, op.A11X);
+    GFCC_CUDA(cudaStreamSynchronize(s));
+    op.have_X = true;
+  }
+  return {op.WrT.p, op.WooX.p, op.VtX.p, op.A12X.p, op.T2pX.p, op.A21X.p, op.A11X.p};
+}
+
 struct LpState {
   TcKind kind;
   int Kr = 0, Kp = 0, Kpv = 0, Kvo = 0;
@@ -274,7 +307,9 @@ struct LpState {
   int nb_cap = 0, ksplit = 1;
 };
 
-static LpState* lp_state(gfcc_ctx* c) { return reinterpret_cast<LpState*>(c->lp.impl); }
+static LpState* lp_state(gfcc_ctx* c, bool transpose = false) {
+  return reinterpret_cast<LpState*>(transpose ? c->lp.implT : c->lp.impl);
+}
 
 // FP64-accurate sigma from exact bf16 slices (residuals of the iterative refinement)
 struct EmuState {
@@ -284,44 +319,53 @@ struct EmuState {
   DBuf<cplx> Xc, Yc;
   OzWork work;
 };
-static EmuState* emu_state(gfcc_ctx* c) { return reinterpret_cast<EmuState*>(c->lp.emu); }
+static EmuState* emu_state(gfcc_ctx* c, bool transpose = false) {
+  return reinterpret_cast<EmuState*>(transpose ? c->lp.emuT : c->lp.emu);
+}
 
 void free_low_precision(gfcc_ctx* c) {
   delete lp_state(c);
+  delete lp_state(c, true);
   c->lp.impl = nullptr;
+  c->lp.implT = nullptr;
   c->lp.kind = 0;
   delete emu_state(c);
+  delete emu_state(c, true);
   c->lp.emu = nullptr;
+  c->lp.emuT = nullptr;
 }
 
-void build_emulated(gfcc_ctx* c) {
-  if (c->lp.emu) return;
+static void build_emulated(gfcc_ctx* c, bool transpose) {
+  if (transpose ? c->lp.emuT : c->lp.emu) return;
   const int o = c->o, v = c->v, P = c->P;
   const long long ov = (long long)o * v, Pv = (long long)P * v;
   cudaStream_t s = c->stream;
+  const OpView ov_ = op_view(c, transpose);
   auto* st = new EmuState();
-  c->lp.emu = st;
-  oz_slice(c->op.Wr.p, ov, ov, ov, false, st->Wr, s);
-  oz_slice(c->op.Woo.p, P, P, P, false, st->Woo, s);
+  (transpose ? c->lp.emuT : c->lp.emu) = st;
+  oz_slice(ov_.Wr, ov, ov, ov, false, st->Wr, s);
+  oz_slice(ov_.Woo, P, P, P, false, st->Woo, s);
   st->Aup.rows = v + o;
   st->Aup.kp = tc_pad_k(TcKind::BF16, Pv);
   st->Aup.reversed = false;
   st->Aup.ns = OZ_SLICES;
   st->Aup.slices.alloc(2LL * (v + o) * OZ_SLICES * st->Aup.kp);
   st->Aup.expo.alloc(v + o);
-  oz_slice_into(c->op.Vt.p, Pv, v, Pv, st->Aup, 0, s);
-  oz_slice_into(c->op.A12.p, Pv, o, Pv, st->Aup, v, s);
+  oz_slice_into(ov_.Vt, Pv, v, Pv, st->Aup, 0, s);
+  oz_slice_into(ov_.A12, Pv, o, Pv, st->Aup, v, s);
   st->stage.alloc(Pv * (v + o));
-  convert_down_kernel<F64Elem><<<grid_for(Pv * (v + o)), 256, 0, s>>>(c->op.T2p.p, c->op.A21.p, Pv, v, o, st->stage.p,
-                                                                       v + o);
+  convert_down_kernel<F64Elem><<<grid_for(Pv * (v + o)), 256, 0, s>>>(ov_.T2p, ov_.A21, Pv, v, o, st->stage.p, v + o);
   GFCC_LAUNCH_CHECK();
   oz_slice(st->stage.p, v + o, Pv, v + o, false, st->Adn, s);
   GFCC_CUDA(cudaStreamSynchronize(s));
 }
 
-void sigma_emulated(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shift, cudaStream_t s) {
-  build_emulated(c);
-  EmuState& st = *emu_state(c);
+void build_emulated(gfcc_ctx* c) { build_emulated(c, false); }
+
+void sigma_emulated(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shift, cudaStream_t s, bool transpose) {
+  build_emulated(c, transpose);
+  EmuState& st = *emu_state(c, transpose);
+  const double* A11 = op_view(c, transpose).A11;
   const int o = c->o, v = c->v, P = c->P;
   const long long ov = (long long)o * v, Pv = (long long)P * v, D = c->D;
   const int chunk = 64;
@@ -355,7 +399,7 @@ void sigma_emulated(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shi
     oz_slice(st.stage.p, ov, nring, ov, true, st.Bring, s);
     oz_gemm(st.Wr, st.Bring, ov, nring, st.CT.p, nring, 0.0, st.work, s);
     combine_lp_kernel<double, cplx><<<grid_for(D * nbc), 256, 0, s>>>(st.Xc.p, st.Yc.p, st.up.p, nsm, st.C2.p, st.CT.p,
-                                                                c->op.A11.p, c->op.diag.p,
+                                                                A11, c->op.diag.p,
                                                                 shift ? shift + c0 : nullptr, o, v, D, nbc);
     GFCC_LAUNCH_CHECK();
     cols_scatter_kernel<<<grid_for(D * nbc), 256, 0, s>>>(st.Yc.p, nbc, Y, nb, c0, D);
@@ -366,16 +410,20 @@ void sigma_emulated(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shi
 }
 
 int emulated_error(gfcc_ctx* c) {
-  EmuState* st = emu_state(c);
-  if (!st || st->work.err.n == 0) return 0;
-  int h = 0;
-  GFCC_CUDA(cudaMemcpyAsync(&h, st->work.err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  GFCC_CUDA(cudaStreamSynchronize(c->stream));
-  return h;
+  int any = 0;
+  for (bool tr : {false, true}) {
+    EmuState* st = emu_state(c, tr);
+    if (!st || st->work.err.n == 0) continue;
+    int h = 0;
+    GFCC_CUDA(cudaMemcpyAsync(&h, st->work.err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GFCC_CUDA(cudaStreamSynchronize(c->stream));
+    any |= h;
+  }
+  return any;
 }
 
 template <TcKind K>
-static void build_ops(gfcc_ctx* c, LpState& st) {
+static void build_ops(gfcc_ctx* c, LpState& st, const OpView& w) {
   using T = typename Elem<K>::T;
   const int o = c->o, v = c->v, P = c->P;
   const long long ov = (long long)o * v, Pv = (long long)P * v;
@@ -385,21 +433,21 @@ static void build_ops(gfcc_ctx* c, LpState& st) {
   st.Kpv = tc_pad_k(K, Pv);
   st.Kvo = tc_pad_k(K, v + o);
   st.Wr.alloc(sizeof(T) * ov * st.Kr);
-  convert_rows_kernel<K><<<grid_for(ov * st.Kr), 256, 0, s>>>(c->op.Wr.p, ov, ov, ov, reinterpret_cast<T*>(st.Wr.p), st.Kr);
+  convert_rows_kernel<K><<<grid_for(ov * st.Kr), 256, 0, s>>>(w.Wr, ov, ov, ov, reinterpret_cast<T*>(st.Wr.p), st.Kr);
   GFCC_LAUNCH_CHECK();
   st.Woo.alloc(sizeof(T) * (long long)P * st.Kp);
-  convert_rows_kernel<K><<<grid_for((long long)P * st.Kp), 256, 0, s>>>(c->op.Woo.p, P, P, P, reinterpret_cast<T*>(st.Woo.p),
+  convert_rows_kernel<K><<<grid_for((long long)P * st.Kp), 256, 0, s>>>(w.Woo, P, P, P, reinterpret_cast<T*>(st.Woo.p),
                                                                        st.Kp);
   GFCC_LAUNCH_CHECK();
   st.Aup.alloc(sizeof(T) * (long long)(v + o) * st.Kpv);
-  convert_rows_kernel<K><<<grid_for((long long)v * st.Kpv), 256, 0, s>>>(c->op.Vt.p, Pv, v, Pv,
+  convert_rows_kernel<K><<<grid_for((long long)v * st.Kpv), 256, 0, s>>>(w.Vt, Pv, v, Pv,
                                                                         reinterpret_cast<T*>(st.Aup.p), st.Kpv);
   GFCC_LAUNCH_CHECK();
   convert_rows_kernel<K><<<grid_for((long long)o * st.Kpv), 256, 0, s>>>(
-      c->op.A12.p, Pv, o, Pv, reinterpret_cast<T*>(st.Aup.p) + (long long)v * st.Kpv, st.Kpv);
+      w.A12, Pv, o, Pv, reinterpret_cast<T*>(st.Aup.p) + (long long)v * st.Kpv, st.Kpv);
   GFCC_LAUNCH_CHECK();
   st.Adn.alloc(sizeof(T) * Pv * st.Kvo);
-  convert_down_kernel<Elem<K>><<<grid_for(Pv * st.Kvo), 256, 0, s>>>(c->op.T2p.p, c->op.A21.p, Pv, v, o,
+  convert_down_kernel<Elem<K>><<<grid_for(Pv * st.Kvo), 256, 0, s>>>(w.T2p, w.A21, Pv, v, o,
                                                                reinterpret_cast<T*>(st.Adn.p), st.Kvo);
   GFCC_LAUNCH_CHECK();
   st.err.alloc(1);
@@ -414,23 +462,41 @@ void build_low_precision(gfcc_ctx* c, int kind) {
   auto* st = new LpState();
   c->lp.impl = st;
   st->kind = kind == GFCC_PREC_BF16 ? TcKind::BF16 : TcKind::TF32;
-  if (st->kind == TcKind::BF16) build_ops<TcKind::BF16>(c, *st);
-  else build_ops<TcKind::TF32>(c, *st);
+  if (st->kind == TcKind::BF16) build_ops<TcKind::BF16>(c, *st, op_view(c, false));
+  else build_ops<TcKind::TF32>(c, *st, op_view(c, false));
   c->lp.kind = kind;
 }
 
+// the low-precision operands of M^T, in the kind of the forward ones (built on first use)
+static LpState* lp_state_transposed(gfcc_ctx* c) {
+  if (!c->lp.implT) {
+    LpState* f = lp_state(c);
+    GFCC_CHECK(f != nullptr, GFCC_ERR_STATE, "low-precision operator not built");
+    auto* st = new LpState();
+    c->lp.implT = st;
+    st->kind = f->kind;
+    if (st->kind == TcKind::BF16) build_ops<TcKind::BF16>(c, *st, op_view(c, true));
+    else build_ops<TcKind::TF32>(c, *st, op_view(c, true));
+  }
+  return lp_state(c, true);
+}
+
 int low_precision_error(gfcc_ctx* c) {
-  LpState* st = lp_state(c);
-  if (!st) return emulated_error(c);
   if (emulated_error(c)) return 1;
-  int h = 0;
-  GFCC_CUDA(cudaMemcpyAsync(&h, st->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  GFCC_CUDA(cudaStreamSynchronize(c->stream));
-  return h;
+  for (bool tr : {false, true}) {
+    LpState* st = lp_state(c, tr);
+    if (!st) continue;
+    int h = 0;
+    GFCC_CUDA(cudaMemcpyAsync(&h, st->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GFCC_CUDA(cudaStreamSynchronize(c->stream));
+    if (h) return 1;
+  }
+  return 0;
 }
 
 template <TcKind K, typename VT>
-static void sigma_lp_impl(gfcc_ctx* c, LpState& st, const VT* X, VT* Y, int nb, const cplx* shift, cudaStream_t s) {
+static void sigma_lp_impl(gfcc_ctx* c, LpState& st, const VT* X, VT* Y, int nb, const cplx* shift, cudaStream_t s,
+                          const double* A11) {
   using T = typename Elem<K>::T;
   const int o = c->o, v = c->v, P = c->P;
   const long long ov = (long long)o * v, Pv = (long long)P * v, D = c->D;
@@ -487,27 +553,29 @@ static void sigma_lp_impl(gfcc_ctx* c, LpState& st, const VT* X, VT* Y, int nb, 
           st.err.p, s, PROF_TC_RING, ov);
   nvtxRangePop();
   ProfScope pc(PROF_LP_COMBINE, 0.0, s);
-  combine_lp_kernel<float, VT><<<grid_for(D * nb), 256, 0, s>>>(X, Y, st.up.p, nsm, st.C2.p, st.CT.p, c->op.A11.p, c->op.diag.p,
+  combine_lp_kernel<float, VT><<<grid_for(D * nb), 256, 0, s>>>(X, Y, st.up.p, nsm, st.C2.p, st.CT.p, A11, c->op.diag.p,
                                                      shift, o, v, D, nb);
   GFCC_LAUNCH_CHECK();
 }
 
-void sigma_lowprec(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shift, cudaStream_t s) {
-  LpState* st = lp_state(c);
+void sigma_lowprec(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shift, cudaStream_t s, bool transpose) {
+  LpState* st = transpose ? lp_state_transposed(c) : lp_state(c);
   GFCC_CHECK(st != nullptr, GFCC_ERR_STATE, "low-precision operator not built");
-  if (st->kind == TcKind::BF16) sigma_lp_impl<TcKind::BF16, cplx>(c, *st, X, Y, nb, shift, s);
-  else sigma_lp_impl<TcKind::TF32, cplx>(c, *st, X, Y, nb, shift, s);
+  const double* A11 = op_view(c, transpose).A11;
+  if (st->kind == TcKind::BF16) sigma_lp_impl<TcKind::BF16, cplx>(c, *st, X, Y, nb, shift, s, A11);
+  else sigma_lp_impl<TcKind::TF32, cplx>(c, *st, X, Y, nb, shift, s, A11);
   c->stats.sigma_calls++;
   c->stats.sigma_cols += nb;
 }
 
 void sigma_lowprec_f32(gfcc_ctx* c, const cuFloatComplex* X, cuFloatComplex* Y, int nb, const cplx* shift,
-                       cudaStream_t s) {
-  LpState* st = lp_state(c);
+                       cudaStream_t s, bool transpose) {
+  LpState* st = transpose ? lp_state_transposed(c) : lp_state(c);
   GFCC_CHECK(st != nullptr, GFCC_ERR_STATE, "low-precision operator not built");
   ProfScope prof(PROF_SIGMA_LP, 0.0, s);
-  if (st->kind == TcKind::BF16) sigma_lp_impl<TcKind::BF16, cuFloatComplex>(c, *st, X, Y, nb, shift, s);
-  else sigma_lp_impl<TcKind::TF32, cuFloatComplex>(c, *st, X, Y, nb, shift, s);
+  const double* A11 = op_view(c, transpose).A11;
+  if (st->kind == TcKind::BF16) sigma_lp_impl<TcKind::BF16, cuFloatComplex>(c, *st, X, Y, nb, shift, s, A11);
+  else sigma_lp_impl<TcKind::TF32, cuFloatComplex>(c, *st, X, Y, nb, shift, s, A11);
   c->stats.sigma_calls++;
   c->stats.sigma_cols += nb;
 }

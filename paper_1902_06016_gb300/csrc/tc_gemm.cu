@@ -7,6 +7,11 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 namespace gfcc {
 namespace {
@@ -393,6 +398,41 @@ int sm_count() {
   return cached[dev];
 }
 
+// ---- autotuner of the M-tile group size ----------------------------------------------------------
+// The group size gm (how many 128-row A tiles a group of work units shares while it runs through the N
+// tiles) trades DRAM re-reads of B against L2 room; it changes the order of the work units, not their
+// arithmetic, so every candidate writes the same result. On the first launch of a shape bucket that
+// overwrites its output (beta = 0; not under stream capture) each distinct gm of the L2 budgets below
+// is timed twice with CUDA events on the launching stream, and the fastest is kept for the process.
+// GFCC_AUTOTUNE=0 keeps the default (40 MB) everywhere.
+struct TuneKey {
+  int kind, exact, tiles_m, tn_log2, nk_split, zs;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(kind, exact, tiles_m, tn_log2, nk_split, zs) <
+           std::tie(o.kind, o.exact, o.tiles_m, o.tn_log2, o.nk_split, o.zs);
+  }
+};
+struct TuneResult {
+  int gm = 1, gm_default = 1;
+  float ms_best = 0.f, ms_default = 0.f;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneResult> g_tune;
+std::vector<TuneKey> g_tune_order;   // keys in the order they were tuned (for the report)
+constexpr long long kGmBudgetMB[] = {16, 40, 64, 96, 128};
+constexpr long long kGmDefaultMB = 40;
+
+bool autotune_enabled() {
+  static const int on = [] {
+    const char* e = getenv("GFCC_AUTOTUNE");
+    return (e && e[0] == '0') ? 0 : 1;
+  }();
+  return on != 0;
+}
+int gm_for_budget(long long budget_mb, long long a_tile_bytes, int tiles_m) {
+  return (int)std::max<long long>(1, std::min<long long>(tiles_m, (budget_mb << 20) / std::max(a_tile_bytes, 1LL)));
+}
+
 template <TcKind K, bool EXACT>
 void launch(const CUtensorMap& ma, const CUtensorMap& mb, void* C, long long ldc, long long M, long long N,
             int tiles_m, int tiles_n, int zs, int nk_total, int nk_split, long long split_stride, int beta, int* err,
@@ -407,12 +447,65 @@ void launch(const CUtensorMap& ma, const CUtensorMap& mb, void* C, long long ldc
   }
   const long long units = (long long)zs * tiles_m * tiles_n;
   const int grid = (int)std::min<long long>(units, sm_count());
-  // M-tile group: the A tiles of one group (128 rows x the split's K) fit in about 40 MB of L2
+  auto run = [&](int gm) {
+    tc_gemm_kernel<K, EXACT><<<grid, EXACT ? 320 : 192, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, tiles_m, tiles_n, gm,
+                                                                         zs, nk_total, nk_split, split_stride, beta,
+                                                                         err);
+    GFCC_LAUNCH_CHECK();
+  };
+  // M-tile group: by default the A tiles of one group (128 rows x the split's K) fit in about 40 MB of L2
   const long long a_tile_bytes = (long long)BM * nk_split * KB_BYTES;
-  const int gm = (int)std::max<long long>(1, std::min<long long>(tiles_m, (40LL << 20) / std::max(a_tile_bytes, 1LL)));
-  tc_gemm_kernel<K, EXACT><<<grid, EXACT ? 320 : 192, SMEM_BYTES, s>>>(ma, mb, C, ldc, M, N, tiles_m, tiles_n, gm,
-                                                                       zs, nk_total, nk_split, split_stride, beta, err);
-  GFCC_LAUNCH_CHECK();
+  const int gm_default = gm_for_budget(kGmDefaultMB, a_tile_bytes, tiles_m);
+  int gm = gm_default;
+  std::vector<int> cand;
+  for (long long mb : kGmBudgetMB) {
+    const int g = gm_for_budget(mb, a_tile_bytes, tiles_m);
+    if (std::find(cand.begin(), cand.end(), g) == cand.end()) cand.push_back(g);
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (beta == 0 && cand.size() > 1 && autotune_enabled() && cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
+      cap == cudaStreamCaptureStatusNone) {
+    int tl = 0;
+    while ((1 << tl) < tiles_n) ++tl;
+    const TuneKey key{K == TcKind::BF16 ? 0 : 1, EXACT ? 1 : 0, tiles_m, tl, nk_split, zs};
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      gm = it->second.gm;
+    } else {
+      std::vector<cudaEvent_t> ev(2 * cand.size());
+      for (auto& e : ev) GFCC_CUDA(cudaEventCreate(&e));
+      std::vector<float> best(cand.size(), 1e30f);
+      for (int pass = 0; pass < 2; ++pass) {
+        for (size_t q = 0; q < cand.size(); ++q) {
+          const size_t i = pass == 0 ? q : cand.size() - 1 - q;   // second pass in reverse order
+          GFCC_CUDA(cudaEventRecord(ev[2 * i], s));
+          run(cand[i]);
+          GFCC_CUDA(cudaEventRecord(ev[2 * i + 1], s));
+        }
+        GFCC_CUDA(cudaStreamSynchronize(s));
+        for (size_t i = 0; i < cand.size(); ++i) {
+          float ms = 0.f;
+          GFCC_CUDA(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
+          best[i] = std::min(best[i], ms);
+        }
+      }
+      for (auto& e : ev) cudaEventDestroy(e);
+      size_t ib = 0;
+      for (size_t i = 1; i < cand.size(); ++i)
+        if (best[i] < best[ib]) ib = i;
+      TuneResult r;
+      r.gm = cand[ib];
+      r.gm_default = gm_default;
+      r.ms_best = best[ib];
+      for (size_t i = 0; i < cand.size(); ++i)
+        if (cand[i] == gm_default) r.ms_default = best[i];
+      g_tune[key] = r;
+      g_tune_order.push_back(key);
+      return;   // the output already holds the product (every candidate computes the same)
+    }
+  }
+  run(gm);
 }
 
 }  // namespace
@@ -476,3 +569,20 @@ int tc_exact_splits(long long M, long long N, long long k_pad) {
 }
 
 }  // namespace gfcc
+
+extern "C" int gfcc_autotune_info(int i, int* kind, int* exact, int* tiles_m, int* tiles_n_log2, int* gm, int* gm_default,
+                                  double* ms_best, double* ms_default) {
+  std::lock_guard<std::mutex> lk(gfcc::g_tune_mu);
+  if (i < 0 || i >= (int)gfcc::g_tune_order.size()) return GFCC_ERR_ARG;
+  const gfcc::TuneKey& k = gfcc::g_tune_order[i];
+  const gfcc::TuneResult& r = gfcc::g_tune[k];
+  if (kind) *kind = k.kind == 0 ? GFCC_PREC_BF16 : GFCC_PREC_TF32;
+  if (exact) *exact = k.exact;
+  if (tiles_m) *tiles_m = k.tiles_m;
+  if (tiles_n_log2) *tiles_n_log2 = k.tn_log2;
+  if (gm) *gm = r.gm;
+  if (gm_default) *gm_default = r.gm_default;
+  if (ms_best) *ms_best = r.ms_best;
+  if (ms_default) *ms_default = r.ms_default;
+  return GFCC_OK;
+}

@@ -69,6 +69,7 @@ PROTOTYPES = {
     "gfcc_spectral": (C.c_int, [_vp, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp, C.c_int, _vp]),
     "gfcc_tc_gemm": (C.c_int, [C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]),
     "gfcc_tc_gemm_noalloc": (C.c_int, [C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
+    "gfcc_autotune_info": (C.c_int, [C.c_int, _ip, _ip, _ip, _ip, _ip, _ip, _dp, _dp]),
     "gfcc_launch_count": (C.c_longlong, []),
     "gfcc_profile": (C.c_int, [C.c_int]),
     "gfcc_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_longlong), _dp, _dp]),
@@ -166,6 +167,23 @@ def spectral_adjoint(Abar, orbitals, nq, qorb=None, Gbar=None, stream=None):
     if rc != 0:
         raise GfccError(rc, "gfcc_spectral (adjoint) failed")
     return Gbar
+
+
+def autotune_report():
+    """The autotuner's decisions so far: one dict per tuned GEMM shape bucket."""
+    lib = load()
+    out = []
+    i = 0
+    while True:
+        vals = [C.c_int() for _ in range(6)]
+        mb, md = C.c_double(), C.c_double()
+        if lib.gfcc_autotune_info(i, *[C.byref(x) for x in vals], C.byref(mb), C.byref(md)) != 0:
+            return out
+        kind, exact, tm, tn, gm, gmd = (x.value for x in vals)
+        out.append({"precision": {PREC_BF16: "bf16", PREC_TF32: "tf32"}[kind], "exact_slices": bool(exact),
+                    "tiles_m": tm, "tiles_n_log2": tn, "gm": gm, "gm_default": gmd, "ms_best": mb.value,
+                    "ms_default": md.value})
+        i += 1
 
 
 def launch_count():

@@ -119,3 +119,46 @@ def test_autograd_t2_gradient(torch):
     for (i, j, a, b) in [(0, 1, 0, 1), (1, 2, 2, 4)]:
         d = (L(grad._perturbed(inp, i, j, a, b, h)) - L(grad._perturbed(inp, i, j, a, b, -h))) / (2 * h)
         assert abs(d - g[i, j, a, b]) <= 1e-6 * np.abs(g).max()
+
+
+@pytest.mark.parametrize("prec,hi", [("tf32", 2.0 ** -12), ("bf16", 2.0 ** -9)])
+@pytest.mark.parametrize("o,v,seed", [(4, 8, 1001), (7, 13, 103)])
+def test_transposed_tensor_core_sigma(torch, prec, hi, o, v, seed):
+    """M^T X on the tensor cores: the low-precision transposed sigma within its operand rounding, and the
+    exact-slice transposed sigma to FP64 level, against X M from the oracle's dense matrix."""
+    from paper_1902_06016_gb300 import Context
+    from gpu_util import random_vectors
+    inp = inputs(o, v, seed)
+    M = sg.dense_matrix(hbar.build(inp))
+    X = random_vectors(inp.dim, 5, seed + 9)
+    ref = X @ M
+    ctx = Context(inp, precision=prec)
+    err = rel_err(ctx.sigma(X, precision=prec, transpose=True), ref)
+    assert 1e-7 < err < hi, err
+    Y = ctx.sigma(X, precision="fp64_tc", transpose=True)
+    for k in range(5):
+        assert np.abs(Y[k] - ref[k]).max() <= 1e-12 * np.abs(ref[k]).max()
+
+
+@pytest.mark.parametrize("o,v,seed", [(4, 8, 1001), (7, 13, 103)])
+def test_adjoint_solves_on_tensor_cores_match_oracle(torch, o, v, seed):
+    """A TF32 context runs the adjoint (transposed) solves of dG/dw, dG/deta and dL/dt2 as GMRES-IR with
+    the TF32 transposed sigma and exact-slice residuals; results as accurate as the FP64 path."""
+    import synth
+    from paper_1902_06016_gb300 import Context
+    inp = inputs(o, v, seed)
+    M = sg.dense_matrix(hbar.build(inp))
+    porb, qorb = list(range(o + 2)), [0, 2, o + 1]
+    ws = np.linspace(-1.0, -0.1, 5)
+    ctx = Context(inp, tol=1e-11, precision="tf32")
+    G, dw, de = ctx.green_derivatives(ws, 0.02, porb, qorb)
+    Go, dwo, deo = grad.derivatives(M, bc.b_vectors(inp, porb), bc.c_vectors(inp, qorb), ws, 0.02)
+    assert rel_err(G, Go) <= 1e-8 and rel_err(dw, dwo) <= 1e-8 and rel_err(de, deo) <= 1e-8
+    inp2 = synth.random_amplitudes(inputs(3, 5, 11), 14)
+    p2, q2 = [0, 1, 2, 3], [0, 2, 4]
+    w2, eta2 = np.array([-0.8, -0.45, -0.1]), 0.05
+    rng = np.random.default_rng(3)
+    Gb = rng.standard_normal((3, 4, 3)) + 1j * rng.standard_normal((3, 4, 3))
+    ctx2 = Context(inp2, tol=1e-11, precision="tf32")
+    _, g = ctx2.green_grad_t2(w2, eta2, p2, Gb, q2)
+    assert rel_err(antisymmetrised(g), grad.green_t2_gradient(inp2, p2, q2, w2, eta2, Gb)) <= 1e-7
