@@ -51,15 +51,17 @@ __global__ void adjoint_rhs_kernel(const double* __restrict__ cvec, long long D,
 
 // Z (batch-minor [D][S] complex) -> real tensors Z1[s][z][i] and Z2[s][z][i][j][a] (full antisymmetric
 // in i, j); z = 0 real part, z = 1 imaginary part times sgn (sgn = -1 makes sum_z u_z r_z = Re(u r))
-__global__ void unpack_kernel(const cplx* __restrict__ Z, long long S, int o, int v, double sgn,
-                              double* __restrict__ Z1, double* __restrict__ Z2) {
+// columns s0 .. s0 + S - 1 of the batch-minor block Z [D][ldS]
+__global__ void unpack_kernel(const cplx* __restrict__ Zb, long long ldS, long long s0, long long S, int o, int v,
+                              double sgn, double* __restrict__ Z1, double* __restrict__ Z2) {
+  const cplx* Z = Zb + s0;
   const long long per = (long long)o + (long long)o * o * v;
   const long long total = S * per;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     const long long sidx = t / per, e = t % per;
     if (e < o) {
-      const cplx x = Z[e * S + sidx];
+      const cplx x = Z[e * ldS + sidx];
       Z1[(sidx * 2 + 0) * o + e] = x.x;
       Z1[(sidx * 2 + 1) * o + e] = sgn * x.y;
     } else {
@@ -68,7 +70,7 @@ __global__ void unpack_kernel(const cplx* __restrict__ Z, long long S, int o, in
       double re = 0.0, im = 0.0;
       if (i != j) {
         const int lo = min(i, j), hi = max(i, j);
-        const cplx x = Z[((long long)o + (long long)pair_of(lo, hi) * v + a) * S + sidx];
+        const cplx x = Z[((long long)o + (long long)pair_of(lo, hi) * v + a) * ldS + sidx];
         const double f = i < j ? 1.0 : -1.0;
         re = f * x.x;
         im = f * x.y;
@@ -145,32 +147,42 @@ void green_grad_t2_core(gfcc_ctx* c, int nw, const std::vector<int>& porb, const
   GFCC_CHECK(S < (1LL << 31), GFCC_ERR_ARG, "gradient: too many columns");
 
   // ---- gradients of the H-bar elements from the sigma bilinear form ------------------------------
-  const int Si = (int)S;
-  Tensor U1("szi", {Si, 2, o}), U2("szija", {Si, 2, o, o, v});
-  Tensor R1("szk", {Si, 2, o}), R2("szkla", {Si, 2, o, o, v});
-  const long long nun = S * ((long long)o + (long long)o * o * v);
-  unpack_kernel<<<grid_for(nun), 256, 0, s>>>(Up, S, o, v, 1.0, U1.p(), U2.p());
-  GFCC_LAUNCH_CHECK();
-  unpack_kernel<<<grid_for(nun), 256, 0, s>>>(Xp, S, o, v, -1.0, R1.p(), R2.p());
-  GFCC_LAUNCH_CHECK();
+  // Every term is a sum over the columns s, so the columns are unpacked and contracted in chunks whose
+  // unpacked blocks (and the contractions' operand copies) stay within a few GB.
   Tensor Fmi("ki", {o, o}), Fae("ac", {v, v}), Wmbij("kaij", {o, v, o, o}), Wmnij("klij", {o, o, o, o}),
       Wmbej("kaci", {o, v, v, o}), t2bar("ijab", {o, o, v, v}), tau("ijab", {o, o, v, v});
   t2bar.buf.zero(s);
   tau.buf.zero(s);
-  // L_M = -Re sum_s u_s^T sigma(x_s); sum over i<j of u sigma = 1/2 sum over all i, j (antisymmetric)
-  contract(1.0, U1.as("szi"), R1.as("szk"), 0.0, Fmi.as("ki"), s);            // -F_ki r_k in s_i
-  contract(1.0, U2.as("szija"), R2.as("szkja"), 1.0, Fmi.as("ki"), s);         // -P(ij) F_ki r_kj^a
-  contract(-0.5, U2.as("szija"), R2.as("szijc"), 0.0, Fae.as("ac"), s);        // F_ac r_ij^c
-  contract(0.5, U2.as("szija"), R1.as("szk"), 0.0, Wmbij.as("kaij"), s);       // -W_kaij r_k
-  contract(-0.25, U2.as("szija"), R2.as("szkla"), 0.0, Wmnij.as("klij"), s);   // 1/2 W_klij r_kl^a
-  contract(-1.0, U2.as("szija"), R2.as("szkjc"), 0.0, Wmbej.as("kaci"), s);    // P(ij) W_kaci r_kj^c
-  {  // three-body term -1/2 (<kl||cd> r_kl^c) t_ij^ad, explicit in T2
-    Tensor Xd("szd", {Si, 2, v});
-    const TV voovv{c->k_oovv.p, "klcd", {o, o, v, v}};
-    contract(1.0, voovv, R2.as("szklc"), 0.0, Xd.as("szd"), s);
-    contract(0.25, U2.as("szija"), Xd.as("szd"), 1.0, t2bar.as("ijad"), s);
+  {
+    const long long per_col = 2LL * ((long long)o + (long long)o * o * v) * (long long)sizeof(double);
+    const long long budget = 3LL << 30;   // bytes of one unpacked block (U2 or R2) per chunk
+    const int chunk = (int)std::max<long long>(1, std::min<long long>(S, budget / per_col));
+    for (long long s0 = 0; s0 < S; s0 += chunk) {
+      const int Si = (int)std::min<long long>(chunk, S - s0);
+      const double b0 = s0 == 0 ? 0.0 : 1.0;   // the first chunk sets, the later ones add
+      Tensor U1("szi", {Si, 2, o}), U2("szija", {Si, 2, o, o, v});
+      Tensor R1("szk", {Si, 2, o}), R2("szkla", {Si, 2, o, o, v});
+      const long long nun = (long long)Si * ((long long)o + (long long)o * o * v);
+      unpack_kernel<<<grid_for(nun), 256, 0, s>>>(Up, S, s0, Si, o, v, 1.0, U1.p(), U2.p());
+      GFCC_LAUNCH_CHECK();
+      unpack_kernel<<<grid_for(nun), 256, 0, s>>>(Xp, S, s0, Si, o, v, -1.0, R1.p(), R2.p());
+      GFCC_LAUNCH_CHECK();
+      // L_M = -Re sum_s u_s^T sigma(x_s); sum over i<j of u sigma = 1/2 sum over all i, j (antisymmetric)
+      contract(1.0, U1.as("szi"), R1.as("szk"), b0, Fmi.as("ki"), s);            // -F_ki r_k in s_i
+      contract(1.0, U2.as("szija"), R2.as("szkja"), 1.0, Fmi.as("ki"), s);        // -P(ij) F_ki r_kj^a
+      contract(-0.5, U2.as("szija"), R2.as("szijc"), b0, Fae.as("ac"), s);       // F_ac r_ij^c
+      contract(0.5, U2.as("szija"), R1.as("szk"), b0, Wmbij.as("kaij"), s);      // -W_kaij r_k
+      contract(-0.25, U2.as("szija"), R2.as("szkla"), b0, Wmnij.as("klij"), s);  // 1/2 W_klij r_kl^a
+      contract(-1.0, U2.as("szija"), R2.as("szkjc"), b0, Wmbej.as("kaci"), s);   // P(ij) W_kaci r_kj^c
+      {  // three-body term -1/2 (<kl||cd> r_kl^c) t_ij^ad, explicit in T2
+        Tensor Xd("szd", {Si, 2, v});
+        const TV voovv{c->k_oovv.p, "klcd", {o, o, v, v}};
+        contract(1.0, voovv, R2.as("szklc"), 0.0, Xd.as("szd"), s);
+        contract(0.25, U2.as("szija"), Xd.as("szd"), 1.0, t2bar.as("ijad"), s);
+      }
+      GFCC_CUDA(cudaStreamSynchronize(s));   // the chunk's blocks are released at the end of this scope
+    }
   }
-  U1.buf.release(); U2.buf.release(); R1.buf.release(); R2.buf.release();
 
   // ---- back through the H-bar build ----------------------------------------------------------------
   const TV t1{c->t1.p, "", {o, v}};

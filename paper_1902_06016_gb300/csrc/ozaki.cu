@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdlib>
 
 namespace gfcc {
@@ -31,33 +32,46 @@ __device__ __forceinline__ int row_exponent(unsigned long long maxbits) {
 // Balanced base-128 digits of x relative to 2^(e - 6):  x ~ 2^(e-6) sum_{i<ns} a_i 2^(-7i), |a_i| <= 64.
 // V = round(|x| 2^(6 - e + 7(ns-1))) is formed exactly from the mantissa (|V| <= 2^(6 + 7(ns-1)) < 2^56);
 // digit i is V / 2^(7(ns-1-i)) rounded half up, V keeps the remainder (|remainder| <= 2^(shift-1)), and
-// the signs of all digits follow x (so -x gives exactly the negated digits). a[i] holds digit i.
-__device__ __forceinline__ void digits(double x, int e, int ns, int (&a)[OZ_SLICES_MAX]) {
+// the signs of all digits follow x (so -x gives exactly the negated digits). a[i] holds digit i. The slice
+// count NS is a template argument (no predicated iterations, constant shifts).
+template <int NS>
+__device__ __forceinline__ void digits_t(double x, int e, int (&a)[NS]) {
   const long long bits = __double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
   long long V = 0;
   if (ex != 0 && e != ZERO_ROW) {
     const long long m = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
-    const int t = ex - 1075 + 6 - e + 7 * (ns - 1);   // t <= 7 ns - 53 <= 3
+    const int t = ex - 1075 + 6 - e + 7 * (NS - 1);
     if (t >= 0) V = m << t;
     else if (t > -62) V = (m + (1LL << (-t - 1))) >> (-t);
   }
   const bool neg = bits < 0;
 #pragma unroll
-  for (int i = 0; i < OZ_SLICES_MAX; ++i) {
-    if (i < ns) {
-      const int shift = 7 * (ns - 1 - i);
-      const long long d = (i < ns - 1) ? ((V + (1LL << (shift - 1))) >> shift) : V;
-      V -= d << shift;
-      a[i] = neg ? -(int)d : (int)d;
-    }
+  for (int i = 0; i < NS; ++i) {
+    const int shift = 7 * (NS - 1 - i);
+    const long long d = (i < NS - 1) ? ((V + (1LL << (shift - 1))) >> shift) : V;
+    V -= d << shift;
+    a[i] = neg ? -(int)d : (int)d;
   }
+}
+// digits of two adjacent elements of a row, written as one bf16 pair per slot (k even)
+template <int NS>
+__device__ __forceinline__ void slice_pair(double x0, double x1, int e, __nv_bfloat16* __restrict__ o, long long kp,
+                                           int reversed, long long k) {
+  int a0[NS], a1[NS];
+  digits_t<NS>(x0, e, a0);
+  digits_t<NS>(x1, e, a1);
+#pragma unroll
+  for (int i = 0; i < NS; ++i)
+    *reinterpret_cast<__nv_bfloat162*>(o + (long long)(reversed ? NS - 1 - i : i) * kp + k) =
+        __halves2bfloat162(__int2bfloat16_rn(a0[i]), __int2bfloat16_rn(a1[i]));
 }
 
 // Real rows (row-major, row stride ldx, K used columns): one block per row (grid-stride) for long
 // rows; slices [r][slot][kp] with slot = i (or ns-1-i when reversed), zeros for K <= k < kp.
+template <int NS>
 __global__ void __launch_bounds__(256) slice_kernel(const double* __restrict__ X, long long ldx, long long rows,
-                                                    long long K, long long kp, int reversed, int ns,
+                                                    long long K, long long kp, int reversed,
                                                     __nv_bfloat16* __restrict__ out, int* __restrict__ expo) {
   __shared__ unsigned long long red[8];
   for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
@@ -72,21 +86,16 @@ __global__ void __launch_bounds__(256) slice_kernel(const double* __restrict__ X
     const int e = row_exponent(mx);
     __syncthreads();
     if (threadIdx.x == 0) expo[r] = e == ZERO_ROW ? 0 : e;
-    __nv_bfloat16* o = out + r * (long long)ns * kp;
-    for (long long k = threadIdx.x; k < kp; k += blockDim.x) {
-      int a[OZ_SLICES_MAX];
-      digits(k < K ? x[k] : 0.0, e, ns, a);
-#pragma unroll
-      for (int i = 0; i < OZ_SLICES_MAX; ++i)
-        if (i < ns) o[(long long)(reversed ? ns - 1 - i : i) * kp + k] = __int2bfloat16_rn(a[i]);
-    }
+    __nv_bfloat16* o = out + r * (long long)NS * kp;
+    for (long long k = 2LL * threadIdx.x; k < kp; k += 2LL * blockDim.x)
+      slice_pair<NS>(k < K ? x[k] : 0.0, k + 1 < K ? x[k + 1] : 0.0, e, o, kp, reversed, k);
   }
 }
 // The same for short rows: one warp per row.
+template <int NS>
 __global__ void __launch_bounds__(256) slice_rows_warp_kernel(const double* __restrict__ X, long long ldx,
                                                               long long rows, long long K, long long kp, int reversed,
-                                                              int ns, __nv_bfloat16* __restrict__ out,
-                                                              int* __restrict__ expo) {
+                                                              __nv_bfloat16* __restrict__ out, int* __restrict__ expo) {
   const long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
@@ -96,14 +105,9 @@ __global__ void __launch_bounds__(256) slice_rows_warp_kernel(const double* __re
   for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
   const int e = row_exponent(mx);
   if (lane == 0) expo[r] = e == ZERO_ROW ? 0 : e;
-  __nv_bfloat16* o = out + r * (long long)ns * kp;
-  for (long long k = lane; k < kp; k += 32) {
-    int a[OZ_SLICES_MAX];
-    digits(k < K ? x[k] : 0.0, e, ns, a);
-#pragma unroll
-    for (int i = 0; i < OZ_SLICES_MAX; ++i)
-      if (i < ns) o[(long long)(reversed ? ns - 1 - i : i) * kp + k] = __int2bfloat16_rn(a[i]);
-  }
+  __nv_bfloat16* o = out + r * (long long)NS * kp;
+  for (long long k = 2LL * lane; k < kp; k += 64)
+    slice_pair<NS>(k < K ? x[k] : 0.0, k + 1 < K ? x[k + 1] : 0.0, e, o, kp, reversed, k);
 }
 
 // The same for a few long rows (fewer rows than it takes to occupy the GPU with a block each): the
@@ -125,21 +129,31 @@ __global__ void __launch_bounds__(256) rowmax_chunk_kernel(const double* __restr
     if (mx > 0) atomicMax(rowmax + r, mx);
   }
 }
+template <int NS>
 __global__ void __launch_bounds__(256) slice_chunk_kernel(const double* __restrict__ X, long long ldx, long long K,
-                                                          long long kp, int reversed, int ns,
+                                                          long long kp, int reversed,
                                                           const unsigned long long* __restrict__ rowmax,
                                                           __nv_bfloat16* __restrict__ out, int* __restrict__ expo) {
-  const long long r = blockIdx.y, k0 = blockIdx.x * SL_CH, k1 = min(kp, k0 + SL_CH);
+  const long long r = blockIdx.y, k0 = blockIdx.x * SL_CH, k1 = min(kp, k0 + SL_CH);   // SL_CH is even
   const double* x = X + r * ldx;
   const int e = row_exponent(rowmax[r]);
   if (blockIdx.x == 0 && threadIdx.x == 0) expo[r] = e == ZERO_ROW ? 0 : e;
-  __nv_bfloat16* o = out + r * (long long)ns * kp;
-  for (long long k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-    int a[OZ_SLICES_MAX];
-    digits(k < K ? x[k] : 0.0, e, ns, a);
-#pragma unroll
-    for (int i = 0; i < OZ_SLICES_MAX; ++i)
-      if (i < ns) o[(long long)(reversed ? ns - 1 - i : i) * kp + k] = __int2bfloat16_rn(a[i]);
+  __nv_bfloat16* o = out + r * (long long)NS * kp;
+  for (long long k = k0 + 2LL * threadIdx.x; k < k1; k += 2LL * blockDim.x)
+    slice_pair<NS>(k < K ? x[k] : 0.0, k + 1 < K ? x[k + 1] : 0.0, e, o, kp, reversed, k);
+}
+
+// the slice count of a launch as a template argument (2..8 slices)
+template <typename F>
+void with_ns(int ns, F&& f) {
+  switch (ns) {
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 3: f(std::integral_constant<int, 3>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    case 6: f(std::integral_constant<int, 6>{}); break;
+    case 7: f(std::integral_constant<int, 7>{}); break;
+    default: f(std::integral_constant<int, 8>{}); break;
   }
 }
 
@@ -195,11 +209,13 @@ __global__ void __launch_bounds__(256) zrowmax_kernel(const cplx* __restrict__ Z
 
 // Slices of row r at (r ns + slot) kp (row-major), or with slot_major at (slot rows_total + r) kp, where
 // rows_total = R (mode 0) or 2R (mode 1): then slots 0..j of all rows form one contiguous block of rows.
+template <int NS>
 __global__ void __launch_bounds__(256) zslice_kernel(const cplx* __restrict__ Z, long long s_r, long long s_k,
                                                      int conj, long long R, long long K, int mode,
                                                      const unsigned long long* __restrict__ rowmax, long long kp,
-                                                     int reversed, int ns, __nv_bfloat16* __restrict__ out,
+                                                     int reversed, __nv_bfloat16* __restrict__ out,
                                                      int* __restrict__ expo, int slot_major = 0) {
+  constexpr int ns = NS;
   __shared__ cplx tile[ZT_R][ZT_K + 1];
   const long long r0 = (long long)blockIdx.y * ZT_R, k0 = (long long)blockIdx.x * ZT_K;
   load_ztile(Z, s_r, s_k, conj, R, K, r0, k0, tile);
@@ -224,12 +240,12 @@ __global__ void __launch_bounds__(256) zslice_kernel(const cplx* __restrict__ Z,
       const long long k = k0 + tk;
       if (2 * k >= kp) break;
       const cplx v = tile[tr][tk];
-      int are[OZ_SLICES_MAX], aim[OZ_SLICES_MAX];
-      digits(v.x, e, ns, are);
-      digits(v.y, e, ns, aim);
+      int are[NS], aim[NS];
+      digits_t<NS>(v.x, e, are);
+      digits_t<NS>(v.y, e, aim);
 #pragma unroll
-      for (int i = 0; i < OZ_SLICES_MAX; ++i) {
-        if (i < ns) {
+      for (int i = 0; i < NS; ++i) {
+        {
           const long long off = (long long)(reversed ? ns - 1 - i : i) * sstep + 2 * k;
           if (mode == 0) {
             *reinterpret_cast<__nv_bfloat162*>(o0 + off) = __halves2bfloat162(__int2bfloat16_rn(are[i]),
@@ -256,7 +272,54 @@ struct OzOut {
   cplx* C = nullptr;
   long long scm = 0, scn = 0;
   cplx alpha = {1.0, 0.0}, cbeta = {0.0, 0.0};
+  // the common cases, so that the output pass spends no FP64 multiplications on them (set by set_kinds):
+  // alpha_kind 1: alpha = 1, 2: alpha = -1, 0: general; beta_kind 0: beta = 0, 1: beta = 1, 2: general
+  int alpha_kind = 1, beta_kind = 0;
+  void set_kinds() {
+    alpha_kind = (alpha.y == 0.0 && alpha.x == 1.0) ? 1 : (alpha.y == 0.0 && alpha.x == -1.0) ? 2 : 0;
+    if (complex_out) beta_kind = (cbeta.x == 0.0 && cbeta.y == 0.0) ? 0 : (cbeta.x == 1.0 && cbeta.y == 0.0) ? 1 : 2;
+    else beta_kind = beta == 0.0 ? 0 : beta == 1.0 ? 1 : 2;
+  }
 };
+
+// x 2^k by one multiplication with an exact power of two when 2^k is a normal number (ldexp otherwise)
+__device__ __forceinline__ double scale_pow2(double x, int k) {
+  if (k >= -1022 && k <= 1023) return x * __longlong_as_double((long long)(k + 1023) << 52);
+  return ldexp(x, k);
+}
+// sum_d S_d 2^(7 (nd - 1 - d)) for nd <= 8 per-diagonal integer sums |S_d| < 2^40: the first (up to four)
+// and the remaining diagonals are combined exactly in two 64-bit integers (each below 2^62) and joined by
+// one fused multiply-add, instead of an FP64 conversion and multiply-add per diagonal (FP64 is the scarce
+// pipe on this GPU: the output passes were bound by it). The caller scales by 2^(-7 (nd - 1)).
+__device__ __forceinline__ double diag_combine(const long long* S, int nd) {
+  const int H = nd < 4 ? nd : 4;
+  long long hi = 0, lo = 0;
+#pragma unroll
+  for (int d = 0; d < OZ_SLICES_MAX; ++d) {
+    if (d < H) hi += S[d] * (1LL << (7 * (H - 1 - d)));
+    else if (d < nd) lo += S[d] * (1LL << (7 * (nd - 1 - d)));
+  }
+  return fma((double)hi, __longlong_as_double((long long)(7 * (nd - H) + 1023) << 52), (double)lo);
+}
+// complex output value: alpha (re + i im) + beta C
+__device__ __forceinline__ cplx out_value(const OzOut& o, double re, double im, const cplx* p) {
+  cplx r;
+  if (o.alpha_kind == 1) r = make_cuDoubleComplex(re, im);
+  else if (o.alpha_kind == 2) r = make_cuDoubleComplex(-re, -im);
+  else r = cuCmul(o.alpha, make_cuDoubleComplex(re, im));
+  if (o.beta_kind == 1) {
+    const cplx q = *p;
+    r.x += q.x;
+    r.y += q.y;
+  } else if (o.beta_kind == 2) {
+    r = cuCadd(r, cuCmul(o.cbeta, *p));
+  }
+  return r;
+}
+// real output value: v + beta out
+__device__ __forceinline__ double out_value_real(const OzOut& o, double v, const double* p) {
+  return o.beta_kind == 0 ? v : o.beta_kind == 1 ? v + *p : o.beta * (*p) + v;
+}
 
 // sum over the zs int32 split sums p[z stride], exactly in 64-bit integers; WARP: the lanes share the
 // splits and every lane returns the total (integer sums do not depend on the grouping)
@@ -314,10 +377,10 @@ __global__ void __launch_bounds__(256) oz_accumulate_kernel(const int* __restric
       if (!first) a = acc[t] + a;
       long long m, n;
       divmod<I>(t, Np, m, n);
-      const double v = ldexp(a, ea[m] + eb[n] - 12);
+      const double v = scale_pow2(a, ea[m] + eb[n] - 12);
       if (writer) {
         double* p = o.out + m * o.ldo + n;
-        *p = (o.beta == 0.0) ? v : o.beta * (*p) + v;
+        *p = out_value_real(o, v, p);
       }
     } else {
       const long long N = Np / 2;
@@ -330,12 +393,10 @@ __global__ void __launch_bounds__(256) oz_accumulate_kernel(const int* __restric
         ar = acc[tr] + ar;
         ai = acc[ti] + ai;
       }
-      const double re = ldexp(ar, ea[m] + eb[n] - 12), im = ldexp(ai, ea[m] + eb[N + n] - 12);
+      const double re = scale_pow2(ar, ea[m] + eb[n] - 12), im = scale_pow2(ai, ea[m] + eb[N + n] - 12);
       if (writer) {
         cplx* p = o.C + m * o.scm + n * o.scn;
-        cplx r = cuCmul(o.alpha, make_cuDoubleComplex(re, im));
-        if (o.cbeta.x != 0.0 || o.cbeta.y != 0.0) r = cuCadd(r, cuCmul(o.cbeta, *p));
-        *p = r;
+        *p = out_value(o, re, im, p);
       }
     }
   }
@@ -348,15 +409,15 @@ struct OzDiags {
   double scale[OZ_SLICES_MAX];
   int nd;
 };
+// sum_d 2^(-7d) (split sums of diagonal d), times 2^(7 (nd - 1)) (see diag_combine)
 template <bool WARP>
 __device__ __forceinline__ double diag_total(const int* __restrict__ slabs, const OzDiags& dg, long long stride,
                                              long long t, int lane) {
-  double a = 0.0;
-  for (int d = 0; d < dg.nd; ++d) {
-    const double v = dg.scale[d] * (double)split_sum<WARP>(slabs + dg.off[d] + t, dg.zs[d], stride, lane);
-    a = d == 0 ? v : a + v;
-  }
-  return a;
+  long long S[OZ_SLICES_MAX];
+#pragma unroll
+  for (int d = 0; d < OZ_SLICES_MAX; ++d)
+    S[d] = d < dg.nd ? split_sum<WARP>(slabs + dg.off[d] + t, dg.zs[d], stride, lane) : 0;
+  return diag_combine(S, dg.nd);
 }
 template <bool WARP, int MODE, typename I>
 __global__ void __launch_bounds__(256) oz_output_kernel(const int* __restrict__ slabs, OzDiags dg, long long M,
@@ -373,23 +434,22 @@ __global__ void __launch_bounds__(256) oz_output_kernel(const int* __restrict__ 
     if constexpr (MODE == 1) {
       long long m, n;
       divmod<I>(t, Np, m, n);
-      const double v = ldexp(diag_total<WARP>(slabs, dg, stride, t, lane), ea[m] + eb[n] - 12);
+      const double v = scale_pow2(diag_total<WARP>(slabs, dg, stride, t, lane), ea[m] + eb[n] - 12 - 7 * (dg.nd - 1));
       if (writer) {
         double* p = o.out + m * o.ldo + n;
-        *p = (o.beta == 0.0) ? v : o.beta * (*p) + v;
+        *p = out_value_real(o, v, p);
       }
     } else {
       const long long N = Np / 2;
       long long m, n;
       divmod<I>(t, N, m, n);
       const long long tr = m * Np + n;
-      const double re = ldexp(diag_total<WARP>(slabs, dg, stride, tr, lane), ea[m] + eb[n] - 12);
-      const double im = ldexp(diag_total<WARP>(slabs, dg, stride, tr + N, lane), ea[m] + eb[N + n] - 12);
+      const int sh = -12 - 7 * (dg.nd - 1);
+      const double re = scale_pow2(diag_total<WARP>(slabs, dg, stride, tr, lane), ea[m] + eb[n] + sh);
+      const double im = scale_pow2(diag_total<WARP>(slabs, dg, stride, tr + N, lane), ea[m] + eb[N + n] + sh);
       if (writer) {
         cplx* p = o.C + m * o.scm + n * o.scn;
-        cplx r = cuCmul(o.alpha, make_cuDoubleComplex(re, im));
-        if (o.cbeta.x != 0.0 || o.cbeta.y != 0.0) r = cuCadd(r, cuCmul(o.cbeta, *p));
-        *p = r;
+        *p = out_value(o, re, im, p);
       }
     }
   }
@@ -405,39 +465,30 @@ __global__ void __launch_bounds__(256) oz_output1_kernel(const int* __restrict__
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
     if constexpr (MODE == 1) {
-      int v[NS];
+      long long v[OZ_SLICES_MAX] = {};
 #pragma unroll
       for (int d = 0; d < NS; ++d) v[d] = slabs[dg.off[d] + t];
-      double a = dg.scale[0] * (double)v[0];
-#pragma unroll
-      for (int d = 1; d < NS; ++d) a = a + dg.scale[d] * (double)v[d];
       long long m, n;
       divmod<I>(t, Np, m, n);
-      const double r = ldexp(a, ea[m] + eb[n] - 12);
+      const double r = scale_pow2(diag_combine(v, NS), ea[m] + eb[n] - 12 - 7 * (NS - 1));
       double* p = o.out + m * o.ldo + n;
-      *p = (o.beta == 0.0) ? r : o.beta * (*p) + r;
+      *p = out_value_real(o, r, p);
     } else {
       const long long N = Np / 2;
       long long m, n;
       divmod<I>(t, N, m, n);
       const long long tr = m * Np + n, ti = tr + N;
-      int vr[NS], vi[NS];
+      long long vr[OZ_SLICES_MAX] = {}, vi[OZ_SLICES_MAX] = {};
 #pragma unroll
       for (int d = 0; d < NS; ++d) {
         vr[d] = slabs[dg.off[d] + tr];
         vi[d] = slabs[dg.off[d] + ti];
       }
-      double ar = dg.scale[0] * (double)vr[0], ai = dg.scale[0] * (double)vi[0];
-#pragma unroll
-      for (int d = 1; d < NS; ++d) {
-        ar = ar + dg.scale[d] * (double)vr[d];
-        ai = ai + dg.scale[d] * (double)vi[d];
-      }
-      const double re = ldexp(ar, ea[m] + eb[n] - 12), im = ldexp(ai, ea[m] + eb[N + n] - 12);
+      const int sh = -12 - 7 * (NS - 1);
+      const double re = scale_pow2(diag_combine(vr, NS), ea[m] + eb[n] + sh);
+      const double im = scale_pow2(diag_combine(vi, NS), ea[m] + eb[N + n] + sh);
       cplx* p = o.C + m * o.scm + n * o.scn;
-      cplx r = cuCmul(o.alpha, make_cuDoubleComplex(re, im));
-      if (o.cbeta.x != 0.0 || o.cbeta.y != 0.0) r = cuCadd(r, cuCmul(o.cbeta, *p));
-      *p = r;
+      *p = out_value(o, re, im, p);
     }
   }
 }
@@ -478,15 +529,15 @@ struct OzStack {
 template <bool WARP>
 __device__ __forceinline__ double stack_total(const int* __restrict__ slabs, const OzStack& st, long long M,
                                               long long Np, long long m, long long col, int lane) {
-  double acc = 0.0;
-  for (int d = 0; d < st.ns; ++d) {
-    long long S = 0;
-    for (int i = 0; i <= d; ++i)
-      S += split_sum<WARP>(slabs + st.off[i] + m * st.ncol[i] + (d - i) * Np + col, st.zs[i], M * st.ncol[i], lane);
-    const double v = st.scale[d] * (double)S;
-    acc = d == 0 ? v : acc + v;
+  long long S[OZ_SLICES_MAX];
+#pragma unroll
+  for (int d = 0; d < OZ_SLICES_MAX; ++d) {
+    S[d] = 0;
+    if (d < st.ns)
+      for (int i = 0; i <= d; ++i)
+        S[d] += split_sum<WARP>(slabs + st.off[i] + m * st.ncol[i] + (d - i) * Np + col, st.zs[i], M * st.ncol[i], lane);
   }
-  return acc;
+  return diag_combine(S, st.ns);   // times 2^(7 (ns - 1))
 }
 // complex output C(m, n) = alpha (re + i im) + beta C (real columns n and N + n of the Np = 2N)
 template <bool WARP, typename I>
@@ -501,13 +552,12 @@ __global__ void __launch_bounds__(256) oz_stack_output_kernel(const int* __restr
   for (long long t = start; t < total; t += step) {
     long long m, n;
     divmod<I>(t, N, m, n);
-    const double re = ldexp(stack_total<WARP>(slabs, st, M, Np, m, n, lane), ea[m] + eb[n] - 12);
-    const double im = ldexp(stack_total<WARP>(slabs, st, M, Np, m, N + n, lane), ea[m] + eb[N + n] - 12);
+    const int sh = -12 - 7 * (st.ns - 1);
+    const double re = scale_pow2(stack_total<WARP>(slabs, st, M, Np, m, n, lane), ea[m] + eb[n] + sh);
+    const double im = scale_pow2(stack_total<WARP>(slabs, st, M, Np, m, N + n, lane), ea[m] + eb[N + n] + sh);
     if (!WARP || lane == 0) {
       cplx* p = o.C + m * o.scm + n * o.scn;
-      cplx r = cuCmul(o.alpha, make_cuDoubleComplex(re, im));
-      if (o.cbeta.x != 0.0 || o.cbeta.y != 0.0) r = cuCadd(r, cuCmul(o.cbeta, *p));
-      *p = r;
+      *p = out_value(o, re, im, p);
     }
   }
 }
@@ -531,24 +581,20 @@ __global__ void __launch_bounds__(256) oz_stack_output1_kernel(const int* __rest
         vr[q] = p[0];
         vi[q] = p[N];
       }
-    double ar = 0.0, ai = 0.0;
+    long long sr[OZ_SLICES_MAX] = {}, si[OZ_SLICES_MAX] = {};
 #pragma unroll
     for (int d = 0, q = 0; d < NS; ++d) {
-      long long sr = 0, si = 0;
 #pragma unroll
       for (int i = 0; i <= d; ++i, ++q) {
-        sr += vr[q];
-        si += vi[q];
+        sr[d] += vr[q];
+        si[d] += vi[q];
       }
-      const double xr = st.scale[d] * (double)sr, xi = st.scale[d] * (double)si;
-      ar = d == 0 ? xr : ar + xr;
-      ai = d == 0 ? xi : ai + xi;
     }
-    const double re = ldexp(ar, ea[m] + eb[n] - 12), im = ldexp(ai, ea[m] + eb[N + n] - 12);
+    const int sh = -12 - 7 * (NS - 1);
+    const double re = scale_pow2(diag_combine(sr, NS), ea[m] + eb[n] + sh);
+    const double im = scale_pow2(diag_combine(si, NS), ea[m] + eb[N + n] + sh);
     cplx* p = o.C + m * o.scm + n * o.scn;
-    cplx r = cuCmul(o.alpha, make_cuDoubleComplex(re, im));
-    if (o.cbeta.x != 0.0 || o.cbeta.y != 0.0) r = cuCadd(r, cuCmul(o.cbeta, *p));
-    *p = r;
+    *p = out_value(o, re, im, p);
   }
 }
 template <typename I>
@@ -848,9 +894,11 @@ void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s) {
     zrowmax_kernel<<<dim3((unsigned)kt_in, (unsigned)((N + ZT_R - 1) / ZT_R)), 256, 0, s>>>(g.B, g.sbn, g.sbk, N, K, mxb.p);
     GFCC_LAUNCH_CHECK();
     if (!reuse) {
-      zslice_kernel<<<dim3((unsigned)kt, (unsigned)((M + ZT_R - 1) / ZT_R)), 256, 0, s>>>(
-          g.A, g.sam, g.sak, g.conjA ? 1 : 0, M, K, 0, mxa.p, sa.kp, 0, ns,
-          reinterpret_cast<__nv_bfloat16*>(sa.slices.p), sa.expo.p);
+      with_ns(ns, [&](auto NSc) {
+        zslice_kernel<decltype(NSc)::value><<<dim3((unsigned)kt, (unsigned)((M + ZT_R - 1) / ZT_R)), 256, 0, s>>>(
+            g.A, g.sam, g.sak, g.conjA ? 1 : 0, M, K, 0, mxa.p, sa.kp, 0,
+            reinterpret_cast<__nv_bfloat16*>(sa.slices.p), sa.expo.p);
+      });
       GFCC_LAUNCH_CHECK();
       if (cache) {
         cache->valid = true;
@@ -858,9 +906,11 @@ void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s) {
         cache->ns = ns; cache->conjA = g.conjA;
       }
     }
-    zslice_kernel<<<dim3((unsigned)kt, (unsigned)((N + ZT_R - 1) / ZT_R)), 256, 0, s>>>(
-        g.B, g.sbn, g.sbk, g.conjB ? 1 : 0, N, K, 1, mxb.p, sb.kp, stacked ? 0 : 1, ns,
-        reinterpret_cast<__nv_bfloat16*>(sb.slices.p), sb.expo.p, stacked ? 1 : 0);
+    with_ns(ns, [&](auto NSc) {
+      zslice_kernel<decltype(NSc)::value><<<dim3((unsigned)kt, (unsigned)((N + ZT_R - 1) / ZT_R)), 256, 0, s>>>(
+          g.B, g.sbn, g.sbk, g.conjB ? 1 : 0, N, K, 1, mxb.p, sb.kp, stacked ? 0 : 1,
+          reinterpret_cast<__nv_bfloat16*>(sb.slices.p), sb.expo.p, stacked ? 1 : 0);
+    });
     GFCC_LAUNCH_CHECK();
   }
   OzOut o;
@@ -870,6 +920,7 @@ void zgemm_oz(const ZGemmDesc& g, int ns, cudaStream_t s) {
   o.scn = g.scn;
   o.alpha = g.alpha;
   o.cbeta = g.beta;
+  o.set_kinds();
   OzWork& w = z.w;
   if (stacked) oz_run_stacked(sa, sb, M, 2 * N, o, w, s);
   else oz_run(sa, sb, M, 2 * N, o, w, s);
@@ -898,9 +949,10 @@ void oz_slice_into(const double* X, long long ldx, long long nrows, long long K,
   ProfScope prof(PROF_OZ_SLICE, 8.0 * (double)nrows * (double)K + 2.0 * (double)nrows * out.ns * (double)out.kp, s);
   __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out.slices.p) + row0 * out.ns * out.kp;
   if (out.kp <= 2048) {   // short rows: a warp per row
-    slice_rows_warp_kernel<<<(unsigned)((nrows * 32 + 255) / 256), 256, 0, s>>>(X, ldx, nrows, K, out.kp,
-                                                                                 out.reversed ? 1 : 0, out.ns, o,
-                                                                                 out.expo.p + row0);
+    with_ns(out.ns, [&](auto NSc) {
+      slice_rows_warp_kernel<decltype(NSc)::value><<<(unsigned)((nrows * 32 + 255) / 256), 256, 0, s>>>(
+          X, ldx, nrows, K, out.kp, out.reversed ? 1 : 0, o, out.expo.p + row0);
+    });
   } else if (nrows < 152LL * 4 && nrows <= 65535) {   // few long rows: split each row over blocks
     DBuf<unsigned long long> mx;
     mx.alloc(nrows);
@@ -909,14 +961,19 @@ void oz_slice_into(const double* X, long long ldx, long long nrows, long long K,
     rowmax_chunk_kernel<<<dim3((unsigned)std::max<long long>(chunks_in, 1), (unsigned)nrows), 256, 0, s>>>(X, ldx, K,
                                                                                                          mx.p);
     GFCC_LAUNCH_CHECK();
-    slice_chunk_kernel<<<dim3((unsigned)chunks, (unsigned)nrows), 256, 0, s>>>(
-        X, ldx, K, out.kp, out.reversed ? 1 : 0, out.ns, mx.p, o, out.expo.p + row0);
+    with_ns(out.ns, [&](auto NSc) {
+      slice_chunk_kernel<decltype(NSc)::value><<<dim3((unsigned)chunks, (unsigned)nrows), 256, 0, s>>>(
+          X, ldx, K, out.kp, out.reversed ? 1 : 0, mx.p, o, out.expo.p + row0);
+    });
     GFCC_LAUNCH_CHECK();
     GFCC_CUDA(cudaStreamSynchronize(s));   // mx is released on return
     return;
   } else {
     const int grid = (int)std::min<long long>(nrows, 152LL * 16);
-    slice_kernel<<<grid, 256, 0, s>>>(X, ldx, nrows, K, out.kp, out.reversed ? 1 : 0, out.ns, o, out.expo.p + row0);
+    with_ns(out.ns, [&](auto NSc) {
+      slice_kernel<decltype(NSc)::value><<<grid, 256, 0, s>>>(X, ldx, nrows, K, out.kp, out.reversed ? 1 : 0, o,
+                                                             out.expo.p + row0);
+    });
   }
   GFCC_LAUNCH_CHECK();
 }
@@ -943,6 +1000,7 @@ void oz_gemm(const SlicedRows& A, const SlicedRows& B, long long M, long long N,
   o.out = out;
   o.ldo = ldo;
   o.beta = beta;
+  o.set_kinds();
   oz_run(A, B, M, N, o, w, s);
 }
 
