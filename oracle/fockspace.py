@@ -188,3 +188,86 @@ def exact_resolvent(bf: BruteForce, omegas: np.ndarray, eta: float) -> np.ndarra
         X = np.linalg.solve(A, bf.ann_phi.T.astype(complex))              # [dim, n]
         out.append((bf.phi_cre @ X).T)                                    # [p, q]
     return np.array(out)
+
+
+# ---- electron attachment: the (N+1)-electron sector ------------------------------------------
+#
+# Basis of the 1p + 2p1h space: index c for a_{o+c}^+ |Phi>, then v + pair(a,b)*o + j for
+# a_{o+a}^+ a_{o+b}^+ a_j |Phi> with a < b (a_j applied first) and pair(a,b) = b(b-1)/2 + a.
+#   M_EA[mu,nu] = <mu| Hbar R_nu |Phi> - <mu| R_nu Hbar |Phi>     (connected action of Hbar_N)
+#   b_q = projection of e^{-T} a_q^+ e^{T} |Phi>                   (the attachment free term)
+#   c_p[nu] = <Phi| (1 + Lambda) e^{-T} a_p e^{T} R_nu |Phi>       (the attachment left vector)
+# so that G^EA_pq(w) = c_p^T (w + i eta - M_EA)^{-1} b_q approximates the second (attachment) term
+# <Psi| a_p (w - (H - E_0) + i eta)^{-1} a_q^+ |Psi> of the retarded Green's function (Eq. gfxn0
+# written out for both orderings of the field operators).
+
+@dataclass
+class BruteForceEA:
+    M: np.ndarray          # [D, D]
+    b: np.ndarray          # [n, D]  row q = b_q
+    c: np.ndarray          # [n, D]  row p = c_p
+    e_hf: float
+    h_np1: np.ndarray      # bare H in the N+1 sector
+    cre_phi: np.ndarray    # [n, dim(N+1)]  a_q^+ |Phi>
+    phi_ann: np.ndarray    # [n, dim(N+1)]  <Phi| a_p as row vectors
+
+
+def build_ea(o: int, v: int, eps: np.ndarray, g: np.ndarray, t1: np.ndarray, t2: np.ndarray,
+             l1: np.ndarray, l2: np.ndarray) -> BruteForceEA:
+    """Build M_EA, b, c by brute force in the N+1 sector (n = o+v <= 14)."""
+    n = o + v
+    f = np.diag(eps)
+    h = f - np.einsum("piqi->pq", g[:, :o, :, :o])
+    SN = Sector(n, o)
+    SP = Sector(n, o + 1)
+
+    H_N = SN.one_body(h) + SN.two_body(g)
+    H_P = SP.one_body(h) + SP.two_body(g)
+    T_N = SN.cluster(o, t1, t2)
+    T_P = SP.cluster(o, t1, t2)
+    L_N = SN.deexcitation(o, l1, l2)
+    eT_N, emT_N = expm_nilpotent(T_N), expm_nilpotent(-T_N)
+    eT_P, emT_P = expm_nilpotent(T_P), expm_nilpotent(-T_P)
+    Hb_N = emT_N @ H_N @ eT_N
+    Hb_P = emT_P @ H_P @ eT_P
+
+    phi = np.zeros(SN.dim)
+    phi[SN.index[(1 << o) - 1]] = 1.0
+    e_hf = float(phi @ H_N @ phi)
+
+    # R_nu as operators N -> N+1 (creation from N to N+1 is the transpose of SP.A)
+    ops = [SP.A[o + c].T for c in range(v)]
+    for b_ in range(v):
+        for a_ in range(b_):
+            for j in range(o):
+                # a_a^+ a_b^+ a_j : a_j (N -> N-1), a_b^+ (N-1 -> N), a_a^+ (N -> N+1)
+                ops.append(SP.A[o + a_].T @ SN.A[o + b_].T @ SN.A[j])
+    basis = np.stack([R @ phi for R in ops], axis=1)                      # [dim(N+1), D]
+    norms = np.einsum("ij,ij->j", basis, basis)
+    assert np.allclose(norms, 1.0), "1p+2p1h basis vectors must be normalised determinants"
+
+    Hb_phi = Hb_N @ phi
+    RH = np.stack([R @ Hb_phi for R in ops], axis=1)
+    M = basis.T @ Hb_P @ basis - basis.T @ RH
+
+    b = np.stack([basis.T @ (emT_P @ SP.A[q].T @ eT_N @ phi) for q in range(n)])
+    left = phi @ (np.eye(SN.dim) + L_N) @ emT_N
+    c = np.stack([(left @ SP.A[p] @ eT_P) @ basis for p in range(n)])
+    cre_phi = np.stack([SP.A[q].T @ phi for q in range(n)])
+    phi_ann = np.stack([phi @ SP.A[p] for p in range(n)])
+    return BruteForceEA(M=M, b=b, c=c, e_hf=e_hf, h_np1=H_P, cre_phi=cre_phi, phi_ann=phi_ann)
+
+
+def build_ea_from_inputs(inp) -> BruteForceEA:
+    return build_ea(inp.o, inp.v, inp.eps, inp.full_antisym(), inp.t1, inp.t2, inp.l1, inp.l2)
+
+
+def exact_resolvent_ea(bf: BruteForceEA, omegas: np.ndarray, eta: float) -> np.ndarray:
+    """G[w, p, q] = <Phi| a_p (w + i eta - (H - E_HF))^{-1} a_q^+ |Phi> over the full N+1 sector."""
+    dim = bf.h_np1.shape[0]
+    out = []
+    for w in omegas:
+        A = (w + 1j * eta + bf.e_hf) * np.eye(dim) - bf.h_np1
+        Y = np.linalg.solve(A, bf.cre_phi.T.astype(complex))              # [dim, n] columns q
+        out.append(bf.phi_ann @ Y)                                         # [p, q]
+    return np.array(out)

@@ -58,7 +58,12 @@ def pack(r1: np.ndarray, r2: np.ndarray) -> np.ndarray:
 
 
 def sigma(hb, x: np.ndarray) -> np.ndarray:
-    """M x for x of shape [D] or [nvec, D] (real or complex)."""
+    """M x for x of shape [D] or [nvec, D] (real or complex). An electron-attachment H-bar
+    (``oracle.ea.EaHbar``) gives the 1p + 2p1h sigma instead, so that the solvers and the reduced
+    model of the oracle run on either space."""
+    if getattr(hb, "sector", "ip") == "ea":
+        from . import ea
+        return ea.sigma(hb, x)
     o, v = hb.o, hb.v
     single = np.asarray(x).ndim == 1
     X = np.atleast_2d(x)
@@ -87,6 +92,9 @@ def sigma_transpose(hb, y: np.ndarray) -> np.ndarray:
 
 def dense_matrix(hb) -> np.ndarray:
     """M as a dense [D, D] array, by applying sigma to the unit vectors."""
+    if getattr(hb, "sector", "ip") == "ea":
+        from . import ea
+        return ea.dense_matrix(hb)
     D = dim(hb.o, hb.v)
     return sigma(hb, np.eye(D)).T
 
@@ -95,6 +103,9 @@ def diagonal(hb) -> np.ndarray:
     """diag(M) from the one-body elements: -F_ii on 1h, F_aa - F_ii - F_jj on 2h1p.
 
     Used only as a (Jacobi) preconditioner; it does not change any solution."""
+    if getattr(hb, "sector", "ip") == "ea":
+        from . import ea
+        return ea.diagonal(hb)
     o, v = hb.o, hb.v
     d1 = -np.diag(hb.Fmi).copy()
     fo = np.diag(hb.Fmi)

@@ -119,6 +119,38 @@ def antisym_block(seed: int, scale: float, P, Q, R, S, chunk: int = 1) -> np.nda
     return out
 
 
+def pair_lists(k: int) -> tuple[np.ndarray, np.ndarray]:
+    """(first, second) index of every pair a < b of range(k), in the packed order
+    pair(a, b) = b(b-1)/2 + a."""
+    b = np.concatenate([np.full(j, j, dtype=np.int64) for j in range(k)]) if k > 1 else np.zeros(0, np.int64)
+    a = np.concatenate([np.arange(j, dtype=np.int64) for j in range(k)]) if k > 1 else np.zeros(0, np.int64)
+    return a, b
+
+
+def antisym_pairs(seed: int, scale: float, P, Q, R, S, chunk: int = 64) -> np.ndarray:
+    """out[k, l] = <P[k] Q[k] || R[l] S[l]>: rows and columns run over index pairs (packed
+    antisymmetric storage); row chunks are generated in parallel threads."""
+    P, Q, R, S = (np.asarray(x, dtype=np.int64) for x in (P, Q, R, S))
+    out = np.empty((len(P), len(R)), dtype=np.float64)
+    r = R[None, :]
+    s = S[None, :]
+
+    def fill(i0):
+        p = P[i0:i0 + chunk, None]
+        q = Q[i0:i0 + chunk, None]
+        out[i0:i0 + chunk] = chem_eri(seed, scale, p, r, q, s) - chem_eri(seed, scale, p, s, q, r)
+
+    starts = list(range(0, len(P), chunk))
+    if out.size < (1 << 20) or len(starts) == 1:
+        for i0 in starts:
+            fill(i0)
+    else:
+        import concurrent.futures as cf
+        with cf.ThreadPoolExecutor(max_workers=min(len(starts), os.cpu_count() or 1)) as ex:
+            list(ex.map(fill, starts))
+    return out
+
+
 def integral_scale(o: int, v: int, mode: str = "size_consistent") -> float:
     if mode == "literal":
         return 0.05
@@ -169,6 +201,15 @@ class Inputs:
         n = self.n
         idx = np.arange(n)
         return antisym_block(self.seed, self.scale, idx, idx, idx, idx)
+
+    def vvvv_pairs(self) -> np.ndarray:
+        """The virtual-virtual block in packed pair form: out[pair(a,b)][pair(c,d)] = <ab||cd> for
+        a < b, c < d (virtual indices counted from 0, pair(a,b) = b(b-1)/2 + a). Generated on demand,
+        from the same integral tensor as the other blocks (the electron-attachment space needs it)."""
+        a, b = pair_lists(self.v)
+        a = a + self.o
+        b = b + self.o
+        return antisym_pairs(self.seed, self.scale, a, b, a, b)
 
 
 def make_inputs(o: int, v: int, seed: int, scale_mode: str = "size_consistent",
