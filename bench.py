@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "G_pq(w) points/s, MOR + mixed precision"
+METRIC_EA = "G^EA_pq(w) points/s (electron-attachment half), MOR + mixed precision"
 UNIT = "points/s"
 
 
@@ -72,6 +73,10 @@ def parse():
                          "autograd: gradients by the adjoint solves against finite differences, and the "
                          "derivative-driven reduced model (run it with --workload adenine_o70_v250)")
     ap.add_argument("--nvec", type=int, default=64, help="vectors per sigma batch (--mode sigma)")
+    ap.add_argument("--sector", default="ip", choices=["ip", "ea"],
+                    help="ip: the ionisation half (1h + 2h1p, default); ea: the electron-attachment half "
+                         "(1p + 2p1h space, gfcc_init_ea) on the workload's attachment window, p = q = the "
+                         "min(o, v) lowest virtual spin-orbitals (all spin-orbitals where the workload uses all)")
     return ap.parse_args()
 
 
@@ -123,6 +128,12 @@ class ClockSampler:
 # the roofline kernel, from an ncu capture of the same kernel; valid only while the kernel's source file
 # is unchanged (its SHA-256 is recorded with the figure).
 TRAFFIC = {
+    ("benzene_o42_v186", 11): {
+        "bytes_per_launch": 5.168e9,
+        "tc_gemm_sha256": "9110833ea70b31ddbac7b19b06fd3679fe50bf183f47b00561481f78df21f98e",
+        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum over the 175 ring-GEMM launches of a timed "
+                  "benchmark step (NVTX range gfcc_ring_gemm, one pass), averaged",
+    },
 }
 
 
@@ -167,6 +178,21 @@ def orbital_set(workload, o, n):
     return list(range(n)) if P_SET.get(workload) == "all" else list(range(o))
 
 
+def ea_orbital_set(workload, inp):
+    """p = q set of the attachment runs: all spin-orbitals where the workload uses all, else the
+    min(o, v) virtual spin-orbitals of lowest energy (the attachment analogue of the occupied set)."""
+    o, v = inp.o, inp.v
+    if P_SET.get(workload) == "all":
+        return list(range(o + v))
+    k = min(o, v)
+    return sorted(int(o + a) for a in np.argsort(inp.eps[o:], kind="stable")[:k])
+
+
+def window(args, W):
+    """(wmin, wmax) of the run: the workload's ionisation window, or its attachment window."""
+    return (W["ea_wmin"], W["ea_wmax"]) if args.sector == "ea" else (W["wmin"], W["wmax"])
+
+
 def pinned_copy(arr):
     """Page-locked host copy of a NumPy array (returned as a NumPy view of a pinned torch tensor)."""
     import torch
@@ -182,10 +208,11 @@ def pinned_empty(shape, dtype):
     return t.numpy(), t
 
 
-def spectrum_peaks(A, grid, rel=0.01):
-    """Peaks of the spectral function on the output grid. A = -(1/pi) sum Im G_pp is negative at poles
-    (the -i eta convention), so the peaks are local minima of A deeper than rel * max |A|."""
-    a = -np.asarray(A)
+def spectrum_peaks(A, grid, rel=0.01, sign=-1.0):
+    """Peaks of the spectral function on the output grid. For the ionisation half A = -(1/pi) sum Im G_pp
+    is negative at poles (the -i eta convention), so the peaks are local minima of A deeper than
+    rel * max |A| (sign = -1); the attachment half (+ i eta) has positive peaks (sign = +1)."""
+    a = sign * np.asarray(A)
     thr = rel * np.abs(a).max()
     k = np.where((a[1:-1] > a[:-2]) & (a[1:-1] >= a[2:]) & (a[1:-1] > thr))[0] + 1
     return {"count": int(len(k)), "threshold_rel": rel, "positions_ha": [round(float(grid[i]), 5) for i in k[:40]]}
@@ -213,32 +240,45 @@ def run_ours(args, rank, world):
     o, v, eta = W["o"], W["v"], W["eta"]
     nw = args.nomega or W["nw"]
     inp = synth.make_inputs(o, v, rank_seed(W["seed"], rank))   # weak scaling: one problem per rank
-    porb = list(range(o + v)) if args.pset == "all" else (list(range(o)) if args.pset == "occupied"
-                                                           else orbital_set(args.workload, o, o + v))
+    ea = args.sector == "ea"
+    if ea:
+        porb = list(range(o + v)) if args.pset == "all" else ea_orbital_set(args.workload, inp)
+    else:
+        porb = list(range(o + v)) if args.pset == "all" else (list(range(o)) if args.pset == "occupied"
+                                                               else orbital_set(args.workload, o, o + v))
     npp = len(porb)
-    seeds = synth.omega_grid(W["wmin"], W["wmax"], args.seeds)
-    grid = np.linspace(W["wmin"], W["wmax"], nw)
+    wmin, wmax = window(args, W)
+    seeds = synth.omega_grid(wmin, wmax, args.seeds)
+    grid = np.linspace(wmin, wmax, nw)
+    t_vvvv = None
+    vp_host = vp_dev = None
+    if ea:   # the packed virtual block <ab||cd> that the attachment space needs (generated once, untimed)
+        t_vvvv = time.perf_counter()
+        vp_host = inp.vvvv_pairs()
+        t_vvvv = time.perf_counter() - t_vvvv
 
     # device-resident inputs (HBM) for the device-timed value
     dev_inputs = synth.Inputs(**{k: (torch.from_numpy(np.ascontiguousarray(getattr(inp, k))).to(dev)
                                      if isinstance(getattr(inp, k), np.ndarray) else getattr(inp, k))
                                  for k in inp.__dataclass_fields__})
+    if ea:
+        vp_dev = torch.from_numpy(vp_host).to(dev)
     G_dev = torch.empty((nw, npp, npp), dtype=torch.complex128, device=dev)
     A_dev = torch.empty((nw,), dtype=torch.float64, device=dev)
     omega_host = np.ascontiguousarray(grid)
 
     stream = torch.cuda.current_stream(dev)
 
-    def step(inputs, G_out, A_out, keep=False):
+    def step(inputs, G_out, A_out, keep=False, vvvv=None):
         ctx = Context(inputs, tol=args.solve_tol, precision=args.precision, stream=stream.cuda_stream,
-                      restart=args.restart)
+                      restart=args.restart, sector=args.sector, vvvv=vvvv)
         if args.siso:
             ctx.mor_build_siso(seeds, eta, porb)
         elif args.krylov > 0:
             ctx.mor_build_krylov(args.krylov, eta, porb)
         else:
             ctx.mor_build(seeds, eta, porb)
-        ref = ctx.mor_refine(W["wmin"], W["wmax"], args.ngrid, args.mor_tol, args.m_max)
+        ref = ctx.mor_refine(wmin, wmax, args.ngrid, args.mor_tol, args.m_max)
         ctx.mor_eval(omega_host, G=G_out, A=A_out)
         info = ctx.mor_info()
         info.update(ctx.mor_stats())
@@ -253,7 +293,7 @@ def run_ours(args, rank, world):
             dist.barrier()
 
     for _ in range(args.warmup):
-        step(dev_inputs, G_dev, A_dev)
+        step(dev_inputs, G_dev, A_dev, vvvv=vp_dev)
     torch.cuda.synchronize()
 
     barrier()
@@ -265,7 +305,7 @@ def run_ours(args, rank, world):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        ref, info, _ = step(dev_inputs, G_dev, A_dev)
+        ref, info, _ = step(dev_inputs, G_dev, A_dev, vvvv=vp_dev)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -279,14 +319,17 @@ def run_ours(args, rank, world):
                    23: "ortho_panel_cholqr", 24: "exact_slice_accumulate", 25: "lowprec_operand_prep",
                    26: "lowprec_combine", 27: "input_upload", 28: "output_copies"}
     phases = {phase_names[k]: round(G.profile_read(k)[1] / args.steps, 1) for k in phase_names}
+    allocs = {"allocations": G.profile_read(29)[0] // args.steps, "alloc_host_ms": round(G.profile_read(29)[1] / args.steps, 1),
+              "frees": G.profile_read(30)[0] // args.steps, "free_host_ms": round(G.profile_read(30)[1] / args.steps, 1)}
     cgs = G.profile_read(14)   # (launch groups, ms, algorithmic bytes) of the Arnoldi sweeps
     slicing, accum = G.profile_read(13), G.profile_read(24)   # exact-slice passes (bytes in the third field)
+    sig_lp, sig_ex = G.profile_read(3), G.profile_read(4)      # whole sigmas (algorithmic flops)
     cgs_parts = {name: G.profile_read(k) for k, name in
                  ((15, "multidot_kernel"), (16, "cgs_update_kernel<dot>"), (17, "cgs_update_kernel<norm>"),
                   (18, "all three, batches < 32 columns"))}
     G.profile(False)
     clk = clocks.stop()
-    spectrum = spectrum_peaks(A_dev.cpu().numpy(), grid)
+    spectrum = spectrum_peaks(A_dev.cpu().numpy(), grid, sign=1.0 if ea else -1.0)
     tuned = autotune_summary(G.autotune_report())
 
     # end to end through the public API with host buffers: the inputs are copied from page-locked host
@@ -306,27 +349,34 @@ def run_ours(args, rank, world):
             else:
                 host_fields[k] = a
         host_inputs = synth.Inputs(**host_fields)
+        vp_pinned = None
+        if ea:
+            vp_pinned, tv = pinned_copy(vp_host)
+            keep_alive.append(tv)
         G_host, tg = pinned_empty((nw, npp, npp), torch.complex128)
         A_host, ta = pinned_empty((nw,), torch.float64)
         keep_alive += [tg, ta]
         n_e2e = max(1, min(args.steps, args.e2e_steps))
-        step(host_inputs, G_host, A_host)
+        step(host_inputs, G_host, A_host, vvvv=vp_pinned)
         torch.cuda.synchronize()
         times = []
         G.profile(True)
         for k in range(n_e2e):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            _, _, kc = step(host_inputs, G_host, A_host, keep=(k == n_e2e - 1))
+            _, _, kc = step(host_inputs, G_host, A_host, keep=(k == n_e2e - 1), vvvv=vp_pinned)
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
             if kc is not None:
                 kept = kc
         e2e_phases = {"input_upload": G.profile_read(27)[1] / n_e2e, "output_copies": G.profile_read(28)[1] / n_e2e,
-                      "hbar_build": G.profile_read(8)[1] / n_e2e}
+                      "hbar_build": G.profile_read(8)[1] / n_e2e, "alloc_host": G.profile_read(29)[1] / n_e2e,
+                      "free_host": G.profile_read(30)[1] / n_e2e}
         G.profile(False)
         e2e_s = statistics.median(times)
         h2d = sum(getattr(inp, k).nbytes for k in ("eps", "oooo", "ooov", "oovv", "ovov", "ovvv", "t1", "t2", "l1", "l2"))
+        if ea:
+            h2d += vp_host.nbytes
         e2e = {"value": nw * npp / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(G_host.nbytes + A_host.nbytes), "steps": n_e2e, "warmup": 1,
                "median_s": e2e_s, "min_s": min(times), "max_s": max(times),
@@ -342,7 +392,7 @@ def run_ours(args, rank, world):
     full = None
     if args.full_stride > 0 and rank == 0:
         if kept is None:
-            _, _, kept = step(dev_inputs, G_dev, A_dev, keep=True)
+            _, _, kept = step(dev_inputs, G_dev, A_dev, keep=True, vvvv=vp_dev)
         full = full_compare(args, kept, grid, porb, eta, stream)
     if kept is not None:
         kept.close()
@@ -390,12 +440,17 @@ def run_ours(args, rank, world):
         if dom in (0, 11) and args.precision == "tf32":
             roof["frac_of_measured_tf32_sustained"] = ach / OWN_PEAKS["tf32_tflops_sustained"]
     return inp, {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRIC_EA if ea else METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup,
         "ms_per_step": dev_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": f"c128 (f64 residuals, {args.precision} tensor-core inner sigma)", "data": "synthetic",
-        "config": {"workload": args.workload, "o": o, "v": v, "D": inp.dim, "n_omega": nw, "n_p": npp, "n_q": npp,
-                   "p_set": "all spin-orbitals" if npp == o + v else "occupied spin-orbitals",
-                   "eta": eta, "window_ha": [W["wmin"], W["wmax"]], "seeds": args.seeds, "mor_tol": args.mor_tol,
+        "config": {"workload": args.workload, "o": o, "v": v, "D": v + v * (v - 1) // 2 * o if ea else inp.dim,
+                   "n_omega": nw, "n_p": npp, "n_q": npp,
+                   **({"vvvv_generation_s": round(t_vvvv, 1)} if ea else {}),
+                   "p_set": "all spin-orbitals" if npp == o + v else (
+                       f"the {npp} lowest virtual spin-orbitals" if ea else "occupied spin-orbitals"),
+                   "sector": "EA (1p + 2p1h, gfcc_init_ea)" if ea else "IP (1h + 2h1p)",
+                   "eta": eta, "window_ha": [wmin, wmax], "seeds": args.seeds, "mor_tol": args.mor_tol,
                    "solve_tol": args.solve_tol, "restart": args.restart,
                    "reduced_model": "one SISO model of G_pp per orbital" if args.siso else
                    (f"block Krylov space of M on the b_p ({args.krylov} initial blocks)" if args.krylov > 0 else
@@ -406,7 +461,7 @@ def run_ours(args, rank, world):
                    "l2": "working set (operators >= 0.5 GB, Krylov bases) larger than L2; no flush",
                    "parallelism": f"replicas x{world}"},
         "e2e": e2e, "gpu_launches": int(launches), "gpu_launches_per_step": int(launches // args.steps),
-        "roofline": roof, "gemm_classes": kernels, "phases_ms": phases,
+        "roofline": roof, "gemm_classes": kernels, "phases_ms": phases, "device_allocations_per_step": allocs,
         "hbm_kernels": {"arnoldi_cgs_sweeps (multidot_kernel, cgs_update_kernel x2)": {
             "bound": "hbm", "steps": cgs[0], "ms": cgs[1], "algorithmic_bytes": cgs[2],
             "achieved": cgs[2] / (cgs[1] / 1e3) / 1e9 if cgs[1] > 0 else None, "unit": "GB/s",
@@ -419,6 +474,16 @@ def run_ours(args, rank, world):
                       "frac": b / (ms / 1e3) / 1e9 / peaks["hbm_gbs"] if ms > 0 and peaks.get("hbm_gbs") else None}
                for name, (n, ms, b) in (("exact_slicing (FP64 rows -> bf16 integer slices)", slicing),
                                         ("exact_slice_accumulate (int32 split sums -> FP64 output)", accum))}},
+        "sigma_rates": {
+            "what": "the method's sigma flops (2 per multiply-add of the ring, oooo, three-body and coupling terms) "
+                    "per second of the whole sigma (operand preparation, GEMMs, combine)",
+            f"{args.precision}_inner": {"calls": sig_lp[0], "ms": sig_lp[1],
+                                        "tflops": sig_lp[2] / (sig_lp[1] / 1e3) / 1e12 if sig_lp[1] > 0 else None},
+            "fp64_accurate_exact_slices": {
+                "calls": sig_ex[0], "ms": sig_ex[1],
+                "fp64_equivalent_tflops": sig_ex[2] / (sig_ex[1] / 1e3) / 1e12 if sig_ex[1] > 0 else None,
+                "vs_measured_fp64_rate": (sig_ex[2] / (sig_ex[1] / 1e3) / 1e12) / OWN_PEAKS["fp64_tflops"]
+                if sig_ex[1] > 0 else None}},
         "clocks": clk,
         "spectrum": spectrum,
         "autotune": {"enabled": os.environ.get("GFCC_AUTOTUNE", "1") != "0",
@@ -459,7 +524,8 @@ def full_compare(args, ctx, grid, porb, eta, stream):
     nw = len(grid)
     w_grid = grid[::args.full_stride]
     sampled = np.asarray(ctx.mor_info()["sampled"])
-    w_mid = 0.5 * (W["wmin"] + W["wmax"])
+    wlo, whi = window(args, W)
+    w_mid = 0.5 * (wlo + whi)
     sub = np.concatenate([w_grid, sampled, [w_mid]])
     ng, ns = len(w_grid), len(sampled)
     ctx.set_opts(tol=args.solve_tol, precision="fp64_tc")
@@ -724,6 +790,26 @@ def oracle_sample(args, ncols, inp=None):
             "seconds": dt, "_G": Gq}
 
 
+def ea_oracle_sample(args, ncols, inp):
+    """The attachment oracle on a bounded sample: full GMRES solves (IP form, frequency -w) of the first
+    ncols free terms of the p set at the middle of the attachment window."""
+    from oracle import ea
+    from oracle import solve as sv
+    W = synth.WORKLOADS[args.workload]
+    hb = ea.build(inp)
+    porb = ea_orbital_set(args.workload, inp) if args.pset != "all" else list(range(inp.n))
+    Bp, Cp = ea.ip_form(inp, hb, porb[:ncols], porb)
+    w = [0.5 * sum(window(args, W))]
+    t0 = time.perf_counter()
+    Y, res = sv.gmres_solve(hb, Bp, [-w[0]], W["eta"], tol=args.solve_tol)
+    dt = time.perf_counter() - t0
+    Gq = sv.green(Cp, Y)[0]
+    return {"value": ncols / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{ncols} full-dimension FP64 GMRES solve(s) of the attachment systems (tol {args.solve_tol}) "
+                      f"at w = {w[0]} Ha, the first {ncols} orbital(s) of the p set, {args.workload}; H-bar build "
+                      f"and input generation untimed", "seconds": dt, "_G": Gq}
+
+
 def run_reference(args):
     """The oracle on the host cores, in bounded steps. Set-up (untimed): inputs, the oracle's H-bar
     build, and one full GMRES solve of (w_mid, p = 0) that gives the number of operator applications a
@@ -797,9 +883,11 @@ def main():
     inp, out = run_ours(args, rank, world)
     if rank == 0:
         full = out.get("full_fp64")
-        if args.cpu_sample > 0:
+        if args.cpu_sample > 0 and args.sector == "ea" and inp.v > 130:
+            out["cpu_baseline"] = {"skipped": "the attachment oracle holds full v^4 arrays; sampled up to v = 130"}
+        elif args.cpu_sample > 0:
             try:
-                cb = oracle_sample(args, args.cpu_sample, inp)
+                cb = (ea_oracle_sample if args.sector == "ea" else oracle_sample)(args, args.cpu_sample, inp)
                 Go = cb.pop("_G")
                 if full is not None:   # the GPU results at the oracle's frequency, p = 0..ncols-1
                     k = Go.shape[0]

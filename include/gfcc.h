@@ -100,14 +100,44 @@ int gfcc_default_opts(gfcc_opts* opts);
  *   vb          integral blocks.
  *   t1[o][v], t2[o][o][v][v] (t_ij^ab, antisymmetric), l1[o][v] (lambda^i_a), l2[o][o][v][v]
  *               (lambda^ij_ab).
- *   All arrays: host or device (copied with cudaMemcpyDefault).
+ *   All arrays: host or device (copied to the device with the copy kind of their memory).
  *   opts        may be NULL (defaults).  stream: cudaStream_t or NULL for the legacy stream.
  * Errors: GFCC_ERR_ARG (o < 2, v < 1, null pointers), GFCC_ERR_NONFINITE, GFCC_ERR_OOM, GFCC_ERR_CUDA. */
 int gfcc_init(gfcc_t* ctx, int o, int v, const double* eps, const gfcc_vblocks* vb,
               const double* t1, const double* t2, const double* l1, const double* l2,
               const gfcc_opts* opts, void* stream);
 
-/* Dimension D of the 1h+2h1p space. */
+/* Create a context for the electron-attachment (EA) half of the Green's function instead: the second
+ * term <Psi| a_p (w - (H - E_0) + i eta)^{-1} a_q^+ |Psi> of the retarded Green's function of Eq. gfxn0,
+ * which the paper names beside the IP term (IP/EA-EOM-CC, Introduction) but does not write out. In the
+ * CC form (Eqs. gfxn1/gfxn2 with the field operators exchanged):
+ *   G^EA_pq(w) = <Phi|(1 + Lambda) abar_p (w - Hbar_N + i eta)^{-1} abar_q^+ |Phi> = c_p^T y_q(w),
+ *   (w + i eta - M_EA) y_q(w) = b_q,  b_q = e^{-T} a_q^+ e^{T}|Phi>,  c_p = <Phi|(1+Lambda) e^{-T} a_p e^{T}
+ * over the 1p + 2p1h space y = sum_a y^a a_a^+ + sum_{a<b,j} y^{ab}_j a_a^+ a_b^+ a_j.
+ *   Arguments as gfcc_init (o >= 1, v >= 2), plus
+ *   vvvv[V][V]  the virtual block <ab||cd> in packed pair form, V = v(v-1)/2, row pair(a,b) and column
+ *               pair(c,d) = d(d-1)/2 + c for a < b, c < d (virtual indices from 0). Host or device; copied.
+ * The space has dimension D = v + V*o; packed vector index a for y^a, v + pair(a,b)*o + j for y^{ab}_j.
+ * Every other entry point then works on the EA systems, with these conventions:
+ *   - frequencies (omegas, seeds, [wmin, wmax], the sampled frequencies reported by gfcc_mor_info and
+ *     gfcc_mor_model_info) are the physical w of the formula above; internally the systems are solved in
+ *     the IP form (w' - i eta + M_EA) y = -b_q at w' = -w, so refinement ties go to the higher w, and
+ *     saved models carry their own tag (a model of one space does not load into the other);
+ *   - the orbital set named "p set" / orbitals is the set of free terms b_q (the solved columns) and the
+ *     "q set" / qorb the set of left vectors c_p: G[(w*np + k)*nq + l] = G^EA_{qorb[l], orbitals[k]}(w);
+ *   - gfcc_vectors returns b_q (transpose = 0) and c_p (transpose = 1); gfcc_sigma applies M_EA;
+ *   - A(w) = -(1/pi) sum_p Im G_pp(w) as for the IP space (positive peaks, since the attachment
+ *     broadening is + i eta);
+ *   - gfcc_green_derivatives returns dG^EA/dw and dG^EA/deta; gfcc_green_grad_t2 returns GFCC_ERR_STATE.
+ * Errors: as gfcc_init; GFCC_ERR_ARG also for a null vvvv. */
+int gfcc_init_ea(gfcc_t* ctx, int o, int v, const double* eps, const gfcc_vblocks* vb, const double* vvvv,
+                 const double* t1, const double* t2, const double* l1, const double* l2, const gfcc_opts* opts,
+                 void* stream);
+
+/* The space of a context: *sector = 0 (IP, gfcc_init) or 1 (EA, gfcc_init_ea). */
+int gfcc_sector(gfcc_t ctx, int* sector);
+
+/* Dimension D of the context's space (1h+2h1p, or 1p+2p1h for an EA context). */
 int gfcc_dim(gfcc_t ctx, int* D);
 
 /* Replace the options (tolerance, restart length, precision, ...) of an existing context. */
@@ -296,12 +326,15 @@ long long gfcc_launch_count(void);
  * 13 splitting of FP64 rows into exact slices; 14 the fused Gram-Schmidt sweeps of FP32-basis Arnoldi
  * steps; 15, 16, 17 the first, second and third of those sweeps alone for batches of at least 32
  * columns; 18 the three sweeps of batches of fewer than 32 columns (classes 14-18 count algorithmic
- * HBM bytes in the "flops" field, as do classes 13 and 24); 19 Householder reductions of Hhat to Hessenberg form; 20 the
+ * HBM bytes in the "flops" field, as do classes 13 and 24; classes 3 and 4 count the sigma's algorithmic
+ * flops, whatever arithmetic carries them out); 19 Householder reductions of Hhat to Hessenberg form; 20 the
  * per-frequency shifted Hessenberg solves; 21, 22 the coefficient products and updates of the block
  * Gram-Schmidt passes; 23 the Cholesky QR of the panels; 24 the accumulation and output passes of the
  * exact-slice products; 25 the operand preparation and 26 the combine pass of the low-precision sigma;
  * 27 the copies of the caller's inputs to the device in gfcc_init; 28 the copies of results into the
- * caller's output buffers (device to host for host buffers).
+ * caller's output buffers (device to host for host buffers); 29 and 30 the library's device
+ * allocations and frees: their count and the host milliseconds spent inside cudaMalloc and cudaFree
+ * (host clock, not events; cudaFree also waits for the device).
  * Events are recorded on the stream each region is launched on. */
 int gfcc_profile(int enable);
 

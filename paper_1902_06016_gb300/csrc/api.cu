@@ -263,7 +263,27 @@ void solve_rhs(gfcc_ctx* c, const std::vector<double>& ws, double eta, int np, c
 }
 
 // Solve at frequencies ws for the model's p set and append the solutions to the subspace.
+void mor_add_chunk(gfcc_ctx* c, const std::vector<double>& ws);
 void mor_add_frequencies(gfcc_ctx* c, const std::vector<double>& ws) {
+  // bounded memory: the solutions, residuals, images, right-hand sides, initial guesses and derivative
+  // solves of a chunk of frequencies (6 vectors per column), and the growth of S, Z and the residual
+  // basis they cause (4 columns per column, doubled while a buffer is regrown), take at most about a
+  // quarter of the free device memory; the chunks keep the frequency order, so the columns reach the
+  // subspace in the same order as in one piece
+  size_t freeb = 0, totalb = 0;
+  if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) { cudaGetLastError(); freeb = 16ull << 30; }
+  if (freeb < totalb / 3) {   // scratch of earlier calls (e.g. adjoint solves) holds much of the device
+    gfcc::release_scratch(c);
+    if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) { cudaGetLastError(); freeb = 16ull << 30; }
+  }
+  const long long per_w = (long long)c->D * (long long)c->mor.porb.size() * (long long)sizeof(cplx) * 14;
+  const size_t per_chunk = (size_t)std::max<long long>(1, (long long)(0.25 * (double)freeb) / std::max(per_w, 1LL));
+  for (size_t i0 = 0; i0 < ws.size(); i0 += per_chunk) {
+    const std::vector<double> part(ws.begin() + i0, ws.begin() + std::min(ws.size(), i0 + per_chunk));
+    mor_add_chunk(c, part);
+  }
+}
+void mor_add_chunk(gfcc_ctx* c, const std::vector<double>& ws) {
   gfcc::MorState& ms = c->mor;
   cudaStream_t s = c->stream;
   const long long D = c->D;
@@ -532,19 +552,23 @@ static int check_opts(const gfcc_opts* o, std::string& why) {
   return GFCC_OK;
 }
 
-int gfcc_init(gfcc_t* out, int o, int v, const double* eps, const gfcc_vblocks* vb, const double* t1,
-              const double* t2, const double* l1, const double* l2, const gfcc_opts* opts, void* stream) {
+static int init_context(gfcc_t* out, int sector, int o, int v, const double* eps, const gfcc_vblocks* vb,
+                        const double* vvvv, const double* t1, const double* t2, const double* l1, const double* l2,
+                        const gfcc_opts* opts, void* stream) {
   if (!out) return GFCC_ERR_ARG;
   *out = nullptr;
-  if (o < 2 || v < 1 || !eps || !vb || !t1 || !t2 || !l1 || !l2 || !vb->oooo || !vb->ooov || !vb->oovv ||
-      !vb->ovov || !vb->ovvv)
+  if (!eps || !vb || !t1 || !t2 || !l1 || !l2 || !vb->oooo || !vb->ooov || !vb->oovv || !vb->ovov || !vb->ovvv)
     return GFCC_ERR_ARG;
-  const long long P = (long long)o * (o - 1) / 2;
-  const long long D = o + P * v;
-  if (D >= (1LL << 31) || (long long)o * v * o * v >= (1LL << 40)) return GFCC_ERR_ARG;
+  if (sector == 0 ? (o < 2 || v < 1) : (o < 1 || v < 2 || !vvvv)) return GFCC_ERR_ARG;
+  // block sizes of the operator: the EA space has the IP layout with the index ranges exchanged
+  const int po = sector == 0 ? o : v, pv = sector == 0 ? v : o;
+  const long long P = (long long)po * (po - 1) / 2;
+  const long long D = po + P * pv;
+  if (D >= (1LL << 31) || (long long)o * v * o * v >= (1LL << 40) || P * P >= (1LL << 40)) return GFCC_ERR_ARG;
   gfcc_ctx* c = new (std::nothrow) gfcc_ctx();
   if (!c) return GFCC_ERR_OOM;
-  c->o = o; c->v = v; c->n = o + v; c->P = (int)P; c->D = (int)D;
+  c->o = po; c->v = pv; c->n = o + v; c->P = (int)P; c->D = (int)D;
+  c->sector = sector;
   c->stream = (cudaStream_t)stream;
   if (opts) c->opts = *opts; else gfcc_default_opts(&c->opts);
   std::string why;
@@ -554,7 +578,9 @@ int gfcc_init(gfcc_t* out, int o, int v, const double* eps, const gfcc_vblocks* 
   try {
     GFCC_CUDA(cudaGetDevice(&c->device));
     gfcc::HostInputs in{eps, vb->oooo, vb->ooov, vb->oovv, vb->ovov, vb->ovvv, t1, t2, l1, l2};
-    gfcc::build_operator(c, in);
+    in.vvvv = vvvv;
+    if (sector == 0) gfcc::build_operator(c, in);
+    else gfcc::build_operator_ea(c, in);
     if (c->opts.precision == GFCC_PREC_TF32 || c->opts.precision == GFCC_PREC_BF16)
       gfcc::build_low_precision(c, c->opts.precision);
   } catch (gfcc::Error& e) {
@@ -565,6 +591,23 @@ int gfcc_init(gfcc_t* out, int o, int v, const double* eps, const gfcc_vblocks* 
   }
   if (status != GFCC_OK) { delete c; return status; }
   *out = c;
+  return GFCC_OK;
+}
+
+int gfcc_init(gfcc_t* out, int o, int v, const double* eps, const gfcc_vblocks* vb, const double* t1,
+              const double* t2, const double* l1, const double* l2, const gfcc_opts* opts, void* stream) {
+  return init_context(out, 0, o, v, eps, vb, nullptr, t1, t2, l1, l2, opts, stream);
+}
+
+int gfcc_init_ea(gfcc_t* out, int o, int v, const double* eps, const gfcc_vblocks* vb, const double* vvvv,
+                 const double* t1, const double* t2, const double* l1, const double* l2, const gfcc_opts* opts,
+                 void* stream) {
+  return init_context(out, 1, o, v, eps, vb, vvvv, t1, t2, l1, l2, opts, stream);
+}
+
+int gfcc_sector(gfcc_t c, int* sector) {
+  if (!c || !sector) return GFCC_ERR_ARG;
+  *sector = c->sector;
   return GFCC_OK;
 }
 
@@ -633,9 +676,17 @@ int gfcc_vectors(gfcc_t c, const int* orbitals, int norb, int transpose, double*
     if (orbitals[k] < 0 || orbitals[k] >= c->n) { c->last_error = "gfcc_vectors: orbital out of range"; return GFCC_ERR_ARG; }
   API_BEGIN
   const double* src = transpose ? c->cvec.p : c->bvec.p;
-  for (int k = 0; k < norb; ++k)
-    copy_out(out + (long long)k * ld, src + (long long)orbitals[k] * c->D, sizeof(double) * c->D, c->stream);
-  GFCC_CUDA(cudaStreamSynchronize(c->stream));
+  DBuf<double> neg;
+  if (c->sector == 1 && !transpose) neg.alloc(c->D);   // EA free terms are held as -b_q (the IP form)
+  for (int k = 0; k < norb; ++k) {
+    const double* row = src + (long long)orbitals[k] * c->D;
+    if (neg.p) {
+      gfcc::axpby(c->D, -1.0, row, 0.0, neg.p, c->stream);
+      row = neg.p;
+    }
+    copy_out(out + (long long)k * ld, row, sizeof(double) * c->D, c->stream);
+    GFCC_CUDA(cudaStreamSynchronize(c->stream));
+  }
   API_END(c)
 }
 
@@ -645,6 +696,16 @@ static int check_orbitals(gfcc_t c, const int* orb, int n, const char* what) {
     if (orb[k] < 0 || orb[k] >= c->n) { c->last_error = std::string(what) + ": orbital out of range"; return GFCC_ERR_ARG; }
   return GFCC_OK;
 }
+
+// Frequencies as the solver sees them: the EA systems (w + i eta - M) y = b are solved in the IP form
+// (w' - i eta + M) y = -b at w' = -w.
+static std::vector<double> solver_freqs(gfcc_t c, const double* w, int n) {
+  std::vector<double> ws(w, w + n);
+  if (c->sector == 1)
+    for (double& x : ws) x = -x;
+  return ws;
+}
+static double user_freq(gfcc_t c, double w) { return c->sector == 1 ? -w : w; }
 
 int gfcc_solve_full(gfcc_t c, const double* omegas, int nw, double eta, const int* orbitals, int np,
                     const int* qorb, int nq, double* G, double* A, double* X, int ldx, gfcc_stats* stats) {
@@ -663,7 +724,7 @@ int gfcc_solve_full(gfcc_t c, const double* omegas, int nw, double eta, const in
   std::vector<int> porb(orbitals, orbitals + np);
   std::vector<int> qv = qorb ? std::vector<int>(qorb, qorb + nq) : porb;
   nq = (int)qv.size();
-  std::vector<double> ws(omegas, omegas + nw);
+  std::vector<double> ws = solver_freqs(c, omegas, nw);
   const long long ncols = (long long)nw * np;
   DBuf<cplx> Gd, Xd;
   DBuf<double> Ad;
@@ -718,7 +779,7 @@ int gfcc_green_derivatives(gfcc_t c, const double* omegas, int nw, double eta, c
   std::vector<int> porb(orbitals, orbitals + np);
   std::vector<int> qv = qorb ? std::vector<int>(qorb, qorb + nq) : porb;
   nq = (int)qv.size();
-  std::vector<double> ws(omegas, omegas + nw);
+  std::vector<double> ws = solver_freqs(c, omegas, nw);
   const long long nx = (long long)nw * np, ny = (long long)nw * nq;
   DBuf<cplx> X, Y, Gd, dwd, ded, part;
   X.alloc(D * nx);
@@ -738,6 +799,8 @@ int gfcc_green_derivatives(gfcc_t c, const double* omegas, int nw, double eta, c
   GFCC_LAUNCH_CHECK();
   bilinear_reduce_kernel<<<(ntrip + 255) / 256, 256, 0, s>>>(part.p, nchunk, ntrip, dwd.p, ded.p);
   GFCC_LAUNCH_CHECK();
+  if (c->sector == 1)   // EA: the solver's frequency is -w, so dG/dw changes sign (eta enters both forms alike)
+    gfcc::axpby(2LL * ntrip, -1.0, reinterpret_cast<const double*>(dwd.p), 0.0, reinterpret_cast<double*>(dwd.p), s);
   if (G) copy_out(G, Gd.p, sizeof(cplx) * ntrip, s);
   if (dG_domega) copy_out(dG_domega, dwd.p, sizeof(cplx) * ntrip, s);
   if (dG_deta) copy_out(dG_deta, ded.p, sizeof(cplx) * ntrip, s);
@@ -752,6 +815,7 @@ int gfcc_green_grad_t2(gfcc_t c, const double* omegas, int nw, double eta, const
     c->last_error = "gfcc_green_grad_t2: bad frequencies, eta or null pointers";
     return GFCC_ERR_ARG;
   }
+  if (c->sector != 0) { c->last_error = "gfcc_green_grad_t2: available for the IP space only"; return GFCC_ERR_STATE; }
   int rc = check_orbitals(c, orbitals, np, "gfcc_green_grad_t2");
   if (rc) return rc;
   if (qorb) { rc = check_orbitals(c, qorb, nq, "gfcc_green_grad_t2(q)"); if (rc) return rc; }
@@ -763,13 +827,13 @@ int gfcc_green_grad_t2(gfcc_t c, const double* omegas, int nw, double eta, const
   std::vector<int> porb(orbitals, orbitals + np);
   std::vector<int> qv = qorb ? std::vector<int>(qorb, qorb + nq) : porb;
   nq = (int)qv.size();
-  std::vector<double> ws(omegas, omegas + nw);
+  std::vector<double> ws = solver_freqs(c, omegas, nw);
   const long long S = (long long)nw * np;
   DBuf<cplx> X, W, U, Gb, Gd;
   DBuf<double> t2b;
   X.alloc(D * S); W.alloc(D * S); U.alloc(D * S);
   Gb.alloc(S * nq);
-  GFCC_CUDA(cudaMemcpyAsync(Gb.p, Gbar, sizeof(cplx) * S * nq, cudaMemcpyDefault, s));
+  GFCC_CUDA(cudaMemcpyAsync(Gb.p, Gbar, sizeof(cplx) * S * nq, gfcc::kind_to_device(Gbar), s));
   if (G) Gd.alloc(S * nq);
   gfcc_stats st{};
   solve_columns(c, ws, eta, porb, qv, G ? Gd.p : nullptr, X.p, nullptr, &st);
@@ -815,7 +879,7 @@ int gfcc_mor_build(gfcc_t c, const double* seeds, int ns, double eta, const int*
     for (double x : ms.bnorm) GFCC_CHECK(x > 0.0, GFCC_ERR_ARG, "gfcc_mor_build: zero right-hand side");
   }
   gfcc::mor_init_basis(c);
-  std::vector<double> ws(seeds, seeds + ns);
+  std::vector<double> ws = solver_freqs(c, seeds, ns);
   std::sort(ws.begin(), ws.end());
   ws.erase(std::unique(ws.begin(), ws.end()), ws.end());
   mor_add_frequencies(c, ws);
@@ -837,6 +901,11 @@ int gfcc_mor_refine(gfcc_t c, double wmin, double wmax, int ngrid, double tol, i
     return GFCC_ERR_ARG;
   }
   API_BEGIN
+  if (c->sector == 1) {   // EA: the window in the solver's frequency w' = -w
+    const double lo = -wmax, hi = -wmin;
+    wmin = lo;
+    wmax = hi;
+  }
   std::vector<double> grid(ngrid);
   for (int k = 0; k < ngrid; ++k) grid[k] = wmin + (wmax - wmin) * (double)k / (double)(ngrid - 1);
   DBuf<double> dres;
@@ -956,6 +1025,8 @@ int gfcc_mor_eval(gfcc_t c, const double* omegas, int nw, double* G, double* A, 
   API_BEGIN
   if (nw == 0) return GFCC_OK;
   cudaStream_t s = c->stream;
+  const std::vector<double> wsol = solver_freqs(c, omegas, nw);
+  omegas = wsol.data();
   if (!c->siso.empty()) {   // per-orbital models: G_pp on the diagonal of [nw][np][np], zero elsewhere
     const int np = (int)c->siso.size();
     DBuf<cplx> Gd, Gk;
@@ -1025,6 +1096,10 @@ int gfcc_mor_info(gfcc_t c, double* w, int cap, int* ns, int* m, int* np, int* n
     if (m) *m = mt;
     if (np) *np = (int)c->siso.size();
     if (nq) *nq = (int)c->siso.size();
+    if (c->sector == 1) {
+      for (double& x : all) x = -x;
+      std::sort(all.begin(), all.end());
+    }
     if (w)
       for (int k = 0; k < cap && k < (int)all.size(); ++k) w[k] = all[k];
     return GFCC_OK;
@@ -1035,7 +1110,7 @@ int gfcc_mor_info(gfcc_t c, double* w, int cap, int* ns, int* m, int* np, int* n
   if (np) *np = (int)ms.porb.size();
   if (nq) *nq = (int)ms.qorb.size();
   if (w)
-    for (int k = 0; k < cap && k < (int)ms.sampled.size(); ++k) w[k] = ms.sampled[k];
+    for (int k = 0; k < cap && k < (int)ms.sampled.size(); ++k) w[k] = user_freq(c, ms.sampled[k]);
   return GFCC_OK;
 }
 
@@ -1048,7 +1123,7 @@ int gfcc_mor_model_info(gfcc_t c, int k, int* orbital, double* w, int cap, int* 
   if (ns) *ns = (int)ms.sampled.size();
   if (m) *m = ms.m;
   if (w)
-    for (int j = 0; j < cap && j < (int)ms.sampled.size(); ++j) w[j] = ms.sampled[j];
+    for (int j = 0; j < cap && j < (int)ms.sampled.size(); ++j) w[j] = user_freq(c, ms.sampled[j]);
   return GFCC_OK;
 }
 
@@ -1098,7 +1173,7 @@ int gfcc_mor_build_siso(gfcc_t c, const double* seeds, int ns, double eta, const
     ms.bnorm = {std::sqrt(bn[k])};
     gfcc::mor_init_basis(c);
   }
-  std::vector<double> ws(seeds, seeds + ns);
+  std::vector<double> ws = solver_freqs(c, seeds, ns);
   std::sort(ws.begin(), ws.end());
   ws.erase(std::unique(ws.begin(), ws.end()), ws.end());
   std::vector<std::pair<int, double>> add;
@@ -1158,7 +1233,8 @@ int gfcc_mor_save(gfcc_t c, const char* path) {
   const int qn = ms.qn, qcap = ms.q_cap;
   std::ofstream f(path, std::ios::binary);
   GFCC_CHECK(f.good(), GFCC_ERR_ARG, std::string("gfcc_mor_save: cannot open ") + path);
-  const char magic[8] = {'G', 'F', 'C', 'C', 'M', 'O', 'R', '2'};
+  // the EA space has its own tag: its block sizes can equal those of an IP space with o and v exchanged
+  const char magic[8] = {'G', 'F', 'C', 'C', 'M', 'O', 'R', c->sector == 1 ? 'E' : '2'};
   f.write(magic, 8);
   int hdr[7] = {c->o, c->v, (int)D, m, np, nq, qn};
   f.write(reinterpret_cast<const char*>(hdr), sizeof(hdr));
@@ -1196,7 +1272,8 @@ int gfcc_mor_load(gfcc_t c, const char* path) {
   GFCC_CHECK(f.good(), GFCC_ERR_ARG, std::string("gfcc_mor_load: cannot open ") + path);
   char magic[8];
   f.read(magic, 8);
-  GFCC_CHECK(f.good() && std::memcmp(magic, "GFCCMOR2", 8) == 0, GFCC_ERR_ARG, "gfcc_mor_load: not a model file");
+  GFCC_CHECK(f.good() && std::memcmp(magic, c->sector == 1 ? "GFCCMORE" : "GFCCMOR2", 8) == 0, GFCC_ERR_ARG,
+             "gfcc_mor_load: not a model file of this space (IP or EA)");
   int hdr[7];
   f.read(reinterpret_cast<char*>(hdr), sizeof(hdr));
   GFCC_CHECK(f.good() && hdr[0] == c->o && hdr[1] == c->v && hdr[2] == c->D, GFCC_ERR_ARG,

@@ -5,6 +5,7 @@
 #include <cuComplex.h>
 #include <cstdint>
 #include <cstdio>
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -71,7 +72,9 @@ enum ProfClass {
   PROF_LP_COMBINE = 26,       // the combine pass of the low-precision sigma (up reduction, final sum)
   PROF_UPLOAD = 27,           // copies of the caller's inputs to the device in gfcc_init
   PROF_DOWNLOAD = 28,         // copies of results into the caller's output buffers
-  PROF_NCLASS = 29
+  PROF_ALLOC = 29,            // device allocations of the library's buffers (host time inside cudaMalloc)
+  PROF_FREE = 30,             // device frees of the library's buffers (host time inside cudaFree)
+  PROF_NCLASS = 31
 };
 struct ProfScope {   // records CUDA events around one launch on stream s when profiling is on
   int cls;
@@ -85,6 +88,10 @@ struct ProfScope {   // records CUDA events around one launch on stream s when p
 // ---------------------------------------------------------------------------------------------
 // device buffers owned by the context
 // ---------------------------------------------------------------------------------------------
+// host-side accounting of device allocations and frees while profiling is on (classes 29, 30)
+bool alloc_profiling();
+void note_alloc(int cls, double ms);
+
 template <typename T>
 struct DBuf {
   T* p = nullptr;
@@ -103,7 +110,15 @@ struct DBuf {
   }
   ~DBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (alloc_profiling()) {
+        const auto t0 = std::chrono::steady_clock::now();
+        cudaFree(p);
+        note_alloc(PROF_FREE, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+      } else {
+        cudaFree(p);
+      }
+    }
     p = nullptr;
     n = 0;
   }
@@ -111,7 +126,14 @@ struct DBuf {
     if (count <= n && p) return;
     release();
     if (count == 0) return;
-    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    cudaError_t e;
+    if (alloc_profiling()) {
+      const auto t0 = std::chrono::steady_clock::now();
+      e = cudaMalloc(&p, count * sizeof(T));
+      note_alloc(PROF_ALLOC, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+    } else {
+      e = cudaMalloc(&p, count * sizeof(T));
+    }
     if (e != cudaSuccess) {
       p = nullptr;
       throw Error{GFCC_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed"};
@@ -225,7 +247,11 @@ struct Stats {
 }  // namespace gfcc
 
 struct gfcc_ctx {
+  // o, v, P, D: the block sizes of the operator. IP space: o occupied, v virtual, P = o(o-1)/2 pairs.
+  // EA space (sector 1): the same layout with the roles exchanged, o = the virtual count (the pair
+  // index), v = the occupied count, P = v(v-1)/2 virtual pairs. n = o + v either way.
   int o = 0, v = 0, n = 0, P = 0, D = 0;
+  int sector = 0;   // 0: ionisation (IP), 1: electron attachment (EA)
   cudaStream_t stream = nullptr;
   int device = 0;
   gfcc_opts opts{};
@@ -302,10 +328,26 @@ void permute(const double* src, const int* dims, int nd, const int* perm, double
 void axpby(long long n, double alpha, const double* x, double beta, double* y, cudaStream_t s);
 
 // ---- hbar.cu -----------------------------------------------------------------------------------
+// Copy kind for a copy from src (host or device memory) into device memory. An explicit kind: on this
+// GPU's driver, cudaMemcpyDefault from page-locked host memory into freshly allocated device memory ran
+// at 25-37 GB/s, the explicit host-to-device kind at 208 GB/s.
+inline cudaMemcpyKind kind_to_device(const void* src) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, src) != cudaSuccess) {
+    cudaGetLastError();
+    return cudaMemcpyHostToDevice;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? cudaMemcpyDeviceToDevice
+                                                                              : cudaMemcpyHostToDevice;
+}
+
 struct HostInputs {
   const double *eps, *oooo, *ooov, *oovv, *ovov, *ovvv, *t1, *t2, *l1, *l2;
+  const double* vvvv = nullptr;   // packed [pair(a,b)][pair(c,d)] <ab||cd> (EA space only)
 };
 void build_operator(gfcc_ctx* c, const HostInputs& in);
+// hbar_ea.cu: the EA (1p + 2p1h) operator in the block layout of the IP one (see gfcc_init_ea)
+void build_operator_ea(gfcc_ctx* c, const HostInputs& in);
 
 // ---- sigma.cu ----------------------------------------------------------------------------------
 // Y = M X (+ shift*X per column) on a batch in batch-minor layout X[nu][c] (complex), c < nb,
@@ -318,6 +360,12 @@ void build_transpose_operator(gfcc_ctx* c);
 // ---- sigma_tc.cu (tcgen05 low-precision sigma for the inner solves) ---------------------------
 void build_low_precision(gfcc_ctx* c, int kind);
 void free_low_precision(gfcc_ctx* c);
+// free the per-batch buffers of the tensor-core sigma states (reallocated on demand)
+void release_sigma_batch_buffers(gfcc_ctx* c);
+// free every grow-only scratch buffer of the context (sigma batch buffers, the FP64 sigma workspace, the
+// exact-slice complex GEMM workspace) after checking the workspace's error flag; used when device memory
+// runs short for the reduced model's own buffers
+void release_scratch(gfcc_ctx* c);
 void sigma_lowprec(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, const cplx* shift, cudaStream_t s,
                    bool transpose = false);
 // the same with FP32 complex vectors (the FP32 Krylov basis of the mixed-precision solver)

@@ -256,66 +256,94 @@ __global__ void nonfinite_kernel(const double* x, long long n, int* flag) {
 
 }  // namespace
 
-void build_operator(gfcc_ctx* c, const HostInputs& in) {
-  const int o = c->o, v = c->v, P = c->P, n = c->n;
-  const long long D = c->D;
-  cudaStream_t s = c->stream;
-  ProfScope prof(PROF_INIT, 0.0, s);
+HbarCommon::HbarCommon(int o_, int v_)
+    : o(o_), v(v_), tau("ijab", {o_, o_, v_, v_}), Fme("me", {o_, v_}), Fmi("mi", {o_, o_}), Fae("ae", {v_, v_}),
+      Y("mbej", {o_, v_, v_, o_}), Wmbej("mbej", {o_, v_, v_, o_}) {}
 
+std::unique_ptr<HbarCommon> build_common(const HostInputs& in, int o, int v, cudaStream_t s) {
+  const int n = o + v;
+  auto h = std::make_unique<HbarCommon>(o, v);
   // ---- upload inputs -------------------------------------------------------------------------
-  auto up = [&](std::vector<int> dims, const double* h) {
+  auto up = [&](std::vector<int> dims, const double* src) {
     std::string lab(dims.size(), 'x');
     for (size_t k = 0; k < dims.size(); ++k) lab[k] = (char)('A' + k);
     auto t = std::make_unique<Tensor>(lab, dims);
-    GFCC_CUDA(cudaMemcpyAsync(t->p(), h, t->size() * sizeof(double), cudaMemcpyDefault, s));   // host or device
+    GFCC_CUDA(cudaMemcpyAsync(t->p(), src, t->size() * sizeof(double), kind_to_device(src), s));   // host or device
     return t;
   };
-  std::unique_ptr<Tensor> eps, v_oooo, v_ooov, v_oovv, v_ovov, v_ovvv, t1, t2, l1, l2;
   {
     ProfScope pu(PROF_UPLOAD, 0.0, s);
-    eps = up({n}, in.eps);
-    v_oooo = up({o, o, o, o}, in.oooo);
-    v_ooov = up({o, o, o, v}, in.ooov);
-    v_oovv = up({o, o, v, v}, in.oovv);
-    v_ovov = up({o, v, o, v}, in.ovov);
-    v_ovvv = up({o, v, v, v}, in.ovvv);
-    t1 = up({o, v}, in.t1);
-    t2 = up({o, o, v, v}, in.t2);
-    l1 = up({o, v}, in.l1);
-    l2 = up({o, o, v, v}, in.l2);
+    h->eps = up({n}, in.eps);
+    h->v_oooo = up({o, o, o, o}, in.oooo);
+    h->v_ooov = up({o, o, o, v}, in.ooov);
+    h->v_oovv = up({o, o, v, v}, in.oovv);
+    h->v_ovov = up({o, v, o, v}, in.ovov);
+    h->v_ovvv = up({o, v, v, v}, in.ovvv);
+    h->t1 = up({o, v}, in.t1);
+    h->t2 = up({o, o, v, v}, in.t2);
+    h->l1 = up({o, v}, in.l1);
+    h->l2 = up({o, o, v, v}, in.l2);
   }
   {  // reject non-finite inputs before any arithmetic
     DBuf<int> flag;
     flag.alloc(1);
     flag.zero(s);
-    for (Tensor* t : {eps.get(), v_oooo.get(), v_ooov.get(), v_oovv.get(), v_ovov.get(), v_ovvv.get(),
-                      t1.get(), t2.get(), l1.get(), l2.get()}) {
+    for (Tensor* t : {h->eps.get(), h->v_oooo.get(), h->v_ooov.get(), h->v_oovv.get(), h->v_ovov.get(),
+                      h->v_ovvv.get(), h->t1.get(), h->t2.get(), h->l1.get(), h->l2.get()}) {
       nonfinite_kernel<<<grid_for(t->size()), 256, 0, s>>>(t->p(), t->size(), flag.p);
       GFCC_LAUNCH_CHECK();
     }
-    int h = 0;
-    GFCC_CUDA(cudaMemcpyAsync(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int hf = 0;
+    GFCC_CUDA(cudaMemcpyAsync(&hf, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     GFCC_CUDA(cudaStreamSynchronize(s));
-    GFCC_CHECK(h == 0, GFCC_ERR_NONFINITE, "gfcc_init: non-finite value in the inputs");
+    GFCC_CHECK(hf == 0, GFCC_ERR_NONFINITE, "gfcc_init: non-finite value in the inputs");
   }
+  Tensor *t1 = h->t1.get(), *t2 = h->t2.get(), *v_oovv = h->v_oovv.get(), *v_ooov = h->v_ooov.get();
+  Tensor *v_ovvv = h->v_ovvv.get(), *v_ovov = h->v_ovov.get();
+  Tensor &tau = h->tau, &Fme = h->Fme, &Fmi = h->Fmi, &Fae = h->Fae, &Y = h->Y, &Wmbej = h->Wmbej;
 
   // tau_ij^ab = t_ij^ab + t_i^a t_j^b - t_i^b t_j^a
-  Tensor tau("ijab", {o, o, v, v});
   perm(t2->as("ijab"), 1.0, 0.0, tau.as("ijab"), s);
   contract(1.0, t1->as("ia"), t1->as("jb"), 1.0, tau.as("ijab"), s);
   contract(-1.0, t1->as("ib"), t1->as("ja"), 1.0, tau.as("ijab"), s);
 
   // one-body elements
-  Tensor Fme("me", {o, v}), Fmi("mi", {o, o}), Fae("ae", {v, v});
   contract(1.0, t1->as("nf"), v_oovv->as("mnef"), 0.0, Fme.as("me"), s);
   contract(1.0, t1->as("ne"), v_ooov->as("mnie"), 0.0, Fmi.as("mi"), s);
   contract(0.5, tau.as("inef"), v_oovv->as("mnef"), 1.0, Fmi.as("mi"), s);
-  add_diag_kernel<<<(o + 255) / 256, 256, 0, s>>>(Fmi.p(), o, eps->p(), 1.0);
+  add_diag_kernel<<<(o + 255) / 256, 256, 0, s>>>(Fmi.p(), o, h->eps->p(), 1.0);
   GFCC_LAUNCH_CHECK();
   contract(-1.0, t1->as("mf"), v_ovvv->as("maef"), 0.0, Fae.as("ae"), s);      // <am||ef> = -<ma||ef>
   contract(-0.5, tau.as("mnaf"), v_oovv->as("mnef"), 1.0, Fae.as("ae"), s);
-  add_diag_kernel<<<(v + 255) / 256, 256, 0, s>>>(Fae.p(), v, eps->p() + o, 1.0);
+  add_diag_kernel<<<(v + 255) / 256, 256, 0, s>>>(Fae.p(), v, h->eps->p() + o, 1.0);
   GFCC_LAUNCH_CHECK();
+
+  // Y_mbej = t_jn^fb <mn||ef>  (shared by W_mbej, W_mbij and W_abej)
+  contract(1.0, t2->as("jnfb"), v_oovv->as("mnef"), 0.0, Y.as("mbej"), s);
+
+  // W_mbej = <mb||ej> + t_j^f <mb||ef> - t_n^b <mn||ej> - Y - t_j^f t_n^b <mn||ef>
+  perm(v_ovov->as("mbje"), -1.0, 0.0, Wmbej.as("mbej"), s);                    // <mb||ej> = -<mb||je>
+  contract(1.0, t1->as("jf"), v_ovvv->as("mbef"), 1.0, Wmbej.as("mbej"), s);
+  contract(1.0, t1->as("nb"), v_ooov->as("mnje"), 1.0, Wmbej.as("mbej"), s);   // <mn||ej> = -<mn||je>
+  perm(Y.as("mbej"), -1.0, 1.0, Wmbej.as("mbej"), s);
+  {
+    Tensor tmp("mnej", {o, o, v, o});
+    contract(1.0, t1->as("jf"), v_oovv->as("mnef"), 0.0, tmp.as("mnej"), s);
+    contract(-1.0, t1->as("nb"), tmp.as("mnej"), 1.0, Wmbej.as("mbej"), s);
+  }
+  return h;
+}
+
+void build_operator(gfcc_ctx* c, const HostInputs& in) {
+  const int o = c->o, v = c->v, P = c->P, n = c->n;
+  const long long D = c->D;
+  cudaStream_t s = c->stream;
+  ProfScope prof(PROF_INIT, 0.0, s);
+  std::unique_ptr<HbarCommon> hc = build_common(in, o, v, s);
+  Tensor *t1 = hc->t1.get(), *t2 = hc->t2.get(), *l1 = hc->l1.get(), *l2 = hc->l2.get();
+  Tensor *v_oooo = hc->v_oooo.get(), *v_ooov = hc->v_ooov.get(), *v_oovv = hc->v_oovv.get();
+  Tensor *v_ovov = hc->v_ovov.get(), *v_ovvv = hc->v_ovvv.get();
+  Tensor &tau = hc->tau, &Fme = hc->Fme, &Fmi = hc->Fmi, &Fae = hc->Fae, &Y = hc->Y, &Wmbej = hc->Wmbej;
 
   // W_mnij
   Tensor Wmnij("mnij", {o, o, o, o});
@@ -328,22 +356,6 @@ void build_operator(gfcc_ctx* c, const HostInputs& in) {
   Tensor Wmnie("mnie", {o, o, o, v});
   perm(v_ooov->as("mnie"), 1.0, 0.0, Wmnie.as("mnie"), s);
   contract(1.0, t1->as("if"), v_oovv->as("mnfe"), 1.0, Wmnie.as("mnie"), s);
-
-  // Y_mbej = t_jn^fb <mn||ef>  (shared by W_mbej and W_mbij)
-  Tensor Y("mbej", {o, v, v, o});
-  contract(1.0, t2->as("jnfb"), v_oovv->as("mnef"), 0.0, Y.as("mbej"), s);
-
-  // W_mbej = <mb||ej> + t_j^f <mb||ef> - t_n^b <mn||ej> - Y - t_j^f t_n^b <mn||ef>
-  Tensor Wmbej("mbej", {o, v, v, o});
-  perm(v_ovov->as("mbje"), -1.0, 0.0, Wmbej.as("mbej"), s);                    // <mb||ej> = -<mb||je>
-  contract(1.0, t1->as("jf"), v_ovvv->as("mbef"), 1.0, Wmbej.as("mbej"), s);
-  contract(1.0, t1->as("nb"), v_ooov->as("mnje"), 1.0, Wmbej.as("mbej"), s);   // <mn||ej> = -<mn||je>
-  perm(Y.as("mbej"), -1.0, 1.0, Wmbej.as("mbej"), s);
-  {
-    Tensor tmp("mnej", {o, o, v, o});
-    contract(1.0, t1->as("jf"), v_oovv->as("mnef"), 0.0, tmp.as("mnej"), s);
-    contract(-1.0, t1->as("nb"), tmp.as("mnej"), 1.0, Wmbej.as("mbej"), s);
-  }
 
   // W_mbij
   Tensor Wmbij("mbij", {o, v, o, o});

@@ -943,11 +943,43 @@ std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cp
 
 }  // namespace
 
+// New column capacity of a model buffer that must hold `need` columns: doubling (few regrowths), unless the
+// doubled buffers (bytes_per_col per column) would take more than half of the free device memory, in
+// which case it grows to what is needed, rounded up to `quantum` (the old buffer is still held while the
+// columns are copied, and large models at the biggest sizes are limited by memory, not by regrowths).
+static int grown_capacity(gfcc_ctx* c, int cap_now, int need, int quantum, double bytes_per_col) {
+  int cap = std::max(need, std::max(quantum, 2 * cap_now));
+  size_t freeb = 0, totalb = 0;
+  if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) {
+    cudaGetLastError();
+    return cap;
+  }
+  if ((double)cap * bytes_per_col > 0.5 * (double)freeb) {
+    // memory is short: give back the scratch buffers first (they regrow on demand), then size exactly
+    release_scratch(c);
+    if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) cudaGetLastError();
+    if ((double)cap * bytes_per_col > 0.5 * (double)freeb)
+      cap = std::max(need, ((need + quantum - 1) / quantum) * quantum);
+  }
+  return cap;
+}
+
+void release_scratch(gfcc_ctx* c) {
+  GFCC_CUDA(cudaStreamSynchronize(c->stream));
+  release_sigma_batch_buffers(c);
+  c->ws.ut.release();
+  c->ws.ct.release();
+  c->ws.xe.release();
+  c->ws.nb_cap = 0;
+  zgemm_work_check(c);
+  zgemm_work_free(c);
+}
+
 static void grow_model(gfcc_ctx* c, int need) {
   MorState& ms = c->mor;
   if (need <= ms.m_cap) return;
   const int np = (int)ms.porb.size(), nq = (int)ms.qorb.size();
-  const int cap = std::max(need, std::max(64, 2 * ms.m_cap));
+  const int cap = grown_capacity(c, ms.m_cap, need, 64, 2.0 * (double)c->D * sizeof(cplx));   // S and Z
   cudaStream_t s = c->stream;
   regrow_rows(ms.S, c->D, ms.m_cap, cap, ms.m, s);
   regrow_rows(ms.Z, c->D, ms.m_cap, cap, ms.m, s);
@@ -963,7 +995,7 @@ static void grow_basis(gfcc_ctx* c, int need) {
   MorState& ms = c->mor;
   if (need <= ms.q_cap) return;
   const int np = (int)ms.porb.size();
-  const int cap = std::max(need, std::max(128, 2 * ms.q_cap));
+  const int cap = grown_capacity(c, ms.q_cap, need, 128, (double)c->D * sizeof(cplx));
   cudaStream_t s = c->stream;
   regrow_rows(ms.Q, c->D, ms.q_cap, cap, ms.qn, s);
   regrow_cm(ms.RS, ms.q_cap, cap, std::max(ms.m_cap, 1), ms.qn, ms.m, s);

@@ -31,9 +31,20 @@ bool take_event(cudaEvent_t* e) {
   *e = g_pool[g_used++];
   return true;
 }
+std::atomic<bool> g_alloc_on{false};
+long long g_alloc_n[2] = {0, 0};
+double g_alloc_ms[2] = {0.0, 0.0};
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+bool alloc_profiling() { return g_alloc_on.load(std::memory_order_relaxed); }
+void note_alloc(int cls, double ms) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  const int k = cls == PROF_FREE ? 1 : 0;
+  ++g_alloc_n[k];
+  g_alloc_ms[k] += ms;
+}
 
 ProfScope::ProfScope(int c, double f, cudaStream_t st) : cls(c), flops(f), s(st) {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -72,12 +83,22 @@ int gfcc_profile(int enable) {
   gfcc::g_recs.clear();
   gfcc::g_used = 0;
   gfcc::g_on = enable != 0;
+  gfcc::g_alloc_n[0] = gfcc::g_alloc_n[1] = 0;
+  gfcc::g_alloc_ms[0] = gfcc::g_alloc_ms[1] = 0.0;
+  gfcc::g_alloc_on.store(enable != 0);
   return GFCC_OK;
 }
 
 int gfcc_profile_read(int cls, long long* launches, double* ms, double* flops) {
   if (cls < 0 || cls >= gfcc::PROF_NCLASS) return GFCC_ERR_ARG;
   std::lock_guard<std::mutex> lk(gfcc::g_mu);
+  if (cls == gfcc::PROF_ALLOC || cls == gfcc::PROF_FREE) {   // host-side counts, no events
+    const int k = cls == gfcc::PROF_FREE ? 1 : 0;
+    if (launches) *launches = gfcc::g_alloc_n[k];
+    if (ms) *ms = gfcc::g_alloc_ms[k];
+    if (flops) *flops = 0.0;
+    return GFCC_OK;
+  }
   long long n = 0;
   double t = 0.0, f = 0.0;
   for (auto& r : gfcc::g_recs) {

@@ -114,7 +114,11 @@ void sigma_batch(gfcc_ctx* c, const cplx* X, cplx* Y, int nb, int ldb, const cpl
   GFCC_CHECK(ldb == nb, GFCC_ERR_ARG, "sigma_batch: internal layout needs ldb == nb");
   if (nb == 0) return;
   const bool lowp = precision == GFCC_PREC_TF32 || precision == GFCC_PREC_BF16;
-  ProfScope prof(lowp ? PROF_SIGMA_LP : PROF_SIGMA_EX, 0.0, s);
+  // algorithmic flops of the sigma on nb complex columns (ring, oooo, three-body and coupling terms; the
+  // method's flops, whatever arithmetic carries them out)
+  const double fo = c->o, fv = c->v, fP = c->P;
+  const double flops = 2.0 * nb * (2.0 * fo * fv * fo * fv * fo + 2.0 * fP * fP * fv + 4.0 * fP * fv * fv + 4.0 * fo * fP * fv);
+  ProfScope prof(lowp ? PROF_SIGMA_LP : PROF_SIGMA_EX, flops, s);
   if (precision == GFCC_PREC_FP64_TC) {
     sigma_emulated(c, X, Y, nb, shift, s, transpose);
     return;

@@ -335,6 +335,29 @@ void free_low_precision(gfcc_ctx* c) {
   c->lp.emuT = nullptr;
 }
 
+// Free the per-batch buffers of the low-precision and exact-slice states (both actions): they are
+// allocated again, at the size needed, by the next sigma. The operands and the error flags stay.
+void release_sigma_batch_buffers(gfcc_ctx* c) {
+  for (bool tr : {false, true}) {
+    if (LpState* st = lp_state(c, tr)) {
+      for (DBuf<uint8_t>* b : {&st->Bring, &st->Boo, &st->Bup, &st->Bdn}) b->release();
+      for (DBuf<float>* b : {&st->CT, &st->C2, &st->up_part, &st->up}) b->release();
+      st->nb_cap = 0;
+    }
+    if (EmuState* st = emu_state(c, tr)) {
+      for (DBuf<double>* b : {&st->stage, &st->CT, &st->C2, &st->up}) b->release();
+      for (SlicedRows* r : {&st->Bring, &st->Boo, &st->Bup, &st->Bdn}) {
+        r->slices.release();
+        r->expo.release();
+      }
+      st->Xc.release();
+      st->Yc.release();
+      st->work.islabs.release();
+      st->work.acc.release();
+    }
+  }
+}
+
 static void build_emulated(gfcc_ctx* c, bool transpose) {
   if (transpose ? c->lp.emuT : c->lp.emu) return;
   const int o = c->o, v = c->v, P = c->P;
@@ -572,7 +595,9 @@ void sigma_lowprec_f32(gfcc_ctx* c, const cuFloatComplex* X, cuFloatComplex* Y, 
                        cudaStream_t s, bool transpose) {
   LpState* st = transpose ? lp_state_transposed(c) : lp_state(c);
   GFCC_CHECK(st != nullptr, GFCC_ERR_STATE, "low-precision operator not built");
-  ProfScope prof(PROF_SIGMA_LP, 0.0, s);
+  const double fo = c->o, fv = c->v, fP = c->P;   // algorithmic flops, as in sigma_batch
+  ProfScope prof(PROF_SIGMA_LP,
+                 2.0 * nb * (2.0 * fo * fv * fo * fv * fo + 2.0 * fP * fP * fv + 4.0 * fP * fv * fv + 4.0 * fo * fP * fv), s);
   const double* A11 = op_view(c, transpose).A11;
   if (st->kind == TcKind::BF16) sigma_lp_impl<TcKind::BF16, cuFloatComplex>(c, *st, X, Y, nb, shift, s, A11);
   else sigma_lp_impl<TcKind::TF32, cuFloatComplex>(c, *st, X, Y, nb, shift, s, A11);

@@ -48,6 +48,9 @@ PROTOTYPES = {
     "gfcc_default_opts": (C.c_int, [C.POINTER(Opts)]),
     "gfcc_init": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, _vp, C.POINTER(VBlocks), _vp, _vp, _vp, _vp,
                             C.POINTER(Opts), _vp]),
+    "gfcc_init_ea": (C.c_int, [C.POINTER(_vp), C.c_int, C.c_int, _vp, C.POINTER(VBlocks), _vp, _vp, _vp, _vp,
+                               _vp, C.POINTER(Opts), _vp]),
+    "gfcc_sector": (C.c_int, [_vp, _ip]),
     "gfcc_dim": (C.c_int, [_vp, _ip]),
     "gfcc_set_opts": (C.c_int, [_vp, C.POINTER(Opts)]),
     "gfcc_sigma": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int]),
@@ -244,15 +247,23 @@ class SolveStats:
 
 
 class Context:
-    """One GFCC problem on the current CUDA device (wraps gfcc_t)."""
+    """One GFCC problem on the current CUDA device (wraps gfcc_t).
+
+    sector="ip" (default): the ionisation half over the 1h + 2h1p space (gfcc_init).
+    sector="ea": the electron-attachment half over the 1p + 2p1h space (gfcc_init_ea); ``vvvv`` is the
+    packed [V][V] virtual block (default: ``inputs.vvvv_pairs()``). Frequencies are the physical w; the
+    G arrays are indexed [w][free-term orbital q][left-vector orbital p] (G^EA_pq)."""
 
     def __init__(self, inputs, tol=1e-8, restart=30, max_restarts=200, precision="fp64", max_batch=0,
                  drop_tol=1e-10, stream=None, residual_precision=None, deriv_indicator=False, mor_guess=True,
-                 verbose=False):
+                 verbose=False, sector="ip", vvvv=None):
         lib = load()
         self._lib = lib
         o, v = inputs.o, inputs.v
         self.o, self.v = o, v
+        if sector not in ("ip", "ea"):
+            raise ValueError("sector must be 'ip' or 'ea'")
+        self.sector = sector
         opts = Opts()
         lib.gfcc_default_opts(C.byref(opts))
         opts.tol, opts.restart, opts.max_restarts = tol, restart, max_restarts
@@ -267,8 +278,14 @@ class Context:
         eps, oooo, ooov, oovv, ovov, ovvv, t1, t2, l1, l2 = self._keep
         vb = VBlocks(_ptr(oooo), _ptr(ooov), _ptr(oovv), _ptr(ovov), _ptr(ovvv))
         h = C.c_void_p()
-        rc = lib.gfcc_init(C.byref(h), o, v, _ptr(eps), C.byref(vb), _ptr(t1), _ptr(t2), _ptr(l1), _ptr(l2),
-                           C.byref(opts), stream)
+        if sector == "ip":
+            rc = lib.gfcc_init(C.byref(h), o, v, _ptr(eps), C.byref(vb), _ptr(t1), _ptr(t2), _ptr(l1), _ptr(l2),
+                               C.byref(opts), stream)
+        else:
+            vp = _c64(inputs.vvvv_pairs() if vvvv is None else vvvv)
+            self._keep.append(vp)
+            rc = lib.gfcc_init_ea(C.byref(h), o, v, _ptr(eps), C.byref(vb), _ptr(vp), _ptr(t1), _ptr(t2), _ptr(l1),
+                                  _ptr(l2), C.byref(opts), stream)
         if rc != 0:
             raise GfccError(rc, "gfcc_init failed")
         self._h = h

@@ -277,11 +277,16 @@ def omega_grid(wmin: float, wmax: float, n: int) -> np.ndarray:
 
 # Named workloads: (o, v, seed, omega window, n_omega, eta). Sizes follow the molecules the
 # method was applied to (CO/cc-pVDZ, butadiene, benzene, adenine) and a tiny brute-force case.
+# The attachment window [ea_wmin, ea_wmax] covers the lower part of the virtual orbital energies
+# (drawn on [0.1, 2.0] Ha) and the lowest 2p1h satellites.
 WORKLOADS = {
-    "tiny_o4_v8": dict(o=4, v=8, seed=1001, wmin=-1.0, wmax=0.0, nw=200, eta=0.01),
-    "co_o14_v42": dict(o=14, v=42, seed=1002, wmin=-1.2, wmax=-0.3, nw=500, eta=0.01),
-    "butadiene_o30_v130": dict(o=30, v=130, seed=1003, wmin=-1.0, wmax=-0.2, nw=1000, eta=0.005),
-    "benzene_o42_v186": dict(o=42, v=186, seed=1004, wmin=-1.0, wmax=-0.2, nw=5000, eta=0.01),
-    "adenine_o70_v250": dict(o=70, v=250, seed=1005, wmin=-0.8, wmax=-0.2, nw=2000, eta=0.01),
+    "tiny_o4_v8": dict(o=4, v=8, seed=1001, wmin=-1.0, wmax=0.0, nw=200, eta=0.01, ea_wmin=0.1, ea_wmax=1.1),
+    "co_o14_v42": dict(o=14, v=42, seed=1002, wmin=-1.2, wmax=-0.3, nw=500, eta=0.01, ea_wmin=0.1, ea_wmax=1.0),
+    "butadiene_o30_v130": dict(o=30, v=130, seed=1003, wmin=-1.0, wmax=-0.2, nw=1000, eta=0.005,
+                               ea_wmin=0.1, ea_wmax=0.9),
+    "benzene_o42_v186": dict(o=42, v=186, seed=1004, wmin=-1.0, wmax=-0.2, nw=5000, eta=0.01,
+                             ea_wmin=0.1, ea_wmax=0.9),
+    "adenine_o70_v250": dict(o=70, v=250, seed=1005, wmin=-0.8, wmax=-0.2, nw=2000, eta=0.01,
+                             ea_wmin=0.1, ea_wmax=0.7),
 }
 

@@ -1,0 +1,158 @@
+"""Electron-attachment (1p + 2p1h) half of G on the GPU against the FP64 oracle (needs a GB300).
+
+The GPU scatters the EA operator into the block layout of the IP one and solves the IP form of the
+systems at negated frequencies; every expected value here comes from ``oracle.ea`` (pinned against the
+brute-force N+1 sector), the oracle's dense LU or GMRES, and the oracle's reduced model run on the IP
+form of the same systems. Tolerances as in the IP parity tests.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ea, mor
+from oracle import solve as sv
+
+from gpu_util import inputs, need_gpu, random_vectors, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return need_gpu()
+
+
+def ctx_for(inp, **kw):
+    from paper_1902_06016_gb300 import Context
+    return Context(inp, sector="ea", **kw)
+
+
+@pytest.mark.parametrize("o,v,seed", [(1, 3, 7), (3, 6, 101), (4, 8, 1001), (7, 13, 103)])
+def test_ea_vectors_and_sigma_match_oracle(torch, o, v, seed):
+    inp = inputs(o, v, seed)
+    hb = ea.build(inp)
+    ctx = ctx_for(inp)
+    assert ctx.D == ea.dim(o, v)
+    n = o + v
+    assert rel_err(ctx.vectors(range(n)), ea.b_vectors(inp)) <= 1e-13
+    assert rel_err(ctx.vectors(range(n), left=True), ea.c_vectors(inp)) <= 1e-13
+    X = random_vectors(ctx.D, 37, seed + 5)
+    Yo = ea.sigma(hb, X)
+    assert rel_err(ctx.sigma(X), Yo) <= 1e-12
+    Y = ctx.sigma(X, precision="fp64_tc")
+    for k in range(0, 37, 6):
+        assert np.abs(Y[k] - Yo[k]).max() <= 1e-12 * np.abs(Yo[k]).max()
+    err = rel_err(ctx.sigma(X, precision="tf32"), Yo)
+    assert 1e-9 < err < 2.0 ** -12, err
+    M = ea.dense_matrix(hb)
+    assert rel_err(ctx.sigma(X, transpose=True), X @ M) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tf32", "fp64_tc"])
+def test_ea_full_solve_matches_dense(torch, precision):
+    """All n orbitals as free terms and left vectors, 6 frequencies in [0.1, 0.9] Ha: G^EA and A
+    against dense LU of (w + i eta - M) y = b. (Higher in this case's spectrum the poles crowd and
+    GMRES(30) stagnates, on the oracle as on the GPU; GMRES(60) here.)"""
+    inp = inputs(4, 8, 1001)
+    hb = ea.build(inp)
+    M = ea.dense_matrix(hb)
+    n = 12
+    ws = np.linspace(0.1, 0.9, 6)
+    eta = 0.01
+    ctx = ctx_for(inp, tol=1e-11, precision=precision, restart=60)
+    r = ctx.solve_full(ws, eta, list(range(n)))
+    assert r["converged"]
+    Go = ea.green(ea.c_vectors(inp), ea.dense_solve(M, ea.b_vectors(inp), ws, eta))     # [w, p, q]
+    assert rel_err(r["G"], Go.transpose(0, 2, 1)) <= 1e-8
+    A_o = -np.imag(np.einsum("wpp->w", Go)) / np.pi
+    assert rel_err(r["A"], A_o) <= 1e-8
+    assert A_o.max() > 0.0                      # attachment peaks are positive with + i eta
+
+
+def test_ea_mor_matches_oracle_ip_form(torch):
+    """Reduced model from 3 seeds refined to 1e-6 on [0.1, 0.9] Ha (201 points): the same sampled
+    frequencies, model order and Ghat as the oracle's reduced model on the IP form (-b, frequencies -w)."""
+    inp = inputs(4, 8, 1001)
+    hb = ea.build(inp)
+    M = ea.dense_matrix(hb)
+    orb = list(range(12))
+    eta, tol = 0.01, 1e-6
+    ctx = ctx_for(inp, tol=1e-11, precision="tf32", restart=60)
+    seeds = np.linspace(0.1, 0.9, 3)
+    ctx.mor_build(seeds, eta, orb)
+    res = ctx.mor_refine(0.1, 0.9, 201, tol, 10 ** 6)
+    assert res["converged"]
+    Bp, Cp = ea.ip_form(inp, hb, orb, orb)
+    orc = mor.build_and_refine(hb, Bp, Cp, -seeds, -0.9, -0.1, 201, eta, tol, 10 ** 6, solver="dense", M=M)
+    info = ctx.mor_info()
+    assert np.array_equal(np.sort(info["sampled"]), np.sort(-np.array(orc.sampled)))
+    assert info["m"] == orc.model.m
+    grid = np.linspace(0.1, 0.9, 61)
+    ev = ctx.mor_eval(grid)
+    assert rel_err(ev["G"], mor.reduced_green(orc.model, -grid, eta)) <= 1e-8
+    Go = ea.green(ea.c_vectors(inp), ea.dense_solve(M, ea.b_vectors(inp), grid, eta))
+    A_o = -np.imag(np.einsum("wpp->w", Go)) / np.pi
+    assert np.abs(ev["A"] - A_o).max() <= 10 * tol * np.abs(A_o).max()
+
+
+def test_ea_derivatives_match_finite_differences(torch):
+    inp = inputs(3, 6, 101)
+    M = ea.dense_matrix(ea.build(inp))
+    B, C = ea.b_vectors(inp), ea.c_vectors(inp)
+    ws = np.array([0.4, 0.9])
+    eta, h = 0.02, 1e-5
+    ctx = ctx_for(inp, tol=1e-12)
+    Gg, dwg, deg = ctx.green_derivatives(ws, eta, list(range(9)))
+    G = lambda w, e: ea.green(C, ea.dense_solve(M, B, w, e)).transpose(0, 2, 1)  # noqa: E731
+    dw = (G(ws + h, eta) - G(ws - h, eta)) / (2 * h)
+    de = (G(ws, eta + h) - G(ws, eta - h)) / (2 * h)
+    assert rel_err(Gg, G(ws, eta)) <= 1e-10
+    assert rel_err(dwg, dw) <= 1e-6
+    assert rel_err(deg, de) <= 1e-6
+
+
+def test_ea_context_state(torch, tmp_path):
+    """The sector is reported; the T2 gradient is IP-only; a saved EA model reloads into an EA context and
+    not into an IP context of the same block sizes (o and v exchanged)."""
+    from paper_1902_06016_gb300 import Context, GfccError
+    inp = inputs(3, 5, 77)
+    ctx = ctx_for(inp, tol=1e-11)
+    assert ctx.sector == "ea"
+    with pytest.raises(GfccError):
+        ctx.green_grad_t2([0.5], 0.01, [0], np.ones((1, 1, 1), dtype=complex))
+    ctx.mor_build([0.3, 0.8, 1.3], 0.01, list(range(8)))
+    ev = ctx.mor_eval([0.55, 1.05])["G"]
+    path = str(tmp_path / "ea.mor")
+    ctx.mor_save(path)
+    ctx2 = ctx_for(inp, tol=1e-11)
+    ctx2.mor_load(path)
+    assert np.array_equal(ctx2.mor_eval([0.55, 1.05])["G"], ev)
+    assert np.allclose(np.sort(ctx2.mor_info()["sampled"]), [0.3, 0.8, 1.3])
+    swapped = synth.make_inputs(5, 3, 78)          # IP space with the same block sizes (o = 5, v = 3)
+    ip = Context(swapped, tol=1e-11)
+    assert ip.D == ctx.D
+    with pytest.raises(GfccError):
+        ip.mor_load(path)
+
+
+def test_ea_co_size_matches_oracle_gmres(torch):
+    """CO size (o = 14, v = 42; EA dimension D = 12,096): sigma on random vectors, and G^EA at w = 0.35 Ha
+    for two free terms (one virtual, one occupied orbital) against oracle GMRES(60) (about 30 s)."""
+    W = synth.WORKLOADS["co_o14_v42"]
+    inp = synth.make_inputs(W["o"], W["v"], W["seed"])
+    hb = ea.build(inp)
+    ctx = ctx_for(inp, tol=1e-10, precision="tf32", restart=60)
+    X = random_vectors(ctx.D, 6, 11)
+    Yo = ea.sigma(hb, X)
+    Y = ctx.sigma(X, precision="fp64_tc")
+    for k in range(6):
+        assert np.abs(Y[k] - Yo[k]).max() <= 1e-12 * np.abs(Yo[k]).max()
+    qs = [W["o"] + 3, 5]
+    ws = np.array([0.35])
+    Bp, Cp = ea.ip_form(inp, hb, qs, list(range(inp.n)))
+    Y, res = sv.gmres_solve(hb, Bp, -ws, W["eta"], tol=1e-10, restart=60)
+    assert res.max() <= 1e-10
+    Go = sv.green(Cp, Y)                                   # [w, q, p]
+    r = ctx.solve_full(ws, W["eta"], qs, qorb=list(range(inp.n)))
+    assert r["converged"]
+    assert rel_err(r["G"], Go) <= 1e-8
