@@ -312,6 +312,15 @@ int gfcc_tc_gemm_noalloc(int precision, const double* A, const double* B, int M,
 int gfcc_autotune_info(int i, int* kind, int* exact, int* tiles_m, int* tiles_n_log2, int* gm, int* gm_default,
                        double* ms_best, double* ms_default);
 
+/* Device memory. The library's buffers come from a stream-ordered memory pool of its own on each
+ * device (cudaMallocFromPoolAsync / cudaFreeAsync on the context's stream), which keeps the memory it
+ * has reserved when buffers are freed: frees do not wait for the device, and a context created after
+ * another one was freed reuses its memory. A context should therefore be freed (gfcc_free) before the
+ * stream it was created with is destroyed. This call waits for every device the library has used and
+ * returns the pools' unused reserve to the device, for callers that need that memory elsewhere.
+ * GFCC_ERR_CUDA if a device reports an error. The paper has no counterpart. */
+int gfcc_release_cached_memory(void);
+
 /* Number of CUDA kernels launched by this library since it was loaded (all contexts). */
 long long gfcc_launch_count(void);
 
@@ -334,7 +343,9 @@ long long gfcc_launch_count(void);
  * 27 the copies of the caller's inputs to the device in gfcc_init; 28 the copies of results into the
  * caller's output buffers (device to host for host buffers); 29 and 30 the library's device
  * allocations and frees: their count and the host milliseconds spent inside cudaMalloc and cudaFree
- * (host clock, not events; cudaFree also waits for the device).
+ * (host clock, not events; cudaFree also waits for the device); 31 the up, oooo and down GEMMs of the
+ * low-precision sigma again (also in class 0), with their algorithmic HBM bytes in the "flops" field
+ * (operands read once, outputs written once, the accumulated down output read and written).
  * Events are recorded on the stream each region is launched on. */
 int gfcc_profile(int enable);
 

@@ -32,8 +32,8 @@ void copy_out(void* dst, const void* src_dev, size_t n, cudaStream_t s) {
 
 int choose_batch(gfcc_ctx* c, long long ncols) {
   if (c->opts.max_batch > 0) return (int)std::min<long long>(ncols, c->opts.max_batch);
-  size_t freeb = 0, totalb = 0;
-  if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) { cudaGetLastError(); freeb = 8ull << 30; }
+  size_t freeb = gfcc::device_free_bytes();
+  if (freeb == 0) freeb = 8ull << 30;
   const long long D = c->D, ov = (long long)c->o * c->v;
   const long long per_col = (long long)sizeof(cplx) * (D * (c->opts.restart + 10)) + 16LL * ov * c->o * 2 + 4096;
   long long nb = (long long)(0.5 * (double)freeb) / per_col;
@@ -271,10 +271,13 @@ void mor_add_frequencies(gfcc_ctx* c, const std::vector<double>& ws) {
   // quarter of the free device memory; the chunks keep the frequency order, so the columns reach the
   // subspace in the same order as in one piece
   size_t freeb = 0, totalb = 0;
-  if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) { cudaGetLastError(); freeb = 16ull << 30; }
+  if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) { cudaGetLastError(); totalb = 0; }
+  freeb = gfcc::device_free_bytes();
+  if (freeb == 0) freeb = 16ull << 30;
   if (freeb < totalb / 3) {   // scratch of earlier calls (e.g. adjoint solves) holds much of the device
     gfcc::release_scratch(c);
-    if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) { cudaGetLastError(); freeb = 16ull << 30; }
+    freeb = gfcc::device_free_bytes();
+    if (freeb == 0) freeb = 16ull << 30;
   }
   const long long per_w = (long long)c->D * (long long)c->mor.porb.size() * (long long)sizeof(cplx) * 14;
   const size_t per_chunk = (size_t)std::max<long long>(1, (long long)(0.25 * (double)freeb) / std::max(per_w, 1LL));
@@ -501,7 +504,8 @@ __global__ void max_into_kernel(const double* __restrict__ x, double* __restrict
 
 }  // namespace
 
-#define API_BEGIN \
+#define API_BEGIN                                                  \
+  gfcc::StreamScope api_stream_scope_(c ? c->stream : nullptr);   \
   try {
 #define API_END(ctx)                                                   \
   }                                                                    \
@@ -575,6 +579,7 @@ static int init_context(gfcc_t* out, int sector, int o, int v, const double* eps
   int rc = check_opts(&c->opts, why);
   if (rc != GFCC_OK) { delete c; return rc; }
   int status = GFCC_OK;
+  gfcc::StreamScope stream_scope(c->stream);
   try {
     GFCC_CUDA(cudaGetDevice(&c->device));
     gfcc::HostInputs in{eps, vb->oooo, vb->ooov, vb->oovv, vb->ovov, vb->ovvv, t1, t2, l1, l2};
@@ -1358,6 +1363,7 @@ int gfcc_spectral(const double* G, int nw, const int* orbitals, int np, const in
                   int adjoint, void* stream) {
   if (nw < 0 || np < 1 || !orbitals || (qorb && nq < 1) || !G || !A) return GFCC_ERR_ARG;
   if (nw == 0) return GFCC_OK;
+  gfcc::StreamScope stream_scope(reinterpret_cast<cudaStream_t>(stream));
   try {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     std::vector<int> porb(orbitals, orbitals + np);
@@ -1393,7 +1399,11 @@ int gfcc_spectral(const double* G, int nw, const int* orbitals, int np, const in
 
 const char* gfcc_last_error(gfcc_t c) { return c ? c->last_error.c_str() : "null context"; }
 
-void gfcc_free(gfcc_t c) { delete c; }
+void gfcc_free(gfcc_t c) {
+  if (!c) return;
+  gfcc::StreamScope stream_scope(c->stream);   // the context's buffers return to the pool in its stream's order
+  delete c;
+}
 
 }  // extern "C"
 

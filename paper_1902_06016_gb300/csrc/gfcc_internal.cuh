@@ -72,9 +72,10 @@ enum ProfClass {
   PROF_LP_COMBINE = 26,       // the combine pass of the low-precision sigma (up reduction, final sum)
   PROF_UPLOAD = 27,           // copies of the caller's inputs to the device in gfcc_init
   PROF_DOWNLOAD = 28,         // copies of results into the caller's output buffers
-  PROF_ALLOC = 29,            // device allocations of the library's buffers (host time inside cudaMalloc)
-  PROF_FREE = 30,             // device frees of the library's buffers (host time inside cudaFree)
-  PROF_NCLASS = 31
+  PROF_ALLOC = 29,            // device allocations of the library's buffers (host time of each allocation)
+  PROF_FREE = 30,             // device frees of the library's buffers (host time of each free)
+  PROF_LP_SMALL_GEMMS = 31,   // the up, oooo and down GEMMs of the low-precision sigma (algorithmic bytes)
+  PROF_NCLASS = 32
 };
 struct ProfScope {   // records CUDA events around one launch on stream s when profiling is on
   int cls;
@@ -91,6 +92,22 @@ struct ProfScope {   // records CUDA events around one launch on stream s when p
 // host-side accounting of device allocations and frees while profiling is on (classes 29, 30)
 bool alloc_profiling();
 void note_alloc(int cls, double ms);
+
+// Device memory (memory.cu): a stream-ordered pool per device that keeps its reserve. Allocations
+// and frees are ordered on the stream of the innermost StreamScope of the calling thread (each
+// entry point opens one with its context's stream); device_free_bytes() is the device's free memory
+// plus the pool's unused reserve.
+cudaStream_t current_alloc_stream();
+struct StreamScope {
+  cudaStream_t prev;
+  explicit StreamScope(cudaStream_t s);
+  ~StreamScope();
+  StreamScope(const StreamScope&) = delete;
+  StreamScope& operator=(const StreamScope&) = delete;
+};
+cudaError_t pool_alloc(void** p, size_t bytes);
+void pool_free(void* p);
+size_t device_free_bytes();
 
 template <typename T>
 struct DBuf {
@@ -113,10 +130,10 @@ struct DBuf {
     if (p) {
       if (alloc_profiling()) {
         const auto t0 = std::chrono::steady_clock::now();
-        cudaFree(p);
+        pool_free(p);
         note_alloc(PROF_FREE, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
       } else {
-        cudaFree(p);
+        pool_free(p);
       }
     }
     p = nullptr;
@@ -127,17 +144,20 @@ struct DBuf {
     release();
     if (count == 0) return;
     cudaError_t e;
+    void* q = nullptr;
     if (alloc_profiling()) {
       const auto t0 = std::chrono::steady_clock::now();
-      e = cudaMalloc(&p, count * sizeof(T));
+      e = pool_alloc(&q, count * sizeof(T));
       note_alloc(PROF_ALLOC, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
     } else {
-      e = cudaMalloc(&p, count * sizeof(T));
+      e = pool_alloc(&q, count * sizeof(T));
     }
     if (e != cudaSuccess) {
+      cudaGetLastError();
       p = nullptr;
-      throw Error{GFCC_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed"};
+      throw Error{GFCC_ERR_OOM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes failed"};
     }
+    p = static_cast<T*>(q);
     n = count;
   }
   void zero(cudaStream_t s) {

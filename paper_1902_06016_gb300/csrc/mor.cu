@@ -949,15 +949,12 @@ std::vector<int> ortho_block(gfcc_ctx* c, const cplx* Bs, int cap, int n_cur, cp
 // columns are copied, and large models at the biggest sizes are limited by memory, not by regrowths).
 static int grown_capacity(gfcc_ctx* c, int cap_now, int need, int quantum, double bytes_per_col) {
   int cap = std::max(need, std::max(quantum, 2 * cap_now));
-  size_t freeb = 0, totalb = 0;
-  if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) {
-    cudaGetLastError();
-    return cap;
-  }
+  size_t freeb = device_free_bytes();
+  if (freeb == 0) return cap;
   if ((double)cap * bytes_per_col > 0.5 * (double)freeb) {
     // memory is short: give back the scratch buffers first (they regrow on demand), then size exactly
     release_scratch(c);
-    if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) cudaGetLastError();
+    freeb = device_free_bytes();
     if ((double)cap * bytes_per_col > 0.5 * (double)freeb)
       cap = std::max(need, ((need + quantum - 1) / quantum) * quantum);
   }
@@ -973,6 +970,7 @@ void release_scratch(gfcc_ctx* c) {
   c->ws.nb_cap = 0;
   zgemm_work_check(c);
   zgemm_work_free(c);
+  GFCC_CUDA(cudaStreamSynchronize(c->stream));   // the frees have reached the pool before memory is measured
 }
 
 static void grow_model(gfcc_ctx* c, int need) {

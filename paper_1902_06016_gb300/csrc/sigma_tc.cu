@@ -551,9 +551,17 @@ static void sigma_lp_impl(gfcc_ctx* c, LpState& st, const VT* X, VT* Y, int nb, 
     prep_operand<Elem<K>, VT, PREP_OOOO>(X, o, v, nb, Boo, st.Kp, s);
     prep_operand<Elem<K>, VT, PREP_RING>(X, o, v, nb, Bring, st.Kr, s);
   }
+  // The up, oooo and down products are short or thin (K = Pv split, K = P, K = v + o): each moves more
+  // bytes than the tensor pipe needs time for, so they are also timed as one HBM-bound class whose
+  // algorithmic bytes are both operands read once and the output written once (read and written for
+  // the accumulating down product), at the operand element size es and FP32 outputs.
+  const double es = sizeof(T);
   // up (split-K) and its reduction
-  tc_gemm(K, TcOperand{st.Aup.p, v + o, st.Kpv}, TcOperand{Bup, nsm, st.Kpv}, st.up_part.p, nsm, v + o, nsm, 0, ksplit,
-          part_stride, st.err.p, s);
+  {
+    ProfScope pb(PROF_LP_SMALL_GEMMS, es * (double)(v + o + nsm) * (double)Pv + 4.0 * (double)(v + o) * nsm, s);
+    tc_gemm(K, TcOperand{st.Aup.p, v + o, st.Kpv}, TcOperand{Bup, nsm, st.Kpv}, st.up_part.p, nsm, v + o, nsm, 0,
+            ksplit, part_stride, st.err.p, s);
+  }
   {
     ProfScope pc(PROF_LP_COMBINE, 0.0, s);
     const int nk_split = (nk_up + ksplit - 1) / ksplit;
@@ -562,14 +570,21 @@ static void sigma_lp_impl(gfcc_ctx* c, LpState& st, const VT* X, VT* Y, int nb, 
     GFCC_LAUNCH_CHECK();
   }
   // oooo into C2 (as [P][(a,c,r)] = [(pij,a)][(c,r)])
-  tc_gemm(K, TcOperand{st.Woo.p, P, st.Kp}, TcOperand{Boo, noo, st.Kp}, st.C2.p, noo, P, noo, 0, 1, 0, st.err.p, s);
+  {
+    ProfScope pb(PROF_LP_SMALL_GEMMS, es * (double)(P + noo) * (double)P + 4.0 * (double)P * noo, s);
+    tc_gemm(K, TcOperand{st.Woo.p, P, st.Kp}, TcOperand{Boo, noo, st.Kp}, st.C2.p, noo, P, noo, 0, 1, 0, st.err.p, s);
+  }
   // down: C2 += [T2p | A21] [Xe ; r1]
   {
     ProfScope pp(PROF_LP_PREP, 0.0, s);
     prep_down_kernel<Elem<K>, float, VT><<<grid_for(nsm * st.Kvo), 256, 0, s>>>(st.up.p, nsm, X, o, v, nb, Bdn, st.Kvo);
     GFCC_LAUNCH_CHECK();
   }
-  tc_gemm(K, TcOperand{st.Adn.p, Pv, st.Kvo}, TcOperand{Bdn, nsm, st.Kvo}, st.C2.p, nsm, Pv, nsm, 1, 1, 0, st.err.p, s);
+  {
+    ProfScope pb(PROF_LP_SMALL_GEMMS, es * (double)(Pv + nsm) * (double)(v + o) + 8.0 * (double)Pv * nsm, s);
+    tc_gemm(K, TcOperand{st.Adn.p, Pv, st.Kvo}, TcOperand{Bdn, nsm, st.Kvo}, st.C2.p, nsm, Pv, nsm, 1, 1, 0, st.err.p,
+            s);
+  }
   // ring (its own profiling class and NVTX range, so that its launches can be timed and profiled alone)
   nvtxRangePushA("gfcc_ring_gemm");
   tc_gemm(K, TcOperand{st.Wr.p, ov, st.Kr}, TcOperand{Bring, nring, st.Kr}, st.CT.p, nring, ov, nring, 0, 1, 0,

@@ -73,6 +73,7 @@ PROTOTYPES = {
     "gfcc_tc_gemm": (C.c_int, [C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]),
     "gfcc_tc_gemm_noalloc": (C.c_int, [C.c_int, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
     "gfcc_autotune_info": (C.c_int, [C.c_int, _ip, _ip, _ip, _ip, _ip, _ip, _dp, _dp]),
+    "gfcc_release_cached_memory": (C.c_int, []),
     "gfcc_launch_count": (C.c_longlong, []),
     "gfcc_profile": (C.c_int, [C.c_int]),
     "gfcc_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_longlong), _dp, _dp]),
@@ -191,6 +192,13 @@ def autotune_report():
 
 def launch_count():
     return int(load().gfcc_launch_count())
+
+
+def release_cached_memory():
+    """Return the unused reserve of the library's device memory pools to the devices."""
+    rc = load().gfcc_release_cached_memory()
+    if rc != 0:
+        raise GfccError(rc, "gfcc_release_cached_memory failed")
 
 
 def profile(enable=True):
