@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1, help="(w, p) columns in the oracle sample")
     ap.add_argument("--ref-iters", type=int, default=6,
                     help="--impl reference: GMRES iterations of the oracle per timed step")
+    ap.add_argument("--model-only", action="store_true",
+                    help="--mode autograd: only the derivative-driven reduced model (no gradient checks)")
+    ap.add_argument("--max-batch", type=int, default=0,
+                    help="--mode autograd: largest batch of columns per solve in the reduced-model step (0: from memory)")
     ap.add_argument("--mode", default="pipeline", choices=["pipeline", "sigma", "peaks", "autograd"],
                     help="pipeline: the whole MOR step (default); sigma: one batch of sigma applications; "
                          "peaks: FP64, TF32 and BF16 GEMM rates of this GPU (library GEMMs, timing only); "
@@ -685,71 +689,85 @@ def run_autograd(args):
     ctx = Context(inp, tol=tol, precision=args.precision, stream=stream.cuda_stream, restart=args.restart)
     torch.cuda.synchronize()
     t_init = time.perf_counter() - t0
-    # 1. autograd forward + backward
-    w_t = torch.tensor(ws, dtype=torch.float64, requires_grad=True)
-    e_t = torch.tensor(eta0, dtype=torch.float64, requires_grad=True)
-    t2_t = torch.tensor(inp.t2, dtype=torch.float64, requires_grad=True)
-    t0 = time.perf_counter()
-    G = green(w_t, e_t, ctx, porb, t2=t2_t)
-    loss = (spectral(G) ** 2).sum() + (G.abs() ** 2).sum()
-    loss.backward()
-    torch.cuda.synchronize()
-    t_ad = time.perf_counter() - t0
-    G_np = G.detach().numpy()
-    # 2. finite differences
-    _, dw, de = ctx.green_derivatives(ws, eta0, porb)
-    t0 = time.perf_counter()
-    Gp = ctx.solve_full(ws + h, eta0, porb, want_A=False)["G"]
-    Gm = ctx.solve_full(ws - h, eta0, porb, want_A=False)["G"]
-    fd_w = (Gp - Gm) / (2 * h)
-    Gp = ctx.solve_full(ws, eta0 + h, porb, want_A=False)["G"]
-    Gm = ctx.solve_full(ws, eta0 - h, porb, want_A=False)["G"]
-    fd_e = (Gp - Gm) / (2 * h)
-    rng = np.random.default_rng(7)
-    dt2 = rng.standard_normal(inp.t2.shape)
-    dt2 = dt2 - dt2.transpose(1, 0, 2, 3)
-    dt2 = dt2 - dt2.transpose(0, 1, 3, 2)
-    dt2 *= np.abs(inp.t2).max() / np.abs(dt2).max()
+    if args.model_only:   # only the derivative-driven model, checked against full solves at 4 of the 20 frequencies
+        ws = ws[::5]
+        G_np = ctx.solve_full(ws, eta0, porb, want_A=False)["G"]
+        A_np = -np.imag(np.einsum("wpp->w", G_np)) / np.pi
+        out = {"metric": "G_pq(w) points/s, dG/dw-driven MOR + mixed precision", "value": None, "unit": UNIT,
+               "n_gpus": 1, "mode": "autograd (model only)", "higher_is_better": True, "data": "synthetic",
+               "dtype": f"c128 (f64 residuals, {args.precision} tensor-core inner sigma)",
+               "config": {"workload": args.workload, "o": o, "v": v, "D": inp.dim, "n_p": len(porb), "eta": eta0,
+                          "solve_tol": tol, "n_omega": nw, "max_batch": args.max_batch},
+               "seconds": {"input_generation_host": t_gen, "gfcc_init": t_init}}
 
-    def loss_at(t2x):
-        fields = {k: getattr(inp, k) for k in inp.__dataclass_fields__}
-        fields["t2"] = t2x                     # lambda_2 held fixed at the original amplitudes
-        cx = Context(synth.Inputs(**fields), tol=tol, precision=args.precision, stream=stream.cuda_stream,
-                     restart=args.restart)
-        Gx = cx.solve_full(ws, eta0, porb, want_A=False)["G"]
-        cx.close()
-        Ax = -np.imag(np.einsum("wpp->w", Gx)) / np.pi
-        return float((Ax ** 2).sum() + (np.abs(Gx) ** 2).sum())
+        def rel(a, b):
+            return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+    else:
+        # 1. autograd forward + backward
+        w_t = torch.tensor(ws, dtype=torch.float64, requires_grad=True)
+        e_t = torch.tensor(eta0, dtype=torch.float64, requires_grad=True)
+        t2_t = torch.tensor(inp.t2, dtype=torch.float64, requires_grad=True)
+        t0 = time.perf_counter()
+        G = green(w_t, e_t, ctx, porb, t2=t2_t)
+        loss = (spectral(G) ** 2).sum() + (G.abs() ** 2).sum()
+        loss.backward()
+        torch.cuda.synchronize()
+        t_ad = time.perf_counter() - t0
+        G_np = G.detach().numpy()
+        # 2. finite differences
+        _, dw, de = ctx.green_derivatives(ws, eta0, porb)
+        t0 = time.perf_counter()
+        Gp = ctx.solve_full(ws + h, eta0, porb, want_A=False)["G"]
+        Gm = ctx.solve_full(ws - h, eta0, porb, want_A=False)["G"]
+        fd_w = (Gp - Gm) / (2 * h)
+        Gp = ctx.solve_full(ws, eta0 + h, porb, want_A=False)["G"]
+        Gm = ctx.solve_full(ws, eta0 - h, porb, want_A=False)["G"]
+        fd_e = (Gp - Gm) / (2 * h)
+        rng = np.random.default_rng(7)
+        dt2 = rng.standard_normal(inp.t2.shape)
+        dt2 = dt2 - dt2.transpose(1, 0, 2, 3)
+        dt2 = dt2 - dt2.transpose(0, 1, 3, 2)
+        dt2 *= np.abs(inp.t2).max() / np.abs(dt2).max()
 
-    fd_t2 = (loss_at(inp.t2 + h * dt2) - loss_at(inp.t2 - h * dt2)) / (2 * h)
-    t_fd = time.perf_counter() - t0
-    ad_t2 = float((t2_t.grad.numpy() * dt2).sum())
-    # the scalar derivatives of the loss with respect to w_k and eta, from the finite differences of G
-    A_np = -np.imag(np.einsum("wpp->w", G_np)) / np.pi
+        def loss_at(t2x):
+            fields = {k: getattr(inp, k) for k in inp.__dataclass_fields__}
+            fields["t2"] = t2x                     # lambda_2 held fixed at the original amplitudes
+            cx = Context(synth.Inputs(**fields), tol=tol, precision=args.precision, stream=stream.cuda_stream,
+                         restart=args.restart)
+            Gx = cx.solve_full(ws, eta0, porb, want_A=False)["G"]
+            cx.close()
+            Ax = -np.imag(np.einsum("wpp->w", Gx)) / np.pi
+            return float((Ax ** 2).sum() + (np.abs(Gx) ** 2).sum())
 
-    def dloss(dG):
-        dA = -np.imag(np.einsum("wpp->w", dG)) / np.pi
-        return 2 * A_np * dA + 2 * np.real(np.conj(G_np) * dG).sum(axis=(1, 2))
+        fd_t2 = (loss_at(inp.t2 + h * dt2) - loss_at(inp.t2 - h * dt2)) / (2 * h)
+        t_fd = time.perf_counter() - t0
+        ad_t2 = float((t2_t.grad.numpy() * dt2).sum())
+        # the scalar derivatives of the loss with respect to w_k and eta, from the finite differences of G
+        A_np = -np.imag(np.einsum("wpp->w", G_np)) / np.pi
 
-    fd_loss_w = dloss(fd_w)
-    fd_loss_e = float(dloss(fd_e).sum())
+        def dloss(dG):
+            dA = -np.imag(np.einsum("wpp->w", dG)) / np.pi
+            return 2 * A_np * dA + 2 * np.real(np.conj(G_np) * dG).sum(axis=(1, 2))
 
-    def rel(a, b):
-        return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+        fd_loss_w = dloss(fd_w)
+        fd_loss_e = float(dloss(fd_e).sum())
 
-    out = {"metric": "G_pq(w) points/s, dG/dw-driven MOR + mixed precision", "value": None,
-           "unit": UNIT, "n_gpus": 1, "mode": "autograd", "higher_is_better": True, "data": "synthetic",
-           "dtype": f"c128 (f64 residuals, {args.precision} tensor-core inner sigma, adjoint on the transposed sigma)",
-           "config": {"workload": args.workload, "o": o, "v": v, "D": inp.dim, "n_p": len(porb), "eta": eta0,
-                      "fd_omegas": 20, "fd_step": h, "solve_tol": tol, "n_omega": nw},
-           "seconds": {"input_generation_host": t_gen, "gfcc_init": t_init,
-                       "autograd_forward_backward": t_ad, "finite_differences": t_fd},
-           "autograd_vs_fd": {
-               "dG_domega_rel_err": rel(dw, fd_w), "dG_deta_rel_err": rel(de, fd_e),
-               "dL_domega_rel_err": rel(w_t.grad.numpy(), fd_loss_w),
-               "dL_deta_rel_err": abs(float(e_t.grad) - fd_loss_e) / max(abs(fd_loss_e), 1e-300),
-               "dL_dt2_directional": {"autograd": ad_t2, "finite_difference": fd_t2,
-                                      "rel_err": abs(ad_t2 - fd_t2) / max(abs(fd_t2), 1e-300)}}}
+        def rel(a, b):
+            return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+        out = {"metric": "G_pq(w) points/s, dG/dw-driven MOR + mixed precision", "value": None,
+               "unit": UNIT, "n_gpus": 1, "mode": "autograd", "higher_is_better": True, "data": "synthetic",
+               "dtype": f"c128 (f64 residuals, {args.precision} tensor-core inner sigma, adjoint on the transposed sigma)",
+               "config": {"workload": args.workload, "o": o, "v": v, "D": inp.dim, "n_p": len(porb), "eta": eta0,
+                          "fd_omegas": 20, "fd_step": h, "solve_tol": tol, "n_omega": nw},
+               "seconds": {"input_generation_host": t_gen, "gfcc_init": t_init,
+                           "autograd_forward_backward": t_ad, "finite_differences": t_fd},
+               "autograd_vs_fd": {
+                   "dG_domega_rel_err": rel(dw, fd_w), "dG_deta_rel_err": rel(de, fd_e),
+                   "dL_domega_rel_err": rel(w_t.grad.numpy(), fd_loss_w),
+                   "dL_deta_rel_err": abs(float(e_t.grad) - fd_loss_e) / max(abs(fd_loss_e), 1e-300),
+                   "dL_dt2_directional": {"autograd": ad_t2, "finite_difference": fd_t2,
+                                          "rel_err": abs(ad_t2 - fd_t2) / max(abs(fd_t2), 1e-300)}}}
     print("autograd part: " + json.dumps(out), file=sys.stderr, flush=True)   # kept if the model step fails
     ctx.close()
 
@@ -758,7 +776,7 @@ def run_autograd(args):
     from paper_1902_06016_gb300 import GfccError
     grid = np.linspace(W["wmin"], W["wmax"], nw)
     ctx = Context(inp, tol=args.solve_tol, precision=args.precision, stream=stream.cuda_stream, restart=args.restart,
-                  deriv_indicator=True)
+                  deriv_indicator=True, max_batch=args.max_batch)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     try:
@@ -779,7 +797,8 @@ def run_autograd(args):
                       "G_rel_err_vs_full_at_fd_omegas": rel(at20["G"], G_np),
                       "spectrum": spectrum_peaks(ev["A"], grid)}
     except GfccError as e:
-        out["mor"] = {"error": str(e)}
+        free_b, total_b = torch.cuda.mem_get_info()
+        out["mor"] = {"error": str(e), "device_free_gb": free_b / 1e9, "device_total_gb": total_b / 1e9}
     ctx.close()
     return out
 
