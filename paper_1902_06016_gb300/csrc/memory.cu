@@ -74,7 +74,10 @@ void pool_free(void* p) {
   int dev = 0;
   if (cudaPointerGetAttributes(&at, p) == cudaSuccess) {
     dev = at.device;
-    pooled = dev >= 0 && dev < kMaxDev && g_pool[dev] != nullptr;
+    if (dev >= 0 && dev < kMaxDev) {
+      std::lock_guard<std::mutex> lk(g_pool_mu);
+      pooled = g_pool[dev] != nullptr;
+    }
   } else {
     cudaGetLastError();
   }
